@@ -1,0 +1,105 @@
+"""Poisson output step of Algorithm 1, Step 2 (Section 4.2, Appendix A).
+
+For each measurement the posterior of z given the Gaussian message
+N(p, tau_p) and the count y ~ Poisson(I0 e^{-z}) (Eq. Poisson_CT with no
+background term) is proportional to
+
+    exp( -(z - p)^2 / (2 tau_p) + y log(I0 e^{-z}) - I0 e^{-z} ).
+
+Laplace's method (Section 4.2 and Appendix A, after Tierney-Kadane) replaces
+it by a Gaussian at its mode z0 with variance the inverse curvature there.
+The appendix's algebra is garbled (the likelihood drops I0, a stray 1/M
+appears, the stationarity and curvature equations have sign errors); this
+oracle uses the corrected first-order reading:
+
+* the mode solves psi(z) = (z - p)/tau_p + y - I0 e^{-z} = 0; psi is strictly
+  increasing, so the root is unique;
+* Var = 1 / (1/tau_p + I0 e^{-z0});
+* s = (z0 - p)/tau_p (Eq. MMSEmm), tau_s_i = (1/tau_p)(1 - Var/tau_p)
+  (Section 3, Eq. for tau_s), i.e. w/(1 + tau_p w) with w = I0 e^{-z0};
+* tau_s = mean_i tau_s_i (Algorithm 1, Step 2).
+
+The root is found for delta = z0 - p (a change of variable that keeps s free
+of cancellation): psi(delta) = delta/tau_p + y - a e^{-delta},
+a = exp(log I0 - p).  The bracket is [min(0, L - p), max(0, L - p)] with
+L = log(I0/y) when y > 0, and [0, m - p + tau_p exp(log I0 - m)] with
+m = max(p, log I0) when y = 0 (psi is negative at the left end and positive
+at the right end in every case).  The search is Newton's method guarded by
+bisection (a step that leaves the bracket, or that shrinks |psi| too slowly,
+is replaced by the bracket midpoint), the classical safeguarded scheme.
+The integrals run over the whole real line (the paper's restriction to
+z >= 0 is not applied).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _psi(delta, y, a, tau_p):
+    with np.errstate(over="ignore", invalid="ignore"):
+        w = a * np.exp(-delta)
+        return delta / tau_p + y - w, 1.0 / tau_p + w, w
+
+
+def laplace_mode_delta(p, y, tau_p, log_I0, max_iter: int = 100, tol: float = 1e-13):
+    """delta = z0 - p for every measurement (vectorised safeguarded Newton)."""
+    p = np.asarray(p, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    with np.errstate(over="ignore", divide="ignore"):
+        a = np.exp(log_I0 - p)
+        L = np.where(y > 0, log_I0 - np.log(np.where(y > 0, y, 1.0)), 0.0)
+    m = np.maximum(p, log_I0)
+    hi0 = m - p + tau_p * np.exp(log_I0 - m)
+    lo = np.where(y > 0, np.minimum(0.0, L - p), 0.0)
+    hi = np.where(y > 0, np.maximum(0.0, L - p), hi0)
+    d = lo.copy()
+    dx_old = hi - lo
+    for _ in range(max_iter):
+        f, df, _w = _psi(d, y, a, tau_p)
+        lo = np.where(f < 0, d, lo)
+        hi = np.where(f > 0, d, hi)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            step = f / df
+        newton = d - step
+        bad = (~np.isfinite(newton)) | (newton <= lo) | (newton >= hi) \
+            | (np.abs(2.0 * f) > np.abs(dx_old * df))
+        nxt = np.where(bad, 0.5 * (lo + hi), newton)
+        nxt = np.where(f == 0, d, nxt)
+        dx_old = np.abs(nxt - d)
+        done = dx_old <= tol * np.abs(nxt)
+        d = nxt
+        if np.all(done):
+            break
+    return d
+
+
+def output_step(p, y, tau_p, I0):
+    """Algorithm 1, Step 2.  Returns (s, tau_s_i, z0, var) as fp64 arrays."""
+    log_I0 = float(np.log(I0))
+    d = laplace_mode_delta(p, y, tau_p, log_I0)
+    z0 = np.asarray(p, dtype=np.float64) + d
+    w = np.exp(log_I0 - z0)
+    var = 1.0 / (1.0 / tau_p + w)
+    s = d / tau_p
+    tau_s_i = w / (1.0 + tau_p * w)
+    return s, tau_s_i, z0, var
+
+
+def posterior_moments_quadrature(p, y, tau_p, I0, half_width: float = 12.0, n: int = 20001):
+    """Exact posterior mean and variance of z by quadrature (test reference).
+
+    Integrates the unnormalised posterior on a uniform grid of ``n`` points
+    spanning +-half_width posterior standard deviations around the Laplace
+    mode (the density is log-concave, so the mass outside is negligible).
+    Scalar inputs only.
+    """
+    d = float(laplace_mode_delta(np.array([p]), np.array([y]), tau_p, np.log(I0))[0])
+    z0 = p + d
+    sd = np.sqrt(1.0 / (1.0 / tau_p + I0 * np.exp(-z0)))
+    z = np.linspace(z0 - half_width * sd, z0 + half_width * sd, n)
+    logpost = -(z - p) ** 2 / (2 * tau_p) + y * (np.log(I0) - z) - I0 * np.exp(-z)
+    wgt = np.exp(logpost - logpost.max())
+    mass = np.trapezoid(wgt, z)
+    mean = np.trapezoid(wgt * z, z) / mass
+    var = np.trapezoid(wgt * (z - mean) ** 2, z) / mass
+    return mean, var

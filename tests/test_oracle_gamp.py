@@ -1,0 +1,53 @@
+"""Pins for the GAMP loop of Algorithm 1: state evolution on an i.i.d. Gaussian A
+(Section 3, Section 4.4) and qualitative checks of the CT solve."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gamp, philox
+from oracle.geometry import Geometry
+
+
+def test_state_evolution_tracks_empirical_mse():
+    # A_ij ~ N(0, 1/M), x ~ N(0, 1), AWGN channel, MMSE denoiser (linear):
+    # SE: tau_r = sigma^2 + tau_x / delta, tau_x+ = tau_r / (1 + tau_r).
+    N, M, sigma2, T = 4000, 2000, 0.01, 10
+    se = np.array(gamp.state_evolution_gaussian(M / N, sigma2, T))
+    mse = np.zeros(T)
+    taux = np.zeros(T)
+    for seed in range(5):
+        A, x, y = gamp.awgn_gaussian_problem(N, M, sigma2, seed)
+        frob2 = float(np.sum(A * A))
+        log = []
+
+        def record(t, xt):
+            mse[t - 1] += np.mean((xt - x) ** 2) / 5
+
+        gamp.gamp(lambda v: A @ v, lambda s: A.T @ s, frob2, M, N,
+                  gamp.awgn_gout(y, sigma2), gamp.gaussian_prior_denoiser,
+                  lambda t, n: philox.probe_normals(n, 100 + seed, t, 0), T,
+                  gamp.Options(eps_rel=1e-3), log=log, on_iter=record)
+        taux += np.array([lg.tau_x for lg in log]) / 5
+    assert np.all(np.abs(mse / se - 1) < 0.1)
+    assert np.all(np.abs(taux / se - 1) < 0.1)
+    assert np.all(np.diff(se) < 0) and se[-1] < 0.8 * se[0]
+
+
+@pytest.fixture(scope="module")
+def small_case():
+    c = synth.make_case("ellipse64_v30", seed=2000)
+    return c, Geometry(c["n"], c["n_views"], c["n_det"])
+
+
+def _psnr(a, b):
+    return 10 * np.log10(b.max() ** 2 / np.mean((a - b) ** 2))
+
+
+def test_ct_solve_error_falls_and_onsager_helps(small_case):
+    c, geom = small_case
+    opts = gamp.Options(c_tv=3.0, k_tv=20)
+    p = [_psnr(gamp.ct_solve(c["y"], c["I0"], geom, T, opts), c["mu"]) for T in (2, 8, 20)]
+    assert p[0] < p[1] < p[2] + 0.5
+    no = gamp.Options(c_tv=3.0, k_tv=20, onsager=False)
+    p_no = _psnr(gamp.ct_solve(c["y"], c["I0"], geom, 20, no), c["mu"])
+    assert p[2] > p_no + 3.0          # Section 7.1: the Onsager term matters
