@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the D-GAMP-CT hot path on one GB300 (or N independent replicas).
+
+One step = one full D-GAMP-CT solve (Algorithm 1: 30 iterations of Steps 1-4
+and the final mu = V^-1 x) of the 512 x 512 / 64-view / 729-bin ellipse
+workload with I0 = 1e5 and the prox-TV denoiser, counts resident in HBM.
+The metric is D-GAMP-CT iterations per second (whole job: all ranks).
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the launching stream; L2 is flushed (a 256 MiB write) between steps,
+outside the events; barrier + synchronize around the timed region; the time
+is the max over ranks.  ``e2e`` repeats the measurement through the host-
+buffer entry point (dgamp_ct_solve_host): counts copied in and mu copied out
+inside the timed region.
+
+Under torchrun (N > 1) every rank solves its own slice (seed 1000 + rank):
+replicas only, no data-path collective.
+
+``--impl reference`` times the FP64 CPU oracle instead, one iteration of the
+same workload per step, on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D-GAMP-CT iters/s at 512²/64 views; A+Aᵀ GB/s; learned vs plain at equal PSNR"
+UNIT = "iters/s"
+WORKLOAD = "ellipse512_v64"
+TV = dict(c_tv=3.0, k_tv=20)
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ----------------------------------------------------------------- helpers --
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _config(n_gpus):
+    from synth import CASES
+    n, nv, nd, ne, rmax, rect, I0, iters = CASES[WORKLOAD]
+    return {"workload": f"{WORKLOAD}: {n}x{n} image of {ne} seeded random ellipses + rectangle object, "
+                        f"parallel beam, {nv} views over 180 deg, {nd} detector bins, Poisson I0={I0:g}, "
+                        f"{iters} iterations, prox-TV denoiser (K={TV['k_tv']}, c={TV['c_tv']})",
+            "image": n, "views": nv, "detector_bins": nd, "I0": I0, "iters_per_step": iters,
+            "l2": "flushed between steps (256 MiB write, outside the timed events)",
+            "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "single GPU"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _psnr(mu, ref):
+    import numpy as np
+    mse = float(np.mean((mu - ref) ** 2))
+    return 10.0 * math.log10(float(ref.max()) ** 2 / mse) if mse > 0 else float("inf")
+
+
+# ------------------------------------------------------- oracle (CPU) leg --
+def _oracle_sample(iters: int, warm: int, seed: int):
+    """Run the FP64 oracle on the workload; returns per-iteration seconds."""
+    import numpy as np  # noqa: F401
+    import synth
+    from oracle import gamp, precond
+    from oracle.geometry import Geometry
+    c = synth.make_case(WORKLOAD, seed=seed)
+    g = Geometry(c["n"], c["n_views"], c["n_det"])
+    frob2 = precond.frobenius_sq(g)
+    stamps = [time.perf_counter()]
+    gamp.ct_solve(c["y"], c["I0"], g, warm + iters, gamp.Options(**TV), frob2=frob2,
+                  on_iter=lambda t, x: stamps.append(time.perf_counter()))
+    d = [b - a for a, b in zip(stamps[:-1], stamps[1:])]
+    return d[warm:]
+
+
+def _run_oracle_subprocess(iters: int, warm: int, seed: int = 1000):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench._oracle_sample({iters}, {warm}, {seed})))")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    per_iter = _run_oracle_subprocess(args.steps, args.warmup)
+    tot = sum(per_iter)
+    value = len(per_iter) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(per_iter),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(_config(1), step="one D-GAMP-CT iteration of the workload"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed iterations (after {args.warmup}) of the "
+                                       f"{WORKLOAD} solve, FP64 numpy oracle, one thread, "
+                                       f"||Phi~||_F^2 precomputed; host CPU {_cpu_model()}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- GPU leg ----
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import synth
+    import paper_1609_04661_gb300 as dg
+    from paper_1609_04661_gb300 import build as _build
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    dg.load()
+
+    case = synth.make_case(WORKLOAD, seed=1000 + rank)
+    T = case["iters"]
+    plan = dg.Plan(case["n"], case["n_views"], case["n_det"], **TV)
+    counts = torch.as_tensor(case["y"]).cuda()
+    mu = torch.empty((case["n"], case["n"]), device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.solve(counts, case["I0"], T, mu_out=mu)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+    except Exception:
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(st)
+        plan.solve(counts, case["I0"], T, mu_out=mu)
+        ev[k][1].record(st)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * T / (ms / 1e3)
+
+    mu_h = mu.cpu().numpy().astype(np.float64)
+    psnr = _psnr(mu_h, case["mu"])
+
+    # e2e: host buffers through dgamp_ct_solve_host
+    pin_c = torch.as_tensor(case["y"]).pin_memory()
+    pin_mu = torch.empty((case["n"], case["n"]), dtype=torch.float32).pin_memory()
+    c_np, mu_np = pin_c.numpy(), pin_mu.numpy()
+    plan.solve_host(c_np, case["I0"], T, mu_out=mu_np)
+    if dist is not None:
+        dist.barrier()
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.solve_host(c_np, case["I0"], T, mu_out=mu_np)
+        e2e_s += time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.steps * T / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(c_np.nbytes), "d2h_bytes_per_step": int(mu_np.nbytes)}
+
+    # per-kernel durations of one iteration, CUDA events on the launching stream
+    prof = plan.profile_iteration(reps=10)
+    iter_ms = sum(prof.values())
+    hbm, peak_kind = _peaks()
+    N, M = plan.N, plan.M
+    algo = {"project": 4 * (N + M), "filter_z": 8 * M, "output_step": 16 * M, "filter_s": 8 * M,
+            "backproject_update": 4 * (M + 2 * N), "probe_input": 8 * N, "tv_final": 2 * 12 * N + 12 * N}
+    for kname in prof:
+        if kname.startswith("tv_step"):
+            algo[kname] = 2 * (8 + 4 + 8) * N
+    groups = {"tv_steps": [k for k in prof if k.startswith("tv_step")]}
+    tv_ms = sum(prof[k] for k in groups["tv_steps"])
+    shares = {k: v / iter_ms for k, v in prof.items()}
+    dom = max(prof, key=prof.get)
+    achieved = algo[dom] / (prof[dom] * 1e-3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+            "algorithmic_bytes_per_launch": algo[dom], "launch_ms": prof[dom]}
+    a_at_bytes = algo["project"] + algo["backproject_update"]
+    a_at_ms = prof["project"] + prof["backproject_update"]
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            per_iter = _run_oracle_subprocess(args.cpu_iters, 0)
+            cpu = {"value": len(per_iter) / sum(per_iter), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{len(per_iter)} of {T} iterations of the {WORKLOAD} solve (seed 1000), FP64 "
+                             f"numpy oracle on one host thread ({_cpu_model()}), ||Phi~||_F^2 precomputed"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": _config(world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": int(args.steps * plan.solve_launches(T)),
+                "psnr_db": psnr,
+                "a_plus_at_gbs": a_at_bytes / (a_at_ms * 1e-3) / 1e9,
+                "iteration_ms": iter_ms, "kernel_ms": prof, "kernel_share": shares,
+                "tv_share": tv_ms / iter_ms}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * dgamp_ct.h -- C ABI of the GB300 D-GAMP-CT library (libdgampct.so).
+ *
+ * D-GAMP-CT (Perelli, Lexa, Can, Davies, "Compressive Computed Tomography
+ * Reconstruction through Denoising Approximate Message Passing") reconstructs
+ * an attenuation image mu from Poisson transmission counts
+ * y_i ~ Poisson(I0 exp(-[A mu]_i)) (Section 2.1, Eq. Poisson_CT) by running
+ * GAMP (Algorithm 1) in the preconditioned space x = V mu (Section 2.4,
+ * Eq. PPFT preconditioner) with a black-box denoiser (Section 4.3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Image: float32, row-major [n][n], row 0 at the top.  Pixel (ix, iy) has
+ *    centre X = ix - (n-1)/2, Y = (n-1)/2 - iy and unit size.
+ *  - Sinogram: float32, row-major [n_views][n_det] (detector axis contiguous).
+ *    Bin d sits at u_d = d - (n_det-1)/2; view k at theta_k = k pi / n_views
+ *    unless explicit angles are given; ray (theta, u) is the line
+ *    X cos(theta) + Y sin(theta) = u.
+ *  - A is Joseph's ray-driven linear-interpolation projector (Eq. linCT's
+ *    a_ij, which the paper leaves to a toolbox); A^T is its exact transpose.
+ *  - H is the detector-axis form of the preconditioner: per view, zero-pad to
+ *    P = smallest power of two >= 2 n_det, FFT, multiply by
+ *    g_k = sqrt(max(|k/P|, 1/(2P))) (signed frequency), inverse FFT, crop.
+ *    A V^-1 = H A (Eq. Aprecon via the Fourier slice theorem) and H = H^T, so
+ *    Phi~ = H A and Phi~^T = A^T H (Eq. precondAMP_op).
+ *  - Device pointers ("d_") must point to memory of the device that was
+ *    current when the plan was made, be 16-byte aligned and not overlap
+ *    unless stated.  Host pointers ("h_") may be pageable or pinned.
+ *  - Every call is asynchronous on the CUDA stream passed as `stream`
+ *    (a cudaStream_t; NULL = legacy default stream) unless stated, and the
+ *    caller keeps every buffer alive until the stream reaches the call.
+ *  - Ownership: the caller owns all input/output buffers and the stream; the
+ *    plan owns its workspace.  A plan must not be used from two streams at
+ *    the same time.
+ *  - Errors: every int-returning call returns DGAMP_CT_OK (0) or a negative
+ *    code below; no exception crosses the ABI.  On DGAMP_CT_ERR_CUDA the CUDA
+ *    error is kept and readable through dgamp_ct_last_cuda_error().
+ *    Numerical events that do not stop the method (the Newton cap, the tau_x
+ *    floor) are counted in dgamp_ct_stats, not returned as errors.
+ */
+#ifndef DGAMP_CT_H
+#define DGAMP_CT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGAMP_CT_OK                        0
+#define DGAMP_CT_ERR_INVALID_ARG          -1
+#define DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY -2
+#define DGAMP_CT_ERR_OOM                  -3
+#define DGAMP_CT_ERR_CUDA                 -4
+#define DGAMP_CT_ERR_TIMEOUT              -5
+#define DGAMP_CT_ERR_NONFINITE            -6
+
+/* Limits of this build (checked by dgamp_ct_plan). */
+#define DGAMP_CT_MAX_N        4096   /* image side                         */
+#define DGAMP_CT_MAX_VIEWS    4096
+#define DGAMP_CT_MAX_P        8192   /* detector FFT length, so n_det <= 4096 */
+
+typedef struct {
+    int32_t n;             /* image side, >= 2                                 */
+    int32_t n_views;       /* number of measured views (rows of S A, Eq. Phi_mtx) */
+    int32_t n_det;         /* detector bins per view, >= 2                      */
+    const double* angles;  /* optional host array of n_views angles (radians);
+                              NULL = theta_k = k pi / n_views.  Copied.         */
+} dgamp_ct_geometry;
+
+typedef struct {
+    int32_t  denoiser;     /* 0 = proximal TV (Section 6.3)                      */
+    int32_t  k_tv;         /* Chambolle iterations per denoiser call (fixed)     */
+    double   c_tv;         /* TV weight: lambda = c_tv * sqrt(tau_r)             */
+    double   eps_rel;      /* MC step: eps = eps_rel * max(max|r|, 1e-6) (Eq. MC_SURE) */
+    uint64_t seed;         /* probe key (Philox4x32-10), see dgamp_ct_probe      */
+    int32_t  slice_id;     /* probe counter word 2                              */
+    int32_t  onsager;      /* 1 = p = z - tau_p s_prev (Algorithm 1); 0 = drop it (Section 7.1) */
+    double   damp_x;       /* x <- damp_x x_new + (1-damp_x) x_old (Section 7.2); 1 = off */
+    double   damp_s;       /* s <- damp_s s_new + (1-damp_s) s_old; 1 = off      */
+    double   tau_x_floor;  /* tau_x = max(tau_r D', tau_x_floor * tau_r)        */
+    int32_t  use_graph;    /* 1 = replay one captured CUDA graph per iteration   */
+} dgamp_ct_options;
+
+typedef struct {
+    /* Optional caller-owned host arrays of length >= iters (NULL = skip).
+       Entry t-1 holds the value computed in iteration t of Algorithm 1.  */
+    double* tau_x;         /* tau_x^{t+1}                                       */
+    double* tau_p;         /* tau_p^t                                           */
+    double* tau_s;         /* tau_s^t                                           */
+    double* tau_r;         /* tau_r^t                                           */
+    double* div;           /* D'(r^t), Monte-Carlo estimate                     */
+    /* Filled on return (always, when stats is non-NULL). */
+    int32_t iters_done;
+    int32_t newton_capped; /* output-step elements that hit the iteration cap   */
+    int32_t tau_x_floored; /* iterations whose tau_x took the floor             */
+} dgamp_ct_stats;
+
+typedef struct dgamp_ct_plan_s* dgamp_ct_plan_t;
+
+/* Fill *opt with the defaults: TV, k_tv = 20, c_tv = 3, eps_rel = 1e-3,
+   seed = 12345, slice_id = 0, onsager = 1, no damping, floor 1e-6, graph on. */
+int dgamp_ct_default_options(dgamp_ct_options* opt);
+
+/* Build a plan for one geometry on the current CUDA device (Algorithm 1's
+   fixed quantities): view constants, filter gains, FFT twiddles,
+   ||Phi~||_F^2 (computed on the device in FP64; Algorithm 1, Steps 1 and 3)
+   and the workspace.  Synchronous.  opt may be NULL (defaults).
+   Errors: INVALID_ARG (NULL pointers, n < 2, n_det < 2, n_views < 1, limits),
+   OOM, CUDA. */
+int dgamp_ct_plan(const dgamp_ct_geometry* g, const dgamp_ct_options* opt,
+                  dgamp_ct_plan_t* out);
+
+/* Release the plan and its workspace (synchronises the device first).
+   NULL is ignored. */
+void dgamp_ct_plan_destroy(dgamp_ct_plan_t plan);
+
+/* Replace the plan's options (e.g. another seed or k_tv).  Invalidates the
+   captured graph; takes effect for the next call. */
+int dgamp_ct_set_options(dgamp_ct_plan_t plan, const dgamp_ct_options* opt);
+
+/* Scalars of the plan: ||Phi~||_F^2 (FP64) and the FFT length P. */
+int dgamp_ct_plan_info(dgamp_ct_plan_t plan, double* frob_sq, int32_t* fft_len);
+
+/* z = A x (precond = 0) or z = Phi~ x = H A x (precond = 1); Eq. linCT and
+   Algorithm 1, Step 1.  d_img [n][n] -> d_sino [n_views][n_det]. */
+int dgamp_ct_project(dgamp_ct_plan_t plan, const float* d_img, float* d_sino,
+                     int precond, void* stream);
+
+/* x = A^T s (precond = 0) or x = Phi~^T s = A^T H s (precond = 1);
+   Eq. precondAMP_op and Algorithm 1, Step 3.  d_sino -> d_img. */
+int dgamp_ct_backproject(dgamp_ct_plan_t plan, const float* d_sino, float* d_img,
+                         int precond, void* stream);
+
+/* d_out = H d_in on [n_views][n_det] sinograms (Eq. Aprecon, detector-axis
+   form).  d_in == d_out is allowed. */
+int dgamp_ct_filter(dgamp_ct_plan_t plan, const float* d_in, float* d_out, void* stream);
+
+/* Poisson output step (Algorithm 1, Step 2; Section 4.2 and Appendix A under
+   the corrected Laplace reading): p = z - tau_p s_prev, z0 = mode of
+   N(z; p, tau_p) Poisson(y; I0 e^{-z}), s = (z0 - p)/tau_p,
+   tau_s = mean_i I0 e^{-z0_i} / (1 + tau_p I0 e^{-z0_i}).
+   d_s_prev may be NULL (treated as 0) and may equal d_s.  *d_tau_s (one
+   device double) receives tau_s. */
+int dgamp_ct_output_step(dgamp_ct_plan_t plan, const float* d_z, const float* d_y,
+                         const float* d_s_prev, double I0, double tau_p,
+                         float* d_s, double* d_tau_s, void* stream);
+
+/* Proximal TV denoiser (Section 6.3): d_x = argmin 1/2||x - r||^2 + lambda TV(x)
+   by k_tv Chambolle iterations from a zero dual (tau = 1/8).  [n][n]. */
+int dgamp_ct_denoise_tv(dgamp_ct_plan_t plan, const float* d_r, double lambda,
+                        float* d_x, void* stream);
+
+/* Denoiser plus its Monte-Carlo divergence (Eq. D_in and Eq. MC_SURE, K = 1):
+   d_x = D(r), *d_div = b^T (D(r + eps b) - D(r)) / (N eps) with b the probe
+   of iteration t (dgamp_ct_probe) and eps = eps_rel max(max|r|, 1e-6).
+   lambda = c_tv sqrt(tau_r).  d_div: one device double. */
+int dgamp_ct_denoise_div(dgamp_ct_plan_t plan, const float* d_r, double tau_r,
+                         int32_t t, float* d_x, double* d_div, void* stream);
+
+/* The Gaussian probe b of iteration t: Philox4x32-10 (Salmon et al., SC'11)
+   with key (seed mod 2^32, seed >> 32) and counter (i/4, t, slice_id, 0),
+   word i%4, u = (word + 1/2) 2^-32, Box-Muller on word pairs (0,1), (2,3).
+   If d_words != NULL it receives the raw words (uint32, n of them). */
+int dgamp_ct_probe(dgamp_ct_plan_t plan, int32_t t, int64_t n, float* d_b,
+                   uint32_t* d_words, void* stream);
+
+/* Image-domain preconditioner map (Algorithm 1, return line; Eq. precondAMP):
+   inverse = 1: d_out = V^-1 d_in (radial gain sqrt(max(rho, 1/(2P)))),
+   inverse = 0: d_out = V d_in (reciprocal gain); both on a 2n x 2n
+   zero-padded 2-D FFT, cropped to [n][n].  d_in == d_out is allowed. */
+int dgamp_ct_precond_image(dgamp_ct_plan_t plan, const float* d_in, float* d_out,
+                           int inverse, void* stream);
+
+/* D-GAMP-CT, Algorithm 1: x = 0, tau_x = 1, then `iters` iterations of
+   Steps 1-4 with the Poisson output step and the plan's denoiser, and
+   d_mu_out = V^-1 x.  d_counts: [n_views][n_det] float32 counts (integer
+   valued, >= 0).  d_x_out (nullable) receives the final x.  With stats !=
+   NULL the call synchronises the stream and fills it; otherwise it only
+   enqueues work.  Errors: INVALID_ARG (iters < 1, I0 <= 0 or not finite),
+   CUDA, NONFINITE (only with stats: a non-finite scalar appeared). */
+int dgamp_ct_solve(dgamp_ct_plan_t plan, const float* d_counts, double I0,
+                   int32_t iters, float* d_mu_out, float* d_x_out,
+                   dgamp_ct_stats* stats, void* stream);
+
+/* dgamp_ct_solve on HOST buffers: copies h_counts to the device, solves and
+   copies mu back to h_mu_out; returns after the result is in h_mu_out. */
+int dgamp_ct_solve_host(dgamp_ct_plan_t plan, const float* h_counts, double I0,
+                        int32_t iters, float* h_mu_out, dgamp_ct_stats* stats,
+                        void* stream);
+
+/* Number of kernels one dgamp_ct_solve enqueues for `iters` iterations. */
+int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t plan, int32_t iters);
+
+/* Kernel-level timing of one Algorithm 1 iteration: enqueues the iteration's
+   kernels one at a time on `stream` with a CUDA event before and after each,
+   `reps` times, and writes the mean duration (ms) of each kernel to h_ms
+   (host array of `cap` doubles) in launch order: A x, H (z), output step,
+   H (s), A^T + update, probe input, k_tv Chambolle steps, final denoiser step.
+   *count receives the number of kernels.  The iterations run on the plan's
+   current state (normally that of the last dgamp_ct_solve) and advance it.
+   Synchronous. */
+int dgamp_ct_profile_iteration(dgamp_ct_plan_t plan, int32_t reps, double* h_ms, int32_t cap,
+                               int32_t* count, void* stream);
+
+/* Human-readable text for an error code (static storage). */
+const char* dgamp_ct_strerror(int code);
+
+/* The CUDA error (cudaError_t value) behind the last DGAMP_CT_ERR_CUDA. */
+int dgamp_ct_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGAMP_CT_H */

@@ -109,17 +109,19 @@ def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
 
 
 def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
-             opts: Options | None = None, return_x: bool = False, log=None):
+             opts: Options | None = None, return_x: bool = False, log=None,
+             frob2: float | None = None, on_iter=None):
     """D-GAMP-CT on one slice with the prox-TV denoiser (parity unpinned).
 
     The full reconstruction has no closed form and the paper prints no
     synthetic result; it is checked only through its pinned parts and the
     tests' qualitative checks (error falls over the iterations, the Onsager
-    term helps).
+    term helps).  ``frob2`` may pass a precomputed ||Phi~||_F^2.
     """
     opts = opts or Options()
     yv = np.asarray(y, dtype=np.float64).reshape(-1)
-    frob2 = _pre.frobenius_sq(geom)
+    if frob2 is None:
+        frob2 = _pre.frobenius_sq(geom)
 
     def Phi(x):
         return _pre.project(x, geom)
@@ -139,7 +141,7 @@ def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
         return _philox.probe_normals(n, opts.seed, t, opts.slice_id)
 
     x = gamp(Phi, PhiT, frob2, geom.M, geom.N, gout, denoise_factory, probe, T,
-             opts, shape=(geom.n, geom.n), log=log)
+             opts, shape=(geom.n, geom.n), log=log, on_iter=on_iter)
     mu = _pre.v_inverse(x, geom)
     return (mu, x) if return_x else mu
 

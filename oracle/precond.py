@@ -20,8 +20,9 @@ Readings where the paper is silent or singular:
   is kept un-normalised, so x = V mu does not change units with the view
   count.  GAMP absorbs the scale through ||Phi~||_F^2 (Algorithm 1).
 * the image-domain map V^-1 used for the returned mu (Algorithm 1, return
-  line) is the 2-D radial gain sqrt(max(rho, f0)) on a 2n x 2n zero-padded
-  FFT, cropped back to n x n; V uses the reciprocal gain.
+  line) is the 2-D radial gain sqrt(max(rho, f0)) on an m x m zero-padded
+  FFT, m the smallest power of two >= 2n (the paper gives no padding),
+  cropped back to n x n; V uses the reciprocal gain.
 """
 from __future__ import annotations
 
@@ -107,7 +108,7 @@ def _radial_gain_2d(m: int, P: int, inverse: bool) -> np.ndarray:
 
 def _image_filter(img: np.ndarray, geom: Geometry, inverse: bool) -> np.ndarray:
     n = geom.n
-    m = 2 * n
+    m = 1 << (2 * n - 1).bit_length()      # smallest power of two >= 2n
     pad = np.zeros((m, m))
     pad[:n, :n] = img
     spec = np.fft.fft2(pad) * _radial_gain_2d(m, geom.P, inverse)

@@ -1,0 +1,10 @@
+"""GB300-native D-GAMP-CT: the per-iteration hot path of denoising GAMP for
+sparse-view CT (Perelli, Lexa, Can, Davies) as hand-written sm_103a CUDA
+kernels behind the C ABI in include/dgamp_ct.h.
+
+``Plan`` (see :mod:`paper_1609_04661_gb300.binding`) wraps one geometry;
+build the library first with ``python -m paper_1609_04661_gb300.build``.
+"""
+from .binding import DgampError, Plan, default_options, load  # noqa: F401
+
+__all__ = ["Plan", "DgampError", "default_options", "load"]

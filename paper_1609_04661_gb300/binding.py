@@ -1,0 +1,295 @@
+"""Thin ctypes binding of libdgampct.so (include/dgamp_ct.h).
+
+Argument marshalling only: every call forwards device pointers of torch
+tensors and the current CUDA stream to the C ABI; all arithmetic runs in the
+library's CUDA kernels.  Importing this module does not touch the GPU; a
+missing library raises immediately (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdgampct.so")
+
+OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED_GEOMETRY", -3: "OOM", -4: "CUDA", -5: "TIMEOUT",
+          -6: "NONFINITE"}
+
+#: every symbol include/dgamp_ct.h declares
+EXPORTS = (
+    "dgamp_ct_default_options", "dgamp_ct_plan", "dgamp_ct_plan_destroy", "dgamp_ct_set_options",
+    "dgamp_ct_plan_info", "dgamp_ct_project", "dgamp_ct_backproject", "dgamp_ct_filter",
+    "dgamp_ct_output_step", "dgamp_ct_denoise_tv", "dgamp_ct_denoise_div", "dgamp_ct_probe",
+    "dgamp_ct_precond_image", "dgamp_ct_solve", "dgamp_ct_solve_host", "dgamp_ct_solve_launches",
+    "dgamp_ct_strerror", "dgamp_ct_last_cuda_error", "dgamp_ct_profile_iteration",
+)
+
+
+class DgampError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what}: {ERRORS.get(code, code)}"
+        if code == -4 and _lib is not None:
+            msg += f" (cudaError {_lib.dgamp_ct_last_cuda_error()})"
+        super().__init__(msg)
+
+
+class Geometry(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_views", C.c_int32), ("n_det", C.c_int32),
+                ("angles", C.POINTER(C.c_double))]
+
+
+class Options(C.Structure):
+    _fields_ = [("denoiser", C.c_int32), ("k_tv", C.c_int32), ("c_tv", C.c_double),
+                ("eps_rel", C.c_double), ("seed", C.c_uint64), ("slice_id", C.c_int32),
+                ("onsager", C.c_int32), ("damp_x", C.c_double), ("damp_s", C.c_double),
+                ("tau_x_floor", C.c_double), ("use_graph", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("tau_x", C.POINTER(C.c_double)), ("tau_p", C.POINTER(C.c_double)),
+                ("tau_s", C.POINTER(C.c_double)), ("tau_r", C.POINTER(C.c_double)),
+                ("div", C.POINTER(C.c_double)), ("iters_done", C.c_int32),
+                ("newton_capped", C.c_int32), ("tau_x_floored", C.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1609_04661_gb300.build` "
+                          "(the CUDA library is required; there is no CPU path)")
+    lib = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "dgamp_ct_default_options": (C.c_int, [C.POINTER(Options)]),
+        "dgamp_ct_plan": (C.c_int, [C.POINTER(Geometry), C.POINTER(Options), C.POINTER(vp)]),
+        "dgamp_ct_plan_destroy": (None, [vp]),
+        "dgamp_ct_set_options": (C.c_int, [vp, C.POINTER(Options)]),
+        "dgamp_ct_plan_info": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i32)]),
+        "dgamp_ct_project": (C.c_int, [vp, vp, vp, C.c_int, vp]),
+        "dgamp_ct_backproject": (C.c_int, [vp, vp, vp, C.c_int, vp]),
+        "dgamp_ct_filter": (C.c_int, [vp, vp, vp, vp]),
+        "dgamp_ct_output_step": (C.c_int, [vp, vp, vp, vp, dbl, dbl, vp, vp, vp]),
+        "dgamp_ct_denoise_tv": (C.c_int, [vp, vp, dbl, vp, vp]),
+        "dgamp_ct_denoise_div": (C.c_int, [vp, vp, dbl, i32, vp, vp, vp]),
+        "dgamp_ct_probe": (C.c_int, [vp, i32, i64, vp, vp, vp]),
+        "dgamp_ct_precond_image": (C.c_int, [vp, vp, vp, C.c_int, vp]),
+        "dgamp_ct_solve": (C.c_int, [vp, vp, dbl, i32, vp, vp, C.POINTER(Stats), vp]),
+        "dgamp_ct_solve_host": (C.c_int, [vp, vp, dbl, i32, vp, C.POINTER(Stats), vp]),
+        "dgamp_ct_solve_launches": (i64, [vp, i32]),
+        "dgamp_ct_strerror": (C.c_char_p, [C.c_int]),
+        "dgamp_ct_last_cuda_error": (C.c_int, []),
+        "dgamp_ct_profile_iteration": (C.c_int, [vp, i32, C.POINTER(dbl), i32, C.POINTER(i32), vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_options(**over) -> Options:
+    o = Options()
+    _check(load().dgamp_ct_default_options(C.byref(o)), "default_options")
+    for k, v in over.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise DgampError(rc, what)
+
+
+def _ptr(t, n_expect=None, name="tensor"):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if n_expect is not None and t.numel() != n_expect:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n_expect}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Plan:
+    """One geometry's plan (dgamp_ct_plan).  Tensors are float32 CUDA tensors."""
+
+    def __init__(self, n: int, n_views: int, n_det: int, angles=None, **options):
+        self._lib = load()
+        self.n, self.n_views, self.n_det = int(n), int(n_views), int(n_det)
+        g = Geometry(self.n, self.n_views, self.n_det, None)
+        self._angles = None
+        if angles is not None:
+            self._angles = np.ascontiguousarray(angles, dtype=np.float64)
+            g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
+        self.options = default_options(**options)
+        h = C.c_void_p()
+        _check(self._lib.dgamp_ct_plan(C.byref(g), C.byref(self.options), C.byref(h)), "dgamp_ct_plan")
+        self._h = h
+        fr = C.c_double()
+        P = C.c_int32()
+        _check(self._lib.dgamp_ct_plan_info(h, C.byref(fr), C.byref(P)), "plan_info")
+        self.frob_sq = fr.value
+        self.fft_len = P.value
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dgamp_ct_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def N(self):
+        return self.n * self.n
+
+    @property
+    def M(self):
+        return self.n_views * self.n_det
+
+    def set_options(self, **options):
+        o = self.options
+        for k, v in options.items():
+            setattr(o, k, v)
+        _check(self._lib.dgamp_ct_set_options(self._h, C.byref(o)), "set_options")
+
+    def _img(self, like=None):
+        import torch
+        return torch.empty((self.n, self.n), dtype=torch.float32, device="cuda")
+
+    def _sino(self):
+        import torch
+        return torch.empty((self.n_views, self.n_det), dtype=torch.float32, device="cuda")
+
+    # -- single steps --
+    def project(self, img, precond: bool = False, out=None):
+        out = self._sino() if out is None else out
+        _check(self._lib.dgamp_ct_project(self._h, _ptr(img, self.N, "img"), _ptr(out, self.M, "out"),
+                                          int(precond), _stream()), "dgamp_ct_project")
+        return out
+
+    def backproject(self, sino, precond: bool = False, out=None):
+        out = self._img() if out is None else out
+        _check(self._lib.dgamp_ct_backproject(self._h, _ptr(sino, self.M, "sino"), _ptr(out, self.N, "out"),
+                                              int(precond), _stream()), "dgamp_ct_backproject")
+        return out
+
+    def filter(self, sino, out=None):
+        out = self._sino() if out is None else out
+        _check(self._lib.dgamp_ct_filter(self._h, _ptr(sino, self.M, "sino"), _ptr(out, self.M, "out"),
+                                         _stream()), "dgamp_ct_filter")
+        return out
+
+    def output_step(self, z, y, s_prev, I0: float, tau_p: float):
+        import torch
+        s = self._sino()
+        ts = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check(self._lib.dgamp_ct_output_step(
+            self._h, _ptr(z, self.M, "z"), _ptr(y, self.M, "y"),
+            _ptr(s_prev, self.M, "s_prev") if s_prev is not None else None,
+            float(I0), float(tau_p), _ptr(s, self.M, "s"), C.c_void_p(ts.data_ptr()), _stream()),
+            "dgamp_ct_output_step")
+        return s, ts
+
+    def denoise_tv(self, r, lam: float):
+        x = self._img()
+        _check(self._lib.dgamp_ct_denoise_tv(self._h, _ptr(r, self.N, "r"), float(lam), _ptr(x, self.N, "x"),
+                                             _stream()), "dgamp_ct_denoise_tv")
+        return x
+
+    def denoise_div(self, r, tau_r: float, t: int):
+        import torch
+        x = self._img()
+        dv = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check(self._lib.dgamp_ct_denoise_div(self._h, _ptr(r, self.N, "r"), float(tau_r), int(t),
+                                              _ptr(x, self.N, "x"), C.c_void_p(dv.data_ptr()), _stream()),
+               "dgamp_ct_denoise_div")
+        return x, dv
+
+    def probe(self, t: int, n: int, words: bool = False):
+        import torch
+        b = torch.empty(n, dtype=torch.float32, device="cuda")
+        w = torch.empty(n, dtype=torch.int32, device="cuda") if words else None
+        _check(self._lib.dgamp_ct_probe(self._h, int(t), int(n), C.c_void_p(b.data_ptr()),
+                                        C.c_void_p(w.data_ptr()) if w is not None else None, _stream()),
+               "dgamp_ct_probe")
+        return (b, w) if words else b
+
+    def precond_image(self, img, inverse: bool = True, out=None):
+        out = self._img() if out is None else out
+        _check(self._lib.dgamp_ct_precond_image(self._h, _ptr(img, self.N, "img"), _ptr(out, self.N, "out"),
+                                                int(inverse), _stream()), "dgamp_ct_precond_image")
+        return out
+
+    # -- the loop --
+    def solve(self, counts, I0: float, iters: int, with_stats: bool = False, mu_out=None, x_out=None):
+        mu = self._img() if mu_out is None else mu_out
+        st, arrays = None, None
+        if with_stats:
+            arrays = {k: np.zeros(iters) for k in ("tau_x", "tau_p", "tau_s", "tau_r", "div")}
+            st = Stats(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrays.values()], 0, 0, 0)
+        rc = self._lib.dgamp_ct_solve(self._h, _ptr(counts, self.M, "counts"), float(I0), int(iters),
+                                      _ptr(mu, self.N, "mu_out"),
+                                      _ptr(x_out, self.N, "x_out") if x_out is not None else None,
+                                      C.byref(st) if st is not None else None, _stream())
+        _check(rc, "dgamp_ct_solve")
+        if with_stats:
+            arrays.update(iters_done=st.iters_done, newton_capped=st.newton_capped,
+                          tau_x_floored=st.tau_x_floored)
+            return mu, arrays
+        return mu
+
+    def solve_host(self, counts: np.ndarray, I0: float, iters: int, mu_out: np.ndarray | None = None):
+        c = np.ascontiguousarray(counts, dtype=np.float32)
+        if c.size != self.M:
+            raise ValueError("counts has the wrong size")
+        mu = np.empty((self.n, self.n), dtype=np.float32) if mu_out is None else mu_out
+        rc = self._lib.dgamp_ct_solve_host(self._h, c.ctypes.data_as(C.c_void_p), float(I0), int(iters),
+                                           mu.ctypes.data_as(C.c_void_p), None, _stream())
+        _check(rc, "dgamp_ct_solve_host")
+        return mu
+
+    def profile_iteration(self, reps: int = 5):
+        """Mean per-kernel durations (ms) of one iteration, in launch order."""
+        cap = 8 + max(int(self.options.k_tv), 0)
+        arr = (C.c_double * cap)()
+        cnt = C.c_int32()
+        _check(self._lib.dgamp_ct_profile_iteration(self._h, int(reps), arr, cap, C.byref(cnt), _stream()),
+               "dgamp_ct_profile_iteration")
+        names = ["project", "filter_z", "output_step", "filter_s", "backproject_update", "probe_input"]
+        k = cnt.value - len(names) - 1
+        names += [f"tv_step{i}" for i in range(k)] + ["tv_final"]
+        return dict(zip(names, [arr[i] for i in range(cnt.value)]))
+
+    def solve_launches(self, iters: int) -> int:
+        return int(self._lib.dgamp_ct_solve_launches(self._h, int(iters)))

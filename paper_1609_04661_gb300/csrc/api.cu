@@ -1,0 +1,514 @@
+// Host side of the C ABI declared in include/dgamp_ct.h: plan construction,
+// the single-step entry points, and the D-GAMP-CT loop (Algorithm 1) with its
+// per-iteration kernel sequence captured once into a CUDA graph.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace dgct {
+
+static thread_local int g_last_cuda = 0;
+
+int cuda_fail(cudaError_t e) {
+    g_last_cuda = (int)e;
+    return DGAMP_CT_ERR_CUDA;
+}
+
+static void free_ws(Workspace& w) {
+    void* ptrs[] = {w.XR, w.XC, w.x, w.r, w.p, w.zraw, w.z, w.s, w.hs, w.y, w.fft2d, w.partial,
+                    w.S, w.log, w.vc, w.gain, w.tw, w.tw2, w.scratch_d};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    w = Workspace{};
+}
+
+template <typename T>
+static int dalloc(T** p, size_t count) {
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) + 16);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        *p = nullptr;
+        return DGAMP_CT_ERR_OOM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    return DGAMP_CT_OK;
+}
+
+#define DGCT_TRY(x)                 \
+    do {                            \
+        int _rc = (x);              \
+        if (_rc != DGAMP_CT_OK) return _rc; \
+    } while (0)
+
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+static bool options_ok(const dgamp_ct_options* o) {
+    if (o->denoiser != 0) return false;
+    if (o->k_tv < 0 || o->k_tv > 100000) return false;
+    if (!std::isfinite(o->c_tv) || o->c_tv < 0) return false;
+    if (!std::isfinite(o->eps_rel) || o->eps_rel <= 0) return false;
+    if (!(o->damp_x > 0 && o->damp_x <= 1) || !(o->damp_s > 0 && o->damp_s <= 1)) return false;
+    if (!(o->tau_x_floor >= 0) || !std::isfinite(o->tau_x_floor)) return false;
+    return true;
+}
+
+// Per-view Joseph constants (see ViewConst), computed in FP64 and rounded.
+static void view_constants(int n, int nd, const std::vector<double>& ang, std::vector<ViewConst>& out) {
+    const double c = 0.5 * (n - 1), cd = 0.5 * (nd - 1);
+    out.resize(ang.size());
+    for (size_t k = 0; k < ang.size(); ++k) {
+        const double st = std::sin(ang[k]), ct = std::cos(ang[k]);
+        ViewConst v{};
+        if (std::fabs(st) >= std::fabs(ct)) {
+            // fractional row at column s: c - (u_d - (s - c) cos)/sin, u_d = d - cd
+            v.col = 1;
+            v.a0 = (float)(c + cd / st - c * ct / st);
+            v.a_step = (float)(ct / st);
+            v.a_det = (float)(-1.0 / st);
+            v.w = (float)(1.0 / std::fabs(st));
+        } else {
+            // fractional column at row s: (u_d - (c - s) sin)/cos + c
+            v.col = 0;
+            v.a0 = (float)(c - cd / ct - c * st / ct);
+            v.a_step = (float)(st / ct);
+            v.a_det = (float)(1.0 / ct);
+            v.w = (float)(1.0 / std::fabs(ct));
+        }
+        out[k] = v;
+    }
+}
+
+static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
+    Workspace& w = pl->ws;
+    const size_t N = (size_t)pl->N, M = (size_t)pl->M;
+    const size_t img_staged = (size_t)pl->n * pl->ldp;
+    DGCT_TRY(dalloc(&w.XR, img_staged));
+    DGCT_TRY(dalloc(&w.XC, img_staged));
+    DGCT_TRY(dalloc(&w.x, N));
+    DGCT_TRY(dalloc(&w.r, 2 * N));
+    DGCT_TRY(dalloc(&w.p, 4 * N));
+    DGCT_TRY(dalloc(&w.zraw, M));
+    DGCT_TRY(dalloc(&w.z, M));
+    DGCT_TRY(dalloc(&w.s, M));
+    DGCT_TRY(dalloc(&w.hs, M));
+    DGCT_TRY(dalloc(&w.y, M));
+    DGCT_TRY(dalloc(&w.fft2d, (size_t)pl->m2 * pl->m2));
+    const size_t tiles32 = (size_t)((pl->n + 31) / 32) * ((pl->n + 31) / 32);
+    pl->max_partials = 1024;
+    const size_t nparts = tiles32 > (size_t)pl->max_partials ? tiles32 : (size_t)pl->max_partials;
+    DGCT_TRY(dalloc(&w.partial, nparts));
+    DGCT_TRY(dalloc(&w.S, 1));
+    DGCT_TRY(dalloc(&w.log, (size_t)kMaxIters));
+    DGCT_TRY(dalloc(&w.vc, (size_t)pl->nv));
+    DGCT_TRY(dalloc(&w.gain, (size_t)pl->P));
+    DGCT_TRY(dalloc(&w.tw, (size_t)pl->P / 2));
+    DGCT_TRY(dalloc(&w.tw2, (size_t)pl->m2 / 2));
+    DGCT_TRY(dalloc(&w.scratch_d, (size_t)(pl->nd + 1) + 2 * pl->nd + pl->nv + (size_t)pl->nv * pl->nd));
+
+    DGCT_CUDA(cudaMemset(w.XR, 0, img_staged * sizeof(float)));
+    DGCT_CUDA(cudaMemset(w.XC, 0, img_staged * sizeof(float)));
+    {
+        DevScalars s0;
+        std::memset(&s0, 0, sizeof(s0));
+        s0.tau_x = 1.0;
+        s0.t = 1u;
+        s0.logI0 = std::log(1e4);
+        DGCT_CUDA(cudaMemcpy(w.S, &s0, sizeof(s0), cudaMemcpyHostToDevice));
+    }
+
+    std::vector<ViewConst> vc;
+    view_constants(pl->n, pl->nd, ang, vc);
+    DGCT_CUDA(cudaMemcpy(w.vc, vc.data(), vc.size() * sizeof(ViewConst), cudaMemcpyHostToDevice));
+
+    const int P = pl->P;
+    std::vector<float> g(P);
+    for (int k = 0; k < P; ++k) {
+        const int kk = k <= P / 2 ? k : P - k;
+        g[k] = (float)std::sqrt(std::fmax((double)kk / P, 1.0 / (2.0 * P)));
+    }
+    DGCT_CUDA(cudaMemcpy(w.gain, g.data(), P * sizeof(float), cudaMemcpyHostToDevice));
+    const double two_pi = 6.283185307179586476925286766559;
+    auto twiddles = [&](int L, float2* dst) -> int {
+        std::vector<float2> t(L / 2);
+        for (int k = 0; k < L / 2; ++k)
+            t[k] = make_float2((float)std::cos(two_pi * k / L), (float)std::sin(two_pi * k / L));
+        DGCT_CUDA(cudaMemcpy(dst, t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        return DGAMP_CT_OK;
+    };
+    DGCT_TRY(twiddles(P, w.tw));
+    DGCT_TRY(twiddles(pl->m2, w.tw2));
+
+    // ||Phi~||_F^2 on the device in FP64
+    double* ang_dev = w.scratch_d + (pl->nd + 1) + 2 * pl->nd;
+    DGCT_CUDA(cudaMemcpy(ang_dev, ang.data(), ang.size() * sizeof(double), cudaMemcpyHostToDevice));
+    DGCT_TRY(launch_frobenius(pl));
+    std::vector<double> terms((size_t)pl->nv * pl->nd);
+    DGCT_CUDA(cudaMemcpy(terms.data(), ang_dev + pl->nv, terms.size() * sizeof(double),
+                         cudaMemcpyDeviceToHost));
+    double tot = 0.0;
+    for (double v : terms) tot += v;
+    pl->frob2 = tot;
+    DGCT_CUDA(cudaMemcpy(&w.S->frob2, &tot, sizeof(double), cudaMemcpyHostToDevice));
+    const int smem_need = 2 * (P > pl->m2 ? P : pl->m2) * (int)sizeof(float2);
+    DGCT_TRY(fft_set_smem_limits(smem_need > 48 * 1024 ? smem_need : 48 * 1024));
+    return DGAMP_CT_OK;
+}
+
+// -------------------------------------------------------------- solve ----
+// One iteration of Algorithm 1 (Steps 1-4); every scalar it needs lives in
+// DevScalars, so the same launch sequence serves every iteration.
+// With `ev` non-NULL, ev[i] is recorded before kernel i and ev[count] after
+// the last one (kernel-level timing on the launching stream).
+static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* ev = nullptr) {
+    Workspace& w = pl->ws;
+    int k = 0;
+    auto mark = [&]() -> int {
+        if (ev) DGCT_CUDA(cudaEventRecord(ev[k], st));
+        ++k;
+        return DGAMP_CT_OK;
+    };
+    DGCT_TRY(mark());
+    DGCT_TRY(launch_project(pl, w.zraw, st));                          // Step 1: A x
+    DGCT_TRY(mark());
+    DGCT_TRY(launch_filter(pl, w.zraw, w.z, st));                       //         H A x
+    DGCT_TRY(mark());
+    DGCT_TRY(launch_output_step(pl, w.z, w.y, w.s, 1, 1, 0.0, 0.0, nullptr, st));  // Step 2
+    DGCT_TRY(mark());
+    DGCT_TRY(launch_filter(pl, w.s, w.hs, st));                         // Step 3: H s
+    DGCT_TRY(mark());
+    DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st));            //         r = x + tau_r A^T H s
+    DGCT_TRY(mark());
+    DGCT_TRY(launch_probe_input(pl, 0, st));                            // Step 4: r + eps b
+    int fb = -1;
+    if (!ev) {
+        DGCT_TRY(launch_tv_iters(pl, 2, 1, 0.0, st, &fb));              //         D(r), D(r + eps b)
+    } else {
+        // the same Chambolle launches, one event each
+        const int K = tv_active(pl, 1, 0.0) ? pl->opt.k_tv : 0;
+        for (int i = 0; i < K; ++i) {
+            DGCT_TRY(mark());
+            DGCT_TRY(launch_tv_step(pl, 2, 1, 0.0, i, st, &fb));
+        }
+    }
+    DGCT_TRY(mark());
+    DGCT_TRY(launch_tv_final(pl, 2, fb, 1, 0.0, w.x, 1, 0, nullptr, st));  //      x, D', tau_x
+    DGCT_TRY(mark());
+    return DGAMP_CT_OK;
+}
+
+static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
+    const int tv = (pl->opt.k_tv > 0 && pl->opt.c_tv > 0) ? pl->opt.k_tv : 0;
+    return 7 + tv;
+}
+
+static void drop_graph(dgamp_ct_plan_s* pl) {
+    if (pl->graph) cudaGraphExecDestroy(pl->graph);
+    pl->graph = nullptr;
+}
+
+static int ensure_graph(dgamp_ct_plan_s* pl) {
+    if (pl->graph) return DGAMP_CT_OK;
+    cudaStream_t cs;
+    DGCT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_fail(e);
+    }
+    int rc = enqueue_iteration(pl, cs);
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc != DGAMP_CT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(&pl->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        pl->graph = nullptr;
+        return cuda_fail(e);
+    }
+    return DGAMP_CT_OK;
+}
+
+}  // namespace dgct
+
+using namespace dgct;
+
+extern "C" {
+
+int dgamp_ct_default_options(dgamp_ct_options* o) {
+    if (!o) return DGAMP_CT_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->denoiser = 0;
+    o->k_tv = 20;
+    o->c_tv = 3.0;
+    o->eps_rel = 1e-3;
+    o->seed = 12345;
+    o->slice_id = 0;
+    o->onsager = 1;
+    o->damp_x = 1.0;
+    o->damp_s = 1.0;
+    o->tau_x_floor = 1e-6;
+    o->use_graph = 1;
+    return DGAMP_CT_OK;
+}
+
+int dgamp_ct_plan(const dgamp_ct_geometry* g, const dgamp_ct_options* opt, dgamp_ct_plan_t* out) {
+    if (!g || !out) return DGAMP_CT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (g->n < 2 || g->n > DGAMP_CT_MAX_N || g->n_views < 1 || g->n_views > DGAMP_CT_MAX_VIEWS ||
+        g->n_det < 2)
+        return DGAMP_CT_ERR_INVALID_ARG;
+    dgamp_ct_options o;
+    if (opt) o = *opt; else dgamp_ct_default_options(&o);
+    if (!options_ok(&o)) return DGAMP_CT_ERR_INVALID_ARG;
+    const int P = 1 << ilog2(2 * g->n_det);
+    if (P > DGAMP_CT_MAX_P) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
+    std::vector<double> ang(g->n_views);
+    for (int k = 0; k < g->n_views; ++k) {
+        ang[k] = g->angles ? g->angles[k] : (double)k * (3.14159265358979323846 / g->n_views);
+        if (!std::isfinite(ang[k])) return DGAMP_CT_ERR_INVALID_ARG;
+    }
+    dgamp_ct_plan_s* pl = new (std::nothrow) dgamp_ct_plan_s();
+    if (!pl) return DGAMP_CT_ERR_OOM;
+    cudaGetDevice(&pl->device);
+    pl->n = g->n;
+    pl->nv = g->n_views;
+    pl->nd = g->n_det;
+    pl->P = P;
+    pl->logP = ilog2(P);
+    pl->m2 = 1 << ilog2(2 * g->n);
+    pl->logm2 = ilog2(pl->m2);
+    pl->ldp = ((g->n + 2 * kPad + 3) / 4) * 4;
+    pl->N = (int64_t)g->n * g->n;
+    pl->M = (int64_t)g->n_views * g->n_det;
+    pl->opt = o;
+    int rc = plan_alloc(pl, ang);
+    if (rc != DGAMP_CT_OK) {
+        free_ws(pl->ws);
+        delete pl;
+        return rc;
+    }
+    *out = pl;
+    return DGAMP_CT_OK;
+}
+
+void dgamp_ct_plan_destroy(dgamp_ct_plan_t pl) {
+    if (!pl) return;
+    cudaDeviceSynchronize();
+    drop_graph(pl);
+    free_ws(pl->ws);
+    delete pl;
+}
+
+int dgamp_ct_set_options(dgamp_ct_plan_t pl, const dgamp_ct_options* opt) {
+    if (!pl || !opt || !options_ok(opt)) return DGAMP_CT_ERR_INVALID_ARG;
+    pl->opt = *opt;
+    drop_graph(pl);
+    return DGAMP_CT_OK;
+}
+
+int dgamp_ct_plan_info(dgamp_ct_plan_t pl, double* frob_sq, int32_t* fft_len) {
+    if (!pl) return DGAMP_CT_ERR_INVALID_ARG;
+    if (frob_sq) *frob_sq = pl->frob2;
+    if (fft_len) *fft_len = pl->P;
+    return DGAMP_CT_OK;
+}
+
+int dgamp_ct_project(dgamp_ct_plan_t pl, const float* d_img, float* d_sino, int precond, void* stream) {
+    if (!pl || !d_img || !d_sino) return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    DGCT_TRY(launch_stage_image(pl, d_img, st));
+    if (!precond) return launch_project(pl, d_sino, st);
+    DGCT_TRY(launch_project(pl, pl->ws.zraw, st));
+    return launch_filter(pl, pl->ws.zraw, d_sino, st);
+}
+
+int dgamp_ct_backproject(dgamp_ct_plan_t pl, const float* d_sino, float* d_img, int precond, void* stream) {
+    if (!pl || !d_sino || !d_img) return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float* src = d_sino;
+    if (precond) {
+        DGCT_TRY(launch_filter(pl, d_sino, pl->ws.hs, st));
+        src = pl->ws.hs;
+    }
+    return launch_backproject(pl, src, nullptr, d_img, 0, st);
+}
+
+int dgamp_ct_filter(dgamp_ct_plan_t pl, const float* d_in, float* d_out, void* stream) {
+    if (!pl || !d_in || !d_out) return DGAMP_CT_ERR_INVALID_ARG;
+    return launch_filter(pl, d_in, d_out, (cudaStream_t)stream);
+}
+
+int dgamp_ct_output_step(dgamp_ct_plan_t pl, const float* d_z, const float* d_y, const float* d_s_prev,
+                         double I0, double tau_p, float* d_s, double* d_tau_s, void* stream) {
+    if (!pl || !d_z || !d_y || !d_s || !d_tau_s) return DGAMP_CT_ERR_INVALID_ARG;
+    if (!(I0 > 0) || !std::isfinite(I0) || !(tau_p > 0) || !std::isfinite(tau_p))
+        return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int use_prev = 0;
+    if (d_s_prev) {
+        if (d_s_prev != d_s)
+            DGCT_CUDA(cudaMemcpyAsync(d_s, d_s_prev, (size_t)pl->M * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, st));
+        use_prev = 1;
+    }
+    return launch_output_step(pl, d_z, d_y, d_s, use_prev, 0, tau_p, std::log(I0), d_tau_s, st);
+}
+
+int dgamp_ct_denoise_tv(dgamp_ct_plan_t pl, const float* d_r, double lambda, float* d_x, void* stream) {
+    if (!pl || !d_r || !d_x || !(lambda >= 0) || !std::isfinite(lambda)) return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    DGCT_CUDA(cudaMemcpyAsync(pl->ws.r, d_r, (size_t)pl->N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    int fb = -1;
+    if (lambda > 0) DGCT_TRY(launch_tv_iters(pl, 1, 0, lambda, st, &fb));
+    return launch_tv_final(pl, 1, fb, 0, lambda, d_x, 0, 0, nullptr, st);
+}
+
+int dgamp_ct_denoise_div(dgamp_ct_plan_t pl, const float* d_r, double tau_r, int32_t t, float* d_x,
+                         double* d_div, void* stream) {
+    if (!pl || !d_r || !d_x || !d_div || !(tau_r > 0) || !std::isfinite(tau_r) || t < 1)
+        return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    DGCT_CUDA(cudaMemcpyAsync(pl->ws.r, d_r, (size_t)pl->N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    DGCT_TRY(launch_absmax(pl, pl->ws.r, st));
+    DGCT_TRY(launch_probe_input(pl, t, st));
+    const double lambda = pl->opt.c_tv * std::sqrt(tau_r);
+    int fb = -1;
+    if (lambda > 0) DGCT_TRY(launch_tv_iters(pl, 2, 0, lambda, st, &fb));
+    return launch_tv_final(pl, 2, fb, 0, lambda, d_x, 0, t, d_div, st);
+}
+
+int dgamp_ct_probe(dgamp_ct_plan_t pl, int32_t t, int64_t n, float* d_b, uint32_t* d_words, void* stream) {
+    if (!pl || n < 0 || (!d_b && !d_words)) return DGAMP_CT_ERR_INVALID_ARG;
+    if (n == 0) return DGAMP_CT_OK;
+    return launch_probe(pl, (unsigned)t, n, d_b, d_words, (cudaStream_t)stream);
+}
+
+int dgamp_ct_precond_image(dgamp_ct_plan_t pl, const float* d_in, float* d_out, int inverse, void* stream) {
+    if (!pl || !d_in || !d_out) return DGAMP_CT_ERR_INVALID_ARG;
+    return launch_precond_image(pl, d_in, d_out, inverse, (cudaStream_t)stream);
+}
+
+int dgamp_ct_profile_iteration(dgamp_ct_plan_t pl, int32_t reps, double* h_ms, int32_t cap,
+                               int32_t* count, void* stream) {
+    if (!pl || reps < 1 || !h_ms || !count) return DGAMP_CT_ERR_INVALID_ARG;
+    const int nk = kernels_per_iteration(pl);
+    *count = nk;
+    if (cap < nk) return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<cudaEvent_t> ev(nk + 1, nullptr);
+    for (auto& e : ev) DGCT_CUDA(cudaEventCreate(&e));
+    std::vector<double> acc(nk, 0.0);
+    int rc = DGAMP_CT_OK;
+    for (int r = 0; r < reps && rc == DGAMP_CT_OK; ++r) {
+        rc = enqueue_iteration(pl, st, ev.data());
+        if (rc != DGAMP_CT_OK) break;
+        cudaError_t e = cudaEventSynchronize(ev[nk]);
+        if (e != cudaSuccess) { rc = cuda_fail(e); break; }
+        for (int i = 0; i < nk; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            acc[i] += ms;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int i = 0; i < nk; ++i) h_ms[i] = acc[i] / reps;
+    return rc;
+}
+
+int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t pl, int32_t iters) {
+    if (!pl || iters < 0) return -1;
+    // per iteration, plus the image staging before and the three V^-1 passes after
+    return (int64_t)iters * kernels_per_iteration(pl) + 4;
+}
+
+int dgamp_ct_solve(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t iters, float* d_mu_out,
+                   float* d_x_out, dgamp_ct_stats* stats, void* stream) {
+    if (!pl || !d_counts || !d_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
+    if (iters < 1 || iters > kMaxIters || !(I0 > 0) || !std::isfinite(I0)) return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace& w = pl->ws;
+    const size_t N = (size_t)pl->N, M = (size_t)pl->M;
+    // Algorithm 1 initialisation: x = 0, tau_x = 1, s_prev = 0
+    DGCT_CUDA(cudaMemcpyAsync(w.y, d_counts, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    DGCT_CUDA(cudaMemsetAsync(w.x, 0, N * sizeof(float), st));
+    DGCT_CUDA(cudaMemsetAsync(w.s, 0, M * sizeof(float), st));
+    DGCT_TRY(launch_stage_image(pl, w.x, st));
+    static thread_local DevScalars init;   // copied by value before the call returns
+    std::memset(&init, 0, sizeof(init));
+    init.tau_x = 1.0;
+    init.frob2 = pl->frob2;
+    init.logI0 = std::log(I0);
+    init.t = 1u;
+    DGCT_CUDA(cudaMemcpyAsync(w.S, &init, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+    DGCT_CUDA(cudaStreamSynchronize(st));   // `init` is host stack-like storage
+    if (pl->opt.use_graph) {
+        DGCT_TRY(ensure_graph(pl));
+        for (int t = 0; t < iters; ++t) DGCT_CUDA(cudaGraphLaunch(pl->graph, st));
+    } else {
+        for (int t = 0; t < iters; ++t) DGCT_TRY(enqueue_iteration(pl, st));
+    }
+    DGCT_TRY(launch_precond_image(pl, w.x, d_mu_out, 1, st));           // mu = V^-1 x
+    if (d_x_out) DGCT_CUDA(cudaMemcpyAsync(d_x_out, w.x, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (!stats) return DGAMP_CT_OK;
+    DGCT_CUDA(cudaStreamSynchronize(st));
+    DevScalars hs;
+    DGCT_CUDA(cudaMemcpy(&hs, w.S, sizeof(hs), cudaMemcpyDeviceToHost));
+    std::vector<IterLog> lg(iters);
+    DGCT_CUDA(cudaMemcpy(lg.data(), w.log, iters * sizeof(IterLog), cudaMemcpyDeviceToHost));
+    for (int t = 0; t < iters; ++t) {
+        if (stats->tau_x) stats->tau_x[t] = lg[t].tau_x;
+        if (stats->tau_p) stats->tau_p[t] = lg[t].tau_p;
+        if (stats->tau_s) stats->tau_s[t] = lg[t].tau_s;
+        if (stats->tau_r) stats->tau_r[t] = lg[t].tau_r;
+        if (stats->div) stats->div[t] = lg[t].div;
+    }
+    stats->iters_done = (int32_t)(hs.t - 1u);
+    stats->newton_capped = (int32_t)hs.newton_capped;
+    stats->tau_x_floored = (int32_t)hs.floored;
+    if (hs.nonfinite) return DGAMP_CT_ERR_NONFINITE;
+    return DGAMP_CT_OK;
+}
+
+int dgamp_ct_solve_host(dgamp_ct_plan_t pl, const float* h_counts, double I0, int32_t iters, float* h_mu_out,
+                        dgamp_ct_stats* stats, void* stream) {
+    if (!pl || !h_counts || !h_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)pl->N, M = (size_t)pl->M;
+    // counts land in the hs buffer (free until the first filter of s), mu in r
+    DGCT_CUDA(cudaMemcpyAsync(pl->ws.hs, h_counts, M * sizeof(float), cudaMemcpyHostToDevice, st));
+    int rc = dgamp_ct_solve(pl, pl->ws.hs, I0, iters, pl->ws.r, nullptr, stats, stream);
+    if (rc != DGAMP_CT_OK && rc != DGAMP_CT_ERR_NONFINITE) return rc;
+    DGCT_CUDA(cudaMemcpyAsync(h_mu_out, pl->ws.r, N * sizeof(float), cudaMemcpyDeviceToHost, st));
+    DGCT_CUDA(cudaStreamSynchronize(st));
+    return rc;
+}
+
+const char* dgamp_ct_strerror(int code) {
+    switch (code) {
+        case DGAMP_CT_OK: return "ok";
+        case DGAMP_CT_ERR_INVALID_ARG: return "invalid argument";
+        case DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY: return "unsupported geometry";
+        case DGAMP_CT_ERR_OOM: return "out of device memory";
+        case DGAMP_CT_ERR_CUDA: return "CUDA error (see dgamp_ct_last_cuda_error)";
+        case DGAMP_CT_ERR_TIMEOUT: return "device wait timed out";
+        case DGAMP_CT_ERR_NONFINITE: return "non-finite scalar in the iteration";
+        default: return "unknown error";
+    }
+}
+
+int dgamp_ct_last_cuda_error(void) { return g_last_cuda; }
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// Shared-memory FFTs for the Radon preconditioner (Section 2.4, Eq. Aprecon).
+//
+//  * H on sinograms: one block filters two views at once, packed as the real
+//    and imaginary parts of one complex line.  Because the gain g is real and
+//    even, filtering a + i b gives H a + i H b, so one forward and one inverse
+//    complex FFT of length P serve two views.
+//  * V^-1 / V on images: a 2-D zero-padded FFT done as row FFTs, column FFTs
+//    with the radial gain applied between the forward and inverse column
+//    transforms, and inverse row FFTs.  It runs once per solve.
+//
+// The transform is a radix-2 Stockham autosort FFT (natural order in and
+// out, ping-pong between two shared-memory buffers): stage Ns (1, 2, 4, ...)
+// combines a[j] and a[j + P/2] with the twiddle exp(-+ 2 pi i (j mod Ns)/(2 Ns))
+// into b[2 (j - j mod Ns) + j mod Ns] and the same index + Ns.
+#include "internal.cuh"
+
+namespace dgct {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// tw[t] = (cos(2 pi t / P), sin(2 pi t / P)), t < P/2.  dir = -1 forward, +1 inverse.
+__device__ float2* fft_stockham(float2* a, float2* b, int P, const float2* __restrict__ tw,
+                                float dir) {
+    const int half = P >> 1;
+    const int nthr = blockDim.x;
+    for (int Ns = 1; Ns < P; Ns <<= 1) {
+        const int tstride = half / Ns;
+        for (int j = threadIdx.x; j < half; j += nthr) {
+            const int k = j & (Ns - 1);
+            float2 w = __ldg(tw + k * tstride);
+            w.y *= dir;
+            const float2 v0 = a[j];
+            const float2 t = cmul(a[j + half], w);
+            const int o = ((j - k) << 1) + k;
+            b[o] = make_float2(v0.x + t.x, v0.y + t.y);
+            b[o + Ns] = make_float2(v0.x - t.x, v0.y - t.y);
+        }
+        __syncthreads();
+        float2* tmp = a;
+        a = b;
+        b = tmp;
+    }
+    return a;
+}
+
+// ------------------------------------------------------------ H on views --
+__global__ void __launch_bounds__(512)
+k_filter_views(const float* in, float* out, int nv, int nd, int P,
+               const float* __restrict__ gain, const float2* __restrict__ tw) {
+    extern __shared__ float2 smem[];
+    float2* a = smem;
+    float2* b = smem + P;
+    const int va = 2 * blockIdx.x, vb = va + 1;
+    const bool hasb = vb < nv;
+    const float* ra = in + (size_t)va * nd;
+    const float* rb = in + (size_t)vb * nd;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        float2 v = make_float2(0.f, 0.f);
+        if (i < nd) {
+            v.x = ra[i];
+            if (hasb) v.y = rb[i];
+        }
+        a[i] = v;
+    }
+    __syncthreads();
+    float2* r = fft_stockham(a, b, P, tw, -1.f);
+    float2* o = (r == a) ? b : a;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const float g = __ldg(gain + i);
+        const float2 v = r[i];
+        r[i] = make_float2(v.x * g, v.y * g);
+    }
+    __syncthreads();
+    r = fft_stockham(r, o, P, tw, 1.f);
+    const float sc = 1.0f / (float)P;
+    float* wa = out + (size_t)va * nd;
+    float* wb = out + (size_t)vb * nd;
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+        const float2 v = r[i];
+        wa[i] = v.x * sc;
+        if (hasb) wb[i] = v.y * sc;
+    }
+}
+
+int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaStream_t st) {
+    const int P = pl->P;
+    const size_t sm = (size_t)2 * P * sizeof(float2);
+    const int thr = P >= 1024 ? 512 : (P / 2 >= 32 ? P / 2 : 32);
+    k_filter_views<<<(pl->nv + 1) / 2, thr, sm, st>>>(in, out, pl->nv, pl->nd, P, pl->ws.gain,
+                                                      pl->ws.tw);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// ------------------------------------------------------- V^-1 / V image --
+// pass 1: rows iy < n of the m x m padded image -> C[iy][:]
+__global__ void __launch_bounds__(512)
+k_img_rows_fwd(const float* __restrict__ img, int n, int m, const float2* __restrict__ tw,
+               float2* __restrict__ C) {
+    extern __shared__ float2 smem[];
+    float2* a = smem;
+    float2* b = smem + m;
+    const int iy = blockIdx.x;
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+        a[i] = make_float2(i < n ? img[(size_t)iy * n + i] : 0.f, 0.f);
+    __syncthreads();
+    float2* r = fft_stockham(a, b, m, tw, -1.f);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) C[(size_t)iy * m + i] = r[i];
+}
+
+// pass 2: every column kx: forward FFT over rows (rows >= n are zero),
+// radial gain, inverse FFT; rows < n are stored back.
+__global__ void __launch_bounds__(512)
+k_img_cols(float2* __restrict__ C, int n, int m, const float2* __restrict__ tw, float f0,
+           int inverse_gain) {
+    extern __shared__ float2 smem[];
+    float2* a = smem;
+    float2* b = smem + m;
+    const int kx = blockIdx.x;
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+        a[i] = i < n ? C[(size_t)i * m + kx] : make_float2(0.f, 0.f);
+    __syncthreads();
+    float2* r = fft_stockham(a, b, m, tw, -1.f);
+    float2* o = (r == a) ? b : a;
+    const float fx = (float)(kx <= m / 2 ? kx : kx - m) / (float)m;
+    for (int ky = threadIdx.x; ky < m; ky += blockDim.x) {
+        const float fy = (float)(ky <= m / 2 ? ky : ky - m) / (float)m;
+        const float rho = sqrtf(fx * fx + fy * fy);
+        float g = sqrtf(fmaxf(rho, f0));
+        if (inverse_gain) g = 1.0f / g;
+        const float2 v = r[ky];
+        r[ky] = make_float2(v.x * g, v.y * g);
+    }
+    __syncthreads();
+    r = fft_stockham(r, o, m, tw, 1.f);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) C[(size_t)i * m + kx] = r[i];
+}
+
+// pass 3: inverse row FFTs, real part of the first n columns, scaled by 1/m^2.
+__global__ void __launch_bounds__(512)
+k_img_rows_inv(const float2* __restrict__ C, int n, int m, const float2* __restrict__ tw,
+               float* __restrict__ out) {
+    extern __shared__ float2 smem[];
+    float2* a = smem;
+    float2* b = smem + m;
+    const int iy = blockIdx.x;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) a[i] = C[(size_t)iy * m + i];
+    __syncthreads();
+    float2* r = fft_stockham(a, b, m, tw, 1.f);
+    const float sc = 1.0f / ((float)m * (float)m);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[(size_t)iy * n + i] = r[i].x * sc;
+}
+
+int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out, int inverse,
+                         cudaStream_t st) {
+    const int n = pl->n, m = pl->m2;
+    const size_t sm = (size_t)2 * m * sizeof(float2);
+    const int thr = m >= 1024 ? 512 : (m / 2 >= 32 ? m / 2 : 32);
+    const float f0 = 1.0f / (2.0f * (float)pl->P);
+    k_img_rows_fwd<<<n, thr, sm, st>>>(in, n, m, pl->ws.tw2, pl->ws.fft2d);
+    DGCT_LAUNCH_CHECK();
+    // V^-1 applies sqrt(max(rho, f0)); V applies its reciprocal
+    k_img_cols<<<m, thr, sm, st>>>(pl->ws.fft2d, n, m, pl->ws.tw2, f0, inverse ? 0 : 1);
+    DGCT_LAUNCH_CHECK();
+    k_img_rows_inv<<<n, thr, sm, st>>>(pl->ws.fft2d, n, m, pl->ws.tw2, out);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+int fft_set_smem_limits(int bytes) {
+    DGCT_CUDA(cudaFuncSetAttribute(k_filter_views, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    DGCT_CUDA(cudaFuncSetAttribute(k_img_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    DGCT_CUDA(cudaFuncSetAttribute(k_img_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    DGCT_CUDA(cudaFuncSetAttribute(k_img_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return DGAMP_CT_OK;
+}
+
+}  // namespace dgct

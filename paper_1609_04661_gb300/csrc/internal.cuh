@@ -1,0 +1,201 @@
+// Internal declarations of the GB300 D-GAMP-CT library: plan layout, device
+// scalar block, and the small device helpers that several kernels share.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dgamp_ct.h"
+
+namespace dgct {
+
+constexpr int kPad = 4;            // zero guard cells on each side of a staged image line
+constexpr int kMaxIters = 1 << 16; // bound on one solve's iteration count (log size)
+constexpr int kNewtonCap = 64;     // output-step iteration cap
+
+// Joseph constants of one view.  The ray of bin d meets march line s (a
+// column for col = 1, a row for col = 0) at fractional index
+//   pos(d, s) = fmaf(s, a_step, fmaf(d, a_det, a0))
+// across that line; the projector and the back-projector evaluate exactly this
+// expression so their weights agree bit for bit.
+struct ViewConst {
+    float a0, a_step, a_det, w;   // w = path length per step (1/|sin| or 1/|cos|)
+    int col;                      // 1: march over columns, interpolate along rows
+    int pad[3];
+};
+
+// Scalars of Algorithm 1 that live on the device for the whole solve.
+struct DevScalars {
+    double tau_x;       // tau_x^t (Step 4 of the previous iteration; 1 at start)
+    double tau_p;       // Step 1
+    double tau_s;       // Step 2
+    double tau_r;       // Step 3
+    double div;         // Step 4, D'
+    double eps;         // MC step of Step 4
+    double frob2;       // ||Phi~||_F^2
+    double logI0;
+    unsigned int rmax_bits;     // max |r| (float bits; |r| >= 0 so integer order works)
+    unsigned int t;             // current iteration, 1-based
+    unsigned int done_out;      // last-block counters
+    unsigned int done_div;
+    unsigned int newton_capped;
+    unsigned int floored;
+    unsigned int nonfinite;
+    unsigned int pad;
+};
+
+// Per-iteration log record (what dgamp_ct_stats exposes).
+struct IterLog { double tau_x, tau_p, tau_s, tau_r, div, eps; };
+
+struct Workspace {
+    float* XR = nullptr;     // staged image, rows padded:  [n][ldp]
+    float* XC = nullptr;     // staged transpose:            [n][ldp]
+    float* x = nullptr;      // current x  [n][n]
+    float* r = nullptr;      // r and r + eps b  [2][n][n]
+    float2* p = nullptr;     // TV duals, ping-pong: [2 buffers][2 images][n][n]
+    float* zraw = nullptr;   // A x           [M]
+    float* z = nullptr;      // H A x         [M]
+    float* s = nullptr;      // s (in place over s_prev) [M]
+    float* hs = nullptr;     // H s           [M]
+    float* y = nullptr;      // counts        [M]
+    float2* fft2d = nullptr; // [2n][2n] complex scratch for V / V^-1
+    double* partial = nullptr;     // block partial sums
+    DevScalars* S = nullptr;
+    IterLog* log = nullptr;        // [kMaxIters]
+    ViewConst* vc = nullptr;       // [n_views]
+    float* gain = nullptr;         // [P]
+    float2* tw = nullptr;          // [P/2]   twiddles exp(-2 pi i k / P)
+    float2* tw2 = nullptr;         // [n]     twiddles of length 2n
+    double* scratch_d = nullptr;   // plan-time FP64 scratch
+};
+
+}  // namespace dgct
+
+struct dgamp_ct_plan_s {
+    int device = 0;
+    int n = 0, nv = 0, nd = 0, P = 0, logP = 0, m2 = 0, logm2 = 0, ldp = 0;
+    int64_t N = 0, M = 0;
+    double frob2 = 0.0;
+    dgamp_ct_options opt{};
+    dgct::Workspace ws;
+    int max_partials = 0;
+    // captured iteration graph
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;   // stream the graph was captured for (identity only)
+    int kernels_per_iter = 0;
+};
+
+namespace dgct {
+
+// ---------------------------------------------------------------- helpers --
+__device__ __forceinline__ float joseph_pos(const ViewConst& c, int d, int s) {
+    return fmaf((float)s, c.a_step, fmaf((float)d, c.a_det, c.a0));
+}
+
+// Split a position into its left tap and the interpolation fraction.
+__device__ __forceinline__ void joseph_tap(float pos, int& i0, float& f) {
+    float fl = floorf(pos);
+    i0 = (int)fl;
+    f = pos - fl;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over a block (any size that is a multiple of 32, <= 1024); result valid in thread 0.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* smem32) {
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int l = tid & 31, w = tid >> 5;
+    v = warp_sum(v);
+    if (l == 0) smem32[w] = v;
+    __syncthreads();
+    T out = T(0);
+    if (w == 0) {
+        out = (l < nw) ? smem32[l] : T(0);
+        out = warp_sum(out);
+    }
+    __syncthreads();
+    return out;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Four probe normals of block g for iteration t (Box-Muller on word pairs).
+__device__ __forceinline__ float4 probe4(unsigned g, unsigned t, unsigned slice, uint2 key) {
+    uint4 w = philox4x32_10(make_uint4(g, t, slice, 0u), key);
+    const float s32 = 2.3283064365386963e-10f;  // 2^-32
+    float u0 = fmaf(__uint2float_rn(w.x), s32, 0.5f * s32);
+    float u1 = fmaf(__uint2float_rn(w.y), s32, 0.5f * s32);
+    float u2 = fmaf(__uint2float_rn(w.z), s32, 0.5f * s32);
+    float u3 = fmaf(__uint2float_rn(w.w), s32, 0.5f * s32);
+    u0 = fminf(u0, 1.0f);
+    u2 = fminf(u2, 1.0f);
+    float r01 = sqrtf(-2.0f * logf(u0));
+    float r23 = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s3, &c3);
+    return make_float4(r01 * c1, r01 * s1, r23 * c3, r23 * s3);
+}
+
+// Launch-error check used by every launcher.
+int cuda_fail(cudaError_t e);
+#define DGCT_LAUNCH_CHECK()                                        \
+    do {                                                           \
+        cudaError_t _e = cudaGetLastError();                       \
+        if (_e != cudaSuccess) return ::dgct::cuda_fail(_e);       \
+    } while (0)
+#define DGCT_CUDA(call)                                            \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return ::dgct::cuda_fail(_e);       \
+    } while (0)
+
+// ----------------------------------------------------------- launchers ----
+// joseph.cu
+int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t st);
+int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st);
+int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
+                       float* out, int update, cudaStream_t st);
+int launch_frobenius(dgamp_ct_plan_s* pl);
+// fft.cu
+int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaStream_t st);
+int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out, int inverse,
+                         cudaStream_t st);
+int fft_set_smem_limits(int bytes);
+// output_step.cu
+int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y, float* s,
+                       int use_prev, int from_scalars, double tau_p_arg, double logI0_arg,
+                       double* tau_s_out, cudaStream_t st);
+// tv.cu
+int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st);
+int launch_absmax(const dgamp_ct_plan_s* pl, const float* r, cudaStream_t st);
+int launch_tv_iters(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg,
+                    cudaStream_t st, int* final_buf);
+int launch_tv_step(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
+                   cudaStream_t st, int* final_buf);
+bool tv_active(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg);
+int launch_tv_final(const dgamp_ct_plan_s* pl, int nimg, int final_buf, int from_scalars,
+                    double lambda_arg, float* x_out, int solve_mode, int t_arg, double* div_out,
+                    cudaStream_t st);
+int launch_probe(const dgamp_ct_plan_s* pl, unsigned t, int64_t n, float* b, uint32_t* words,
+                 cudaStream_t st);
+
+}  // namespace dgct

@@ -1,0 +1,265 @@
+// Joseph ray-driven projector A, its exact transpose A^T, and the plan-time
+// FP64 evaluation of ||Phi~||_F^2 (Eq. linCT; Algorithm 1, Steps 1 and 3).
+//
+// Layout.  Before a projection the image is staged twice in row-padded form:
+// XR[iy][kPad + ix] (rows) and XC[ix][kPad + iy] (the transpose), each line
+// with kPad zero cells on both sides.  A view that marches over rows reads
+// XR, one that marches over columns reads XC, so in both cases a warp of
+// adjacent rays reads adjacent floats of one line per step, and taps that
+// fall just outside the image read zeros instead of being bounds-checked.
+#include "internal.cuh"
+
+namespace dgct {
+
+// ------------------------------------------------------------- staging ----
+__global__ void k_stage_image(const float* __restrict__ img, int n, int ldp,
+                              float* __restrict__ XR, float* __restrict__ XC) {
+    __shared__ float tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int iy = by + j, ix = bx + threadIdx.x;
+        float v = 0.f;
+        if (iy < n && ix < n) {
+            v = img[(size_t)iy * n + ix];
+            XR[(size_t)iy * ldp + kPad + ix] = v;
+        }
+        tile[j][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int ix = bx + j, iy = by + threadIdx.x;
+        if (iy < n && ix < n) XC[(size_t)ix * ldp + kPad + iy] = tile[threadIdx.x][j];
+    }
+}
+
+int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t st) {
+    dim3 blk(32, 8), grd((pl->n + 31) / 32, (pl->n + 31) / 32);
+    k_stage_image<<<grd, blk, 0, st>>>(img, pl->n, pl->ldp, pl->ws.XR, pl->ws.XC);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// --------------------------------------------------------- projection ----
+// Steps of ray `base` (position at s = 0) whose taps can touch the image:
+// pos in [-1, n) widened by one step each way (|a_step| <= 1, so the taps of
+// the extra steps stay inside the zero guard cells).
+__device__ __forceinline__ void step_range(float base, float a_step, int n, int& s0, int& s1) {
+    if (fabsf(a_step) < 1e-12f) {
+        if (base >= -1.f && base < (float)n) { s0 = 0; s1 = n - 1; } else { s0 = 1; s1 = 0; }
+        return;
+    }
+    float t0 = (-1.f - base) / a_step, t1 = ((float)n - base) / a_step;
+    float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
+    lo = fmaxf(lo, -1.f);
+    hi = fminf(hi, (float)n);
+    s0 = max(0, (int)floorf(lo) - 1);
+    s1 = min(n - 1, (int)ceilf(hi) + 1);
+}
+
+__global__ void __launch_bounds__(128)
+k_project(const float* __restrict__ XR, const float* __restrict__ XC, int ldp, int n, int nd,
+          const ViewConst* __restrict__ vcs, float* __restrict__ sino) {
+    const int v = blockIdx.y;
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= nd) return;
+    const ViewConst c = vcs[v];
+    const float* __restrict__ B = c.col ? XC : XR;
+    const float base = fmaf((float)d, c.a_det, c.a0);
+    int s0, s1;
+    step_range(base, c.a_step, n, s0, s1);
+    float acc = 0.f;
+    for (int s = s0; s <= s1; ++s) {
+        const float pos = fmaf((float)s, c.a_step, base);
+        int i0;
+        float f;
+        joseph_tap(pos, i0, f);
+        const float* q = B + (size_t)s * ldp + kPad + i0;
+        const float x0 = __ldg(q), x1 = __ldg(q + 1);
+        acc += fmaf(f, x1 - x0, x0);
+    }
+    sino[(size_t)v * nd + d] = acc * c.w;
+}
+
+int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st) {
+    dim3 blk(128), grd((pl->nd + 127) / 128, pl->nv);
+    k_project<<<grd, blk, 0, st>>>(pl->ws.XR, pl->ws.XC, pl->ldp, pl->n, pl->nd, pl->ws.vc, sino);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// ---------------------------------------------------- back-projection ----
+// Pixel-driven gather of the exact transpose: for every view, the rays whose
+// interpolation taps include this pixel are found from the same pos(d, s)
+// expression the projector uses, so each weight equals the projector's.
+// With update = 1 the kernel also forms r = x + tau_r A^T s (Algorithm 1,
+// Step 3) and the running max |r| used by the MC step of Step 4.
+constexpr int kBpViews = 256;
+
+__global__ void __launch_bounds__(256)
+k_backproject(const float* __restrict__ sino, int nv, int nd, int n,
+              const ViewConst* __restrict__ vcs, const float* __restrict__ x_in,
+              float* __restrict__ out, int update, DevScalars* __restrict__ S) {
+    __shared__ ViewConst svc[kBpViews];
+    __shared__ unsigned s_max;
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const bool live = ix < n && iy < n;
+    if (tid == 0) s_max = 0u;
+    float acc = 0.f;
+    for (int v0 = 0; v0 < nv; v0 += kBpViews) {
+        const int cnt = min(kBpViews, nv - v0);
+        __syncthreads();
+        for (int i = tid; i < cnt; i += blockDim.x * blockDim.y) svc[i] = vcs[v0 + i];
+        __syncthreads();
+        if (!live) continue;
+        for (int vi = 0; vi < cnt; ++vi) {
+            const ViewConst c = svc[vi];
+            const int s = c.col ? ix : iy;        // march line of this pixel
+            const int k = c.col ? iy : ix;        // index across the line
+            // rays with pos(d, s) in (k-1, k+1): pos ~= a0 + s a_step + d a_det
+            const float t = fmaf((float)s, c.a_step, c.a0);
+            float dl = ((float)k - 1.f - t) / c.a_det;
+            float dh = ((float)k + 1.f - t) / c.a_det;
+            if (dl > dh) { const float tmp = dl; dl = dh; dh = tmp; }
+            dl = fmaxf(dl, -1.f);
+            dh = fminf(dh, (float)nd);
+            const int d0 = max(0, (int)ceilf(dl - 0.01f));
+            const int d1 = min(nd - 1, (int)floorf(dh + 0.01f));
+            const float* __restrict__ row = sino + (size_t)(v0 + vi) * nd;
+            float av = 0.f;
+            for (int d = d0; d <= d1; ++d) {
+                const float pos = joseph_pos(c, d, s);
+                int i0;
+                float f;
+                joseph_tap(pos, i0, f);
+                const float wgt = (i0 == k) ? (1.f - f) : ((i0 + 1 == k) ? f : 0.f);
+                av = fmaf(wgt, __ldg(row + d), av);
+            }
+            acc = fmaf(av, c.w, acc);
+        }
+    }
+    const size_t o = (size_t)iy * n + ix;
+    if (update && live) {
+        const float tau_r = (float)S->tau_r;
+        const float rv = fmaf(tau_r, acc, x_in[o]);
+        out[o] = rv;
+        // |r| >= 0, so its float bit pattern orders like the value
+        atomicMax(&s_max, __float_as_uint(fabsf(rv)));
+    }
+    if (!update) {
+        if (live) out[o] = acc;
+        return;
+    }
+    __syncthreads();
+    if (tid == 0) atomicMax(&S->rmax_bits, s_max);
+}
+
+int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
+                       float* out, int update, cudaStream_t st) {
+    dim3 blk(32, 8), grd((pl->n + 31) / 32, (pl->n + 7) / 8);
+    k_backproject<<<grd, blk, 0, st>>>(sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in, out, update,
+                                       pl->ws.S);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// ---------------------------------------------- ||Phi~||_F^2 in FP64 ----
+// ||H A||_F^2 = sum_k trace(T^T T G_k) with T[i,j] = h[(i-j) mod P] the matrix
+// of H and G_k = A_k A_k^T, which is tridiagonal for Joseph weights (two
+// rays of one view share a pixel only if |d - d'| <= 1).  Everything here is
+// FP64 and runs once per plan.
+
+// h[m] = (1/P) sum_k g_k cos(2 pi k m / P), m = 0..nd (h is even).
+__global__ void k_filter_kernel_fp64(int P, int nd, double* __restrict__ h) {
+    const int m = blockIdx.x;
+    if (m > nd) return;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        const int kk = (k <= P / 2) ? k : P - k;
+        const double f = (double)kk / (double)P;
+        const double g = sqrt(fmax(f, 1.0 / (2.0 * P)));
+        const long long arg = ((long long)k * m) % P;       // exact argument reduction
+        acc += g * cospi(2.0 * (double)arg / (double)P);
+    }
+    __shared__ double sm[32];
+    acc = block_sum(acc, sm);
+    if (threadIdx.x == 0) h[m] = acc / (double)P;
+}
+
+// TT0[i] = (T^T T)[i,i], TT1[i] = (T^T T)[i,i+1]
+__global__ void k_tt_band(const double* __restrict__ h, int nd, double* __restrict__ tt0,
+                          double* __restrict__ tt1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nd) return;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nd; ++k) {
+        const double hi = h[abs(k - i)];
+        a += hi * hi;
+        if (i + 1 < nd) b += hi * h[abs(k - i - 1)];
+    }
+    tt0[i] = a;
+    tt1[i] = (i + 1 < nd) ? b : 0.0;
+}
+
+// One (view, ray) per thread: G_k[d,d] and G_k[d,d+1] from FP64 Joseph
+// weights, weighted by the T^T T band.
+__global__ void k_frob_terms(int n, int nv, int nd, const double* __restrict__ ang,
+                             const double* __restrict__ tt0, const double* __restrict__ tt1,
+                             double* __restrict__ term) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y;
+    if (d >= nd) return;
+    const double th = ang[v];
+    double st, ct;
+    sincos(th, &st, &ct);
+    const double c = 0.5 * (n - 1), cd = 0.5 * (nd - 1);
+    const bool col = fabs(st) >= fabs(ct);
+    const double w = col ? 1.0 / fabs(st) : 1.0 / fabs(ct);
+    const double u0 = d - cd, u1 = d + 1 - cd;
+    double g0 = 0.0, g1 = 0.0;
+    for (int s = 0; s < n; ++s) {
+        double p0, p1;
+        if (col) {
+            const double X = s - c;
+            p0 = c - (u0 - X * ct) / st;
+            p1 = c - (u1 - X * ct) / st;
+        } else {
+            const double Y = c - s;
+            p0 = (u0 - Y * st) / ct + c;
+            p1 = (u1 - Y * st) / ct + c;
+        }
+        const double f0 = floor(p0), f1 = floor(p1);
+        const int a0 = (int)f0, b0 = (int)f1;
+        const double wa[2] = {(1.0 - (p0 - f0)) * w, (p0 - f0) * w};
+        const double wb[2] = {(1.0 - (p1 - f1)) * w, (p1 - f1) * w};
+        for (int i = 0; i < 2; ++i) {
+            const int ia = a0 + i;
+            if (ia < 0 || ia > n - 1) continue;
+            g0 += wa[i] * wa[i];
+            if (d + 1 < nd)
+                for (int j = 0; j < 2; ++j)
+                    if (b0 + j == ia) g1 += wa[i] * wb[j];
+        }
+    }
+    term[(size_t)v * nd + d] = tt0[d] * g0 + 2.0 * tt1[d] * g1;
+}
+
+int launch_frobenius(dgamp_ct_plan_s* pl) {
+    const int nd = pl->nd, nv = pl->nv;
+    double* h = pl->ws.scratch_d;               // [nd+1]
+    double* tt0 = h + (nd + 1);                 // [nd]
+    double* tt1 = tt0 + nd;                     // [nd]
+    double* ang = tt1 + nd;                     // [nv]
+    double* term = ang + nv;                    // [nv*nd]
+    k_filter_kernel_fp64<<<nd + 1, 256>>>(pl->P, nd, h);
+    DGCT_LAUNCH_CHECK();
+    k_tt_band<<<(nd + 127) / 128, 128>>>(h, nd, tt0, tt1);
+    DGCT_LAUNCH_CHECK();
+    dim3 grd((nd + 127) / 128, nv);
+    k_frob_terms<<<grd, 128>>>(pl->n, nv, nd, ang, tt0, tt1, term);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+}  // namespace dgct

@@ -1,0 +1,230 @@
+"""GPU parity: every step of the D-GAMP-CT iteration through the C ABI against
+the FP64 oracle on the same seeded inputs.
+
+Tolerances: 1e-5 relative L2 for each linear operator (A, A^T, H, V^-1) and
+for the elementwise/denoiser steps, computed in FP32 against FP64; 1e-3
+relative L2 on the reconstruction after a fixed number of iterations; integer
+probe words bit-exact.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gamp, joseph, output_step, philox, precond, tv
+from oracle.geometry import Geometry
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_04661_gb300 import build
+    build.build()
+    import paper_1609_04661_gb300 as dg
+    dg.load()
+    return dg
+
+
+def cu(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+# geometries: several tiles and a ragged tail in both the ray and the pixel
+# direction, odd and even sizes, the 45-degree tie, explicit angles.
+GEOMS = [
+    (64, 30, 95, None),
+    (37, 13, 55, None),
+    (50, 8, 73, (0.0, 0.3, np.pi / 4, 1.2, np.pi / 2, 2.0, 3 * np.pi / 4, 3.0)),
+    (129, 7, 190, None),
+]
+
+
+def _img(n, seed, kind="random"):
+    rng = np.random.default_rng(seed)
+    if kind == "random":
+        return rng.uniform(0.0, 1.0, (n, n))
+    ph = synth.random_phantom(n, 5, seed)
+    return synth.rasterise(ph, n)
+
+
+@pytest.mark.parametrize("n,nv,nd,ang", GEOMS)
+@pytest.mark.parametrize("kind", ["random", "phantom"])
+def test_project_matches_oracle(dg, n, nv, nd, ang, kind):
+    g = Geometry(n, nv, nd, ang)
+    x = _img(n, 3, kind)
+    with dg.Plan(n, nv, nd, angles=ang) as pl:
+        z = host(pl.project(cu(x)))
+        zp = host(pl.project(cu(x), precond=True))
+    assert rel(z, joseph.forward_project(x, g)) < 1e-5
+    assert rel(zp, precond.project(x, g)) < 1e-5
+
+
+@pytest.mark.parametrize("n,nv,nd,ang", GEOMS)
+def test_backproject_matches_oracle(dg, n, nv, nd, ang):
+    g = Geometry(n, nv, nd, ang)
+    s = np.random.default_rng(4).standard_normal((nv, nd))
+    with dg.Plan(n, nv, nd, angles=ang) as pl:
+        b = host(pl.backproject(cu(s)))
+        bp = host(pl.backproject(cu(s), precond=True))
+    assert rel(b, joseph.back_project(s, g)) < 1e-5
+    assert rel(bp, precond.backproject(s, g)) < 1e-5
+
+
+def test_gpu_pair_is_adjoint(dg):
+    n, nv, nd = 96, 17, 139
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((n, n))
+    s = rng.standard_normal((nv, nd))
+    with dg.Plan(n, nv, nd) as pl:
+        for pc in (False, True):
+            ax = host(pl.project(cu(x), precond=pc))
+            ats = host(pl.backproject(cu(s), precond=pc))
+            lhs, rhs = np.sum(ax * s), np.sum(x * ats)
+            assert abs(lhs - rhs) <= 1e-5 * np.sqrt(np.sum(ax * ax) * np.sum(s * s))
+
+
+@pytest.mark.parametrize("n,nv,nd", [(64, 30, 95), (40, 9, 300), (16, 3, 24)])
+def test_filter_matches_oracle(dg, n, nv, nd):
+    g = Geometry(n, nv, nd)
+    s = np.random.default_rng(6).standard_normal((nv, nd))
+    with dg.Plan(n, nv, nd) as pl:
+        h = host(pl.filter(cu(s)))
+        # in place as well
+        t = cu(s)
+        pl.filter(t, out=t)
+        h2 = host(t)
+    ref = precond.filter_views(s, g)
+    assert rel(h, ref) < 1e-5 and rel(h2, ref) < 1e-5
+
+
+def test_frobenius_matches_oracle(dg):
+    for n, nv, nd in [(64, 30, 95), (37, 13, 55)]:
+        with dg.Plan(n, nv, nd) as pl:
+            assert pl.frob_sq == pytest.approx(precond.frobenius_sq(Geometry(n, nv, nd)), rel=1e-11)
+
+
+@pytest.mark.parametrize("tau_p", [1e-4, 0.05, 3.0])
+def test_output_step_matches_oracle(dg, tau_p):
+    n, nv, nd = 32, 21, 401          # M = 8421: several blocks and a ragged tail
+    rng = np.random.default_rng(7)
+    I0 = 1e5
+    z_true = rng.uniform(0.0, 14.0, (nv, nd))
+    y = rng.poisson(I0 * np.exp(-z_true)).astype(np.float64)
+    z = z_true + rng.normal(0, 0.5, (nv, nd))
+    s_prev = rng.normal(0, 1.0, (nv, nd))
+    with dg.Plan(n, nv, nd) as pl:
+        s, ts = pl.output_step(cu(z), cu(y), cu(s_prev), I0, tau_p)
+        s, ts = host(s), float(host(ts)[0])
+    # the kernel forms p = fma(-tau_p, s_prev, z) in FP32; give the oracle that same p
+    f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    p = f32(f32(z).reshape(-1) - f32(tau_p) * f32(s_prev).reshape(-1))
+    s_ref, tsi_ref, _, _ = output_step.output_step(p, y.reshape(-1), float(f32(tau_p)), I0)
+    assert rel(s, s_ref) < 1e-5
+    assert ts == pytest.approx(np.mean(tsi_ref), rel=1e-5)
+    assert (y == 0).any()
+
+
+@pytest.mark.parametrize("n,lam", [(64, 0.3), (77, 0.05), (33, 0.0)])
+def test_tv_matches_oracle(dg, n, lam):
+    r = np.cumsum(np.random.default_rng(8).standard_normal((n, n)), axis=1) * 0.1
+    with dg.Plan(n, 10, 2 * n, k_tv=20) as pl:
+        x = host(pl.denoise_tv(cu(r), lam))
+    assert rel(x, tv.tv_prox(r, lam, 20)) < 1e-5
+
+
+def test_probe_words_bitexact_and_normals_close(dg):
+    n = 10_003
+    with dg.Plan(16, 4, 24, seed=0x1234_5678_9ABC, slice_id=3) as pl:
+        b, w = pl.probe(7, n, words=True)
+        b, w = host(b), w.cpu().numpy().view(np.uint32)
+    ref_w = philox.probe_words(n, 0x1234_5678_9ABC, 7, 3)
+    assert np.array_equal(w, ref_w)
+    ref_b = philox.probe_normals(n, 0x1234_5678_9ABC, 7, 3)
+    assert np.max(np.abs(b - ref_b)) < 1e-5
+
+
+def test_denoise_divergence_matches_oracle(dg):
+    n = 64
+    r = np.cumsum(np.random.default_rng(9).standard_normal((n, n)), axis=0) * 0.2
+    tau_r, t = 0.01, 4
+    opts = gamp.Options(c_tv=3.0, k_tv=20, seed=77, slice_id=0)
+    with dg.Plan(n, 10, 2 * n, k_tv=20, c_tv=3.0, seed=77) as pl:
+        x, dv = pl.denoise_div(cu(r), tau_r, t)
+        x, dv = host(x), float(host(dv)[0])
+    lam = opts.c_tv * np.sqrt(tau_r)
+    D = lambda v: tv.tv_prox(v, lam, 20)
+    x_ref = D(r)
+    b = philox.probe_normals(n * n, 77, t, 0).reshape(n, n)
+    eps = 1e-3 * max(np.max(np.abs(r)), 1e-6)
+    div_ref = gamp.mc_divergence(D, r, x_ref, b, eps)
+    assert rel(x, x_ref) < 1e-5
+    assert dv == pytest.approx(div_ref, rel=2e-3)
+
+
+@pytest.mark.parametrize("n", [64, 48])
+def test_precond_image_matches_oracle(dg, n):
+    g = Geometry(n, 10, 2 * n)
+    x = np.random.default_rng(10).standard_normal((n, n))
+    with dg.Plan(n, 10, 2 * n) as pl:
+        vi = host(pl.precond_image(cu(x), inverse=True))
+        vf = host(pl.precond_image(cu(x), inverse=False))
+    assert rel(vi, precond.v_inverse(x, g)) < 1e-5
+    assert rel(vf, precond.v_forward(x, g)) < 1e-5
+
+
+# ---------------------------------------------------------------- solve ----
+@pytest.fixture(scope="module")
+def case64():
+    c = synth.make_case("ellipse64_v30")
+    return c, Geometry(c["n"], c["n_views"], c["n_det"])
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_solve_matches_oracle_after_20_iterations(dg, case64, use_graph):
+    c, g = case64
+    T = c["iters"]
+    log = []
+    mu_ref, x_ref = gamp.ct_solve(c["y"], c["I0"], g, T, gamp.Options(c_tv=3.0, k_tv=20), return_x=True,
+                                  log=log)
+    with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, use_graph=use_graph) as pl:
+        xo = torch.empty((g.n, g.n), device="cuda")
+        mu, st = pl.solve(cu(c["y"]), c["I0"], T, with_stats=True, x_out=xo)
+        mu, xo = host(mu), host(xo)
+    assert st["iters_done"] == T
+    assert rel(xo, x_ref) < 1e-3
+    assert rel(mu, mu_ref) < 1e-3
+    ref_tx = np.array([lg.tau_x for lg in log])
+    ref_tr = np.array([lg.tau_r for lg in log])
+    assert np.allclose(st["tau_r"], ref_tr, rtol=1e-3)
+    assert np.allclose(st["tau_x"], ref_tx, rtol=2e-2)
+
+
+def test_solve_host_buffers_match_device_path(dg, case64):
+    c, g = case64
+    with dg.Plan(g.n, g.n_views, g.n_det) as pl:
+        mu_d = host(pl.solve(cu(c["y"]), c["I0"], 5))
+        mu_h = pl.solve_host(c["y"], c["I0"], 5)
+    assert np.array_equal(mu_h.astype(np.float64), mu_d)
+
+
+def test_solve_rejects_bad_arguments(dg, case64):
+    c, g = case64
+    with dg.Plan(g.n, g.n_views, g.n_det) as pl:
+        for bad in [dict(I0=0.0, iters=3), dict(I0=float("nan"), iters=3), dict(I0=1e4, iters=0)]:
+            with pytest.raises(dg.DgampError):
+                pl.solve(cu(c["y"]), bad["I0"], bad["iters"])
