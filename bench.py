@@ -38,7 +38,7 @@ if ROOT not in sys.path:
 METRIC = "D-GAMP-CT iters/s at 512²/64 views; A+Aᵀ GB/s; learned vs plain at equal PSNR"
 UNIT = "iters/s"
 WORKLOAD = "ellipse512_v64"
-TV = dict(c_tv=3.0, k_tv=20)
+TV = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -63,7 +63,7 @@ def _config(n_gpus):
     n, nv, nd, ne, rmax, rect, I0, iters = CASES[WORKLOAD]
     return {"workload": f"{WORKLOAD}: {n}x{n} image of {ne} seeded random ellipses + rectangle object, "
                         f"parallel beam, {nv} views over 180 deg, {nd} detector bins, Poisson I0={I0:g}, "
-                        f"{iters} iterations, prox-TV denoiser (K={TV['k_tv']}, c={TV['c_tv']})",
+                        f"{iters} iterations, prox-TV denoiser (K={TV['k_tv']}, c={TV['c_tv']}), damping eta_x={TV['damp_x']}, eta_s={TV['damp_s']}",
             "image": n, "views": nv, "detector_bins": nd, "I0": I0, "iters_per_step": iters,
             "l2": "flushed between steps (256 MiB write, outside the timed events)",
             "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "single GPU"}

@@ -82,6 +82,14 @@ static void view_constants(int n, int nd, const std::vector<double>& ang, std::v
             v.a_det = (float)(1.0 / ct);
             v.w = (float)(1.0 / std::fabs(ct));
         }
+        // 32.32 fixed point from the FP64 values (not from the rounded floats)
+        const double a0 = v.col ? (c + cd / st - c * ct / st) : (c - cd / ct - c * st / ct);
+        const double as = v.col ? ct / st : st / ct;
+        const double ad = v.col ? -1.0 / st : 1.0 / ct;
+        const double q = 4294967296.0;
+        v.P0 = (long long)std::llround(a0 * q);
+        v.PSTEP = (long long)std::llround(as * q);
+        v.PDET = (long long)std::llround(ad * q);
         out[k] = v;
     }
 }

@@ -15,13 +15,17 @@ constexpr int kNewtonCap = 64;     // output-step iteration cap
 
 // Joseph constants of one view.  The ray of bin d meets march line s (a
 // column for col = 1, a row for col = 0) at fractional index
-//   pos(d, s) = fmaf(s, a_step, fmaf(d, a_det, a0))
-// across that line; the projector and the back-projector evaluate exactly this
-// expression so their weights agree bit for bit.
+//   pos(d, s) = a0 + d a_det + s a_step
+// across that line.  Positions are carried in 32.32 fixed point
+// (P0 + d PDET + s PSTEP, 64-bit integers), so stepping along a ray is exact
+// and the projector and the back-projector obtain bit-identical taps and
+// weights however they evaluate the sum.  The float copies serve only to
+// bound loops.
 struct ViewConst {
+    long long P0, PSTEP, PDET;    // a0, a_step, a_det scaled by 2^32
     float a0, a_step, a_det, w;   // w = path length per step (1/|sin| or 1/|cos|)
     int col;                      // 1: march over columns, interpolate along rows
-    int pad[3];
+    int pad;
 };
 
 // Scalars of Algorithm 1 that live on the device for the whole solve.
@@ -88,15 +92,14 @@ struct dgamp_ct_plan_s {
 namespace dgct {
 
 // ---------------------------------------------------------------- helpers --
-__device__ __forceinline__ float joseph_pos(const ViewConst& c, int d, int s) {
-    return fmaf((float)s, c.a_step, fmaf((float)d, c.a_det, c.a0));
+__device__ __forceinline__ long long joseph_pos(const ViewConst& c, int d, int s) {
+    return c.P0 + (long long)d * c.PDET + (long long)s * c.PSTEP;
 }
 
-// Split a position into its left tap and the interpolation fraction.
-__device__ __forceinline__ void joseph_tap(float pos, int& i0, float& f) {
-    float fl = floorf(pos);
-    i0 = (int)fl;
-    f = pos - fl;
+// Split a 32.32 position into its left tap (floor) and the fraction in [0, 1].
+__device__ __forceinline__ void joseph_tap(long long pos, int& i0, float& f) {
+    i0 = (int)(pos >> 32);
+    f = __uint2float_rn((unsigned)(pos & 0xffffffffLL)) * 2.3283064365386963e-10f;
 }
 
 template <typename T>

@@ -68,8 +68,8 @@ k_project(const float* __restrict__ XR, const float* __restrict__ XC, int ldp, i
     int s0, s1;
     step_range(base, c.a_step, n, s0, s1);
     float acc = 0.f;
-    for (int s = s0; s <= s1; ++s) {
-        const float pos = fmaf((float)s, c.a_step, base);
+    long long pos = joseph_pos(c, d, s0);
+    for (int s = s0; s <= s1; ++s, pos += c.PSTEP) {
         int i0;
         float f;
         joseph_tap(pos, i0, f);
@@ -129,7 +129,7 @@ k_backproject(const float* __restrict__ sino, int nv, int nd, int n,
             const float* __restrict__ row = sino + (size_t)(v0 + vi) * nd;
             float av = 0.f;
             for (int d = d0; d <= d1; ++d) {
-                const float pos = joseph_pos(c, d, s);
+                const long long pos = joseph_pos(c, d, s);
                 int i0;
                 float f;
                 joseph_tap(pos, i0, f);
