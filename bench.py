@@ -265,13 +265,14 @@ def run_gpu(args):
     iter_ms = sum(prof.values())
     hbm, peak_kind = _peaks()
     N, M = plan.N, plan.M
+    # compulsory bytes per launch (FP32 images/sinograms, float2 TV duals, two images in the denoiser)
     algo = {"project": 4 * (N + M), "filter_z": 8 * M, "output_step": 16 * M, "filter_s": 8 * M,
-            "backproject_update": 4 * (M + 2 * N), "probe_input": 8 * N, "tv_final": 2 * 12 * N + 12 * N}
+            "backproject_update": 4 * (M + 2 * N), "probe_input": 8 * N,
+            "tv_block_final": 8 * N + 16 * N + 16 * N}
     for kname in prof:
-        if kname.startswith("tv_step"):
-            algo[kname] = 2 * (8 + 4 + 8) * N
-    groups = {"tv_steps": [k for k in prof if k.startswith("tv_step")]}
-    tv_ms = sum(prof[k] for k in groups["tv_steps"])
+        if kname.startswith("tv_block") and kname != "tv_block_final":
+            algo[kname] = 8 * N + 16 * N + (0 if kname == "tv_block0" else 16 * N)
+    tv_ms = sum(v for k, v in prof.items() if k.startswith("tv_block"))
     shares = {k: v / iter_ms for k, v in prof.items()}
     dom = max(prof, key=prof.get)
     achieved = algo[dom] / (prof[dom] * 1e-3) / 1e9

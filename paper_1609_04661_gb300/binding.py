@@ -288,7 +288,7 @@ class Plan:
                "dgamp_ct_profile_iteration")
         names = ["project", "filter_z", "output_step", "filter_s", "backproject_update", "probe_input"]
         k = cnt.value - len(names) - 1
-        names += [f"tv_step{i}" for i in range(k)] + ["tv_final"]
+        names += [f"tv_block{i}" for i in range(k)] + ["tv_block_final"]
         return dict(zip(names, [arr[i] for i in range(cnt.value)]))
 
     def solve_launches(self, iters: int) -> int:

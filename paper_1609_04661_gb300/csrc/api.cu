@@ -87,6 +87,7 @@ static void view_constants(int n, int nd, const std::vector<double>& ang, std::v
         const double as = v.col ? ct / st : st / ct;
         const double ad = v.col ? -1.0 / st : 1.0 / ct;
         const double q = 4294967296.0;
+        v.inv_adet = (float)(1.0 / ad);
         v.P0 = (long long)std::llround(a0 * q);
         v.PSTEP = (long long)std::llround(as * q);
         v.PDET = (long long)std::llround(ad * q);
@@ -167,6 +168,7 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_CUDA(cudaMemcpy(&w.S->frob2, &tot, sizeof(double), cudaMemcpyHostToDevice));
     const int smem_need = 2 * (P > pl->m2 ? P : pl->m2) * (int)sizeof(float2);
     DGCT_TRY(fft_set_smem_limits(smem_need > 48 * 1024 ? smem_need : 48 * 1024));
+    DGCT_TRY(tv_set_smem_limits(pl->tv_kb));
     return DGAMP_CT_OK;
 }
 
@@ -195,26 +197,18 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
     DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st));            //         r = x + tau_r A^T H s
     DGCT_TRY(mark());
     DGCT_TRY(launch_probe_input(pl, 0, st));                            // Step 4: r + eps b
-    int fb = -1;
-    if (!ev) {
-        DGCT_TRY(launch_tv_iters(pl, 2, 1, 0.0, st, &fb));              //         D(r), D(r + eps b)
-    } else {
-        // the same Chambolle launches, one event each
-        const int K = tv_active(pl, 1, 0.0) ? pl->opt.k_tv : 0;
-        for (int i = 0; i < K; ++i) {
-            DGCT_TRY(mark());
-            DGCT_TRY(launch_tv_step(pl, 2, 1, 0.0, i, st, &fb));
-        }
+    // D(r), D(r + eps b), x, D', tau_x: the blocked TV launches, the last one final
+    const int ntv = tv_num_launches(pl, 1, 0.0);
+    for (int i = 0; i < ntv; ++i) {
+        DGCT_TRY(mark());
+        DGCT_TRY(launch_tv_chunk(pl, 2, 1, 0.0, i, w.x, 1, 0, nullptr, st));
     }
-    DGCT_TRY(mark());
-    DGCT_TRY(launch_tv_final(pl, 2, fb, 1, 0.0, w.x, 1, 0, nullptr, st));  //      x, D', tau_x
     DGCT_TRY(mark());
     return DGAMP_CT_OK;
 }
 
 static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
-    const int tv = (pl->opt.k_tv > 0 && pl->opt.c_tv > 0) ? pl->opt.k_tv : 0;
-    return 7 + tv;
+    return 6 + tv_num_launches(pl, 1, 0.0);
 }
 
 static void drop_graph(dgamp_ct_plan_s* pl) {
@@ -379,9 +373,7 @@ int dgamp_ct_denoise_tv(dgamp_ct_plan_t pl, const float* d_r, double lambda, flo
     if (!pl || !d_r || !d_x || !(lambda >= 0) || !std::isfinite(lambda)) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     DGCT_CUDA(cudaMemcpyAsync(pl->ws.r, d_r, (size_t)pl->N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    int fb = -1;
-    if (lambda > 0) DGCT_TRY(launch_tv_iters(pl, 1, 0, lambda, st, &fb));
-    return launch_tv_final(pl, 1, fb, 0, lambda, d_x, 0, 0, nullptr, st);
+    return launch_tv(pl, 1, 0, lambda, d_x, 0, 0, nullptr, st);
 }
 
 int dgamp_ct_denoise_div(dgamp_ct_plan_t pl, const float* d_r, double tau_r, int32_t t, float* d_x,
@@ -393,9 +385,7 @@ int dgamp_ct_denoise_div(dgamp_ct_plan_t pl, const float* d_r, double tau_r, int
     DGCT_TRY(launch_absmax(pl, pl->ws.r, st));
     DGCT_TRY(launch_probe_input(pl, t, st));
     const double lambda = pl->opt.c_tv * std::sqrt(tau_r);
-    int fb = -1;
-    if (lambda > 0) DGCT_TRY(launch_tv_iters(pl, 2, 0, lambda, st, &fb));
-    return launch_tv_final(pl, 2, fb, 0, lambda, d_x, 0, t, d_div, st);
+    return launch_tv(pl, 2, 0, lambda, d_x, 0, t, d_div, st);
 }
 
 int dgamp_ct_probe(dgamp_ct_plan_t pl, int32_t t, int64_t n, float* d_b, uint32_t* d_words, void* stream) {

@@ -24,8 +24,8 @@ constexpr int kNewtonCap = 64;     // output-step iteration cap
 struct ViewConst {
     long long P0, PSTEP, PDET;    // a0, a_step, a_det scaled by 2^32
     float a0, a_step, a_det, w;   // w = path length per step (1/|sin| or 1/|cos|)
+    float inv_adet;               // 1 / a_det
     int col;                      // 1: march over columns, interpolate along rows
-    int pad;
 };
 
 // Scalars of Algorithm 1 that live on the device for the whole solve.
@@ -83,6 +83,7 @@ struct dgamp_ct_plan_s {
     dgamp_ct_options opt{};
     dgct::Workspace ws;
     int max_partials = 0;
+    int tv_kb = 5;                         // Chambolle steps per blocked TV launch
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;   // stream the graph was captured for (identity only)
@@ -190,14 +191,13 @@ int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y
 // tv.cu
 int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st);
 int launch_absmax(const dgamp_ct_plan_s* pl, const float* r, cudaStream_t st);
-int launch_tv_iters(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg,
-                    cudaStream_t st, int* final_buf);
-int launch_tv_step(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
-                   cudaStream_t st, int* final_buf);
 bool tv_active(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg);
-int launch_tv_final(const dgamp_ct_plan_s* pl, int nimg, int final_buf, int from_scalars,
-                    double lambda_arg, float* x_out, int solve_mode, int t_arg, double* div_out,
-                    cudaStream_t st);
+int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg);
+int tv_set_smem_limits(int kb);
+int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
+                    float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st);
+int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, float* x_out,
+              int solve_mode, int t_arg, double* div_out, cudaStream_t st);
 int launch_probe(const dgamp_ct_plan_s* pl, unsigned t, int64_t n, float* b, uint32_t* words,
                  cudaStream_t st);
 

@@ -56,32 +56,53 @@ __device__ __forceinline__ void step_range(float base, float a_step, int n, int&
     s1 = min(n - 1, (int)ceilf(hi) + 1);
 }
 
-__global__ void __launch_bounds__(128)
+// One block = 32 adjacent rays of one view; its 8 warps march disjoint
+// eighths of the step range of those rays and the partial sums are added in
+// a fixed order, so the result does not depend on scheduling.  A warp's 32
+// rays read ~32-46 adjacent floats of one staged line per step.
+constexpr int kPjRays = 32, kPjSeg = 8;
+
+__global__ void __launch_bounds__(kPjRays * kPjSeg)
 k_project(const float* __restrict__ XR, const float* __restrict__ XC, int ldp, int n, int nd,
           const ViewConst* __restrict__ vcs, float* __restrict__ sino) {
+    __shared__ float red[kPjSeg][kPjRays];
     const int v = blockIdx.y;
-    const int d = blockIdx.x * blockDim.x + threadIdx.x;
-    if (d >= nd) return;
+    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int d = blockIdx.x * kPjRays + lane;
     const ViewConst c = vcs[v];
-    const float* __restrict__ B = c.col ? XC : XR;
-    const float base = fmaf((float)d, c.a_det, c.a0);
-    int s0, s1;
-    step_range(base, c.a_step, n, s0, s1);
     float acc = 0.f;
-    long long pos = joseph_pos(c, d, s0);
-    for (int s = s0; s <= s1; ++s, pos += c.PSTEP) {
-        int i0;
-        float f;
-        joseph_tap(pos, i0, f);
-        const float* q = B + (size_t)s * ldp + kPad + i0;
-        const float x0 = __ldg(q), x1 = __ldg(q + 1);
-        acc += fmaf(f, x1 - x0, x0);
+    if (d < nd) {
+        const float* __restrict__ B = c.col ? XC : XR;
+        const float base = fmaf((float)d, c.a_det, c.a0);
+        int s0, s1;
+        step_range(base, c.a_step, n, s0, s1);
+        const int len = (n + kPjSeg - 1) / kPjSeg;
+        s0 = max(s0, seg * len);
+        s1 = min(s1, seg * len + len - 1);
+        if (s0 <= s1) {
+            long long pos = joseph_pos(c, d, s0);
+            const float* __restrict__ line = B + (size_t)s0 * ldp + kPad;
+            for (int s = s0; s <= s1; ++s, pos += c.PSTEP, line += ldp) {
+                int i0;
+                float f;
+                joseph_tap(pos, i0, f);
+                const float x0 = __ldg(line + i0), x1 = __ldg(line + i0 + 1);
+                acc += fmaf(f, x1 - x0, x0);
+            }
+        }
     }
-    sino[(size_t)v * nd + d] = acc * c.w;
+    red[seg][lane] = acc;
+    __syncthreads();
+    if (seg == 0 && d < nd) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < kPjSeg; ++k) t += red[k][lane];
+        sino[(size_t)v * nd + d] = t * c.w;
+    }
 }
 
 int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st) {
-    dim3 blk(128), grd((pl->nd + 127) / 128, pl->nv);
+    dim3 blk(kPjRays * kPjSeg), grd((pl->nd + kPjRays - 1) / kPjRays, pl->nv);
     k_project<<<grd, blk, 0, st>>>(pl->ws.XR, pl->ws.XC, pl->ldp, pl->n, pl->nd, pl->ws.vc, sino);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
@@ -117,19 +138,17 @@ k_backproject(const float* __restrict__ sino, int nv, int nd, int n,
             const ViewConst c = svc[vi];
             const int s = c.col ? ix : iy;        // march line of this pixel
             const int k = c.col ? iy : ix;        // index across the line
-            // rays with pos(d, s) in (k-1, k+1): pos ~= a0 + s a_step + d a_det
+            // rays with pos(d, s) in [k-1, k+1): pos ~= t + d a_det, so d lies
+            // within |1/a_det| of dc = (k - t)/a_det (pad is the float rounding margin)
             const float t = fmaf((float)s, c.a_step, c.a0);
-            float dl = ((float)k - 1.f - t) / c.a_det;
-            float dh = ((float)k + 1.f - t) / c.a_det;
-            if (dl > dh) { const float tmp = dl; dl = dh; dh = tmp; }
-            dl = fmaxf(dl, -1.f);
-            dh = fminf(dh, (float)nd);
-            const int d0 = max(0, (int)ceilf(dl - 0.01f));
-            const int d1 = min(nd - 1, (int)floorf(dh + 0.01f));
+            const float dc = ((float)k - t) * c.inv_adet;
+            const float hw = fabsf(c.inv_adet) + 0.01f;
+            const int d0 = max(0, (int)ceilf(fmaxf(dc - hw, -1.f)));
+            const int d1 = min(nd - 1, (int)floorf(fminf(dc + hw, (float)nd)));
             const float* __restrict__ row = sino + (size_t)(v0 + vi) * nd;
             float av = 0.f;
-            for (int d = d0; d <= d1; ++d) {
-                const long long pos = joseph_pos(c, d, s);
+            long long pos = joseph_pos(c, d0, s);
+            for (int d = d0; d <= d1; ++d, pos += c.PDET) {
                 int i0;
                 float f;
                 joseph_tap(pos, i0, f);

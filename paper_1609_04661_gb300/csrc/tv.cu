@@ -1,23 +1,28 @@
 // Denoiser and divergence, Algorithm 1 Step 4 (Section 4.3, Section 6.3).
 //
 // D is the l2 proximal map of isotropic TV, solved by Chambolle's 2004 dual
-// projection (forward differences, Neumann boundary, step 1/8, fixed
-// iteration count from a zero dual).  The MC divergence of Eq. MC_SURE with
-// one probe needs D at r and at r + eps b; both images are denoised by the
-// same launches (blockIdx.z selects the image), and the final kernel forms
-// x = D(r), b^T (D(r + eps b) - D(r)) in FP64, and -- inside a solve --
-// tau_x = max(tau_r D', floor tau_r) for the next iteration.
+// projection (forward differences, Neumann boundary, step 1/8, a fixed
+// number of iterations from a zero dual).  The MC divergence of Eq. MC_SURE
+// with one probe needs D at r and at r + eps b; both images are denoised by
+// the same blocks, and the last launch forms x = D(r), b^T (D(r+eps b) - D(r))
+// in FP64 and -- inside a solve -- tau_x = max(tau_r D', floor tau_r).
 //
-// Dual layout: float2 (px, py) per pixel, [image][n][n], ping-pong buffers.
-// px is the dual of the horizontal difference, py of the vertical one; px in
-// the last column and py in the last row stay zero (their differences are
-// zero), so div p = px(i,j) - px(i,j-1) + py(i,j) - py(i-1,j) with the
-// out-of-image terms taken as zero reproduces the Neumann divergence.
+// Temporal blocking.  One Chambolle step updates p at a pixel from p within
+// one pixel of it:
+//   q = div p - r/lambda,  div p = px(i,j) - px(i,j-1) + py(i,j) - py(i-1,j)
+//   p <- (p + tau grad q) / (1 + tau |grad q|),  grad q uses q(i,j+1), q(i+1,j)
+// so a block that holds a 32 x 32 tile plus a halo of H pixels in shared
+// memory can run up to H - 1 steps with no global traffic (the valid region
+// shrinks by one pixel per side per step) and still form div p on its tile
+// for the final x = r - lambda div p.  Duals outside the image stay zero,
+// and grad q is zero on the last row/column (Neumann), which reproduces the
+// boundary rules exactly.  Successive launches exchange the tile's duals
+// through ping-pong global buffers [image][n][n] of float2.
 #include "internal.cuh"
 
 namespace dgct {
 
-constexpr int TX = 32, TY = 8;
+constexpr int TB = 32;             // interior tile edge
 constexpr float kTau = 0.125f;
 
 __device__ __forceinline__ float solve_lambda(const DevScalars* S, float c_tv, int from_scalars,
@@ -45,13 +50,16 @@ __global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r
         if (i0 + k < N) r2[i0 + k] = fmaf(eps, bb[k], r[i0 + k]);
 }
 
+static uint2 probe_key(const dgamp_ct_plan_s* pl) {
+    return make_uint2((unsigned)(pl->opt.seed & 0xffffffffu), (unsigned)(pl->opt.seed >> 32));
+}
+
 int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st) {
     const long long N = pl->N;
     const long long groups = (N + 3) / 4;
-    const uint2 key = make_uint2((unsigned)(pl->opt.seed & 0xffffffffu), (unsigned)(pl->opt.seed >> 32));
     k_probe_input<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(
-        pl->ws.r, pl->ws.r + N, N, (float)pl->opt.eps_rel, t_arg, (unsigned)pl->opt.slice_id, key,
-        pl->ws.S);
+        pl->ws.r, pl->ws.r + N, N, (float)pl->opt.eps_rel, t_arg, (unsigned)pl->opt.slice_id,
+        probe_key(pl), pl->ws.S);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -75,158 +83,143 @@ int launch_absmax(const dgamp_ct_plan_s* pl, const float* r, cudaStream_t st) {
     return DGAMP_CT_OK;
 }
 
-// ------------------------------------------------------ Chambolle step ----
-// One iteration p <- (p + tau grad q) / (1 + tau |grad q|), q = div p - r/lambda.
-// Tile TX x TY pixels; q is formed in shared memory on the tile plus one
-// column to the right and one row below; p is read with a one-pixel halo
-// above and to the left.
-template <bool FIRST>
-__global__ void __launch_bounds__(TX * TY)
-k_tv_iter(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout,
-          int n, float c_tv, int from_scalars, float lambda_arg, const DevScalars* __restrict__ S) {
-    __shared__ float2 sp[TY + 2][TX + 2];   // p at rows i0-1..i0+TY, cols j0-1..j0+TX
-    __shared__ float sq[TY + 1][TX + 1];    // q at rows i0..i0+TY, cols j0..j0+TX
+// --------------------------------------------------- blocked Chambolle ----
+struct TvFinal {
+    float* x_out;          // D(r) (with damping against the old x in a solve)
+    float* XR;             // staged copies for the next projection (nullable)
+    float* XC;
+    int ldp;
+    float damp_x;
+    int t_arg;             // probe iteration (0: from S)
+    unsigned slice;
+    uint2 key;
+    double tau_x_floor;
+    double* partial;
+    IterLog* log;
+    double* div_out;       // nullable
+    int solve_mode;        // 1: update tau_x, the log and t in S
+};
+
+__global__ void __launch_bounds__(256)
+k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout,
+           int n, int nimg, int H, int iters, int first, int final_step, float c_tv, int from_scalars,
+           float lambda_arg, DevScalars* S, TvFinal F) {
+    extern __shared__ float sm[];
+    const int R = TB + 2 * H, RR = R * R;
+    float* spx = sm;
+    float* spy = sm + nimg * RR;
+    float* sq = sm + 2 * nimg * RR;
+    float* sr = sm + 3 * nimg * RR;
     const size_t N = (size_t)n * n;
-    const int img = blockIdx.z;
-    const float* __restrict__ r = rbase + img * N;
-    const float2* __restrict__ P = pin + img * N;
-    float2* __restrict__ Q = pout + img * N;
-    const int i0 = blockIdx.y * TY, j0 = blockIdx.x * TX;
-    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int gi0 = blockIdx.y * TB - H, gj0 = blockIdx.x * TB - H;
+    const int tid = threadIdx.x, nthr = blockDim.x;
     const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
-    const float inv_lam = 1.0f / lam;
-    if (!FIRST) {
-        for (int e = tid; e < (TY + 2) * (TX + 2); e += TX * TY) {
-            const int a = e / (TX + 2), b = e % (TX + 2);
-            const int gi = i0 - 1 + a, gj = j0 - 1 + b;
-            sp[a][b] = (gi >= 0 && gi < n && gj >= 0 && gj < n) ? P[(size_t)gi * n + gj]
-                                                                 : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < (TY + 1) * (TX + 1); e += TX * TY) {
-        const int a = e / (TX + 1), b = e % (TX + 1);
-        const int gi = i0 + a, gj = j0 + b;
-        float q = 0.f;
-        if (gi < n && gj < n) {
-            float dv = 0.f;
-            if (!FIRST) dv = sp[a + 1][b + 1].x - sp[a + 1][b].x + sp[a + 1][b + 1].y - sp[a][b + 1].y;
-            q = dv - r[(size_t)gi * n + gj] * inv_lam;
-        }
-        sq[a][b] = q;
+    const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
+
+    for (int e = tid; e < nimg * RR; e += nthr) {
+        const int im = e / RR, c = e - im * RR;
+        const int a = c / R, b = c - (c / R) * R;
+        const int gi = gi0 + a, gj = gj0 + b;
+        const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
+        const size_t o = im * N + (size_t)gi * n + gj;
+        sr[e] = in ? rbase[o] : 0.f;
+        float2 p = make_float2(0.f, 0.f);
+        if (in && !first) p = pin[o];
+        spx[e] = p.x;
+        spy[e] = p.y;
     }
     __syncthreads();
-    const int i = i0 + threadIdx.y, j = j0 + threadIdx.x;
-    if (i >= n || j >= n) return;
-    const float qc = sq[threadIdx.y][threadIdx.x];
-    const float gx = (j < n - 1) ? sq[threadIdx.y][threadIdx.x + 1] - qc : 0.f;
-    const float gy = (i < n - 1) ? sq[threadIdx.y + 1][threadIdx.x] - qc : 0.f;
-    const float den = 1.f + kTau * sqrtf(gx * gx + gy * gy);
-    float2 pv = FIRST ? make_float2(0.f, 0.f) : sp[threadIdx.y + 1][threadIdx.x + 1];
-    pv.x = (pv.x + kTau * gx) / den;
-    pv.y = (pv.y + kTau * gy) / den;
-    Q[(size_t)i * n + j] = pv;
-}
 
-bool tv_active(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg) {
-    if (pl->opt.k_tv <= 0) return false;
-    return from_scalars ? pl->opt.c_tv > 0.0 : lambda_arg > 0.0;
-}
-
-// Chambolle iteration i (0-based) on nimg images of ws.r: iteration i writes
-// dual buffer i & 1 and reads buffer (i - 1) & 1; *final_buf names the buffer
-// written.
-int launch_tv_step(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
-                   cudaStream_t st, int* final_buf) {
-    const int n = pl->n;
-    const size_t N = (size_t)pl->N;
-    float2* buf[2] = {pl->ws.p, pl->ws.p + 2 * N};
-    dim3 blk(TX, TY), grd((n + TX - 1) / TX, (n + TY - 1) / TY, nimg);
-    const float c_tv = (float)pl->opt.c_tv;
-    if (i == 0)
-        k_tv_iter<true><<<grd, blk, 0, st>>>(pl->ws.r, buf[0], buf[0], n, c_tv, from_scalars,
-                                              (float)lambda_arg, pl->ws.S);
-    else
-        k_tv_iter<false><<<grd, blk, 0, st>>>(pl->ws.r, buf[(i - 1) & 1], buf[i & 1], n, c_tv,
-                                               from_scalars, (float)lambda_arg, pl->ws.S);
-    DGCT_LAUNCH_CHECK();
-    *final_buf = i & 1;
-    return DGAMP_CT_OK;
-}
-
-// k_tv iterations (none when lambda would be 0); *final_buf = -1 means x = r.
-int launch_tv_iters(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg,
-                    cudaStream_t st, int* final_buf) {
-    *final_buf = -1;
-    if (!tv_active(pl, from_scalars, lambda_arg)) return DGAMP_CT_OK;
-    for (int i = 0; i < pl->opt.k_tv; ++i) {
-        const int rc = launch_tv_step(pl, nimg, from_scalars, lambda_arg, i, st, final_buf);
-        if (rc != DGAMP_CT_OK) return rc;
+    for (int k = 0; k < iters; ++k) {
+        // q on rows/cols [k+1, R-k)
+        const int lo = k + 1, W = R - k - lo;
+        for (int e = tid; e < nimg * W * W; e += nthr) {
+            const int im = e / (W * W), c = e - im * W * W;
+            const int a = lo + c / W, b = lo + (c - (c / W) * W);
+            const int gi = gi0 + a, gj = gj0 + b;
+            const int idx = im * RR + a * R + b;
+            float q = 0.f;
+            if (gi >= 0 && gi < n && gj >= 0 && gj < n)
+                q = (spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R]) - sr[idx] * inv_lam;
+            sq[idx] = q;
+        }
+        __syncthreads();
+        // p on rows/cols [k+1, R-k-1)
+        const int W2 = W - 1;
+        for (int e = tid; e < nimg * W2 * W2; e += nthr) {
+            const int im = e / (W2 * W2), c = e - im * W2 * W2;
+            const int a = lo + c / W2, b = lo + (c - (c / W2) * W2);
+            const int gi = gi0 + a, gj = gj0 + b;
+            if (gi < 0 || gi >= n || gj < 0 || gj >= n) continue;
+            const int idx = im * RR + a * R + b;
+            const float qc = sq[idx];
+            const float gx = (gj < n - 1) ? sq[idx + 1] - qc : 0.f;
+            const float gy = (gi < n - 1) ? sq[idx + R] - qc : 0.f;
+            const float den = 1.f + kTau * sqrtf(gx * gx + gy * gy);
+            spx[idx] = (spx[idx] + kTau * gx) / den;
+            spy[idx] = (spy[idx] + kTau * gy) / den;
+        }
+        __syncthreads();
     }
-    return DGAMP_CT_OK;
-}
 
-// ------------------------------------------------------- final step -----
-// x = r - lambda div p for each image; optional staging of x for the next
-// projection; divergence b^T (x2 - x1) / (N eps) and, in a solve, tau_x.
-// Tiles of 32 x 32 pixels so that the transposed staging write is coalesced.
-__global__ void __launch_bounds__(TX * TY)
-k_tv_final(const float* __restrict__ rbase, const float2* __restrict__ pbase, int have_p, int n,
-           int nimg, float c_tv, int from_scalars, float lambda_arg, float* x_out,
-           float* __restrict__ XR, float* __restrict__ XC, int ldp, float damp_x, int t_arg,
-           unsigned slice, uint2 key, double tau_r_arg, double tau_x_floor, DevScalars* S,
-           double* partial, IterLog* log, double* div_out, int solve_mode) {
-    __shared__ float tile[32][33];
-    __shared__ double sm[32];
+    if (!final_step) {
+        for (int e = tid; e < nimg * TB * TB; e += nthr) {
+            const int im = e / (TB * TB), c = e - im * TB * TB;
+            const int a = H + c / TB, b = H + (c - (c / TB) * TB);
+            const int gi = gi0 + a, gj = gj0 + b;
+            if (gi >= n || gj >= n) continue;
+            const int idx = im * RR + a * R + b;
+            pout[im * N + (size_t)gi * n + gj] = make_float2(spx[idx], spy[idx]);
+        }
+        return;
+    }
+
+    // ---- final: x = r - lambda div p on the tile, staging, divergence ----
+    __shared__ double red[32];
     __shared__ bool am_last;
-    const size_t N = (size_t)n * n;
-    const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
-    const unsigned t = t_arg > 0 ? (unsigned)t_arg : S->t;
-    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    const unsigned t = F.t_arg > 0 ? (unsigned)F.t_arg : S->t;
     double acc = 0.0;
-    for (int jj = threadIdx.y; jj < 32; jj += TY) {
-        const int i = by + jj, j = bx + threadIdx.x;
+    float* tile = sq;                  // [TB][TB+1] staging tile for the transposed copy
+    for (int c = tid; c < TB * TB; c += nthr) {
+        const int ta = c / TB, tb = c - (c / TB) * TB;
+        const int a = H + ta, b = H + tb;
+        const int gi = gi0 + a, gj = gj0 + b;
         float xv = 0.f;
-        if (i < n && j < n) {
-            const size_t o = (size_t)i * n + j;
+        if (gi < n && gj < n) {
             float xs[2];
             for (int im = 0; im < nimg; ++im) {
-                float dv = 0.f;
-                if (have_p) {
-                    const float2* P = pbase + im * N;
-                    const float2 pc = P[o];
-                    dv = pc.x + pc.y;
-                    if (j > 0) dv -= P[o - 1].x;
-                    if (i > 0) dv -= P[o - n].y;
-                }
-                xs[im] = rbase[im * N + o] - lam * dv;
+                const int idx = im * RR + a * R + b;
+                const float dv = spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R];
+                xs[im] = sr[idx] - lam * dv;
             }
+            const size_t o = (size_t)gi * n + gj;
             xv = xs[0];
             if (nimg == 2) {
-                const float4 b4 = probe4((unsigned)(o >> 2), t, slice, key);
-                const int k = (int)(o & 3);
-                const float b = k == 0 ? b4.x : (k == 1 ? b4.y : (k == 2 ? b4.z : b4.w));
-                acc += (double)b * (double)(xs[1] - xs[0]);
+                const float4 b4 = probe4((unsigned)(o >> 2), t, F.slice, F.key);
+                const int kk = (int)(o & 3);
+                const float bv = kk == 0 ? b4.x : (kk == 1 ? b4.y : (kk == 2 ? b4.z : b4.w));
+                acc += (double)bv * (double)(xs[1] - xs[0]);
             }
-            if (solve_mode && damp_x != 1.f) xv = damp_x * xv + (1.f - damp_x) * x_out[o];
-            x_out[o] = xv;
-            if (XR) XR[(size_t)i * ldp + kPad + j] = xv;
+            if (F.solve_mode && F.damp_x != 1.f) xv = F.damp_x * xv + (1.f - F.damp_x) * F.x_out[o];
+            F.x_out[o] = xv;
+            if (F.XR) F.XR[(size_t)gi * F.ldp + kPad + gj] = xv;
         }
-        tile[jj][threadIdx.x] = xv;
+        tile[ta * (TB + 1) + tb] = xv;
     }
-    if (XC) {
+    if (F.XC) {
         __syncthreads();
-        for (int jj = threadIdx.y; jj < 32; jj += TY) {
-            const int j = bx + jj, i = by + threadIdx.x;
-            if (i < n && j < n) XC[(size_t)j * ldp + kPad + i] = tile[threadIdx.x][jj];
+        for (int c = tid; c < TB * TB; c += nthr) {
+            const int ta = c / TB, tb = c - (c / TB) * TB;     // ta: tile column, tb: tile row
+            const int gj = gj0 + H + ta, gi = gi0 + H + tb;
+            if (gi < n && gj < n) F.XC[(size_t)gj * F.ldp + kPad + gi] = tile[tb * (TB + 1) + ta];
         }
     }
     if (nimg < 2) return;
-    acc = block_sum(acc, sm);
+    acc = block_sum(acc, red);
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        partial[bid] = acc;
+    if (tid == 0) {
+        F.partial[bid] = acc;
         __threadfence();
         const unsigned prev = atomicAdd(&S->done_div, 1u);
         am_last = (prev == (unsigned)nblk - 1);
@@ -234,17 +227,16 @@ k_tv_final(const float* __restrict__ rbase, const float2* __restrict__ pbase, in
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    const int tid = threadIdx.y * TX + threadIdx.x;
     double tot = 0.0;
-    for (int b = tid; b < nblk; b += TX * TY) tot += ((volatile double*)partial)[b];
-    tot = block_sum(tot, sm);
+    for (int b = tid; b < nblk; b += nthr) tot += ((volatile double*)F.partial)[b];
+    tot = block_sum(tot, red);
     if (tid == 0) {
         const double div = tot / ((double)N * S->eps);
-        if (div_out) *div_out = div;
-        if (solve_mode) {
+        if (F.div_out) *F.div_out = div;
+        if (F.solve_mode) {
             const double tau_r = S->tau_r;
             double tx = tau_r * div;
-            const double fl = tau_x_floor * tau_r;
+            const double fl = F.tau_x_floor * tau_r;
             if (!(tx >= fl)) { tx = fl; S->floored += 1u; }
             if (!isfinite(tx)) S->nonfinite += 1u;
             S->div = div;
@@ -254,30 +246,80 @@ k_tv_final(const float* __restrict__ rbase, const float2* __restrict__ pbase, in
                 IterLog L;
                 L.tau_x = tx; L.tau_p = S->tau_p; L.tau_s = S->tau_s; L.tau_r = tau_r;
                 L.div = div; L.eps = S->eps;
-                log[tt - 1] = L;
+                F.log[tt - 1] = L;
             }
             S->t = tt + 1u;
         }
-        (void)tau_r_arg;
         S->done_div = 0u;
     }
 }
 
-int launch_tv_final(const dgamp_ct_plan_s* pl, int nimg, int final_buf, int from_scalars,
-                    double lambda_arg, float* x_out, int solve_mode, int t_arg, double* div_out,
-                    cudaStream_t st) {
+bool tv_active(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg) {
+    if (pl->opt.k_tv <= 0) return false;
+    return from_scalars ? pl->opt.c_tv > 0.0 : lambda_arg > 0.0;
+}
+
+int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg) {
+    if (!tv_active(pl, from_scalars, lambda_arg)) return 1;
+    return (pl->opt.k_tv + pl->tv_kb - 1) / pl->tv_kb;
+}
+
+size_t tv_smem_bytes(int nimg, int kb) {
+    const int R = TB + 2 * (kb + 1);
+    return (size_t)4 * nimg * R * R * sizeof(float);
+}
+
+// Launch i (0-based) of the blocked denoiser on nimg images of ws.r; the last
+// launch (i = tv_num_launches - 1) performs the final step.
+int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
+                    float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st) {
     const int n = pl->n;
     const size_t N = (size_t)pl->N;
-    const float2* pb = final_buf < 0 ? pl->ws.p : pl->ws.p + (size_t)final_buf * 2 * N;
-    dim3 blk(TX, TY), grd((n + 31) / 32, (n + 31) / 32);
-    const uint2 key = make_uint2((unsigned)(pl->opt.seed & 0xffffffffu), (unsigned)(pl->opt.seed >> 32));
-    k_tv_final<<<grd, blk, 0, st>>>(pl->ws.r, pb, final_buf >= 0, n, nimg, (float)pl->opt.c_tv,
-                                    from_scalars, (float)lambda_arg, x_out,
-                                    solve_mode ? pl->ws.XR : nullptr, solve_mode ? pl->ws.XC : nullptr,
-                                    pl->ldp, (float)pl->opt.damp_x, t_arg, (unsigned)pl->opt.slice_id,
-                                    key, 0.0, pl->opt.tau_x_floor, pl->ws.S, pl->ws.partial,
-                                    pl->ws.log, div_out, solve_mode);
+    const int KB = pl->tv_kb, H = KB + 1;
+    const bool active = tv_active(pl, from_scalars, lambda_arg);
+    const int nl = tv_num_launches(pl, from_scalars, lambda_arg);
+    const int K = active ? pl->opt.k_tv : 0;
+    const int iters = active ? ((i + 1) * KB <= K ? KB : K - i * KB) : 0;
+    float2* buf[2] = {pl->ws.p, pl->ws.p + 2 * N};
+    const float2* pin = buf[(i + 1) & 1];
+    float2* pout = buf[i & 1];
+    TvFinal F;
+    F.x_out = x_out;
+    F.XR = solve_mode ? pl->ws.XR : nullptr;
+    F.XC = solve_mode ? pl->ws.XC : nullptr;
+    F.ldp = pl->ldp;
+    F.damp_x = (float)pl->opt.damp_x;
+    F.t_arg = t_arg;
+    F.slice = (unsigned)pl->opt.slice_id;
+    F.key = probe_key(pl);
+    F.tau_x_floor = pl->opt.tau_x_floor;
+    F.partial = pl->ws.partial;
+    F.log = pl->ws.log;
+    F.div_out = div_out;
+    F.solve_mode = solve_mode;
+    dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
+    k_tv_block<<<grd, 256, tv_smem_bytes(nimg, KB), st>>>(
+        pl->ws.r, pin, pout, n, nimg, H, iters, i == 0, i == nl - 1, (float)pl->opt.c_tv, from_scalars,
+        (float)lambda_arg, pl->ws.S, F);
     DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// The whole denoiser (and, for nimg = 2, the divergence): tv_num_launches launches.
+int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, float* x_out,
+              int solve_mode, int t_arg, double* div_out, cudaStream_t st) {
+    const int nl = tv_num_launches(pl, from_scalars, lambda_arg);
+    for (int i = 0; i < nl; ++i) {
+        const int rc = launch_tv_chunk(pl, nimg, from_scalars, lambda_arg, i, x_out, solve_mode, t_arg,
+                                       div_out, st);
+        if (rc != DGAMP_CT_OK) return rc;
+    }
+    return DGAMP_CT_OK;
+}
+
+int tv_set_smem_limits(int kb) {
+    const size_t need = tv_smem_bytes(2, kb);
+    DGCT_CUDA(cudaFuncSetAttribute(k_tv_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
     return DGAMP_CT_OK;
 }
 
@@ -304,9 +346,8 @@ __global__ void k_probe(long long n, unsigned t, unsigned slice, uint2 key, floa
 int launch_probe(const dgamp_ct_plan_s* pl, unsigned t, int64_t n, float* b, uint32_t* words,
                  cudaStream_t st) {
     const long long groups = (n + 3) / 4;
-    const uint2 key = make_uint2((unsigned)(pl->opt.seed & 0xffffffffu), (unsigned)(pl->opt.seed >> 32));
-    k_probe<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(n, t, (unsigned)pl->opt.slice_id, key, b,
-                                                              words);
+    k_probe<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(n, t, (unsigned)pl->opt.slice_id,
+                                                              probe_key(pl), b, words);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
