@@ -112,64 +112,76 @@ k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
     float* sr = sm + 3 * nimg * RR;
     const size_t N = (size_t)n * n;
     const int gi0 = blockIdx.y * TB - H, gj0 = blockIdx.x * TB - H;
+    // 2-D thread layout (TX x TY): loops walk rows by TY and columns by TX
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, TY = blockDim.x >> 5;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
     const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
 
-    for (int e = tid; e < nimg * RR; e += nthr) {
-        const int im = e / RR, c = e - im * RR;
-        const int a = c / R, b = c - (c / R) * R;
-        const int gi = gi0 + a, gj = gj0 + b;
-        const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
-        const size_t o = im * N + (size_t)gi * n + gj;
-        sr[e] = in ? rbase[o] : 0.f;
-        float2 p = make_float2(0.f, 0.f);
-        if (in && !first) p = pin[o];
-        spx[e] = p.x;
-        spy[e] = p.y;
+    for (int a = ty; a < R; a += TY) {
+        const int gi = gi0 + a;
+        for (int b = tx; b < R; b += 32) {
+            const int gj = gj0 + b;
+            const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
+            for (int im = 0; im < nimg; ++im) {
+                const int e = im * RR + a * R + b;
+                const size_t o = im * N + (size_t)gi * n + gj;
+                sr[e] = in ? rbase[o] : 0.f;
+                float2 p = make_float2(0.f, 0.f);
+                if (in && !first) p = pin[o];
+                spx[e] = p.x;
+                spy[e] = p.y;
+            }
+        }
     }
     __syncthreads();
 
     for (int k = 0; k < iters; ++k) {
         // q on rows/cols [k+1, R-k)
-        const int lo = k + 1, W = R - k - lo;
-        for (int e = tid; e < nimg * W * W; e += nthr) {
-            const int im = e / (W * W), c = e - im * W * W;
-            const int a = lo + c / W, b = lo + (c - (c / W) * W);
-            const int gi = gi0 + a, gj = gj0 + b;
-            const int idx = im * RR + a * R + b;
-            float q = 0.f;
-            if (gi >= 0 && gi < n && gj >= 0 && gj < n)
-                q = (spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R]) - sr[idx] * inv_lam;
-            sq[idx] = q;
+        const int lo = k + 1, hi = R - k;
+        for (int a = lo + ty; a < hi; a += TY) {
+            const int gi = gi0 + a;
+            for (int b = lo + tx; b < hi; b += 32) {
+                const int gj = gj0 + b;
+                const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
+                for (int im = 0; im < nimg; ++im) {
+                    const int idx = im * RR + a * R + b;
+                    float q = 0.f;
+                    if (in) q = (spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R]) - sr[idx] * inv_lam;
+                    sq[idx] = q;
+                }
+            }
         }
         __syncthreads();
         // p on rows/cols [k+1, R-k-1)
-        const int W2 = W - 1;
-        for (int e = tid; e < nimg * W2 * W2; e += nthr) {
-            const int im = e / (W2 * W2), c = e - im * W2 * W2;
-            const int a = lo + c / W2, b = lo + (c - (c / W2) * W2);
-            const int gi = gi0 + a, gj = gj0 + b;
-            if (gi < 0 || gi >= n || gj < 0 || gj >= n) continue;
-            const int idx = im * RR + a * R + b;
-            const float qc = sq[idx];
-            const float gx = (gj < n - 1) ? sq[idx + 1] - qc : 0.f;
-            const float gy = (gi < n - 1) ? sq[idx + R] - qc : 0.f;
-            const float den = 1.f + kTau * sqrtf(gx * gx + gy * gy);
-            spx[idx] = (spx[idx] + kTau * gx) / den;
-            spy[idx] = (spy[idx] + kTau * gy) / den;
+        for (int a = lo + ty; a < hi - 1; a += TY) {
+            const int gi = gi0 + a;
+            for (int b = lo + tx; b < hi - 1; b += 32) {
+                const int gj = gj0 + b;
+                if (gi < 0 || gi >= n || gj < 0 || gj >= n) continue;
+                for (int im = 0; im < nimg; ++im) {
+                    const int idx = im * RR + a * R + b;
+                    const float qc = sq[idx];
+                    const float gx = (gj < n - 1) ? sq[idx + 1] - qc : 0.f;
+                    const float gy = (gi < n - 1) ? sq[idx + R] - qc : 0.f;
+                    const float inv = 1.f / (1.f + kTau * sqrtf(gx * gx + gy * gy));
+                    spx[idx] = (spx[idx] + kTau * gx) * inv;
+                    spy[idx] = (spy[idx] + kTau * gy) * inv;
+                }
+            }
         }
         __syncthreads();
     }
 
     if (!final_step) {
-        for (int e = tid; e < nimg * TB * TB; e += nthr) {
-            const int im = e / (TB * TB), c = e - im * TB * TB;
-            const int a = H + c / TB, b = H + (c - (c / TB) * TB);
-            const int gi = gi0 + a, gj = gj0 + b;
+        for (int a = H + ty; a < H + TB; a += TY) {
+            const int gi = gi0 + a;
+            const int gj = gj0 + H + tx;
             if (gi >= n || gj >= n) continue;
-            const int idx = im * RR + a * R + b;
-            pout[im * N + (size_t)gi * n + gj] = make_float2(spx[idx], spy[idx]);
+            for (int im = 0; im < nimg; ++im) {
+                const int idx = im * RR + a * R + H + tx;
+                pout[im * N + (size_t)gi * n + gj] = make_float2(spx[idx], spy[idx]);
+            }
         }
         return;
     }
