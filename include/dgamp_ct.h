@@ -203,6 +203,27 @@ int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t plan, int32_t iters);
 int dgamp_ct_profile_iteration(dgamp_ct_plan_t plan, int32_t reps, double* h_ms, int32_t cap,
                                int32_t* count, void* stream);
 
+/* The output step of dgamp_ct_output_step, for callers that cannot allocate
+   device memory (the paper has no counterpart: this is a deployment aid).
+   A host that reserves all GPU memory for its own pool and forbids library
+   allocations, or a latency-critical loop that must not pay for an
+   allocation, can call it without a plan: it allocates nothing, neither
+   with cudaMalloc nor through any library.  Its scratch (the per-block
+   partial sums of tau_s and an arrival counter, about 8 KiB) lives in a
+   fixed __device__ array inside the library that every GPU loading the
+   library keeps until the process exits.
+   Arguments are those of dgamp_ct_output_step plus M, the number of
+   measurements (1 <= M <= DGAMP_CT_NOALLOC_MAX_M; larger M returns
+   DGAMP_CT_ERR_INVALID_ARG).  The first call on a device looks up the
+   scratch's device address with the device current; make that first call
+   before any stream capture.  All calls share the one scratch array: calls
+   that overlap on the GPU (other streams, other host threads) race and
+   must be serialised by the caller. */
+#define DGAMP_CT_NOALLOC_MAX_M (1LL << 24)
+int dgamp_ct_output_step_noalloc(const float* d_z, const float* d_y, const float* d_s_prev,
+                                 int64_t M, double I0, double tau_p, float* d_s, double* d_tau_s,
+                                 void* stream);
+
 /* Human-readable text for an error code (static storage). */
 const char* dgamp_ct_strerror(int code);
 

@@ -26,6 +26,7 @@ EXPORTS = (
     "dgamp_ct_output_step", "dgamp_ct_denoise_tv", "dgamp_ct_denoise_div", "dgamp_ct_probe",
     "dgamp_ct_precond_image", "dgamp_ct_solve", "dgamp_ct_solve_host", "dgamp_ct_solve_launches",
     "dgamp_ct_strerror", "dgamp_ct_last_cuda_error", "dgamp_ct_profile_iteration",
+    "dgamp_ct_output_step_noalloc",
 )
 
 
@@ -90,6 +91,7 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_strerror": (C.c_char_p, [C.c_int]),
         "dgamp_ct_last_cuda_error": (C.c_int, []),
         "dgamp_ct_profile_iteration": (C.c_int, [vp, i32, C.POINTER(dbl), i32, C.POINTER(i32), vp]),
+        "dgamp_ct_output_step_noalloc": (C.c_int, [vp, vp, vp, i64, dbl, dbl, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -128,6 +130,25 @@ def _ptr(t, n_expect=None, name="tensor"):
 def _stream():
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def output_step_noalloc(z, y, s_prev, I0: float, tau_p: float, s_out, tau_s_out):
+    """dgamp_ct_output_step_noalloc: the output step with no plan and no allocation.
+
+    For callers that cannot allocate device memory while running; every
+    buffer is the caller's (``s_out`` float32 like ``z``; ``tau_s_out`` one
+    float64 CUDA element).  Calls share one library-owned scratch array, so
+    calls that overlap on the GPU must be serialised by the caller.
+    """
+    import torch
+    M = z.numel()
+    if not (isinstance(tau_s_out, torch.Tensor) and tau_s_out.is_cuda and tau_s_out.dtype == torch.float64):
+        raise TypeError("tau_s_out must be a float64 CUDA tensor")
+    _check(load().dgamp_ct_output_step_noalloc(
+        _ptr(z, M, "z"), _ptr(y, M, "y"), _ptr(s_prev, M, "s_prev") if s_prev is not None else None,
+        int(M), float(I0), float(tau_p), _ptr(s_out, M, "s_out"), C.c_void_p(tau_s_out.data_ptr()), _stream()),
+        "dgamp_ct_output_step_noalloc")
+    return s_out, tau_s_out
 
 
 class Plan:

@@ -124,4 +124,19 @@ int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y
     return DGAMP_CT_OK;
 }
 
+// The same kernel on caller-supplied scratch (no plan): S holds the arrival
+// counter and the Newton-cap counter, partial[] one FP64 sum per block
+// (at most max_blocks blocks).
+int launch_output_step_scratch(const float* z, const float* y, float* s, long long M, int use_prev,
+                               double tau_p, double logI0, double* tau_s_out, DevScalars* S,
+                               double* partial, int max_blocks, cudaStream_t st) {
+    long long blocks = (M + 255) / 256;
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+    k_output_step<<<(int)blocks, 256, 0, st>>>(z, y, s, M, use_prev, 0, tau_p, logI0, 1, 1.f, 0.0, S,
+                                               partial, tau_s_out);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
 }  // namespace dgct
