@@ -91,6 +91,8 @@ static void view_constants(int n, int nd, const std::vector<double>& ang, std::v
         v.P0 = (long long)std::llround(a0 * q);
         v.PSTEP = (long long)std::llround(as * q);
         v.PDET = (long long)std::llround(ad * q);
+        v.AP = v.PDET > 0 ? v.PDET : -v.PDET;
+        v.sg = v.PDET > 0 ? 1 : -1;
         out[k] = v;
     }
 }
@@ -124,6 +126,10 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
 
     DGCT_CUDA(cudaMemset(w.XR, 0, img_staged * sizeof(float)));
     DGCT_CUDA(cudaMemset(w.XC, 0, img_staged * sizeof(float)));
+    // blocked-TV steps per launch: timed on this geometry (uses the workspace
+    // before the scalar block below is initialised)
+    DGCT_TRY(tv_set_smem_limits());
+    DGCT_TRY(tv_autotune(pl));
     {
         DevScalars s0;
         std::memset(&s0, 0, sizeof(s0));
@@ -168,7 +174,7 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_CUDA(cudaMemcpy(&w.S->frob2, &tot, sizeof(double), cudaMemcpyHostToDevice));
     const int smem_need = 2 * (P > pl->m2 ? P : pl->m2) * (int)sizeof(float2);
     DGCT_TRY(fft_set_smem_limits(smem_need > 48 * 1024 ? smem_need : 48 * 1024));
-    DGCT_TRY(tv_set_smem_limits(pl->tv_kb));
+    DGCT_TRY(tv_set_smem_limits());
     return DGAMP_CT_OK;
 }
 

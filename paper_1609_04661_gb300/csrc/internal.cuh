@@ -23,9 +23,12 @@ constexpr int kNewtonCap = 64;     // output-step iteration cap
 // bound loops.
 struct ViewConst {
     long long P0, PSTEP, PDET;    // a0, a_step, a_det scaled by 2^32
+    long long AP;                 // |PDET|: ray spacing on a march line (>= 2^32)
     float a0, a_step, a_det, w;   // w = path length per step (1/|sin| or 1/|cos|)
     float inv_adet;               // 1 / a_det
     int col;                      // 1: march over columns, interpolate along rows
+    int sg;                       // sign of PDET: +1 if position grows with d
+    int pad;
 };
 
 // Scalars of Algorithm 1 that live on the device for the whole solve.
@@ -193,7 +196,8 @@ int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st);
 int launch_absmax(const dgamp_ct_plan_s* pl, const float* r, cudaStream_t st);
 bool tv_active(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg);
 int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg);
-int tv_set_smem_limits(int kb);
+int tv_set_smem_limits();
+int tv_autotune(dgamp_ct_plan_s* pl);
 int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
                     float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st);
 int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, float* x_out,

@@ -82,6 +82,7 @@ k_project(const float* __restrict__ XR, const float* __restrict__ XC, int ldp, i
         if (s0 <= s1) {
             long long pos = joseph_pos(c, d, s0);
             const float* __restrict__ line = B + (size_t)s0 * ldp + kPad;
+#pragma unroll 4
             for (int s = s0; s <= s1; ++s, pos += c.PSTEP, line += ldp) {
                 int i0;
                 float f;
@@ -138,24 +139,34 @@ k_backproject(const float* __restrict__ sino, int nv, int nd, int n,
             const ViewConst c = svc[vi];
             const int s = c.col ? ix : iy;        // march line of this pixel
             const int k = c.col ? iy : ix;        // index across the line
-            // rays with pos(d, s) in [k-1, k+1): pos ~= t + d a_det, so d lies
-            // within |1/a_det| of dc = (k - t)/a_det (pad is the float rounding margin)
+            // Rays of one view are >= 1 pixel apart on a march line, so pixel k
+            // is tapped by at most two rays: the last ray (in position order)
+            // with pos < k + 1, d1, and the one before it, d2.  d1 is estimated
+            // in float from pos ~= t + d a_det and corrected by at most one ray
+            // with exact fixed-point positions.
             const float t = fmaf((float)s, c.a_step, c.a0);
-            const float dc = ((float)k - t) * c.inv_adet;
-            const float hw = fabsf(c.inv_adet) + 0.01f;
-            const int d0 = max(0, (int)ceilf(fmaxf(dc - hw, -1.f)));
-            const int d1 = min(nd - 1, (int)floorf(fminf(dc + hw, (float)nd)));
-            const float* __restrict__ row = sino + (size_t)(v0 + vi) * nd;
-            float av = 0.f;
-            long long pos = joseph_pos(c, d0, s);
-            for (int d = d0; d <= d1; ++d, pos += c.PDET) {
-                int i0;
-                float f;
-                joseph_tap(pos, i0, f);
-                const float wgt = (i0 == k) ? (1.f - f) : ((i0 + 1 == k) ? f : 0.f);
-                av = fmaf(wgt, __ldg(row + d), av);
+            float df = ((float)(k + 1) - t) * c.inv_adet;          // where pos == k + 1
+            df = fminf(fmaxf(df, -4.f), (float)nd + 4.f);
+            int d1 = c.sg > 0 ? (int)ceilf(df) - 1 : (int)floorf(df) + 1;
+            long long pos1 = joseph_pos(c, d1, s);
+            if ((int)(pos1 >> 32) > k) {
+                pos1 -= c.AP;
+                d1 -= c.sg;
+            } else if ((int)((pos1 + c.AP) >> 32) <= k) {
+                pos1 += c.AP;
+                d1 += c.sg;
             }
-            acc = fmaf(av, c.w, acc);
+            int i1, i2;
+            float f1, f2;
+            joseph_tap(pos1, i1, f1);
+            joseph_tap(pos1 - c.AP, i2, f2);
+            const int d2 = d1 - c.sg;
+            const float w1 = (i1 == k) ? (1.f - f1) : ((i1 == k - 1) ? f1 : 0.f);
+            const float w2 = (i1 == k && i2 == k - 1) ? f2 : 0.f;
+            const float* __restrict__ row = sino + (size_t)(v0 + vi) * nd;
+            const float v1 = (d1 >= 0 && d1 < nd) ? __ldg(row + d1) : 0.f;
+            const float v2 = (d2 >= 0 && d2 < nd) ? __ldg(row + d2) : 0.f;
+            acc = fmaf(fmaf(w1, v1, w2 * v2), c.w, acc);
         }
     }
     const size_t o = (size_t)iy * n + ix;

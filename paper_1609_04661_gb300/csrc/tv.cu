@@ -11,18 +11,22 @@
 // one pixel of it:
 //   q = div p - r/lambda,  div p = px(i,j) - px(i,j-1) + py(i,j) - py(i-1,j)
 //   p <- (p + tau grad q) / (1 + tau |grad q|),  grad q uses q(i,j+1), q(i+1,j)
-// so a block that holds a 32 x 32 tile plus a halo of H pixels in shared
-// memory can run up to H - 1 steps with no global traffic (the valid region
-// shrinks by one pixel per side per step) and still form div p on its tile
-// for the final x = r - lambda div p.  Duals outside the image stay zero,
-// and grad q is zero on the last row/column (Neumann), which reproduces the
-// boundary rules exactly.  Successive launches exchange the tile's duals
-// through ping-pong global buffers [image][n][n] of float2.
+// so a block that holds a 32 x 32 tile plus a halo of H = KB + 1 pixels in
+// shared memory runs KB steps with no global traffic (the valid region
+// shrinks by one pixel per side per step) and can still form div p on its
+// tile for the final x = r - lambda div p.  Duals outside the image stay
+// zero, and grad q is zero on the last row/column (Neumann), which
+// reproduces the boundary rules exactly.  Successive launches exchange the
+// tile's duals through ping-pong global buffers [image][n][n] of float2.
+// KB is a template parameter chosen per plan by timing (tv_autotune).
+#include <vector>
+
 #include "internal.cuh"
 
 namespace dgct {
 
 constexpr int TB = 32;             // interior tile edge
+constexpr int kTvThreads = 1024;
 constexpr float kTau = 0.125f;
 
 __device__ __forceinline__ float solve_lambda(const DevScalars* S, float c_tv, int from_scalars,
@@ -100,88 +104,82 @@ struct TvFinal {
     int solve_mode;        // 1: update tau_x, the log and t in S
 };
 
-__global__ void __launch_bounds__(256)
+template <int NIMG, int KB>
+__global__ void __launch_bounds__(kTvThreads)
 k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout,
-           int n, int nimg, int H, int iters, int first, int final_step, float c_tv, int from_scalars,
-           float lambda_arg, DevScalars* S, TvFinal F) {
+           int n, int iters, int first, int final_step, float c_tv, int from_scalars, float lambda_arg,
+           DevScalars* S, TvFinal F) {
+    constexpr int H = KB + 1, R = TB + 2 * H, RR = R * R;
     extern __shared__ float sm[];
-    const int R = TB + 2 * H, RR = R * R;
-    float* spx = sm;
-    float* spy = sm + nimg * RR;
-    float* sq = sm + 2 * nimg * RR;
-    float* sr = sm + 3 * nimg * RR;
+    float* __restrict__ spx = sm;
+    float* __restrict__ spy = sm + NIMG * RR;
+    float* __restrict__ sq = sm + 2 * NIMG * RR;
+    float* __restrict__ sr = sm + 3 * NIMG * RR;
     const size_t N = (size_t)n * n;
     const int gi0 = blockIdx.y * TB - H, gj0 = blockIdx.x * TB - H;
-    // 2-D thread layout (TX x TY): loops walk rows by TY and columns by TX
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, TY = blockDim.x >> 5;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x;
     const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
     const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
 
-    for (int a = ty; a < R; a += TY) {
-        const int gi = gi0 + a;
-        for (int b = tx; b < R; b += 32) {
-            const int gj = gj0 + b;
-            const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
-            for (int im = 0; im < nimg; ++im) {
-                const int e = im * RR + a * R + b;
-                const size_t o = im * N + (size_t)gi * n + gj;
-                sr[e] = in ? rbase[o] : 0.f;
-                float2 p = make_float2(0.f, 0.f);
-                if (in && !first) p = pin[o];
-                spx[e] = p.x;
-                spy[e] = p.y;
-            }
-        }
+    for (int e = tid; e < NIMG * RR; e += kTvThreads) {
+        const int im = e / RR, c = e - im * RR;
+        const int a = c / R, b = c - a * R;
+        const int gi = gi0 + a, gj = gj0 + b;
+        const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
+        const size_t o = im * N + (size_t)gi * n + gj;
+        sr[e] = in ? rbase[o] : 0.f;
+        float2 p = make_float2(0.f, 0.f);
+        if (in && !first) p = pin[o];
+        spx[e] = p.x;
+        spy[e] = p.y;
     }
     __syncthreads();
 
-    for (int k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+        if (k >= iters) break;
+        const int lo = k + 1;
+        const int W = R - 2 * k - 1;            // compile-time after unrolling
         // q on rows/cols [k+1, R-k)
-        const int lo = k + 1, hi = R - k;
-        for (int a = lo + ty; a < hi; a += TY) {
-            const int gi = gi0 + a;
-            for (int b = lo + tx; b < hi; b += 32) {
-                const int gj = gj0 + b;
-                const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
-                for (int im = 0; im < nimg; ++im) {
-                    const int idx = im * RR + a * R + b;
-                    float q = 0.f;
-                    if (in) q = (spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R]) - sr[idx] * inv_lam;
-                    sq[idx] = q;
-                }
-            }
+        for (int e = tid; e < NIMG * W * W; e += kTvThreads) {
+            const int im = e / (W * W), c = e - im * (W * W);
+            const int a = lo + c / W, b = lo + (c - (c / W) * W);
+            const int gi = gi0 + a, gj = gj0 + b;
+            const int idx = im * RR + a * R + b;
+            float q = 0.f;
+            if (gi >= 0 && gi < n && gj >= 0 && gj < n)
+                q = (spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R]) - sr[idx] * inv_lam;
+            sq[idx] = q;
         }
         __syncthreads();
         // p on rows/cols [k+1, R-k-1)
-        for (int a = lo + ty; a < hi - 1; a += TY) {
-            const int gi = gi0 + a;
-            for (int b = lo + tx; b < hi - 1; b += 32) {
-                const int gj = gj0 + b;
-                if (gi < 0 || gi >= n || gj < 0 || gj >= n) continue;
-                for (int im = 0; im < nimg; ++im) {
-                    const int idx = im * RR + a * R + b;
-                    const float qc = sq[idx];
-                    const float gx = (gj < n - 1) ? sq[idx + 1] - qc : 0.f;
-                    const float gy = (gi < n - 1) ? sq[idx + R] - qc : 0.f;
-                    const float inv = 1.f / (1.f + kTau * sqrtf(gx * gx + gy * gy));
-                    spx[idx] = (spx[idx] + kTau * gx) * inv;
-                    spy[idx] = (spy[idx] + kTau * gy) * inv;
-                }
-            }
+        const int W2 = W - 1;
+        for (int e = tid; e < NIMG * W2 * W2; e += kTvThreads) {
+            const int im = e / (W2 * W2), c = e - im * (W2 * W2);
+            const int a = lo + c / W2, b = lo + (c - (c / W2) * W2);
+            const int gi = gi0 + a, gj = gj0 + b;
+            if (gi < 0 || gi >= n || gj < 0 || gj >= n) continue;
+            const int idx = im * RR + a * R + b;
+            const float qc = sq[idx];
+            const float gx = (gj < n - 1) ? sq[idx + 1] - qc : 0.f;
+            const float gy = (gi < n - 1) ? sq[idx + R] - qc : 0.f;
+            const float g2 = fmaf(gx, gx, gy * gy);
+            const float nrm = g2 > 0.f ? g2 * rsqrtf(g2) : 0.f;
+            const float inv = __frcp_rn(fmaf(kTau, nrm, 1.f));
+            spx[idx] = fmaf(kTau, gx, spx[idx]) * inv;
+            spy[idx] = fmaf(kTau, gy, spy[idx]) * inv;
         }
         __syncthreads();
     }
 
     if (!final_step) {
-        for (int a = H + ty; a < H + TB; a += TY) {
-            const int gi = gi0 + a;
-            const int gj = gj0 + H + tx;
+        for (int e = tid; e < NIMG * TB * TB; e += kTvThreads) {
+            const int im = e / (TB * TB), c = e - im * (TB * TB);
+            const int a = H + c / TB, b = H + (c & (TB - 1));
+            const int gi = gi0 + a, gj = gj0 + b;
             if (gi >= n || gj >= n) continue;
-            for (int im = 0; im < nimg; ++im) {
-                const int idx = im * RR + a * R + H + tx;
-                pout[im * N + (size_t)gi * n + gj] = make_float2(spx[idx], spy[idx]);
-            }
+            const int idx = im * RR + a * R + b;
+            pout[im * N + (size_t)gi * n + gj] = make_float2(spx[idx], spy[idx]);
         }
         return;
     }
@@ -192,25 +190,26 @@ k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
     const unsigned t = F.t_arg > 0 ? (unsigned)F.t_arg : S->t;
     double acc = 0.0;
     float* tile = sq;                  // [TB][TB+1] staging tile for the transposed copy
-    for (int c = tid; c < TB * TB; c += nthr) {
-        const int ta = c / TB, tb = c - (c / TB) * TB;
+    {
+        const int ta = tid >> 5, tb = tid & 31;     // one tile pixel per thread
         const int a = H + ta, b = H + tb;
         const int gi = gi0 + a, gj = gj0 + b;
         float xv = 0.f;
         if (gi < n && gj < n) {
-            float xs[2];
-            for (int im = 0; im < nimg; ++im) {
+            float xs[NIMG];
+#pragma unroll
+            for (int im = 0; im < NIMG; ++im) {
                 const int idx = im * RR + a * R + b;
                 const float dv = spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R];
                 xs[im] = sr[idx] - lam * dv;
             }
             const size_t o = (size_t)gi * n + gj;
             xv = xs[0];
-            if (nimg == 2) {
+            if (NIMG == 2) {
                 const float4 b4 = probe4((unsigned)(o >> 2), t, F.slice, F.key);
                 const int kk = (int)(o & 3);
                 const float bv = kk == 0 ? b4.x : (kk == 1 ? b4.y : (kk == 2 ? b4.z : b4.w));
-                acc += (double)bv * (double)(xs[1] - xs[0]);
+                acc += (double)bv * (double)(xs[NIMG - 1] - xs[0]);
             }
             if (F.solve_mode && F.damp_x != 1.f) xv = F.damp_x * xv + (1.f - F.damp_x) * F.x_out[o];
             F.x_out[o] = xv;
@@ -220,13 +219,11 @@ k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
     }
     if (F.XC) {
         __syncthreads();
-        for (int c = tid; c < TB * TB; c += nthr) {
-            const int ta = c / TB, tb = c - (c / TB) * TB;     // ta: tile column, tb: tile row
-            const int gj = gj0 + H + ta, gi = gi0 + H + tb;
-            if (gi < n && gj < n) F.XC[(size_t)gj * F.ldp + kPad + gi] = tile[tb * (TB + 1) + ta];
-        }
+        const int ta = tid >> 5, tb = tid & 31;     // ta: tile column, tb: tile row
+        const int gj = gj0 + H + ta, gi = gi0 + H + tb;
+        if (gi < n && gj < n) F.XC[(size_t)gj * F.ldp + kPad + gi] = tile[tb * (TB + 1) + ta];
     }
-    if (nimg < 2) return;
+    if (NIMG < 2) return;
     acc = block_sum(acc, red);
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
@@ -240,7 +237,7 @@ k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
     if (!am_last) return;
     __threadfence();
     double tot = 0.0;
-    for (int b = tid; b < nblk; b += nthr) tot += ((volatile double*)F.partial)[b];
+    for (int b = tid; b < nblk; b += kTvThreads) tot += ((volatile double*)F.partial)[b];
     tot = block_sum(tot, red);
     if (tid == 0) {
         const double div = tot / ((double)N * S->eps);
@@ -266,6 +263,9 @@ k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
     }
 }
 
+// Steps per launch the autotuner may choose.
+static const int kTvKbChoices[] = {3, 4, 5, 6, 8, 10};
+
 bool tv_active(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg) {
     if (pl->opt.k_tv <= 0) return false;
     return from_scalars ? pl->opt.c_tv > 0.0 : lambda_arg > 0.0;
@@ -276,9 +276,33 @@ int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_a
     return (pl->opt.k_tv + pl->tv_kb - 1) / pl->tv_kb;
 }
 
-size_t tv_smem_bytes(int nimg, int kb) {
+static size_t tv_smem_bytes(int nimg, int kb) {
     const int R = TB + 2 * (kb + 1);
     return (size_t)4 * nimg * R * R * sizeof(float);
+}
+
+template <int NIMG, int KB>
+static void launch_kb(dim3 grd, size_t smem, cudaStream_t st, const float* r, const float2* pin, float2* pout,
+                      int n, int iters, int first, int fin, float c_tv, int fs, float lam, DevScalars* S,
+                      const TvFinal& F) {
+    k_tv_block<NIMG, KB><<<grd, kTvThreads, smem, st>>>(r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F);
+}
+
+template <int NIMG>
+static int launch_dispatch(int kb, dim3 grd, size_t smem, cudaStream_t st, const float* r, const float2* pin,
+                           float2* pout, int n, int iters, int first, int fin, float c_tv, int fs, float lam,
+                           DevScalars* S, const TvFinal& F) {
+    switch (kb) {
+        case 3: launch_kb<NIMG, 3>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
+        case 4: launch_kb<NIMG, 4>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
+        case 5: launch_kb<NIMG, 5>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
+        case 6: launch_kb<NIMG, 6>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
+        case 8: launch_kb<NIMG, 8>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
+        case 10: launch_kb<NIMG, 10>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
+        default: return DGAMP_CT_ERR_INVALID_ARG;
+    }
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
 }
 
 // Launch i (0-based) of the blocked denoiser on nimg images of ws.r; the last
@@ -287,7 +311,7 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
                     float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st) {
     const int n = pl->n;
     const size_t N = (size_t)pl->N;
-    const int KB = pl->tv_kb, H = KB + 1;
+    const int KB = pl->tv_kb;
     const bool active = tv_active(pl, from_scalars, lambda_arg);
     const int nl = tv_num_launches(pl, from_scalars, lambda_arg);
     const int K = active ? pl->opt.k_tv : 0;
@@ -310,11 +334,13 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     F.div_out = div_out;
     F.solve_mode = solve_mode;
     dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
-    k_tv_block<<<grd, 256, tv_smem_bytes(nimg, KB), st>>>(
-        pl->ws.r, pin, pout, n, nimg, H, iters, i == 0, i == nl - 1, (float)pl->opt.c_tv, from_scalars,
-        (float)lambda_arg, pl->ws.S, F);
-    DGCT_LAUNCH_CHECK();
-    return DGAMP_CT_OK;
+    const size_t smem = tv_smem_bytes(nimg, KB);
+    const float c_tv = (float)pl->opt.c_tv, lam = (float)lambda_arg;
+    if (nimg == 2)
+        return launch_dispatch<2>(KB, grd, smem, st, pl->ws.r, pin, pout, n, iters, i == 0, i == nl - 1, c_tv,
+                                  from_scalars, lam, pl->ws.S, F);
+    return launch_dispatch<1>(KB, grd, smem, st, pl->ws.r, pin, pout, n, iters, i == 0, i == nl - 1, c_tv,
+                              from_scalars, lam, pl->ws.S, F);
 }
 
 // The whole denoiser (and, for nimg = 2, the divergence): tv_num_launches launches.
@@ -329,9 +355,58 @@ int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lamb
     return DGAMP_CT_OK;
 }
 
-int tv_set_smem_limits(int kb) {
-    const size_t need = tv_smem_bytes(2, kb);
-    DGCT_CUDA(cudaFuncSetAttribute(k_tv_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+template <int NIMG, int KB>
+static int set_attr() {
+    DGCT_CUDA(cudaFuncSetAttribute(k_tv_block<NIMG, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tv_smem_bytes(NIMG, KB)));
+    return DGAMP_CT_OK;
+}
+
+int tv_set_smem_limits() {
+    int rc = DGAMP_CT_OK;
+    rc = rc ? rc : set_attr<1, 3>(); rc = rc ? rc : set_attr<2, 3>();
+    rc = rc ? rc : set_attr<1, 4>(); rc = rc ? rc : set_attr<2, 4>();
+    rc = rc ? rc : set_attr<1, 5>(); rc = rc ? rc : set_attr<2, 5>();
+    rc = rc ? rc : set_attr<1, 6>(); rc = rc ? rc : set_attr<2, 6>();
+    rc = rc ? rc : set_attr<1, 8>(); rc = rc ? rc : set_attr<2, 8>();
+    rc = rc ? rc : set_attr<1, 10>(); rc = rc ? rc : set_attr<2, 10>();
+    return rc;
+}
+
+// Plan-time choice of the steps per launch: time the two-image denoiser of
+// the plan's geometry (K = opt.k_tv) for every choice and keep the fastest.
+// Runs on zeroed workspace; the timing does not depend on the values.
+int tv_autotune(dgamp_ct_plan_s* pl) {
+    if (pl->opt.k_tv <= 0) return DGAMP_CT_OK;
+    const size_t N = (size_t)pl->N;
+    DGCT_CUDA(cudaMemset(pl->ws.r, 0, 2 * N * sizeof(float)));
+    DGCT_CUDA(cudaMemset(pl->ws.S, 0, sizeof(DevScalars)));
+    cudaEvent_t e0, e1;
+    DGCT_CUDA(cudaEventCreate(&e0));
+    DGCT_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_kb = pl->tv_kb;
+    for (int kb : kTvKbChoices) {
+        pl->tv_kb = kb;
+        int rc = DGAMP_CT_OK;
+        for (int rep = 0; rep < 4 && rc == DGAMP_CT_OK; ++rep) {      // first rep warms up
+            if (rep == 1) cudaEventRecord(e0, 0);
+            rc = launch_tv(pl, 2, 0, 1.0, pl->ws.x, 0, 1, nullptr, 0);
+        }
+        cudaEventRecord(e1, 0);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (rc != DGAMP_CT_OK || e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rc != DGAMP_CT_OK ? rc : cuda_fail(e);
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_kb = kb; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pl->tv_kb = best_kb;
     return DGAMP_CT_OK;
 }
 
