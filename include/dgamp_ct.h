@@ -122,6 +122,17 @@ int dgamp_ct_set_options(dgamp_ct_plan_t plan, const dgamp_ct_options* opt);
 /* Scalars of the plan: ||Phi~||_F^2 (FP64) and the FFT length P. */
 int dgamp_ct_plan_info(dgamp_ct_plan_t plan, double* frob_sq, int32_t* fft_len);
 
+/* Implementation choices dgamp_ct_plan makes by timing on the plan's
+   geometry (they change speed, not the operator):
+     filter_mode: 0 = H by FFT, 1 = H as a Toeplitz product with the same
+                  kernel h = IFFT_P(g) (no wrap-around since P >= 2 n_det);
+     tv_kb:       Chambolle steps per blocked TV launch, 1..10.
+   get: either pointer may be NULL.  set: a negative value keeps the current
+   choice; out-of-range values return INVALID_ARG.  Setting drops the
+   captured graph. */
+int dgamp_ct_get_tuning(dgamp_ct_plan_t plan, int32_t* filter_mode, int32_t* tv_kb);
+int dgamp_ct_set_tuning(dgamp_ct_plan_t plan, int32_t filter_mode, int32_t tv_kb);
+
 /* z = A x (precond = 0) or z = Phi~ x = H A x (precond = 1); Eq. linCT and
    Algorithm 1, Step 1.  d_img [n][n] -> d_sino [n_views][n_det]. */
 int dgamp_ct_project(dgamp_ct_plan_t plan, const float* d_img, float* d_sino,

@@ -26,7 +26,7 @@ EXPORTS = (
     "dgamp_ct_output_step", "dgamp_ct_denoise_tv", "dgamp_ct_denoise_div", "dgamp_ct_probe",
     "dgamp_ct_precond_image", "dgamp_ct_solve", "dgamp_ct_solve_host", "dgamp_ct_solve_launches",
     "dgamp_ct_strerror", "dgamp_ct_last_cuda_error", "dgamp_ct_profile_iteration",
-    "dgamp_ct_output_step_noalloc",
+    "dgamp_ct_output_step_noalloc", "dgamp_ct_get_tuning", "dgamp_ct_set_tuning",
 )
 
 
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_last_cuda_error": (C.c_int, []),
         "dgamp_ct_profile_iteration": (C.c_int, [vp, i32, C.POINTER(dbl), i32, C.POINTER(i32), vp]),
         "dgamp_ct_output_step_noalloc": (C.c_int, [vp, vp, vp, i64, dbl, dbl, vp, vp, vp]),
+        "dgamp_ct_get_tuning": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32)]),
+        "dgamp_ct_set_tuning": (C.c_int, [vp, i32, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -197,6 +199,15 @@ class Plan:
     @property
     def M(self):
         return self.n_views * self.n_det
+
+    def tuning(self):
+        """The plan-time choices: {"filter_mode": 0 FFT | 1 Toeplitz, "tv_kb": steps per TV launch}."""
+        fm, kb = C.c_int32(), C.c_int32()
+        _check(self._lib.dgamp_ct_get_tuning(self._h, C.byref(fm), C.byref(kb)), "get_tuning")
+        return {"filter_mode": fm.value, "tv_kb": kb.value}
+
+    def set_tuning(self, filter_mode: int = -1, tv_kb: int = -1):
+        _check(self._lib.dgamp_ct_set_tuning(self._h, int(filter_mode), int(tv_kb)), "set_tuning")
 
     def set_options(self, **options):
         o = self.options

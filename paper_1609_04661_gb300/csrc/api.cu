@@ -20,7 +20,7 @@ int cuda_fail(cudaError_t e) {
 
 static void free_ws(Workspace& w) {
     void* ptrs[] = {w.XR, w.XC, w.x, w.r, w.p, w.zraw, w.z, w.s, w.hs, w.y, w.fft2d, w.partial,
-                    w.S, w.log, w.vc, w.gain, w.tw, w.tw2, w.scratch_d};
+                    w.S, w.log, w.vc, w.gain, w.tw, w.tw2, w.scratch_d, w.hx, w.zraw2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -122,6 +122,8 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_TRY(dalloc(&w.gain, (size_t)pl->P));
     DGCT_TRY(dalloc(&w.tw, (size_t)pl->P / 2));
     DGCT_TRY(dalloc(&w.tw2, (size_t)pl->m2 / 2));
+    DGCT_TRY(dalloc(&w.hx, (size_t)2 * pl->nd));
+    DGCT_TRY(dalloc(&w.zraw2, M));
     DGCT_TRY(dalloc(&w.scratch_d, (size_t)(pl->nd + 1) + 2 * pl->nd + pl->nv + (size_t)pl->nv * pl->nd));
 
     DGCT_CUDA(cudaMemset(w.XR, 0, img_staged * sizeof(float)));
@@ -172,9 +174,19 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     for (double v : terms) tot += v;
     pl->frob2 = tot;
     DGCT_CUDA(cudaMemcpy(&w.S->frob2, &tot, sizeof(double), cudaMemcpyHostToDevice));
+    // H's kernel h[0..nd] (FP64, computed on the device above) -> hx for the Toeplitz form
+    {
+        const int nd = pl->nd;
+        std::vector<double> h(nd + 1);
+        DGCT_CUDA(cudaMemcpy(h.data(), w.scratch_d, (nd + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+        std::vector<float> hx(2 * nd - 1);
+        for (int m = -(nd - 1); m <= nd - 1; ++m) hx[m + nd - 1] = (float)h[m < 0 ? -m : m];
+        DGCT_CUDA(cudaMemcpy(w.hx, hx.data(), hx.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     const int smem_need = 2 * (P > pl->m2 ? P : pl->m2) * (int)sizeof(float2);
     DGCT_TRY(fft_set_smem_limits(smem_need > 48 * 1024 ? smem_need : 48 * 1024));
-    DGCT_TRY(tv_set_smem_limits());
+    DGCT_TRY(toeplitz_set_smem_limit(pl->nd));
+    DGCT_TRY(filter_autotune(pl));
     return DGAMP_CT_OK;
 }
 
@@ -331,6 +343,21 @@ int dgamp_ct_plan_info(dgamp_ct_plan_t pl, double* frob_sq, int32_t* fft_len) {
     if (!pl) return DGAMP_CT_ERR_INVALID_ARG;
     if (frob_sq) *frob_sq = pl->frob2;
     if (fft_len) *fft_len = pl->P;
+    return DGAMP_CT_OK;
+}
+
+int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, int32_t* filter_mode, int32_t* tv_kb) {
+    if (!pl) return DGAMP_CT_ERR_INVALID_ARG;
+    if (filter_mode) *filter_mode = pl->filter_mode;
+    if (tv_kb) *tv_kb = pl->tv_kb;
+    return DGAMP_CT_OK;
+}
+
+int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, int32_t filter_mode, int32_t tv_kb) {
+    if (!pl || filter_mode > 1 || tv_kb > 10 || tv_kb == 0) return DGAMP_CT_ERR_INVALID_ARG;
+    if (filter_mode >= 0) pl->filter_mode = filter_mode;
+    if (tv_kb > 0) pl->tv_kb = tv_kb;
+    drop_graph(pl);
     return DGAMP_CT_OK;
 }
 

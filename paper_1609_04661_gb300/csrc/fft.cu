@@ -84,13 +84,130 @@ k_filter_views(const float* in, float* out, int nv, int nd, int P,
     }
 }
 
+// ------------------------------------------------- H as a Toeplitz product --
+// The same operator without an FFT: with zero padding to P >= 2 n_det there
+// is no wrap-around, so (H z)[d] = sum_d' h[|d - d'|] z[d'] with
+// h = IFFT_P(g) (real and even), computed in FP64 at plan time and stored as
+// hx[m + n_det - 1] = h[|m|] for m in (-n_det, n_det).  Block = one view x
+// 128 outputs; each lane keeps 4 consecutive outputs (a sliding window of
+// hx in registers) and the 8 warps split the d' range, their partial sums
+// added in a fixed order.
+constexpr int kTzOut = 128, kTzWarps = 8;
+
+__global__ void __launch_bounds__(32 * kTzWarps)
+k_filter_toeplitz(const float* in, float* out, int nd, const float* __restrict__ hx) {
+    extern __shared__ float sm[];
+    float* zs = sm;                       // [nd]
+    float* hs = sm + nd;                  // [2 nd - 1]
+    float* red = hs + 2 * nd - 1;         // [kTzWarps][kTzOut]
+    const int v = blockIdx.y;
+    const int d0 = blockIdx.x * kTzOut;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const float* row = in + (size_t)v * nd;
+    for (int i = tid; i < nd; i += blockDim.x) zs[i] = row[i];
+    for (int i = tid; i < 2 * nd - 1; i += blockDim.x) hs[i] = hx[i];
+    __syncthreads();
+    const int dl = d0 + 4 * lane;          // this lane's first output
+    const int len = (nd + kTzWarps - 1) / kTzWarps;
+    const int p0 = w * len, p1 = min(nd, p0 + len);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (dl < nd && p0 < p1) {
+        // output dl + i at input d' uses hs[dl + i - d' + nd - 1]
+        int base = dl - p0 + nd - 1;
+        float h0 = hs[base], h1 = hs[min(base + 1, 2 * nd - 2)], h2 = hs[min(base + 2, 2 * nd - 2)],
+              h3 = hs[min(base + 3, 2 * nd - 2)];
+        for (int dp = p0; dp < p1; ++dp) {
+            const float zv = zs[dp];
+            a0 = fmaf(h0, zv, a0);
+            a1 = fmaf(h1, zv, a1);
+            a2 = fmaf(h2, zv, a2);
+            a3 = fmaf(h3, zv, a3);
+            // next d' shifts every index down by one
+            h3 = h2;
+            h2 = h1;
+            h1 = h0;
+            --base;
+            h0 = base >= 0 ? hs[base] : 0.f;
+        }
+    }
+    red[w * kTzOut + 4 * lane + 0] = a0;
+    red[w * kTzOut + 4 * lane + 1] = a1;
+    red[w * kTzOut + 4 * lane + 2] = a2;
+    red[w * kTzOut + 4 * lane + 3] = a3;
+    __syncthreads();
+    for (int o = tid; o < kTzOut; o += blockDim.x) {
+        const int d = d0 + o;
+        if (d >= nd) continue;
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < kTzWarps; ++k) t += red[k * kTzOut + o];
+        out[(size_t)v * nd + d] = t;
+    }
+}
+
+static size_t toeplitz_smem(int nd) {
+    return ((size_t)nd + 2 * nd - 1 + kTzWarps * kTzOut) * sizeof(float);
+}
+
 int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaStream_t st) {
+    if (pl->filter_mode == 1) {
+        // the block reads its whole input row first, so in == out needs a copy
+        const float* src = in;
+        if (in == out) {
+            DGCT_CUDA(cudaMemcpyAsync(pl->ws.zraw2, in, (size_t)pl->M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            src = pl->ws.zraw2;
+        }
+        dim3 grd((pl->nd + kTzOut - 1) / kTzOut, pl->nv);
+        k_filter_toeplitz<<<grd, 32 * kTzWarps, toeplitz_smem(pl->nd), st>>>(src, out, pl->nd, pl->ws.hx);
+        DGCT_LAUNCH_CHECK();
+        return DGAMP_CT_OK;
+    }
     const int P = pl->P;
     const size_t sm = (size_t)2 * P * sizeof(float2);
     const int thr = P >= 1024 ? 512 : (P / 2 >= 32 ? P / 2 : 32);
     k_filter_views<<<(pl->nv + 1) / 2, thr, sm, st>>>(in, out, pl->nv, pl->nd, P, pl->ws.gain,
                                                       pl->ws.tw);
     DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// Plan-time choice between the FFT and the Toeplitz form of H (same operator):
+// time both on the plan's geometry and keep the faster.
+int filter_autotune(dgamp_ct_plan_s* pl) {
+    DGCT_CUDA(cudaMemset(pl->ws.zraw, 0, (size_t)pl->M * sizeof(float)));
+    cudaEvent_t e0, e1;
+    DGCT_CUDA(cudaEventCreate(&e0));
+    DGCT_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_mode = 0;
+    for (int mode = 0; mode < 2; ++mode) {
+        pl->filter_mode = mode;
+        int rc = DGAMP_CT_OK;
+        for (int rep = 0; rep < 6 && rc == DGAMP_CT_OK; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, 0);
+            rc = launch_filter(pl, pl->ws.zraw, pl->ws.z, 0);
+        }
+        cudaEventRecord(e1, 0);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (rc != DGAMP_CT_OK || e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rc != DGAMP_CT_OK ? rc : cuda_fail(e);
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_mode = mode; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pl->filter_mode = best_mode;
+    return DGAMP_CT_OK;
+}
+
+int toeplitz_set_smem_limit(int nd) {
+    const size_t need = toeplitz_smem(nd);
+    if (need > 48 * 1024)
+        DGCT_CUDA(cudaFuncSetAttribute(k_filter_toeplitz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
     return DGAMP_CT_OK;
 }
 

@@ -71,6 +71,8 @@ struct Workspace {
     IterLog* log = nullptr;        // [kMaxIters]
     ViewConst* vc = nullptr;       // [n_views]
     float* gain = nullptr;         // [P]
+    float* hx = nullptr;           // [2 n_det - 1]  H's kernel h[|m|], m = -(n_det-1)..n_det-1
+    float* zraw2 = nullptr;        // [M]  copy for in-place Toeplitz filtering
     float2* tw = nullptr;          // [P/2]   twiddles exp(-2 pi i k / P)
     float2* tw2 = nullptr;         // [n]     twiddles of length 2n
     double* scratch_d = nullptr;   // plan-time FP64 scratch
@@ -87,6 +89,7 @@ struct dgamp_ct_plan_s {
     dgct::Workspace ws;
     int max_partials = 0;
     int tv_kb = 5;                         // Chambolle steps per blocked TV launch
+    int filter_mode = 0;                   // H by 0: FFT, 1: Toeplitz product (plan-time choice)
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;   // stream the graph was captured for (identity only)
@@ -100,10 +103,17 @@ __device__ __forceinline__ long long joseph_pos(const ViewConst& c, int d, int s
     return c.P0 + (long long)d * c.PDET + (long long)s * c.PSTEP;
 }
 
-// Split a 32.32 position into its left tap (floor) and the fraction in [0, 1].
+// Split a 32.32 position into its left tap (floor) and the fraction in [0, 1):
+// the fraction's top 23 bits become the mantissa of a float in [1, 2), so no
+// int-to-float conversion is needed (truncation error < 2^-23).
 __device__ __forceinline__ void joseph_tap(long long pos, int& i0, float& f) {
     i0 = (int)(pos >> 32);
-    f = __uint2float_rn((unsigned)(pos & 0xffffffffLL)) * 2.3283064365386963e-10f;
+    f = __uint_as_float(0x3F800000u | ((unsigned)pos >> 9)) - 1.0f;
+}
+
+// Nearest integer of |x| < 2^22 without a float-to-int conversion.
+__device__ __forceinline__ int round_magic(float x) {
+    return __float_as_int(x + 12582912.0f) - 0x4B400000;
 }
 
 template <typename T>
@@ -187,6 +197,8 @@ int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaSt
 int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out, int inverse,
                          cudaStream_t st);
 int fft_set_smem_limits(int bytes);
+int filter_autotune(dgamp_ct_plan_s* pl);
+int toeplitz_set_smem_limit(int nd);
 // output_step.cu
 int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y, float* s,
                        int use_prev, int from_scalars, double tau_p_arg, double logI0_arg,

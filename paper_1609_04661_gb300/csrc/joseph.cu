@@ -127,6 +127,7 @@ k_backproject(const float* __restrict__ sino, int nv, int nd, int n,
     const int iy = blockIdx.y * blockDim.y + threadIdx.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const bool live = ix < n && iy < n;
+    const float fx = (float)ix, fy = (float)iy, fx1 = fx + 1.f, fy1 = fy + 1.f;
     if (tid == 0) s_max = 0u;
     float acc = 0.f;
     for (int v0 = 0; v0 < nv; v0 += kBpViews) {
@@ -144,10 +145,13 @@ k_backproject(const float* __restrict__ sino, int nv, int nd, int n,
             // with pos < k + 1, d1, and the one before it, d2.  d1 is estimated
             // in float from pos ~= t + d a_det and corrected by at most one ray
             // with exact fixed-point positions.
-            const float t = fmaf((float)s, c.a_step, c.a0);
-            float df = ((float)(k + 1) - t) * c.inv_adet;          // where pos == k + 1
+            const float t = fmaf(c.col ? fx : fy, c.a_step, c.a0);
+            float df = ((c.col ? fy1 : fx1) - t) * c.inv_adet;     // where pos == k + 1
             df = fminf(fmaxf(df, -4.f), (float)nd + 4.f);
-            int d1 = c.sg > 0 ? (int)ceilf(df) - 1 : (int)floorf(df) + 1;
+            // the last ray below k + 1 is ceil(df) - 1 (or floor(df) + 1 when the
+            // position falls with d); rounding df - sg/2 lands within one ray of
+            // it, which the exact correction below absorbs
+            int d1 = round_magic(df - 0.5f * (float)c.sg);
             long long pos1 = joseph_pos(c, d1, s);
             if ((int)(pos1 >> 32) > k) {
                 pos1 -= c.AP;

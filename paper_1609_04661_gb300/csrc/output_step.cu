@@ -37,7 +37,7 @@ __device__ __forceinline__ float mode_delta(float p, float y, float tau_p, float
         if (fabsf(f) <= 4.0e-7f * (fabsf(d * inv_tp) + y + w)) break;
         if (f < 0.f) lo = d; else hi = d;
         const float df = inv_tp + w;
-        const float nt = d - f / df;
+        const float nt = d - __fdividef(f, df);     // an iterate: a fast quotient is enough
         const bool bad = !(nt > lo && nt < hi) || fabsf(2.f * f) > fabsf(dxold * df);
         const float nx = bad ? 0.5f * (lo + hi) : nt;
         dxold = fabsf(nx - d);
@@ -113,11 +113,11 @@ int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y
                        int use_prev, int from_scalars, double tau_p_arg, double logI0_arg,
                        double* tau_s_out, cudaStream_t st) {
     const long long M = pl->M;
-    int blocks = (int)((M + 255) / 256);
+    int blocks = (int)((M + 127) / 128);          // one element per thread, 128-thread blocks
     if (blocks > pl->max_partials) blocks = pl->max_partials;
     const int onsager = from_scalars ? pl->opt.onsager : 1;
     const float damp_s = from_scalars ? (float)pl->opt.damp_s : 1.f;
-    k_output_step<<<blocks, 256, 0, st>>>(z, y, s, M, use_prev, from_scalars, tau_p_arg, logI0_arg,
+    k_output_step<<<blocks, 128, 0, st>>>(z, y, s, M, use_prev, from_scalars, tau_p_arg, logI0_arg,
                                           onsager, damp_s, (double)pl->N, pl->ws.S, pl->ws.partial,
                                           tau_s_out);
     DGCT_LAUNCH_CHECK();

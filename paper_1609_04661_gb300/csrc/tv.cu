@@ -27,6 +27,7 @@ namespace dgct {
 
 constexpr int TB = 32;             // interior tile edge
 constexpr int kTvThreads = 1024;
+constexpr int kTvMaxKb = 10;       // most Chambolle steps one launch may run
 constexpr float kTau = 0.125f;
 
 __device__ __forceinline__ float solve_lambda(const DevScalars* S, float c_tv, int from_scalars,
@@ -104,10 +105,65 @@ struct TvFinal {
     int solve_mode;        // 1: update tau_x, the log and t in S
 };
 
+// KB Chambolle steps on the block's region in shared memory.  BORDER = false
+// is the fast path for blocks whose whole region lies inside the image and
+// away from its last row/column, where no boundary rule applies.
+template <int NIMG, int KB, bool BORDER>
+__device__ __forceinline__ void tv_steps(float* __restrict__ spx, float* __restrict__ spy,
+                                         float* __restrict__ sq, const float* __restrict__ sr, int n,
+                                         int gi0, int gj0, float inv_lam) {
+    constexpr int H = KB + 1, R = TB + 2 * H, RR = R * R;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+        const int lo = k + 1;
+        const int W = R - 2 * k - 1;            // a constant once the loop is unrolled
+        // q on rows/cols [k+1, R-k)
+#pragma unroll
+        for (int im = 0; im < NIMG; ++im) {
+            for (int e = tid; e < W * W; e += kTvThreads) {
+                const int a = lo + e / W, b = lo + (e - (e / W) * W);
+                const int idx = im * RR + a * R + b;
+                float q = (spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R]) - sr[idx] * inv_lam;
+                if (BORDER) {
+                    const int gi = gi0 + a, gj = gj0 + b;
+                    if (!(gi >= 0 && gi < n && gj >= 0 && gj < n)) q = 0.f;
+                }
+                sq[idx] = q;
+            }
+        }
+        __syncthreads();
+        // p on rows/cols [k+1, R-k-1)
+        const int W2 = W - 1;
+#pragma unroll
+        for (int im = 0; im < NIMG; ++im) {
+            for (int e = tid; e < W2 * W2; e += kTvThreads) {
+                const int a = lo + e / W2, b = lo + (e - (e / W2) * W2);
+                const int idx = im * RR + a * R + b;
+                const float qc = sq[idx];
+                float gx = sq[idx + 1] - qc;
+                float gy = sq[idx + R] - qc;
+                if (BORDER) {
+                    const int gi = gi0 + a, gj = gj0 + b;
+                    if (gi < 0 || gi >= n || gj < 0 || gj >= n) continue;
+                    if (gj >= n - 1) gx = 0.f;
+                    if (gi >= n - 1) gy = 0.f;
+                }
+                const float g2 = fmaf(gx, gx, gy * gy);
+                const float nrm = g2 > 0.f ? g2 * rsqrtf(g2) : 0.f;
+                const float inv = __frcp_rn(fmaf(kTau, nrm, 1.f));
+                spx[idx] = fmaf(kTau, gx, spx[idx]) * inv;
+                spy[idx] = fmaf(kTau, gy, spy[idx]) * inv;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <int NIMG, int KB>
 __global__ void __launch_bounds__(kTvThreads)
 k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout,
-           int n, int iters, int first, int final_step, float c_tv, int from_scalars, float lambda_arg,
+           int n, int first, int final_step, float c_tv, int from_scalars, float lambda_arg,
            DevScalars* S, TvFinal F) {
     constexpr int H = KB + 1, R = TB + 2 * H, RR = R * R;
     extern __shared__ float sm[];
@@ -135,42 +191,11 @@ k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
     }
     __syncthreads();
 
-#pragma unroll
-    for (int k = 0; k < KB; ++k) {
-        if (k >= iters) break;
-        const int lo = k + 1;
-        const int W = R - 2 * k - 1;            // compile-time after unrolling
-        // q on rows/cols [k+1, R-k)
-        for (int e = tid; e < NIMG * W * W; e += kTvThreads) {
-            const int im = e / (W * W), c = e - im * (W * W);
-            const int a = lo + c / W, b = lo + (c - (c / W) * W);
-            const int gi = gi0 + a, gj = gj0 + b;
-            const int idx = im * RR + a * R + b;
-            float q = 0.f;
-            if (gi >= 0 && gi < n && gj >= 0 && gj < n)
-                q = (spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R]) - sr[idx] * inv_lam;
-            sq[idx] = q;
-        }
-        __syncthreads();
-        // p on rows/cols [k+1, R-k-1)
-        const int W2 = W - 1;
-        for (int e = tid; e < NIMG * W2 * W2; e += kTvThreads) {
-            const int im = e / (W2 * W2), c = e - im * (W2 * W2);
-            const int a = lo + c / W2, b = lo + (c - (c / W2) * W2);
-            const int gi = gi0 + a, gj = gj0 + b;
-            if (gi < 0 || gi >= n || gj < 0 || gj >= n) continue;
-            const int idx = im * RR + a * R + b;
-            const float qc = sq[idx];
-            const float gx = (gj < n - 1) ? sq[idx + 1] - qc : 0.f;
-            const float gy = (gi < n - 1) ? sq[idx + R] - qc : 0.f;
-            const float g2 = fmaf(gx, gx, gy * gy);
-            const float nrm = g2 > 0.f ? g2 * rsqrtf(g2) : 0.f;
-            const float inv = __frcp_rn(fmaf(kTau, nrm, 1.f));
-            spx[idx] = fmaf(kTau, gx, spx[idx]) * inv;
-            spy[idx] = fmaf(kTau, gy, spy[idx]) * inv;
-        }
-        __syncthreads();
-    }
+    const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + R < n && gj0 + R < n;
+    if (interior)
+        tv_steps<NIMG, KB, false>(spx, spy, sq, sr, n, gi0, gj0, inv_lam);
+    else
+        tv_steps<NIMG, KB, true>(spx, spy, sq, sr, n, gi0, gj0, inv_lam);
 
     if (!final_step) {
         for (int e = tid; e < NIMG * TB * TB; e += kTvThreads) {
@@ -276,31 +301,31 @@ int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_a
     return (pl->opt.k_tv + pl->tv_kb - 1) / pl->tv_kb;
 }
 
-static size_t tv_smem_bytes(int nimg, int kb) {
+static constexpr size_t tv_smem_bytes(int nimg, int kb) {
     const int R = TB + 2 * (kb + 1);
     return (size_t)4 * nimg * R * R * sizeof(float);
 }
 
 template <int NIMG, int KB>
-static void launch_kb(dim3 grd, size_t smem, cudaStream_t st, const float* r, const float2* pin, float2* pout,
-                      int n, int iters, int first, int fin, float c_tv, int fs, float lam, DevScalars* S,
-                      const TvFinal& F) {
-    k_tv_block<NIMG, KB><<<grd, kTvThreads, smem, st>>>(r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F);
+static void launch_kb(dim3 grd, cudaStream_t st, const float* r, const float2* pin, float2* pout, int n,
+                      int first, int fin, float c_tv, int fs, float lam, DevScalars* S, const TvFinal& F) {
+    k_tv_block<NIMG, KB><<<grd, kTvThreads, tv_smem_bytes(NIMG, KB), st>>>(r, pin, pout, n, first, fin, c_tv,
+                                                                           fs, lam, S, F);
 }
 
+// One launch running exactly `steps` Chambolle steps (0..kTvMaxKb).
 template <int NIMG>
-static int launch_dispatch(int kb, dim3 grd, size_t smem, cudaStream_t st, const float* r, const float2* pin,
-                           float2* pout, int n, int iters, int first, int fin, float c_tv, int fs, float lam,
+static int launch_dispatch(int steps, dim3 grd, cudaStream_t st, const float* r, const float2* pin,
+                           float2* pout, int n, int first, int fin, float c_tv, int fs, float lam,
                            DevScalars* S, const TvFinal& F) {
-    switch (kb) {
-        case 3: launch_kb<NIMG, 3>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
-        case 4: launch_kb<NIMG, 4>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
-        case 5: launch_kb<NIMG, 5>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
-        case 6: launch_kb<NIMG, 6>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
-        case 8: launch_kb<NIMG, 8>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
-        case 10: launch_kb<NIMG, 10>(grd, smem, st, r, pin, pout, n, iters, first, fin, c_tv, fs, lam, S, F); break;
+#define DGCT_TV_CASE(KB) \
+    case KB: launch_kb<NIMG, KB>(grd, st, r, pin, pout, n, first, fin, c_tv, fs, lam, S, F); break;
+    switch (steps) {
+        DGCT_TV_CASE(0) DGCT_TV_CASE(1) DGCT_TV_CASE(2) DGCT_TV_CASE(3) DGCT_TV_CASE(4) DGCT_TV_CASE(5)
+        DGCT_TV_CASE(6) DGCT_TV_CASE(7) DGCT_TV_CASE(8) DGCT_TV_CASE(9) DGCT_TV_CASE(10)
         default: return DGAMP_CT_ERR_INVALID_ARG;
     }
+#undef DGCT_TV_CASE
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -334,12 +359,11 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     F.div_out = div_out;
     F.solve_mode = solve_mode;
     dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
-    const size_t smem = tv_smem_bytes(nimg, KB);
     const float c_tv = (float)pl->opt.c_tv, lam = (float)lambda_arg;
     if (nimg == 2)
-        return launch_dispatch<2>(KB, grd, smem, st, pl->ws.r, pin, pout, n, iters, i == 0, i == nl - 1, c_tv,
+        return launch_dispatch<2>(iters, grd, st, pl->ws.r, pin, pout, n, i == 0, i == nl - 1, c_tv,
                                   from_scalars, lam, pl->ws.S, F);
-    return launch_dispatch<1>(KB, grd, smem, st, pl->ws.r, pin, pout, n, iters, i == 0, i == nl - 1, c_tv,
+    return launch_dispatch<1>(iters, grd, st, pl->ws.r, pin, pout, n, i == 0, i == nl - 1, c_tv,
                               from_scalars, lam, pl->ws.S, F);
 }
 
@@ -356,21 +380,16 @@ int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lamb
 }
 
 template <int NIMG, int KB>
-static int set_attr() {
+static int set_attr_range() {
     DGCT_CUDA(cudaFuncSetAttribute(k_tv_block<NIMG, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)tv_smem_bytes(NIMG, KB)));
+    if constexpr (KB > 0) return set_attr_range<NIMG, KB - 1>();
     return DGAMP_CT_OK;
 }
 
 int tv_set_smem_limits() {
-    int rc = DGAMP_CT_OK;
-    rc = rc ? rc : set_attr<1, 3>(); rc = rc ? rc : set_attr<2, 3>();
-    rc = rc ? rc : set_attr<1, 4>(); rc = rc ? rc : set_attr<2, 4>();
-    rc = rc ? rc : set_attr<1, 5>(); rc = rc ? rc : set_attr<2, 5>();
-    rc = rc ? rc : set_attr<1, 6>(); rc = rc ? rc : set_attr<2, 6>();
-    rc = rc ? rc : set_attr<1, 8>(); rc = rc ? rc : set_attr<2, 8>();
-    rc = rc ? rc : set_attr<1, 10>(); rc = rc ? rc : set_attr<2, 10>();
-    return rc;
+    const int rc = set_attr_range<1, kTvMaxKb>();
+    return rc != DGAMP_CT_OK ? rc : set_attr_range<2, kTvMaxKb>();
 }
 
 // Plan-time choice of the steps per launch: time the two-image denoiser of

@@ -98,11 +98,14 @@ def test_gpu_pair_is_adjoint(dg):
             assert abs(lhs - rhs) <= 1e-5 * np.sqrt(np.sum(ax * ax) * np.sum(s * s))
 
 
-@pytest.mark.parametrize("n,nv,nd", [(64, 30, 95), (40, 9, 300), (16, 3, 24)])
-def test_filter_matches_oracle(dg, n, nv, nd):
+@pytest.mark.parametrize("mode", [0, 1])                  # FFT, Toeplitz
+@pytest.mark.parametrize("n,nv,nd", [(64, 30, 95), (40, 9, 300), (16, 3, 24), (512, 5, 729)])
+def test_filter_matches_oracle(dg, n, nv, nd, mode):
     g = Geometry(n, nv, nd)
     s = np.random.default_rng(6).standard_normal((nv, nd))
     with dg.Plan(n, nv, nd) as pl:
+        pl.set_tuning(filter_mode=mode)
+        assert pl.tuning()["filter_mode"] == mode
         h = host(pl.filter(cu(s)))
         # in place as well
         t = cu(s)
@@ -139,10 +142,12 @@ def test_output_step_matches_oracle(dg, tau_p):
     assert (y == 0).any()
 
 
-@pytest.mark.parametrize("n,lam", [(64, 0.3), (77, 0.05), (33, 0.0)])
-def test_tv_matches_oracle(dg, n, lam):
+@pytest.mark.parametrize("kb", [1, 3, 7, 10])           # steps per blocked launch (remainders too)
+@pytest.mark.parametrize("n,lam", [(64, 0.3), (77, 0.05), (33, 0.0), (130, 0.2)])
+def test_tv_matches_oracle(dg, n, lam, kb):
     r = np.cumsum(np.random.default_rng(8).standard_normal((n, n)), axis=1) * 0.1
     with dg.Plan(n, 10, 2 * n, k_tv=20) as pl:
+        pl.set_tuning(tv_kb=kb)
         x = host(pl.denoise_tv(cu(r), lam))
     assert rel(x, tv.tv_prox(r, lam, 20)) < 1e-5
 
