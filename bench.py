@@ -274,11 +274,26 @@ def run_gpu(args):
             algo[kname] = 8 * N + 16 * N + (0 if kname == "tv_block0" else 16 * N)
     tv_ms = sum(v for k, v in prof.items() if k.startswith("tv_block"))
     shares = {k: v / iter_ms for k, v in prof.items()}
-    dom = max(prof, key=prof.get)
-    achieved = algo[dom] / (prof[dom] * 1e-3) / 1e9
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
-            "algorithmic_bytes_per_launch": algo[dom], "launch_ms": prof[dom]}
+    # Dominant kernel = the blocked TV kernel (all its launches of one iteration).
+    # The 512^2 working set is L2-resident, so it is bound by FP32 issue, not HBM:
+    # algorithmic FLOP = 19 per Chambolle pixel-step (q: 3 adds, a scaled r, 1 sub;
+    # grad: 2 subs; |grad|: 2 mul + add + sqrt; 1 + tau|g|: 2; p: 2 x (fma + div))
+    # x K_TV steps x 2 images x N, plus 5 per pixel and image for x = r - lambda div p.
+    # Peak = 152 SMs x 128 FP32 lanes x 2 FLOP x the median SM clock sampled here.
+    tv_launches = [k for k in prof if k.startswith("tv_block")]
+    tv_flop = (19.0 * TV["k_tv"] * 2 + 5.0 * 2) * N
+    clk_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+    tv_tflops = tv_flop / (tv_ms * 1e-3) / 1e12
+    tv_bytes = sum(algo[k] for k in tv_launches)
+    roof = {"kernel": f"k_tv_block ({len(tv_launches)} launches per iteration)", "bound": "alu",
+            "achieved": tv_tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tv_tflops / alu_peak,
+            "traffic": None,
+            "peak_kind": f"FP32 FMA issue peak at the sampled median SM clock ({clk_mhz:.0f} MHz), derived",
+            "algorithmic_flop_per_iteration": tv_flop, "launch_ms_per_iteration": tv_ms,
+            "hbm_view": {"algorithmic_bytes_per_iteration": tv_bytes,
+                         "achieved_gbs": tv_bytes / (tv_ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                         "peak_kind": f"{peak_kind} copy bandwidth"}}
     a_at_bytes = algo["project"] + algo["backproject_update"]
     a_at_ms = prof["project"] + prof["backproject_update"]
 
