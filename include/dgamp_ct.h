@@ -214,6 +214,42 @@ int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t plan, int32_t iters);
 int dgamp_ct_profile_iteration(dgamp_ct_plan_t plan, int32_t reps, double* h_ms, int32_t cap,
                                int32_t* count, void* stream);
 
+/* ---------------------------------------------------------------------------
+   Learned denoiser (Step 4 of Algorithm 1 with a trained network; the paper's
+   Section 4.3 admits any denoiser and Section 1 points to residual CNNs).
+     f: `layers` 3x3 same-padded convolutions, 1 -> 64 -> ... -> 64 -> 1,
+        a bias per output channel, ReLU after every layer but the last;
+     D_sigma(r) = r - sigma f(r / sigma), sigma = sqrt(tau_r) inside a solve.
+   Hidden activations are BF16, accumulation FP32 (tensor cores).  Parameters
+   are FP32 masters in this flat order, per layer l: W_l[ky][kx][c_in][c_out]
+   then b_l[c_out]; the compute copies of the weights are rounded to BF16.
+   Images: float32 [batch][H][W] device buffers.  h_sigma: host array of
+   `batch` positive floats.  The network object owns its parameters, Adam
+   state and workspace (grown on demand).  Calls are stream-ordered except
+   where a host result is returned (then they synchronise the stream). */
+typedef struct dgamp_ct_cnn_s* dgamp_ct_cnn_t;
+
+/* New network with He-initialised weights (std sqrt(2/(9 c_in)), last layer
+   x0.1) from `seed`, zero biases.  3 <= layers <= 64.  Synchronous. */
+int dgamp_ct_cnn_create(int32_t layers, uint64_t seed, dgamp_ct_cnn_t* out);
+void dgamp_ct_cnn_destroy(dgamp_ct_cnn_t net);
+int64_t dgamp_ct_cnn_num_params(dgamp_ct_cnn_t net);
+/* Copy parameters in/out (host float32, exactly num_params values);
+   set_params also resets the Adam state.  Synchronous. */
+int dgamp_ct_cnn_set_params(dgamp_ct_cnn_t net, const float* h_params, int64_t count);
+int dgamp_ct_cnn_get_params(dgamp_ct_cnn_t net, float* h_params, int64_t count);
+/* d_out = D_sigma(d_r) for a batch of images. */
+int dgamp_ct_cnn_denoise(dgamp_ct_cnn_t net, const float* d_r, const float* h_sigma, int32_t batch,
+                         int32_t H, int32_t W, float* d_out, void* stream);
+/* Training loss mean((D_sigma(r) - x)^2) over the batch and its gradient with
+   respect to every parameter (h_grad: num_params floats, may be NULL). */
+int dgamp_ct_cnn_gradients(dgamp_ct_cnn_t net, const float* d_r, const float* d_x, const float* h_sigma,
+                           int32_t batch, int32_t H, int32_t W, double* h_loss, float* h_grad,
+                           void* stream);
+/* One Adam step (beta 0.9/0.999, eps 1e-8, learning rate lr) on that loss. */
+int dgamp_ct_cnn_train_step(dgamp_ct_cnn_t net, const float* d_r, const float* d_x, const float* h_sigma,
+                            int32_t batch, int32_t H, int32_t W, float lr, double* h_loss, void* stream);
+
 /* The output step of dgamp_ct_output_step, for callers that cannot allocate
    device memory (the paper has no counterpart: this is a deployment aid).
    A host that reserves all GPU memory for its own pool and forbids library

@@ -27,6 +27,8 @@ EXPORTS = (
     "dgamp_ct_precond_image", "dgamp_ct_solve", "dgamp_ct_solve_host", "dgamp_ct_solve_launches",
     "dgamp_ct_strerror", "dgamp_ct_last_cuda_error", "dgamp_ct_profile_iteration",
     "dgamp_ct_output_step_noalloc", "dgamp_ct_get_tuning", "dgamp_ct_set_tuning",
+    "dgamp_ct_cnn_create", "dgamp_ct_cnn_destroy", "dgamp_ct_cnn_num_params", "dgamp_ct_cnn_set_params",
+    "dgamp_ct_cnn_get_params", "dgamp_ct_cnn_denoise", "dgamp_ct_cnn_gradients", "dgamp_ct_cnn_train_step",
 )
 
 
@@ -94,6 +96,14 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_output_step_noalloc": (C.c_int, [vp, vp, vp, i64, dbl, dbl, vp, vp, vp]),
         "dgamp_ct_get_tuning": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32)]),
         "dgamp_ct_set_tuning": (C.c_int, [vp, i32, i32]),
+        "dgamp_ct_cnn_create": (C.c_int, [i32, C.c_uint64, C.POINTER(vp)]),
+        "dgamp_ct_cnn_destroy": (None, [vp]),
+        "dgamp_ct_cnn_num_params": (i64, [vp]),
+        "dgamp_ct_cnn_set_params": (C.c_int, [vp, vp, i64]),
+        "dgamp_ct_cnn_get_params": (C.c_int, [vp, vp, i64]),
+        "dgamp_ct_cnn_denoise": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, vp]),
+        "dgamp_ct_cnn_gradients": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, C.POINTER(dbl), vp, vp]),
+        "dgamp_ct_cnn_train_step": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, C.c_float, C.POINTER(dbl), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -325,3 +335,95 @@ class Plan:
 
     def solve_launches(self, iters: int) -> int:
         return int(self._lib.dgamp_ct_solve_launches(self._h, int(iters)))
+
+
+class CNN:
+    """The learned residual denoiser (dgamp_ct_cnn_*): D_sigma(r) = r - sigma f(r/sigma)."""
+
+    def __init__(self, layers: int = 17, seed: int = 0):
+        self._lib = load()
+        h = C.c_void_p()
+        _check(self._lib.dgamp_ct_cnn_create(int(layers), int(seed), C.byref(h)), "dgamp_ct_cnn_create")
+        self._h = h
+        self.layers = int(layers)
+        self.num_params = int(self._lib.dgamp_ct_cnn_num_params(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dgamp_ct_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, flat: np.ndarray):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(self._lib.dgamp_ct_cnn_set_params(self._h, a.ctypes.data_as(C.c_void_p), a.size), "cnn_set_params")
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.num_params, dtype=np.float32)
+        _check(self._lib.dgamp_ct_cnn_get_params(self._h, a.ctypes.data_as(C.c_void_p), a.size), "cnn_get_params")
+        return a
+
+    @staticmethod
+    def _sig(sigma, batch):
+        s = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma, dtype=np.float32), (batch,)))
+        return s
+
+    def denoise(self, r, sigma):
+        import torch
+        B, H, W = (1,) + tuple(r.shape) if r.dim() == 2 else tuple(r.shape)
+        out = torch.empty_like(r)
+        s = self._sig(sigma, B)
+        _check(self._lib.dgamp_ct_cnn_denoise(self._h, _ptr(r), s.ctypes.data_as(C.c_void_p), B, H, W, _ptr(out),
+                                              _stream()), "cnn_denoise")
+        return out
+
+    def gradients(self, r, x, sigma):
+        B, H, W = tuple(r.shape)
+        s = self._sig(sigma, B)
+        loss = C.c_double()
+        g = np.empty(self.num_params, dtype=np.float32)
+        _check(self._lib.dgamp_ct_cnn_gradients(self._h, _ptr(r), _ptr(x), s.ctypes.data_as(C.c_void_p), B, H, W,
+                                                C.byref(loss), g.ctypes.data_as(C.c_void_p), _stream()),
+               "cnn_gradients")
+        return loss.value, g
+
+    def train_step(self, r, x, sigma, lr: float):
+        B, H, W = tuple(r.shape)
+        s = self._sig(sigma, B)
+        loss = C.c_double()
+        _check(self._lib.dgamp_ct_cnn_train_step(self._h, _ptr(r), _ptr(x), s.ctypes.data_as(C.c_void_p), B, H, W,
+                                                 C.c_float(lr), C.byref(loss), _stream()), "cnn_train_step")
+        return loss.value
+
+
+def flatten_params(ws, bs) -> np.ndarray:
+    """Reference-layout parameter vector (per layer W[ky][kx][ci][co] then b) as float32."""
+    parts = []
+    for w, b in zip(ws, bs):
+        parts.append(np.asarray(w, dtype=np.float32).reshape(-1))
+        parts.append(np.asarray(b, dtype=np.float32).reshape(-1))
+    return np.concatenate(parts)
+
+
+def unflatten_params(flat: np.ndarray, layers: int = 17, channels: int = 64):
+    ws, bs, off = [], [], 0
+    for l in range(layers):
+        cin = 1 if l == 0 else channels
+        cout = 1 if l == layers - 1 else channels
+        n = 9 * cin * cout
+        ws.append(np.asarray(flat[off:off + n], dtype=np.float64).reshape(3, 3, cin, cout))
+        off += n
+        bs.append(np.asarray(flat[off:off + cout], dtype=np.float64))
+        off += cout
+    return ws, bs

@@ -1,0 +1,817 @@
+// Learned denoiser of Step 4 (Section 4.3 black-box denoiser; the residual
+// CNN the paper points to in Section 1): forward, backward and Adam on the GPU.
+//
+//   f: 17 layers of 3x3 same-padded convolutions, 1 -> 64 -> ... -> 64 -> 1,
+//      bias per output channel, ReLU after layers 1..16;
+//   D_sigma(r) = r - sigma f(r / sigma)   (residual form, scale-normalised).
+//
+// Layout.  Images FP32 [B][H][W]; hidden activations BF16 channels-last
+// [B][H][W][64]; master parameters FP32 in the flat order of the reference
+// (per layer W[ky][kx][ci][co] then b[co]); compute copies of the 15 hidden
+// weight tensors in BF16 as [co][k] (k = tap*64 + ci) for the forward pass and
+// as [ci][k'] (k' = (8 - tap)*64 + co) for the input gradient, which is then
+// a forward convolution of the output gradient with the flipped, transposed
+// kernel.
+//
+// The 64 -> 64 layers are implicit GEMMs on the tensor cores (mma.sync
+// m16n8k16, BF16 in, FP32 accumulate): a block keeps the whole 64 x 576
+// weight matrix in shared memory, walks 8 x 16-pixel tiles of the batch, and
+// for each tile stages the 10 x 18-pixel input window; each warp owns two
+// 16-pixel rows of the tile and all 64 output channels.  The weight gradient
+// (M = 64 co, N = 64 ci per tap, K = pixels) writes per-block FP32 partials
+// that a second kernel adds in a fixed order.  The first (1 -> 64) and last
+// (64 -> 1) layers are small and run on the CUDA cores.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace dgct {
+
+constexpr int CH = 64;          // hidden channels
+constexpr int KW = 9 * CH;      // GEMM K of a hidden layer (576)
+constexpr int TH = 8, TWD = 16; // pixel tile of the tensor-core kernels (128 pixels)
+constexpr int HALO_H = TH + 2, HALO_W = TWD + 2;
+constexpr int PSTR = 72;        // shared-memory stride (bf16) of one pixel's 64 channels
+constexpr int WSTR = KW + 8;    // shared-memory stride (bf16) of one weight row
+constexpr int CONV_THREADS = 128;
+
+typedef __nv_bfloat16 bf16;
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma16816(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------- first layer --
+// a1 = relu(b0 + conv(u, W0)), u = r / sigma; also stores u for the weight gradient.
+__global__ void k_conv_first(const float* __restrict__ r, const float* __restrict__ sigma, int B, int H, int W,
+                             const float* __restrict__ w0, const float* __restrict__ b0, bf16* __restrict__ a1,
+                             float* __restrict__ u_out) {
+    __shared__ float sw[9 * CH + CH];
+    for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = w0[i];
+    for (int i = threadIdx.x; i < CH; i += blockDim.x) sw[9 * CH + i] = b0[i];
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long HW = (long long)H * W;
+    if (p >= (long long)B * HW) return;
+    const int b = (int)(p / HW);
+    const int y = (int)((p - b * HW) / W), x = (int)(p - b * HW - (long long)y * W);
+    const float inv = 1.0f / sigma[b];
+    const float* img = r + b * HW;
+    float u[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+        u[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? img[(long long)yy * W + xx] * inv : 0.f;
+    }
+    if (u_out) u_out[p] = u[4];
+    bf16* out = a1 + p * CH;
+#pragma unroll 1
+    for (int c0 = 0; c0 < CH; c0 += 8) {
+        __align__(16) bf16 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float acc = sw[9 * CH + c0 + j];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc = fmaf(u[t], sw[t * CH + c0 + j], acc);
+            v[j] = __float2bfloat16_rn(fmaxf(acc, 0.f));
+        }
+        *reinterpret_cast<uint4*>(out + c0) = *reinterpret_cast<const uint4*>(v);
+    }
+}
+
+// ------------------------------------------------------ hidden 64 -> 64 --
+// MODE 0 (forward):  out = relu(bias + conv(in, Wk)), Wk = [co][tap*64 + ci].
+// MODE 1 (input gradient): out = conv(in, Wk) * (mask > 0), Wk = flipped/transposed
+// kernel, `in` = the output gradient, mask = this layer's input activation.
+template <int MODE>
+__global__ void __launch_bounds__(CONV_THREADS)
+k_conv64(const bf16* __restrict__ in, const bf16* __restrict__ wk, const float* __restrict__ bias,
+         const bf16* __restrict__ mask, bf16* __restrict__ out, int B, int H, int W) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    bf16* sw = reinterpret_cast<bf16*>(smraw);                  // [64][WSTR]
+    bf16* st = sw + CH * WSTR;                                  // [HALO_H*HALO_W][PSTR]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // weights: 64 rows x 576 bf16, 16-byte chunks
+    for (int i = tid; i < CH * (KW / 8); i += CONV_THREADS) {
+        const int row = i / (KW / 8), c = i - row * (KW / 8);
+        *reinterpret_cast<uint4*>(sw + row * WSTR + c * 8) = *reinterpret_cast<const uint4*>(wk + row * KW + c * 8);
+    }
+    const int tiles_x = (W + TWD - 1) / TWD, tiles_y = (H + TH - 1) / TH;
+    const int ntiles = B * tiles_x * tiles_y;
+    const int q = lane >> 3, j = lane & 7;
+    const int gid = lane >> 2, tig = lane & 3;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int b = tile / (tiles_x * tiles_y);
+        const int rem = tile - b * tiles_x * tiles_y;
+        const int y0 = (rem / tiles_x) * TH, x0 = (rem - (rem / tiles_x) * tiles_x) * TWD;
+        __syncthreads();   // previous tile's reads of st are done (and weights are in place)
+        for (int i = tid; i < HALO_H * HALO_W * 8; i += CONV_THREADS) {
+            const int pix = i >> 3, c = i & 7;
+            const int yy = y0 - 1 + pix / HALO_W, xx = x0 - 1 + pix % HALO_W;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = *reinterpret_cast<const uint4*>(in + (((long long)b * H + yy) * W + xx) * CH + c * 8);
+            *reinterpret_cast<uint4*>(st + pix * PSTR + c * 8) = v;
+        }
+        __syncthreads();
+        float acc[2][8][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;           // window offsets (0..2) in the halo tile
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                uint32_t a[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int trow = 2 * warp + mt;          // tile row of this m-tile
+                    const int tcol = j + 8 * (q & 1);        // A row = tile column
+                    const bf16* p = st + ((trow + dy) * HALO_W + tcol + dx) * PSTR + kc * 16 + 8 * (q >> 1);
+                    ldsm_x4(a[mt][0], a[mt][1], a[mt][2], a[mt][3], p);
+                }
+#pragma unroll
+                for (int np = 0; np < 4; ++np) {
+                    uint32_t b0, b1, b2, b3;
+                    const bf16* p = sw + (np * 16 + j + 8 * (q >> 1)) * WSTR + tap * CH + kc * 16 + 8 * (q & 1);
+                    ldsm_x4(b0, b1, b2, b3, p);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        mma16816(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                        mma16816(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+                    }
+                }
+            }
+        }
+        // epilogue
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int y = y0 + 2 * warp + mt;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = x0 + gid + 8 * h;
+                if (y >= H || x >= W) continue;
+                const long long o = (((long long)b * H + y) * W + x) * CH;
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const int co = nt * 8 + 2 * tig;
+                    float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
+                    if (MODE == 0) {
+                        v0 = fmaxf(v0 + bias[co], 0.f);
+                        v1 = fmaxf(v1 + bias[co + 1], 0.f);
+                    } else {
+                        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + o + co);
+                        if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
+                        if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
+                    }
+                    *reinterpret_cast<__nv_bfloat162*>(out + o + co) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ last layer --
+// f = b16 + conv(a16, W16) (W16 as [tap][ci]); D = r - sigma f.
+__global__ void k_conv_last(const bf16* __restrict__ a16, const float* __restrict__ w16, const float* __restrict__ b16,
+                            const float* __restrict__ r, const float* __restrict__ sigma, int B, int H, int W,
+                            float* __restrict__ f_out, float* __restrict__ d_out) {
+    __shared__ float sw[9 * CH];
+    for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = w16[i];
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long HW = (long long)H * W;
+    if (p >= (long long)B * HW) return;
+    const int b = (int)(p / HW);
+    const int y = (int)((p - b * HW) / W), x = (int)(p - b * HW - (long long)y * W);
+    float acc = b16[0];
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+        const bf16* a = a16 + (((long long)b * H + yy) * W + xx) * CH;
+#pragma unroll
+        for (int c0 = 0; c0 < CH; c0 += 8) {
+            const uint4 raw = *reinterpret_cast<const uint4*>(a + c0);
+            const __nv_bfloat162* v2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f2 = __bfloat1622float2(v2[k]);
+                acc = fmaf(f2.x, sw[t * CH + c0 + 2 * k], acc);
+                acc = fmaf(f2.y, sw[t * CH + c0 + 2 * k + 1], acc);
+            }
+        }
+    }
+    if (f_out) f_out[p] = acc;
+    if (d_out) d_out[p] = r[p] - sigma[b] * acc;
+}
+
+// g16 = (sum_tap gout[p - off(tap)] W16[tap][ci]) * (a16 > 0)
+__global__ void k_dgrad_last(const float* __restrict__ gout, const float* __restrict__ w16,
+                             const bf16* __restrict__ a16, bf16* __restrict__ g16, int B, int H, int W) {
+    __shared__ float sw[9 * CH];
+    for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = w16[i];
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long HW = (long long)H * W;
+    if (p >= (long long)B * HW) return;
+    const int b = (int)(p / HW);
+    const int y = (int)((p - b * HW) / W), x = (int)(p - b * HW - (long long)y * W);
+    float gv[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        const int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
+        gv[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? gout[b * HW + (long long)yy * W + xx] : 0.f;
+    }
+    const bf16* a = a16 + p * CH;
+    bf16* g = g16 + p * CH;
+    for (int c0 = 0; c0 < CH; c0 += 8) {
+        const uint4 raw = *reinterpret_cast<const uint4*>(a + c0);
+        const bf16* av = reinterpret_cast<const bf16*>(&raw);
+        __align__(16) bf16 o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc = fmaf(gv[t], sw[t * CH + c0 + k], acc);
+            o[k] = __float2bfloat16_rn(__bfloat162float(av[k]) > 0.f ? acc : 0.f);
+        }
+        *reinterpret_cast<uint4*>(g + c0) = *reinterpret_cast<const uint4*>(o);
+    }
+}
+
+// ----------------------------------------------------- weight gradients --
+// Hidden layer: partial[group][tap][co][ci] = sum over the group's pixels of
+// g[p][co] * a[p + off(tap)][ci] (tensor cores: M = co, N = ci, K = pixels).
+__global__ void __launch_bounds__(CONV_THREADS)
+k_wgrad64(const bf16* __restrict__ a, const bf16* __restrict__ g, int B, int H, int W, int ngroups,
+          float* __restrict__ partial) {
+    __shared__ __align__(16) bf16 sg[TH * TWD * PSTR];
+    __shared__ __align__(16) bf16 sa[TH * TWD * PSTR];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q = lane >> 3, j = lane & 7, gid = lane >> 2, tig = lane & 3;
+    const int tap = blockIdx.y, dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int group = blockIdx.x;
+    const int tiles_x = (W + TWD - 1) / TWD, tiles_y = (H + TH - 1) / TH;
+    const int ntiles = B * tiles_x * tiles_y;
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+    for (int tile = group; tile < ntiles; tile += ngroups) {
+        const int b = tile / (tiles_x * tiles_y);
+        const int rem = tile - b * tiles_x * tiles_y;
+        const int y0 = (rem / tiles_x) * TH, x0 = (rem - (rem / tiles_x) * tiles_x) * TWD;
+        __syncthreads();
+        for (int i = tid; i < TH * TWD * 8; i += CONV_THREADS) {
+            const int pix = i >> 3, c = i & 7;
+            const int y = y0 + pix / TWD, x = x0 + pix % TWD;
+            uint4 gv = make_uint4(0u, 0u, 0u, 0u), av = make_uint4(0u, 0u, 0u, 0u);
+            if (y < H && x < W) {
+                gv = *reinterpret_cast<const uint4*>(g + (((long long)b * H + y) * W + x) * CH + c * 8);
+                const int yy = y + dy, xx = x + dx;
+                if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                    av = *reinterpret_cast<const uint4*>(a + (((long long)b * H + yy) * W + xx) * CH + c * 8);
+            }
+            *reinterpret_cast<uint4*>(sg + pix * PSTR + c * 8) = gv;
+            *reinterpret_cast<uint4*>(sa + pix * PSTR + c * 8) = av;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < TH * TWD / 16; ++ks) {
+            // A[m = co][k = pixel]: stored [pixel][co] -> transposed load
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4_t(a0, a1, a2, a3, sg + (ks * 16 + j + 8 * (q >> 1)) * PSTR + warp * 16 + 8 * (q & 1));
+#pragma unroll
+            for (int np = 0; np < 4; ++np) {
+                // B[k = pixel][n = ci]: stored [pixel][ci] -> transposed load
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4_t(b0, b1, b2, b3, sa + (ks * 16 + j + 8 * (q & 1)) * PSTR + np * 16 + 8 * (q >> 1));
+                mma16816(acc[2 * np], a0, a1, a2, a3, b0, b1);
+                mma16816(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+            }
+        }
+    }
+    float* out = partial + ((size_t)group * 9 + tap) * CH * CH;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int ci = nt * 8 + 2 * tig;
+        const int co = warp * 16 + gid;
+        out[co * CH + ci] = acc[nt][0];
+        out[co * CH + ci + 1] = acc[nt][1];
+        out[(co + 8) * CH + ci] = acc[nt][2];
+        out[(co + 8) * CH + ci + 1] = acc[nt][3];
+    }
+}
+
+// grad W (reference layout [tap][ci][co]) = sum over groups of partial[group][tap][co][ci]
+__global__ void k_reduce_wgrad64(const float* __restrict__ partial, int ngroups, float* __restrict__ gw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;     // index in [tap][ci][co]
+    if (i >= 9 * CH * CH) return;
+    const int tap = i / (CH * CH), ci = (i / CH) % CH, co = i % CH;
+    double s = 0.0;
+    for (int gq = 0; gq < ngroups; ++gq) s += partial[((size_t)gq * 9 + tap) * CH * CH + co * CH + ci];
+    gw[i] = (float)s;
+}
+
+// per-group partial sums of a [npix][64] bf16 tensor over pixels (bias gradient)
+__global__ void k_bias_partial(const bf16* __restrict__ g, long long npix, int ngroups, float* __restrict__ partial) {
+    const int c = threadIdx.x & 63, sub = threadIdx.x >> 6, nsub = blockDim.x >> 6;
+    double s = 0.0;
+    for (long long p = (long long)blockIdx.x * nsub + sub; p < npix; p += (long long)ngroups * nsub)
+        s += (double)__bfloat162float(g[p * CH + c]);
+    __shared__ double sm[16][CH];
+    sm[sub][c] = s;
+    __syncthreads();
+    if (sub == 0) {
+        double t = 0.0;
+        for (int k = 0; k < nsub; ++k) t += sm[k][c];
+        partial[blockIdx.x * CH + c] = (float)t;
+    }
+}
+
+__global__ void k_reduce_rows(const float* __restrict__ partial, int ngroups, int width, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= width) return;
+    double s = 0.0;
+    for (int gq = 0; gq < ngroups; ++gq) s += partial[(size_t)gq * width + i];
+    out[i] = (float)s;
+}
+
+// First layer: partial[group][tap*64 + co] = sum_p u[p + off(tap)] g1[p][co];
+// partial[group][9*64 + co] = sum_p g1[p][co].  u is the scaled input r/sigma.
+__global__ void k_wgrad_first(const float* __restrict__ r, const float* __restrict__ sigma, const bf16* __restrict__ g1,
+                              int B, int H, int W, int ngroups, float* __restrict__ partial) {
+    const int c = threadIdx.x & 63, sub = threadIdx.x >> 6, nsub = blockDim.x >> 6;
+    const long long HW = (long long)H * W, npix = B * HW;
+    double s[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) s[t] = 0.0;
+    for (long long p = (long long)blockIdx.x * nsub + sub; p < npix; p += (long long)ngroups * nsub) {
+        const int b = (int)(p / HW);
+        const int y = (int)((p - b * HW) / W), x = (int)(p - b * HW - (long long)y * W);
+        const float gv = __bfloat162float(g1[p * CH + c]);
+        const float inv = 1.0f / sigma[b];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) s[t] += (double)(r[b * HW + (long long)yy * W + xx] * inv) * gv;
+        }
+        s[9] += gv;
+    }
+    __shared__ double sm[4][10 * CH];          // launched with 256 threads: 4 pixel lanes x 64 channels
+#pragma unroll
+    for (int t = 0; t < 10; ++t) sm[sub][t * CH + c] = s[t];
+    __syncthreads();
+    if (sub == 0)
+        for (int t = 0; t < 10; ++t) {
+            double v = 0.0;
+            for (int k = 0; k < nsub; ++k) v += sm[k][t * CH + c];
+            partial[(size_t)blockIdx.x * 10 * CH + t * CH + c] = (float)v;
+        }
+}
+
+// Last layer: partial[group][tap*64 + ci] = sum_p a16[p + off(tap)][ci] gout[p]; [9*64] = sum gout.
+__global__ void k_wgrad_last(const bf16* __restrict__ a16, const float* __restrict__ gout, int B, int H, int W,
+                             int ngroups, float* __restrict__ partial) {
+    const int c = threadIdx.x & 63, sub = threadIdx.x >> 6, nsub = blockDim.x >> 6;
+    const long long HW = (long long)H * W, npix = B * HW;
+    double s[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) s[t] = 0.0;
+    for (long long p = (long long)blockIdx.x * nsub + sub; p < npix; p += (long long)ngroups * nsub) {
+        const int b = (int)(p / HW);
+        const int y = (int)((p - b * HW) / W), x = (int)(p - b * HW - (long long)y * W);
+        const float gv = gout[p];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                s[t] += (double)__bfloat162float(a16[(((long long)b * H + yy) * W + xx) * CH + c]) * gv;
+        }
+        if (c == 0) s[9] += gv;
+    }
+    __shared__ double sm[4][10 * CH];          // launched with 256 threads: 4 pixel lanes x 64 channels
+#pragma unroll
+    for (int t = 0; t < 10; ++t) sm[sub][t * CH + c] = s[t];
+    __syncthreads();
+    if (sub == 0)
+        for (int t = 0; t < 10; ++t) {
+            double v = 0.0;
+            for (int k = 0; k < nsub; ++k) v += sm[k][t * CH + c];
+            partial[(size_t)blockIdx.x * 10 * CH + t * CH + c] = (float)v;
+        }
+}
+
+// ------------------------------------------------------------- training --
+// e = (r - sigma f) - x_true; loss partials sum e^2; gout = -2 sigma e / count
+__global__ void k_loss(const float* __restrict__ r, const float* __restrict__ sigma, const float* __restrict__ f,
+                       const float* __restrict__ xt, long long HW, long long npix, float* __restrict__ gout,
+                       double* __restrict__ partial) {
+    __shared__ double red[32];
+    double s = 0.0;
+    const double inv_count = 1.0 / (double)npix;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (long long)gridDim.x * blockDim.x) {
+        const float sg = sigma[p / HW];
+        const float e = (r[p] - sg * f[p]) - xt[p];
+        s += (double)e * e;
+        gout[p] = (float)(-2.0 * sg * e * inv_count);
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_loss_final(const double* __restrict__ partial, int n, long long npix, double* __restrict__ loss) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) *loss = s / (double)npix;
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// master (reference layout) -> compute copies.  Hidden weights are rounded to
+// BF16 (round to nearest even) into [co][tap*64+ci] and the flipped
+// transpose [ci][(8-tap)*64+co]; first/last layer weights are rounded to
+// BF16 values and kept in FP32 [tap][c].
+__global__ void k_pack(const float* __restrict__ master, int nhidden, long long off_first, long long off_hidden,
+                       long long stride_hidden, long long off_last, bf16* __restrict__ wh, bf16* __restrict__ wt,
+                       float* __restrict__ w0, float* __restrict__ w16) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long hid = (long long)nhidden * 9 * CH * CH;
+    if (i < hid) {
+        const int l = (int)(i / (9 * CH * CH));
+        const int rem = (int)(i - (long long)l * 9 * CH * CH);
+        const int tap = rem / (CH * CH), ci = (rem / CH) % CH, co = rem % CH;
+        const bf16 v = __float2bfloat16_rn(master[off_hidden + l * stride_hidden + rem]);
+        wh[((size_t)l * CH + co) * KW + tap * CH + ci] = v;
+        wt[((size_t)l * CH + ci) * KW + (8 - tap) * CH + co] = v;
+        return;
+    }
+    const long long k = i - hid;
+    if (k < 9 * CH) {
+        w0[k] = __bfloat162float(__float2bfloat16_rn(master[off_first + k]));    // [tap][co]
+    } else if (k < 18 * CH) {
+        const long long kk = k - 9 * CH;                                           // [tap][ci] (cout = 1)
+        w16[kk] = __bfloat162float(__float2bfloat16_rn(master[off_last + kk]));
+    }
+}
+
+}  // namespace dgct
+
+// ======================================================================
+//                               C ABI
+// ======================================================================
+using namespace dgct;
+
+struct dgamp_ct_cnn_s {
+    int L = 17;
+    int64_t nparam = 0;
+    std::vector<int64_t> w_off, b_off;
+    float* master = nullptr;
+    float* grad = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    int64_t step = 0;
+    bf16* wh = nullptr;   // [15][64][576]
+    bf16* wt = nullptr;   // [15][64][576]
+    float* w0 = nullptr;  // [9][64]
+    float* w16 = nullptr; // [9][64]
+    // shape-dependent workspace
+    int64_t cap_pix = 0;
+    int cap_store = 0;    // activations kept for all layers (training) or 2 (inference)
+    bf16* act = nullptr;  // [cap_store][cap_pix][64]
+    bf16* g0 = nullptr;   // [cap_pix][64]
+    bf16* g1 = nullptr;
+    float* f = nullptr;   // [cap_pix]
+    float* gout = nullptr;
+    float* partial = nullptr;   // wgrad partials
+    double* dpart = nullptr;
+    double* loss = nullptr;
+    float* sig_buf = nullptr;   // per-image sigma (device) [cap_batch]
+    int cap_batch = 0;
+    int conv_grid = 0;
+};
+
+static int kGroups = 32;
+
+static void cnn_free_ws(dgamp_ct_cnn_s* c) {
+    void* ptrs[] = {c->act, c->g0, c->g1, c->f, c->gout, c->partial, c->dpart, c->loss, c->sig_buf};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    c->act = c->g0 = c->g1 = nullptr;
+    c->f = c->gout = c->partial = c->sig_buf = nullptr;
+    c->dpart = c->loss = nullptr;
+    c->cap_pix = 0;
+    c->cap_store = 0;
+    c->cap_batch = 0;
+}
+
+static int cnn_ensure_ws(dgamp_ct_cnn_s* c, int64_t npix, int nstore, int batch) {
+    if (npix <= c->cap_pix && nstore <= c->cap_store && batch <= c->cap_batch) return DGAMP_CT_OK;
+    const int64_t cap = npix > c->cap_pix ? npix : c->cap_pix;
+    const int ns = nstore > c->cap_store ? nstore : c->cap_store;
+    const int cb = batch > c->cap_batch ? batch : c->cap_batch;
+    cnn_free_ws(c);
+    auto A = [](void** p, size_t bytes) -> int {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return DGAMP_CT_ERR_OOM; }
+        return e == cudaSuccess ? DGAMP_CT_OK : cuda_fail(e);
+    };
+    int rc;
+    if ((rc = A((void**)&c->act, (size_t)ns * cap * CH * sizeof(bf16))) != DGAMP_CT_OK) return rc;
+    if ((rc = A((void**)&c->g0, (size_t)cap * CH * sizeof(bf16))) != DGAMP_CT_OK) return rc;
+    if ((rc = A((void**)&c->g1, (size_t)cap * CH * sizeof(bf16))) != DGAMP_CT_OK) return rc;
+    if ((rc = A((void**)&c->f, (size_t)cap * sizeof(float))) != DGAMP_CT_OK) return rc;
+    if ((rc = A((void**)&c->gout, (size_t)cap * sizeof(float))) != DGAMP_CT_OK) return rc;
+    if ((rc = A((void**)&c->partial, (size_t)kGroups * 9 * CH * CH * sizeof(float))) != DGAMP_CT_OK) return rc;
+    if ((rc = A((void**)&c->dpart, 1024 * sizeof(double))) != DGAMP_CT_OK) return rc;
+    if ((rc = A((void**)&c->loss, sizeof(double))) != DGAMP_CT_OK) return rc;
+    if ((rc = A((void**)&c->sig_buf, (size_t)cb * sizeof(float))) != DGAMP_CT_OK) return rc;
+    c->cap_pix = cap;
+    c->cap_store = ns;
+    c->cap_batch = cb;
+    return DGAMP_CT_OK;
+}
+
+static size_t conv_smem() { return (size_t)(CH * WSTR + HALO_H * HALO_W * PSTR) * sizeof(bf16); }
+
+static int cnn_pack(dgamp_ct_cnn_s* c, cudaStream_t st) {
+    const long long tot = (long long)(c->L - 2) * 9 * CH * CH + 18 * CH;
+    const long long stride_hidden = 9LL * CH * CH + CH;
+    k_pack<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(c->master, c->L - 2, c->w_off[0], c->w_off[1], stride_hidden,
+                                                         c->w_off[c->L - 1], c->wh, c->wt, c->w0, c->w16);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// forward over a batch; store_all keeps every activation (for the backward pass)
+static int cnn_forward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int B, int H, int W, float* d_out,
+                       int store_all, cudaStream_t st) {
+    const int64_t npix = (int64_t)B * H * W;
+    const int L = c->L;
+    auto act = [&](int l) -> bf16* {   // activation a_l, l = 1..L-1
+        const int slot = store_all ? (l - 1) : ((l - 1) & 1);
+        return c->act + (size_t)slot * c->cap_pix * CH;
+    };
+    const unsigned blocks = (unsigned)((npix + 127) / 128);
+    k_conv_first<<<blocks, 128, 0, st>>>(r, sig, B, H, W, c->w0, c->master + c->b_off[0], act(1), nullptr);
+    DGCT_LAUNCH_CHECK();
+    const int tiles = B * ((W + TWD - 1) / TWD) * ((H + TH - 1) / TH);
+    const int grid = tiles < c->conv_grid ? tiles : c->conv_grid;
+    for (int l = 1; l <= L - 2; ++l) {
+        k_conv64<0><<<grid, CONV_THREADS, conv_smem(), st>>>(act(l), c->wh + (size_t)(l - 1) * CH * KW,
+                                                             c->master + c->b_off[l], nullptr, act(l + 1), B, H, W);
+        DGCT_LAUNCH_CHECK();
+    }
+    k_conv_last<<<blocks, 128, 0, st>>>(act(L - 1), c->w16, c->master + c->b_off[L - 1], r, sig, B, H, W, c->f, d_out);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// backward of sum(gout * f) after a store_all forward; writes c->grad (reference layout)
+static int cnn_backward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int B, int H, int W, cudaStream_t st) {
+    const int64_t npix = (int64_t)B * H * W;
+    const int L = c->L;
+    auto act = [&](int l) -> bf16* { return c->act + (size_t)(l - 1) * c->cap_pix * CH; };
+    const unsigned blocks = (unsigned)((npix + 127) / 128);
+    const int G = kGroups;
+    // last layer weights and bias
+    k_wgrad_last<<<G, 256, 0, st>>>(act(L - 1), c->gout, B, H, W, G, c->partial);
+    DGCT_LAUNCH_CHECK();
+    k_reduce_rows<<<(10 * CH + 255) / 256, 256, 0, st>>>(c->partial, G, 10 * CH, c->partial + (size_t)G * 10 * CH);
+    DGCT_LAUNCH_CHECK();
+    // scatter [tap*64+ci] -> grad W[L-1] ([tap][ci][1]) and [9*64] -> b
+    DGCT_CUDA(cudaMemcpyAsync(c->grad + c->w_off[L - 1], c->partial + (size_t)G * 10 * CH, 9 * CH * sizeof(float),
+                              cudaMemcpyDeviceToDevice, st));
+    DGCT_CUDA(cudaMemcpyAsync(c->grad + c->b_off[L - 1], c->partial + (size_t)G * 10 * CH + 9 * CH, sizeof(float),
+                              cudaMemcpyDeviceToDevice, st));
+    bf16* gcur = c->g0;
+    bf16* gnext = c->g1;
+    k_dgrad_last<<<blocks, 128, 0, st>>>(c->gout, c->w16, act(L - 1), gcur, B, H, W);
+    DGCT_LAUNCH_CHECK();
+    const int tiles = B * ((W + TWD - 1) / TWD) * ((H + TH - 1) / TH);
+    const int grid = tiles < c->conv_grid ? tiles : c->conv_grid;
+    for (int l = L - 2; l >= 1; --l) {
+        // layer l maps a_l -> z_{l+1}; gcur = dL/dz_{l+1}
+        k_wgrad64<<<dim3(G, 9), CONV_THREADS, 0, st>>>(act(l), gcur, B, H, W, G, c->partial);
+        DGCT_LAUNCH_CHECK();
+        k_reduce_wgrad64<<<(9 * CH * CH + 255) / 256, 256, 0, st>>>(c->partial, G, c->grad + c->w_off[l]);
+        DGCT_LAUNCH_CHECK();
+        k_bias_partial<<<G, 256, 0, st>>>(gcur, npix, G, c->partial);
+        DGCT_LAUNCH_CHECK();
+        k_reduce_rows<<<1, 64, 0, st>>>(c->partial, G, CH, c->grad + c->b_off[l]);
+        DGCT_LAUNCH_CHECK();
+        k_conv64<1><<<grid, CONV_THREADS, conv_smem(), st>>>(gcur, c->wt + (size_t)(l - 1) * CH * KW, nullptr, act(l),
+                                                             gnext, B, H, W);
+        DGCT_LAUNCH_CHECK();
+        bf16* t = gcur;
+        gcur = gnext;
+        gnext = t;
+    }
+    // first layer: gcur = dL/dz_1
+    k_wgrad_first<<<G, 256, 0, st>>>(r, sig, gcur, B, H, W, G, c->partial);
+    DGCT_LAUNCH_CHECK();
+    k_reduce_rows<<<(10 * CH + 255) / 256, 256, 0, st>>>(c->partial, G, 10 * CH, c->grad + c->w_off[0]);
+    DGCT_LAUNCH_CHECK();   // w_off[0] .. +9*64 are W0 [tap][0][co]; the next 64 are b0 (b_off[0] == w_off[0] + 576)
+    return DGAMP_CT_OK;
+}
+
+static int upload_sigma(dgamp_ct_cnn_s* c, const float* h_sigma, int B, cudaStream_t st) {
+    DGCT_CUDA(cudaMemcpyAsync(c->sig_buf, h_sigma, (size_t)B * sizeof(float), cudaMemcpyHostToDevice, st));
+    DGCT_CUDA(cudaStreamSynchronize(st));
+    return DGAMP_CT_OK;
+}
+
+extern "C" {
+
+int dgamp_ct_cnn_create(int32_t layers, uint64_t seed, dgamp_ct_cnn_t* out) {
+    if (!out || layers < 3 || layers > 64) return DGAMP_CT_ERR_INVALID_ARG;
+    *out = nullptr;
+    dgamp_ct_cnn_s* c = new (std::nothrow) dgamp_ct_cnn_s();
+    if (!c) return DGAMP_CT_ERR_OOM;
+    c->L = layers;
+    int64_t off = 0;
+    for (int l = 0; l < layers; ++l) {
+        const int cin = l == 0 ? 1 : CH, cout = l == layers - 1 ? 1 : CH;
+        c->w_off.push_back(off);
+        off += 9LL * cin * cout;
+        c->b_off.push_back(off);
+        off += cout;
+    }
+    c->nparam = off;
+    // He initialisation (std sqrt(2/(9 cin)), last layer x0.1), zero biases, weights rounded to BF16
+    std::vector<float> h(off, 0.f);
+    uint64_t s = seed * 0x9E3779B97F4A7C15ull + 1;
+    auto nextu = [&]() {
+        s ^= s << 13; s ^= s >> 7; s ^= s << 17;
+        return (double)((s >> 11) + 0.5) / 9007199254740992.0;
+    };
+    for (int l = 0; l < layers; ++l) {
+        const int cin = l == 0 ? 1 : CH, cout = l == layers - 1 ? 1 : CH;
+        const double sd = std::sqrt(2.0 / (9.0 * cin)) * (l == layers - 1 ? 0.1 : 1.0);
+        for (int64_t i = 0; i < 9LL * cin * cout; ++i) {
+            const double u1 = nextu(), u2 = nextu();
+            const double g = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+            h[c->w_off[l] + i] = (float)(g * sd);
+        }
+    }
+    const size_t hid = (size_t)(layers - 2) * CH * KW;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc(&c->master, off * sizeof(float));
+    e = e ? e : cudaMalloc(&c->grad, off * sizeof(float));
+    e = e ? e : cudaMalloc(&c->adam_m, off * sizeof(float));
+    e = e ? e : cudaMalloc(&c->adam_v, off * sizeof(float));
+    e = e ? e : cudaMalloc(&c->wh, hid * sizeof(bf16));
+    e = e ? e : cudaMalloc(&c->wt, hid * sizeof(bf16));
+    e = e ? e : cudaMalloc(&c->w0, 9 * CH * sizeof(float));
+    e = e ? e : cudaMalloc(&c->w16, 9 * CH * sizeof(float));
+    e = e ? e : cudaMemcpy(c->master, h.data(), off * sizeof(float), cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemset(c->adam_m, 0, off * sizeof(float));
+    e = e ? e : cudaMemset(c->adam_v, 0, off * sizeof(float));
+    e = e ? e : cudaMemset(c->grad, 0, off * sizeof(float));
+    e = e ? e : cudaFuncSetAttribute(k_conv64<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem());
+    e = e ? e : cudaFuncSetAttribute(k_conv64<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem());
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    c->conv_grid = 2 * (nsm > 0 ? nsm : 152);
+    if (e != cudaSuccess) {
+        dgamp_ct_cnn_destroy(c);
+        return e == cudaErrorMemoryAllocation ? DGAMP_CT_ERR_OOM : cuda_fail(e);
+    }
+    int rc = cnn_pack(c, 0);
+    if (rc == DGAMP_CT_OK) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_fail(e);
+    }
+    if (rc != DGAMP_CT_OK) {
+        dgamp_ct_cnn_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return DGAMP_CT_OK;
+}
+
+void dgamp_ct_cnn_destroy(dgamp_ct_cnn_t c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    cnn_free_ws(c);
+    void* ptrs[] = {c->master, c->grad, c->adam_m, c->adam_v, c->wh, c->wt, c->w0, c->w16};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+int64_t dgamp_ct_cnn_num_params(dgamp_ct_cnn_t c) { return c ? c->nparam : -1; }
+
+int dgamp_ct_cnn_set_params(dgamp_ct_cnn_t c, const float* h_params, int64_t count) {
+    if (!c || !h_params || count != c->nparam) return DGAMP_CT_ERR_INVALID_ARG;
+    DGCT_CUDA(cudaMemcpy(c->master, h_params, count * sizeof(float), cudaMemcpyHostToDevice));
+    DGCT_CUDA(cudaMemset(c->adam_m, 0, count * sizeof(float)));
+    DGCT_CUDA(cudaMemset(c->adam_v, 0, count * sizeof(float)));
+    c->step = 0;
+    int rc = cnn_pack(c, 0);
+    if (rc != DGAMP_CT_OK) return rc;
+    DGCT_CUDA(cudaDeviceSynchronize());
+    return DGAMP_CT_OK;
+}
+
+int dgamp_ct_cnn_get_params(dgamp_ct_cnn_t c, float* h_params, int64_t count) {
+    if (!c || !h_params || count != c->nparam) return DGAMP_CT_ERR_INVALID_ARG;
+    DGCT_CUDA(cudaDeviceSynchronize());
+    DGCT_CUDA(cudaMemcpy(h_params, c->master, count * sizeof(float), cudaMemcpyDeviceToHost));
+    return DGAMP_CT_OK;
+}
+
+int dgamp_ct_cnn_denoise(dgamp_ct_cnn_t c, const float* d_r, const float* h_sigma, int32_t batch, int32_t H,
+                         int32_t W, float* d_out, void* stream) {
+    if (!c || !d_r || !h_sigma || !d_out || batch < 1 || H < 1 || W < 1) return DGAMP_CT_ERR_INVALID_ARG;
+    for (int b = 0; b < batch; ++b)
+        if (!(h_sigma[b] > 0.f) || !std::isfinite(h_sigma[b])) return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t npix = (int64_t)batch * H * W;
+    int rc = cnn_ensure_ws(c, npix, 2, batch);
+    if (rc != DGAMP_CT_OK) return rc;
+    if ((rc = upload_sigma(c, h_sigma, batch, st)) != DGAMP_CT_OK) return rc;
+    return cnn_forward(c, d_r, c->sig_buf, batch, H, W, d_out, 0, st);
+}
+
+int dgamp_ct_cnn_gradients(dgamp_ct_cnn_t c, const float* d_r, const float* d_x, const float* h_sigma, int32_t batch,
+                           int32_t H, int32_t W, double* h_loss, float* h_grad, void* stream) {
+    if (!c || !d_r || !d_x || !h_sigma || batch < 1 || H < 1 || W < 1) return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t npix = (int64_t)batch * H * W;
+    int rc = cnn_ensure_ws(c, npix, c->L - 1, batch);
+    if (rc != DGAMP_CT_OK) return rc;
+    if ((rc = upload_sigma(c, h_sigma, batch, st)) != DGAMP_CT_OK) return rc;
+    if ((rc = cnn_forward(c, d_r, c->sig_buf, batch, H, W, nullptr, 1, st)) != DGAMP_CT_OK) return rc;
+    const int lb = 256;
+    k_loss<<<lb, 256, 0, st>>>(d_r, c->sig_buf, c->f, d_x, (long long)H * W, npix, c->gout, c->dpart);
+    DGCT_LAUNCH_CHECK();
+    k_loss_final<<<1, 256, 0, st>>>(c->dpart, lb, npix, c->loss);
+    DGCT_LAUNCH_CHECK();
+    if ((rc = cnn_backward(c, d_r, c->sig_buf, batch, H, W, st)) != DGAMP_CT_OK) return rc;
+    if (h_loss) DGCT_CUDA(cudaMemcpyAsync(h_loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (h_grad) DGCT_CUDA(cudaMemcpyAsync(h_grad, c->grad, c->nparam * sizeof(float), cudaMemcpyDeviceToHost, st));
+    DGCT_CUDA(cudaStreamSynchronize(st));
+    return DGAMP_CT_OK;
+}
+
+int dgamp_ct_cnn_train_step(dgamp_ct_cnn_t c, const float* d_r, const float* d_x, const float* h_sigma, int32_t batch,
+                            int32_t H, int32_t W, float lr, double* h_loss, void* stream) {
+    if (!(lr > 0.f)) return DGAMP_CT_ERR_INVALID_ARG;
+    int rc = dgamp_ct_cnn_gradients(c, d_r, d_x, h_sigma, batch, H, W, h_loss, nullptr, stream);
+    if (rc != DGAMP_CT_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    c->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)c->step), c2 = 1.f - std::pow(b2, (float)c->step);
+    k_adam<<<(unsigned)((c->nparam + 255) / 256), 256, 0, st>>>(c->master, c->grad, c->adam_m, c->adam_v, c->nparam, lr,
+                                                                b1, b2, 1e-8f, c1, c2);
+    DGCT_LAUNCH_CHECK();
+    return cnn_pack(c, st);
+}
+
+}  // extern "C"
