@@ -69,7 +69,7 @@ typedef struct {
 } dgamp_ct_geometry;
 
 typedef struct {
-    int32_t  denoiser;     /* 0 = proximal TV (Section 6.3)                      */
+    int32_t  denoiser;     /* 0 = proximal TV (Section 6.3), 1 = the attached CNN */
     int32_t  k_tv;         /* Chambolle iterations per denoiser call (fixed)     */
     double   c_tv;         /* TV weight: lambda = c_tv * sqrt(tau_r)             */
     double   eps_rel;      /* MC step: eps = eps_rel * max(max|r|, 1e-6) (Eq. MC_SURE) */
@@ -80,6 +80,10 @@ typedef struct {
     double   damp_s;       /* s <- damp_s s_new + (1-damp_s) s_old; 1 = off      */
     double   tau_x_floor;  /* tau_x = max(tau_r D', tau_x_floor * tau_r)        */
     int32_t  use_graph;    /* 1 = replay one captured CUDA graph per iteration   */
+    int32_t  cnn_scale;    /* learned denoiser: 0 = blind, D(r) = r - f(r);
+                              1 = D(r) = r - sigma f(r/sigma), sigma = sqrt(tau_r) */
+    double   tau_x0;       /* initial tau_x (Algorithm 1 sets 1 in its own, unstated,
+                              normalisation of x); default 1 */
 } dgamp_ct_options;
 
 typedef struct {
@@ -97,6 +101,7 @@ typedef struct {
 } dgamp_ct_stats;
 
 typedef struct dgamp_ct_plan_s* dgamp_ct_plan_t;
+typedef struct dgamp_ct_cnn_s* dgamp_ct_cnn_t;     /* learned denoiser, see dgamp_ct_cnn_create */
 
 /* Fill *opt with the defaults: TV, k_tv = 20, c_tv = 3, eps_rel = 1e-3,
    seed = 12345, slice_id = 0, onsager = 1, no damping, floor 1e-6, graph on. */
@@ -194,6 +199,22 @@ int dgamp_ct_solve(dgamp_ct_plan_t plan, const float* d_counts, double I0,
                    int32_t iters, float* d_mu_out, float* d_x_out,
                    dgamp_ct_stats* stats, void* stream);
 
+/* Attach a learned denoiser to the plan (NULL detaches it).  With
+   opt.denoiser = 1 Step 4 then runs D_sigma(r) = r - sigma f(r/sigma),
+   sigma = sqrt(tau_r), on r and r + eps b as one batch, and the divergence
+   of Eq. MC_SURE from the two outputs.  The network is not owned and must
+   outlive its use; it is not re-entrant either (one stream at a time).
+   Allocates the pair's workspace; synchronous. */
+int dgamp_ct_plan_set_cnn(dgamp_ct_plan_t plan, dgamp_ct_cnn_t net);
+
+/* dgamp_ct_solve without the graph, recording for t = 1..iters the
+   denoiser input r^t into d_r_trace[t-1] ([iters][n][n] device floats,
+   nullable) and tau_r^t into h_tau_r[t-1] (host, nullable; the call then
+   synchronises).  Used to harvest training pairs from the method's own
+   iterates. */
+int dgamp_ct_solve_trace(dgamp_ct_plan_t plan, const float* d_counts, double I0, int32_t iters,
+                         float* d_mu_out, float* d_r_trace, double* h_tau_r, void* stream);
+
 /* dgamp_ct_solve on HOST buffers: copies h_counts to the device, solves and
    copies mu back to h_mu_out; returns after the result is in h_mu_out. */
 int dgamp_ct_solve_host(dgamp_ct_plan_t plan, const float* h_counts, double I0,
@@ -227,7 +248,6 @@ int dgamp_ct_profile_iteration(dgamp_ct_plan_t plan, int32_t reps, double* h_ms,
    `batch` positive floats.  The network object owns its parameters, Adam
    state and workspace (grown on demand).  Calls are stream-ordered except
    where a host result is returned (then they synchronise the stream). */
-typedef struct dgamp_ct_cnn_s* dgamp_ct_cnn_t;
 
 /* New network with He-initialised weights (std sqrt(2/(9 c_in)), last layer
    x0.1) from `seed`, zero biases.  3 <= layers <= 64.  Synchronous. */

@@ -45,6 +45,7 @@ class Options:
     damp_x: float = 1.0
     damp_s: float = 1.0
     tau_x_floor: float = 1e-6
+    tau_x0: float = 1.0      # initial tau_x (Algorithm 1 uses 1)
 
 
 @dataclasses.dataclass
@@ -75,7 +76,7 @@ def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
     Returns the final x.
     """
     x = np.zeros(shape if shape is not None else N) if x0 is None else np.array(x0, dtype=np.float64)
-    tau_x = 1.0
+    tau_x = opts.tau_x0
     s_prev = np.zeros(M)
     for t in range(1, T + 1):
         # Step 1: estimate in the measurement domain

@@ -29,6 +29,7 @@ EXPORTS = (
     "dgamp_ct_output_step_noalloc", "dgamp_ct_get_tuning", "dgamp_ct_set_tuning",
     "dgamp_ct_cnn_create", "dgamp_ct_cnn_destroy", "dgamp_ct_cnn_num_params", "dgamp_ct_cnn_set_params",
     "dgamp_ct_cnn_get_params", "dgamp_ct_cnn_denoise", "dgamp_ct_cnn_gradients", "dgamp_ct_cnn_train_step",
+    "dgamp_ct_plan_set_cnn", "dgamp_ct_solve_trace",
 )
 
 
@@ -50,7 +51,8 @@ class Options(C.Structure):
     _fields_ = [("denoiser", C.c_int32), ("k_tv", C.c_int32), ("c_tv", C.c_double),
                 ("eps_rel", C.c_double), ("seed", C.c_uint64), ("slice_id", C.c_int32),
                 ("onsager", C.c_int32), ("damp_x", C.c_double), ("damp_s", C.c_double),
-                ("tau_x_floor", C.c_double), ("use_graph", C.c_int32)]
+                ("tau_x_floor", C.c_double), ("use_graph", C.c_int32), ("cnn_scale", C.c_int32),
+                ("tau_x0", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -104,6 +106,8 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_cnn_denoise": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, vp]),
         "dgamp_ct_cnn_gradients": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, C.POINTER(dbl), vp, vp]),
         "dgamp_ct_cnn_train_step": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, C.c_float, C.POINTER(dbl), vp]),
+        "dgamp_ct_plan_set_cnn": (C.c_int, [vp, vp]),
+        "dgamp_ct_solve_trace": (C.c_int, [vp, vp, dbl, i32, vp, vp, C.POINTER(dbl), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -329,9 +333,28 @@ class Plan:
         _check(self._lib.dgamp_ct_profile_iteration(self._h, int(reps), arr, cap, C.byref(cnt), _stream()),
                "dgamp_ct_profile_iteration")
         names = ["project", "filter_z", "output_step", "filter_s", "backproject_update", "probe_input"]
-        k = cnt.value - len(names) - 1
-        names += [f"tv_block{i}" for i in range(k)] + ["tv_block_final"]
+        if self.options.denoiser == 1:
+            names += ["cnn_pair", "denoise_final"]
+        else:
+            k = cnt.value - len(names) - 1
+            names += [f"tv_block{i}" for i in range(k)] + ["tv_block_final"]
         return dict(zip(names, [arr[i] for i in range(cnt.value)]))
+
+    def set_cnn(self, net):
+        """Attach a learned denoiser (a CNN) or detach it (None); use with options.denoiser = 1."""
+        _check(self._lib.dgamp_ct_plan_set_cnn(self._h, net._h if net is not None else None), "plan_set_cnn")
+        self._cnn = net
+
+    def solve_trace(self, counts, I0: float, iters: int):
+        """Solve and return (mu, r^t for t = 1..iters as [iters][n][n], tau_r^t)."""
+        import torch
+        mu = self._img()
+        rt = torch.empty((iters, self.n, self.n), dtype=torch.float32, device="cuda")
+        tr = np.zeros(iters)
+        _check(self._lib.dgamp_ct_solve_trace(self._h, _ptr(counts, self.M, "counts"), float(I0), int(iters),
+                                              _ptr(mu), _ptr(rt), tr.ctypes.data_as(C.POINTER(C.c_double)),
+                                              _stream()), "dgamp_ct_solve_trace")
+        return mu, rt, tr
 
     def solve_launches(self, iters: int) -> int:
         return int(self._lib.dgamp_ct_solve_launches(self._h, int(iters)))

@@ -51,12 +51,14 @@ static int ilog2(int v) {
 }
 
 static bool options_ok(const dgamp_ct_options* o) {
-    if (o->denoiser != 0) return false;
+    if (o->denoiser != 0 && o->denoiser != 1) return false;
     if (o->k_tv < 0 || o->k_tv > 100000) return false;
     if (!std::isfinite(o->c_tv) || o->c_tv < 0) return false;
     if (!std::isfinite(o->eps_rel) || o->eps_rel <= 0) return false;
     if (!(o->damp_x > 0 && o->damp_x <= 1) || !(o->damp_s > 0 && o->damp_s <= 1)) return false;
     if (!(o->tau_x_floor >= 0) || !std::isfinite(o->tau_x_floor)) return false;
+    if (!(o->tau_x0 > 0) || !std::isfinite(o->tau_x0)) return false;
+    if (o->cnn_scale != 0 && o->cnn_scale != 1) return false;
     return true;
 }
 
@@ -215,17 +217,34 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
     DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st));            //         r = x + tau_r A^T H s
     DGCT_TRY(mark());
     DGCT_TRY(launch_probe_input(pl, 0, st));                            // Step 4: r + eps b
-    // D(r), D(r + eps b), x, D', tau_x: the blocked TV launches, the last one final
-    const int ntv = tv_num_launches(pl, 1, 0.0);
-    for (int i = 0; i < ntv; ++i) {
+    if (pl->opt.denoiser == 1) {
+        // learned denoiser: D(r) and D(r + eps b) as one batch of two, then x, D', tau_x
         DGCT_TRY(mark());
-        DGCT_TRY(launch_tv_chunk(pl, 2, 1, 0.0, i, w.x, 1, 0, nullptr, st));
+        DGCT_TRY(cnn_denoise_pair(pl->cnn, w.r, w.S, pl->n, pl->dn, pl->opt.cnn_scale, st));
+        DGCT_TRY(mark());
+        DGCT_TRY(launch_denoise_final(pl, pl->dn, w.x, 1, 0, nullptr, st));
+    } else {
+        // D(r), D(r + eps b), x, D', tau_x: the blocked TV launches, the last one final
+        const int ntv = tv_num_launches(pl, 1, 0.0);
+        for (int i = 0; i < ntv; ++i) {
+            DGCT_TRY(mark());
+            DGCT_TRY(launch_tv_chunk(pl, 2, 1, 0.0, i, w.x, 1, 0, nullptr, st));
+        }
     }
     DGCT_TRY(mark());
     return DGAMP_CT_OK;
 }
 
+// kernels one iteration launches
 static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
+    if (pl->opt.denoiser == 1 && pl->cnn) return 6 + cnn_launches_per_pair(pl->cnn) + 1;
+    return 6 + tv_num_launches(pl, 1, 0.0);
+}
+
+// timed segments of one iteration (dgamp_ct_profile_iteration): every kernel,
+// except that the learned denoiser's launches form one segment
+static int segments_per_iteration(const dgamp_ct_plan_s* pl) {
+    if (pl->opt.denoiser == 1 && pl->cnn) return 8;
     return 6 + tv_num_launches(pl, 1, 0.0);
 }
 
@@ -281,6 +300,8 @@ int dgamp_ct_default_options(dgamp_ct_options* o) {
     o->damp_s = 1.0;
     o->tau_x_floor = 1e-6;
     o->use_graph = 1;
+    o->cnn_scale = 0;
+    o->tau_x0 = 1.0;
     return DGAMP_CT_OK;
 }
 
@@ -329,7 +350,27 @@ void dgamp_ct_plan_destroy(dgamp_ct_plan_t pl) {
     cudaDeviceSynchronize();
     drop_graph(pl);
     free_ws(pl->ws);
+    if (pl->dn) cudaFree(pl->dn);
     delete pl;
+}
+
+int dgamp_ct_plan_set_cnn(dgamp_ct_plan_t pl, dgamp_ct_cnn_t net) {
+    if (!pl) return DGAMP_CT_ERR_INVALID_ARG;
+    drop_graph(pl);
+    pl->cnn = net;
+    if (!net) return DGAMP_CT_OK;
+    if (!pl->dn) {
+        cudaError_t e = cudaMalloc(&pl->dn, 2 * (size_t)pl->N * sizeof(float));
+        if (e != cudaSuccess) {
+            pl->dn = nullptr;
+            pl->cnn = nullptr;
+            if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return DGAMP_CT_ERR_OOM; }
+            return cuda_fail(e);
+        }
+    }
+    const int rc = cnn_prepare_pair(net, pl->n);
+    if (rc != DGAMP_CT_OK) pl->cnn = nullptr;
+    return rc;
 }
 
 int dgamp_ct_set_options(dgamp_ct_plan_t pl, const dgamp_ct_options* opt) {
@@ -435,7 +476,8 @@ int dgamp_ct_precond_image(dgamp_ct_plan_t pl, const float* d_in, float* d_out, 
 int dgamp_ct_profile_iteration(dgamp_ct_plan_t pl, int32_t reps, double* h_ms, int32_t cap,
                                int32_t* count, void* stream) {
     if (!pl || reps < 1 || !h_ms || !count) return DGAMP_CT_ERR_INVALID_ARG;
-    const int nk = kernels_per_iteration(pl);
+    if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
+    const int nk = segments_per_iteration(pl);
     *count = nk;
     if (cap < nk) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -461,30 +503,74 @@ int dgamp_ct_profile_iteration(dgamp_ct_plan_t pl, int32_t reps, double* h_ms, i
 
 int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t pl, int32_t iters) {
     if (!pl || iters < 0) return -1;
-    // per iteration, plus the image staging before and the three V^-1 passes after
-    return (int64_t)iters * kernels_per_iteration(pl) + 4;
+    // per iteration, plus the image staging and scalar init before and the three V^-1 passes after
+    return (int64_t)iters * kernels_per_iteration(pl) + 5;
+}
+
+}  // extern "C"
+
+namespace dgct {
+
+__global__ void k_init_scalars(DevScalars* S, double frob2, double logI0, double tau_x0) {
+    DevScalars s;
+    memset(&s, 0, sizeof(s));
+    s.tau_x = tau_x0;              // Algorithm 1 initialisation (1 by default)
+    s.frob2 = frob2;
+    s.logI0 = logI0;
+    s.t = 1u;
+    *S = s;
+}
+
+// Algorithm 1 initialisation (x = 0, tau_x = tau_x0, s_prev = 0) and the counts.
+static int solve_begin(dgamp_ct_plan_s* pl, const float* d_counts, double I0, cudaStream_t st) {
+    Workspace& w = pl->ws;
+    const size_t N = (size_t)pl->N, M = (size_t)pl->M;
+    DGCT_CUDA(cudaMemcpyAsync(w.y, d_counts, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    DGCT_CUDA(cudaMemsetAsync(w.x, 0, N * sizeof(float), st));
+    DGCT_CUDA(cudaMemsetAsync(w.s, 0, M * sizeof(float), st));
+    DGCT_TRY(launch_stage_image(pl, w.x, st));
+    k_init_scalars<<<1, 1, 0, st>>>(w.S, pl->frob2, std::log(I0), pl->opt.tau_x0);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+}  // namespace dgct
+
+extern "C" {
+
+int dgamp_ct_solve_trace(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t iters, float* d_mu_out,
+                         float* d_r_trace, double* h_tau_r, void* stream) {
+    if (!pl || !d_counts || !d_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
+    if (iters < 1 || iters > kMaxIters || !(I0 > 0) || !std::isfinite(I0)) return DGAMP_CT_ERR_INVALID_ARG;
+    if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)pl->N;
+    DGCT_TRY(solve_begin(pl, d_counts, I0, st));
+    for (int t = 0; t < iters; ++t) {
+        DGCT_TRY(enqueue_iteration(pl, st));
+        if (d_r_trace)   // r^t: the denoiser input of iteration t+1 (ws.r image 0)
+            DGCT_CUDA(cudaMemcpyAsync(d_r_trace + (size_t)t * N, pl->ws.r, N * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, st));
+    }
+    DGCT_TRY(launch_precond_image(pl, pl->ws.x, d_mu_out, 1, st));
+    if (h_tau_r) {
+        std::vector<IterLog> lg(iters);
+        DGCT_CUDA(cudaMemcpyAsync(lg.data(), pl->ws.log, iters * sizeof(IterLog), cudaMemcpyDeviceToHost, st));
+        DGCT_CUDA(cudaStreamSynchronize(st));
+        for (int t = 0; t < iters; ++t) h_tau_r[t] = lg[t].tau_r;
+    }
+    return DGAMP_CT_OK;
 }
 
 int dgamp_ct_solve(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t iters, float* d_mu_out,
                    float* d_x_out, dgamp_ct_stats* stats, void* stream) {
     if (!pl || !d_counts || !d_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
     if (iters < 1 || iters > kMaxIters || !(I0 > 0) || !std::isfinite(I0)) return DGAMP_CT_ERR_INVALID_ARG;
+    if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace& w = pl->ws;
-    const size_t N = (size_t)pl->N, M = (size_t)pl->M;
-    // Algorithm 1 initialisation: x = 0, tau_x = 1, s_prev = 0
-    DGCT_CUDA(cudaMemcpyAsync(w.y, d_counts, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    DGCT_CUDA(cudaMemsetAsync(w.x, 0, N * sizeof(float), st));
-    DGCT_CUDA(cudaMemsetAsync(w.s, 0, M * sizeof(float), st));
-    DGCT_TRY(launch_stage_image(pl, w.x, st));
-    static thread_local DevScalars init;   // copied by value before the call returns
-    std::memset(&init, 0, sizeof(init));
-    init.tau_x = 1.0;
-    init.frob2 = pl->frob2;
-    init.logI0 = std::log(I0);
-    init.t = 1u;
-    DGCT_CUDA(cudaMemcpyAsync(w.S, &init, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
-    DGCT_CUDA(cudaStreamSynchronize(st));   // `init` is host stack-like storage
+    const size_t N = (size_t)pl->N;
+    DGCT_TRY(solve_begin(pl, d_counts, I0, st));
     if (pl->opt.use_graph) {
         DGCT_TRY(ensure_graph(pl));
         for (int t = 0; t < iters; ++t) DGCT_CUDA(cudaGraphLaunch(pl->graph, st));

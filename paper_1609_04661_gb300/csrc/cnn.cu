@@ -658,6 +658,28 @@ static int cnn_backward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int
     return DGAMP_CT_OK;
 }
 
+// ------------------------------------------------- use inside a solve ----
+// scaled = 1: sigma = sqrt(tau_r) (read on the device); 0: blind network, sigma = 1
+__global__ void k_sigma_from_tau(const DevScalars* __restrict__ S, float* __restrict__ sig, int n, int scaled) {
+    if (threadIdx.x < n) sig[threadIdx.x] = scaled ? sqrtf((float)S->tau_r) : 1.0f;
+}
+
+namespace dgct {
+// Workspace for denoising pairs of n x n images; call before any capture.
+int cnn_prepare_pair(dgamp_ct_cnn_s* c, int n) { return cnn_ensure_ws(c, 2LL * n * n, 2, 2); }
+
+// out[2][n][n] = D_sigma(rr[2][n][n]), sigma = sqrt(tau_r) read on the device
+// (scaled = 1) or 1 (blind network).
+int cnn_denoise_pair(dgamp_ct_cnn_s* c, const float* rr, const DevScalars* S, int n, float* out, int scaled,
+                     cudaStream_t st) {
+    k_sigma_from_tau<<<1, 32, 0, st>>>(S, c->sig_buf, 2, scaled);
+    DGCT_LAUNCH_CHECK();
+    return cnn_forward(c, rr, c->sig_buf, 2, n, n, out, 0, st);
+}
+
+int cnn_launches_per_pair(const dgamp_ct_cnn_s* c) { return 1 + c->L; }
+}  // namespace dgct
+
 static int upload_sigma(dgamp_ct_cnn_s* c, const float* h_sigma, int B, cudaStream_t st) {
     DGCT_CUDA(cudaMemcpyAsync(c->sig_buf, h_sigma, (size_t)B * sizeof(float), cudaMemcpyHostToDevice, st));
     DGCT_CUDA(cudaStreamSynchronize(st));

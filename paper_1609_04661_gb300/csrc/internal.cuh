@@ -80,7 +80,11 @@ struct Workspace {
 
 }  // namespace dgct
 
+struct dgamp_ct_cnn_s;
+
 struct dgamp_ct_plan_s {
+    dgamp_ct_cnn_s* cnn = nullptr;         // learned denoiser (not owned), used when opt.denoiser == 1
+    float* dn = nullptr;                   // [2][n][n] its outputs D(r), D(r + eps b)
     int device = 0;
     int n = 0, nv = 0, nd = 0, P = 0, logP = 0, m2 = 0, logm2 = 0, ldp = 0;
     int64_t N = 0, M = 0;
@@ -216,5 +220,13 @@ int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lamb
               int solve_mode, int t_arg, double* div_out, cudaStream_t st);
 int launch_probe(const dgamp_ct_plan_s* pl, unsigned t, int64_t n, float* b, uint32_t* words,
                  cudaStream_t st);
+// x, staging, divergence and tau_x from two denoised images (learned denoiser)
+int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_out, int solve_mode, int t_arg,
+                         double* div_out, cudaStream_t st);
+// cnn.cu
+int cnn_prepare_pair(dgamp_ct_cnn_s* c, int n);
+int cnn_denoise_pair(dgamp_ct_cnn_s* c, const float* rr, const DevScalars* S, int n, float* out, int scaled,
+                     cudaStream_t st);
+int cnn_launches_per_pair(const dgamp_ct_cnn_s* c);
 
 }  // namespace dgct

@@ -429,6 +429,101 @@ int tv_autotune(dgamp_ct_plan_s* pl) {
     return DGAMP_CT_OK;
 }
 
+// ------------------------------------- final step for a learned denoiser --
+// x = D(r) (damped in a solve), staged copies, b^T (D(r + eps b) - D(r)) and
+// tau_x, from the two denoised images dn[0], dn[1] ([2][n][n]); 32 x 32 tiles
+// as in the blocked TV's final launch.
+__global__ void __launch_bounds__(1024)
+k_denoise_final(const float* __restrict__ dn, int n, DevScalars* S, TvFinal F) {
+    __shared__ float tile[TB][TB + 1];
+    __shared__ double red[32];
+    __shared__ bool am_last;
+    const size_t N = (size_t)n * n;
+    const int tid = threadIdx.x, ta = tid >> 5, tb = tid & 31;
+    const int gi = blockIdx.y * TB + ta, gj = blockIdx.x * TB + tb;
+    const unsigned t = F.t_arg > 0 ? (unsigned)F.t_arg : S->t;
+    double acc = 0.0;
+    float xv = 0.f;
+    if (gi < n && gj < n) {
+        const size_t o = (size_t)gi * n + gj;
+        const float x1 = dn[o], x2 = dn[N + o];
+        const float4 b4 = probe4((unsigned)(o >> 2), t, F.slice, F.key);
+        const int kk = (int)(o & 3);
+        const float bv = kk == 0 ? b4.x : (kk == 1 ? b4.y : (kk == 2 ? b4.z : b4.w));
+        acc = (double)bv * (double)(x2 - x1);
+        xv = x1;
+        if (F.solve_mode && F.damp_x != 1.f) xv = F.damp_x * xv + (1.f - F.damp_x) * F.x_out[o];
+        F.x_out[o] = xv;
+        if (F.XR) F.XR[(size_t)gi * F.ldp + kPad + gj] = xv;
+    }
+    tile[ta][tb] = xv;
+    if (F.XC) {
+        __syncthreads();
+        const int gj2 = blockIdx.x * TB + ta, gi2 = blockIdx.y * TB + tb;
+        if (gi2 < n && gj2 < n) F.XC[(size_t)gj2 * F.ldp + kPad + gi2] = tile[tb][ta];
+    }
+    acc = block_sum(acc, red);
+    const int nblk = gridDim.x * gridDim.y;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (tid == 0) {
+        F.partial[bid] = acc;
+        __threadfence();
+        const unsigned prev = atomicAdd(&S->done_div, 1u);
+        am_last = (prev == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double tot = 0.0;
+    for (int b = tid; b < nblk; b += blockDim.x) tot += ((volatile double*)F.partial)[b];
+    tot = block_sum(tot, red);
+    if (tid == 0) {
+        const double div = tot / ((double)N * S->eps);
+        if (F.div_out) *F.div_out = div;
+        if (F.solve_mode) {
+            const double tau_r = S->tau_r;
+            double tx = tau_r * div;
+            const double fl = F.tau_x_floor * tau_r;
+            if (!(tx >= fl)) { tx = fl; S->floored += 1u; }
+            if (!isfinite(tx)) S->nonfinite += 1u;
+            S->div = div;
+            S->tau_x = tx;
+            const unsigned tt = S->t;
+            if (tt >= 1u && tt <= (unsigned)kMaxIters) {
+                IterLog L;
+                L.tau_x = tx; L.tau_p = S->tau_p; L.tau_s = S->tau_s; L.tau_r = tau_r;
+                L.div = div; L.eps = S->eps;
+                F.log[tt - 1] = L;
+            }
+            S->t = tt + 1u;
+        }
+        S->done_div = 0u;
+    }
+}
+
+int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_out, int solve_mode, int t_arg,
+                         double* div_out, cudaStream_t st) {
+    TvFinal F;
+    F.x_out = x_out;
+    F.XR = solve_mode ? pl->ws.XR : nullptr;
+    F.XC = solve_mode ? pl->ws.XC : nullptr;
+    F.ldp = pl->ldp;
+    F.damp_x = (float)pl->opt.damp_x;
+    F.t_arg = t_arg;
+    F.slice = (unsigned)pl->opt.slice_id;
+    F.key = probe_key(pl);
+    F.tau_x_floor = pl->opt.tau_x_floor;
+    F.partial = pl->ws.partial;
+    F.log = pl->ws.log;
+    F.div_out = div_out;
+    F.solve_mode = solve_mode;
+    const int n = pl->n;
+    dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
+    k_denoise_final<<<grd, 1024, 0, st>>>(dn, n, pl->ws.S, F);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
 // ------------------------------------------------------------ probe -----
 __global__ void k_probe(long long n, unsigned t, unsigned slice, uint2 key, float* __restrict__ b,
                         uint32_t* __restrict__ words) {

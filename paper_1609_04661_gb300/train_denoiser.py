@@ -1,0 +1,148 @@
+"""Train the learned D-GAMP-CT denoiser on the method's own iterates (GPU).
+
+Training pairs are (r^t, x_true) patches: r^t is the denoiser input of
+iteration t of a plain (prox-TV, damped) D-GAMP-CT solve of a training
+phantom, x_true = V mu_true is the phantom in the preconditioned space
+(Eq. precondAMP), and sigma = sqrt(tau_r^t) is the effective noise level the
+network is told (D_sigma(r) = r - sigma f(r / sigma)).  Every array
+operation runs in the library's kernels through the C ABI: the solve and
+its trace, V, the forward/backward passes and Adam.  numpy only draws patch
+positions.
+
+    python -m paper_1609_04661_gb300.train_denoiser --out weights.bin
+
+Weight file: 8-byte magic b"DGCTCNN1", int32 layers, int32 reserved,
+int64 parameter count, uint32 CRC-32 of the parameter bytes, uint32 reserved,
+then the float32 parameters in the library's flat order.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import struct
+import sys
+import time
+import zlib
+
+import numpy as np
+
+MAGIC = b"DGCTCNN1"
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "dncnn17_ellipse512_v64.bin")
+PLAIN = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
+
+
+def save_weights(path: str, params: np.ndarray, layers: int) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    raw = p.tobytes()
+    hdr = MAGIC + struct.pack("<iiqII", layers, 0, p.size, zlib.crc32(raw) & 0xFFFFFFFF, 0)
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    with open(path, "wb") as f:
+        f.write(hdr)
+        f.write(raw)
+
+
+def load_weights(path: str = DEFAULT_WEIGHTS):
+    """Returns (layers, params float32); raises on a bad magic, size or checksum."""
+    with open(path, "rb") as f:
+        data = f.read()
+    if data[:8] != MAGIC:
+        raise ValueError(f"{path}: not a D-GAMP-CT CNN weight file")
+    layers, _, count, crc, _ = struct.unpack("<iiqII", data[8:32])
+    raw = data[32:]
+    if len(raw) != 4 * count or (zlib.crc32(raw) & 0xFFFFFFFF) != crc:
+        raise ValueError(f"{path}: corrupt weight file")
+    return layers, np.frombuffer(raw, dtype=np.float32).copy()
+
+
+def load_cnn(path: str = DEFAULT_WEIGHTS):
+    """A library CNN object holding the weights stored at `path`."""
+    from .binding import CNN
+    layers, params = load_weights(path)
+    net = CNN(layers)
+    net.set_params(params)
+    return net
+
+
+def harvest(n_phantoms: int, iters: int, patches_per_iter: int, patch: int, seed0: int = 2000,
+            workload: str = "ellipse512_v64", scaled: bool = False):
+    """(r patches, x_true patches, sigma) on the GPU from plain solves of training phantoms.
+
+    sigma is sqrt(tau_r^t) for a scale-normalised network (scaled=True) and 1
+    for the blind network (the default): GAMP's tau_r does not track the
+    actual error of r^t on this operator, so the network is better off
+    estimating the noise level itself.
+    """
+    import torch
+    import synth
+    from .binding import Plan
+    rng = np.random.default_rng(7)
+    rs, xs, sg = [], [], []
+    plan = None
+    for k in range(n_phantoms):
+        c = synth.make_case(workload, seed=seed0 + k)
+        if plan is None:
+            plan = Plan(c["n"], c["n_views"], c["n_det"], **PLAIN)
+        y = torch.as_tensor(c["y"]).cuda()
+        _, rt, tau_r = plan.solve_trace(y, c["I0"], iters)
+        xt = plan.precond_image(torch.as_tensor(c["mu"], dtype=torch.float32).cuda(), inverse=False)
+        n = c["n"]
+        for t in range(iters):
+            if not np.isfinite(tau_r[t]) or tau_r[t] <= 0:
+                continue
+            for _ in range(patches_per_iter):
+                i, j = rng.integers(0, n - patch + 1, size=2)
+                rs.append(rt[t, i:i + patch, j:j + patch])
+                xs.append(xt[i:i + patch, j:j + patch])
+                sg.append(np.sqrt(tau_r[t]) if scaled else 1.0)
+    plan.close()
+    return torch.stack(rs).contiguous(), torch.stack(xs).contiguous(), np.asarray(sg, dtype=np.float32)
+
+
+def train(r, x, sigma, steps: int, batch: int, lr: float, seed: int = 0, log_every: int = 100):
+    from .binding import CNN
+    net = CNN(17, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    n = r.shape[0]
+    hist = []
+    t0 = time.time()
+    for s in range(steps):
+        idx = rng.choice(n, size=batch, replace=False)
+        ti = __import__("torch").as_tensor(idx, device=r.device)
+        lr_s = lr * (0.5 if s > 0.6 * steps else 1.0) * (0.5 if s > 0.85 * steps else 1.0)
+        loss = net.train_step(r[ti].contiguous(), x[ti].contiguous(), sigma[idx], lr_s)
+        if s % log_every == 0 or s == steps - 1:
+            hist.append((s, loss))
+    return net, hist, time.time() - t0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--phantoms", type=int, default=40)
+    ap.add_argument("--iters", type=int, default=30)
+    ap.add_argument("--patches", type=int, default=17, help="patches per phantom and iteration")
+    ap.add_argument("--patch", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    args = ap.parse_args(argv)
+    import torch
+    from . import build
+    build.build()
+    t0 = time.time()
+    r, x, sg = harvest(args.phantoms, args.iters, args.patches, args.patch)
+    t_h = time.time() - t0
+    net, hist, t_t = train(r, x, sg, args.steps, args.batch, args.lr)
+    save_weights(args.out, net.get_params(), net.layers)
+    meta = {"pairs": int(r.shape[0]), "patch": args.patch, "sigma_range": [float(sg.min()), float(sg.max())],
+            "steps": args.steps, "batch": args.batch, "lr": args.lr, "harvest_s": t_h, "train_s": t_t,
+            "loss": hist}
+    print(json.dumps(meta))
+    torch.cuda.synchronize()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
