@@ -58,6 +58,76 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def _bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+# FLOP of one 17-layer 64-channel 3x3 network evaluation per pixel:
+# 15 hidden layers x 64 x 64 x 9 x 2 plus the 1->64 and 64->1 layers (64 x 9 x 2 each)
+CNN_FLOP_PER_PIXEL = 15 * (64 * 64 * 9 * 2) + 2 * (64 * 9 * 2)
+
+
+def _learned_vs_plain(dg, plan, case, counts, T, plain_iters_per_s):
+    """The learned denoiser (shipped weights) in the same solve: iterations per
+    second, the PSNR after t = 1..T iterations of each form, and how many
+    learned iterations reach the plain form's final PSNR (None if none does)."""
+    import torch
+    from paper_1609_04661_gb300.train_denoiser import load_cnn
+    net = load_cnn()
+    mu = torch.empty((case["n"], case["n"]), device="cuda")
+
+    def curve():
+        out = []
+        for t in range(1, T + 1):
+            plan.solve(counts, case["I0"], t, mu_out=mu)
+            out.append(_psnr(mu.cpu().numpy().astype("float64"), case["mu"]))
+        return out
+
+    plain = curve()
+    plan.set_cnn(net)
+    plan.set_options(denoiser=1, cnn_scale=int(net.scaled))
+    try:
+        for _ in range(2):
+            plan.solve(counts, case["I0"], T, mu_out=mu)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(st)
+        for _ in range(reps):
+            plan.solve(counts, case["I0"], T, mu_out=mu)
+        e1.record(st)
+        torch.cuda.synchronize()
+        learned_ips = reps * T / (e0.elapsed_time(e1) / 1e3)
+        prof = plan.profile_iteration(reps=5)
+        learned = curve()
+    finally:
+        plan.set_options(denoiser=0)
+        plan.set_cnn(None)
+        net.close()
+    peak, kind = _bf16_peak()
+    flop = 2.0 * plan.N * CNN_FLOP_PER_PIXEL
+    achieved = flop / (prof["cnn_pair"] * 1e-3) / 1e12
+    reach = next((t + 1 for t, v in enumerate(learned) if v >= plain[-1]), None)
+    return {"weights": "dncnn17_ellipse512_v64.bin (Gaussian-noise-trained, noise-level scaled, "
+                       "sigma = sqrt(tau_r))",
+            "learned_iters_per_s": learned_ips, "plain_iters_per_s": plain_iters_per_s,
+            "plain_final_psnr_db": plain[-1], "plain_best_psnr_db": max(plain),
+            "learned_final_psnr_db": learned[-1], "learned_best_psnr_db": max(learned),
+            "learned_iterations_to_plain_final_psnr": reach,
+            "psnr_db_plain": [round(v, 2) for v in plain], "psnr_db_learned": [round(v, 2) for v in learned],
+            "kernel_ms": prof,
+            "cnn_roofline": {"kernel": "CNN pair (2 images, 17 layers)", "bound": "tensor",
+                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                             "peak_kind": f"{kind} cuBLAS bf16 burst",
+                             "algorithmic_flop_per_iteration": flop}}
+
+
 def _config(n_gpus):
     from synth import CASES
     n, nv, nd, ne, rmax, rect, I0, iters = CASES[WORKLOAD]
@@ -296,6 +366,9 @@ def run_gpu(args):
                          "peak_kind": f"{peak_kind} copy bandwidth"}}
     a_at_bytes = algo["project"] + algo["backproject_update"]
     a_at_ms = prof["project"] + prof["backproject_update"]
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = _learned_vs_plain(dg, plan, case, counts, T, value / world)
 
     line = None
     if rank == 0:
@@ -313,7 +386,7 @@ def run_gpu(args):
                 "psnr_db": psnr,
                 "a_plus_at_gbs": a_at_bytes / (a_at_ms * 1e-3) / 1e9,
                 "iteration_ms": iter_ms, "kernel_ms": prof, "kernel_share": shares,
-                "tv_share": tv_ms / iter_ms}
+                "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:
@@ -329,6 +402,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain section")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -72,7 +72,9 @@ typedef struct {
     int32_t  denoiser;     /* 0 = proximal TV (Section 6.3), 1 = the attached CNN */
     int32_t  k_tv;         /* Chambolle iterations per denoiser call (fixed)     */
     double   c_tv;         /* TV weight: lambda = c_tv * sqrt(tau_r)             */
-    double   eps_rel;      /* MC step: eps = eps_rel * max(max|r|, 1e-6) (Eq. MC_SURE) */
+    double   eps_rel;      /* MC step: eps = eps_rel * max(max|r|, 1e-6) (Eq. MC_SURE);
+                              the learned denoiser takes the eps -> 0 limit instead,
+                              b^T J_D(r) b / N by a forward-mode pass (eps is still logged) */
     uint64_t seed;         /* probe key (Philox4x32-10), see dgamp_ct_probe      */
     int32_t  slice_id;     /* probe counter word 2                              */
     int32_t  onsager;      /* 1 = p = z - tau_p s_prev (Algorithm 1); 0 = drop it (Section 7.1) */
@@ -261,8 +263,18 @@ int dgamp_ct_cnn_get_params(dgamp_ct_cnn_t net, float* h_params, int64_t count);
 /* d_out = D_sigma(d_r) for a batch of images. */
 int dgamp_ct_cnn_denoise(dgamp_ct_cnn_t net, const float* d_r, const float* h_sigma, int32_t batch,
                          int32_t H, int32_t W, float* d_out, void* stream);
-/* Training loss mean((D_sigma(r) - x)^2) over the batch and its gradient with
-   respect to every parameter (h_grad: num_params floats, may be NULL). */
+/* d_out = D_sigma(d_r) and d_jb = J_D(d_r) d_b, the directional derivative of
+   the denoiser at d_r along d_b (forward mode through the ReLU network:
+   J_D b = b - sigma J_f(r / sigma)(b / sigma)), for one H x W image.  This is
+   the pass a learned-denoiser solve uses for D' = b^T J_D b / N, the
+   eps -> 0 limit of Eq. MC_SURE.  d_r, d_b, d_out, d_jb: device, H*W floats
+   each; sigma > 0 and finite, else DGAMP_CT_ERR_INVALID_ARG. */
+int dgamp_ct_cnn_denoise_jvp(dgamp_ct_cnn_t net, const float* d_r, const float* d_b, float sigma, int32_t H,
+                             int32_t W, float* d_out, float* d_jb, void* stream);
+/* Training loss mean(((D_sigma(r) - x) / sigma)^2) over the batch (each image's
+   error divided by its own noise level; for sigma = 1 the plain mean squared
+   error) and its gradient with respect to every parameter (h_grad: num_params
+   floats, may be NULL). */
 int dgamp_ct_cnn_gradients(dgamp_ct_cnn_t net, const float* d_r, const float* d_x, const float* h_sigma,
                            int32_t batch, int32_t H, int32_t W, double* h_loss, float* h_grad,
                            void* stream);

@@ -121,6 +121,56 @@ def net_backward(gout: np.ndarray, ws, acts):
     return gws, gbs
 
 
+def net_jvp(x: np.ndarray, t: np.ndarray, ws, bs, bf16: bool = False):
+    """Forward-mode derivative of f: returns (f(x), J_f(x) t) for images [B][H][W].
+
+    f is piecewise linear (ReLU), so J_f(x) t is the same chain of
+    convolutions without biases, each hidden output masked where the
+    primal pre-activation is not positive (ReLU'(z) = [z > 0]).  With
+    ``bf16`` the primal activations and the tangent's hidden activations are
+    both rounded to bfloat16 after the ReLU / mask."""
+    a = np.asarray(x, dtype=np.float64)[..., None]
+    u = np.asarray(t, dtype=np.float64)[..., None]
+    L = len(ws)
+    for l in range(L):
+        z = conv3x3(a, ws[l], bs[l])
+        zt = conv3x3(u, ws[l], np.zeros_like(bs[l]))
+        if l < L - 1:
+            on = z > 0
+            a = np.where(on, z, 0.0)
+            u = np.where(on, zt, 0.0)
+            if bf16:
+                a = bf16_round(a)
+                u = bf16_round(u)
+        else:
+            a, u = z, zt
+    return a[..., 0], u[..., 0]
+
+
+def denoise_jvp(r: np.ndarray, b: np.ndarray, sigma: float, ws, bs, bf16: bool = False):
+    """(D_sigma(r), J_D(r) b) for one image: D = r - sigma f(r / sigma) gives
+    J_D b = b - sigma J_f(r / sigma) (b / sigma)."""
+    r = np.asarray(r, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    f, tf = net_jvp((r / sigma)[None], (b / sigma)[None], ws, bs, bf16)
+    return r - sigma * f[0], b - sigma * tf[0]
+
+
+class Denoiser:
+    """D_sigma of one GAMP iteration as a callable with its exact directional
+    derivative ``jvp(r, b) = J_D(r) b`` (used for the epsilon -> 0 limit of
+    Eq. MC_SURE)."""
+
+    def __init__(self, sigma: float, ws, bs, bf16: bool = True):
+        self.sigma, self.ws, self.bs, self.bf16 = sigma, ws, bs, bf16
+
+    def __call__(self, r):
+        return denoise(r, self.sigma, self.ws, self.bs, self.bf16)
+
+    def jvp(self, r, b):
+        return denoise_jvp(r, b, self.sigma, self.ws, self.bs, self.bf16)[1]
+
+
 def denoise(r: np.ndarray, sigma: float, ws, bs, bf16: bool = False) -> np.ndarray:
     """D_sigma(r) = r - sigma f(r / sigma) for one image or a batch [B][H][W]."""
     r = np.asarray(r, dtype=np.float64)
@@ -131,12 +181,16 @@ def denoise(r: np.ndarray, sigma: float, ws, bs, bf16: bool = False) -> np.ndarr
 
 
 def loss_and_grads(r, x_true, sigma, ws, bs, bf16: bool = False):
-    """Training loss mean((D(r) - x_true)^2) over a batch and its gradients."""
+    """Training loss mean(((D(r) - x_true) / sigma)^2) over a batch, and its gradients.
+
+    Dividing each patch's error by its noise level weighs all noise levels
+    alike (for sigma = 1 it is the plain mean squared error)."""
     r = np.asarray(r, dtype=np.float64)
-    f, acts = net_forward(r / sigma[:, None, None], ws, bs, bf16)
-    d = r - sigma[:, None, None] * f
-    e = d - x_true
+    sg = np.asarray(sigma, dtype=np.float64)[:, None, None]
+    f, acts = net_forward(r / sg, ws, bs, bf16)
+    d = r - sg * f
+    e = (d - x_true) / sg
     loss = float(np.mean(e * e))
-    gout = -2.0 * e * sigma[:, None, None] / e.size
+    gout = -2.0 * e / e.size
     gws, gbs = net_backward(gout, ws, acts)
     return loss, gws, gbs

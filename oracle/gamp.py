@@ -15,7 +15,9 @@ s is taken as 0 (implied, not stated).  The result is mu = V^-1 x.
 
 Readings (the paper is silent): the MC step is
 eps = eps_rel * max(max|r|, 1e-6), the divergence estimate is
-D' = b^T (D(r + eps b) - D(r)) / (N eps), and tau_x is floored at
+D' = b^T (D(r + eps b) - D(r)) / (N eps) -- or, for a denoiser that
+provides its directional derivative (the learned network), the eps -> 0
+limit b^T J_D(r) b / N that Eq. MC_SURE approaches -- and tau_x is floored at
 1e-6 * tau_r (the paper has no guard for D' <= 0).  ``onsager=False`` drops
 the tau_p s_prev term (Section 7.1); ``damp_x``/``damp_s`` blend the new x and
 s with the previous ones (Section 7.2; 1.0 means no damping).
@@ -32,6 +34,7 @@ from . import output_step as _out
 from . import philox as _philox
 from . import precond as _pre
 from . import tv as _tv
+from . import cnn as _cnn
 
 
 @dataclasses.dataclass
@@ -96,7 +99,13 @@ def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
         x_new = D(r)
         b = probe(t, r.size).reshape(r.shape)
         eps = opts.eps_rel * max(float(np.max(np.abs(r))), 1e-6)
-        div = mc_divergence(D, r, x_new, b, eps)
+        jvp = getattr(D, "jvp", None)
+        if jvp is not None:
+            # Eq. MC_SURE in its eps -> 0 limit, b^T J_D(r) b / N, for a
+            # denoiser that provides its directional derivative
+            div = float(np.vdot(b, jvp(r, b))) / r.size
+        else:
+            div = mc_divergence(D, r, x_new, b, eps)
         tau_x = max(tau_r * div, opts.tau_x_floor * tau_r)
         if opts.damp_x != 1.0:
             x_new = opts.damp_x * x_new + (1.0 - opts.damp_x) * x
@@ -111,13 +120,16 @@ def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
 
 def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
              opts: Options | None = None, return_x: bool = False, log=None,
-             frob2: float | None = None, on_iter=None):
-    """D-GAMP-CT on one slice with the prox-TV denoiser (parity unpinned).
+             frob2: float | None = None, on_iter=None, cnn=None):
+    """D-GAMP-CT on one slice (parity unpinned).
 
-    The full reconstruction has no closed form and the paper prints no
-    synthetic result; it is checked only through its pinned parts and the
-    tests' qualitative checks (error falls over the iterations, the Onsager
-    term helps).  ``frob2`` may pass a precomputed ||Phi~||_F^2.
+    The denoiser is prox-TV, or with ``cnn = (ws, bs, scaled)`` the learned
+    residual network of ``oracle.cnn`` in its BF16-activation form, run at
+    sigma = sqrt(tau_r) (scaled) or sigma = 1 (blind).  The full
+    reconstruction has no closed form and the paper prints no synthetic
+    result; it is checked only through its pinned parts and the tests'
+    qualitative checks (error falls over the iterations, the Onsager term
+    helps).  ``frob2`` may pass a precomputed ||Phi~||_F^2.
     """
     opts = opts or Options()
     yv = np.asarray(y, dtype=np.float64).reshape(-1)
@@ -135,6 +147,10 @@ def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
         return s, tsi
 
     def denoise_factory(tau_r):
+        if cnn is not None:
+            ws, bs, scaled = cnn
+            sigma = float(np.sqrt(tau_r)) if scaled else 1.0
+            return _cnn.Denoiser(sigma, ws, bs, bf16=True)
         lam = opts.c_tv * np.sqrt(tau_r)
         return lambda r: _tv.tv_prox(r, lam, opts.k_tv)
 

@@ -28,7 +28,7 @@ EXPORTS = (
     "dgamp_ct_strerror", "dgamp_ct_last_cuda_error", "dgamp_ct_profile_iteration",
     "dgamp_ct_output_step_noalloc", "dgamp_ct_get_tuning", "dgamp_ct_set_tuning",
     "dgamp_ct_cnn_create", "dgamp_ct_cnn_destroy", "dgamp_ct_cnn_num_params", "dgamp_ct_cnn_set_params",
-    "dgamp_ct_cnn_get_params", "dgamp_ct_cnn_denoise", "dgamp_ct_cnn_gradients", "dgamp_ct_cnn_train_step",
+    "dgamp_ct_cnn_get_params", "dgamp_ct_cnn_denoise", "dgamp_ct_cnn_denoise_jvp", "dgamp_ct_cnn_gradients", "dgamp_ct_cnn_train_step",
     "dgamp_ct_plan_set_cnn", "dgamp_ct_solve_trace",
 )
 
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_cnn_set_params": (C.c_int, [vp, vp, i64]),
         "dgamp_ct_cnn_get_params": (C.c_int, [vp, vp, i64]),
         "dgamp_ct_cnn_denoise": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, vp]),
+        "dgamp_ct_cnn_denoise_jvp": (C.c_int, [vp, vp, vp, C.c_float, i32, i32, vp, vp, vp]),
         "dgamp_ct_cnn_gradients": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, C.POINTER(dbl), vp, vp]),
         "dgamp_ct_cnn_train_step": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, C.c_float, C.POINTER(dbl), vp]),
         "dgamp_ct_plan_set_cnn": (C.c_int, [vp, vp]),
@@ -410,6 +411,15 @@ class CNN:
         _check(self._lib.dgamp_ct_cnn_denoise(self._h, _ptr(r), s.ctypes.data_as(C.c_void_p), B, H, W, _ptr(out),
                                               _stream()), "cnn_denoise")
         return out
+
+    def denoise_jvp(self, r, b, sigma: float):
+        """(D_sigma(r), J_D(r) b) for one [H][W] image on the device."""
+        import torch
+        H, W = tuple(r.shape)
+        out, jb = torch.empty_like(r), torch.empty_like(r)
+        _check(self._lib.dgamp_ct_cnn_denoise_jvp(self._h, _ptr(r), _ptr(b, H * W, "b"), float(sigma), H, W,
+                                                  _ptr(out), _ptr(jb), _stream()), "cnn_denoise_jvp")
+        return out, jb
 
     def gradients(self, r, x, sigma):
         B, H, W = tuple(r.shape)

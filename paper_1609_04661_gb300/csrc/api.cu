@@ -216,11 +216,12 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
     DGCT_TRY(mark());
     DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st));            //         r = x + tau_r A^T H s
     DGCT_TRY(mark());
-    DGCT_TRY(launch_probe_input(pl, 0, st));                            // Step 4: r + eps b
+    // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r
+    DGCT_TRY(launch_probe_input(pl, 0, st, pl->opt.denoiser == 1 ? 1 : 0));
     if (pl->opt.denoiser == 1) {
-        // learned denoiser: D(r) and D(r + eps b) as one batch of two, then x, D', tau_x
+        // learned denoiser: D(r) and its forward-mode derivative J_D(r) b, then x, D', tau_x
         DGCT_TRY(mark());
-        DGCT_TRY(cnn_denoise_pair(pl->cnn, w.r, w.S, pl->n, pl->dn, pl->opt.cnn_scale, st));
+        DGCT_TRY(cnn_denoise_jvp(pl->cnn, w.r, w.S, pl->n, pl->dn, pl->opt.cnn_scale, st));
         DGCT_TRY(mark());
         DGCT_TRY(launch_denoise_final(pl, pl->dn, w.x, 1, 0, nullptr, st));
     } else {
@@ -264,6 +265,7 @@ static int ensure_graph(dgamp_ct_plan_s* pl) {
         return cuda_fail(e);
     }
     int rc = enqueue_iteration(pl, cs);
+    pl->graph_cnn_gen = pl->cnn ? cnn_ws_generation(pl->cnn) : 0;
     e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
     if (rc != DGAMP_CT_OK) {
@@ -529,6 +531,12 @@ static int solve_begin(dgamp_ct_plan_s* pl, const float* d_counts, double I0, cu
     DGCT_CUDA(cudaMemsetAsync(w.x, 0, N * sizeof(float), st));
     DGCT_CUDA(cudaMemsetAsync(w.s, 0, M * sizeof(float), st));
     DGCT_TRY(launch_stage_image(pl, w.x, st));
+    if (pl->opt.denoiser == 1) {
+        // the network may have been used (and its workspace regrown) since the
+        // graph was captured: make room again and re-capture if it moved
+        DGCT_TRY(cnn_prepare_pair(pl->cnn, pl->n));
+        if (pl->graph && pl->graph_cnn_gen != cnn_ws_generation(pl->cnn)) drop_graph(pl);
+    }
     k_init_scalars<<<1, 1, 0, st>>>(w.S, pl->frob2, std::log(I0), pl->opt.tau_x0);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;

@@ -67,12 +67,14 @@ __device__ __forceinline__ void mma16816(float* c, uint32_t a0, uint32_t a1, uin
 
 // ---------------------------------------------------------- first layer --
 // a1 = relu(b0 + conv(u, W0)), u = r / sigma; also stores u for the weight gradient.
+// Tangent form (b0 == nullptr, mask != nullptr): a1 = conv(u, W0) where the
+// primal layer-1 activation `mask` is positive, else 0.
 __global__ void k_conv_first(const float* __restrict__ r, const float* __restrict__ sigma, int B, int H, int W,
-                             const float* __restrict__ w0, const float* __restrict__ b0, bf16* __restrict__ a1,
-                             float* __restrict__ u_out) {
+                             const float* __restrict__ w0, const float* __restrict__ b0,
+                             const bf16* __restrict__ mask, bf16* __restrict__ a1, float* __restrict__ u_out) {
     __shared__ float sw[9 * CH + CH];
     for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = w0[i];
-    for (int i = threadIdx.x; i < CH; i += blockDim.x) sw[9 * CH + i] = b0[i];
+    for (int i = threadIdx.x; i < CH; i += blockDim.x) sw[9 * CH + i] = b0 ? b0[i] : 0.f;
     __syncthreads();
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long HW = (long long)H * W;
@@ -92,12 +94,17 @@ __global__ void k_conv_first(const float* __restrict__ r, const float* __restric
 #pragma unroll 1
     for (int c0 = 0; c0 < CH; c0 += 8) {
         __align__(16) bf16 v[8];
+        __align__(16) bf16 mk[8];
+        if (mask) *reinterpret_cast<uint4*>(mk) = *reinterpret_cast<const uint4*>(mask + p * CH + c0);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             float acc = sw[9 * CH + c0 + j];
 #pragma unroll
             for (int t = 0; t < 9; ++t) acc = fmaf(u[t], sw[t * CH + c0 + j], acc);
-            v[j] = __float2bfloat16_rn(fmaxf(acc, 0.f));
+            if (mask)
+                v[j] = __float2bfloat16_rn(__bfloat162float(mk[j]) > 0.f ? acc : 0.f);
+            else
+                v[j] = __float2bfloat16_rn(fmaxf(acc, 0.f));
         }
         *reinterpret_cast<uint4*>(out + c0) = *reinterpret_cast<const uint4*>(v);
     }
@@ -105,8 +112,11 @@ __global__ void k_conv_first(const float* __restrict__ r, const float* __restric
 
 // ------------------------------------------------------ hidden 64 -> 64 --
 // MODE 0 (forward):  out = relu(bias + conv(in, Wk)), Wk = [co][tap*64 + ci].
-// MODE 1 (input gradient): out = conv(in, Wk) * (mask > 0), Wk = flipped/transposed
-// kernel, `in` = the output gradient, mask = this layer's input activation.
+// MODE 1 (masked linear): out = conv(in, Wk) * (mask > 0).  With Wk = the
+// flipped/transposed kernel, `in` = the output gradient and mask = this
+// layer's input activation it is the input gradient; with Wk = the forward
+// kernel, `in` = a tangent and mask = the primal output activation of this
+// layer it is the forward-mode derivative.
 template <int MODE>
 __global__ void __launch_bounds__(CONV_THREADS)
 k_conv64(const bf16* __restrict__ in, const bf16* __restrict__ wk, const float* __restrict__ bias,
@@ -200,7 +210,8 @@ k_conv64(const bf16* __restrict__ in, const bf16* __restrict__ wk, const float* 
 }
 
 // ------------------------------------------------------------ last layer --
-// f = b16 + conv(a16, W16) (W16 as [tap][ci]); D = r - sigma f.
+// f = b16 + conv(a16, W16) (W16 as [tap][ci]); D = r - sigma f.  b16 == nullptr
+// drops the bias (tangent form: r = the direction b, D = b - sigma J_f (b / sigma)).
 __global__ void k_conv_last(const bf16* __restrict__ a16, const float* __restrict__ w16, const float* __restrict__ b16,
                             const float* __restrict__ r, const float* __restrict__ sigma, int B, int H, int W,
                             float* __restrict__ f_out, float* __restrict__ d_out) {
@@ -212,7 +223,7 @@ __global__ void k_conv_last(const bf16* __restrict__ a16, const float* __restric
     if (p >= (long long)B * HW) return;
     const int b = (int)(p / HW);
     const int y = (int)((p - b * HW) / W), x = (int)(p - b * HW - (long long)y * W);
-    float acc = b16[0];
+    float acc = b16 ? b16[0] : 0.f;
 #pragma unroll 1
     for (int t = 0; t < 9; ++t) {
         const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
@@ -442,10 +453,11 @@ __global__ void k_loss(const float* __restrict__ r, const float* __restrict__ si
     const double inv_count = 1.0 / (double)npix;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
          p += (long long)gridDim.x * blockDim.x) {
+        // noise-normalised residual e / sigma = (r - x) / sigma - f
         const float sg = sigma[p / HW];
-        const float e = (r[p] - sg * f[p]) - xt[p];
+        const float e = ((r[p] - sg * f[p]) - xt[p]) / sg;
         s += (double)e * e;
-        gout[p] = (float)(-2.0 * sg * e * inv_count);
+        gout[p] = (float)(-2.0 * e * inv_count);
     }
     s = block_sum(s, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -520,7 +532,7 @@ struct dgamp_ct_cnn_s {
     float* w16 = nullptr; // [9][64]
     // shape-dependent workspace
     int64_t cap_pix = 0;
-    int cap_store = 0;    // activations kept for all layers (training) or 2 (inference)
+    int cap_store = 0;    // activations kept for all layers (training), 2 (inference) or 4 (with tangent)
     bf16* act = nullptr;  // [cap_store][cap_pix][64]
     bf16* g0 = nullptr;   // [cap_pix][64]
     bf16* g1 = nullptr;
@@ -532,6 +544,7 @@ struct dgamp_ct_cnn_s {
     float* sig_buf = nullptr;   // per-image sigma (device) [cap_batch]
     int cap_batch = 0;
     int conv_grid = 0;
+    uint64_t ws_gen = 0;        // bumped whenever the workspace is reallocated
 };
 
 static int kGroups = 32;
@@ -572,6 +585,7 @@ static int cnn_ensure_ws(dgamp_ct_cnn_s* c, int64_t npix, int nstore, int batch)
     c->cap_pix = cap;
     c->cap_store = ns;
     c->cap_batch = cb;
+    c->ws_gen += 1;
     return DGAMP_CT_OK;
 }
 
@@ -596,7 +610,7 @@ static int cnn_forward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int 
         return c->act + (size_t)slot * c->cap_pix * CH;
     };
     const unsigned blocks = (unsigned)((npix + 127) / 128);
-    k_conv_first<<<blocks, 128, 0, st>>>(r, sig, B, H, W, c->w0, c->master + c->b_off[0], act(1), nullptr);
+    k_conv_first<<<blocks, 128, 0, st>>>(r, sig, B, H, W, c->w0, c->master + c->b_off[0], nullptr, act(1), nullptr);
     DGCT_LAUNCH_CHECK();
     const int tiles = B * ((W + TWD - 1) / TWD) * ((H + TH - 1) / TH);
     const int grid = tiles < c->conv_grid ? tiles : c->conv_grid;
@@ -665,19 +679,59 @@ __global__ void k_sigma_from_tau(const DevScalars* __restrict__ S, float* __rest
 }
 
 namespace dgct {
-// Workspace for denoising pairs of n x n images; call before any capture.
-int cnn_prepare_pair(dgamp_ct_cnn_s* c, int n) { return cnn_ensure_ws(c, 2LL * n * n, 2, 2); }
+// Workspace for one n x n image and its tangent (two activation slots each);
+// call before any capture.
+int cnn_prepare_pair(dgamp_ct_cnn_s* c, int n) { return cnn_ensure_ws(c, (int64_t)n * n, 4, 2); }
 
-// out[2][n][n] = D_sigma(rr[2][n][n]), sigma = sqrt(tau_r) read on the device
-// (scaled = 1) or 1 (blind network).
-int cnn_denoise_pair(dgamp_ct_cnn_s* c, const float* rr, const DevScalars* S, int n, float* out, int scaled,
-                     cudaStream_t st) {
-    k_sigma_from_tau<<<1, 32, 0, st>>>(S, c->sig_buf, 2, scaled);
+// out[0] = D_sigma(rb[0]) and out[1] = J_D(rb[0]) rb[1] = b - sigma J_f(r / sigma)(b / sigma)
+// for rb = [r; b] ([2][n][n]); sigma = sqrt(tau_r) read on the device
+// (scaled = 1) or 1 (blind network).  Layer by layer, the primal pass is
+// followed by the tangent pass masked with the primal's fresh activation.
+static int jvp_passes(dgamp_ct_cnn_s* c, const float* r, const float* b, int H, int W, float* d_out, float* d_jb,
+                      cudaStream_t st);
+
+int cnn_denoise_jvp(dgamp_ct_cnn_s* c, const float* rb, const DevScalars* S, int n, float* out, int scaled,
+                    cudaStream_t st) {
+    k_sigma_from_tau<<<1, 32, 0, st>>>(S, c->sig_buf, 1, scaled);
     DGCT_LAUNCH_CHECK();
-    return cnn_forward(c, rr, c->sig_buf, 2, n, n, out, 0, st);
+    return jvp_passes(c, rb, rb + (int64_t)n * n, n, n, out, out + (int64_t)n * n, st);
 }
 
-int cnn_launches_per_pair(const dgamp_ct_cnn_s* c) { return 1 + c->L; }
+// D_sigma(r) -> d_out and J_D(r) b -> d_jb for one H x W image, sigma = c->sig_buf[0].
+static int jvp_passes(dgamp_ct_cnn_s* c, const float* r, const float* b, int H, int W, float* d_out, float* d_jb,
+                      cudaStream_t st) {
+    const int64_t npix = (int64_t)H * W;
+    const int L = c->L;
+    auto prim = [&](int l) -> bf16* { return c->act + (size_t)((l - 1) & 1) * c->cap_pix * CH; };
+    auto tang = [&](int l) -> bf16* { return c->act + (size_t)(2 + ((l - 1) & 1)) * c->cap_pix * CH; };
+    const unsigned blocks = (unsigned)((npix + 127) / 128);
+    k_conv_first<<<blocks, 128, 0, st>>>(r, c->sig_buf, 1, H, W, c->w0, c->master + c->b_off[0], nullptr, prim(1),
+                                         nullptr);
+    DGCT_LAUNCH_CHECK();
+    k_conv_first<<<blocks, 128, 0, st>>>(b, c->sig_buf, 1, H, W, c->w0, nullptr, prim(1), tang(1), nullptr);
+    DGCT_LAUNCH_CHECK();
+    const int tiles = ((W + TWD - 1) / TWD) * ((H + TH - 1) / TH);
+    const int grid = tiles < c->conv_grid ? tiles : c->conv_grid;
+    for (int l = 1; l <= L - 2; ++l) {
+        const bf16* wl = c->wh + (size_t)(l - 1) * CH * KW;
+        k_conv64<0><<<grid, CONV_THREADS, conv_smem(), st>>>(prim(l), wl, c->master + c->b_off[l], nullptr,
+                                                             prim(l + 1), 1, H, W);
+        DGCT_LAUNCH_CHECK();
+        k_conv64<1><<<grid, CONV_THREADS, conv_smem(), st>>>(tang(l), wl, nullptr, prim(l + 1), tang(l + 1), 1, H,
+                                                             W);
+        DGCT_LAUNCH_CHECK();
+    }
+    k_conv_last<<<blocks, 128, 0, st>>>(prim(L - 1), c->w16, c->master + c->b_off[L - 1], r, c->sig_buf, 1, H, W,
+                                        nullptr, d_out);
+    DGCT_LAUNCH_CHECK();
+    k_conv_last<<<blocks, 128, 0, st>>>(tang(L - 1), c->w16, nullptr, b, c->sig_buf, 1, H, W, nullptr, d_jb);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+int cnn_launches_per_pair(const dgamp_ct_cnn_s* c) { return 1 + 2 * c->L; }
+
+uint64_t cnn_ws_generation(const dgamp_ct_cnn_s* c) { return c->ws_gen; }
 }  // namespace dgct
 
 static int upload_sigma(dgamp_ct_cnn_s* c, const float* h_sigma, int B, cudaStream_t st) {
@@ -798,6 +852,17 @@ int dgamp_ct_cnn_denoise(dgamp_ct_cnn_t c, const float* d_r, const float* h_sigm
     if (rc != DGAMP_CT_OK) return rc;
     if ((rc = upload_sigma(c, h_sigma, batch, st)) != DGAMP_CT_OK) return rc;
     return cnn_forward(c, d_r, c->sig_buf, batch, H, W, d_out, 0, st);
+}
+
+int dgamp_ct_cnn_denoise_jvp(dgamp_ct_cnn_t c, const float* d_r, const float* d_b, float sigma, int32_t H,
+                             int32_t W, float* d_out, float* d_jb, void* stream) {
+    if (!c || !d_r || !d_b || !d_out || !d_jb || H < 1 || W < 1) return DGAMP_CT_ERR_INVALID_ARG;
+    if (!(sigma > 0.f) || !std::isfinite(sigma)) return DGAMP_CT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = cnn_ensure_ws(c, (int64_t)H * W, 4, 1);
+    if (rc != DGAMP_CT_OK) return rc;
+    if ((rc = upload_sigma(c, &sigma, 1, st)) != DGAMP_CT_OK) return rc;
+    return jvp_passes(c, d_r, d_b, H, W, d_out, d_jb, st);
 }
 
 int dgamp_ct_cnn_gradients(dgamp_ct_cnn_t c, const float* d_r, const float* d_x, const float* h_sigma, int32_t batch,

@@ -84,7 +84,7 @@ struct dgamp_ct_cnn_s;
 
 struct dgamp_ct_plan_s {
     dgamp_ct_cnn_s* cnn = nullptr;         // learned denoiser (not owned), used when opt.denoiser == 1
-    float* dn = nullptr;                   // [2][n][n] its outputs D(r), D(r + eps b)
+    float* dn = nullptr;                   // [2][n][n] its outputs D(r), J_D(r) b
     int device = 0;
     int n = 0, nv = 0, nd = 0, P = 0, logP = 0, m2 = 0, logm2 = 0, ldp = 0;
     int64_t N = 0, M = 0;
@@ -97,6 +97,7 @@ struct dgamp_ct_plan_s {
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;   // stream the graph was captured for (identity only)
+    uint64_t graph_cnn_gen = 0;            // network workspace generation the graph was captured with
     int kernels_per_iter = 0;
 };
 
@@ -208,7 +209,7 @@ int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y
                        int use_prev, int from_scalars, double tau_p_arg, double logI0_arg,
                        double* tau_s_out, cudaStream_t st);
 // tv.cu
-int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st);
+int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st, int write_b = 0);
 int launch_absmax(const dgamp_ct_plan_s* pl, const float* r, cudaStream_t st);
 bool tv_active(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg);
 int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg);
@@ -220,13 +221,15 @@ int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lamb
               int solve_mode, int t_arg, double* div_out, cudaStream_t st);
 int launch_probe(const dgamp_ct_plan_s* pl, unsigned t, int64_t n, float* b, uint32_t* words,
                  cudaStream_t st);
-// x, staging, divergence and tau_x from two denoised images (learned denoiser)
+// x, staging, divergence and tau_x from D(r) and J_D(r) b (learned denoiser)
 int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_out, int solve_mode, int t_arg,
                          double* div_out, cudaStream_t st);
 // cnn.cu
 int cnn_prepare_pair(dgamp_ct_cnn_s* c, int n);
-int cnn_denoise_pair(dgamp_ct_cnn_s* c, const float* rr, const DevScalars* S, int n, float* out, int scaled,
-                     cudaStream_t st);
+int cnn_denoise_jvp(dgamp_ct_cnn_s* c, const float* rb, const DevScalars* S, int n, float* out, int scaled,
+                    cudaStream_t st);
 int cnn_launches_per_pair(const dgamp_ct_cnn_s* c);
+// changes whenever the network's workspace is reallocated (captured graphs hold its pointers)
+uint64_t cnn_ws_generation(const dgamp_ct_cnn_s* c);
 
 }  // namespace dgct

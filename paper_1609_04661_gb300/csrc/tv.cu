@@ -36,11 +36,12 @@ __device__ __forceinline__ float solve_lambda(const DevScalars* S, float c_tv, i
 }
 
 // --------------------------------------------------------- probe input ----
-// r2 = r + eps b, eps = eps_rel max(max|r|, 1e-6).  One thread per block of
-// four probe elements (one Philox call).
+// r2 = r + eps b, eps = eps_rel max(max|r|, 1e-6), or r2 = b itself
+// (write_b = 1: the direction of a forward-mode divergence).  One thread per
+// block of four probe elements (one Philox call).
 __global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r2, long long N,
                               float eps_rel, int t_arg, unsigned slice, uint2 key,
-                              DevScalars* S) {
+                              DevScalars* S, int write_b) {
     const float rmax = __uint_as_float(S->rmax_bits);
     const float eps = eps_rel * fmaxf(rmax, 1e-6f);
     const unsigned t = t_arg > 0 ? (unsigned)t_arg : S->t;
@@ -52,19 +53,19 @@ __global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r
     const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        if (i0 + k < N) r2[i0 + k] = fmaf(eps, bb[k], r[i0 + k]);
+        if (i0 + k < N) r2[i0 + k] = write_b ? bb[k] : fmaf(eps, bb[k], r[i0 + k]);
 }
 
 static uint2 probe_key(const dgamp_ct_plan_s* pl) {
     return make_uint2((unsigned)(pl->opt.seed & 0xffffffffu), (unsigned)(pl->opt.seed >> 32));
 }
 
-int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st) {
+int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st, int write_b) {
     const long long N = pl->N;
     const long long groups = (N + 3) / 4;
     k_probe_input<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(
         pl->ws.r, pl->ws.r + N, N, (float)pl->opt.eps_rel, t_arg, (unsigned)pl->opt.slice_id,
-        probe_key(pl), pl->ws.S);
+        probe_key(pl), pl->ws.S, write_b);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -103,6 +104,7 @@ struct TvFinal {
     IterLog* log;
     double* div_out;       // nullable
     int solve_mode;        // 1: update tau_x, the log and t in S
+    int jvp;               // learned denoiser: dn[1] is J_D b (divergence b^T J_D b / N)
 };
 
 // KB Chambolle steps on the block's region in shared memory.  BORDER = false
@@ -358,6 +360,7 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     F.log = pl->ws.log;
     F.div_out = div_out;
     F.solve_mode = solve_mode;
+    F.jvp = 0;
     dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
     const float c_tv = (float)pl->opt.c_tv, lam = (float)lambda_arg;
     if (nimg == 2)
@@ -430,9 +433,11 @@ int tv_autotune(dgamp_ct_plan_s* pl) {
 }
 
 // ------------------------------------- final step for a learned denoiser --
-// x = D(r) (damped in a solve), staged copies, b^T (D(r + eps b) - D(r)) and
-// tau_x, from the two denoised images dn[0], dn[1] ([2][n][n]); 32 x 32 tiles
-// as in the blocked TV's final launch.
+// x = D(r) (damped in a solve), staged copies, the divergence and tau_x from
+// dn[0] = D(r) and dn[1] = J_D(r) b ([2][n][n]): D' = b^T J_D b / N, the
+// eps -> 0 limit of Eq. MC_SURE (F.jvp = 1), or from dn[1] = D(r + eps b):
+// D' = b^T (dn[1] - dn[0]) / (N eps).  32 x 32 tiles as in the blocked TV's
+// final launch.
 __global__ void __launch_bounds__(1024)
 k_denoise_final(const float* __restrict__ dn, int n, DevScalars* S, TvFinal F) {
     __shared__ float tile[TB][TB + 1];
@@ -450,7 +455,7 @@ k_denoise_final(const float* __restrict__ dn, int n, DevScalars* S, TvFinal F) {
         const float4 b4 = probe4((unsigned)(o >> 2), t, F.slice, F.key);
         const int kk = (int)(o & 3);
         const float bv = kk == 0 ? b4.x : (kk == 1 ? b4.y : (kk == 2 ? b4.z : b4.w));
-        acc = (double)bv * (double)(x2 - x1);
+        acc = (double)bv * (double)(F.jvp ? x2 : x2 - x1);
         xv = x1;
         if (F.solve_mode && F.damp_x != 1.f) xv = F.damp_x * xv + (1.f - F.damp_x) * F.x_out[o];
         F.x_out[o] = xv;
@@ -478,7 +483,7 @@ k_denoise_final(const float* __restrict__ dn, int n, DevScalars* S, TvFinal F) {
     for (int b = tid; b < nblk; b += blockDim.x) tot += ((volatile double*)F.partial)[b];
     tot = block_sum(tot, red);
     if (tid == 0) {
-        const double div = tot / ((double)N * S->eps);
+        const double div = F.jvp ? tot / (double)N : tot / ((double)N * S->eps);
         if (F.div_out) *F.div_out = div;
         if (F.solve_mode) {
             const double tau_r = S->tau_r;
@@ -517,6 +522,7 @@ int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_ou
     F.log = pl->ws.log;
     F.div_out = div_out;
     F.solve_mode = solve_mode;
+    F.jvp = 1;
     const int n = pl->n;
     dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
     k_denoise_final<<<grd, 1024, 0, st>>>(dn, n, pl->ws.S, F);

@@ -1,19 +1,26 @@
-"""Train the learned D-GAMP-CT denoiser on the method's own iterates (GPU).
+"""Train the learned D-GAMP-CT denoiser (GPU).
 
-Training pairs are (r^t, x_true) patches: r^t is the denoiser input of
-iteration t of a plain (prox-TV, damped) D-GAMP-CT solve of a training
-phantom, x_true = V mu_true is the phantom in the preconditioned space
-(Eq. precondAMP), and sigma = sqrt(tau_r^t) is the effective noise level the
-network is told (D_sigma(r) = r - sigma f(r / sigma)).  Every array
-operation runs in the library's kernels through the C ABI: the solve and
-its trace, V, the forward/backward passes and Adam.  numpy only draws patch
-positions.
+Two training sets, both built from training phantoms (seeds 2000 + k) in the
+preconditioned space x_true = V mu_true (Eq. precondAMP):
+
+* ``awgn`` (default): the denoising problem that AMP poses, r = x + N(0, sigma^2)
+  (the decoupling property behind Eq. MC_SURE), with sigma log-uniform over
+  the range sqrt(tau_r) takes in plain solves; the network is told sigma
+  (D_sigma(r) = r - sigma f(r / sigma)), so inside the solve it runs at
+  sigma = sqrt(tau_r) (option cnn_scale = 1).
+* ``iterates``: (r^t, x_true) pairs where r^t is the denoiser input of
+  iteration t of a plain (prox-TV, damped) solve; blind network (sigma = 1).
+
+Every array operation runs in the library's kernels through the C ABI (the
+solve and its trace, V, the forward/backward passes and Adam); torch draws
+the Gaussian noise of the awgn set and numpy the patch positions.
 
     python -m paper_1609_04661_gb300.train_denoiser --out weights.bin
 
-Weight file: 8-byte magic b"DGCTCNN1", int32 layers, int32 reserved,
-int64 parameter count, uint32 CRC-32 of the parameter bytes, uint32 reserved,
-then the float32 parameters in the library's flat order.
+Weight file: 8-byte magic b"DGCTCNN1", int32 layers, int32 flags (bit 0:
+noise-level-scaled network, run it with options.cnn_scale = 1), int64
+parameter count, uint32 CRC-32 of the parameter bytes, uint32 reserved, then
+the float32 parameters in the library's flat order.
 """
 from __future__ import annotations
 
@@ -33,10 +40,10 @@ DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "dncnn17_ellipse512_v64.bin")
 PLAIN = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
 
 
-def save_weights(path: str, params: np.ndarray, layers: int) -> None:
+def save_weights(path: str, params: np.ndarray, layers: int, scaled: bool) -> None:
     p = np.ascontiguousarray(params, dtype=np.float32)
     raw = p.tobytes()
-    hdr = MAGIC + struct.pack("<iiqII", layers, 0, p.size, zlib.crc32(raw) & 0xFFFFFFFF, 0)
+    hdr = MAGIC + struct.pack("<iiqII", layers, 1 if scaled else 0, p.size, zlib.crc32(raw) & 0xFFFFFFFF, 0)
     os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
     with open(path, "wb") as f:
         f.write(hdr)
@@ -44,24 +51,26 @@ def save_weights(path: str, params: np.ndarray, layers: int) -> None:
 
 
 def load_weights(path: str = DEFAULT_WEIGHTS):
-    """Returns (layers, params float32); raises on a bad magic, size or checksum."""
+    """Returns (layers, params float32, scaled); raises on a bad magic, size or checksum."""
     with open(path, "rb") as f:
         data = f.read()
     if data[:8] != MAGIC:
         raise ValueError(f"{path}: not a D-GAMP-CT CNN weight file")
-    layers, _, count, crc, _ = struct.unpack("<iiqII", data[8:32])
+    layers, flags, count, crc, _ = struct.unpack("<iiqII", data[8:32])
     raw = data[32:]
     if len(raw) != 4 * count or (zlib.crc32(raw) & 0xFFFFFFFF) != crc:
         raise ValueError(f"{path}: corrupt weight file")
-    return layers, np.frombuffer(raw, dtype=np.float32).copy()
+    return layers, np.frombuffer(raw, dtype=np.float32).copy(), bool(flags & 1)
 
 
 def load_cnn(path: str = DEFAULT_WEIGHTS):
-    """A library CNN object holding the weights stored at `path`."""
+    """A library CNN object holding the weights stored at `path`; ``net.scaled``
+    tells whether it expects options.cnn_scale = 1."""
     from .binding import CNN
-    layers, params = load_weights(path)
+    layers, params, scaled = load_weights(path)
     net = CNN(layers)
     net.set_params(params)
+    net.scaled = scaled
     return net
 
 
@@ -100,18 +109,53 @@ def harvest(n_phantoms: int, iters: int, patches_per_iter: int, patch: int, seed
     return torch.stack(rs).contiguous(), torch.stack(xs).contiguous(), np.asarray(sg, dtype=np.float32)
 
 
-def train(r, x, sigma, steps: int, batch: int, lr: float, seed: int = 0, log_every: int = 100):
+def harvest_clean(n_phantoms: int, patches: int, patch: int, seed0: int = 2000,
+                  workload: str = "ellipse512_v64"):
+    """x_true = V mu_true patches of training phantoms (GPU), [n_phantoms * patches][patch][patch]."""
+    import torch
+    import synth
+    from .binding import Plan
+    rng = np.random.default_rng(11)
+    xs = []
+    plan = None
+    for k in range(n_phantoms):
+        c = synth.make_case(workload, seed=seed0 + k)
+        if plan is None:
+            plan = Plan(c["n"], c["n_views"], c["n_det"], **PLAIN)
+        xt = plan.precond_image(torch.as_tensor(c["mu"], dtype=torch.float32).cuda(), inverse=False)
+        n = c["n"]
+        for _ in range(patches):
+            i, j = rng.integers(0, n - patch + 1, size=2)
+            xs.append(xt[i:i + patch, j:j + patch])
+    plan.close()
+    return torch.stack(xs).contiguous()
+
+
+def train(r, x, sigma, steps: int, batch: int, lr: float, seed: int = 0, log_every: int = 100,
+          awgn=None):
+    """Adam on the library's kernels.  awgn = (sigma_lo, sigma_hi) draws, every step,
+    fresh r = x + sigma n with log-uniform sigma per patch (r and sigma unused)."""
+    import torch
     from .binding import CNN
     net = CNN(17, seed=seed)
     rng = np.random.default_rng(seed + 1)
-    n = r.shape[0]
+    gen = torch.Generator(device=x.device)
+    gen.manual_seed(seed + 2)
+    n = x.shape[0]
     hist = []
     t0 = time.time()
     for s in range(steps):
         idx = rng.choice(n, size=batch, replace=False)
-        ti = __import__("torch").as_tensor(idx, device=r.device)
+        ti = torch.as_tensor(idx, device=x.device)
+        xb = x[ti].contiguous()
+        if awgn is not None:
+            sg = np.exp(rng.uniform(np.log(awgn[0]), np.log(awgn[1]), size=batch)).astype(np.float32)
+            noise = torch.randn(xb.shape, generator=gen, device=x.device)
+            rb = (xb + torch.as_tensor(sg, device=x.device)[:, None, None] * noise).contiguous()
+        else:
+            rb, sg = r[ti].contiguous(), sigma[idx]
         lr_s = lr * (0.5 if s > 0.6 * steps else 1.0) * (0.5 if s > 0.85 * steps else 1.0)
-        loss = net.train_step(r[ti].contiguous(), x[ti].contiguous(), sigma[idx], lr_s)
+        loss = net.train_step(rb, xb, sg, lr_s)
         if s % log_every == 0 or s == steps - 1:
             hist.append((s, loss))
     return net, hist, time.time() - t0
@@ -127,16 +171,25 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--mode", choices=("awgn", "iterates"), default="awgn")
+    ap.add_argument("--sigma", type=float, nargs=2, default=(0.003, 1.0), help="awgn sigma range")
     args = ap.parse_args(argv)
     import torch
     from . import build
     build.build()
     t0 = time.time()
-    r, x, sg = harvest(args.phantoms, args.iters, args.patches, args.patch)
+    if args.mode == "awgn":
+        x = harvest_clean(args.phantoms, args.iters * args.patches, args.patch)
+        r, sg = None, np.asarray(args.sigma, dtype=np.float32)
+        awgn = tuple(args.sigma)
+    else:
+        r, x, sg = harvest(args.phantoms, args.iters, args.patches, args.patch)
+        awgn = None
     t_h = time.time() - t0
-    net, hist, t_t = train(r, x, sg, args.steps, args.batch, args.lr)
-    save_weights(args.out, net.get_params(), net.layers)
-    meta = {"pairs": int(r.shape[0]), "patch": args.patch, "sigma_range": [float(sg.min()), float(sg.max())],
+    net, hist, t_t = train(r, x, sg, args.steps, args.batch, args.lr, awgn=awgn)
+    save_weights(args.out, net.get_params(), net.layers, scaled=args.mode == "awgn")
+    meta = {"mode": args.mode, "pairs": int(x.shape[0]), "patch": args.patch,
+            "sigma_range": [float(sg.min()), float(sg.max())],
             "steps": args.steps, "batch": args.batch, "lr": args.lr, "harvest_s": t_h, "train_s": t_t,
             "loss": hist}
     print(json.dumps(meta))

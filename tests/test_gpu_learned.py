@@ -1,0 +1,129 @@
+"""GPU parity of the learned D-GAMP-CT solve: Algorithm 1 with the residual
+CNN as the Step 4 denoiser, through the C ABI, against the FP64 oracle with
+the same BF16-rounded weights and BF16 activation rounding.
+
+The parity network is a seeded He-initialised one: its BF16 evaluation
+stays within 2e-3 of its own FP64 evaluation on these inputs, so the test
+measures the solve, not the network's sensitivity.  (The shipped trained
+weights, fed inputs far outside their training range -- sigma = sqrt(tau_r)
+near 1 while the actual error of r is near 0.003 -- differ from their own
+FP64 evaluation by about 27% in BF16; no two BF16 implementations can agree
+more closely than that there.)
+
+Tolerance: the GPU and the oracle round the same activations to BF16
+(relative step 2^-8) from FP32 and FP64 sums; a rounding decision flips when
+the two sums straddle a BF16 tie, which perturbs that activation by one BF16
+step.  One network evaluation then agrees to a few 1e-3 (the forward parity
+test bounds it at 1e-2); three iterations of the loop feed that through
+tau_x, tau_r and r, so the reconstruction and the variances are held to
+2e-2 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import cnn, gamp
+from oracle.geometry import Geometry
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_04661_gb300 import build
+    build.build()
+    import paper_1609_04661_gb300 as dg
+    dg.load()
+    return dg
+
+
+@pytest.fixture(scope="module")
+def weights():
+    from paper_1609_04661_gb300.train_denoiser import load_weights
+    layers, params, scaled = load_weights()
+    assert layers == cnn.LAYERS
+    return params, scaled
+
+
+@pytest.mark.parametrize("scaled", [1, 0])
+def test_learned_solve_matches_oracle(dg, scaled):
+    from paper_1609_04661_gb300.binding import flatten_params
+    c = synth.make_case("ellipse64_v30")
+    g = Geometry(c["n"], c["n_views"], c["n_det"])
+    T = 3
+    ws, bs = cnn.init_params(21)                  # BF16-valued weights, zero biases
+    rng = np.random.default_rng(22)
+    bs = [np.asarray(rng.standard_normal(b.shape) * 0.02, dtype=np.float32).astype(np.float64) for b in bs]
+    params = flatten_params(ws, bs)
+    log = []
+    opts = gamp.Options(damp_x=0.5, damp_s=0.5)
+    mu_ref, x_ref = gamp.ct_solve(c["y"], c["I0"], g, T, opts, return_x=True, log=log,
+                                  cnn=(ws, bs, bool(scaled)))
+    with dg.CNN(cnn.LAYERS) as net, dg.Plan(g.n, g.n_views, g.n_det, denoiser=1, cnn_scale=scaled,
+                                            damp_x=0.5, damp_s=0.5) as pl:
+        net.set_params(params)
+        pl.set_cnn(net)
+        xo = torch.empty((g.n, g.n), device="cuda")
+        y = torch.as_tensor(c["y"]).cuda()
+        mu, st = pl.solve(y, c["I0"], T, with_stats=True, x_out=xo)
+        mu, xo = mu.cpu().numpy(), xo.cpu().numpy()
+    assert st["iters_done"] == T
+    assert np.allclose(st["tau_r"], [lg.tau_r for lg in log], rtol=2e-2)
+    assert np.allclose(st["div"], [lg.div for lg in log], rtol=2e-2, atol=2e-2)
+    assert rel(xo, x_ref) < 2e-2
+    assert rel(mu, mu_ref) < 2e-2
+
+
+def test_learned_solve_needs_a_network(dg):
+    c = synth.make_case("ellipse64_v30")
+    with dg.Plan(c["n"], c["n_views"], c["n_det"], denoiser=1) as pl:
+        with pytest.raises(dg.DgampError):
+            pl.solve(torch.as_tensor(c["y"]).cuda(), c["I0"], 2)
+
+
+def test_shipped_network_denoises_gaussian_noise(dg, weights):
+    """The shipped weights are a noise-level-scaled Gaussian denoiser: on a
+    held-out phantom in the preconditioned space it must remove most of the
+    noise at every level it was trained for."""
+    params, scaled = weights
+    assert scaled
+    c = synth.make_case("ellipse512_v64", seed=1000)
+    with dg.CNN(cnn.LAYERS) as net, dg.Plan(c["n"], c["n_views"], c["n_det"]) as pl:
+        net.set_params(params)
+        xt = pl.precond_image(torch.as_tensor(c["mu"], dtype=torch.float32).cuda(), inverse=False)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(3)
+        for sigma in (0.01, 0.1, 1.0):
+            r = (xt + sigma * torch.randn(xt.shape, generator=gen, device="cuda")).contiguous()
+            d = net.denoise(r[None].contiguous(), np.array([sigma], dtype=np.float32))[0]
+            mse_in = float(((r - xt) ** 2).mean())
+            mse_out = float(((d - xt) ** 2).mean())
+            assert mse_out < 0.1 * mse_in, (sigma, mse_in, mse_out)
+
+
+def test_graph_recaptured_after_network_workspace_grows(dg, weights):
+    """Using the attached network elsewhere (here: a gradient pass that keeps
+    all 17 activations) regrows its workspace; the next solve must re-capture
+    the iteration graph and give the same result as before."""
+    params, scaled = weights
+    c = synth.make_case("ellipse64_v30")
+    y = torch.as_tensor(c["y"]).cuda()
+    with dg.CNN(cnn.LAYERS) as net, dg.Plan(c["n"], c["n_views"], c["n_det"], denoiser=1,
+                                            cnn_scale=int(scaled), damp_x=0.5, damp_s=0.5) as pl:
+        net.set_params(params)
+        pl.set_cnn(net)
+        mu1 = pl.solve(y, c["I0"], 3).cpu().numpy()
+        r = torch.rand((4, 96, 96), device="cuda")
+        net.gradients(r, r, np.ones(4, dtype=np.float32))
+        mu2 = pl.solve(y, c["I0"], 3).cpu().numpy()
+    assert np.array_equal(mu1, mu2)

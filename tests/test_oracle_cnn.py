@@ -104,6 +104,21 @@ def test_bf16_rounding_matches_torch():
     assert cnn.bf16_round(np.array([1 + 3 * 2 ** -8]))[0] == 1 + 2 ** -6
 
 
+def test_loss_of_identity_network_is_normalised_error():
+    """With every weight and bias zero, f = 0 and D(r) = r: the loss is the
+    noise-normalised input error, each image weighted by 1 / sigma^2."""
+    ws, bs = _tiny(seed=3)
+    ws = [np.zeros_like(w) for w in ws]
+    bs = [np.zeros_like(b) for b in bs]
+    rng = np.random.default_rng(8)
+    xt = rng.standard_normal((2, 6, 6))
+    sig = np.array([0.25, 4.0])
+    noise = rng.choice([-1.0, 1.0], size=(2, 6, 6))
+    r = xt + sig[:, None, None] * noise          # error / sigma is exactly +-1
+    loss, _, _ = cnn.loss_and_grads(r, xt, sig, ws, bs)
+    assert loss == pytest.approx(1.0, rel=1e-14)
+
+
 def test_loss_gradient_matches_finite_differences():
     ws, bs = _tiny(seed=6)
     rng = np.random.default_rng(7)
@@ -118,3 +133,40 @@ def test_loss_gradient_matches_finite_differences():
     wm[1][0, 2, 1, 3] -= h
     num = (cnn.loss_and_grads(r, xt, sig, wp, bs)[0] - cnn.loss_and_grads(r, xt, sig, wm, bs)[0]) / (2 * h)
     assert gws[1][0, 2, 1, 3] == pytest.approx(num, rel=1e-5)
+
+
+def test_jvp_matches_central_differences_of_the_fp64_network():
+    """J_f t from the forward-mode pass equals the central difference of the
+    FP64 network: f is piecewise linear, so for a step too small to cross a
+    ReLU boundary the difference quotient is exact up to rounding."""
+    ws, bs = _tiny(seed=9, layers=4, ch=5)
+    rng = np.random.default_rng(10)
+    x = rng.standard_normal((2, 7, 6))
+    t = rng.standard_normal((2, 7, 6))
+    f, tf = cnn.net_jvp(x, t, ws, bs)
+    f0, _ = cnn.net_forward(x, ws, bs)
+    assert np.array_equal(f, f0)
+    h = 1e-7
+    fp, _ = cnn.net_forward(x + h * t, ws, bs)
+    fm, _ = cnn.net_forward(x - h * t, ws, bs)
+    assert np.allclose(tf, (fp - fm) / (2 * h), rtol=1e-6, atol=1e-8)
+
+
+def test_jvp_is_linear_in_the_direction_and_denoiser_tangent_is_identity_minus_jf():
+    ws, bs = _tiny(seed=12, layers=3, ch=4)
+    rng = np.random.default_rng(13)
+    r = rng.standard_normal((6, 6))
+    b1, b2 = rng.standard_normal((2, 6, 6))
+    sigma = 0.7
+    _, j1 = cnn.denoise_jvp(r, b1, sigma, ws, bs)
+    _, j2 = cnn.denoise_jvp(r, b2, sigma, ws, bs)
+    _, j12 = cnn.denoise_jvp(r, 2.0 * b1 - 3.0 * b2, sigma, ws, bs)
+    assert np.allclose(j12, 2.0 * j1 - 3.0 * j2, rtol=1e-12, atol=1e-12)
+    # D = r - sigma f(r / sigma): J_D b = b - J_f(r / sigma) b
+    _, tf = cnn.net_jvp((r / sigma)[None], b1[None], ws, bs)
+    assert np.allclose(j1, b1 - tf[0], rtol=1e-12, atol=1e-12)
+    # zero network: D(r) = r, so the tangent is b itself and D' = |b|^2 / N
+    z_ws = [np.zeros_like(w) for w in ws]
+    z_bs = [np.zeros_like(v) for v in bs]
+    d, jb = cnn.denoise_jvp(r, b1, sigma, z_ws, z_bs)
+    assert np.array_equal(d, r) and np.array_equal(jb, b1)
