@@ -128,6 +128,65 @@ def _learned_vs_plain(dg, plan, case, counts, T, plain_iters_per_s):
                              "algorithmic_flop_per_iteration": flop}}
 
 
+def _batched(dg, rank, world, dist, flush, steps):
+    """The 64-slice mixed batch (n in {256, 384, 512}, 32-128 views) through
+    dgamp_ct_solve_batched; under torchrun each rank takes its largest-first
+    share of the slices (strong scaling: the batch is fixed)."""
+    import numpy as np
+    import torch
+    import synth
+    batch = synth.make_batch("mixed64")
+    T = batch[0]["iters"]
+    work = np.array([c["n_views"] * c["n_det"] * c["n"] for c in batch], dtype=np.int64)
+    owner, _ = dg.schedule_lpt(work, world)
+    mine = [c for c, q in zip(batch, owner) if q == rank]
+    plans = [dg.Plan(c["n"], c["n_views"], c["n_det"], **TV) for c in mine]
+    counts = [torch.as_tensor(c["y"]).cuda() for c in mine]
+    I0 = [c["I0"] for c in mine]
+    mus = [torch.empty((c["n"], c["n"]), device="cuda") for c in mine]
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        dg.solve_batched(plans, counts, I0, T, mu_out=mus)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([total], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total / steps
+
+    ms = timed(lambda: dg.solve_batched(plans, counts, I0, T, mu_out=mus))
+
+    def serial():
+        for p, c, i0, m in zip(plans, counts, I0, mus):
+            p.solve(c, i0, T, mu_out=m)
+
+    ms_serial = timed(serial)
+    launches = sum(p.solve_launches(T) for p in plans)
+    for p in plans:
+        p.close()
+    return {"workload": "mixed64: 64 slices, n in {256,384,512}, views in {32,48,64,96,128}, bins ceil(1.42 n), "
+                        "log10 I0 ~ U(4,6), 10 ellipses + rectangle each (seed 3000), 30 iterations, prox-TV",
+            "slices": len(batch), "iters_per_slice": T, "scaling": "strong",
+            "ms_per_batch": ms, "iters_per_s": len(batch) * T / (ms / 1e3),
+            "slices_per_s": len(batch) / (ms / 1e3),
+            "one_stream_ms_per_batch": ms_serial, "concurrency_speedup": ms_serial / ms,
+            "joseph_steps_per_batch": int(work.sum()), "gpu_launches_per_batch_rank0": int(launches)}
+
+
 def _config(n_gpus):
     from synth import CASES
     n, nv, nd, ne, rmax, rect, I0, iters = CASES[WORKLOAD]
@@ -369,6 +428,7 @@ def run_gpu(args):
     learned = None
     if rank == 0 and not args.no_learned:
         learned = _learned_vs_plain(dg, plan, case, counts, T, value / world)
+    batched = None if args.no_batched else _batched(dg, rank, world, dist, flush, 3)
 
     line = None
     if rank == 0:
@@ -386,7 +446,7 @@ def run_gpu(args):
                 "psnr_db": psnr,
                 "a_plus_at_gbs": a_at_bytes / (a_at_ms * 1e-3) / 1e9,
                 "iteration_ms": iter_ms, "kernel_ms": prof, "kernel_share": shares,
-                "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned}
+                "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned, "batched": batched}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:
@@ -403,6 +463,7 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain section")
+    ap.add_argument("--no-batched", action="store_true", help="skip the mixed-batch section")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -95,7 +95,7 @@ typedef struct {
     double* tau_p;         /* tau_p^t                                           */
     double* tau_s;         /* tau_s^t                                           */
     double* tau_r;         /* tau_r^t                                           */
-    double* div;           /* D'(r^t), Monte-Carlo estimate                     */
+    double* div;           /* D'(r^t) (Eq. MC_SURE; eps -> 0 limit for the CNN) */
     /* Filled on return (always, when stats is non-NULL). */
     int32_t iters_done;
     int32_t newton_capped; /* output-step elements that hit the iteration cap   */
@@ -222,6 +222,31 @@ int dgamp_ct_solve_trace(dgamp_ct_plan_t plan, const float* d_counts, double I0,
 int dgamp_ct_solve_host(dgamp_ct_plan_t plan, const float* h_counts, double I0,
                         int32_t iters, float* h_mu_out, dgamp_ct_stats* stats,
                         void* stream);
+
+/* A batch of independent slices (the paper reconstructs one 2-D slice per
+   solve, Section 6; a volume or a queue of scans is many of them): slice i
+   is dgamp_ct_solve(plans[i], d_counts[i], I0[i], iters, d_mu_out[i]).  Plans
+   may have different geometries and denoisers but must be distinct and made
+   on the current device.  The slices are scheduled largest-first (work =
+   n_views * n_det * n, the Joseph steps of one projection) over up to 16
+   streams that fork from and join back into `stream`, so small slices run
+   concurrently; the call only enqueues work unless stats != NULL, in which
+   case it synchronises and fills stats[0..n-1].  The result of each slice is
+   bit-identical to its own dgamp_ct_solve.  Errors: INVALID_ARG (n < 0, a
+   NULL pointer, a repeated plan, a plan of another device, a learned plan
+   without a network, I0 <= 0 or not finite, iters < 1), CUDA, NONFINITE
+   (only with stats). */
+int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float* const* d_counts,
+                           const double* I0, int32_t iters, float* const* d_mu_out,
+                           dgamp_ct_stats* stats, void* stream);
+
+/* Host-only scheduler (no device work): assigns n jobs of the given work
+   (>= 0) to `queues` queues, largest job first, each to the least-loaded
+   queue (ties: the lowest queue index; equal work keeps input order).
+   queue_of[i] receives job i's queue; load (nullable, `queues` entries) the
+   total work per queue.  Used for the streams of dgamp_ct_solve_batched and
+   to split a batch across processes.  Errors: INVALID_ARG. */
+int dgamp_ct_schedule_lpt(int32_t n, const int64_t* work, int32_t queues, int32_t* queue_of, int64_t* load);
 
 /* Number of kernels one dgamp_ct_solve enqueues for `iters` iterations. */
 int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t plan, int32_t iters);

@@ -29,7 +29,7 @@ EXPORTS = (
     "dgamp_ct_output_step_noalloc", "dgamp_ct_get_tuning", "dgamp_ct_set_tuning",
     "dgamp_ct_cnn_create", "dgamp_ct_cnn_destroy", "dgamp_ct_cnn_num_params", "dgamp_ct_cnn_set_params",
     "dgamp_ct_cnn_get_params", "dgamp_ct_cnn_denoise", "dgamp_ct_cnn_denoise_jvp", "dgamp_ct_cnn_gradients", "dgamp_ct_cnn_train_step",
-    "dgamp_ct_plan_set_cnn", "dgamp_ct_solve_trace",
+    "dgamp_ct_plan_set_cnn", "dgamp_ct_solve_trace", "dgamp_ct_solve_batched", "dgamp_ct_schedule_lpt",
 )
 
 
@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_cnn_get_params": (C.c_int, [vp, vp, i64]),
         "dgamp_ct_cnn_denoise": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, vp]),
         "dgamp_ct_cnn_denoise_jvp": (C.c_int, [vp, vp, vp, C.c_float, i32, i32, vp, vp, vp]),
+        "dgamp_ct_solve_batched": (C.c_int, [i32, vp, vp, vp, i32, vp, vp, vp]),
+        "dgamp_ct_schedule_lpt": (C.c_int, [i32, vp, i32, vp, vp]),
         "dgamp_ct_cnn_gradients": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, C.POINTER(dbl), vp, vp]),
         "dgamp_ct_cnn_train_step": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, C.c_float, C.POINTER(dbl), vp]),
         "dgamp_ct_plan_set_cnn": (C.c_int, [vp, vp]),
@@ -438,6 +440,47 @@ class CNN:
         _check(self._lib.dgamp_ct_cnn_train_step(self._h, _ptr(r), _ptr(x), s.ctypes.data_as(C.c_void_p), B, H, W,
                                                  C.c_float(lr), C.byref(loss), _stream()), "cnn_train_step")
         return loss.value
+
+
+def schedule_lpt(work, queues: int):
+    """Largest-first assignment of jobs to queues (dgamp_ct_schedule_lpt):
+    returns (queue of each job, total work per queue)."""
+    lib = load()
+    w = np.ascontiguousarray(work, dtype=np.int64)
+    q = np.empty(w.size, dtype=np.int32)
+    load_ = np.empty(int(queues), dtype=np.int64)
+    _check(lib.dgamp_ct_schedule_lpt(int(w.size), w.ctypes.data_as(C.c_void_p), int(queues),
+                                     q.ctypes.data_as(C.c_void_p), load_.ctypes.data_as(C.c_void_p)),
+           "dgamp_ct_schedule_lpt")
+    return q, load_
+
+
+def solve_batched(plans, counts, I0, iters: int, mu_out=None, with_stats: bool = False):
+    """dgamp_ct_solve_batched over a list of plans: one slice per plan, each with
+    its own counts tensor and I0; returns the list of mu (and per-slice stats)."""
+    n = len(plans)
+    if len(counts) != n or len(I0) != n:
+        raise ValueError("plans, counts and I0 must have the same length")
+    lib = load()
+    mus = [p._img() for p in plans] if mu_out is None else list(mu_out)
+    P = (C.c_void_p * n)(*[p._h.value if isinstance(p._h, C.c_void_p) else p._h for p in plans])
+    Cn = (C.c_void_p * n)(*[_ptr(c, p.M, "counts").value for c, p in zip(counts, plans)])
+    Mu = (C.c_void_p * n)(*[_ptr(m, p.N, "mu_out").value for m, p in zip(mus, plans)])
+    i0 = np.ascontiguousarray(I0, dtype=np.float64)
+    st, arrays = None, None
+    if with_stats:
+        arrays = [{k: np.zeros(iters) for k in ("tau_x", "tau_p", "tau_s", "tau_r", "div")} for _ in range(n)]
+        st = (Stats * n)(*[Stats(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in ar.values()], 0, 0, 0)
+                           for ar in arrays])
+    rc = lib.dgamp_ct_solve_batched(n, P, Cn, i0.ctypes.data_as(C.c_void_p), int(iters), Mu,
+                                    st if st is not None else None, _stream())
+    _check(rc, "dgamp_ct_solve_batched")
+    if with_stats:
+        for k in range(n):
+            arrays[k].update(iters_done=st[k].iters_done, newton_capped=st[k].newton_capped,
+                             tau_x_floored=st[k].tau_x_floored)
+        return mus, arrays
+    return mus
 
 
 def flatten_params(ws, bs) -> np.ndarray:

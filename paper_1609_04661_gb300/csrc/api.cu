@@ -38,12 +38,6 @@ static int dalloc(T** p, size_t count) {
     return DGAMP_CT_OK;
 }
 
-#define DGCT_TRY(x)                 \
-    do {                            \
-        int _rc = (x);              \
-        if (_rc != DGAMP_CT_OK) return _rc; \
-    } while (0)
-
 static int ilog2(int v) {
     int l = 0;
     while ((1 << l) < v) ++l;
@@ -589,6 +583,17 @@ int dgamp_ct_solve(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t
     if (d_x_out) DGCT_CUDA(cudaMemcpyAsync(d_x_out, w.x, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
     if (!stats) return DGAMP_CT_OK;
     DGCT_CUDA(cudaStreamSynchronize(st));
+    return fill_stats(pl, iters, stats);
+}
+
+}  // extern "C"
+
+namespace dgct {
+
+// Per-iteration log and counters of the plan's last solve (the solve's work
+// must be complete).
+int fill_stats(const dgamp_ct_plan_s* pl, int iters, dgamp_ct_stats* stats) {
+    const Workspace& w = pl->ws;
     DevScalars hs;
     DGCT_CUDA(cudaMemcpy(&hs, w.S, sizeof(hs), cudaMemcpyDeviceToHost));
     std::vector<IterLog> lg(iters);
@@ -606,6 +611,10 @@ int dgamp_ct_solve(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t
     if (hs.nonfinite) return DGAMP_CT_ERR_NONFINITE;
     return DGAMP_CT_OK;
 }
+
+}  // namespace dgct
+
+extern "C" {
 
 int dgamp_ct_solve_host(dgamp_ct_plan_t pl, const float* h_counts, double I0, int32_t iters, float* h_mu_out,
                         dgamp_ct_stats* stats, void* stream) {

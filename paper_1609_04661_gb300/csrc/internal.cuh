@@ -12,6 +12,7 @@ namespace dgct {
 constexpr int kPad = 4;            // zero guard cells on each side of a staged image line
 constexpr int kMaxIters = 1 << 16; // bound on one solve's iteration count (log size)
 constexpr int kNewtonCap = 64;     // output-step iteration cap
+constexpr int kBatchStreams = 16;  // streams a batched solve spreads its slices over
 
 // Joseph constants of one view.  The ray of bin d meets march line s (a
 // column for col = 1, a row for col = 0) at fractional index
@@ -184,11 +185,19 @@ int cuda_fail(cudaError_t e);
         cudaError_t _e = cudaGetLastError();                       \
         if (_e != cudaSuccess) return ::dgct::cuda_fail(_e);       \
     } while (0)
+#define DGCT_TRY(x)                                                \
+    do {                                                           \
+        int _rc = (x);                                             \
+        if (_rc != DGAMP_CT_OK) return _rc;                        \
+    } while (0)
 #define DGCT_CUDA(call)                                            \
     do {                                                           \
         cudaError_t _e = (call);                                   \
         if (_e != cudaSuccess) return ::dgct::cuda_fail(_e);       \
     } while (0)
+
+// api.cu: copy the last solve's log and counters to *stats (work must be complete)
+int fill_stats(const dgamp_ct_plan_s* pl, int iters, dgamp_ct_stats* stats);
 
 // ----------------------------------------------------------- launchers ----
 // joseph.cu

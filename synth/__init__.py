@@ -240,3 +240,35 @@ def make_case(name: str, seed: int = 1000):
     y = poisson_counts(z, I0, seed + 7)
     return dict(name=name, phantom=ph, mu=rasterise(ph, n), z=z, y=y, I0=I0,
                 n=n, n_views=nv, n_det=nd, iters=iters, seed=seed)
+
+
+# Mixed batch of independent slices: image side, view count, detector bins
+# ceil(1.42 n) and dose drawn per slice (the paper reconstructs slice by
+# slice; a batch stands in for a volume or a queue of scans of varying size).
+BATCHES = {
+    # 64 slices, n in {256, 384, 512}, views in {32, 48, 64, 96, 128},
+    # log10 I0 ~ U(4, 6), 10 ellipses + rectangle object each, 30 iterations
+    "mixed64": dict(count=64, sides=(256, 384, 512), views=(32, 48, 64, 96, 128), log10_I0=(4.0, 6.0),
+                    n_ellipses=10, with_rect=True, iters=30),
+}
+
+
+def make_batch(name: str = "mixed64", seed: int = 3000, with_mu: bool = False, count: int | None = None):
+    """Slices of a named batch: a list of dicts like :func:`make_case` (``mu``
+    only with ``with_mu``; rasterising is the slow part).  Slice k's phantom
+    uses seed ``seed + 1 + k`` and its counts ``seed + 1 + k + 7``."""
+    spec = BATCHES[name]
+    k_total = spec["count"] if count is None else int(count)
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(k_total):
+        n = int(rng.choice(spec["sides"]))
+        nv = int(rng.choice(spec["views"]))
+        nd = int(math.ceil(1.42 * n))
+        I0 = float(10.0 ** rng.uniform(*spec["log10_I0"]))
+        ph = random_phantom(n, spec["n_ellipses"], seed + 1 + k, with_rect=spec["with_rect"])
+        z = analytic_sinogram(ph, view_angles(nv), nd)
+        y = poisson_counts(z, I0, seed + 1 + k + 7)
+        out.append(dict(name=f"{name}[{k}]", phantom=ph, mu=rasterise(ph, n) if with_mu else None, z=z, y=y,
+                        I0=I0, n=n, n_views=nv, n_det=nd, iters=spec["iters"], seed=seed + 1 + k))
+    return out
