@@ -128,6 +128,26 @@ def _learned_vs_plain(dg, plan, case, counts, T, plain_iters_per_s):
                              "algorithmic_flop_per_iteration": flop}}
 
 
+def _ablation(plan, case, counts, T):
+    """PSNR after t = 1..T iterations with and without the Onsager term and
+    the damping (Sections 7.1 and 7.2), on the benchmark slice."""
+    import torch
+    mu = torch.empty((case["n"], case["n"]), device="cuda")
+    out = {}
+    for name, ons, damp in [("onsager_damped", 1, TV["damp_x"]), ("onsager_undamped", 1, 1.0),
+                            ("no_onsager_damped", 0, TV["damp_x"]), ("no_onsager_undamped", 0, 1.0)]:
+        plan.set_options(onsager=ons, damp_x=damp, damp_s=damp)
+        curve = []
+        for t in range(1, T + 1):
+            plan.solve(counts, case["I0"], t, mu_out=mu)
+            curve.append(_psnr(mu.cpu().numpy().astype("float64"), case["mu"]))
+        best = max(range(T), key=lambda k: curve[k])
+        out[name] = {"psnr_db_final": round(curve[-1], 2), "psnr_db_best": round(curve[best], 2),
+                     "best_at_iteration": best + 1, "psnr_db_at_10": round(curve[9], 2) if T >= 10 else None}
+    plan.set_options(onsager=1, damp_x=TV["damp_x"], damp_s=TV["damp_s"])
+    return out
+
+
 def _batched(dg, rank, world, dist, flush, steps):
     """The 64-slice mixed batch (n in {256, 384, 512}, 32-128 views) through
     dgamp_ct_solve_batched; under torchrun each rank takes its largest-first
@@ -429,6 +449,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_learned:
         learned = _learned_vs_plain(dg, plan, case, counts, T, value / world)
     batched = None if args.no_batched else _batched(dg, rank, world, dist, flush, 3)
+    ablation = _ablation(plan, case, counts, T) if rank == 0 and not args.no_learned else None
 
     line = None
     if rank == 0:
@@ -446,7 +467,8 @@ def run_gpu(args):
                 "psnr_db": psnr,
                 "a_plus_at_gbs": a_at_bytes / (a_at_ms * 1e-3) / 1e9,
                 "iteration_ms": iter_ms, "kernel_ms": prof, "kernel_share": shares,
-                "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned, "batched": batched}
+                "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned, "batched": batched,
+                "ablation": ablation}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:

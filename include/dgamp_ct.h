@@ -86,6 +86,9 @@ typedef struct {
                               1 = D(r) = r - sigma f(r/sigma), sigma = sqrt(tau_r) */
     double   tau_x0;       /* initial tau_x (Algorithm 1 sets 1 in its own, unstated,
                               normalisation of x); default 1 */
+    int32_t  truncate_z;   /* 0 (default): the output step's posterior runs over the whole
+                              line (Section 4.2); 1: restricted to z >= 0 (mode max(z0, 0);
+                              where clamped s = -p/tau_p and tau_s_i = 1/tau_p) */
 } dgamp_ct_options;
 
 typedef struct {
@@ -158,8 +161,9 @@ int dgamp_ct_filter(dgamp_ct_plan_t plan, const float* d_in, float* d_out, void*
    the corrected Laplace reading): p = z - tau_p s_prev, z0 = mode of
    N(z; p, tau_p) Poisson(y; I0 e^{-z}), s = (z0 - p)/tau_p,
    tau_s = mean_i I0 e^{-z0_i} / (1 + tau_p I0 e^{-z0_i}).
-   d_s_prev may be NULL (treated as 0) and may equal d_s.  *d_tau_s (one
-   device double) receives tau_s. */
+   With the plan's option truncate_z = 1 the posterior is restricted to
+   z >= 0.  d_s_prev may be NULL (treated as 0) and may equal d_s.  *d_tau_s
+   (one device double) receives tau_s. */
 int dgamp_ct_output_step(dgamp_ct_plan_t plan, const float* d_z, const float* d_y,
                          const float* d_s_prev, double I0, double tau_p,
                          float* d_s, double* d_tau_s, void* stream);

@@ -49,6 +49,7 @@ class Options:
     damp_s: float = 1.0
     tau_x_floor: float = 1e-6
     tau_x0: float = 1.0      # initial tau_x (Algorithm 1 uses 1)
+    truncate_z: bool = False  # output step on z >= 0 instead of the whole line
 
 
 @dataclasses.dataclass
@@ -143,7 +144,7 @@ def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
         return _pre.backproject(s.reshape(geom.n_views, geom.n_det), geom)
 
     def gout(p, tau_p):
-        s, tsi, _z0, _v = _out.output_step(p, yv, tau_p, I0)
+        s, tsi, _z0, _v = _out.output_step(p, yv, tau_p, I0, truncate=opts.truncate_z)
         return s, tsi
 
     def denoise_factory(tau_r):

@@ -73,15 +73,28 @@ def laplace_mode_delta(p, y, tau_p, log_I0, max_iter: int = 100, tol: float = 1e
     return d
 
 
-def output_step(p, y, tau_p, I0):
-    """Algorithm 1, Step 2.  Returns (s, tau_s_i, z0, var) as fp64 arrays."""
+def output_step(p, y, tau_p, I0, truncate: bool = False):
+    """Algorithm 1, Step 2.  Returns (s, tau_s_i, z0, var) as fp64 arrays.
+
+    ``truncate``: the posterior of z restricted to z >= 0 (a line integral of
+    a non-negative attenuation map; the paper's integrals run over the whole
+    line by default).  Its mode is max(z0, 0); where the bound is active the
+    mode does not move with p, so s = -p / tau_p, var = 0 and
+    tau_s_i = -ds/dp = 1 / tau_p."""
     log_I0 = float(np.log(I0))
+    p = np.asarray(p, dtype=np.float64)
     d = laplace_mode_delta(p, y, tau_p, log_I0)
-    z0 = np.asarray(p, dtype=np.float64) + d
+    z0 = p + d
     w = np.exp(log_I0 - z0)
     var = 1.0 / (1.0 / tau_p + w)
     s = d / tau_p
     tau_s_i = w / (1.0 + tau_p * w)
+    if truncate:
+        act = z0 < 0.0
+        z0 = np.where(act, 0.0, z0)
+        s = np.where(act, -p / tau_p, s)
+        var = np.where(act, 0.0, var)
+        tau_s_i = np.where(act, 1.0 / tau_p, tau_s_i)
     return s, tau_s_i, z0, var
 
 

@@ -53,6 +53,7 @@ static bool options_ok(const dgamp_ct_options* o) {
     if (!(o->tau_x_floor >= 0) || !std::isfinite(o->tau_x_floor)) return false;
     if (!(o->tau_x0 > 0) || !std::isfinite(o->tau_x0)) return false;
     if (o->cnn_scale != 0 && o->cnn_scale != 1) return false;
+    if (o->truncate_z != 0 && o->truncate_z != 1) return false;
     return true;
 }
 
@@ -298,6 +299,7 @@ int dgamp_ct_default_options(dgamp_ct_options* o) {
     o->use_graph = 1;
     o->cnn_scale = 0;
     o->tau_x0 = 1.0;
+    o->truncate_z = 0;
     return DGAMP_CT_OK;
 }
 

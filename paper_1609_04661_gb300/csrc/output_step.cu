@@ -8,6 +8,8 @@
 // bracket where psi changes sign:
 //   y > 0:  [min(0, L - p), max(0, L - p)], L = log(I0 / y)
 //   y = 0:  [0, m - p + tau_p e^{log I0 - m}], m = max(p, log I0).
+// With truncate = 1 the posterior is restricted to z >= 0: where z0 < 0 the
+// mode is 0, s = -p/tau_p and tau_s_i = 1/tau_p (the mode no longer moves with p).
 // Arithmetic is FP32; tau_s = mean(tau_s_i) is accumulated in FP64 and
 // finished by the last block to arrive, which (inside a solve) also forms
 // tau_r = N / (||Phi~||_F^2 tau_s) for Step 3.
@@ -51,7 +53,7 @@ __device__ __forceinline__ float mode_delta(float p, float y, float tau_p, float
 __global__ void __launch_bounds__(256)
 k_output_step(const float* z, const float* y, float* s, long long M, int use_prev,
               int from_scalars, double tau_p_arg, double logI0_arg, int onsager, float damp_s,
-              double N, DevScalars* S, double* partial, double* tau_s_out) {
+              int truncate, double N, DevScalars* S, double* partial, double* tau_s_out) {
     __shared__ double sm[32];
     __shared__ float s_tp, s_inv, s_logI0;
     __shared__ bool am_last;
@@ -70,12 +72,14 @@ k_output_step(const float* z, const float* y, float* s, long long M, int use_pre
         const float sp = use_prev ? s[i] : 0.f;
         const float p = onsager ? fmaf(-tau_p, sp, z[i]) : z[i];
         const float yv = y[i];
-        const float d = mode_delta(p, yv, tau_p, inv_tp, logI0, capped);
+        float d = mode_delta(p, yv, tau_p, inv_tp, logI0, capped);
+        const bool clamp = truncate && p + d < 0.f;
+        if (clamp) d = -p;
         float sv = d * inv_tp;
         if (damp_s != 1.f) sv = damp_s * sv + (1.f - damp_s) * sp;
         s[i] = sv;
         const float w = expf(logI0 - p - d);
-        const float tsi = isinf(w) ? inv_tp : w / fmaf(tau_p, w, 1.f);
+        const float tsi = (clamp || isinf(w)) ? inv_tp : w / fmaf(tau_p, w, 1.f);
         acc += (double)tsi;
     }
     capped = warp_sum(capped);
@@ -118,8 +122,8 @@ int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y
     const int onsager = from_scalars ? pl->opt.onsager : 1;
     const float damp_s = from_scalars ? (float)pl->opt.damp_s : 1.f;
     k_output_step<<<blocks, 128, 0, st>>>(z, y, s, M, use_prev, from_scalars, tau_p_arg, logI0_arg,
-                                          onsager, damp_s, (double)pl->N, pl->ws.S, pl->ws.partial,
-                                          tau_s_out);
+                                          onsager, damp_s, pl->opt.truncate_z, (double)pl->N, pl->ws.S,
+                                          pl->ws.partial, tau_s_out);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -133,7 +137,7 @@ int launch_output_step_scratch(const float* z, const float* y, float* s, long lo
     long long blocks = (M + 255) / 256;
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
-    k_output_step<<<(int)blocks, 256, 0, st>>>(z, y, s, M, use_prev, 0, tau_p, logI0, 1, 1.f, 0.0, S,
+    k_output_step<<<(int)blocks, 256, 0, st>>>(z, y, s, M, use_prev, 0, tau_p, logI0, 1, 1.f, 0, 0.0, S,
                                                partial, tau_s_out);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;

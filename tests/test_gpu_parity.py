@@ -142,6 +142,26 @@ def test_output_step_matches_oracle(dg, tau_p):
     assert (y == 0).any()
 
 
+def test_truncated_output_step_matches_oracle(dg):
+    """truncate_z = 1: rays through (almost) nothing, where counts can exceed
+    I0 and the unconstrained mode falls below 0, mixed with ordinary rays."""
+    n, nv, nd = 32, 9, 301
+    rng = np.random.default_rng(11)
+    I0, tau_p = 1e4, 0.4
+    z_true = np.where(rng.random((nv, nd)) < 0.4, rng.uniform(-0.03, 0.01, (nv, nd)), rng.uniform(0.5, 8, (nv, nd)))
+    y = rng.poisson(I0 * np.exp(-z_true)).astype(np.float64)
+    z = z_true + rng.normal(0, 0.3, (nv, nd))
+    with dg.Plan(n, nv, nd, truncate_z=1) as pl:
+        s, ts = pl.output_step(cu(z), cu(y), None, I0, tau_p)
+        s, ts = host(s), float(host(ts)[0])
+    f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    s_ref, tsi_ref, z0, _ = output_step.output_step(f32(z).reshape(-1), y.reshape(-1), float(f32(tau_p)), I0,
+                                                    truncate=True)
+    assert (z0 == 0).sum() > 100
+    assert rel(s.reshape(-1), s_ref) < 1e-5
+    assert ts == pytest.approx(np.mean(tsi_ref), rel=1e-5)
+
+
 @pytest.mark.parametrize("kb", [1, 3, 7, 10])           # steps per blocked launch (remainders too)
 @pytest.mark.parametrize("n,lam", [(64, 0.3), (77, 0.05), (33, 0.0), (130, 0.2)])
 def test_tv_matches_oracle(dg, n, lam, kb):
@@ -199,14 +219,15 @@ def case64():
     return c, Geometry(c["n"], c["n_views"], c["n_det"])
 
 
-@pytest.mark.parametrize("use_graph", [1, 0])
-def test_solve_matches_oracle_after_20_iterations(dg, case64, use_graph):
+@pytest.mark.parametrize("use_graph,damp,trunc", [(1, 1.0, 0), (0, 1.0, 0), (1, 0.5, 0), (1, 1.0, 1)])
+def test_solve_matches_oracle_after_20_iterations(dg, case64, use_graph, damp, trunc):
     c, g = case64
     T = c["iters"]
     log = []
-    mu_ref, x_ref = gamp.ct_solve(c["y"], c["I0"], g, T, gamp.Options(c_tv=3.0, k_tv=20), return_x=True,
-                                  log=log)
-    with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, use_graph=use_graph) as pl:
+    opts = gamp.Options(c_tv=3.0, k_tv=20, damp_x=damp, damp_s=damp, truncate_z=bool(trunc))
+    mu_ref, x_ref = gamp.ct_solve(c["y"], c["I0"], g, T, opts, return_x=True, log=log)
+    with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, use_graph=use_graph, damp_x=damp, damp_s=damp,
+                 truncate_z=trunc) as pl:
         xo = torch.empty((g.n, g.n), device="cuda")
         mu, st = pl.solve(cu(c["y"]), c["I0"], T, with_stats=True, x_out=xo)
         mu, xo = host(mu), host(xo)

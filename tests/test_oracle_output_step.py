@@ -82,3 +82,41 @@ def test_gaussian_channel_limit_closed_form():
     _, _, z0, _ = out.output_step(np.array([p]), np.array([y]), tau_p, I0)
     ref = (p / tau_p + y * L) / (1 / tau_p + y)
     assert abs(z0[0] - ref) < 1e-6
+
+
+def test_truncated_mode_is_the_argmax_over_nonnegative_z():
+    """The truncated reading: the mode of the posterior restricted to z >= 0 is
+    found by brute force on a fine grid of [0, 20]; where the unconstrained
+    mode is already >= 0 nothing changes."""
+    I0, tau_p = 1e4, 0.5
+    rng = np.random.default_rng(3)
+    # rays through (almost) nothing: counts can exceed I0, pulling the mode below 0
+    p = np.concatenate([rng.uniform(-3.0, 0.5, 40), rng.uniform(1.0, 8.0, 40)])
+    u = np.concatenate([rng.uniform(-0.05, 0.02, 40), p[40:]])
+    y = rng.poisson(I0 * np.exp(-u)).astype(float)
+    s_f, tsi_f, z_f, _ = out.output_step(p, y, tau_p, I0)
+    s_t, tsi_t, z_t, var_t = out.output_step(p, y, tau_p, I0, truncate=True)
+    grid = np.linspace(0.0, 20.0, 400001)
+    for k in range(p.size):
+        logpost = -(grid - p[k]) ** 2 / (2 * tau_p) + y[k] * (np.log(I0) - grid) - I0 * np.exp(-grid)
+        assert abs(z_t[k] - grid[np.argmax(logpost)]) <= 1e-4
+    keep = z_f >= 0
+    assert np.array_equal(z_t[keep], z_f[keep]) and np.array_equal(s_t[keep], s_f[keep])
+    assert np.array_equal(tsi_t[keep], tsi_f[keep])
+    act = ~keep
+    assert act.sum() > 5
+    assert np.all(var_t[act] == 0.0) and np.allclose(tsi_t[act], 1.0 / tau_p)
+
+
+def test_truncated_tau_s_is_minus_derivative_of_s():
+    """-ds/dp = tau_s_i holds on both branches of the truncated reading."""
+    I0, tau_p = 1e4, 0.3
+    rng = np.random.default_rng(5)
+    p = rng.uniform(-2.0, 6.0, 200)
+    y = rng.poisson(I0 * np.exp(-np.clip(p, 0.05, None))).astype(float)
+    h = 1e-6
+    s_p, *_ = out.output_step(p + h, y, tau_p, I0, truncate=True)
+    s_m, *_ = out.output_step(p - h, y, tau_p, I0, truncate=True)
+    _, tsi, z0, _ = out.output_step(p, y, tau_p, I0, truncate=True)
+    away = np.abs(z0) > 1e-3             # not at the kink itself
+    assert np.allclose(-(s_p - s_m)[away] / (2 * h), tsi[away], rtol=1e-5, atol=1e-6)
