@@ -16,6 +16,12 @@ inside the timed region.
 Under torchrun (N > 1) every rank solves its own slice (seed 1000 + rank):
 replicas only, no data-path collective.
 
+Extra objects on the line: ``learned_vs_plain`` (the learned denoiser in the
+same solve: iterations/s and PSNR per iteration of both forms),
+``batched`` (the 64-slice mixed batch through dgamp_ct_solve_batched,
+split largest-first across ranks) and ``ablation`` (Onsager term and
+damping on and off).
+
 ``--impl reference`` times the FP64 CPU oracle instead, one iteration of the
 same workload per step, on the host cores (rank 0 only).
 """
