@@ -136,12 +136,14 @@ int dgamp_ct_plan_info(dgamp_ct_plan_t plan, double* frob_sq, int32_t* fft_len);
    geometry (they change speed, not the operator):
      filter_mode: 0 = H by FFT, 1 = H as a Toeplitz product with the same
                   kernel h = IFFT_P(g) (no wrap-around since P >= 2 n_det);
-     tv_kb:       Chambolle steps per blocked TV launch, 1..10.
-   get: either pointer may be NULL.  set: a negative value keeps the current
+     tv_kb:       Chambolle steps per blocked TV launch, 1..10;
+     tv_rows:     rows of the image region one TV block holds, 32, 64 or 128
+                  (the region is 64 columns wide).
+   get: any pointer may be NULL.  set: a negative value keeps the current
    choice; out-of-range values return INVALID_ARG.  Setting drops the
    captured graph. */
-int dgamp_ct_get_tuning(dgamp_ct_plan_t plan, int32_t* filter_mode, int32_t* tv_kb);
-int dgamp_ct_set_tuning(dgamp_ct_plan_t plan, int32_t filter_mode, int32_t tv_kb);
+int dgamp_ct_get_tuning(dgamp_ct_plan_t plan, int32_t* filter_mode, int32_t* tv_kb, int32_t* tv_rows);
+int dgamp_ct_set_tuning(dgamp_ct_plan_t plan, int32_t filter_mode, int32_t tv_kb, int32_t tv_rows);
 
 /* z = A x (precond = 0) or z = Phi~ x = H A x (precond = 1); Eq. linCT and
    Algorithm 1, Step 1.  d_img [n][n] -> d_sino [n_views][n_det]. */

@@ -19,7 +19,7 @@ int cuda_fail(cudaError_t e) {
 }
 
 static void free_ws(Workspace& w) {
-    void* ptrs[] = {w.XR, w.XC, w.x, w.r, w.p, w.zraw, w.z, w.s, w.hs, w.y, w.fft2d, w.partial,
+    void* ptrs[] = {w.XR, w.XC, w.x, w.r, w.b, w.p, w.zraw, w.z, w.s, w.hs, w.y, w.fft2d, w.partial,
                     w.S, w.log, w.vc, w.gain, w.tw, w.tw2, w.scratch_d, w.hx, w.zraw2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -102,6 +102,7 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_TRY(dalloc(&w.XC, img_staged));
     DGCT_TRY(dalloc(&w.x, N));
     DGCT_TRY(dalloc(&w.r, 2 * N));
+    DGCT_TRY(dalloc(&w.b, N));
     DGCT_TRY(dalloc(&w.p, 4 * N));
     DGCT_TRY(dalloc(&w.zraw, M));
     DGCT_TRY(dalloc(&w.z, M));
@@ -111,7 +112,10 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_TRY(dalloc(&w.fft2d, (size_t)pl->m2 * pl->m2));
     const size_t tiles32 = (size_t)((pl->n + 31) / 32) * ((pl->n + 31) / 32);
     pl->max_partials = 1024;
-    const size_t nparts = tiles32 > (size_t)pl->max_partials ? tiles32 : (size_t)pl->max_partials;
+    // blocks of the last blocked-TV launch, smallest tiles (43 x 11 pixels), two images
+    const size_t tv_parts = 2 * (size_t)((pl->n + 42) / 43) * ((pl->n + 10) / 11);
+    size_t nparts = tiles32 > (size_t)pl->max_partials ? tiles32 : (size_t)pl->max_partials;
+    if (tv_parts > nparts) nparts = tv_parts;
     DGCT_TRY(dalloc(&w.partial, nparts));
     DGCT_TRY(dalloc(&w.S, 1));
     DGCT_TRY(dalloc(&w.log, (size_t)kMaxIters));
@@ -385,17 +389,20 @@ int dgamp_ct_plan_info(dgamp_ct_plan_t pl, double* frob_sq, int32_t* fft_len) {
     return DGAMP_CT_OK;
 }
 
-int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, int32_t* filter_mode, int32_t* tv_kb) {
+int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, int32_t* filter_mode, int32_t* tv_kb, int32_t* tv_rows) {
     if (!pl) return DGAMP_CT_ERR_INVALID_ARG;
     if (filter_mode) *filter_mode = pl->filter_mode;
     if (tv_kb) *tv_kb = pl->tv_kb;
+    if (tv_rows) *tv_rows = pl->tv_rows;
     return DGAMP_CT_OK;
 }
 
-int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, int32_t filter_mode, int32_t tv_kb) {
+int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, int32_t filter_mode, int32_t tv_kb, int32_t tv_rows) {
     if (!pl || filter_mode > 1 || tv_kb > 10 || tv_kb == 0) return DGAMP_CT_ERR_INVALID_ARG;
+    if (tv_rows >= 0 && tv_rows != 32 && tv_rows != 64 && tv_rows != 128) return DGAMP_CT_ERR_INVALID_ARG;
     if (filter_mode >= 0) pl->filter_mode = filter_mode;
     if (tv_kb > 0) pl->tv_kb = tv_kb;
+    if (tv_rows > 0) pl->tv_rows = tv_rows;
     drop_graph(pl);
     return DGAMP_CT_OK;
 }

@@ -77,6 +77,7 @@ struct Workspace {
     float2* tw = nullptr;          // [P/2]   twiddles exp(-2 pi i k / P)
     float2* tw2 = nullptr;         // [n]     twiddles of length 2n
     double* scratch_d = nullptr;   // plan-time FP64 scratch
+    float* b = nullptr;            // the iteration's probe b (Eq. MC_SURE) [n][n]
 };
 
 }  // namespace dgct
@@ -94,6 +95,7 @@ struct dgamp_ct_plan_s {
     dgct::Workspace ws;
     int max_partials = 0;
     int tv_kb = 5;                         // Chambolle steps per blocked TV launch
+    int tv_rows = 64;                      // rows of a blocked TV region (64 or 128)
     int filter_mode = 0;                   // H by 0: FFT, 1: Toeplitz product (plan-time choice)
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;

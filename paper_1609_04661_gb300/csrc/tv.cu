@@ -11,22 +11,22 @@
 // one pixel of it:
 //   q = div p - r/lambda,  div p = px(i,j) - px(i,j-1) + py(i,j) - py(i-1,j)
 //   p <- (p + tau grad q) / (1 + tau |grad q|),  grad q uses q(i,j+1), q(i+1,j)
-// so a block that holds a 32 x 32 tile plus a halo of H = KB + 1 pixels in
-// shared memory runs KB steps with no global traffic (the valid region
-// shrinks by one pixel per side per step) and can still form div p on its
-// tile for the final x = r - lambda div p.  Duals outside the image stay
-// zero, and grad q is zero on the last row/column (Neumann), which
-// reproduces the boundary rules exactly.  Successive launches exchange the
-// tile's duals through ping-pong global buffers [image][n][n] of float2.
-// KB is a template parameter chosen per plan by timing (tv_autotune).
+// so a block that holds a region of the image runs KB steps with no global
+// traffic while the valid part shrinks by one pixel per side per step, and
+// writes back the region minus KB pixels on each side.  The region lives in
+// registers (see k_tv_steps).  Duals outside the image stay zero, and
+// grad q is zero on the last row/column (Neumann), which reproduces the
+// boundary rules exactly.  Successive launches exchange duals through
+// ping-pong global buffers [image][n][n] of float2; a last launch forms
+// x = r - lambda div p and the divergence.  KB and the region height are
+// chosen per plan by timing (tv_autotune).
 #include <vector>
 
 #include "internal.cuh"
 
 namespace dgct {
 
-constexpr int TB = 32;             // interior tile edge
-constexpr int kTvThreads = 1024;
+constexpr int TB = 32;             // pixel tile edge of the final step
 constexpr int kTvMaxKb = 10;       // most Chambolle steps one launch may run
 constexpr float kTau = 0.125f;
 
@@ -37,10 +37,11 @@ __device__ __forceinline__ float solve_lambda(const DevScalars* S, float c_tv, i
 
 // --------------------------------------------------------- probe input ----
 // r2 = r + eps b, eps = eps_rel max(max|r|, 1e-6), or r2 = b itself
-// (write_b = 1: the direction of a forward-mode divergence).  One thread per
-// block of four probe elements (one Philox call).
-__global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r2, long long N,
-                              float eps_rel, int t_arg, unsigned slice, uint2 key,
+// (write_b = 1: the direction of a forward-mode divergence); b itself also
+// to bout for the divergence sum.  One thread per block of four probe
+// elements (one Philox call).
+__global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r2, float* __restrict__ bout,
+                              long long N, float eps_rel, int t_arg, unsigned slice, uint2 key,
                               DevScalars* S, int write_b) {
     const float rmax = __uint_as_float(S->rmax_bits);
     const float eps = eps_rel * fmaxf(rmax, 1e-6f);
@@ -53,7 +54,10 @@ __global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r
     const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        if (i0 + k < N) r2[i0 + k] = write_b ? bb[k] : fmaf(eps, bb[k], r[i0 + k]);
+        if (i0 + k < N) {
+            r2[i0 + k] = write_b ? bb[k] : fmaf(eps, bb[k], r[i0 + k]);
+            bout[i0 + k] = bb[k];
+        }
 }
 
 static uint2 probe_key(const dgamp_ct_plan_s* pl) {
@@ -64,7 +68,7 @@ int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st, in
     const long long N = pl->N;
     const long long groups = (N + 3) / 4;
     k_probe_input<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(
-        pl->ws.r, pl->ws.r + N, N, (float)pl->opt.eps_rel, t_arg, (unsigned)pl->opt.slice_id,
+        pl->ws.r, pl->ws.r + N, pl->ws.b, N, (float)pl->opt.eps_rel, t_arg, (unsigned)pl->opt.slice_id,
         probe_key(pl), pl->ws.S, write_b);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
@@ -89,7 +93,7 @@ int launch_absmax(const dgamp_ct_plan_s* pl, const float* r, cudaStream_t st) {
     return DGAMP_CT_OK;
 }
 
-// --------------------------------------------------- blocked Chambolle ----
+// ------------------------------------------- register-blocked Chambolle ----
 struct TvFinal {
     float* x_out;          // D(r) (with damping against the old x in a solve)
     float* XR;             // staged copies for the next projection (nullable)
@@ -107,164 +111,96 @@ struct TvFinal {
     int jvp;               // learned denoiser: dn[1] is J_D b (divergence b^T J_D b / N)
 };
 
-// KB Chambolle steps on the block's region in shared memory.  BORDER = false
-// is the fast path for blocks whose whole region lies inside the image and
-// away from its last row/column, where no boundary rule applies.
-template <int NIMG, int KB, bool BORDER>
-__device__ __forceinline__ void tv_steps(float* __restrict__ spx, float* __restrict__ spy,
-                                         float* __restrict__ sq, const float* __restrict__ sr, int n,
-                                         int gi0, int gj0, float inv_lam) {
-    constexpr int H = KB + 1, R = TB + 2 * H, RR = R * R;
-    const int tid = threadIdx.x;
+// A block holds a region of kTvRW = 64 columns by RH = 4 WY rows of one image
+// in registers: thread (warp w, lane l) owns rows 4w..4w+3 of columns l and
+// l + 32.  Horizontal neighbours come from warp shuffles (lane 0 and lane 31
+// wrap between the two columns), vertical ones from the thread's own
+// registers except across warps, where the first row's q and the last row's
+// py pass through shared memory (two barriers per step).  After KB steps the
+// region minus KB pixels on each side holds exact duals and is written back.
+constexpr int kTvU = 2;            // columns per thread
+constexpr int kTvV = 4;            // rows per thread
+constexpr int kTvRW = 32 * kTvU;   // region width
+
+template <int WY, int KB, bool BORDER>
+__device__ __forceinline__ void tv_region_steps(float (&px)[kTvV][kTvU], float (&py)[kTvV][kTvU],
+                                                const float (&rl)[kTvV][kTvU], unsigned inside, unsigned lastc,
+                                                unsigned lastr, float (*e_py)[kTvU][32], float (*e_q)[kTvU][32]) {
+    constexpr int U = kTvU, V = kTvV;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float q[V][U];
 #pragma unroll
+    for (int u = 0; u < U; ++u) e_py[w][u][lane] = py[V - 1][u];
+    __syncthreads();
+#pragma unroll 1
     for (int k = 0; k < KB; ++k) {
-        const int lo = k + 1;
-        const int W = R - 2 * k - 1;            // a constant once the loop is unrolled
-        // q on rows/cols [k+1, R-k)
+        // q = div p - r / lambda  (zero outside the image)
 #pragma unroll
-        for (int im = 0; im < NIMG; ++im) {
-            for (int e = tid; e < W * W; e += kTvThreads) {
-                const int a = lo + e / W, b = lo + (e - (e / W) * W);
-                const int idx = im * RR + a * R + b;
-                float q = (spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R]) - sr[idx] * inv_lam;
-                if (BORDER) {
-                    const int gi = gi0 + a, gj = gj0 + b;
-                    if (!(gi >= 0 && gi < n && gj >= 0 && gj < n)) q = 0.f;
-                }
-                sq[idx] = q;
+        for (int v = 0; v < V; ++v) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float send = lane == 31 ? (u > 0 ? px[v][u - 1] : 0.f) : px[v][u];
+                const float pxl = __shfl_sync(0xffffffffu, send, (lane + 31) & 31);
+                const float pyu = v > 0 ? py[v - 1][u] : (w > 0 ? e_py[w - 1][u][lane] : 0.f);
+                float qq = (px[v][u] - pxl + py[v][u] - pyu) - rl[v][u];
+                if (BORDER && !((inside >> (v * U + u)) & 1u)) qq = 0.f;
+                q[v][u] = qq;
             }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) e_q[w][u][lane] = q[0][u];
         __syncthreads();
-        // p on rows/cols [k+1, R-k-1)
-        const int W2 = W - 1;
+        // p <- (p + tau grad q) / (1 + tau |grad q|)  (grad q = 0 across the last row/column)
 #pragma unroll
-        for (int im = 0; im < NIMG; ++im) {
-            for (int e = tid; e < W2 * W2; e += kTvThreads) {
-                const int a = lo + e / W2, b = lo + (e - (e / W2) * W2);
-                const int idx = im * RR + a * R + b;
-                const float qc = sq[idx];
-                float gx = sq[idx + 1] - qc;
-                float gy = sq[idx + R] - qc;
+        for (int v = 0; v < V; ++v) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float send = lane == 0 ? (u + 1 < U ? q[v][u + 1] : 0.f) : q[v][u];
+                const float qr = __shfl_sync(0xffffffffu, send, (lane + 1) & 31);
+                const float qd = v + 1 < V ? q[v + 1][u] : (w + 1 < WY ? e_q[w + 1][u][lane] : 0.f);
+                float gx = qr - q[v][u];
+                float gy = qd - q[v][u];
+                bool upd = true;
                 if (BORDER) {
-                    const int gi = gi0 + a, gj = gj0 + b;
-                    if (gi < 0 || gi >= n || gj < 0 || gj >= n) continue;
-                    if (gj >= n - 1) gx = 0.f;
-                    if (gi >= n - 1) gy = 0.f;
+                    const int bit = v * U + u;
+                    upd = (inside >> bit) & 1u;
+                    if ((lastc >> bit) & 1u) gx = 0.f;
+                    if ((lastr >> bit) & 1u) gy = 0.f;
                 }
-                const float g2 = fmaf(gx, gx, gy * gy);
-                const float nrm = g2 > 0.f ? g2 * rsqrtf(g2) : 0.f;
-                const float inv = __frcp_rn(fmaf(kTau, nrm, 1.f));
-                spx[idx] = fmaf(kTau, gx, spx[idx]) * inv;
-                spy[idx] = fmaf(kTau, gy, spy[idx]) * inv;
+                if (upd) {
+                    // |grad q| = g2 / sqrt(g2); the floor only keeps rsqrt finite at g2 = 0
+                    const float g2 = fmaf(gx, gx, gy * gy);
+                    const float nrm = g2 * rsqrtf(fmaxf(g2, 1e-30f));
+                    const float inv = __fdividef(1.f, fmaf(kTau, nrm, 1.f));   // denominator >= 1
+                    px[v][u] = fmaf(kTau, gx, px[v][u]) * inv;
+                    py[v][u] = fmaf(kTau, gy, py[v][u]) * inv;
+                }
             }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) e_py[w][u][lane] = py[V - 1][u];
         __syncthreads();
     }
 }
 
-template <int NIMG, int KB>
-__global__ void __launch_bounds__(kTvThreads)
-k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout,
-           int n, int first, int final_step, float c_tv, int from_scalars, float lambda_arg,
-           DevScalars* S, TvFinal F) {
-    constexpr int H = KB + 1, R = TB + 2 * H, RR = R * R;
-    extern __shared__ float sm[];
-    float* __restrict__ spx = sm;
-    float* __restrict__ spy = sm + NIMG * RR;
-    float* __restrict__ sq = sm + 2 * NIMG * RR;
-    float* __restrict__ sr = sm + 3 * NIMG * RR;
-    const size_t N = (size_t)n * n;
-    const int gi0 = blockIdx.y * TB - H, gj0 = blockIdx.x * TB - H;
+// Divergence sum of one block (FP64, any image) -> partial[bid]; the last
+// block to arrive forms D' = (sum of partials) / (N eps) and, in a solve,
+// tau_x = max(tau_r D', floor tau_r), the log record and the next t.
+__device__ __forceinline__ void tv_divergence_finish(double acc, int nblk, int bid, size_t N, DevScalars* S,
+                                                     const TvFinal& F, double* red, bool* am_last) {
     const int tid = threadIdx.x;
-    const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
-    const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
-
-    for (int e = tid; e < NIMG * RR; e += kTvThreads) {
-        const int im = e / RR, c = e - im * RR;
-        const int a = c / R, b = c - a * R;
-        const int gi = gi0 + a, gj = gj0 + b;
-        const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
-        const size_t o = im * N + (size_t)gi * n + gj;
-        sr[e] = in ? rbase[o] : 0.f;
-        float2 p = make_float2(0.f, 0.f);
-        if (in && !first) p = pin[o];
-        spx[e] = p.x;
-        spy[e] = p.y;
-    }
-    __syncthreads();
-
-    const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + R < n && gj0 + R < n;
-    if (interior)
-        tv_steps<NIMG, KB, false>(spx, spy, sq, sr, n, gi0, gj0, inv_lam);
-    else
-        tv_steps<NIMG, KB, true>(spx, spy, sq, sr, n, gi0, gj0, inv_lam);
-
-    if (!final_step) {
-        for (int e = tid; e < NIMG * TB * TB; e += kTvThreads) {
-            const int im = e / (TB * TB), c = e - im * (TB * TB);
-            const int a = H + c / TB, b = H + (c & (TB - 1));
-            const int gi = gi0 + a, gj = gj0 + b;
-            if (gi >= n || gj >= n) continue;
-            const int idx = im * RR + a * R + b;
-            pout[im * N + (size_t)gi * n + gj] = make_float2(spx[idx], spy[idx]);
-        }
-        return;
-    }
-
-    // ---- final: x = r - lambda div p on the tile, staging, divergence ----
-    __shared__ double red[32];
-    __shared__ bool am_last;
-    const unsigned t = F.t_arg > 0 ? (unsigned)F.t_arg : S->t;
-    double acc = 0.0;
-    float* tile = sq;                  // [TB][TB+1] staging tile for the transposed copy
-    {
-        const int ta = tid >> 5, tb = tid & 31;     // one tile pixel per thread
-        const int a = H + ta, b = H + tb;
-        const int gi = gi0 + a, gj = gj0 + b;
-        float xv = 0.f;
-        if (gi < n && gj < n) {
-            float xs[NIMG];
-#pragma unroll
-            for (int im = 0; im < NIMG; ++im) {
-                const int idx = im * RR + a * R + b;
-                const float dv = spx[idx] - spx[idx - 1] + spy[idx] - spy[idx - R];
-                xs[im] = sr[idx] - lam * dv;
-            }
-            const size_t o = (size_t)gi * n + gj;
-            xv = xs[0];
-            if (NIMG == 2) {
-                const float4 b4 = probe4((unsigned)(o >> 2), t, F.slice, F.key);
-                const int kk = (int)(o & 3);
-                const float bv = kk == 0 ? b4.x : (kk == 1 ? b4.y : (kk == 2 ? b4.z : b4.w));
-                acc += (double)bv * (double)(xs[NIMG - 1] - xs[0]);
-            }
-            if (F.solve_mode && F.damp_x != 1.f) xv = F.damp_x * xv + (1.f - F.damp_x) * F.x_out[o];
-            F.x_out[o] = xv;
-            if (F.XR) F.XR[(size_t)gi * F.ldp + kPad + gj] = xv;
-        }
-        tile[ta * (TB + 1) + tb] = xv;
-    }
-    if (F.XC) {
-        __syncthreads();
-        const int ta = tid >> 5, tb = tid & 31;     // ta: tile column, tb: tile row
-        const int gj = gj0 + H + ta, gi = gi0 + H + tb;
-        if (gi < n && gj < n) F.XC[(size_t)gj * F.ldp + kPad + gi] = tile[tb * (TB + 1) + ta];
-    }
-    if (NIMG < 2) return;
     acc = block_sum(acc, red);
-    const int nblk = gridDim.x * gridDim.y;
-    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (tid == 0) {
         F.partial[bid] = acc;
         __threadfence();
         const unsigned prev = atomicAdd(&S->done_div, 1u);
-        am_last = (prev == (unsigned)nblk - 1);
+        *am_last = (prev == (unsigned)nblk - 1);
     }
     __syncthreads();
-    if (!am_last) return;
+    if (!*am_last) return;
     __threadfence();
     double tot = 0.0;
-    for (int b = tid; b < nblk; b += kTvThreads) tot += ((volatile double*)F.partial)[b];
+    for (int b = tid; b < nblk; b += blockDim.x) tot += ((volatile double*)F.partial)[b];
     tot = block_sum(tot, red);
     if (tid == 0) {
         const double div = tot / ((double)N * S->eps);
@@ -290,40 +226,207 @@ k_tv_block(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
     }
 }
 
-// Steps per launch the autotuner may choose.
+// KB Chambolle steps of image blockIdx.z (of nimg) from the duals pin (zero
+// when first).  Not FINAL: the region minus KB pixels per side goes to pout.
+// FINAL: x = r - lambda div p on the region minus KB + 1 pixels at the top
+// and left (div p reads the left and upper neighbours) and KB at the bottom
+// and right; image 0's x (damped in a solve) to x_out and the staged
+// copies; for nimg = 2 the divergence b^T (x_1 - x_0) / (N eps), summed as
+// +b^T x_1 and -b^T x_0 over the blocks of the two images.
+template <int WY, int KB, bool FINAL>
+__global__ void __launch_bounds__(32 * WY)
+k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout, int n,
+           int first, float c_tv, int from_scalars, float lambda_arg, DevScalars* S,
+           const float* __restrict__ bprobe, TvFinal F) {
+    constexpr int U = kTvU, V = kTvV, RW = kTvRW, RH = V * WY;
+    constexpr int E = FINAL ? KB + 1 : KB;      // top/left margin of the tile
+    constexpr int TW = RW - KB - E, TH = RH - KB - E;
+    __shared__ float e_py[WY][U][32];
+    __shared__ float e_q[WY][U][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t N = (size_t)n * n;
+    const int im = (int)blockIdx.z;
+    const size_t img = (size_t)im * N;
+    const int gi0 = (int)blockIdx.y * TH - E, gj0 = (int)blockIdx.x * TW - E;
+    const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
+    const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
+    float px[V][U], py[V][U], rl[V][U];
+    unsigned inside = 0u, lastc = 0u, lastr = 0u;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int gi = gi0 + w * V + v;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int gj = gj0 + 32 * u + lane;
+            const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
+            float rv = 0.f;
+            float2 p = make_float2(0.f, 0.f);
+            if (in) {
+                const size_t o = img + (size_t)gi * n + gj;
+                rv = rbase[o];
+                if (!first) p = pin[o];
+            }
+            rl[v][u] = rv * inv_lam;
+            px[v][u] = p.x;
+            py[v][u] = p.y;
+            const unsigned bit = 1u << (v * U + u);
+            if (in) inside |= bit;
+            if (gj == n - 1) lastc |= bit;
+            if (gi == n - 1) lastr |= bit;
+        }
+    }
+    const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + RH < n && gj0 + RW < n;
+    if (interior)
+        tv_region_steps<WY, KB, false>(px, py, rl, inside, lastc, lastr, e_py, e_q);
+    else
+        tv_region_steps<WY, KB, true>(px, py, rl, inside, lastc, lastr, e_py, e_q);
+    if (!FINAL) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int rr = w * V + v;
+            if (rr < KB || rr >= RH - KB) continue;
+            const int gi = gi0 + rr;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int cc = 32 * u + lane;
+                const int gj = gj0 + cc;
+                if (cc < KB || cc >= RW - KB || gi >= n || gj >= n) continue;
+                pout[img + (size_t)gi * n + gj] = make_float2(px[v][u], py[v][u]);
+            }
+        }
+        return;
+    }
+    // ---- final: x = r - lambda div p (e_py holds the last rows' py) ----
+    __shared__ double red[32];
+    __shared__ bool am_last;
+    const int nimg = (int)gridDim.z;
+    double acc = 0.0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int rr = w * V + v;
+        const int gi = gi0 + rr;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float send = lane == 31 ? (u > 0 ? px[v][u - 1] : 0.f) : px[v][u];
+            const float pxl = __shfl_sync(0xffffffffu, send, (lane + 31) & 31);
+            const float pyu = v > 0 ? py[v - 1][u] : (w > 0 ? e_py[w - 1][u][lane] : 0.f);
+            const int cc = 32 * u + lane;
+            const int gj = gj0 + cc;
+            if (rr < E || rr >= RH - KB || cc < E || cc >= RW - KB || gi >= n || gj >= n) continue;
+            const size_t o = (size_t)gi * n + gj;
+            const float dv = px[v][u] - pxl + py[v][u] - pyu;
+            const float xv = rbase[img + o] - lam * dv;
+            if (nimg == 2) acc += (double)bprobe[o] * (double)(im == 1 ? xv : -xv);
+            if (im == 0) {
+                float xo = xv;
+                if (F.solve_mode && F.damp_x != 1.f) xo = F.damp_x * xo + (1.f - F.damp_x) * F.x_out[o];
+                F.x_out[o] = xo;
+                if (F.XR) F.XR[(size_t)gi * F.ldp + kPad + gj] = xo;
+                if (F.XC) F.XC[(size_t)gj * F.ldp + kPad + gi] = xo;
+            }
+        }
+    }
+    if (nimg < 2) return;
+    const int nblk = (int)(gridDim.x * gridDim.y * gridDim.z);
+    const int bid = (int)((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+    tv_divergence_finish(acc, nblk, bid, N, S, F, red, &am_last);
+}
+
+// Final step: x = r - lambda div p for NIMG images (p = 0 when pfin is NULL),
+// x of image 0 (damped in a solve) to x_out and the staged copies, and for
+// NIMG = 2 the divergence b^T (x_1 - x_0) / (N eps) (b as k_probe_input
+// stored it) and, in a solve, tau_x.  32 x 32 pixel tiles, one pixel per thread.
+template <int NIMG>
+__global__ void __launch_bounds__(1024)
+k_tv_final(const float* __restrict__ rbase, const float2* __restrict__ pfin, const float* __restrict__ bprobe, int n,
+           float c_tv, int from_scalars, float lambda_arg, DevScalars* S, TvFinal F) {
+    __shared__ float tile[TB][TB + 1];
+    __shared__ double red[32];
+    __shared__ bool am_last;
+    const size_t N = (size_t)n * n;
+    const int tid = threadIdx.x, ta = tid >> 5, tb = tid & 31;
+    const int gi = blockIdx.y * TB + ta, gj = blockIdx.x * TB + tb;
+    const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
+    double acc = 0.0;
+    float xv = 0.f;
+    if (gi < n && gj < n) {
+        const size_t o = (size_t)gi * n + gj;
+        float xs[NIMG];
+#pragma unroll
+        for (int im = 0; im < NIMG; ++im) {
+            float dv = 0.f;
+            if (pfin) {
+                const float2* p = pfin + im * N;
+                const float2 pc = p[o];
+                const float pxl = gj > 0 ? p[o - 1].x : 0.f;
+                const float pyu = gi > 0 ? p[o - n].y : 0.f;
+                dv = pc.x - pxl + pc.y - pyu;
+            }
+            xs[im] = rbase[im * N + o] - lam * dv;
+        }
+        xv = xs[0];
+        if (NIMG == 2) acc = (double)bprobe[o] * (double)(xs[NIMG - 1] - xs[0]);
+        if (F.solve_mode && F.damp_x != 1.f) xv = F.damp_x * xv + (1.f - F.damp_x) * F.x_out[o];
+        F.x_out[o] = xv;
+        if (F.XR) F.XR[(size_t)gi * F.ldp + kPad + gj] = xv;
+    }
+    tile[ta][tb] = xv;
+    if (F.XC) {
+        __syncthreads();
+        const int gj2 = blockIdx.x * TB + ta, gi2 = blockIdx.y * TB + tb;
+        if (gi2 < n && gj2 < n) F.XC[(size_t)gj2 * F.ldp + kPad + gi2] = tile[tb][ta];
+    }
+    if (NIMG < 2) return;
+    tv_divergence_finish(acc, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x, N, S, F, red, &am_last);
+}
+
+// Steps per launch and region heights the autotuner may choose.
 static const int kTvKbChoices[] = {3, 4, 5, 6, 8, 10};
+static const int kTvRowChoices[] = {32, 64, 128};
 
 bool tv_active(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg) {
     if (pl->opt.k_tv <= 0) return false;
     return from_scalars ? pl->opt.c_tv > 0.0 : lambda_arg > 0.0;
 }
 
-int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg) {
-    if (!tv_active(pl, from_scalars, lambda_arg)) return 1;
+static int tv_step_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg) {
+    if (!tv_active(pl, from_scalars, lambda_arg)) return 0;
     return (pl->opt.k_tv + pl->tv_kb - 1) / pl->tv_kb;
 }
 
-static constexpr size_t tv_smem_bytes(int nimg, int kb) {
-    const int R = TB + 2 * (kb + 1);
-    return (size_t)4 * nimg * R * R * sizeof(float);
+// the step launches, the last of them forming x (or one final launch when
+// the denoiser is the identity: no steps or lambda = 0)
+int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg) {
+    const int ns = tv_step_launches(pl, from_scalars, lambda_arg);
+    return ns > 0 ? ns : 1;
 }
 
-template <int NIMG, int KB>
-static void launch_kb(dim3 grd, cudaStream_t st, const float* r, const float2* pin, float2* pout, int n,
-                      int first, int fin, float c_tv, int fs, float lam, DevScalars* S, const TvFinal& F) {
-    k_tv_block<NIMG, KB><<<grd, kTvThreads, tv_smem_bytes(NIMG, KB), st>>>(r, pin, pout, n, first, fin, c_tv,
-                                                                           fs, lam, S, F);
+struct TvLaunch {
+    int n, nimg, first;
+    const float* r;
+    const float2* pin;
+    float2* pout;
+    float c_tv, lam;
+    int fs;
+    DevScalars* S;
+    const float* b;
+};
+
+template <int WY, int KB, bool FIN>
+static void launch_steps_kb(const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
+    constexpr int E = FIN ? KB + 1 : KB;
+    constexpr int TW = kTvRW - KB - E, TH = kTvV * WY - KB - E;
+    dim3 grd((L.n + TW - 1) / TW, (L.n + TH - 1) / TH, L.nimg);
+    k_tv_steps<WY, KB, FIN><<<grd, 32 * WY, 0, st>>>(L.r, L.pin, L.pout, L.n, L.first, L.c_tv, L.fs, L.lam, L.S,
+                                                     L.b, F);
 }
 
-// One launch running exactly `steps` Chambolle steps (0..kTvMaxKb).
-template <int NIMG>
-static int launch_dispatch(int steps, dim3 grd, cudaStream_t st, const float* r, const float2* pin,
-                           float2* pout, int n, int first, int fin, float c_tv, int fs, float lam,
-                           DevScalars* S, const TvFinal& F) {
+template <int WY, bool FIN>
+static int launch_steps_wy(int steps, const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
 #define DGCT_TV_CASE(KB) \
-    case KB: launch_kb<NIMG, KB>(grd, st, r, pin, pout, n, first, fin, c_tv, fs, lam, S, F); break;
+    case KB: launch_steps_kb<WY, KB, FIN>(L, st, F); break;
     switch (steps) {
-        DGCT_TV_CASE(0) DGCT_TV_CASE(1) DGCT_TV_CASE(2) DGCT_TV_CASE(3) DGCT_TV_CASE(4) DGCT_TV_CASE(5)
+        DGCT_TV_CASE(1) DGCT_TV_CASE(2) DGCT_TV_CASE(3) DGCT_TV_CASE(4) DGCT_TV_CASE(5)
         DGCT_TV_CASE(6) DGCT_TV_CASE(7) DGCT_TV_CASE(8) DGCT_TV_CASE(9) DGCT_TV_CASE(10)
         default: return DGAMP_CT_ERR_INVALID_ARG;
     }
@@ -332,20 +435,22 @@ static int launch_dispatch(int steps, dim3 grd, cudaStream_t st, const float* r,
     return DGAMP_CT_OK;
 }
 
-// Launch i (0-based) of the blocked denoiser on nimg images of ws.r; the last
-// launch (i = tv_num_launches - 1) performs the final step.
+template <bool FIN>
+static int launch_steps(int rows, int steps, const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
+    if (rows == 128) return launch_steps_wy<32, FIN>(steps, L, st, F);
+    if (rows == 32) return launch_steps_wy<8, FIN>(steps, L, st, F);
+    return launch_steps_wy<16, FIN>(steps, L, st, F);
+}
+
+// Launch i (0-based) of the denoiser on nimg images of ws.r.
 int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
                     float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st) {
     const int n = pl->n;
     const size_t N = (size_t)pl->N;
     const int KB = pl->tv_kb;
-    const bool active = tv_active(pl, from_scalars, lambda_arg);
-    const int nl = tv_num_launches(pl, from_scalars, lambda_arg);
-    const int K = active ? pl->opt.k_tv : 0;
-    const int iters = active ? ((i + 1) * KB <= K ? KB : K - i * KB) : 0;
+    const int ns = tv_step_launches(pl, from_scalars, lambda_arg);
     float2* buf[2] = {pl->ws.p, pl->ws.p + 2 * N};
-    const float2* pin = buf[(i + 1) & 1];
-    float2* pout = buf[i & 1];
+    const float c_tv = (float)pl->opt.c_tv, lam = (float)lambda_arg;
     TvFinal F;
     F.x_out = x_out;
     F.XR = solve_mode ? pl->ws.XR : nullptr;
@@ -361,13 +466,22 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     F.div_out = div_out;
     F.solve_mode = solve_mode;
     F.jvp = 0;
-    dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
-    const float c_tv = (float)pl->opt.c_tv, lam = (float)lambda_arg;
-    if (nimg == 2)
-        return launch_dispatch<2>(iters, grd, st, pl->ws.r, pin, pout, n, i == 0, i == nl - 1, c_tv,
-                                  from_scalars, lam, pl->ws.S, F);
-    return launch_dispatch<1>(iters, grd, st, pl->ws.r, pin, pout, n, i == 0, i == nl - 1, c_tv,
-                              from_scalars, lam, pl->ws.S, F);
+    if (ns == 0) {   // identity denoiser: x = r
+        dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
+        if (nimg == 2)
+            k_tv_final<2><<<grd, 1024, 0, st>>>(pl->ws.r, nullptr, pl->ws.b, n, c_tv, from_scalars, lam, pl->ws.S,
+                                                F);
+        else
+            k_tv_final<1><<<grd, 1024, 0, st>>>(pl->ws.r, nullptr, pl->ws.b, n, c_tv, from_scalars, lam, pl->ws.S,
+                                                F);
+        DGCT_LAUNCH_CHECK();
+        return DGAMP_CT_OK;
+    }
+    const int steps = (i + 1) * KB <= pl->opt.k_tv ? KB : pl->opt.k_tv - i * KB;
+    TvLaunch L{n, nimg, i == 0, pl->ws.r, buf[(i + 1) & 1], buf[i & 1], c_tv, lam, from_scalars, pl->ws.S,
+               pl->ws.b};
+    if (i == ns - 1) return launch_steps<true>(pl->tv_rows, steps, L, st, F);
+    return launch_steps<false>(pl->tv_rows, steps, L, st, F);
 }
 
 // The whole denoiser (and, for nimg = 2, the divergence): tv_num_launches launches.
@@ -382,22 +496,13 @@ int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lamb
     return DGAMP_CT_OK;
 }
 
-template <int NIMG, int KB>
-static int set_attr_range() {
-    DGCT_CUDA(cudaFuncSetAttribute(k_tv_block<NIMG, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)tv_smem_bytes(NIMG, KB)));
-    if constexpr (KB > 0) return set_attr_range<NIMG, KB - 1>();
-    return DGAMP_CT_OK;
-}
+// Shared memory is static (at most 16 KiB): nothing to raise.
+int tv_set_smem_limits() { return DGAMP_CT_OK; }
 
-int tv_set_smem_limits() {
-    const int rc = set_attr_range<1, kTvMaxKb>();
-    return rc != DGAMP_CT_OK ? rc : set_attr_range<2, kTvMaxKb>();
-}
-
-// Plan-time choice of the steps per launch: time the two-image denoiser of
-// the plan's geometry (K = opt.k_tv) for every choice and keep the fastest.
-// Runs on zeroed workspace; the timing does not depend on the values.
+// Plan-time choice of the steps per launch and the region height: time the
+// two-image denoiser of the plan's geometry (K = opt.k_tv) for every pair
+// and keep the fastest.  Runs on zeroed workspace; the timing does not
+// depend on the values.
 int tv_autotune(dgamp_ct_plan_s* pl) {
     if (pl->opt.k_tv <= 0) return DGAMP_CT_OK;
     const size_t N = (size_t)pl->N;
@@ -407,28 +512,36 @@ int tv_autotune(dgamp_ct_plan_s* pl) {
     DGCT_CUDA(cudaEventCreate(&e0));
     DGCT_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_kb = pl->tv_kb;
-    for (int kb : kTvKbChoices) {
-        pl->tv_kb = kb;
-        int rc = DGAMP_CT_OK;
-        for (int rep = 0; rep < 4 && rc == DGAMP_CT_OK; ++rep) {      // first rep warms up
-            if (rep == 1) cudaEventRecord(e0, 0);
-            rc = launch_tv(pl, 2, 0, 1.0, pl->ws.x, 0, 1, nullptr, 0);
+    int best_kb = pl->tv_kb, best_rows = pl->tv_rows;
+    for (int rows : kTvRowChoices) {
+        for (int kb : kTvKbChoices) {
+            pl->tv_kb = kb;
+            pl->tv_rows = rows;
+            int rc = DGAMP_CT_OK;
+            for (int rep = 0; rep < 4 && rc == DGAMP_CT_OK; ++rep) {      // first rep warms up
+                if (rep == 1) cudaEventRecord(e0, 0);
+                rc = launch_tv(pl, 2, 0, 1.0, pl->ws.x, 0, 1, nullptr, 0);
+            }
+            cudaEventRecord(e1, 0);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (rc != DGAMP_CT_OK || e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return rc != DGAMP_CT_OK ? rc : cuda_fail(e);
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_kb = kb;
+                best_rows = rows;
+            }
         }
-        cudaEventRecord(e1, 0);
-        cudaError_t e = cudaEventSynchronize(e1);
-        if (rc != DGAMP_CT_OK || e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return rc != DGAMP_CT_OK ? rc : cuda_fail(e);
-        }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; best_kb = kb; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     pl->tv_kb = best_kb;
+    pl->tv_rows = best_rows;
     return DGAMP_CT_OK;
 }
 
@@ -439,23 +552,19 @@ int tv_autotune(dgamp_ct_plan_s* pl) {
 // D' = b^T (dn[1] - dn[0]) / (N eps).  32 x 32 tiles as in the blocked TV's
 // final launch.
 __global__ void __launch_bounds__(1024)
-k_denoise_final(const float* __restrict__ dn, int n, DevScalars* S, TvFinal F) {
+k_denoise_final(const float* __restrict__ dn, const float* __restrict__ bprobe, int n, DevScalars* S, TvFinal F) {
     __shared__ float tile[TB][TB + 1];
     __shared__ double red[32];
     __shared__ bool am_last;
     const size_t N = (size_t)n * n;
     const int tid = threadIdx.x, ta = tid >> 5, tb = tid & 31;
     const int gi = blockIdx.y * TB + ta, gj = blockIdx.x * TB + tb;
-    const unsigned t = F.t_arg > 0 ? (unsigned)F.t_arg : S->t;
     double acc = 0.0;
     float xv = 0.f;
     if (gi < n && gj < n) {
         const size_t o = (size_t)gi * n + gj;
         const float x1 = dn[o], x2 = dn[N + o];
-        const float4 b4 = probe4((unsigned)(o >> 2), t, F.slice, F.key);
-        const int kk = (int)(o & 3);
-        const float bv = kk == 0 ? b4.x : (kk == 1 ? b4.y : (kk == 2 ? b4.z : b4.w));
-        acc = (double)bv * (double)(F.jvp ? x2 : x2 - x1);
+        acc = (double)bprobe[o] * (double)(F.jvp ? x2 : x2 - x1);
         xv = x1;
         if (F.solve_mode && F.damp_x != 1.f) xv = F.damp_x * xv + (1.f - F.damp_x) * F.x_out[o];
         F.x_out[o] = xv;
@@ -525,7 +634,7 @@ int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_ou
     F.jvp = 1;
     const int n = pl->n;
     dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
-    k_denoise_final<<<grd, 1024, 0, st>>>(dn, n, pl->ws.S, F);
+    k_denoise_final<<<grd, 1024, 0, st>>>(dn, pl->ws.b, n, pl->ws.S, F);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }

@@ -162,12 +162,13 @@ def test_truncated_output_step_matches_oracle(dg):
     assert ts == pytest.approx(np.mean(tsi_ref), rel=1e-5)
 
 
+@pytest.mark.parametrize("rows", [32, 64, 128])             # region height of a TV block
 @pytest.mark.parametrize("kb", [1, 3, 7, 10])           # steps per blocked launch (remainders too)
-@pytest.mark.parametrize("n,lam", [(64, 0.3), (77, 0.05), (33, 0.0), (130, 0.2)])
-def test_tv_matches_oracle(dg, n, lam, kb):
+@pytest.mark.parametrize("n,lam", [(64, 0.3), (77, 0.05), (33, 0.0), (130, 0.2), (300, 0.1)])
+def test_tv_matches_oracle(dg, n, lam, kb, rows):
     r = np.cumsum(np.random.default_rng(8).standard_normal((n, n)), axis=1) * 0.1
     with dg.Plan(n, 10, 2 * n, k_tv=20) as pl:
-        pl.set_tuning(tv_kb=kb)
+        pl.set_tuning(tv_kb=kb, tv_rows=rows)
         x = host(pl.denoise_tv(cu(r), lam))
     assert rel(x, tv.tv_prox(r, lam, 20)) < 1e-5
 
