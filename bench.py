@@ -46,6 +46,11 @@ UNIT = "iters/s"
 WORKLOAD = "ellipse512_v64"
 TV = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the blocked-TV
+# launches of one iteration, from the ncu capture summarised in
+# profiles/tv_blocked_ellipse512_v64.md, valid only for the configuration
+# profiled there (steps per launch, region rows) and the current kernel.
+TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 32, "bytes_per_iteration": 2120960 + 8430592}
 
 
 # ----------------------------------------------------------------- helpers --
@@ -436,14 +441,20 @@ def run_gpu(args):
     # x K_TV steps x 2 images x N, plus 5 per pixel and image for x = r - lambda div p.
     # Peak = 152 SMs x 128 FP32 lanes x 2 FLOP x the median SM clock sampled here.
     tv_launches = [k for k in prof if k.startswith("tv_block")]
+    tun = plan.tuning()
+    traffic = (TV_TRAFFIC["bytes_per_iteration"]
+               if (tun["tv_kb"], tun["tv_rows"]) == (TV_TRAFFIC["tv_kb"], TV_TRAFFIC["tv_rows"]) else None)
     tv_flop = (19.0 * TV["k_tv"] * 2 + 5.0 * 2) * N
     clk_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
     tv_tflops = tv_flop / (tv_ms * 1e-3) / 1e12
     tv_bytes = sum(algo[k] for k in tv_launches)
-    roof = {"kernel": f"k_tv_block ({len(tv_launches)} launches per iteration)", "bound": "alu",
+    roof = {"kernel": f"k_tv_steps ({len(tv_launches)} launches per iteration, KB={tun['tv_kb']}, "
+                                f"{tun['tv_rows']} region rows)", "bound": "alu",
             "achieved": tv_tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tv_tflops / alu_peak,
-            "traffic": None,
+            "traffic": traffic,
+            "traffic_note": "DRAM bytes of the TV launches of one iteration (ncu, cold cache), null unless the "
+                            "plan chose the profiled configuration",
             "peak_kind": f"FP32 FMA issue peak at the sampled median SM clock ({clk_mhz:.0f} MHz), derived",
             "algorithmic_flop_per_iteration": tv_flop, "launch_ms_per_iteration": tv_ms,
             "hbm_view": {"algorithmic_bytes_per_iteration": tv_bytes,
