@@ -13,13 +13,11 @@
 // a forward convolution of the output gradient with the flipped, transposed
 // kernel.
 //
-// The 64 -> 64 layers are implicit GEMMs on the tensor cores (mma.sync
-// m16n8k16, BF16 in, FP32 accumulate): a block keeps the whole 64 x 576
-// weight matrix in shared memory, walks 8 x 16-pixel tiles of the batch, and
-// for each tile stages the 10 x 18-pixel input window; each warp owns two
-// 16-pixel rows of the tile and all 64 output channels.  The weight gradient
-// (M = 64 co, N = 64 ci per tap, K = pixels) writes per-block FP32 partials
-// that a second kernel adds in a fixed order.  The first (1 -> 64) and last
+// The 64 -> 64 layers (forward, input gradient and forward-mode tangent) are
+// implicit GEMMs on the tcgen05 tensor cores with TMEM accumulators
+// (conv_tc.cu).  The weight gradient (M = 64 co, N = 64 ci per tap, K =
+// pixels, mma.sync m16n8k16 BF16) writes per-block FP32 partials that a
+// second kernel adds in a fixed order.  The first (1 -> 64) and last
 // (64 -> 1) layers are small and run on the CUDA cores.
 #include <cuda_bf16.h>
 
@@ -34,10 +32,8 @@ namespace dgct {
 
 constexpr int CH = 64;          // hidden channels
 constexpr int KW = 9 * CH;      // GEMM K of a hidden layer (576)
-constexpr int TH = 8, TWD = 16; // pixel tile of the tensor-core kernels (128 pixels)
-constexpr int HALO_H = TH + 2, HALO_W = TWD + 2;
+constexpr int TH = 8, TWD = 16; // pixel tile of the weight-gradient kernel (128 pixels)
 constexpr int PSTR = 72;        // shared-memory stride (bf16) of one pixel's 64 channels
-constexpr int WSTR = KW + 8;    // shared-memory stride (bf16) of one weight row
 constexpr int CONV_THREADS = 128;
 
 typedef __nv_bfloat16 bf16;
@@ -111,103 +107,13 @@ __global__ void k_conv_first(const float* __restrict__ r, const float* __restric
 }
 
 // ------------------------------------------------------ hidden 64 -> 64 --
-// MODE 0 (forward):  out = relu(bias + conv(in, Wk)), Wk = [co][tap*64 + ci].
-// MODE 1 (masked linear): out = conv(in, Wk) * (mask > 0).  With Wk = the
-// flipped/transposed kernel, `in` = the output gradient and mask = this
-// layer's input activation it is the input gradient; with Wk = the forward
-// kernel, `in` = a tangent and mask = the primal output activation of this
-// layer it is the forward-mode derivative.
-template <int MODE>
-__global__ void __launch_bounds__(CONV_THREADS)
-k_conv64(const bf16* __restrict__ in, const bf16* __restrict__ wk, const float* __restrict__ bias,
-         const bf16* __restrict__ mask, bf16* __restrict__ out, int B, int H, int W) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    bf16* sw = reinterpret_cast<bf16*>(smraw);                  // [64][WSTR]
-    bf16* st = sw + CH * WSTR;                                  // [HALO_H*HALO_W][PSTR]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // weights: 64 rows x 576 bf16, 16-byte chunks
-    for (int i = tid; i < CH * (KW / 8); i += CONV_THREADS) {
-        const int row = i / (KW / 8), c = i - row * (KW / 8);
-        *reinterpret_cast<uint4*>(sw + row * WSTR + c * 8) = *reinterpret_cast<const uint4*>(wk + row * KW + c * 8);
-    }
-    const int tiles_x = (W + TWD - 1) / TWD, tiles_y = (H + TH - 1) / TH;
-    const int ntiles = B * tiles_x * tiles_y;
-    const int q = lane >> 3, j = lane & 7;
-    const int gid = lane >> 2, tig = lane & 3;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int b = tile / (tiles_x * tiles_y);
-        const int rem = tile - b * tiles_x * tiles_y;
-        const int y0 = (rem / tiles_x) * TH, x0 = (rem - (rem / tiles_x) * tiles_x) * TWD;
-        __syncthreads();   // previous tile's reads of st are done (and weights are in place)
-        for (int i = tid; i < HALO_H * HALO_W * 8; i += CONV_THREADS) {
-            const int pix = i >> 3, c = i & 7;
-            const int yy = y0 - 1 + pix / HALO_W, xx = x0 - 1 + pix % HALO_W;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                v = *reinterpret_cast<const uint4*>(in + (((long long)b * H + yy) * W + xx) * CH + c * 8);
-            *reinterpret_cast<uint4*>(st + pix * PSTR + c * 8) = v;
-        }
-        __syncthreads();
-        float acc[2][8][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
-#pragma unroll 1
-        for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap % 3;           // window offsets (0..2) in the halo tile
-#pragma unroll
-            for (int kc = 0; kc < 4; ++kc) {
-                uint32_t a[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int trow = 2 * warp + mt;          // tile row of this m-tile
-                    const int tcol = j + 8 * (q & 1);        // A row = tile column
-                    const bf16* p = st + ((trow + dy) * HALO_W + tcol + dx) * PSTR + kc * 16 + 8 * (q >> 1);
-                    ldsm_x4(a[mt][0], a[mt][1], a[mt][2], a[mt][3], p);
-                }
-#pragma unroll
-                for (int np = 0; np < 4; ++np) {
-                    uint32_t b0, b1, b2, b3;
-                    const bf16* p = sw + (np * 16 + j + 8 * (q >> 1)) * WSTR + tap * CH + kc * 16 + 8 * (q & 1);
-                    ldsm_x4(b0, b1, b2, b3, p);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-                        mma16816(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
-                        mma16816(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
-                    }
-                }
-            }
-        }
-        // epilogue
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int y = y0 + 2 * warp + mt;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int x = x0 + gid + 8 * h;
-                if (y >= H || x >= W) continue;
-                const long long o = (((long long)b * H + y) * W + x) * CH;
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const int co = nt * 8 + 2 * tig;
-                    float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
-                    if (MODE == 0) {
-                        v0 = fmaxf(v0 + bias[co], 0.f);
-                        v1 = fmaxf(v1 + bias[co + 1], 0.f);
-                    } else {
-                        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + o + co);
-                        if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
-                        if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
-                    }
-                    *reinterpret_cast<__nv_bfloat162*>(out + o + co) = __floats2bfloat162_rn(v0, v1);
-                }
-            }
-        }
-    }
-}
+// On the tcgen05 tensor cores, conv_tc.cu (launch_conv64_tc): mode 0 is the
+// forward layer relu(bias + conv(in, Wk)); mode 1 the masked linear layer
+// conv(in, Wk) * (mask > 0).  With Wk = the flipped/transposed kernel, `in`
+// = the output gradient and mask = this layer's input activation, mode 1 is
+// the input gradient; with Wk = the forward kernel, `in` = a tangent and mask
+// = the primal output activation of this layer, it is the forward-mode
+// derivative.
 
 // ------------------------------------------------------------ last layer --
 // f = b16 + conv(a16, W16) (W16 as [tap][ci]); D = r - sigma f.  b16 == nullptr
@@ -543,7 +449,8 @@ struct dgamp_ct_cnn_s {
     double* loss = nullptr;
     float* sig_buf = nullptr;   // per-image sigma (device) [cap_batch]
     int cap_batch = 0;
-    int conv_grid = 0;
+    int sm_count = 0;           // persistent grid of the tensor-core convolutions
+    unsigned* tc_err = nullptr; // set by a tensor-core convolution whose bounded wait timed out
     uint64_t ws_gen = 0;        // bumped whenever the workspace is reallocated
 };
 
@@ -589,7 +496,6 @@ static int cnn_ensure_ws(dgamp_ct_cnn_s* c, int64_t npix, int nstore, int batch)
     return DGAMP_CT_OK;
 }
 
-static size_t conv_smem() { return (size_t)(CH * WSTR + HALO_H * HALO_W * PSTR) * sizeof(bf16); }
 
 static int cnn_pack(dgamp_ct_cnn_s* c, cudaStream_t st) {
     const long long tot = (long long)(c->L - 2) * 9 * CH * CH + 18 * CH;
@@ -612,13 +518,9 @@ static int cnn_forward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int 
     const unsigned blocks = (unsigned)((npix + 127) / 128);
     k_conv_first<<<blocks, 128, 0, st>>>(r, sig, B, H, W, c->w0, c->master + c->b_off[0], nullptr, act(1), nullptr);
     DGCT_LAUNCH_CHECK();
-    const int tiles = B * ((W + TWD - 1) / TWD) * ((H + TH - 1) / TH);
-    const int grid = tiles < c->conv_grid ? tiles : c->conv_grid;
-    for (int l = 1; l <= L - 2; ++l) {
-        k_conv64<0><<<grid, CONV_THREADS, conv_smem(), st>>>(act(l), c->wh + (size_t)(l - 1) * CH * KW,
-                                                             c->master + c->b_off[l], nullptr, act(l + 1), B, H, W);
-        DGCT_LAUNCH_CHECK();
-    }
+    for (int l = 1; l <= L - 2; ++l)
+        DGCT_TRY(launch_conv64_tc(0, act(l), c->wh, L - 2, l - 1, c->master + c->b_off[l], nullptr, act(l + 1), B, H,
+                                  W, c->sm_count, c->tc_err, st));
     k_conv_last<<<blocks, 128, 0, st>>>(act(L - 1), c->w16, c->master + c->b_off[L - 1], r, sig, B, H, W, c->f, d_out);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
@@ -645,8 +547,6 @@ static int cnn_backward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int
     bf16* gnext = c->g1;
     k_dgrad_last<<<blocks, 128, 0, st>>>(c->gout, c->w16, act(L - 1), gcur, B, H, W);
     DGCT_LAUNCH_CHECK();
-    const int tiles = B * ((W + TWD - 1) / TWD) * ((H + TH - 1) / TH);
-    const int grid = tiles < c->conv_grid ? tiles : c->conv_grid;
     for (int l = L - 2; l >= 1; --l) {
         // layer l maps a_l -> z_{l+1}; gcur = dL/dz_{l+1}
         k_wgrad64<<<dim3(G, 9), CONV_THREADS, 0, st>>>(act(l), gcur, B, H, W, G, c->partial);
@@ -657,9 +557,8 @@ static int cnn_backward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int
         DGCT_LAUNCH_CHECK();
         k_reduce_rows<<<1, 64, 0, st>>>(c->partial, G, CH, c->grad + c->b_off[l]);
         DGCT_LAUNCH_CHECK();
-        k_conv64<1><<<grid, CONV_THREADS, conv_smem(), st>>>(gcur, c->wt + (size_t)(l - 1) * CH * KW, nullptr, act(l),
-                                                             gnext, B, H, W);
-        DGCT_LAUNCH_CHECK();
+        DGCT_TRY(launch_conv64_tc(1, gcur, c->wt, L - 2, l - 1, nullptr, act(l), gnext, B, H, W, c->sm_count,
+                                  c->tc_err, st));
         bf16* t = gcur;
         gcur = gnext;
         gnext = t;
@@ -710,16 +609,11 @@ static int jvp_passes(dgamp_ct_cnn_s* c, const float* r, const float* b, int H, 
     DGCT_LAUNCH_CHECK();
     k_conv_first<<<blocks, 128, 0, st>>>(b, c->sig_buf, 1, H, W, c->w0, nullptr, prim(1), tang(1), nullptr);
     DGCT_LAUNCH_CHECK();
-    const int tiles = ((W + TWD - 1) / TWD) * ((H + TH - 1) / TH);
-    const int grid = tiles < c->conv_grid ? tiles : c->conv_grid;
     for (int l = 1; l <= L - 2; ++l) {
-        const bf16* wl = c->wh + (size_t)(l - 1) * CH * KW;
-        k_conv64<0><<<grid, CONV_THREADS, conv_smem(), st>>>(prim(l), wl, c->master + c->b_off[l], nullptr,
-                                                             prim(l + 1), 1, H, W);
-        DGCT_LAUNCH_CHECK();
-        k_conv64<1><<<grid, CONV_THREADS, conv_smem(), st>>>(tang(l), wl, nullptr, prim(l + 1), tang(l + 1), 1, H,
-                                                             W);
-        DGCT_LAUNCH_CHECK();
+        DGCT_TRY(launch_conv64_tc(0, prim(l), c->wh, L - 2, l - 1, c->master + c->b_off[l], nullptr, prim(l + 1), 1,
+                                  H, W, c->sm_count, c->tc_err, st));
+        DGCT_TRY(launch_conv64_tc(1, tang(l), c->wh, L - 2, l - 1, nullptr, prim(l + 1), tang(l + 1), 1, H, W,
+                                  c->sm_count, c->tc_err, st));
     }
     k_conv_last<<<blocks, 128, 0, st>>>(prim(L - 1), c->w16, c->master + c->b_off[L - 1], r, c->sig_buf, 1, H, W,
                                         nullptr, d_out);
@@ -733,6 +627,15 @@ int cnn_launches_per_pair(const dgamp_ct_cnn_s* c) { return 1 + 2 * c->L; }
 
 uint64_t cnn_ws_generation(const dgamp_ct_cnn_s* c) { return c->ws_gen; }
 }  // namespace dgct
+
+// a tensor-core convolution whose bounded wait ran out sets c->tc_err
+static int cnn_check_timeout(dgamp_ct_cnn_s* c) {
+    unsigned flag = 0;
+    DGCT_CUDA(cudaMemcpy(&flag, c->tc_err, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (!flag) return DGAMP_CT_OK;
+    DGCT_CUDA(cudaMemset(c->tc_err, 0, sizeof(flag)));
+    return DGAMP_CT_ERR_TIMEOUT;
+}
 
 static int upload_sigma(dgamp_ct_cnn_s* c, const float* h_sigma, int B, cudaStream_t st) {
     DGCT_CUDA(cudaMemcpyAsync(c->sig_buf, h_sigma, (size_t)B * sizeof(float), cudaMemcpyHostToDevice, st));
@@ -787,17 +690,18 @@ int dgamp_ct_cnn_create(int32_t layers, uint64_t seed, dgamp_ct_cnn_t* out) {
     e = e ? e : cudaMemset(c->adam_m, 0, off * sizeof(float));
     e = e ? e : cudaMemset(c->adam_v, 0, off * sizeof(float));
     e = e ? e : cudaMemset(c->grad, 0, off * sizeof(float));
-    e = e ? e : cudaFuncSetAttribute(k_conv64<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem());
-    e = e ? e : cudaFuncSetAttribute(k_conv64<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem());
+    e = e ? e : cudaMalloc(&c->tc_err, sizeof(unsigned));
+    e = e ? e : cudaMemset(c->tc_err, 0, sizeof(unsigned));
     int nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    c->conv_grid = 2 * (nsm > 0 ? nsm : 152);
+    c->sm_count = nsm > 0 ? nsm : 152;
     if (e != cudaSuccess) {
         dgamp_ct_cnn_destroy(c);
         return e == cudaErrorMemoryAllocation ? DGAMP_CT_ERR_OOM : cuda_fail(e);
     }
-    int rc = cnn_pack(c, 0);
+    int rc = conv64_tc_init();
+    if (rc == DGAMP_CT_OK) rc = cnn_pack(c, 0);
     if (rc == DGAMP_CT_OK) {
         e = cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = cuda_fail(e);
@@ -814,7 +718,7 @@ void dgamp_ct_cnn_destroy(dgamp_ct_cnn_t c) {
     if (!c) return;
     cudaDeviceSynchronize();
     cnn_free_ws(c);
-    void* ptrs[] = {c->master, c->grad, c->adam_m, c->adam_v, c->wh, c->wt, c->w0, c->w16};
+    void* ptrs[] = {c->master, c->grad, c->adam_m, c->adam_v, c->wh, c->wt, c->w0, c->w16, c->tc_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -883,7 +787,7 @@ int dgamp_ct_cnn_gradients(dgamp_ct_cnn_t c, const float* d_r, const float* d_x,
     if (h_loss) DGCT_CUDA(cudaMemcpyAsync(h_loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (h_grad) DGCT_CUDA(cudaMemcpyAsync(h_grad, c->grad, c->nparam * sizeof(float), cudaMemcpyDeviceToHost, st));
     DGCT_CUDA(cudaStreamSynchronize(st));
-    return DGAMP_CT_OK;
+    return cnn_check_timeout(c);
 }
 
 int dgamp_ct_cnn_train_step(dgamp_ct_cnn_t c, const float* d_r, const float* d_x, const float* h_sigma, int32_t batch,

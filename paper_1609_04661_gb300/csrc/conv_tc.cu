@@ -1,0 +1,419 @@
+// Hidden 64 -> 64 layers of the learned denoiser on the 5th-generation
+// tensor cores (tcgen05, sm_103a): an implicit GEMM per strip of 128 pixels,
+//   D[m][co] = sum_{tap, ci} A_tap[m][ci] W[co][tap*64 + ci],
+// M = 128 pixels of one image row, N = 64 output channels, K = 9 x 64.
+//
+// Operands are K-major with the 128-byte swizzle: a pixel's 64 channels are
+// one 128-byte row, exactly as the activations lie in global memory
+// ([B][H][W][64] BF16), so one TMA copy (box 64 channels x 130 pixels, zero
+// fill outside the image = the convolution's zero padding) brings a whole
+// halo row, and the operand of tap (dy, dx) is the row slot of input row
+// y + dy - 1 started dx rows later.  Weights are staged once per CTA, one 64 x 64
+// block per tap.  A CTA takes a contiguous range of strips, consecutive rows
+// of one 128-column band, so each strip needs one new input row: a ring of six
+// row slots keeps three in use and three loading ahead.  The FP32
+// accumulators live in tensor memory, two of them (128 columns), so the
+// epilogue of one strip (tcgen05.ld, bias + ReLU or the mask, BF16 store)
+// overlaps the MMAs of the next.
+//
+// One elected thread issues the 36 MMAs of a strip and commits them to an
+// mbarrier; every wait on it is bounded and reports a timeout through
+// *err instead of hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace dgct {
+namespace tc {
+
+constexpr int CH = 64;
+constexpr int M = 128;                    // pixels per strip (MMA M)
+constexpr int HWL = M + 2;                // halo pixels loaded per row
+constexpr int HWP = 136;                  // row slot: 136 pixels x 128 B = 17 x 1024 B
+constexpr int A_ROW = HWP * 128;          // bytes of one row slot (pixel-major, 128-byte swizzle)
+constexpr int RING = 6;                   // row slots: three rows in use, three loading ahead
+constexpr int A_BYTES = RING * A_ROW;     // the ring
+constexpr int ROW_BYTES = HWL * 128;      // bytes one row load delivers (130 pixels x 64 channels)
+constexpr int B_TAP = 64 * 128;           // one tap of the weights: 64 co x 64 ci, 128-byte swizzle
+constexpr int B_BYTES = 9 * B_TAP;
+constexpr int SMEM = 1024 + B_BYTES + A_BYTES;       // + alignment slack
+constexpr int THREADS = 256;
+constexpr unsigned TMEM_COLS = 128;       // two 64-column FP32 accumulators
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // bound of every mbarrier wait (2 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// K-major operand with 128-byte swizzle (rows of 64 BF16 = 128 B, 8-row groups
+// 1024 B apart): start address and SBO = 1024.  The swizzle follows the
+// absolute shared-memory address (the TMA wrote with the same rule), so a
+// start moved by whole 128-byte rows or by 32 bytes within a row needs no
+// base offset.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major, N = 64, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                           ((uint32_t)(M >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(d_tmem), "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `parity` of the mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// TMA tiled loads (zero fill outside the tensor), completion counted on mbar
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                       uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+        : "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+typedef __nv_bfloat16 bf16;
+
+// Strip s of the batch (row fastest): band = s / H is a 128-column band of
+// image b = band / nx at x0 = (band % nx) * 128, row y = s % H.  A CTA takes a
+// contiguous range of strips, so its consecutive strips are consecutive rows
+// of one band and share two of their three input rows.
+struct Strip {
+    int b, y, x0;
+};
+__device__ __forceinline__ Strip strip_of(int s, int H, int nx) {
+    const int band = s / H;
+    Strip t;
+    t.b = band / nx;
+    t.y = s - band * H;
+    t.x0 = (band - t.b * nx) * M;
+    return t;
+}
+
+// Input rows in the order the CTA's strips need them: a run of strips of one
+// band needs rows y_first - 1 .. y_last + 1 (rows -1 and H load as zeros);
+// row number q of the sequence goes to ring slot q % RING.
+struct RowCursor {
+    int s_a, s_e;   // current run of strips [s_a, s_e]
+    int y, q;       // next row to load and its sequence number
+    bool done;
+};
+
+__device__ __forceinline__ int run_end(int s_a, int s1, int H) {
+    const int e = (s_a / H + 1) * H;
+    return (e < s1 ? e : s1) - 1;
+}
+
+// one input row (130 pixels x 64 channels) -> its ring slot: one TMA copy
+__device__ __forceinline__ void load_row(const CUtensorMap* map, RowCursor& c, int H, int nx, int s1, uint32_t sA,
+                                         uint64_t* row_bar) {
+    const int band = c.s_a / H;
+    const int b = band / nx, x0 = (band - b * nx) * M;
+    const int slot = c.q % RING;
+    const uint32_t bar = smem_u32(&row_bar[slot]);
+    mbar_expect_tx(bar, ROW_BYTES);
+    tma_4d(sA + (uint32_t)(slot * A_ROW), map, 0, x0 - 1, c.y, b, bar);
+    ++c.q;
+    if (++c.y > c.s_e - band * H + 1) {   // past the run's last row + 1: next run
+        c.s_a = c.s_e + 1;
+        if (c.s_a >= s1) {
+            c.done = true;
+        } else {
+            c.s_e = run_end(c.s_a, s1, H);
+            c.y = c.s_a - (c.s_a / H) * H - 1;
+        }
+    }
+}
+
+// accumulator of a strip (TMEM columns tcol .. tcol + 63) -> out, with bias +
+// ReLU (MODE 0) or the mask (MODE 1).  Warp w reads TMEM lanes 32 (w % 4) ..
+// +31 (pixels of the strip) and columns 32 (w / 4) .. +31 (output channels).
+template <int MODE>
+__device__ __forceinline__ void epilogue(uint32_t tcol, const Strip& s, int H, int W, const float* __restrict__ bias,
+                                         const bf16* __restrict__ mask, bf16* __restrict__ out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quad = warp & 3, c0 = (warp >> 2) * 32;
+    const int x = s.x0 + quad * 32 + lane;
+    const bool live = x < W;
+    const size_t o = (((size_t)s.b * H + s.y) * W + (live ? x : 0)) * CH + c0;
+    const uint32_t taddr = tcol + (uint32_t)c0 + ((uint32_t)(quad * 32) << 16);
+    float v[32];
+    tmem_ld16(taddr, v);          // warp-collective: every lane takes part
+    tmem_ld16(taddr + 16, v + 16);
+    if (!live) return;
+    if (MODE == 0) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i] + __ldg(bias + c0 + i), 0.f);
+    } else {
+        __align__(16) bf16 mk[32];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(mk + 8 * q) = *reinterpret_cast<const uint4*>(mask + o + 8 * q);
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (!(__bfloat162float(mk[i]) > 0.f)) v[i] = 0.f;
+    }
+    __align__(16) __nv_bfloat162 pk[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) pk[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(out + o + 8 * q) = *reinterpret_cast<const uint4*>(pk + 4 * q);
+}
+
+// MODE 0: out = relu(bias + conv(in, Wk)); MODE 1: out = conv(in, Wk) * (mask > 0).
+// Wk = layer `layer` of a [layers][co][tap*64 + ci] BF16 array (map_w); the
+// input is [B][H][W][64] BF16 (map_in).  CTA k takes strips [k per, (k+1) per).
+// Thread 0 issues the copies and the MMAs; all four warps run the epilogue of
+// the previous strip meanwhile.
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, 1)
+k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w, int layer,
+            const float* __restrict__ bias, const bf16* __restrict__ mask, bf16* __restrict__ out, int B, int H,
+            int W, int per, unsigned* err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ __align__(8) uint64_t row_bar[RING];
+    __shared__ __align__(8) uint64_t w_bar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sB = (raw + 1023u) & ~1023u, sA = sB + B_BYTES;
+    const int nx = (W + M - 1) / M;
+    const int nstrips = B * H * nx;
+    const int s0 = (int)blockIdx.x * per;
+    const int s1 = s0 + per < nstrips ? s0 + per : nstrips;
+    if (s0 >= s1) return;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mma_bar[0]), 1);
+        mbar_init(smem_u32(&mma_bar[1]), 1);
+        for (int r = 0; r < RING; ++r) mbar_init(smem_u32(&row_bar[r]), 1);
+        mbar_init(smem_u32(&w_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    RowCursor cur;
+    cur.s_a = s0;
+    cur.s_e = run_end(s0, s1, H);
+    cur.y = s0 - (s0 / H) * H - 1;
+    cur.q = 0;
+    cur.done = false;
+    if (tid == 0) {
+        // weights -> [9 taps][64 co][64 ci] (128-byte swizzle), then the first RING rows
+        mbar_expect_tx(smem_u32(&w_bar), B_BYTES);
+#pragma unroll 1
+        for (int t = 0; t < 9; ++t) tma_3d(sB + (uint32_t)(t * B_TAP), &map_w, 64 * t, 0, layer, smem_u32(&w_bar));
+        while (!cur.done && cur.q < RING) load_row(&map_in, cur, H, nx, s1, sA, row_bar);
+    }
+    const uint32_t tmem = tmem_slot;
+    bool ok = true;
+    int Q = 0;   // sequence number of the current strip's first input row (thread 0)
+    int k = 0;
+    for (int s = s0; s < s1; ++s, ++k) {
+        const int buf = k & 1;
+        const uint32_t par_prev = (uint32_t)(((k - 1) >> 1) & 1);
+        // the epilogue of strip k - 2 (accumulator buf) is finished
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+            if (k > 0) Q += (s % H == 0) ? 3 : 1;   // a new band starts three fresh rows
+            if (k == 0 && !mbar_wait(smem_u32(&w_bar), 0u)) ok = false;
+#pragma unroll 1
+            for (int dy = 0; dy < 3; ++dy) {
+                const int q = Q + dy;
+                if (!mbar_wait(smem_u32(&row_bar[q % RING]), (uint32_t)((q / RING) & 1))) ok = false;
+            }
+            fence_after();
+            const uint32_t d = tmem + (uint32_t)(buf * 64);
+#pragma unroll 1
+            for (int t = 0; t < 9; ++t) {
+                const int dy = t / 3, dx = t - 3 * (t / 3);
+                // pixel m of the strip reads halo pixel m + dx: the row slot started dx rows later
+                const uint32_t row = sA + (uint32_t)(((Q + dy) % RING) * A_ROW + dx * 128);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {   // 16 channels (32 bytes of each row) per MMA
+                    const uint64_t a = sdesc_sw128(row + (uint32_t)(kk * 32));
+                    const uint64_t b = sdesc_sw128(sB + (uint32_t)(t * B_TAP + kk * 32));
+                    mma_bf16(d, a, b, (t | kk) != 0 ? 1u : 0u);
+                }
+            }
+            mma_commit(smem_u32(&mma_bar[buf]));
+            // once the previous strip's MMAs are done, rows up to Q - 1 are free
+            if (k > 0 && !mbar_wait(smem_u32(&mma_bar[buf ^ 1]), par_prev)) ok = false;
+            while (!cur.done && cur.q <= Q + RING - 1) load_row(&map_in, cur, H, nx, s1, sA, row_bar);
+        }
+        if (k > 0) {
+            if (tid != 0 && !mbar_wait(smem_u32(&mma_bar[buf ^ 1]), par_prev)) ok = false;
+            fence_after();
+            epilogue<MODE>(tmem + (uint32_t)((buf ^ 1) * 64), strip_of(s - 1, H, nx), H, W, bias, mask, out);
+        }
+    }
+    {
+        const int lb = (k - 1) & 1;
+        if (!mbar_wait(smem_u32(&mma_bar[lb]), (uint32_t)(((k - 1) >> 1) & 1))) ok = false;
+        fence_after();
+        epilogue<MODE>(tmem + (uint32_t)(lb * 64), strip_of(s1 - 1, H, nx), H, W, bias, mask, out);
+    }
+    if (!ok) atomicOr(err, 1u);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace tc
+}  // namespace dgct
+
+namespace dgct {
+
+int conv64_tc_init() {
+    DGCT_CUDA(cudaFuncSetAttribute(tc::k_conv64_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
+    DGCT_CUDA(cudaFuncSetAttribute(tc::k_conv64_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
+    return DGAMP_CT_OK;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn tensor_map_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+static int encode(CUtensorMap* map, cuuint32_t rank, const void* base, const cuuint64_t* dims,
+                  const cuuint64_t* strides, const cuuint32_t* box) {
+    EncodeTiledFn fn = tensor_map_encoder();
+    if (!fn) return cuda_fail(cudaErrorNotSupported);
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), dims, strides, box,
+                          es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? DGAMP_CT_OK : cuda_fail(cudaErrorInvalidValue);
+}
+
+// in: [B][H][W][64] BF16; wk_all: [layers][64][576] BF16 (layer `layer` used);
+// out (mode 0: bias + ReLU, mode 1: times mask > 0) like in.
+int launch_conv64_tc(int mode, const void* in, const void* wk_all, int layers, int layer, const float* bias,
+                     const void* mask, void* out, int B, int H, int W, int grid_cap, unsigned* err, cudaStream_t st) {
+    const long long nstrips = (long long)B * H * ((W + tc::M - 1) / tc::M);
+    if (nstrips <= 0) return DGAMP_CT_OK;
+    if (layer < 0 || layer >= layers) return DGAMP_CT_ERR_INVALID_ARG;
+    CUtensorMap map_in, map_w;
+    {
+        const cuuint64_t dims[4] = {64, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+        const cuuint64_t strides[3] = {128, (cuuint64_t)W * 128, (cuuint64_t)H * W * 128};
+        const cuuint32_t box[4] = {64, (cuuint32_t)tc::HWL, 1, 1};
+        DGCT_TRY(encode(&map_in, 4, in, dims, strides, box));
+    }
+    {
+        const cuuint64_t dims[3] = {576, 64, (cuuint64_t)layers};
+        const cuuint64_t strides[2] = {1152, 1152 * 64};
+        const cuuint32_t box[3] = {64, 64, 1};
+        DGCT_TRY(encode(&map_w, 3, wk_all, dims, strides, box));
+    }
+    // contiguous ranges of strips, one per CTA, at most grid_cap CTAs
+    const int cap = grid_cap > 0 ? grid_cap : 1;
+    const int per = (int)((nstrips + cap - 1) / cap);
+    const int grid = (int)((nstrips + per - 1) / per);
+    typedef __nv_bfloat16 bf16;
+    if (mode == 0)
+        tc::k_conv64_tc<0><<<grid, tc::THREADS, tc::SMEM, st>>>(map_in, map_w, layer, bias, (const bf16*)mask,
+                                                                (bf16*)out, B, H, W, per, err);
+    else
+        tc::k_conv64_tc<1><<<grid, tc::THREADS, tc::SMEM, st>>>(map_in, map_w, layer, bias, (const bf16*)mask,
+                                                                (bf16*)out, B, H, W, per, err);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+}  // namespace dgct

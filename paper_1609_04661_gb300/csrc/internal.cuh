@@ -240,6 +240,10 @@ int cnn_prepare_pair(dgamp_ct_cnn_s* c, int n);
 int cnn_denoise_jvp(dgamp_ct_cnn_s* c, const float* rb, const DevScalars* S, int n, float* out, int scaled,
                     cudaStream_t st);
 int cnn_launches_per_pair(const dgamp_ct_cnn_s* c);
+// conv_tc.cu: hidden 64 -> 64 layers on tcgen05 (mode 0: bias + ReLU, mode 1: masked linear)
+int conv64_tc_init();
+int launch_conv64_tc(int mode, const void* in, const void* wk_all, int layers, int layer, const float* bias,
+                     const void* mask, void* out, int B, int H, int W, int grid_cap, unsigned* err, cudaStream_t st);
 // changes whenever the network's workspace is reallocated (captured graphs hold its pointers)
 uint64_t cnn_ws_generation(const dgamp_ct_cnn_s* c);
 
