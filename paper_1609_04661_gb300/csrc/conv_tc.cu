@@ -40,7 +40,9 @@ constexpr int ROW_BYTES = HWL * 128;      // bytes one row load delivers (130 pi
 constexpr int B_TAP = 64 * 128;           // one tap of the weights: 64 co x 64 ci, 128-byte swizzle
 constexpr int B_BYTES = 9 * B_TAP;
 constexpr int SMEM = 1024 + B_BYTES + A_BYTES;       // + alignment slack
-constexpr int THREADS = 256;
+constexpr int EPI_WARP0 = 4;              // warps 4..11: epilogue; warp 0: TMA; warp 1: MMA
+constexpr int THREADS = 32 * (EPI_WARP0 + 8);
+constexpr int EPI_THREADS = 32 * 8;
 constexpr unsigned TMEM_COLS = 128;       // two 64-column FP32 accumulators
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bound of every mbarrier wait (2 s)
 
@@ -195,13 +197,14 @@ __device__ __forceinline__ void load_row(const CUtensorMap* map, RowCursor& c, i
 }
 
 // accumulator of a strip (TMEM columns tcol .. tcol + 63) -> out, with bias +
-// ReLU (MODE 0) or the mask (MODE 1).  Warp w reads TMEM lanes 32 (w % 4) ..
-// +31 (pixels of the strip) and columns 32 (w / 4) .. +31 (output channels).
+// ReLU (MODE 0) or the mask (MODE 1).  Epilogue warp e (warp e + 4) reads TMEM
+// lanes 32 (e % 4) .. +31 (pixels of the strip) and columns 32 (e / 4) .. +31
+// (output channels).
 template <int MODE>
 __device__ __forceinline__ void epilogue(uint32_t tcol, const Strip& s, int H, int W, const float* __restrict__ bias,
-                                         const bf16* __restrict__ mask, bf16* __restrict__ out) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int quad = warp & 3, c0 = (warp >> 2) * 32;
+                                         const bf16* __restrict__ mask, bf16* __restrict__ out, uint32_t empty_bar) {
+    const int ew = (threadIdx.x >> 5) - EPI_WARP0, lane = threadIdx.x & 31;
+    const int quad = ew & 3, c0 = (ew >> 2) * 32;   // quad == warp % 4: the TMEM lanes this warp may read
     const int x = s.x0 + quad * 32 + lane;
     const bool live = x < W;
     const size_t o = (((size_t)s.b * H + s.y) * W + (live ? x : 0)) * CH + c0;
@@ -209,6 +212,8 @@ __device__ __forceinline__ void epilogue(uint32_t tcol, const Strip& s, int H, i
     float v[32];
     tmem_ld16(taddr, v);          // warp-collective: every lane takes part
     tmem_ld16(taddr + 16, v + 16);
+    fence_before();               // the reads are complete: the accumulator may be reused
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(empty_bar) : "memory");
     if (!live) return;
     if (MODE == 0) {
 #pragma unroll
@@ -230,22 +235,34 @@ __device__ __forceinline__ void epilogue(uint32_t tcol, const Strip& s, int H, i
         *reinterpret_cast<uint4*>(out + o + 8 * q) = *reinterpret_cast<const uint4*>(pk + 4 * q);
 }
 
+// first input-row number of a CTA's strip k given that of strip k - 1: +1
+// inside a band, +3 when strip s starts a new band
+__device__ __forceinline__ int next_q(int Q, int s, int H) { return Q + ((s % H == 0) ? 3 : 1); }
+
 // MODE 0: out = relu(bias + conv(in, Wk)); MODE 1: out = conv(in, Wk) * (mask > 0).
 // Wk = layer `layer` of a [layers][co][tap*64 + ci] BF16 array (map_w); the
 // input is [B][H][W][64] BF16 (map_in).  CTA k takes strips [k per, (k+1) per).
-// Thread 0 issues the copies and the MMAs; all four warps run the epilogue of
-// the previous strip meanwhile.
+// Warp-specialised, with no block barrier inside the loop:
+//   warp 0 (one lane): TMA producer -- weights, then input rows into the ring,
+//     a slot refilled once row_empty says its last strip's MMAs are done;
+//   warp 1 (one lane): MMA issuer -- per strip, waits for its three rows and a
+//     free accumulator, issues 9 taps x 4 channel steps, commits acc_full and
+//     the row_empty barriers of rows no later strip reads;
+//   warps 4..11: epilogue -- wait acc_full, read TMEM, free the accumulator
+//     (acc_empty), then bias + ReLU or mask and the BF16 store.
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
 k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w, int layer,
             const float* __restrict__ bias, const bf16* __restrict__ mask, bf16* __restrict__ out, int B, int H,
             int W, int per, unsigned* err) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mma_bar[2];
-    __shared__ __align__(8) uint64_t row_bar[RING];
+    __shared__ __align__(8) uint64_t row_full[RING];
+    __shared__ __align__(8) uint64_t row_empty[RING];
+    __shared__ __align__(8) uint64_t acc_full[2];
+    __shared__ __align__(8) uint64_t acc_empty[2];
     __shared__ __align__(8) uint64_t w_bar;
     __shared__ uint32_t tmem_slot;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t sB = (raw + 1023u) & ~1023u, sA = sB + B_BYTES;
     const int nx = (W + M - 1) / M;
@@ -253,89 +270,101 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
     const int s0 = (int)blockIdx.x * per;
     const int s1 = s0 + per < nstrips ? s0 + per : nstrips;
     if (s0 >= s1) return;
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
                      "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(smem_u32(&mma_bar[0]), 1);
-        mbar_init(smem_u32(&mma_bar[1]), 1);
-        for (int r = 0; r < RING; ++r) mbar_init(smem_u32(&row_bar[r]), 1);
+        for (int r = 0; r < RING; ++r) {
+            mbar_init(smem_u32(&row_full[r]), 1);
+            mbar_init(smem_u32(&row_empty[r]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), EPI_THREADS);
+        }
         mbar_init(smem_u32(&w_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     fence_before();
     __syncthreads();
     fence_after();
-    RowCursor cur;
-    cur.s_a = s0;
-    cur.s_e = run_end(s0, s1, H);
-    cur.y = s0 - (s0 / H) * H - 1;
-    cur.q = 0;
-    cur.done = false;
-    if (tid == 0) {
-        // weights -> [9 taps][64 co][64 ci] (128-byte swizzle), then the first RING rows
-        mbar_expect_tx(smem_u32(&w_bar), B_BYTES);
-#pragma unroll 1
-        for (int t = 0; t < 9; ++t) tma_3d(sB + (uint32_t)(t * B_TAP), &map_w, 64 * t, 0, layer, smem_u32(&w_bar));
-        while (!cur.done && cur.q < RING) load_row(&map_in, cur, H, nx, s1, sA, row_bar);
-    }
     const uint32_t tmem = tmem_slot;
     bool ok = true;
-    int Q = 0;   // sequence number of the current strip's first input row (thread 0)
-    int k = 0;
-    for (int s = s0; s < s1; ++s, ++k) {
-        const int buf = k & 1;
-        const uint32_t par_prev = (uint32_t)(((k - 1) >> 1) & 1);
-        // the epilogue of strip k - 2 (accumulator buf) is finished
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (tid == 0) {
-            if (k > 0) Q += (s % H == 0) ? 3 : 1;   // a new band starts three fresh rows
-            if (k == 0 && !mbar_wait(smem_u32(&w_bar), 0u)) ok = false;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer ----
+            mbar_expect_tx(smem_u32(&w_bar), B_BYTES);
 #pragma unroll 1
-            for (int dy = 0; dy < 3; ++dy) {
-                const int q = Q + dy;
-                if (!mbar_wait(smem_u32(&row_bar[q % RING]), (uint32_t)((q / RING) & 1))) ok = false;
+            for (int t = 0; t < 9; ++t) tma_3d(sB + (uint32_t)(t * B_TAP), &map_w, 64 * t, 0, layer, smem_u32(&w_bar));
+            RowCursor cur;
+            cur.s_a = s0;
+            cur.s_e = run_end(s0, s1, H);
+            cur.y = s0 - (s0 / H) * H - 1;
+            cur.q = 0;
+            cur.done = false;
+            while (!cur.done) {
+                const int slot = cur.q % RING;
+                if (cur.q >= RING && !mbar_wait(smem_u32(&row_empty[slot]), (uint32_t)((cur.q / RING - 1) & 1)))
+                    ok = false;
+                load_row(&map_in, cur, H, nx, s1, sA, row_full);
             }
-            fence_after();
-            const uint32_t d = tmem + (uint32_t)(buf * 64);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            if (!mbar_wait(smem_u32(&w_bar), 0u)) ok = false;
+            int Q = 0;
+            int k = 0;
+            for (int s = s0; s < s1; ++s, ++k) {
+                if (k > 0) Q = next_q(Q, s, H);
+                const int buf = k & 1;
+                if (k >= 2 && !mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)(((k - 2) >> 1) & 1))) ok = false;
 #pragma unroll 1
-            for (int t = 0; t < 9; ++t) {
-                const int dy = t / 3, dx = t - 3 * (t / 3);
-                // pixel m of the strip reads halo pixel m + dx: the row slot started dx rows later
-                const uint32_t row = sA + (uint32_t)(((Q + dy) % RING) * A_ROW + dx * 128);
+                for (int dy = 0; dy < 3; ++dy) {
+                    const int q = Q + dy;
+                    if (!mbar_wait(smem_u32(&row_full[q % RING]), (uint32_t)((q / RING) & 1))) ok = false;
+                }
+                fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * 64);
+#pragma unroll 1
+                for (int t = 0; t < 9; ++t) {
+                    const int dy = t / 3, dx = t - 3 * (t / 3);
+                    // pixel m of the strip reads halo pixel m + dx: the row slot started dx rows later
+                    const uint32_t row = sA + (uint32_t)(((Q + dy) % RING) * A_ROW + dx * 128);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {   // 16 channels (32 bytes of each row) per MMA
-                    const uint64_t a = sdesc_sw128(row + (uint32_t)(kk * 32));
-                    const uint64_t b = sdesc_sw128(sB + (uint32_t)(t * B_TAP + kk * 32));
-                    mma_bf16(d, a, b, (t | kk) != 0 ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk) {   // 16 channels (32 bytes of each row) per MMA
+                        const uint64_t a = sdesc_sw128(row + (uint32_t)(kk * 32));
+                        const uint64_t b = sdesc_sw128(sB + (uint32_t)(t * B_TAP + kk * 32));
+                        mma_bf16(d, a, b, (t | kk) != 0 ? 1u : 0u);
+                    }
+                }
+                mma_commit(smem_u32(&acc_full[buf]));
+                // rows no later strip reads: Q always; Q + 1, Q + 2 at the end of a run
+                mma_commit(smem_u32(&row_empty[Q % RING]));
+                if (s + 1 >= s1 || (s + 1) % H == 0) {
+                    mma_commit(smem_u32(&row_empty[(Q + 1) % RING]));
+                    mma_commit(smem_u32(&row_empty[(Q + 2) % RING]));
                 }
             }
-            mma_commit(smem_u32(&mma_bar[buf]));
-            // once the previous strip's MMAs are done, rows up to Q - 1 are free
-            if (k > 0 && !mbar_wait(smem_u32(&mma_bar[buf ^ 1]), par_prev)) ok = false;
-            while (!cur.done && cur.q <= Q + RING - 1) load_row(&map_in, cur, H, nx, s1, sA, row_bar);
         }
-        if (k > 0) {
-            if (tid != 0 && !mbar_wait(smem_u32(&mma_bar[buf ^ 1]), par_prev)) ok = false;
+    } else if (warp >= EPI_WARP0) {
+        // ---- epilogue ----
+        int k = 0;
+        for (int s = s0; s < s1; ++s, ++k) {
+            const int buf = k & 1;
+            if (!mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)((k >> 1) & 1))) ok = false;
             fence_after();
-            epilogue<MODE>(tmem + (uint32_t)((buf ^ 1) * 64), strip_of(s - 1, H, nx), H, W, bias, mask, out);
+            epilogue<MODE>(tmem + (uint32_t)(buf * 64), strip_of(s, H, nx), H, W, bias, mask, out,
+                           smem_u32(&acc_empty[buf]));
         }
-    }
-    {
-        const int lb = (k - 1) & 1;
-        if (!mbar_wait(smem_u32(&mma_bar[lb]), (uint32_t)(((k - 1) >> 1) & 1))) ok = false;
-        fence_after();
-        epilogue<MODE>(tmem + (uint32_t)(lb * 64), strip_of(s1 - 1, H, nx), H, W, bias, mask, out);
     }
     if (!ok) atomicOr(err, 1u);
     fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
