@@ -92,19 +92,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded wait for phase `parity` of the mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of the mbarrier; false on timeout.  The
+// clock is read only when the first try fails.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    if (mbar_try(mbar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(ok)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (ok) return true;
+        if (mbar_try(mbar, parity)) return true;
         if (global_ns() - t0 > WAIT_NS) return false;
     }
 }
@@ -329,15 +335,19 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
                 }
                 fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * 64);
-#pragma unroll 1
-                for (int t = 0; t < 9; ++t) {
-                    const int dy = t / 3, dx = t - 3 * (t / 3);
-                    // pixel m of the strip reads halo pixel m + dx: the row slot started dx rows later
-                    const uint32_t row = sA + (uint32_t)(((Q + dy) % RING) * A_ROW + dx * 128);
+                // descriptors advance by (byte offset >> 4) in their address field
+                const uint64_t bdesc0 = sdesc_sw128(sB);
+                uint64_t arow[3];
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {   // 16 channels (32 bytes of each row) per MMA
-                        const uint64_t a = sdesc_sw128(row + (uint32_t)(kk * 32));
-                        const uint64_t b = sdesc_sw128(sB + (uint32_t)(t * B_TAP + kk * 32));
+                for (int dy = 0; dy < 3; ++dy) arow[dy] = sdesc_sw128(sA + (uint32_t)(((Q + dy) % RING) * A_ROW));
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        // pixel m of the strip reads halo pixel m + dx (dx = t % 3 rows later);
+                        // 16 channels (32 bytes of each row) per MMA
+                        const uint64_t a = arow[t / 3] + (uint64_t)(((t % 3) * 128 + kk * 32) >> 4);
+                        const uint64_t b = bdesc0 + (uint64_t)((t * B_TAP + kk * 32) >> 4);
                         mma_bf16(d, a, b, (t | kk) != 0 ? 1u : 0u);
                     }
                 }
