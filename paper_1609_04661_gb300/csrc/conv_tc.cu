@@ -40,10 +40,10 @@ constexpr int ROW_BYTES = HWL * 128;      // bytes one row load delivers (130 pi
 constexpr int B_TAP = 64 * 128;           // one tap of the weights: 64 co x 64 ci, 128-byte swizzle
 constexpr int B_BYTES = 9 * B_TAP;
 constexpr int SMEM = 1024 + B_BYTES + A_BYTES;       // + alignment slack
-constexpr int EPI_WARP0 = 4;              // warps 4..11: epilogue; warp 0: TMA; warp 1: MMA
+constexpr int EPI_WARP0 = 4;              // warps 4..11: epilogue; warp 0: TMA; warps 1, 2: MMA
 constexpr int THREADS = 32 * (EPI_WARP0 + 8);
 constexpr int EPI_THREADS = 32 * 8;
-constexpr unsigned TMEM_COLS = 128;       // two 64-column FP32 accumulators
+constexpr unsigned TMEM_COLS = 256;       // four 64-column FP32 accumulators, two per MMA warp
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bound of every mbarrier wait (2 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -245,15 +245,22 @@ __device__ __forceinline__ void epilogue(uint32_t tcol, const Strip& s, int H, i
 // inside a band, +3 when strip s starts a new band
 __device__ __forceinline__ int next_q(int Q, int s, int H) { return Q + ((s % H == 0) ? 3 : 1); }
 
+// accumulator of a CTA's strip k: MMA warp k % 2, its own buffer (k / 2) % 2
+__device__ __forceinline__ int acc_of(int k) { return 2 * (k & 1) + ((k >> 1) & 1); }
+
 // MODE 0: out = relu(bias + conv(in, Wk)); MODE 1: out = conv(in, Wk) * (mask > 0).
 // Wk = layer `layer` of a [layers][co][tap*64 + ci] BF16 array (map_w); the
 // input is [B][H][W][64] BF16 (map_in).  CTA k takes strips [k per, (k+1) per).
 // Warp-specialised, with no block barrier inside the loop:
 //   warp 0 (one lane): TMA producer -- weights, then input rows into the ring,
-//     a slot refilled once row_empty says its last strip's MMAs are done;
-//   warp 1 (one lane): MMA issuer -- per strip, waits for its three rows and a
-//     free accumulator, issues 9 taps x 4 channel steps, commits acc_full and
-//     the row_empty barriers of rows no later strip reads;
+//     a slot refilled once both MMA warps have released its previous row;
+//   warps 1 and 2 (one lane each): MMA issuers for the even and the odd
+//     strips -- a single issuing thread cannot feed the tensor core with
+//     N = 64 instructions, two can.  Each waits for its strip's three rows
+//     and a free accumulator of its own, issues 9 taps x 4 channel steps,
+//     commits acc_full, and commits row_empty for every row below its next
+//     strip's first row (each row gets one release from each MMA warp, so a
+//     slot is refilled only after both warps' MMAs reading it are done);
 //   warps 4..11: epilogue -- wait acc_full, read TMEM, free the accumulator
 //     (acc_empty), then bias + ReLU or mask and the BF16 store.
 template <int MODE>
@@ -264,8 +271,8 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t row_full[RING];
     __shared__ __align__(8) uint64_t row_empty[RING];
-    __shared__ __align__(8) uint64_t acc_full[2];
-    __shared__ __align__(8) uint64_t acc_empty[2];
+    __shared__ __align__(8) uint64_t acc_full[4];
+    __shared__ __align__(8) uint64_t acc_empty[4];
     __shared__ __align__(8) uint64_t w_bar;
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -285,9 +292,9 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
     if (tid == 0) {
         for (int r = 0; r < RING; ++r) {
             mbar_init(smem_u32(&row_full[r]), 1);
-            mbar_init(smem_u32(&row_empty[r]), 1);
+            mbar_init(smem_u32(&row_empty[r]), 2);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < 4; ++b) {
             mbar_init(smem_u32(&acc_full[b]), 1);
             mbar_init(smem_u32(&acc_empty[b]), EPI_THREADS);
         }
@@ -318,25 +325,31 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
                 load_row(&map_in, cur, H, nx, s1, sA, row_full);
             }
         }
-    } else if (warp == 1) {
+    } else if (warp == 1 || warp == 2) {
         if (lane == 0) {
-            // ---- MMA issuer ----
+            // ---- MMA issuer X for strips k with k % 2 == X ----
+            const int X = warp - 1;
+            int q_total = 0;   // input rows of the CTA: first row of the last strip + 3
+            for (int s = s0 + 1; s < s1; ++s) q_total = next_q(q_total, s, H);
+            q_total += 3;
             if (!mbar_wait(smem_u32(&w_bar), 0u)) ok = false;
-            int Q = 0;
+            const uint64_t bdesc0 = sdesc_sw128(sB);
+            int Q = 0, fx = 0;   // first row of strip k; rows below fx released by this warp
             int k = 0;
             for (int s = s0; s < s1; ++s, ++k) {
                 if (k > 0) Q = next_q(Q, s, H);
-                const int buf = k & 1;
-                if (k >= 2 && !mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)(((k - 2) >> 1) & 1))) ok = false;
+                if ((k & 1) != X) continue;
+                for (; fx < Q; ++fx) mma_commit(smem_u32(&row_empty[fx % RING]));   // rows this warp skips
+                const int a = acc_of(k);
+                if (k >= 4 && !mbar_wait(smem_u32(&acc_empty[a]), (uint32_t)(((k - 4) >> 2) & 1))) ok = false;
 #pragma unroll 1
                 for (int dy = 0; dy < 3; ++dy) {
                     const int q = Q + dy;
                     if (!mbar_wait(smem_u32(&row_full[q % RING]), (uint32_t)((q / RING) & 1))) ok = false;
                 }
                 fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * 64);
+                const uint32_t d = tmem + (uint32_t)(a * 64);
                 // descriptors advance by (byte offset >> 4) in their address field
-                const uint64_t bdesc0 = sdesc_sw128(sB);
                 uint64_t arow[3];
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy) arow[dy] = sdesc_sw128(sA + (uint32_t)(((Q + dy) % RING) * A_ROW));
@@ -346,29 +359,28 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
                     for (int kk = 0; kk < 4; ++kk) {
                         // pixel m of the strip reads halo pixel m + dx (dx = t % 3 rows later);
                         // 16 channels (32 bytes of each row) per MMA
-                        const uint64_t a = arow[t / 3] + (uint64_t)(((t % 3) * 128 + kk * 32) >> 4);
-                        const uint64_t b = bdesc0 + (uint64_t)((t * B_TAP + kk * 32) >> 4);
-                        mma_bf16(d, a, b, (t | kk) != 0 ? 1u : 0u);
+                        const uint64_t ad = arow[t / 3] + (uint64_t)(((t % 3) * 128 + kk * 32) >> 4);
+                        const uint64_t bd = bdesc0 + (uint64_t)((t * B_TAP + kk * 32) >> 4);
+                        mma_bf16(d, ad, bd, (t | kk) != 0 ? 1u : 0u);
                     }
                 }
-                mma_commit(smem_u32(&acc_full[buf]));
-                // rows no later strip reads: Q always; Q + 1, Q + 2 at the end of a run
-                mma_commit(smem_u32(&row_empty[Q % RING]));
-                if (s + 1 >= s1 || (s + 1) % H == 0) {
-                    mma_commit(smem_u32(&row_empty[(Q + 1) % RING]));
-                    mma_commit(smem_u32(&row_empty[(Q + 2) % RING]));
-                }
+                mma_commit(smem_u32(&acc_full[a]));
+                // release the rows below this warp's next strip (strip k + 2)
+                int bound = q_total;
+                if (s + 2 < s1) bound = next_q(next_q(Q, s + 1, H), s + 2, H);
+                for (; fx < bound; ++fx) mma_commit(smem_u32(&row_empty[fx % RING]));
             }
+            for (; fx < q_total; ++fx) mma_commit(smem_u32(&row_empty[fx % RING]));
         }
     } else if (warp >= EPI_WARP0) {
         // ---- epilogue ----
         int k = 0;
         for (int s = s0; s < s1; ++s, ++k) {
-            const int buf = k & 1;
-            if (!mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)((k >> 1) & 1))) ok = false;
+            const int a = acc_of(k);
+            if (!mbar_wait(smem_u32(&acc_full[a]), (uint32_t)((k >> 2) & 1))) ok = false;
             fence_after();
-            epilogue<MODE>(tmem + (uint32_t)(buf * 64), strip_of(s, H, nx), H, W, bias, mask, out,
-                           smem_u32(&acc_empty[buf]));
+            epilogue<MODE>(tmem + (uint32_t)(a * 64), strip_of(s, H, nx), H, W, bias, mask, out,
+                           smem_u32(&acc_empty[a]));
         }
     }
     if (!ok) atomicOr(err, 1u);
