@@ -159,10 +159,11 @@ def _ablation(plan, case, counts, T):
     return out
 
 
-def _batched(dg, rank, world, dist, flush, steps):
+def _batched(dg, rank, world, dist, flush, steps, learned=False):
     """The 64-slice mixed batch (n in {256, 384, 512}, 32-128 views) through
     dgamp_ct_solve_batched; under torchrun each rank takes its largest-first
-    share of the slices (strong scaling: the batch is fixed)."""
+    share of the slices (strong scaling: the batch is fixed).  learned: the
+    shipped network as denoiser, one network object per slice."""
     import numpy as np
     import torch
     import synth
@@ -172,6 +173,14 @@ def _batched(dg, rank, world, dist, flush, steps):
     owner, _ = dg.schedule_lpt(work, world)
     mine = [c for c, q in zip(batch, owner) if q == rank]
     plans = [dg.Plan(c["n"], c["n_views"], c["n_det"], **TV) for c in mine]
+    nets = []
+    if learned:
+        from paper_1609_04661_gb300.train_denoiser import load_cnn
+        for p in plans:
+            net = load_cnn()
+            p.set_cnn(net)
+            p.set_options(denoiser=1, cnn_scale=int(net.scaled))
+            nets.append(net)
     counts = [torch.as_tensor(c["y"]).cuda() for c in mine]
     I0 = [c["I0"] for c in mine]
     mus = [torch.empty((c["n"], c["n"]), device="cuda") for c in mine]
@@ -209,8 +218,11 @@ def _batched(dg, rank, world, dist, flush, steps):
     launches = sum(p.solve_launches(T) for p in plans)
     for p in plans:
         p.close()
+    for net in nets:
+        net.close()
     return {"workload": "mixed64: 64 slices, n in {256,384,512}, views in {32,48,64,96,128}, bins ceil(1.42 n), "
-                        "log10 I0 ~ U(4,6), 10 ellipses + rectangle each (seed 3000), 30 iterations, prox-TV",
+                        "log10 I0 ~ U(4,6), 10 ellipses + rectangle each (seed 3000), 30 iterations, "
+                        + ("learned denoiser (one network per slice)" if learned else "prox-TV"),
             "slices": len(batch), "iters_per_slice": T, "scaling": "strong",
             "ms_per_batch": ms, "iters_per_s": len(batch) * T / (ms / 1e3),
             "slices_per_s": len(batch) / (ms / 1e3),
@@ -466,6 +478,8 @@ def run_gpu(args):
     if rank == 0 and not args.no_learned:
         learned = _learned_vs_plain(dg, plan, case, counts, T, value / world)
     batched = None if args.no_batched else _batched(dg, rank, world, dist, flush, 3)
+    batched_learned = None if (args.no_batched or args.no_learned) else _batched(dg, rank, world, dist, flush, 1,
+                                                                                   learned=True)
     ablation = _ablation(plan, case, counts, T) if rank == 0 and not args.no_learned else None
 
     line = None
@@ -484,7 +498,7 @@ def run_gpu(args):
                 "psnr_db": psnr,
                 "a_plus_at_gbs": a_at_bytes / (a_at_ms * 1e-3) / 1e9,
                 "iteration_ms": iter_ms, "kernel_ms": prof, "kernel_share": shares,
-                "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned, "batched": batched,
+                "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned, "batched": batched, "batched_learned": batched_learned,
                 "ablation": ablation}
         print(json.dumps(line), flush=True)
     plan.close()

@@ -238,10 +238,13 @@ int dgamp_ct_solve_host(dgamp_ct_plan_t plan, const float* h_counts, double I0,
    streams that fork from and join back into `stream`, so small slices run
    concurrently; the call only enqueues work unless stats != NULL, in which
    case it synchronises and fills stats[0..n-1].  The result of each slice is
-   bit-identical to its own dgamp_ct_solve.  Errors: INVALID_ARG (n < 0, a
-   NULL pointer, a repeated plan, a plan of another device, a learned plan
-   without a network, I0 <= 0 or not finite, iters < 1), CUDA, NONFINITE
-   (only with stats). */
+   bit-identical to its own dgamp_ct_solve.  Learned plans need a network
+   each (dgamp_ct_cnn_create per slice, same weights): a network's
+   activation workspace serves one solve at a time, and the slices run
+   concurrently.  Errors: INVALID_ARG (n < 0, a NULL pointer, a repeated
+   plan, two learned plans sharing a network, a plan of another device, a
+   learned plan without a network, I0 <= 0 or not finite, iters < 1), CUDA,
+   NONFINITE (only with stats). */
 int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float* const* d_counts,
                            const double* I0, int32_t iters, float* const* d_mu_out,
                            dgamp_ct_stats* stats, void* stream);

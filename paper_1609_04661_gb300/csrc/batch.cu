@@ -68,6 +68,7 @@ int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float*
     int device = 0;
     DGCT_CUDA(cudaGetDevice(&device));
     std::set<dgamp_ct_plan_t> seen;
+    std::set<const dgamp_ct_cnn_s*> nets;   // a network's workspace serves one solve at a time
     std::vector<int64_t> work(n);
     for (int32_t i = 0; i < n; ++i) {
         const dgamp_ct_plan_t pl = plans[i];
@@ -75,6 +76,7 @@ int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float*
         if (pl->device != device) return DGAMP_CT_ERR_INVALID_ARG;
         if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
         if (!seen.insert(pl).second) return DGAMP_CT_ERR_INVALID_ARG;   // a plan holds one slice's state
+        if (pl->opt.denoiser == 1 && !nets.insert(pl->cnn).second) return DGAMP_CT_ERR_INVALID_ARG;
         work[i] = (int64_t)pl->nv * pl->nd * pl->n;                   // Joseph steps of one projection
     }
     const int32_t queues = std::min<int32_t>(n, kBatchStreams);

@@ -75,3 +75,36 @@ def test_batched_rejects_a_repeated_plan(dg):
             dg.solve_batched([p, p], [c, c], [s["I0"], s["I0"]], 2)
         with pytest.raises(dg.DgampError):
             dg.solve_batched([p], [c], [0.0], 2)
+
+
+def test_learned_batch_equals_single_solves_and_rejects_a_shared_network(dg):
+    """A batch of learned slices, one network per slice (same weights): every
+    slice equals its own solve bit for bit; two plans sharing a network are
+    rejected (a network's workspace serves one solve at a time)."""
+    from oracle import cnn as ocnn
+    from paper_1609_04661_gb300.binding import flatten_params
+    ws, bs = ocnn.init_params(31)
+    params = flatten_params(ws, bs)
+    sl = _slices()[:3]
+    T = 3
+    nets = [dg.CNN(17) for _ in sl]
+    plans = [dg.Plan(s["n"], s["nv"], s["nd"], denoiser=1, damp_x=0.5, damp_s=0.5) for s in sl]
+    try:
+        for net, pl in zip(nets, plans):
+            net.set_params(params)
+            pl.set_cnn(net)
+        counts = [torch.as_tensor(s["y"]).cuda() for s in sl]
+        I0 = [s["I0"] for s in sl]
+        mus = dg.solve_batched(plans, counts, I0, T)
+        single = [p.solve(c, i0, T) for p, c, i0 in zip(plans, counts, I0)]
+        torch.cuda.synchronize()
+        for k in range(len(sl)):
+            assert torch.equal(mus[k], single[k]), k
+        plans[1].set_cnn(nets[0])
+        with pytest.raises(dg.DgampError):
+            dg.solve_batched(plans, counts, I0, T)
+    finally:
+        for p in plans:
+            p.close()
+        for n in nets:
+            n.close()
