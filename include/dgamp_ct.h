@@ -89,6 +89,12 @@ typedef struct {
     int32_t  truncate_z;   /* 0 (default): the output step's posterior runs over the whole
                               line (Section 4.2); 1: restricted to z >= 0 (mode max(z0, 0);
                               where clamped s = -p/tau_p and tau_s_i = 1/tau_p) */
+    int32_t  storage;      /* inside dgamp_ct_solve: 0 (default) FP32; 1 = the sinograms
+                              between projector, filter, output step and back-projector
+                              (A x, H A x, s, H s) and the image copies the projector reads
+                              are stored in BF16, every sum in FP32 and the GAMP scalars
+                              in FP64; the counts and the denoiser's images stay FP32.
+                              The single-step entry points always take FP32 buffers. */
 } dgamp_ct_options;
 
 typedef struct {

@@ -52,7 +52,7 @@ class Options(C.Structure):
                 ("eps_rel", C.c_double), ("seed", C.c_uint64), ("slice_id", C.c_int32),
                 ("onsager", C.c_int32), ("damp_x", C.c_double), ("damp_s", C.c_double),
                 ("tau_x_floor", C.c_double), ("use_graph", C.c_int32), ("cnn_scale", C.c_int32),
-                ("tau_x0", C.c_double), ("truncate_z", C.c_int32)]
+                ("tau_x0", C.c_double), ("truncate_z", C.c_int32), ("storage", C.c_int32)]
 
 
 class Stats(C.Structure):

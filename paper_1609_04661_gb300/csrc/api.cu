@@ -54,6 +54,7 @@ static bool options_ok(const dgamp_ct_options* o) {
     if (!(o->tau_x0 > 0) || !std::isfinite(o->tau_x0)) return false;
     if (o->cnn_scale != 0 && o->cnn_scale != 1) return false;
     if (o->truncate_z != 0 && o->truncate_z != 1) return false;
+    if (o->storage != 0 && o->storage != 1) return false;
     return true;
 }
 
@@ -205,15 +206,16 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
         return DGAMP_CT_OK;
     };
     DGCT_TRY(mark());
-    DGCT_TRY(launch_project(pl, w.zraw, st));                          // Step 1: A x
+    const int bf = pl->opt.storage;                                      // BF16 sinograms / staged image
+    DGCT_TRY(launch_project(pl, w.zraw, st, bf));                      // Step 1: A x
     DGCT_TRY(mark());
-    DGCT_TRY(launch_filter(pl, w.zraw, w.z, st));                       //         H A x
+    DGCT_TRY(launch_filter(pl, w.zraw, w.z, st, bf));                   //         H A x
     DGCT_TRY(mark());
-    DGCT_TRY(launch_output_step(pl, w.z, w.y, w.s, 1, 1, 0.0, 0.0, nullptr, st));  // Step 2
+    DGCT_TRY(launch_output_step(pl, w.z, w.y, w.s, 1, 1, 0.0, 0.0, nullptr, st, bf));  // Step 2
     DGCT_TRY(mark());
-    DGCT_TRY(launch_filter(pl, w.s, w.hs, st));                         // Step 3: H s
+    DGCT_TRY(launch_filter(pl, w.s, w.hs, st, bf));                     // Step 3: H s
     DGCT_TRY(mark());
-    DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st));            //         r = x + tau_r A^T H s
+    DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st, bf));        //         r = x + tau_r A^T H s
     DGCT_TRY(mark());
     // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r
     DGCT_TRY(launch_probe_input(pl, 0, st, pl->opt.denoiser == 1 ? 1 : 0));
@@ -304,6 +306,7 @@ int dgamp_ct_default_options(dgamp_ct_options* o) {
     o->cnn_scale = 0;
     o->tau_x0 = 1.0;
     o->truncate_z = 0;
+    o->storage = 0;
     return DGAMP_CT_OK;
 }
 
@@ -533,7 +536,7 @@ static int solve_begin(dgamp_ct_plan_s* pl, const float* d_counts, double I0, cu
     DGCT_CUDA(cudaMemcpyAsync(w.y, d_counts, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
     DGCT_CUDA(cudaMemsetAsync(w.x, 0, N * sizeof(float), st));
     DGCT_CUDA(cudaMemsetAsync(w.s, 0, M * sizeof(float), st));
-    DGCT_TRY(launch_stage_image(pl, w.x, st));
+    DGCT_TRY(launch_stage_image(pl, w.x, st, pl->opt.storage));
     if (pl->opt.denoiser == 1) {
         // the network may have been used (and its workspace regrown) since the
         // graph was captured: make room again and re-capture if it moved

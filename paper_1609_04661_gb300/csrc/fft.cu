@@ -46,21 +46,22 @@ __device__ float2* fft_stockham(float2* a, float2* b, int P, const float2* __res
 }
 
 // ------------------------------------------------------------ H on views --
+template <typename T>
 __global__ void __launch_bounds__(512)
-k_filter_views(const float* in, float* out, int nv, int nd, int P,
+k_filter_views(const T* in, T* out, int nv, int nd, int P,
                const float* __restrict__ gain, const float2* __restrict__ tw) {
     extern __shared__ float2 smem[];
     float2* a = smem;
     float2* b = smem + P;
     const int va = 2 * blockIdx.x, vb = va + 1;
     const bool hasb = vb < nv;
-    const float* ra = in + (size_t)va * nd;
-    const float* rb = in + (size_t)vb * nd;
+    const T* ra = in + (size_t)va * nd;
+    const T* rb = in + (size_t)vb * nd;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         float2 v = make_float2(0.f, 0.f);
         if (i < nd) {
-            v.x = ra[i];
-            if (hasb) v.y = rb[i];
+            v.x = ldf(ra + i);
+            if (hasb) v.y = ldf(rb + i);
         }
         a[i] = v;
     }
@@ -75,12 +76,12 @@ k_filter_views(const float* in, float* out, int nv, int nd, int P,
     __syncthreads();
     r = fft_stockham(r, o, P, tw, 1.f);
     const float sc = 1.0f / (float)P;
-    float* wa = out + (size_t)va * nd;
-    float* wb = out + (size_t)vb * nd;
+    T* wa = out + (size_t)va * nd;
+    T* wb = out + (size_t)vb * nd;
     for (int i = threadIdx.x; i < nd; i += blockDim.x) {
         const float2 v = r[i];
-        wa[i] = v.x * sc;
-        if (hasb) wb[i] = v.y * sc;
+        stf(wa + i, v.x * sc);
+        if (hasb) stf(wb + i, v.y * sc);
     }
 }
 
@@ -94,8 +95,9 @@ k_filter_views(const float* in, float* out, int nv, int nd, int P,
 // added in a fixed order.
 constexpr int kTzOut = 128, kTzWarps = 8;
 
+template <typename T>
 __global__ void __launch_bounds__(32 * kTzWarps)
-k_filter_toeplitz(const float* in, float* out, int nd, const float* __restrict__ hx) {
+k_filter_toeplitz(const T* in, T* out, int nd, const float* __restrict__ hx) {
     extern __shared__ float sm[];
     float* zs = sm;                       // [nd]
     float* hs = sm + nd;                  // [2 nd - 1]
@@ -103,8 +105,8 @@ k_filter_toeplitz(const float* in, float* out, int nd, const float* __restrict__
     const int v = blockIdx.y;
     const int d0 = blockIdx.x * kTzOut;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const float* row = in + (size_t)v * nd;
-    for (int i = tid; i < nd; i += blockDim.x) zs[i] = row[i];
+    const T* row = in + (size_t)v * nd;
+    for (int i = tid; i < nd; i += blockDim.x) zs[i] = ldf(row + i);
     for (int i = tid; i < 2 * nd - 1; i += blockDim.x) hs[i] = hx[i];
     __syncthreads();
     const int dl = d0 + 4 * lane;          // this lane's first output
@@ -141,7 +143,7 @@ k_filter_toeplitz(const float* in, float* out, int nd, const float* __restrict__
         float t = 0.f;
 #pragma unroll
         for (int k = 0; k < kTzWarps; ++k) t += red[k * kTzOut + o];
-        out[(size_t)v * nd + d] = t;
+        stf(out + (size_t)v * nd + d, t);
     }
 }
 
@@ -149,24 +151,33 @@ static size_t toeplitz_smem(int nd) {
     return ((size_t)nd + 2 * nd - 1 + kTzWarps * kTzOut) * sizeof(float);
 }
 
-int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaStream_t st) {
+// bf = 1: in and out hold BF16 (a solve with storage = 1); sums in FP32 either way
+int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaStream_t st, int bf) {
     if (pl->filter_mode == 1) {
         // the block reads its whole input row first, so in == out needs a copy
         const float* src = in;
         if (in == out) {
-            DGCT_CUDA(cudaMemcpyAsync(pl->ws.zraw2, in, (size_t)pl->M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            DGCT_CUDA(cudaMemcpyAsync(pl->ws.zraw2, in, (size_t)pl->M * (bf ? 2 : 4), cudaMemcpyDeviceToDevice, st));
             src = pl->ws.zraw2;
         }
         dim3 grd((pl->nd + kTzOut - 1) / kTzOut, pl->nv);
-        k_filter_toeplitz<<<grd, 32 * kTzWarps, toeplitz_smem(pl->nd), st>>>(src, out, pl->nd, pl->ws.hx);
+        if (bf)
+            k_filter_toeplitz<bf16s><<<grd, 32 * kTzWarps, toeplitz_smem(pl->nd), st>>>((const bf16s*)src, (bf16s*)out,
+                                                                                        pl->nd, pl->ws.hx);
+        else
+            k_filter_toeplitz<float><<<grd, 32 * kTzWarps, toeplitz_smem(pl->nd), st>>>(src, out, pl->nd, pl->ws.hx);
         DGCT_LAUNCH_CHECK();
         return DGAMP_CT_OK;
     }
     const int P = pl->P;
     const size_t sm = (size_t)2 * P * sizeof(float2);
     const int thr = P >= 1024 ? 512 : (P / 2 >= 32 ? P / 2 : 32);
-    k_filter_views<<<(pl->nv + 1) / 2, thr, sm, st>>>(in, out, pl->nv, pl->nd, P, pl->ws.gain,
-                                                      pl->ws.tw);
+    if (bf)
+        k_filter_views<bf16s><<<(pl->nv + 1) / 2, thr, sm, st>>>((const bf16s*)in, (bf16s*)out, pl->nv, pl->nd, P,
+                                                                 pl->ws.gain, pl->ws.tw);
+    else
+        k_filter_views<float><<<(pl->nv + 1) / 2, thr, sm, st>>>(in, out, pl->nv, pl->nd, P, pl->ws.gain,
+                                                                 pl->ws.tw);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -207,7 +218,9 @@ int filter_autotune(dgamp_ct_plan_s* pl) {
 int toeplitz_set_smem_limit(int nd) {
     const size_t need = toeplitz_smem(nd);
     if (need > 48 * 1024)
-        DGCT_CUDA(cudaFuncSetAttribute(k_filter_toeplitz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+        DGCT_CUDA(cudaFuncSetAttribute(k_filter_toeplitz<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+    if (need > 48 * 1024)
+        DGCT_CUDA(cudaFuncSetAttribute(k_filter_toeplitz<bf16s>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
     return DGAMP_CT_OK;
 }
 
@@ -287,7 +300,8 @@ int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out,
 }
 
 int fft_set_smem_limits(int bytes) {
-    DGCT_CUDA(cudaFuncSetAttribute(k_filter_views, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    DGCT_CUDA(cudaFuncSetAttribute(k_filter_views<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    DGCT_CUDA(cudaFuncSetAttribute(k_filter_views<bf16s>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     DGCT_CUDA(cudaFuncSetAttribute(k_img_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     DGCT_CUDA(cudaFuncSetAttribute(k_img_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     DGCT_CUDA(cudaFuncSetAttribute(k_img_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));

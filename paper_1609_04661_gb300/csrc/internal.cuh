@@ -2,6 +2,7 @@
 // scalar block, and the small device helpers that several kernels share.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -107,6 +108,14 @@ struct dgamp_ct_plan_s {
 namespace dgct {
 
 // ---------------------------------------------------------------- helpers --
+// Storage of the solve's sinograms and staged images: float, or BF16 with
+// every sum in FP32 (option storage = 1).
+typedef __nv_bfloat16 bf16s;
+__device__ __forceinline__ float ldf(const float* p) { return *p; }
+__device__ __forceinline__ float ldf(const bf16s* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void stf(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stf(bf16s* p, float v) { *p = __float2bfloat16_rn(v); }
+
 __device__ __forceinline__ long long joseph_pos(const ViewConst& c, int d, int s) {
     return c.P0 + (long long)d * c.PDET + (long long)s * c.PSTEP;
 }
@@ -203,13 +212,14 @@ int fill_stats(const dgamp_ct_plan_s* pl, int iters, dgamp_ct_stats* stats);
 
 // ----------------------------------------------------------- launchers ----
 // joseph.cu
-int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t st);
-int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st);
+// bf = 1: the staged image XR/XC and the sinogram `sino` hold BF16 (solve with storage = 1)
+int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t st, int bf = 0);
+int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf = 0);
 int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
-                       float* out, int update, cudaStream_t st);
+                       float* out, int update, cudaStream_t st, int bf = 0);
 int launch_frobenius(dgamp_ct_plan_s* pl);
 // fft.cu
-int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaStream_t st);
+int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaStream_t st, int bf = 0);
 int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out, int inverse,
                          cudaStream_t st);
 int fft_set_smem_limits(int bytes);
@@ -218,7 +228,7 @@ int toeplitz_set_smem_limit(int nd);
 // output_step.cu
 int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y, float* s,
                        int use_prev, int from_scalars, double tau_p_arg, double logI0_arg,
-                       double* tau_s_out, cudaStream_t st);
+                       double* tau_s_out, cudaStream_t st, int bf = 0);
 // tv.cu
 int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st, int write_b = 0);
 int launch_absmax(const dgamp_ct_plan_s* pl, const float* r, cudaStream_t st);

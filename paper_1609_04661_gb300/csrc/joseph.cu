@@ -12,8 +12,9 @@
 namespace dgct {
 
 // ------------------------------------------------------------- staging ----
+template <typename T>
 __global__ void k_stage_image(const float* __restrict__ img, int n, int ldp,
-                              float* __restrict__ XR, float* __restrict__ XC) {
+                              T* __restrict__ XR, T* __restrict__ XC) {
     __shared__ float tile[32][33];
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
@@ -21,20 +22,38 @@ __global__ void k_stage_image(const float* __restrict__ img, int n, int ldp,
         float v = 0.f;
         if (iy < n && ix < n) {
             v = img[(size_t)iy * n + ix];
-            XR[(size_t)iy * ldp + kPad + ix] = v;
+            stf(XR + (size_t)iy * ldp + kPad + ix, v);
         }
         tile[j][threadIdx.x] = v;
     }
     __syncthreads();
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
         const int ix = bx + j, iy = by + threadIdx.x;
-        if (iy < n && ix < n) XC[(size_t)ix * ldp + kPad + iy] = tile[threadIdx.x][j];
+        if (iy < n && ix < n) stf(XC + (size_t)ix * ldp + kPad + iy, tile[threadIdx.x][j]);
+    }
+    // Guard cells of the lines that start or end in this block.  An FP32 and
+    // a BF16 staging share the same bytes, so the guards are rewritten each
+    // time rather than left from the allocation's zero fill.
+    const int gr = ldp - kPad - n;   // 4..7 cells on the right
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int t = threadIdx.x, iy = by + j, ix = bx + j;
+        if (iy < n) {
+            if (blockIdx.x == 0 && t < kPad) stf(XR + (size_t)iy * ldp + t, 0.f);
+            if (blockIdx.x == gridDim.x - 1 && t < gr) stf(XR + (size_t)iy * ldp + kPad + n + t, 0.f);
+        }
+        if (ix < n) {
+            if (blockIdx.y == 0 && t < kPad) stf(XC + (size_t)ix * ldp + t, 0.f);
+            if (blockIdx.y == gridDim.y - 1 && t < gr) stf(XC + (size_t)ix * ldp + kPad + n + t, 0.f);
+        }
     }
 }
 
-int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t st) {
+int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t st, int bf) {
     dim3 blk(32, 8), grd((pl->n + 31) / 32, (pl->n + 31) / 32);
-    k_stage_image<<<grd, blk, 0, st>>>(img, pl->n, pl->ldp, pl->ws.XR, pl->ws.XC);
+    if (bf)
+        k_stage_image<bf16s><<<grd, blk, 0, st>>>(img, pl->n, pl->ldp, (bf16s*)pl->ws.XR, (bf16s*)pl->ws.XC);
+    else
+        k_stage_image<float><<<grd, blk, 0, st>>>(img, pl->n, pl->ldp, pl->ws.XR, pl->ws.XC);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -62,9 +81,10 @@ __device__ __forceinline__ void step_range(float base, float a_step, int n, int&
 // rays read ~32-46 adjacent floats of one staged line per step.
 constexpr int kPjRays = 32, kPjSeg = 8;
 
+template <typename T>
 __global__ void __launch_bounds__(kPjRays * kPjSeg)
-k_project(const float* __restrict__ XR, const float* __restrict__ XC, int ldp, int n, int nd,
-          const ViewConst* __restrict__ vcs, float* __restrict__ sino) {
+k_project(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int n, int nd,
+          const ViewConst* __restrict__ vcs, T* __restrict__ sino) {
     __shared__ float red[kPjSeg][kPjRays];
     const int v = blockIdx.y;
     const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
@@ -72,7 +92,7 @@ k_project(const float* __restrict__ XR, const float* __restrict__ XC, int ldp, i
     const ViewConst c = vcs[v];
     float acc = 0.f;
     if (d < nd) {
-        const float* __restrict__ B = c.col ? XC : XR;
+        const T* __restrict__ B = c.col ? XC : XR;
         const float base = fmaf((float)d, c.a_det, c.a0);
         int s0, s1;
         step_range(base, c.a_step, n, s0, s1);
@@ -81,13 +101,13 @@ k_project(const float* __restrict__ XR, const float* __restrict__ XC, int ldp, i
         s1 = min(s1, seg * len + len - 1);
         if (s0 <= s1) {
             long long pos = joseph_pos(c, d, s0);
-            const float* __restrict__ line = B + (size_t)s0 * ldp + kPad;
+            const T* __restrict__ line = B + (size_t)s0 * ldp + kPad;
 #pragma unroll 4
             for (int s = s0; s <= s1; ++s, pos += c.PSTEP, line += ldp) {
                 int i0;
                 float f;
                 joseph_tap(pos, i0, f);
-                const float x0 = __ldg(line + i0), x1 = __ldg(line + i0 + 1);
+                const float x0 = ldf(line + i0), x1 = ldf(line + i0 + 1);
                 acc += fmaf(f, x1 - x0, x0);
             }
         }
@@ -98,13 +118,17 @@ k_project(const float* __restrict__ XR, const float* __restrict__ XC, int ldp, i
         float t = 0.f;
 #pragma unroll
         for (int k = 0; k < kPjSeg; ++k) t += red[k][lane];
-        sino[(size_t)v * nd + d] = t * c.w;
+        stf(sino + (size_t)v * nd + d, t * c.w);
     }
 }
 
-int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st) {
+int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf) {
     dim3 blk(kPjRays * kPjSeg), grd((pl->nd + kPjRays - 1) / kPjRays, pl->nv);
-    k_project<<<grd, blk, 0, st>>>(pl->ws.XR, pl->ws.XC, pl->ldp, pl->n, pl->nd, pl->ws.vc, sino);
+    if (bf)
+        k_project<bf16s><<<grd, blk, 0, st>>>((const bf16s*)pl->ws.XR, (const bf16s*)pl->ws.XC, pl->ldp, pl->n,
+                                              pl->nd, pl->ws.vc, (bf16s*)sino);
+    else
+        k_project<float><<<grd, blk, 0, st>>>(pl->ws.XR, pl->ws.XC, pl->ldp, pl->n, pl->nd, pl->ws.vc, sino);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -117,8 +141,9 @@ int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st) {
 // Step 3) and the running max |r| used by the MC step of Step 4.
 constexpr int kBpViews = 256;
 
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_backproject(const float* __restrict__ sino, int nv, int nd, int n,
+k_backproject(const T* __restrict__ sino, int nv, int nd, int n,
               const ViewConst* __restrict__ vcs, const float* __restrict__ x_in,
               float* __restrict__ out, int update, DevScalars* __restrict__ S) {
     __shared__ ViewConst svc[kBpViews];
@@ -167,9 +192,9 @@ k_backproject(const float* __restrict__ sino, int nv, int nd, int n,
             const int d2 = d1 - c.sg;
             const float w1 = (i1 == k) ? (1.f - f1) : ((i1 == k - 1) ? f1 : 0.f);
             const float w2 = (i1 == k && i2 == k - 1) ? f2 : 0.f;
-            const float* __restrict__ row = sino + (size_t)(v0 + vi) * nd;
-            const float v1 = (d1 >= 0 && d1 < nd) ? __ldg(row + d1) : 0.f;
-            const float v2 = (d2 >= 0 && d2 < nd) ? __ldg(row + d2) : 0.f;
+            const T* __restrict__ row = sino + (size_t)(v0 + vi) * nd;
+            const float v1 = (d1 >= 0 && d1 < nd) ? ldf(row + d1) : 0.f;
+            const float v2 = (d2 >= 0 && d2 < nd) ? ldf(row + d2) : 0.f;
             acc = fmaf(fmaf(w1, v1, w2 * v2), c.w, acc);
         }
     }
@@ -190,10 +215,14 @@ k_backproject(const float* __restrict__ sino, int nv, int nd, int n,
 }
 
 int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
-                       float* out, int update, cudaStream_t st) {
+                       float* out, int update, cudaStream_t st, int bf) {
     dim3 blk(32, 8), grd((pl->n + 31) / 32, (pl->n + 7) / 8);
-    k_backproject<<<grd, blk, 0, st>>>(sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in, out, update,
-                                       pl->ws.S);
+    if (bf)
+        k_backproject<bf16s><<<grd, blk, 0, st>>>((const bf16s*)sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in, out,
+                                                  update, pl->ws.S);
+    else
+        k_backproject<float><<<grd, blk, 0, st>>>(sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in, out, update,
+                                                  pl->ws.S);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }

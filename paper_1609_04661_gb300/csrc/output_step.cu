@@ -50,8 +50,9 @@ __device__ __forceinline__ float mode_delta(float p, float y, float tau_p, float
     return d;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_output_step(const float* z, const float* y, float* s, long long M, int use_prev,
+k_output_step(const T* z, const float* y, T* s, long long M, int use_prev,
               int from_scalars, double tau_p_arg, double logI0_arg, int onsager, float damp_s,
               int truncate, double N, DevScalars* S, double* partial, double* tau_s_out) {
     __shared__ double sm[32];
@@ -69,15 +70,16 @@ k_output_step(const float* z, const float* y, float* s, long long M, int use_pre
     unsigned capped = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M;
          i += (long long)gridDim.x * blockDim.x) {
-        const float sp = use_prev ? s[i] : 0.f;
-        const float p = onsager ? fmaf(-tau_p, sp, z[i]) : z[i];
+        const float sp = use_prev ? ldf(s + i) : 0.f;
+        const float zi = ldf(z + i);
+        const float p = onsager ? fmaf(-tau_p, sp, zi) : zi;
         const float yv = y[i];
         float d = mode_delta(p, yv, tau_p, inv_tp, logI0, capped);
         const bool clamp = truncate && p + d < 0.f;
         if (clamp) d = -p;
         float sv = d * inv_tp;
         if (damp_s != 1.f) sv = damp_s * sv + (1.f - damp_s) * sp;
-        s[i] = sv;
+        stf(s + i, sv);
         const float w = expf(logI0 - p - d);
         const float tsi = (clamp || isinf(w)) ? inv_tp : w / fmaf(tau_p, w, 1.f);
         acc += (double)tsi;
@@ -115,15 +117,20 @@ k_output_step(const float* z, const float* y, float* s, long long M, int use_pre
 
 int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y, float* s,
                        int use_prev, int from_scalars, double tau_p_arg, double logI0_arg,
-                       double* tau_s_out, cudaStream_t st) {
+                       double* tau_s_out, cudaStream_t st, int bf) {
     const long long M = pl->M;
     int blocks = (int)((M + 127) / 128);          // one element per thread, 128-thread blocks
     if (blocks > pl->max_partials) blocks = pl->max_partials;
     const int onsager = from_scalars ? pl->opt.onsager : 1;
     const float damp_s = from_scalars ? (float)pl->opt.damp_s : 1.f;
-    k_output_step<<<blocks, 128, 0, st>>>(z, y, s, M, use_prev, from_scalars, tau_p_arg, logI0_arg,
-                                          onsager, damp_s, pl->opt.truncate_z, (double)pl->N, pl->ws.S,
-                                          pl->ws.partial, tau_s_out);
+    if (bf)   // z and s in BF16 (a solve with storage = 1); the counts stay FP32
+        k_output_step<bf16s><<<blocks, 128, 0, st>>>((const bf16s*)z, y, (bf16s*)s, M, use_prev, from_scalars,
+                                                     tau_p_arg, logI0_arg, onsager, damp_s, pl->opt.truncate_z,
+                                                     (double)pl->N, pl->ws.S, pl->ws.partial, tau_s_out);
+    else
+        k_output_step<float><<<blocks, 128, 0, st>>>(z, y, s, M, use_prev, from_scalars, tau_p_arg, logI0_arg,
+                                                     onsager, damp_s, pl->opt.truncate_z, (double)pl->N, pl->ws.S,
+                                                     pl->ws.partial, tau_s_out);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -137,8 +144,8 @@ int launch_output_step_scratch(const float* z, const float* y, float* s, long lo
     long long blocks = (M + 255) / 256;
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
-    k_output_step<<<(int)blocks, 256, 0, st>>>(z, y, s, M, use_prev, 0, tau_p, logI0, 1, 1.f, 0, 0.0, S,
-                                               partial, tau_s_out);
+    k_output_step<float><<<(int)blocks, 256, 0, st>>>(z, y, s, M, use_prev, 0, tau_p, logI0, 1, 1.f, 0, 0.0, S,
+                                                      partial, tau_s_out);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }

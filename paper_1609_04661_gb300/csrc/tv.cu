@@ -94,11 +94,20 @@ int launch_absmax(const dgamp_ct_plan_s* pl, const float* r, cudaStream_t st) {
 }
 
 // ------------------------------------------- register-blocked Chambolle ----
+struct TvFinal;
+__device__ __forceinline__ void stage_store(float* base, int xbf, size_t idx, float v) {
+    if (xbf)
+        stf(reinterpret_cast<bf16s*>(base) + idx, v);
+    else
+        base[idx] = v;
+}
+
 struct TvFinal {
     float* x_out;          // D(r) (with damping against the old x in a solve)
     float* XR;             // staged copies for the next projection (nullable)
     float* XC;
     int ldp;
+    int xbf;               // staged copies in BF16 (a solve with storage = 1)
     float damp_x;
     int t_arg;             // probe iteration (0: from S)
     unsigned slice;
@@ -321,8 +330,8 @@ k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
                 float xo = xv;
                 if (F.solve_mode && F.damp_x != 1.f) xo = F.damp_x * xo + (1.f - F.damp_x) * F.x_out[o];
                 F.x_out[o] = xo;
-                if (F.XR) F.XR[(size_t)gi * F.ldp + kPad + gj] = xo;
-                if (F.XC) F.XC[(size_t)gj * F.ldp + kPad + gi] = xo;
+                if (F.XR) stage_store(F.XR, F.xbf, (size_t)gi * F.ldp + kPad + gj, xo);
+                if (F.XC) stage_store(F.XC, F.xbf, (size_t)gj * F.ldp + kPad + gi, xo);
             }
         }
     }
@@ -368,13 +377,13 @@ k_tv_final(const float* __restrict__ rbase, const float2* __restrict__ pfin, con
         if (NIMG == 2) acc = (double)bprobe[o] * (double)(xs[NIMG - 1] - xs[0]);
         if (F.solve_mode && F.damp_x != 1.f) xv = F.damp_x * xv + (1.f - F.damp_x) * F.x_out[o];
         F.x_out[o] = xv;
-        if (F.XR) F.XR[(size_t)gi * F.ldp + kPad + gj] = xv;
+        if (F.XR) stage_store(F.XR, F.xbf, (size_t)gi * F.ldp + kPad + gj, xv);
     }
     tile[ta][tb] = xv;
     if (F.XC) {
         __syncthreads();
         const int gj2 = blockIdx.x * TB + ta, gi2 = blockIdx.y * TB + tb;
-        if (gi2 < n && gj2 < n) F.XC[(size_t)gj2 * F.ldp + kPad + gi2] = tile[tb][ta];
+        if (gi2 < n && gj2 < n) stage_store(F.XC, F.xbf, (size_t)gj2 * F.ldp + kPad + gi2, tile[tb][ta]);
     }
     if (NIMG < 2) return;
     tv_divergence_finish(acc, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x, N, S, F, red, &am_last);
@@ -456,6 +465,7 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     F.XR = solve_mode ? pl->ws.XR : nullptr;
     F.XC = solve_mode ? pl->ws.XC : nullptr;
     F.ldp = pl->ldp;
+    F.xbf = solve_mode ? pl->opt.storage : 0;
     F.damp_x = (float)pl->opt.damp_x;
     F.t_arg = t_arg;
     F.slice = (unsigned)pl->opt.slice_id;
@@ -568,13 +578,13 @@ k_denoise_final(const float* __restrict__ dn, const float* __restrict__ bprobe, 
         xv = x1;
         if (F.solve_mode && F.damp_x != 1.f) xv = F.damp_x * xv + (1.f - F.damp_x) * F.x_out[o];
         F.x_out[o] = xv;
-        if (F.XR) F.XR[(size_t)gi * F.ldp + kPad + gj] = xv;
+        if (F.XR) stage_store(F.XR, F.xbf, (size_t)gi * F.ldp + kPad + gj, xv);
     }
     tile[ta][tb] = xv;
     if (F.XC) {
         __syncthreads();
         const int gj2 = blockIdx.x * TB + ta, gi2 = blockIdx.y * TB + tb;
-        if (gi2 < n && gj2 < n) F.XC[(size_t)gj2 * F.ldp + kPad + gi2] = tile[tb][ta];
+        if (gi2 < n && gj2 < n) stage_store(F.XC, F.xbf, (size_t)gj2 * F.ldp + kPad + gi2, tile[tb][ta]);
     }
     acc = block_sum(acc, red);
     const int nblk = gridDim.x * gridDim.y;
@@ -622,6 +632,7 @@ int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_ou
     F.XR = solve_mode ? pl->ws.XR : nullptr;
     F.XC = solve_mode ? pl->ws.XC : nullptr;
     F.ldp = pl->ldp;
+    F.xbf = solve_mode ? pl->opt.storage : 0;
     F.damp_x = (float)pl->opt.damp_x;
     F.t_arg = t_arg;
     F.slice = (unsigned)pl->opt.slice_id;

@@ -250,6 +250,12 @@ BATCHES = {
     # log10 I0 ~ U(4, 6), 10 ellipses + rectangle object each, 30 iterations
     "mixed64": dict(count=64, sides=(256, 384, 512), views=(32, 48, 64, 96, 128), log10_I0=(4.0, 6.0),
                     n_ellipses=10, with_rect=True, iters=30),
+    # 128 slices of 1024 x 1024, 90 views, 1449 bins, I0 = 1e5, 10 ellipses
+    # each.  Densities are halved (rho_max 0.01 per pixel): the same objects
+    # as the 512 x 512 workloads on a grid of half the pixel size, so that the
+    # line integrals (and the photon counts) span the same range.
+    "large128": dict(count=128, sides=(1024,), views=(90,), bins=1449, log10_I0=(5.0, 5.0),
+                     n_ellipses=10, with_rect=False, iters=30, rho_max=0.01),
 }
 
 
@@ -264,9 +270,10 @@ def make_batch(name: str = "mixed64", seed: int = 3000, with_mu: bool = False, c
     for k in range(k_total):
         n = int(rng.choice(spec["sides"]))
         nv = int(rng.choice(spec["views"]))
-        nd = int(math.ceil(1.42 * n))
+        nd = int(spec["bins"]) if "bins" in spec else int(math.ceil(1.42 * n))
         I0 = float(10.0 ** rng.uniform(*spec["log10_I0"]))
-        ph = random_phantom(n, spec["n_ellipses"], seed + 1 + k, with_rect=spec["with_rect"])
+        ph = random_phantom(n, spec["n_ellipses"], seed + 1 + k, rho_max=spec.get("rho_max", 0.02),
+                            with_rect=spec["with_rect"])
         z = analytic_sinogram(ph, view_angles(nv), nd)
         y = poisson_counts(z, I0, seed + 1 + k + 7)
         out.append(dict(name=f"{name}[{k}]", phantom=ph, mu=rasterise(ph, n) if with_mu else None, z=z, y=y,
