@@ -507,6 +507,7 @@ def run_gpu(args):
     N, M = plan.N, plan.M
     # compulsory bytes per launch (FP32 images/sinograms, float2 TV duals, two images in the denoiser)
     algo = {"project": 4 * (N + M), "filter_z": 8 * M, "output_step": 16 * M, "filter_s": 8 * M,
+            "sino_step": 20 * M,
             "backproject_update": 4 * (M + 2 * N), "probe_input": 8 * N,
             "tv_block_final": 8 * N + 16 * N + 16 * N}
     for kname in prof:

@@ -90,11 +90,12 @@ typedef struct {
                               line (Section 4.2); 1: restricted to z >= 0 (mode max(z0, 0);
                               where clamped s = -p/tau_p and tau_s_i = 1/tau_p) */
     int32_t  storage;      /* inside dgamp_ct_solve: 0 (default) FP32; 1 = the sinograms
-                              between projector, filter, output step and back-projector
-                              (A x, H A x, s, H s) and the image copies the projector reads
-                              are stored in BF16, every sum in FP32 and the GAMP scalars
-                              in FP64; the counts and the denoiser's images stay FP32.
-                              The single-step entry points always take FP32 buffers. */
+                              the solve keeps in memory (A x, s, H s, and H A x when the
+                              three-kernel form of the tuning runs) and the image copies
+                              the projector reads are stored in BF16, every sum in FP32
+                              and the GAMP scalars in FP64; the counts and the denoiser's
+                              images stay FP32.  The single-step entry points always take
+                              FP32 buffers. */
 } dgamp_ct_options;
 
 typedef struct {
@@ -144,12 +145,20 @@ int dgamp_ct_plan_info(dgamp_ct_plan_t plan, double* frob_sq, int32_t* fft_len);
                   kernel h = IFFT_P(g) (no wrap-around since P >= 2 n_det);
      tv_kb:       Chambolle steps per blocked TV launch, 1..10;
      tv_rows:     rows of the image region one TV block holds, 32, 64 or 128
-                  (the region is 64 columns wide).
+                  (the region is 64 columns wide);
+     sino_fused:  1 = inside dgamp_ct_solve, H A x, the output step and H s
+                  run as one kernel per pair of views (FFT form of H; needs
+                  P <= 8192), 0 = three kernels (H in filter_mode's form).
+                  The plan sets 1 where the geometry allows it.  filter_mode
+                  alone governs the single-step entry points.
    get: any pointer may be NULL.  set: a negative value keeps the current
-   choice; out-of-range values return INVALID_ARG.  Setting drops the
+   choice; out-of-range values return INVALID_ARG, sino_fused = 1 where the
+   geometry does not allow it UNSUPPORTED_GEOMETRY.  Setting drops the
    captured graph. */
-int dgamp_ct_get_tuning(dgamp_ct_plan_t plan, int32_t* filter_mode, int32_t* tv_kb, int32_t* tv_rows);
-int dgamp_ct_set_tuning(dgamp_ct_plan_t plan, int32_t filter_mode, int32_t tv_kb, int32_t tv_rows);
+int dgamp_ct_get_tuning(dgamp_ct_plan_t plan, int32_t* filter_mode, int32_t* tv_kb, int32_t* tv_rows,
+                        int32_t* sino_fused);
+int dgamp_ct_set_tuning(dgamp_ct_plan_t plan, int32_t filter_mode, int32_t tv_kb, int32_t tv_rows,
+                        int32_t sino_fused);
 
 /* z = A x (precond = 0) or z = Phi~ x = H A x (precond = 1); Eq. linCT and
    Algorithm 1, Step 1.  d_img [n][n] -> d_sino [n_views][n_det]. */
@@ -269,8 +278,10 @@ int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t plan, int32_t iters);
 /* Kernel-level timing of one Algorithm 1 iteration: enqueues the iteration's
    kernels one at a time on `stream` with a CUDA event before and after each,
    `reps` times, and writes the mean duration (ms) of each kernel to h_ms
-   (host array of `cap` doubles) in launch order: A x, H (z), output step,
-   H (s), A^T + update, probe input, k_tv Chambolle steps, final denoiser step.
+   (host array of `cap` doubles) in launch order: A x; H (z), output step,
+   H (s) -- one fused kernel when the tuning's sino_fused is 1; A^T + update,
+   probe input, then the denoiser: the blocked TV launches (the last one
+   final), or the learned network's pair of passes and its final step.
    *count receives the number of kernels.  The iterations run on the plan's
    current state (normally that of the last dgamp_ct_solve) and advance it.
    Synchronous. */

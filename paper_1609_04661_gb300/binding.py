@@ -96,8 +96,8 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_last_cuda_error": (C.c_int, []),
         "dgamp_ct_profile_iteration": (C.c_int, [vp, i32, C.POINTER(dbl), i32, C.POINTER(i32), vp]),
         "dgamp_ct_output_step_noalloc": (C.c_int, [vp, vp, vp, i64, dbl, dbl, vp, vp, vp]),
-        "dgamp_ct_get_tuning": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
-        "dgamp_ct_set_tuning": (C.c_int, [vp, i32, i32, i32]),
+        "dgamp_ct_get_tuning": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+        "dgamp_ct_set_tuning": (C.c_int, [vp, i32, i32, i32, i32]),
         "dgamp_ct_cnn_create": (C.c_int, [i32, C.c_uint64, C.POINTER(vp)]),
         "dgamp_ct_cnn_destroy": (None, [vp]),
         "dgamp_ct_cnn_num_params": (i64, [vp]),
@@ -219,13 +219,16 @@ class Plan:
 
     def tuning(self):
         """The plan-time choices: {"filter_mode": 0 FFT | 1 Toeplitz, "tv_kb": steps per TV launch,
-        "tv_rows": rows of a TV block's region}."""
-        fm, kb, rows = C.c_int32(), C.c_int32(), C.c_int32()
-        _check(self._lib.dgamp_ct_get_tuning(self._h, C.byref(fm), C.byref(kb), C.byref(rows)), "get_tuning")
-        return {"filter_mode": fm.value, "tv_kb": kb.value, "tv_rows": rows.value}
+        "tv_rows": rows of a TV block's region, "sino_fused": 1 if the solve runs H A x, the output
+        step and H s as one kernel}."""
+        fm, kb, rows, fu = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(self._lib.dgamp_ct_get_tuning(self._h, C.byref(fm), C.byref(kb), C.byref(rows), C.byref(fu)),
+               "get_tuning")
+        return {"filter_mode": fm.value, "tv_kb": kb.value, "tv_rows": rows.value, "sino_fused": fu.value}
 
-    def set_tuning(self, filter_mode: int = -1, tv_kb: int = -1, tv_rows: int = -1):
-        _check(self._lib.dgamp_ct_set_tuning(self._h, int(filter_mode), int(tv_kb), int(tv_rows)), "set_tuning")
+    def set_tuning(self, filter_mode: int = -1, tv_kb: int = -1, tv_rows: int = -1, sino_fused: int = -1):
+        _check(self._lib.dgamp_ct_set_tuning(self._h, int(filter_mode), int(tv_kb), int(tv_rows), int(sino_fused)),
+               "set_tuning")
 
     def set_options(self, **options):
         o = self.options
@@ -336,7 +339,8 @@ class Plan:
         cnt = C.c_int32()
         _check(self._lib.dgamp_ct_profile_iteration(self._h, int(reps), arr, cap, C.byref(cnt), _stream()),
                "dgamp_ct_profile_iteration")
-        names = ["project", "filter_z", "output_step", "filter_s", "backproject_update", "probe_input"]
+        sino = ["sino_step"] if self.tuning()["sino_fused"] else ["filter_z", "output_step", "filter_s"]
+        names = ["project"] + sino + ["backproject_update", "probe_input"]
         if self.options.denoiser == 1:
             names += ["cnn_pair", "denoise_final"]
         else:

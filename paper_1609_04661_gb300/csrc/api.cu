@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -122,8 +123,8 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_TRY(dalloc(&w.log, (size_t)kMaxIters));
     DGCT_TRY(dalloc(&w.vc, (size_t)pl->nv));
     DGCT_TRY(dalloc(&w.gain, (size_t)pl->P));
-    DGCT_TRY(dalloc(&w.tw, (size_t)pl->P / 2));
-    DGCT_TRY(dalloc(&w.tw2, (size_t)pl->m2 / 2));
+    DGCT_TRY(dalloc(&w.tw, (size_t)pl->P));
+    DGCT_TRY(dalloc(&w.tw2, (size_t)pl->m2));
     DGCT_TRY(dalloc(&w.hx, (size_t)2 * pl->nd));
     DGCT_TRY(dalloc(&w.zraw2, M));
     DGCT_TRY(dalloc(&w.scratch_d, (size_t)(pl->nd + 1) + 2 * pl->nd + pl->nv + (size_t)pl->nv * pl->nd));
@@ -156,8 +157,8 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_CUDA(cudaMemcpy(w.gain, g.data(), P * sizeof(float), cudaMemcpyHostToDevice));
     const double two_pi = 6.283185307179586476925286766559;
     auto twiddles = [&](int L, float2* dst) -> int {
-        std::vector<float2> t(L / 2);
-        for (int k = 0; k < L / 2; ++k)
+        std::vector<float2> t(L);
+        for (int k = 0; k < L; ++k)
             t[k] = make_float2((float)std::cos(two_pi * k / L), (float)std::sin(two_pi * k / L));
         DGCT_CUDA(cudaMemcpy(dst, t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice));
         return DGAMP_CT_OK;
@@ -188,7 +189,19 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     const int smem_need = 2 * (P > pl->m2 ? P : pl->m2) * (int)sizeof(float2);
     DGCT_TRY(fft_set_smem_limits(smem_need > 48 * 1024 ? smem_need : 48 * 1024));
     DGCT_TRY(toeplitz_set_smem_limit(pl->nd));
+    DGCT_TRY(sino_step_set_smem_limit(pl));
     DGCT_TRY(filter_autotune(pl));
+    pl->sino_fused = sino_step_eligible(pl) ? 1 : 0;
+    return DGAMP_CT_OK;
+}
+
+int raise_smem_limit(const void* kernel, int bytes) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa;
+    DGCT_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    if (fa.maxDynamicSharedSizeBytes >= bytes) return DGAMP_CT_OK;
+    DGCT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     return DGAMP_CT_OK;
 }
 
@@ -209,12 +222,17 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
     const int bf = pl->opt.storage;                                      // BF16 sinograms / staged image
     DGCT_TRY(launch_project(pl, w.zraw, st, bf));                      // Step 1: A x
     DGCT_TRY(mark());
-    DGCT_TRY(launch_filter(pl, w.zraw, w.z, st, bf));                   //         H A x
-    DGCT_TRY(mark());
-    DGCT_TRY(launch_output_step(pl, w.z, w.y, w.s, 1, 1, 0.0, 0.0, nullptr, st, bf));  // Step 2
-    DGCT_TRY(mark());
-    DGCT_TRY(launch_filter(pl, w.s, w.hs, st, bf));                     // Step 3: H s
-    DGCT_TRY(mark());
+    if (pl->sino_fused) {
+        DGCT_TRY(launch_sino_step(pl, st, bf));                         // H A x, Step 2, H s
+        DGCT_TRY(mark());
+    } else {
+        DGCT_TRY(launch_filter(pl, w.zraw, w.z, st, bf));               //         H A x
+        DGCT_TRY(mark());
+        DGCT_TRY(launch_output_step(pl, w.z, w.y, w.s, 1, 1, 0.0, 0.0, nullptr, st, bf));  // Step 2
+        DGCT_TRY(mark());
+        DGCT_TRY(launch_filter(pl, w.s, w.hs, st, bf));                 // Step 3: H s
+        DGCT_TRY(mark());
+    }
     DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st, bf));        //         r = x + tau_r A^T H s
     DGCT_TRY(mark());
     // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r
@@ -239,15 +257,17 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
 
 // kernels one iteration launches
 static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
-    if (pl->opt.denoiser == 1 && pl->cnn) return 6 + cnn_launches_per_pair(pl->cnn) + 1;
-    return 6 + tv_num_launches(pl, 1, 0.0);
+    const int sino = pl->sino_fused ? 1 : 3;        // H A x, output step, H s
+    if (pl->opt.denoiser == 1 && pl->cnn) return sino + 3 + cnn_launches_per_pair(pl->cnn) + 1;
+    return sino + 3 + tv_num_launches(pl, 1, 0.0);
 }
 
 // timed segments of one iteration (dgamp_ct_profile_iteration): every kernel,
 // except that the learned denoiser's launches form one segment
 static int segments_per_iteration(const dgamp_ct_plan_s* pl) {
-    if (pl->opt.denoiser == 1 && pl->cnn) return 8;
-    return 6 + tv_num_launches(pl, 1, 0.0);
+    const int sino = pl->sino_fused ? 1 : 3;
+    if (pl->opt.denoiser == 1 && pl->cnn) return sino + 5;
+    return sino + 3 + tv_num_launches(pl, 1, 0.0);
 }
 
 static void drop_graph(dgamp_ct_plan_s* pl) {
@@ -392,20 +412,25 @@ int dgamp_ct_plan_info(dgamp_ct_plan_t pl, double* frob_sq, int32_t* fft_len) {
     return DGAMP_CT_OK;
 }
 
-int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, int32_t* filter_mode, int32_t* tv_kb, int32_t* tv_rows) {
+int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, int32_t* filter_mode, int32_t* tv_kb, int32_t* tv_rows,
+                        int32_t* sino_fused) {
     if (!pl) return DGAMP_CT_ERR_INVALID_ARG;
     if (filter_mode) *filter_mode = pl->filter_mode;
     if (tv_kb) *tv_kb = pl->tv_kb;
     if (tv_rows) *tv_rows = pl->tv_rows;
+    if (sino_fused) *sino_fused = pl->sino_fused;
     return DGAMP_CT_OK;
 }
 
-int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, int32_t filter_mode, int32_t tv_kb, int32_t tv_rows) {
-    if (!pl || filter_mode > 1 || tv_kb > 10 || tv_kb == 0) return DGAMP_CT_ERR_INVALID_ARG;
+int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, int32_t filter_mode, int32_t tv_kb, int32_t tv_rows,
+                        int32_t sino_fused) {
+    if (!pl || filter_mode > 1 || tv_kb > 10 || tv_kb == 0 || sino_fused > 1) return DGAMP_CT_ERR_INVALID_ARG;
     if (tv_rows >= 0 && tv_rows != 32 && tv_rows != 64 && tv_rows != 128) return DGAMP_CT_ERR_INVALID_ARG;
+    if (sino_fused == 1 && !sino_step_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (filter_mode >= 0) pl->filter_mode = filter_mode;
     if (tv_kb > 0) pl->tv_kb = tv_kb;
     if (tv_rows > 0) pl->tv_rows = tv_rows;
+    if (sino_fused >= 0) pl->sino_fused = sino_fused;
     drop_graph(pl);
     return DGAMP_CT_OK;
 }

@@ -8,42 +8,14 @@
 //    with the radial gain applied between the forward and inverse column
 //    transforms, and inverse row FFTs.  It runs once per solve.
 //
-// The transform is a radix-2 Stockham autosort FFT (natural order in and
-// out, ping-pong between two shared-memory buffers): stage Ns (1, 2, 4, ...)
-// combines a[j] and a[j + P/2] with the twiddle exp(-+ 2 pi i (j mod Ns)/(2 Ns))
-// into b[2 (j - j mod Ns) + j mod Ns] and the same index + Ns.
-#include "internal.cuh"
+// The transform (fft_device.cuh) is a Stockham autosort FFT with radix-8
+// stages, in shared memory.
+#include "fft_device.cuh"
 
 namespace dgct {
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// tw[t] = (cos(2 pi t / P), sin(2 pi t / P)), t < P/2.  dir = -1 forward, +1 inverse.
-__device__ float2* fft_stockham(float2* a, float2* b, int P, const float2* __restrict__ tw,
-                                float dir) {
-    const int half = P >> 1;
-    const int nthr = blockDim.x;
-    for (int Ns = 1; Ns < P; Ns <<= 1) {
-        const int tstride = half / Ns;
-        for (int j = threadIdx.x; j < half; j += nthr) {
-            const int k = j & (Ns - 1);
-            float2 w = __ldg(tw + k * tstride);
-            w.y *= dir;
-            const float2 v0 = a[j];
-            const float2 t = cmul(a[j + half], w);
-            const int o = ((j - k) << 1) + k;
-            b[o] = make_float2(v0.x + t.x, v0.y + t.y);
-            b[o + Ns] = make_float2(v0.x - t.x, v0.y - t.y);
-        }
-        __syncthreads();
-        float2* tmp = a;
-        a = b;
-        b = tmp;
-    }
-    return a;
-}
+// one thread per radix-8 butterfly, 32 to 512 threads
+static int fft_threads(int P) { return P / 8 < 32 ? 32 : (P / 8 > 512 ? 512 : P / 8); }
 
 // ------------------------------------------------------------ H on views --
 template <typename T>
@@ -171,7 +143,7 @@ int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaSt
     }
     const int P = pl->P;
     const size_t sm = (size_t)2 * P * sizeof(float2);
-    const int thr = P >= 1024 ? 512 : (P / 2 >= 32 ? P / 2 : 32);
+    const int thr = fft_threads(P);
     if (bf)
         k_filter_views<bf16s><<<(pl->nv + 1) / 2, thr, sm, st>>>((const bf16s*)in, (bf16s*)out, pl->nv, pl->nd, P,
                                                                  pl->ws.gain, pl->ws.tw);
@@ -217,10 +189,8 @@ int filter_autotune(dgamp_ct_plan_s* pl) {
 
 int toeplitz_set_smem_limit(int nd) {
     const size_t need = toeplitz_smem(nd);
-    if (need > 48 * 1024)
-        DGCT_CUDA(cudaFuncSetAttribute(k_filter_toeplitz<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
-    if (need > 48 * 1024)
-        DGCT_CUDA(cudaFuncSetAttribute(k_filter_toeplitz<bf16s>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+    DGCT_TRY(raise_smem_limit((const void*)k_filter_toeplitz<float>, (int)need));
+    DGCT_TRY(raise_smem_limit((const void*)k_filter_toeplitz<bf16s>, (int)need));
     return DGAMP_CT_OK;
 }
 
@@ -287,7 +257,7 @@ int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out,
                          cudaStream_t st) {
     const int n = pl->n, m = pl->m2;
     const size_t sm = (size_t)2 * m * sizeof(float2);
-    const int thr = m >= 1024 ? 512 : (m / 2 >= 32 ? m / 2 : 32);
+    const int thr = fft_threads(m);
     const float f0 = 1.0f / (2.0f * (float)pl->P);
     k_img_rows_fwd<<<n, thr, sm, st>>>(in, n, m, pl->ws.tw2, pl->ws.fft2d);
     DGCT_LAUNCH_CHECK();
@@ -300,11 +270,11 @@ int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out,
 }
 
 int fft_set_smem_limits(int bytes) {
-    DGCT_CUDA(cudaFuncSetAttribute(k_filter_views<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    DGCT_CUDA(cudaFuncSetAttribute(k_filter_views<bf16s>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    DGCT_CUDA(cudaFuncSetAttribute(k_img_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    DGCT_CUDA(cudaFuncSetAttribute(k_img_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    DGCT_CUDA(cudaFuncSetAttribute(k_img_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    DGCT_TRY(raise_smem_limit((const void*)k_filter_views<float>, bytes));
+    DGCT_TRY(raise_smem_limit((const void*)k_filter_views<bf16s>, bytes));
+    DGCT_TRY(raise_smem_limit((const void*)k_img_rows_fwd, bytes));
+    DGCT_TRY(raise_smem_limit((const void*)k_img_cols, bytes));
+    DGCT_TRY(raise_smem_limit((const void*)k_img_rows_inv, bytes));
     return DGAMP_CT_OK;
 }
 

@@ -75,8 +75,8 @@ struct Workspace {
     float* gain = nullptr;         // [P]
     float* hx = nullptr;           // [2 n_det - 1]  H's kernel h[|m|], m = -(n_det-1)..n_det-1
     float* zraw2 = nullptr;        // [M]  copy for in-place Toeplitz filtering
-    float2* tw = nullptr;          // [P/2]   twiddles exp(-2 pi i k / P)
-    float2* tw2 = nullptr;         // [n]     twiddles of length 2n
+    float2* tw = nullptr;          // [P]     twiddles exp(2 pi i k / P)
+    float2* tw2 = nullptr;         // [m2]    twiddles exp(2 pi i k / m2)
     double* scratch_d = nullptr;   // plan-time FP64 scratch
     float* b = nullptr;            // the iteration's probe b (Eq. MC_SURE) [n][n]
 };
@@ -98,6 +98,7 @@ struct dgamp_ct_plan_s {
     int tv_kb = 5;                         // Chambolle steps per blocked TV launch
     int tv_rows = 64;                      // rows of a blocked TV region (64 or 128)
     int filter_mode = 0;                   // H by 0: FFT, 1: Toeplitz product (plan-time choice)
+    int sino_fused = 0;                    // solve: H A x, output step, H s in one kernel (k_sino_step)
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;   // stream the graph was captured for (identity only)
@@ -220,6 +221,13 @@ int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float
 int launch_frobenius(dgamp_ct_plan_s* pl);
 // fft.cu
 int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaStream_t st, int bf = 0);
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`, never
+// lowering it: the limit belongs to the kernel in the whole context, and a
+// plan made earlier may launch it with more.
+int raise_smem_limit(const void* kernel, int bytes);
+bool sino_step_eligible(const dgamp_ct_plan_s* pl);
+int sino_step_set_smem_limit(const dgamp_ct_plan_s* pl);
+int launch_sino_step(const dgamp_ct_plan_s* pl, cudaStream_t st, int bf);
 int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out, int inverse,
                          cudaStream_t st);
 int fft_set_smem_limits(int bytes);

@@ -1,0 +1,143 @@
+// The sinogram part of one iteration as one kernel (Algorithm 1, Steps 1-3
+// between the projector and the back-projector):
+//   z = H (A x)            detector-axis preconditioner, Section 2.4
+//   s, tau_s_i             Poisson output step, Section 4.2 / Appendix A
+//   H s                    the adjoint side, H being symmetric
+// One block takes two views packed as the real and imaginary parts of one
+// complex line (the gain is real and even, so one FFT pair filters both), as
+// the stand-alone filter kernel does.  z stays in shared memory; the
+// twiddle table is staged there once for the four transforms; s is written
+// for the next iteration and, rounded as stored, filtered in place.  tau_s
+// is reduced as in the stand-alone output step (the last block finishes it
+// and forms tau_r).  This replaces three launches, two round trips of a
+// sinogram through L2, and the per-stage twiddle loads from global memory.
+#include "fft_device.cuh"
+#include "output_device.cuh"
+
+namespace dgct {
+
+constexpr int kSinoThreads = 512;
+constexpr int kSinoMaxP = 8192;       // 3 P complex values of shared memory: 192 KB
+
+// the value a store of v into T and a load back give
+__device__ __forceinline__ float as_stored(float v, const float*) { return v; }
+__device__ __forceinline__ float as_stored(float v, const bf16s*) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+template <typename T>
+__global__ void __launch_bounds__(kSinoThreads)
+k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __restrict__ hs, int nv, int nd,
+            int P, const float* __restrict__ gain, const float2* __restrict__ tw_g, long long M, double N,
+            int onsager, float damp_s, int truncate, DevScalars* S, double* partial) {
+    extern __shared__ float2 smem[];
+    float2* a = smem;                 // [P]
+    float2* b = smem + P;             // [P]
+    float2* tw = smem + 2 * P;        // [P]
+    __shared__ double sm[32];
+    __shared__ float s_tp, s_inv, s_logI0;
+    const int va = 2 * blockIdx.x, vb = va + 1;
+    const bool hasb = vb < nv;
+    if (threadIdx.x == 0) {
+        const double tp = S->frob2 * S->tau_x / (double)M;      // Step 2: tau_p
+        s_tp = (float)tp;
+        s_inv = (float)(1.0 / tp);
+        s_logI0 = (float)S->logI0;
+    }
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        tw[i] = tw_g[i];
+        float2 v = make_float2(0.f, 0.f);
+        if (i < nd) {
+            v.x = ldf(zraw + (size_t)va * nd + i);
+            if (hasb) v.y = ldf(zraw + (size_t)vb * nd + i);
+        }
+        a[i] = v;
+    }
+    __syncthreads();
+    // z = H A x; the 1/P of the inverse transform is folded into the gain
+    // (a power of two: the same rounding as scaling afterwards)
+    const float invP = 1.0f / (float)P;
+    float2* r = fft_stockham(a, b, P, tw, -1.f);
+    float2* o = (r == a) ? b : a;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const float g = __ldg(gain + i) * invP;
+        r[i] = make_float2(r[i].x * g, r[i].y * g);
+    }
+    __syncthreads();
+    r = fft_stockham(r, o, P, tw, 1.f);
+    o = (r == a) ? b : a;
+
+    // output step on both views; s (as stored) goes into o, zero-padded
+    const float tau_p = s_tp, inv_tp = s_inv, logI0 = s_logI0;
+    for (int i = nd + threadIdx.x; i < P; i += blockDim.x) o[i] = make_float2(0.f, 0.f);
+    double acc = 0.0;
+    unsigned capped = 0;
+    const int ne = hasb ? 2 * nd : nd;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const bool isb = e >= nd;
+        const int d = isb ? e - nd : e;
+        const size_t gi = (size_t)(isb ? vb : va) * nd + d;
+        const float sp = ldf(s + gi);
+        float sv;
+        acc += (double)output_element(isb ? r[d].y : r[d].x, sp, y[gi], tau_p, inv_tp, logI0, onsager, damp_s,
+                                      truncate, capped, sv);
+        stf(s + gi, sv);
+        const float sq = as_stored(sv, s);
+        if (!hasb)
+            o[d] = make_float2(sq, 0.f);
+        else if (isb)
+            o[d].y = sq;
+        else
+            o[d].x = sq;
+    }
+    __syncthreads();
+    // H s
+    float2* q = fft_stockham(o, r, P, tw, -1.f);
+    float2* q2 = (q == o) ? r : o;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const float g = __ldg(gain + i) * invP;
+        q[i] = make_float2(q[i].x * g, q[i].y * g);
+    }
+    __syncthreads();
+    q = fft_stockham(q, q2, P, tw, 1.f);
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+        stf(hs + (size_t)va * nd + i, q[i].x);
+        if (hasb) stf(hs + (size_t)vb * nd + i, q[i].y);
+    }
+    finish_tau_s(acc, capped, M, N, 1, S, partial, nullptr, sm);
+}
+
+bool sino_step_eligible(const dgamp_ct_plan_s* pl) {
+    return pl->P <= kSinoMaxP && (pl->nv + 1) / 2 <= pl->max_partials;
+}
+
+int sino_step_set_smem_limit(const dgamp_ct_plan_s* pl) {
+    if (!sino_step_eligible(pl)) return DGAMP_CT_OK;
+    // set even at or below 48 KB: the static shared memory of the reduction
+    // comes on top of the dynamic part
+    const int bytes = 3 * pl->P * (int)sizeof(float2);
+    DGCT_TRY(raise_smem_limit((const void*)k_sino_step<float>, bytes));
+    DGCT_TRY(raise_smem_limit((const void*)k_sino_step<bf16s>, bytes));
+    return DGAMP_CT_OK;
+}
+
+// z = H zraw, the output step into s (s_prev in, damped s out), hs = H s;
+// bf = 1: the three sinograms in BF16 (counts stay FP32)
+int launch_sino_step(const dgamp_ct_plan_s* pl, cudaStream_t st, int bf) {
+    if (!sino_step_eligible(pl)) return DGAMP_CT_ERR_INVALID_ARG;
+    const Workspace& w = pl->ws;
+    const int grid = (pl->nv + 1) / 2;
+    const size_t sm = (size_t)3 * pl->P * sizeof(float2);
+    const float damp_s = (float)pl->opt.damp_s;
+    if (bf)
+        k_sino_step<bf16s><<<grid, kSinoThreads, sm, st>>>((const bf16s*)w.zraw, w.y, (bf16s*)w.s, (bf16s*)w.hs,
+                                                           pl->nv, pl->nd, pl->P, w.gain, w.tw, pl->M,
+                                                           (double)pl->N, pl->opt.onsager, damp_s,
+                                                           pl->opt.truncate_z, w.S, w.partial);
+    else
+        k_sino_step<float><<<grid, kSinoThreads, sm, st>>>(w.zraw, w.y, w.s, w.hs, pl->nv, pl->nd, pl->P, w.gain,
+                                                           w.tw, pl->M, (double)pl->N, pl->opt.onsager, damp_s,
+                                                           pl->opt.truncate_z, w.S, w.partial);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+}  // namespace dgct
