@@ -567,7 +567,7 @@ def run_gpu(args):
                 "clocks": clocks, "gpu_launches": int(args.steps * plan.solve_launches(T)),
                 "psnr_db": psnr,
                 "a_plus_at_gbs": a_at_bytes / (a_at_ms * 1e-3) / 1e9,
-                "iteration_ms": iter_ms, "kernel_ms": prof, "kernel_share": shares,
+                "iteration_ms": iter_ms, "tuning": tun, "kernel_ms": prof, "kernel_share": shares,
                 "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned, "batched": batched, "batched_learned": batched_learned, "large_bf16": c5,
                 "ablation": ablation}
         print(json.dumps(line), flush=True)

@@ -139,26 +139,31 @@ int dgamp_ct_set_options(dgamp_ct_plan_t plan, const dgamp_ct_options* opt);
 /* Scalars of the plan: ||Phi~||_F^2 (FP64) and the FFT length P. */
 int dgamp_ct_plan_info(dgamp_ct_plan_t plan, double* frob_sq, int32_t* fft_len);
 
-/* Implementation choices dgamp_ct_plan makes by timing on the plan's
-   geometry (they change speed, not the operator):
-     filter_mode: 0 = H by FFT, 1 = H as a Toeplitz product with the same
-                  kernel h = IFFT_P(g) (no wrap-around since P >= 2 n_det);
-     tv_kb:       Chambolle steps per blocked TV launch, 1..10;
-     tv_rows:     rows of the image region one TV block holds, 32, 64 or 128
-                  (the region is 64 columns wide);
-     sino_fused:  1 = inside dgamp_ct_solve, H A x, the output step and H s
-                  run as one kernel per pair of views (FFT form of H; needs
-                  P <= 8192), 0 = three kernels (H in filter_mode's form).
-                  The plan sets 1 where the geometry allows it.  filter_mode
-                  alone governs the single-step entry points.
-   get: any pointer may be NULL.  set: a negative value keeps the current
-   choice; out-of-range values return INVALID_ARG, sino_fused = 1 where the
-   geometry does not allow it UNSUPPORTED_GEOMETRY.  Setting drops the
-   captured graph. */
-int dgamp_ct_get_tuning(dgamp_ct_plan_t plan, int32_t* filter_mode, int32_t* tv_kb, int32_t* tv_rows,
-                        int32_t* sino_fused);
-int dgamp_ct_set_tuning(dgamp_ct_plan_t plan, int32_t filter_mode, int32_t tv_kb, int32_t tv_rows,
-                        int32_t sino_fused);
+/* Implementation choices of a plan (they change speed, not the operator);
+   dgamp_ct_plan makes them by timing on the plan's geometry.  */
+typedef struct {
+    int32_t filter_mode;  /* 0 = H by FFT, 1 = H as a Toeplitz product with the same
+                             kernel h = IFFT_P(g) (no wrap-around since P >= 2 n_det) */
+    int32_t tv_kb;        /* Chambolle steps per blocked TV launch, 1..10 */
+    int32_t tv_rows;      /* rows of the image region one TV block holds: 32, 64 or 128
+                             (the region is 64 columns wide) */
+    int32_t sino_fused;   /* 1 = inside dgamp_ct_solve, H A x, the output step and H s run
+                             as one kernel per pair of views (FFT form of H; needs
+                             P <= 8192); 0 = three kernels, H in filter_mode's form.  The
+                             plan sets 1 where the geometry allows it; filter_mode alone
+                             governs the single-step entry points */
+    int32_t bp_mode;      /* A^T: 0 = pixel-driven gather (each pixel finds the <= 2 rays
+                             of a view that tap it), 1 = ray-driven over 16 x 16 image
+                             tiles with per-warp shared-memory accumulators.  Both are the
+                             exact transpose of the projector and deterministic */
+} dgamp_ct_tuning;
+
+/* get: writes the plan's choices.  set: fields < 0 keep the current choice;
+   out-of-range values return INVALID_ARG, sino_fused = 1 where the geometry
+   does not allow it UNSUPPORTED_GEOMETRY (nothing is changed then).  Setting
+   drops the captured graph. */
+int dgamp_ct_get_tuning(dgamp_ct_plan_t plan, dgamp_ct_tuning* out);
+int dgamp_ct_set_tuning(dgamp_ct_plan_t plan, const dgamp_ct_tuning* tuning);
 
 /* z = A x (precond = 0) or z = Phi~ x = H A x (precond = 1); Eq. linCT and
    Algorithm 1, Step 1.  d_img [n][n] -> d_sino [n_views][n_det]. */

@@ -47,6 +47,12 @@ class Geometry(C.Structure):
                 ("angles", C.POINTER(C.c_double))]
 
 
+class Tuning(C.Structure):
+    """dgamp_ct_tuning."""
+    _fields_ = [("filter_mode", C.c_int32), ("tv_kb", C.c_int32), ("tv_rows", C.c_int32),
+                ("sino_fused", C.c_int32), ("bp_mode", C.c_int32)]
+
+
 class Options(C.Structure):
     _fields_ = [("denoiser", C.c_int32), ("k_tv", C.c_int32), ("c_tv", C.c_double),
                 ("eps_rel", C.c_double), ("seed", C.c_uint64), ("slice_id", C.c_int32),
@@ -96,8 +102,8 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_last_cuda_error": (C.c_int, []),
         "dgamp_ct_profile_iteration": (C.c_int, [vp, i32, C.POINTER(dbl), i32, C.POINTER(i32), vp]),
         "dgamp_ct_output_step_noalloc": (C.c_int, [vp, vp, vp, i64, dbl, dbl, vp, vp, vp]),
-        "dgamp_ct_get_tuning": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
-        "dgamp_ct_set_tuning": (C.c_int, [vp, i32, i32, i32, i32]),
+        "dgamp_ct_get_tuning": (C.c_int, [vp, C.POINTER(Tuning)]),
+        "dgamp_ct_set_tuning": (C.c_int, [vp, C.POINTER(Tuning)]),
         "dgamp_ct_cnn_create": (C.c_int, [i32, C.c_uint64, C.POINTER(vp)]),
         "dgamp_ct_cnn_destroy": (None, [vp]),
         "dgamp_ct_cnn_num_params": (i64, [vp]),
@@ -218,17 +224,22 @@ class Plan:
         return self.n_views * self.n_det
 
     def tuning(self):
-        """The plan-time choices: {"filter_mode": 0 FFT | 1 Toeplitz, "tv_kb": steps per TV launch,
-        "tv_rows": rows of a TV block's region, "sino_fused": 1 if the solve runs H A x, the output
-        step and H s as one kernel}."""
-        fm, kb, rows, fu = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
-        _check(self._lib.dgamp_ct_get_tuning(self._h, C.byref(fm), C.byref(kb), C.byref(rows), C.byref(fu)),
-               "get_tuning")
-        return {"filter_mode": fm.value, "tv_kb": kb.value, "tv_rows": rows.value, "sino_fused": fu.value}
+        """The plan's implementation choices (dgamp_ct_tuning): {"filter_mode": 0 FFT | 1 Toeplitz,
+        "tv_kb": steps per TV launch, "tv_rows": rows of a TV block's region, "sino_fused": 1 if the
+        solve runs H A x, the output step and H s as one kernel, "bp_mode": 0 pixel-driven | 1
+        ray-driven A^T}."""
+        t = Tuning()
+        _check(self._lib.dgamp_ct_get_tuning(self._h, C.byref(t)), "get_tuning")
+        return {name: getattr(t, name) for name, _ in Tuning._fields_}
 
-    def set_tuning(self, filter_mode: int = -1, tv_kb: int = -1, tv_rows: int = -1, sino_fused: int = -1):
-        _check(self._lib.dgamp_ct_set_tuning(self._h, int(filter_mode), int(tv_kb), int(tv_rows), int(sino_fused)),
-               "set_tuning")
+    def set_tuning(self, **choices):
+        """Set some of the tuning's fields by name; the others keep their values."""
+        t = Tuning(*([-1] * len(Tuning._fields_)))
+        for k, v in choices.items():
+            if k not in dict(Tuning._fields_):
+                raise TypeError(f"unknown tuning field {k!r}")
+            setattr(t, k, int(v))
+        _check(self._lib.dgamp_ct_set_tuning(self._h, C.byref(t)), "set_tuning")
 
     def set_options(self, **options):
         o = self.options

@@ -191,6 +191,7 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_TRY(toeplitz_set_smem_limit(pl->nd));
     DGCT_TRY(sino_step_set_smem_limit(pl));
     DGCT_TRY(filter_autotune(pl));
+    DGCT_TRY(backproject_autotune(pl));
     pl->sino_fused = sino_step_eligible(pl) ? 1 : 0;
     return DGAMP_CT_OK;
 }
@@ -412,25 +413,26 @@ int dgamp_ct_plan_info(dgamp_ct_plan_t pl, double* frob_sq, int32_t* fft_len) {
     return DGAMP_CT_OK;
 }
 
-int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, int32_t* filter_mode, int32_t* tv_kb, int32_t* tv_rows,
-                        int32_t* sino_fused) {
-    if (!pl) return DGAMP_CT_ERR_INVALID_ARG;
-    if (filter_mode) *filter_mode = pl->filter_mode;
-    if (tv_kb) *tv_kb = pl->tv_kb;
-    if (tv_rows) *tv_rows = pl->tv_rows;
-    if (sino_fused) *sino_fused = pl->sino_fused;
+int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, dgamp_ct_tuning* out) {
+    if (!pl || !out) return DGAMP_CT_ERR_INVALID_ARG;
+    out->filter_mode = pl->filter_mode;
+    out->tv_kb = pl->tv_kb;
+    out->tv_rows = pl->tv_rows;
+    out->sino_fused = pl->sino_fused;
+    out->bp_mode = pl->bp_mode;
     return DGAMP_CT_OK;
 }
 
-int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, int32_t filter_mode, int32_t tv_kb, int32_t tv_rows,
-                        int32_t sino_fused) {
-    if (!pl || filter_mode > 1 || tv_kb > 10 || tv_kb == 0 || sino_fused > 1) return DGAMP_CT_ERR_INVALID_ARG;
-    if (tv_rows >= 0 && tv_rows != 32 && tv_rows != 64 && tv_rows != 128) return DGAMP_CT_ERR_INVALID_ARG;
-    if (sino_fused == 1 && !sino_step_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
-    if (filter_mode >= 0) pl->filter_mode = filter_mode;
-    if (tv_kb > 0) pl->tv_kb = tv_kb;
-    if (tv_rows > 0) pl->tv_rows = tv_rows;
-    if (sino_fused >= 0) pl->sino_fused = sino_fused;
+int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
+    if (!pl || !t || t->filter_mode > 1 || t->tv_kb > 10 || t->tv_kb == 0 || t->sino_fused > 1 || t->bp_mode > 1)
+        return DGAMP_CT_ERR_INVALID_ARG;
+    if (t->tv_rows >= 0 && t->tv_rows != 32 && t->tv_rows != 64 && t->tv_rows != 128) return DGAMP_CT_ERR_INVALID_ARG;
+    if (t->sino_fused == 1 && !sino_step_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
+    if (t->filter_mode >= 0) pl->filter_mode = t->filter_mode;
+    if (t->tv_kb > 0) pl->tv_kb = t->tv_kb;
+    if (t->tv_rows > 0) pl->tv_rows = t->tv_rows;
+    if (t->sino_fused >= 0) pl->sino_fused = t->sino_fused;
+    if (t->bp_mode >= 0) pl->bp_mode = t->bp_mode;
     drop_graph(pl);
     return DGAMP_CT_OK;
 }

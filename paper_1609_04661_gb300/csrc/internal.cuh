@@ -99,6 +99,7 @@ struct dgamp_ct_plan_s {
     int tv_rows = 64;                      // rows of a blocked TV region (64 or 128)
     int filter_mode = 0;                   // H by 0: FFT, 1: Toeplitz product (plan-time choice)
     int sino_fused = 0;                    // solve: H A x, output step, H s in one kernel (k_sino_step)
+    int bp_mode = 0;                       // A^T: 0 pixel-driven gather, 1 ray-driven tiles (plan-time choice)
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;   // stream the graph was captured for (identity only)
@@ -216,6 +217,7 @@ int fill_stats(const dgamp_ct_plan_s* pl, int iters, dgamp_ct_stats* stats);
 // bf = 1: the staged image XR/XC and the sinogram `sino` hold BF16 (solve with storage = 1)
 int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t st, int bf = 0);
 int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf = 0);
+int backproject_autotune(dgamp_ct_plan_s* pl);
 int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
                        float* out, int update, cudaStream_t st, int bf = 0);
 int launch_frobenius(dgamp_ct_plan_s* pl);

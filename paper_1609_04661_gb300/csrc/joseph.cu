@@ -214,8 +214,115 @@ k_backproject(const T* __restrict__ sino, int nv, int nd, int n,
     if (tid == 0) atomicMax(&S->rmax_bits, s_max);
 }
 
+// Ray-driven form of the same transpose (bp_mode 1).  One block = one
+// kBtS x kBtS image tile; warp w takes views w, w + 8, ...  For each view it
+// marches the rays that have a tap in the tile, 32 rays at a time, over the
+// tile's steps with the projector's own fixed-point positions, and adds
+// (1 - f) v w at the left tap into one accumulator tile and f v w at the
+// right tap into a second one (both the warp's own).  On one march line the
+// rays' left taps are distinct (rays are >= 1 apart), and so are their right
+// taps, so no two lanes of a warp ever add to the same word of one
+// accumulator in the same step.  The warps' tiles are summed in a fixed
+// order, so the result does not depend on scheduling.
+constexpr int kBtS = 16, kBtLd = kBtS + 1, kBtWarps = 8;
+
+// One view's rays over the tile.  COL = 1: the view marches over columns
+// (step k = column s0 + k, taps along rows), else over rows.
+template <int COL, typename T>
+__device__ __forceinline__ void bp_tile_view(const ViewConst& c, const T* __restrict__ row, int nd, int n,
+                                             int tx0, int ty0, float* __restrict__ AL, float* __restrict__ AR) {
+    constexpr int as = COL ? 1 : kBtLd, ac = COL ? kBtLd : 1;     // accumulator strides: step, tap
+    const int lane = threadIdx.x & 31;
+    const int s0 = COL ? tx0 : ty0, c0 = COL ? ty0 : tx0;
+    const int ns = min(kBtS, n - s0), nc = min(kBtS, n - c0);
+    // rays with a left tap in [c0 - 1, c0 + nc) at a step of [s0, s0 + ns),
+    // i.e. a0 + d a_det + s a_step in [c0 - 1, c0 + nc): solved for d in
+    // float and widened by one ray on each side
+    const float e0 = (float)s0 * c.a_step, e1 = (float)(s0 + ns - 1) * c.a_step;
+    const float dA = ((float)(c0 - 1) - fmaxf(e0, e1) - c.a0) * c.inv_adet;
+    const float dB = ((float)(c0 + nc) - fminf(e0, e1) - c.a0) * c.inv_adet;
+    const int dlo = max(0, (int)floorf(fminf(dA, dB)) - 1);
+    const int dhi = min(nd - 1, (int)ceilf(fmaxf(dA, dB)) + 1);
+    for (int d0 = dlo; d0 <= dhi; d0 += 32) {
+        const int d = d0 + lane;
+        const float vw = d <= dhi ? ldf(row + d) * c.w : 0.f;        // rays past dhi add zeros
+        // positions relative to the tile: the left tap's index in the tile is the high word
+        long long pos = joseph_pos(c, d, s0) - ((long long)c0 << 32);
+        auto step = [&](int k) {
+            const int rel = (int)(pos >> 32);
+            const float f = __uint_as_float(0x3F800000u | ((unsigned)pos >> 9)) - 1.0f;
+            const int at = k * as + rel * ac;
+            if ((unsigned)rel < (unsigned)nc) AL[at] += (1.f - f) * vw;
+            if ((unsigned)(rel + 1) < (unsigned)nc) AR[at + ac] += f * vw;
+            pos += c.PSTEP;
+        };
+        if (ns == kBtS) {
+#pragma unroll
+            for (int k = 0; k < kBtS; ++k) step(k);
+        } else {
+            for (int k = 0; k < ns; ++k) step(k);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBtWarps * 32, 4)
+k_backproject_tile(const T* __restrict__ sino, int nv, int nd, int n, const ViewConst* __restrict__ vcs,
+                   const float* __restrict__ x_in, float* __restrict__ out, int update,
+                   DevScalars* __restrict__ S) {
+    __shared__ float accL[kBtWarps][kBtS * kBtLd], accR[kBtWarps][kBtS * kBtLd];
+    __shared__ unsigned s_max;
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    const int tx0 = blockIdx.x * kBtS, ty0 = blockIdx.y * kBtS;
+    float* AL = accL[wp];
+    float* AR = accR[wp];
+    for (int i = lane; i < kBtS * kBtLd; i += 32) AL[i] = AR[i] = 0.f;
+    if (tid == 0) s_max = 0u;
+    __syncwarp();
+    for (int v = wp; v < nv; v += kBtWarps) {
+        const ViewConst c = vcs[v];
+        const T* row = sino + (size_t)v * nd;
+        if (c.col)
+            bp_tile_view<1>(c, row, nd, n, tx0, ty0, AL, AR);
+        else
+            bp_tile_view<0>(c, row, nd, n, tx0, ty0, AL, AR);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int p = tid; p < kBtS * kBtS; p += blockDim.x) {
+        const int ly = p / kBtS, lx = p % kBtS;
+        const int ix = tx0 + lx, iy = ty0 + ly;
+        if (ix >= n || iy >= n) continue;
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < kBtWarps; ++w) t += accL[w][ly * kBtLd + lx] + accR[w][ly * kBtLd + lx];
+        const size_t o = (size_t)iy * n + ix;
+        if (update) {
+            const float rv = fmaf((float)S->tau_r, t, x_in[o]);
+            out[o] = rv;
+            atomicMax(&s_max, __float_as_uint(fabsf(rv)));
+        } else {
+            out[o] = t;
+        }
+    }
+    if (!update) return;
+    __syncthreads();
+    if (tid == 0) atomicMax(&S->rmax_bits, s_max);
+}
+
 int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
                        float* out, int update, cudaStream_t st, int bf) {
+    if (pl->bp_mode == 1) {
+        dim3 grd((pl->n + kBtS - 1) / kBtS, (pl->n + kBtS - 1) / kBtS);
+        if (bf)
+            k_backproject_tile<bf16s><<<grd, kBtWarps * 32, 0, st>>>((const bf16s*)sino, pl->nv, pl->nd, pl->n,
+                                                                     pl->ws.vc, x_in, out, update, pl->ws.S);
+        else
+            k_backproject_tile<float><<<grd, kBtWarps * 32, 0, st>>>(sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in,
+                                                                     out, update, pl->ws.S);
+        DGCT_LAUNCH_CHECK();
+        return DGAMP_CT_OK;
+    }
     dim3 blk(32, 8), grd((pl->n + 31) / 32, (pl->n + 7) / 8);
     if (bf)
         k_backproject<bf16s><<<grd, blk, 0, st>>>((const bf16s*)sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in, out,
@@ -225,6 +332,38 @@ int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float
                                                   pl->ws.S);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
+}
+
+// Plan-time choice between the two forms of A^T (same operator): time both
+// on the plan's geometry (a zero sinogram; the work does not depend on the
+// values) and keep the faster.
+int backproject_autotune(dgamp_ct_plan_s* pl) {
+    DGCT_CUDA(cudaMemset(pl->ws.hs, 0, (size_t)pl->M * sizeof(float)));
+    cudaEvent_t e0, e1;
+    DGCT_CUDA(cudaEventCreate(&e0));
+    DGCT_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_mode = 0, rc = DGAMP_CT_OK;
+    for (int mode = 0; mode < 2 && rc == DGAMP_CT_OK; ++mode) {
+        pl->bp_mode = mode;
+        for (int rep = 0; rep < 6 && rc == DGAMP_CT_OK; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, 0);
+            rc = launch_backproject(pl, pl->ws.hs, nullptr, pl->ws.r, 0, 0);
+        }
+        cudaEventRecord(e1, 0);
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (rc == DGAMP_CT_OK && e != cudaSuccess) rc = cuda_fail(e);
+        float ms = 0.f;
+        if (rc == DGAMP_CT_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == DGAMP_CT_OK && ms < best) {
+            best = ms;
+            best_mode = mode;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pl->bp_mode = best_mode;
+    return rc;
 }
 
 // ---------------------------------------------- ||Phi~||_F^2 in FP64 ----

@@ -74,23 +74,30 @@ def test_project_matches_oracle(dg, n, nv, nd, ang, kind):
     assert rel(zp, precond.project(x, g)) < 1e-5
 
 
-@pytest.mark.parametrize("n,nv,nd,ang", GEOMS)
-def test_backproject_matches_oracle(dg, n, nv, nd, ang):
+@pytest.mark.parametrize("n,nv,nd,ang", GEOMS + [(512, 4, 729, None)])
+@pytest.mark.parametrize("bp_mode", [0, 1])                # pixel-driven gather, ray-driven tiles
+def test_backproject_matches_oracle(dg, n, nv, nd, ang, bp_mode):
     g = Geometry(n, nv, nd, ang)
     s = np.random.default_rng(4).standard_normal((nv, nd))
     with dg.Plan(n, nv, nd, angles=ang) as pl:
+        pl.set_tuning(bp_mode=bp_mode)
+        assert pl.tuning()["bp_mode"] == bp_mode
         b = host(pl.backproject(cu(s)))
         bp = host(pl.backproject(cu(s), precond=True))
+        again = host(pl.backproject(cu(s)))
     assert rel(b, joseph.back_project(s, g)) < 1e-5
     assert rel(bp, precond.backproject(s, g)) < 1e-5
+    assert np.array_equal(b, again)                         # deterministic
 
 
-def test_gpu_pair_is_adjoint(dg):
+@pytest.mark.parametrize("bp_mode", [0, 1])
+def test_gpu_pair_is_adjoint(dg, bp_mode):
     n, nv, nd = 96, 17, 139
     rng = np.random.default_rng(5)
     x = rng.standard_normal((n, n))
     s = rng.standard_normal((nv, nd))
     with dg.Plan(n, nv, nd) as pl:
+        pl.set_tuning(bp_mode=bp_mode)
         for pc in (False, True):
             ax = host(pl.project(cu(x), precond=pc))
             ats = host(pl.backproject(cu(s), precond=pc))
@@ -239,6 +246,18 @@ def test_solve_matches_oracle_after_20_iterations(dg, case64, use_graph, damp, t
     ref_tr = np.array([lg.tau_r for lg in log])
     assert np.allclose(st["tau_r"], ref_tr, rtol=1e-3)
     assert np.allclose(st["tau_x"], ref_tx, rtol=2e-2)
+
+
+def test_solve_same_with_either_backprojection(dg, case64):
+    """The two forms of A^T sum the same products in different orders: the
+    solves agree to FP32 rounding amplified over the iterations."""
+    c, g = case64
+    out = {}
+    for mode in (0, 1):
+        with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, damp_x=0.7, damp_s=0.7) as pl:
+            pl.set_tuning(bp_mode=mode)
+            out[mode] = host(pl.solve(cu(c["y"]), c["I0"], 5))
+    assert rel(out[1], out[0]) < 1e-4
 
 
 def test_solve_host_buffers_match_device_path(dg, case64):
