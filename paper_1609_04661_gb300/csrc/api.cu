@@ -8,7 +8,7 @@
 #include <new>
 #include <vector>
 
-#include "internal.cuh"
+#include "fft_device.cuh"
 
 namespace dgct {
 
@@ -123,8 +123,8 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_TRY(dalloc(&w.log, (size_t)kMaxIters));
     DGCT_TRY(dalloc(&w.vc, (size_t)pl->nv));
     DGCT_TRY(dalloc(&w.gain, (size_t)pl->P));
-    DGCT_TRY(dalloc(&w.tw, (size_t)pl->P));
-    DGCT_TRY(dalloc(&w.tw2, (size_t)pl->m2));
+    DGCT_TRY(dalloc(&w.tw, (size_t)fft_twiddle_count(pl->P) + 1));
+    DGCT_TRY(dalloc(&w.tw2, (size_t)fft_twiddle_count(pl->m2) + 1));
     DGCT_TRY(dalloc(&w.hx, (size_t)2 * pl->nd));
     DGCT_TRY(dalloc(&w.zraw2, M));
     DGCT_TRY(dalloc(&w.scratch_d, (size_t)(pl->nd + 1) + 2 * pl->nd + pl->nv + (size_t)pl->nv * pl->nd));
@@ -156,10 +156,18 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     }
     DGCT_CUDA(cudaMemcpy(w.gain, g.data(), P * sizeof(float), cudaMemcpyHostToDevice));
     const double two_pi = 6.283185307179586476925286766559;
+    // the FFT's stage-by-stage twiddle table (fft_device.cuh), from FP64
     auto twiddles = [&](int L, float2* dst) -> int {
-        std::vector<float2> t(L);
-        for (int k = 0; k < L; ++k)
-            t[k] = make_float2((float)std::cos(two_pi * k / L), (float)std::sin(two_pi * k / L));
+        std::vector<float2> t;
+        for (int Ns = 1, R = fft_stage_radix(L, 1); R > 1; Ns *= R, R = fft_stage_radix(L, Ns)) {
+            if (Ns == 1) continue;
+            for (int r = 1; r < R; ++r)
+                for (int k = 0; k < Ns; ++k) {
+                    const double a = two_pi * (double)r * (double)k / ((double)Ns * R);
+                    t.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+                }
+        }
+        if (t.empty()) return DGAMP_CT_OK;
         DGCT_CUDA(cudaMemcpy(dst, t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice));
         return DGAMP_CT_OK;
     };
@@ -186,7 +194,7 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
         for (int m = -(nd - 1); m <= nd - 1; ++m) hx[m + nd - 1] = (float)h[m < 0 ? -m : m];
         DGCT_CUDA(cudaMemcpy(w.hx, hx.data(), hx.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
-    const int smem_need = 2 * (P > pl->m2 ? P : pl->m2) * (int)sizeof(float2);
+    const int smem_need = 2 * fft_buf_len(P > pl->m2 ? P : pl->m2) * (int)sizeof(float2);
     DGCT_TRY(fft_set_smem_limits(smem_need > 48 * 1024 ? smem_need : 48 * 1024));
     DGCT_TRY(toeplitz_set_smem_limit(pl->nd));
     DGCT_TRY(sino_step_set_smem_limit(pl));
@@ -234,7 +242,8 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
         DGCT_TRY(launch_filter(pl, w.s, w.hs, st, bf));                 // Step 3: H s
         DGCT_TRY(mark());
     }
-    DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st, bf));        //         r = x + tau_r A^T H s
+    DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st, bf,          //         r = x + tau_r A^T H s
+                                pl->sino_fused ? sino_step_partials(pl) : 0));
     DGCT_TRY(mark());
     // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r
     DGCT_TRY(launch_probe_input(pl, 0, st, pl->opt.denoiser == 1 ? 1 : 0));

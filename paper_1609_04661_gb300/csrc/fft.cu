@@ -24,7 +24,7 @@ k_filter_views(const T* in, T* out, int nv, int nd, int P,
                const float* __restrict__ gain, const float2* __restrict__ tw) {
     extern __shared__ float2 smem[];
     float2* a = smem;
-    float2* b = smem + P;
+    float2* b = smem + fft_buf_len(P);
     const int va = 2 * blockIdx.x, vb = va + 1;
     const bool hasb = vb < nv;
     const T* ra = in + (size_t)va * nd;
@@ -35,15 +35,15 @@ k_filter_views(const T* in, T* out, int nv, int nd, int P,
             v.x = ldf(ra + i);
             if (hasb) v.y = ldf(rb + i);
         }
-        a[i] = v;
+        a[fpad(i)] = v;
     }
     __syncthreads();
     float2* r = fft_stockham(a, b, P, tw, -1.f);
     float2* o = (r == a) ? b : a;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const float g = __ldg(gain + i);
-        const float2 v = r[i];
-        r[i] = make_float2(v.x * g, v.y * g);
+        const float2 v = r[fpad(i)];
+        r[fpad(i)] = make_float2(v.x * g, v.y * g);
     }
     __syncthreads();
     r = fft_stockham(r, o, P, tw, 1.f);
@@ -51,7 +51,7 @@ k_filter_views(const T* in, T* out, int nv, int nd, int P,
     T* wa = out + (size_t)va * nd;
     T* wb = out + (size_t)vb * nd;
     for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-        const float2 v = r[i];
+        const float2 v = r[fpad(i)];
         stf(wa + i, v.x * sc);
         if (hasb) stf(wb + i, v.y * sc);
     }
@@ -142,7 +142,7 @@ int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaSt
         return DGAMP_CT_OK;
     }
     const int P = pl->P;
-    const size_t sm = (size_t)2 * P * sizeof(float2);
+    const size_t sm = (size_t)2 * fft_buf_len(P) * sizeof(float2);
     const int thr = fft_threads(P);
     if (bf)
         k_filter_views<bf16s><<<(pl->nv + 1) / 2, thr, sm, st>>>((const bf16s*)in, (bf16s*)out, pl->nv, pl->nd, P,
@@ -201,13 +201,13 @@ k_img_rows_fwd(const float* __restrict__ img, int n, int m, const float2* __rest
                float2* __restrict__ C) {
     extern __shared__ float2 smem[];
     float2* a = smem;
-    float2* b = smem + m;
+    float2* b = smem + fft_buf_len(m);
     const int iy = blockIdx.x;
     for (int i = threadIdx.x; i < m; i += blockDim.x)
-        a[i] = make_float2(i < n ? img[(size_t)iy * n + i] : 0.f, 0.f);
+        a[fpad(i)] = make_float2(i < n ? img[(size_t)iy * n + i] : 0.f, 0.f);
     __syncthreads();
     float2* r = fft_stockham(a, b, m, tw, -1.f);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) C[(size_t)iy * m + i] = r[i];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) C[(size_t)iy * m + i] = r[fpad(i)];
 }
 
 // pass 2: every column kx: forward FFT over rows (rows >= n are zero),
@@ -217,10 +217,10 @@ k_img_cols(float2* __restrict__ C, int n, int m, const float2* __restrict__ tw, 
            int inverse_gain) {
     extern __shared__ float2 smem[];
     float2* a = smem;
-    float2* b = smem + m;
+    float2* b = smem + fft_buf_len(m);
     const int kx = blockIdx.x;
     for (int i = threadIdx.x; i < m; i += blockDim.x)
-        a[i] = i < n ? C[(size_t)i * m + kx] : make_float2(0.f, 0.f);
+        a[fpad(i)] = i < n ? C[(size_t)i * m + kx] : make_float2(0.f, 0.f);
     __syncthreads();
     float2* r = fft_stockham(a, b, m, tw, -1.f);
     float2* o = (r == a) ? b : a;
@@ -230,12 +230,12 @@ k_img_cols(float2* __restrict__ C, int n, int m, const float2* __restrict__ tw, 
         const float rho = sqrtf(fx * fx + fy * fy);
         float g = sqrtf(fmaxf(rho, f0));
         if (inverse_gain) g = 1.0f / g;
-        const float2 v = r[ky];
-        r[ky] = make_float2(v.x * g, v.y * g);
+        const float2 v = r[fpad(ky)];
+        r[fpad(ky)] = make_float2(v.x * g, v.y * g);
     }
     __syncthreads();
     r = fft_stockham(r, o, m, tw, 1.f);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) C[(size_t)i * m + kx] = r[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) C[(size_t)i * m + kx] = r[fpad(i)];
 }
 
 // pass 3: inverse row FFTs, real part of the first n columns, scaled by 1/m^2.
@@ -244,19 +244,19 @@ k_img_rows_inv(const float2* __restrict__ C, int n, int m, const float2* __restr
                float* __restrict__ out) {
     extern __shared__ float2 smem[];
     float2* a = smem;
-    float2* b = smem + m;
+    float2* b = smem + fft_buf_len(m);
     const int iy = blockIdx.x;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) a[i] = C[(size_t)iy * m + i];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) a[fpad(i)] = C[(size_t)iy * m + i];
     __syncthreads();
     float2* r = fft_stockham(a, b, m, tw, 1.f);
     const float sc = 1.0f / ((float)m * (float)m);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) out[(size_t)iy * n + i] = r[i].x * sc;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[(size_t)iy * n + i] = r[fpad(i)].x * sc;
 }
 
 int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out, int inverse,
                          cudaStream_t st) {
     const int n = pl->n, m = pl->m2;
-    const size_t sm = (size_t)2 * m * sizeof(float2);
+    const size_t sm = (size_t)2 * fft_buf_len(m) * sizeof(float2);
     const int thr = fft_threads(m);
     const float f0 = 1.0f / (2.0f * (float)pl->P);
     k_img_rows_fwd<<<n, thr, sm, st>>>(in, n, m, pl->ws.tw2, pl->ws.fft2d);

@@ -8,6 +8,14 @@
 // reads a[j + r P/R], r < R, multiplies input r by w^(r k) with k = j mod Ns
 // and w = exp(-+ 2 pi i / (Ns R)), takes the R-point DFT in registers and
 // writes output q to b[(j - k) R + k + q Ns].
+//
+// Shared-memory layout.  Element i of a buffer lives at fpad(i) = i + i/8
+// (a buffer of P elements takes fft_buf_len(P) = P + P/8 slots): the first
+// stage's stores b[8 j + q] and the second's fall on distinct banks for the
+// 16 lanes of a 64-bit access, which without the padding collide 8- and
+// 4-fold.  Twiddles are stored stage by stage (fft_twiddle_count(P) values):
+// for every stage with Ns > 1, the (R - 1) Ns values exp(2 pi i r k / (Ns R))
+// at [(r - 1) Ns + k], so the lanes of a warp read consecutive words.
 #pragma once
 #include "internal.cuh"
 
@@ -66,21 +74,34 @@ template <> __device__ __forceinline__ void dft_small<8>(float2* v, float dir) {
     v[7] = csub(E[3], t3);
 }
 
-// tw[t] = (cos(2 pi t / P), sin(2 pi t / P)), t < P; dir = -1 forward, +1 inverse.
+__host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 3); }
+__host__ __device__ __forceinline__ int fft_buf_len(int P) { return P + P / 8 + 1; }
+
+// Radices of the stages: 8 while Ns * 8 <= P, then 4 or 2 for the rest.
+__host__ __device__ __forceinline__ int fft_stage_radix(int P, int Ns) {
+    return Ns * 8 <= P ? 8 : (Ns * 4 == P ? 4 : (Ns * 2 == P ? 2 : 1));
+}
+__host__ __device__ __forceinline__ int fft_twiddle_count(int P) {
+    int cnt = 0;
+    for (int Ns = 1, R = fft_stage_radix(P, 1); R > 1; Ns *= R, R = fft_stage_radix(P, Ns))
+        if (Ns > 1) cnt += (R - 1) * Ns;
+    return cnt;
+}
+
+// One stage; tws = this stage's twiddles; dir = -1 forward, +1 inverse.
 template <int R>
 __device__ __forceinline__ void stockham_stage(const float2* a, float2* b, int P, int Ns,
-                                               const float2* tw, float dir) {
+                                               const float2* tws, float dir) {
     const int nb = P / R;
-    const int tstride = P / (Ns * R);        // w^(r k) = tw[r k tstride], r k tstride < P
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
         const int k = j & (Ns - 1);
         float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = a[j + r * nb];
+        for (int r = 0; r < R; ++r) v[r] = a[fpad(j + r * nb)];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = tw[r * k * tstride];
+                float2 w = tws[(r - 1) * Ns + k];
                 w.y *= dir;
                 v[r] = cmul(v[r], w);
             }
@@ -88,26 +109,23 @@ __device__ __forceinline__ void stockham_stage(const float2* a, float2* b, int P
         dft_small<R>(v, dir);
         const int o = (j - k) * R + k;
 #pragma unroll
-        for (int q = 0; q < R; ++q) b[o + q * Ns] = v[q];
+        for (int q = 0; q < R; ++q) b[fpad(o + q * Ns)] = v[q];
     }
 }
 
-// Transforms a[0..P) (P a power of two); returns the buffer holding the result.
-// Every thread of the block takes part; tw may point to global or shared memory.
+// Transforms a[0..P) (P a power of two, padded layout); returns the buffer
+// holding the result.  Every thread of the block takes part; tw (the
+// stage-by-stage table) may point to global or shared memory.
 __device__ __forceinline__ float2* fft_stockham(float2* a, float2* b, int P, const float2* tw, float dir) {
-    int Ns = 1;
-    for (; Ns * 8 <= P; Ns *= 8) {
-        stockham_stage<8>(a, b, P, Ns, tw, dir);
-        __syncthreads();
-        float2* t = a;
-        a = b;
-        b = t;
-    }
-    if (Ns * 4 == P || Ns * 2 == P) {
-        if (Ns * 4 == P)
-            stockham_stage<4>(a, b, P, Ns, tw, dir);
+    int off = 0;
+    for (int Ns = 1, R = fft_stage_radix(P, 1); R > 1; Ns *= R, R = fft_stage_radix(P, Ns)) {
+        if (R == 8)
+            stockham_stage<8>(a, b, P, Ns, tw + off, dir);
+        else if (R == 4)
+            stockham_stage<4>(a, b, P, Ns, tw + off, dir);
         else
-            stockham_stage<2>(a, b, P, Ns, tw, dir);
+            stockham_stage<2>(a, b, P, Ns, tw + off, dir);
+        if (Ns > 1) off += (R - 1) * Ns;
         __syncthreads();
         float2* t = a;
         a = b;

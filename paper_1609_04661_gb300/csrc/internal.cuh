@@ -75,8 +75,8 @@ struct Workspace {
     float* gain = nullptr;         // [P]
     float* hx = nullptr;           // [2 n_det - 1]  H's kernel h[|m|], m = -(n_det-1)..n_det-1
     float* zraw2 = nullptr;        // [M]  copy for in-place Toeplitz filtering
-    float2* tw = nullptr;          // [P]     twiddles exp(2 pi i k / P)
-    float2* tw2 = nullptr;         // [m2]    twiddles exp(2 pi i k / m2)
+    float2* tw = nullptr;          // FFT twiddles for length P, stage by stage (fft_device.cuh)
+    float2* tw2 = nullptr;         // the same for length m2
     double* scratch_d = nullptr;   // plan-time FP64 scratch
     float* b = nullptr;            // the iteration's probe b (Eq. MC_SURE) [n][n]
 };
@@ -219,7 +219,7 @@ int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t
 int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf = 0);
 int backproject_autotune(dgamp_ct_plan_s* pl);
 int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
-                       float* out, int update, cudaStream_t st, int bf = 0);
+                       float* out, int update, cudaStream_t st, int bf = 0, int nparts = 0);
 int launch_frobenius(dgamp_ct_plan_s* pl);
 // fft.cu
 int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaStream_t st, int bf = 0);
@@ -230,6 +230,7 @@ int raise_smem_limit(const void* kernel, int bytes);
 bool sino_step_eligible(const dgamp_ct_plan_s* pl);
 int sino_step_set_smem_limit(const dgamp_ct_plan_s* pl);
 int launch_sino_step(const dgamp_ct_plan_s* pl, cudaStream_t st, int bf);
+int sino_step_partials(const dgamp_ct_plan_s* pl);   // FP64 partial sums of tau_s_i it leaves in ws.partial
 int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out, int inverse,
                          cudaStream_t st);
 int fft_set_smem_limits(int bytes);

@@ -141,19 +141,51 @@ int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int 
 // Step 3) and the running max |r| used by the MC step of Step 4.
 constexpr int kBpViews = 256;
 
+// tau_r of the update r = x + tau_r A^T H s (Algorithm 1, Step 3), by warp 0
+// of a block into *s_tau_r.  nparts > 0: the fused sinogram kernel left
+// nparts FP64 partial sums of tau_s_i; every block adds them in the same
+// fixed order (lane-strided, then the warp's shuffle tree), forms
+// tau_s = sum / M and tau_r = N / (||Phi~||_F^2 tau_s) in FP64, and block 0
+// records tau_p, tau_s and tau_r in S for the kernels after it.
+// nparts == 0: tau_r is already in S.
+__device__ __forceinline__ void bp_tau_r(DevScalars* __restrict__ S, const double* __restrict__ partial,
+                                         int nparts, double M, double N, float* s_tau_r) {
+    const int lane = threadIdx.x & 31;
+    if (nparts == 0) {
+        if (lane == 0) *s_tau_r = (float)S->tau_r;
+        return;
+    }
+    double a = 0.0;
+    for (int i = lane; i < nparts; i += 32) a += partial[i];
+    a = warp_sum(a);
+    if (lane == 0) {
+        const double tau_s = a / M, tau_r = N / (S->frob2 * tau_s);
+        *s_tau_r = (float)tau_r;
+        if (blockIdx.x == 0 && blockIdx.y == 0) {
+            S->tau_p = S->frob2 * S->tau_x / M;
+            S->tau_s = tau_s;
+            S->tau_r = tau_r;
+            if (!isfinite(tau_r)) S->nonfinite += 1u;
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_backproject(const T* __restrict__ sino, int nv, int nd, int n,
               const ViewConst* __restrict__ vcs, const float* __restrict__ x_in,
-              float* __restrict__ out, int update, DevScalars* __restrict__ S) {
+              float* __restrict__ out, int update, DevScalars* __restrict__ S,
+              const double* __restrict__ partial, int nparts, double M) {
     __shared__ ViewConst svc[kBpViews];
     __shared__ unsigned s_max;
+    __shared__ float s_tau_r;
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iy = blockIdx.y * blockDim.y + threadIdx.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const bool live = ix < n && iy < n;
     const float fx = (float)ix, fy = (float)iy, fx1 = fx + 1.f, fy1 = fy + 1.f;
     if (tid == 0) s_max = 0u;
+    if (update && tid < 32) bp_tau_r(S, partial, nparts, M, (double)n * n, &s_tau_r);
     float acc = 0.f;
     for (int v0 = 0; v0 < nv; v0 += kBpViews) {
         const int cnt = min(kBpViews, nv - v0);
@@ -200,8 +232,7 @@ k_backproject(const T* __restrict__ sino, int nv, int nd, int n,
     }
     const size_t o = (size_t)iy * n + ix;
     if (update && live) {
-        const float tau_r = (float)S->tau_r;
-        const float rv = fmaf(tau_r, acc, x_in[o]);
+        const float rv = fmaf(s_tau_r, acc, x_in[o]);
         out[o] = rv;
         // |r| >= 0, so its float bit pattern orders like the value
         atomicMax(&s_max, __float_as_uint(fabsf(rv)));
@@ -269,15 +300,17 @@ template <typename T>
 __global__ void __launch_bounds__(kBtWarps * 32, 4)
 k_backproject_tile(const T* __restrict__ sino, int nv, int nd, int n, const ViewConst* __restrict__ vcs,
                    const float* __restrict__ x_in, float* __restrict__ out, int update,
-                   DevScalars* __restrict__ S) {
+                   DevScalars* __restrict__ S, const double* __restrict__ partial, int nparts, double M) {
     __shared__ float accL[kBtWarps][kBtS * kBtLd], accR[kBtWarps][kBtS * kBtLd];
     __shared__ unsigned s_max;
+    __shared__ float s_tau_r;
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const int tx0 = blockIdx.x * kBtS, ty0 = blockIdx.y * kBtS;
     float* AL = accL[wp];
     float* AR = accR[wp];
     for (int i = lane; i < kBtS * kBtLd; i += 32) AL[i] = AR[i] = 0.f;
     if (tid == 0) s_max = 0u;
+    if (update && wp == 0) bp_tau_r(S, partial, nparts, M, (double)n * n, &s_tau_r);
     __syncwarp();
     for (int v = wp; v < nv; v += kBtWarps) {
         const ViewConst c = vcs[v];
@@ -298,7 +331,7 @@ k_backproject_tile(const T* __restrict__ sino, int nv, int nd, int n, const View
         for (int w = 0; w < kBtWarps; ++w) t += accL[w][ly * kBtLd + lx] + accR[w][ly * kBtLd + lx];
         const size_t o = (size_t)iy * n + ix;
         if (update) {
-            const float rv = fmaf((float)S->tau_r, t, x_in[o]);
+            const float rv = fmaf(s_tau_r, t, x_in[o]);
             out[o] = rv;
             atomicMax(&s_max, __float_as_uint(fabsf(rv)));
         } else {
@@ -310,26 +343,31 @@ k_backproject_tile(const T* __restrict__ sino, int nv, int nd, int n, const View
     if (tid == 0) atomicMax(&S->rmax_bits, s_max);
 }
 
+// nparts > 0 (update = 1 after the fused sinogram kernel): tau_r from the
+// nparts partial sums in ws.partial; else from S.
 int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
-                       float* out, int update, cudaStream_t st, int bf) {
+                       float* out, int update, cudaStream_t st, int bf, int nparts) {
+    const double M = (double)pl->M;
+    const double* part = pl->ws.partial;
     if (pl->bp_mode == 1) {
         dim3 grd((pl->n + kBtS - 1) / kBtS, (pl->n + kBtS - 1) / kBtS);
         if (bf)
             k_backproject_tile<bf16s><<<grd, kBtWarps * 32, 0, st>>>((const bf16s*)sino, pl->nv, pl->nd, pl->n,
-                                                                     pl->ws.vc, x_in, out, update, pl->ws.S);
+                                                                     pl->ws.vc, x_in, out, update, pl->ws.S, part,
+                                                                     nparts, M);
         else
             k_backproject_tile<float><<<grd, kBtWarps * 32, 0, st>>>(sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in,
-                                                                     out, update, pl->ws.S);
+                                                                     out, update, pl->ws.S, part, nparts, M);
         DGCT_LAUNCH_CHECK();
         return DGAMP_CT_OK;
     }
     dim3 blk(32, 8), grd((pl->n + 31) / 32, (pl->n + 7) / 8);
     if (bf)
         k_backproject<bf16s><<<grd, blk, 0, st>>>((const bf16s*)sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in, out,
-                                                  update, pl->ws.S);
+                                                  update, pl->ws.S, part, nparts, M);
     else
         k_backproject<float><<<grd, blk, 0, st>>>(sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in, out, update,
-                                                  pl->ws.S);
+                                                  pl->ws.S, part, nparts, M);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }

@@ -9,15 +9,22 @@
 // twiddle table is staged there once for the four transforms; s is written
 // for the next iteration and, rounded as stored, filtered in place.  tau_s
 // is reduced as in the stand-alone output step (the last block finishes it
-// and forms tau_r).  This replaces three launches, two round trips of a
-// sinogram through L2, and the per-stage twiddle loads from global memory.
+// Each block stores its FP64 partial sum of tau_s_i; the back-projection
+// that follows adds the partials in a fixed order and forms tau_s and tau_r
+// (so no block here waits for the others).  This replaces three launches,
+// two round trips of a sinogram through L2 and a grid-wide reduction tail.
 #include "fft_device.cuh"
 #include "output_device.cuh"
 
 namespace dgct {
 
 constexpr int kSinoThreads = 512;
-constexpr int kSinoMaxP = 8192;       // 3 P complex values of shared memory: 192 KB
+constexpr int kSinoMaxP = 8192;       // two padded buffers and the twiddles: 213 KB of shared memory
+
+// elements of the output step one thread keeps in registers from the start
+// (s_prev and y are loaded before the first transform, which hides their
+// latency); beyond 2 n_det = kSinoPre * kSinoThreads they are loaded in place
+constexpr int kSinoPre = 4;
 
 // the value a store of v into T and a load back give
 __device__ __forceinline__ float as_stored(float v, const float*) { return v; }
@@ -26,30 +33,47 @@ __device__ __forceinline__ float as_stored(float v, const bf16s*) { return __bfl
 template <typename T>
 __global__ void __launch_bounds__(kSinoThreads)
 k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __restrict__ hs, int nv, int nd,
-            int P, const float* __restrict__ gain, const float2* __restrict__ tw_g, long long M, double N,
-            int onsager, float damp_s, int truncate, DevScalars* S, double* partial) {
+            int P, const float* __restrict__ gain, const float2* __restrict__ tw_g, long long M,
+            int onsager, float damp_s, int truncate, DevScalars* S, double* __restrict__ partial) {
     extern __shared__ float2 smem[];
-    float2* a = smem;                 // [P]
-    float2* b = smem + P;             // [P]
-    float2* tw = smem + 2 * P;        // [P]
+    const int BL = fft_buf_len(P), TC = fft_twiddle_count(P);
+    float2* a = smem;                 // [BL], padded layout
+    float2* b = smem + BL;            // [BL]
+    float2* tw = smem + 2 * BL;       // [TC], stage by stage
     __shared__ double sm[32];
     __shared__ float s_tp, s_inv, s_logI0;
     const int va = 2 * blockIdx.x, vb = va + 1;
     const bool hasb = vb < nv;
+    const int ne = hasb ? 2 * nd : nd;
     if (threadIdx.x == 0) {
         const double tp = S->frob2 * S->tau_x / (double)M;      // Step 2: tau_p
         s_tp = (float)tp;
         s_inv = (float)(1.0 / tp);
         s_logI0 = (float)S->logI0;
+        // max |r| of this iteration is gathered by the back-projection that follows
+        if (blockIdx.x == 0) S->rmax_bits = 0u;
     }
+    // s_prev and y of this thread's first kSinoPre elements
+    float pre_sp[kSinoPre], pre_y[kSinoPre];
+#pragma unroll
+    for (int j = 0; j < kSinoPre; ++j) {
+        const int e = threadIdx.x + j * kSinoThreads;
+        pre_sp[j] = pre_y[j] = 0.f;
+        if (e < ne) {
+            const int d = e >= nd ? e - nd : e;
+            const size_t gi = (size_t)(e >= nd ? vb : va) * nd + d;
+            pre_sp[j] = ldf(s + gi);
+            pre_y[j] = y[gi];
+        }
+    }
+    for (int i = threadIdx.x; i < TC; i += blockDim.x) tw[i] = tw_g[i];
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        tw[i] = tw_g[i];
         float2 v = make_float2(0.f, 0.f);
         if (i < nd) {
             v.x = ldf(zraw + (size_t)va * nd + i);
             if (hasb) v.y = ldf(zraw + (size_t)vb * nd + i);
         }
-        a[i] = v;
+        a[fpad(i)] = v;
     }
     __syncthreads();
     // z = H A x; the 1/P of the inverse transform is folded into the gain
@@ -59,7 +83,8 @@ k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __
     float2* o = (r == a) ? b : a;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const float g = __ldg(gain + i) * invP;
-        r[i] = make_float2(r[i].x * g, r[i].y * g);
+        const float2 v = r[fpad(i)];
+        r[fpad(i)] = make_float2(v.x * g, v.y * g);
     }
     __syncthreads();
     r = fft_stockham(r, o, P, tw, 1.f);
@@ -67,26 +92,39 @@ k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __
 
     // output step on both views; s (as stored) goes into o, zero-padded
     const float tau_p = s_tp, inv_tp = s_inv, logI0 = s_logI0;
-    for (int i = nd + threadIdx.x; i < P; i += blockDim.x) o[i] = make_float2(0.f, 0.f);
+    for (int i = nd + threadIdx.x; i < P; i += blockDim.x) o[fpad(i)] = make_float2(0.f, 0.f);
     double acc = 0.0;
     unsigned capped = 0;
-    const int ne = hasb ? 2 * nd : nd;
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+#pragma unroll 1
+    for (int j = 0, e = threadIdx.x; e < ne; ++j, e += kSinoThreads) {
         const bool isb = e >= nd;
         const int d = isb ? e - nd : e;
         const size_t gi = (size_t)(isb ? vb : va) * nd + d;
-        const float sp = ldf(s + gi);
+        float sp, yv;
+        if (j < kSinoPre) {
+            sp = pre_sp[0];
+            yv = pre_y[0];
+#pragma unroll
+            for (int u = 1; u < kSinoPre; ++u)
+                if (j == u) {
+                    sp = pre_sp[u];
+                    yv = pre_y[u];
+                }
+        } else {
+            sp = ldf(s + gi);
+            yv = y[gi];
+        }
         float sv;
-        acc += (double)output_element(isb ? r[d].y : r[d].x, sp, y[gi], tau_p, inv_tp, logI0, onsager, damp_s,
-                                      truncate, capped, sv);
+        acc += (double)output_element(isb ? r[fpad(d)].y : r[fpad(d)].x, sp, yv, tau_p, inv_tp, logI0, onsager,
+                                      damp_s, truncate, capped, sv);
         stf(s + gi, sv);
         const float sq = as_stored(sv, s);
         if (!hasb)
-            o[d] = make_float2(sq, 0.f);
+            o[fpad(d)] = make_float2(sq, 0.f);
         else if (isb)
-            o[d].y = sq;
+            o[fpad(d)].y = sq;
         else
-            o[d].x = sq;
+            o[fpad(d)].x = sq;
     }
     __syncthreads();
     // H s
@@ -94,16 +132,27 @@ k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __
     float2* q2 = (q == o) ? r : o;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const float g = __ldg(gain + i) * invP;
-        q[i] = make_float2(q[i].x * g, q[i].y * g);
+        const float2 v = q[fpad(i)];
+        q[fpad(i)] = make_float2(v.x * g, v.y * g);
     }
     __syncthreads();
     q = fft_stockham(q, q2, P, tw, 1.f);
     for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-        stf(hs + (size_t)va * nd + i, q[i].x);
-        if (hasb) stf(hs + (size_t)vb * nd + i, q[i].y);
+        const float2 v = q[fpad(i)];
+        stf(hs + (size_t)va * nd + i, v.x);
+        if (hasb) stf(hs + (size_t)vb * nd + i, v.y);
     }
-    finish_tau_s(acc, capped, M, N, 1, S, partial, nullptr, sm);
+    capped = warp_sum(capped);
+    if ((threadIdx.x & 31) == 0 && capped) atomicAdd(&S->newton_capped, capped);
+    acc = block_sum(acc, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
+
+static int sino_step_smem(int P) {
+    return (2 * fft_buf_len(P) + fft_twiddle_count(P)) * (int)sizeof(float2);
+}
+
+int sino_step_partials(const dgamp_ct_plan_s* pl) { return (pl->nv + 1) / 2; }
 
 bool sino_step_eligible(const dgamp_ct_plan_s* pl) {
     return pl->P <= kSinoMaxP && (pl->nv + 1) / 2 <= pl->max_partials;
@@ -113,7 +162,7 @@ int sino_step_set_smem_limit(const dgamp_ct_plan_s* pl) {
     if (!sino_step_eligible(pl)) return DGAMP_CT_OK;
     // set even at or below 48 KB: the static shared memory of the reduction
     // comes on top of the dynamic part
-    const int bytes = 3 * pl->P * (int)sizeof(float2);
+    const int bytes = sino_step_smem(pl->P);
     DGCT_TRY(raise_smem_limit((const void*)k_sino_step<float>, bytes));
     DGCT_TRY(raise_smem_limit((const void*)k_sino_step<bf16s>, bytes));
     return DGAMP_CT_OK;
@@ -125,17 +174,17 @@ int launch_sino_step(const dgamp_ct_plan_s* pl, cudaStream_t st, int bf) {
     if (!sino_step_eligible(pl)) return DGAMP_CT_ERR_INVALID_ARG;
     const Workspace& w = pl->ws;
     const int grid = (pl->nv + 1) / 2;
-    const size_t sm = (size_t)3 * pl->P * sizeof(float2);
+    const size_t sm = (size_t)sino_step_smem(pl->P);
     const float damp_s = (float)pl->opt.damp_s;
     if (bf)
         k_sino_step<bf16s><<<grid, kSinoThreads, sm, st>>>((const bf16s*)w.zraw, w.y, (bf16s*)w.s, (bf16s*)w.hs,
                                                            pl->nv, pl->nd, pl->P, w.gain, w.tw, pl->M,
-                                                           (double)pl->N, pl->opt.onsager, damp_s,
-                                                           pl->opt.truncate_z, w.S, w.partial);
+                                                           pl->opt.onsager, damp_s, pl->opt.truncate_z, w.S,
+                                                           w.partial);
     else
         k_sino_step<float><<<grid, kSinoThreads, sm, st>>>(w.zraw, w.y, w.s, w.hs, pl->nv, pl->nd, pl->P, w.gain,
-                                                           w.tw, pl->M, (double)pl->N, pl->opt.onsager, damp_s,
-                                                           pl->opt.truncate_z, w.S, w.partial);
+                                                           w.tw, pl->M, pl->opt.onsager, damp_s, pl->opt.truncate_z,
+                                                           w.S, w.partial);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
