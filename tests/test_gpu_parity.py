@@ -62,7 +62,7 @@ def _img(n, seed, kind="random"):
     return synth.rasterise(ph, n)
 
 
-@pytest.mark.parametrize("n,nv,nd,ang", GEOMS)
+@pytest.mark.parametrize("n,nv,nd,ang", GEOMS + [(512, 4, 729, None), (300, 5, 1100, None)])
 @pytest.mark.parametrize("kind", ["random", "phantom"])
 def test_project_matches_oracle(dg, n, nv, nd, ang, kind):
     g = Geometry(n, nv, nd, ang)
@@ -70,8 +70,10 @@ def test_project_matches_oracle(dg, n, nv, nd, ang, kind):
     with dg.Plan(n, nv, nd, angles=ang) as pl:
         z = host(pl.project(cu(x)))
         zp = host(pl.project(cu(x), precond=True))
+        again = host(pl.project(cu(x)))
     assert rel(z, joseph.forward_project(x, g)) < 1e-5
     assert rel(zp, precond.project(x, g)) < 1e-5
+    assert np.array_equal(z, again)                          # deterministic
 
 
 @pytest.mark.parametrize("n,nv,nd,ang", GEOMS + [(512, 4, 729, None)])
@@ -248,16 +250,18 @@ def test_solve_matches_oracle_after_20_iterations(dg, case64, use_graph, damp, t
     assert np.allclose(st["tau_x"], ref_tx, rtol=2e-2)
 
 
-def test_solve_same_with_either_backprojection(dg, case64):
+@pytest.mark.parametrize("storage", [0, 1])
+def test_solve_same_with_either_backprojection(dg, case64, storage):
     """The two forms of A^T sum the same products in different orders: the
-    solves agree to FP32 rounding amplified over the iterations."""
+    solves agree to FP32 rounding amplified over the iterations (BF16
+    storage: to its own rounding, as both read the same BF16 values)."""
     c, g = case64
     out = {}
     for mode in (0, 1):
-        with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, damp_x=0.7, damp_s=0.7) as pl:
+        with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, damp_x=0.7, damp_s=0.7, storage=storage) as pl:
             pl.set_tuning(bp_mode=mode)
             out[mode] = host(pl.solve(cu(c["y"]), c["I0"], 5))
-    assert rel(out[1], out[0]) < 1e-4
+    assert rel(out[1], out[0]) < (1e-4 if storage == 0 else 3e-3)
 
 
 def test_solve_host_buffers_match_device_path(dg, case64):
