@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "fft_device.cuh"
+#include "output_device.cuh"
 
 namespace dgct {
 
@@ -21,7 +22,7 @@ int cuda_fail(cudaError_t e) {
 
 static void free_ws(Workspace& w) {
     void* ptrs[] = {w.XR, w.XC, w.x, w.r, w.b, w.p, w.zraw, w.z, w.s, w.hs, w.y, w.fft2d, w.partial,
-                    w.S, w.log, w.vc, w.gain, w.tw, w.tw2, w.scratch_d, w.hx, w.zraw2};
+                    w.partial_div, w.S, w.log, w.vc, w.gain, w.tw, w.tw2, w.scratch_d, w.hx, w.zraw2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -119,6 +120,7 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     size_t nparts = tiles32 > (size_t)pl->max_partials ? tiles32 : (size_t)pl->max_partials;
     if (tv_parts > nparts) nparts = tv_parts;
     DGCT_TRY(dalloc(&w.partial, nparts));
+    DGCT_TRY(dalloc(&w.partial_div, nparts));
     DGCT_TRY(dalloc(&w.S, 1));
     DGCT_TRY(dalloc(&w.log, (size_t)kMaxIters));
     DGCT_TRY(dalloc(&w.vc, (size_t)pl->nv));
@@ -547,13 +549,29 @@ int dgamp_ct_profile_iteration(dgamp_ct_plan_t pl, int32_t reps, double* h_ms, i
 
 int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t pl, int32_t iters) {
     if (!pl || iters < 0) return -1;
-    // per iteration, plus the image staging and scalar init before and the three V^-1 passes after
-    return (int64_t)iters * kernels_per_iteration(pl) + 5;
+    // per iteration, plus the image staging and scalar init before, and the
+    // pending-divergence finish and the three V^-1 passes after
+    return (int64_t)iters * kernels_per_iteration(pl) + 6;
 }
 
 }  // extern "C"
 
 namespace dgct {
+
+// After a solve's last iteration: the divergence its TV step left in partials
+// (the next iteration's output step would have finished it).
+__global__ void k_finish_pending(DevScalars* S, const double* partial_div, double N, double floor_rel,
+                                 IterLog* log) {
+    pending_tau_x(S, partial_div, N, floor_rel, log, true);
+    __syncwarp();
+    if (threadIdx.x == 0) S->div_pending = 0u;
+}
+
+static int solve_end(dgamp_ct_plan_s* pl, cudaStream_t st) {
+    k_finish_pending<<<1, 32, 0, st>>>(pl->ws.S, pl->ws.partial_div, (double)pl->N, pl->opt.tau_x_floor, pl->ws.log);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
 
 __global__ void k_init_scalars(DevScalars* S, double frob2, double logI0, double tau_x0) {
     DevScalars s;
@@ -602,6 +620,7 @@ int dgamp_ct_solve_trace(dgamp_ct_plan_t pl, const float* d_counts, double I0, i
             DGCT_CUDA(cudaMemcpyAsync(d_r_trace + (size_t)t * N, pl->ws.r, N * sizeof(float),
                                       cudaMemcpyDeviceToDevice, st));
     }
+    DGCT_TRY(solve_end(pl, st));
     DGCT_TRY(launch_precond_image(pl, pl->ws.x, d_mu_out, 1, st));
     if (h_tau_r) {
         std::vector<IterLog> lg(iters);
@@ -627,6 +646,7 @@ int dgamp_ct_solve(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t
     } else {
         for (int t = 0; t < iters; ++t) DGCT_TRY(enqueue_iteration(pl, st));
     }
+    DGCT_TRY(solve_end(pl, st));
     DGCT_TRY(launch_precond_image(pl, w.x, d_mu_out, 1, st));           // mu = V^-1 x
     if (d_x_out) DGCT_CUDA(cudaMemcpyAsync(d_x_out, w.x, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
     if (!stats) return DGAMP_CT_OK;

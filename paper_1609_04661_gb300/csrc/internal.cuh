@@ -50,7 +50,7 @@ struct DevScalars {
     unsigned int newton_capped;
     unsigned int floored;
     unsigned int nonfinite;
-    unsigned int pad;
+    unsigned int div_pending;   // TV divergence partial sums left for the next output step (0: none)
 };
 
 // Per-iteration log record (what dgamp_ct_stats exposes).
@@ -69,6 +69,7 @@ struct Workspace {
     float* y = nullptr;      // counts        [M]
     float2* fft2d = nullptr; // [2n][2n] complex scratch for V / V^-1
     double* partial = nullptr;     // block partial sums
+    double* partial_div = nullptr; // the TV divergence's block partial sums inside a solve
     DevScalars* S = nullptr;
     IterLog* log = nullptr;        // [kMaxIters]
     ViewConst* vc = nullptr;       // [n_views]

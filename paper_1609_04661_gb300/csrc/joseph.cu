@@ -151,6 +151,8 @@ constexpr int kBpViews = 256;
 __device__ __forceinline__ void bp_tau_r(DevScalars* __restrict__ S, const double* __restrict__ partial,
                                          int nparts, double M, double N, float* s_tau_r) {
     const int lane = threadIdx.x & 31;
+    // the divergence partials of the previous TV step have been consumed
+    if (lane == 0 && blockIdx.x == 0 && blockIdx.y == 0) S->div_pending = 0u;
     if (nparts == 0) {
         if (lane == 0) *s_tau_r = (float)S->tau_r;
         return;

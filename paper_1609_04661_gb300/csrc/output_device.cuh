@@ -67,6 +67,54 @@ __device__ __forceinline__ float mode_delta(float p, float y, float tau_p, float
     return d;
 }
 
+// The end of Step 4 of the previous iteration when the blocked TV denoiser
+// left its divergence as FP64 partial sums (S->div_pending of them in
+// partial_div; Eq. MC_SURE): D' = sum / (N eps), tau_x = max(tau_r D',
+// floor tau_r).  Run by one warp of every block of the output step that
+// needs tau_x: the partials are added in one fixed order (lane-strided, then
+// the warp's shuffle tree), so every block gets the same tau_x; the block
+// with record = true also stores D', tau_x, the iteration's log record and
+// the next t.  Returns tau_x (S->tau_x when nothing is pending).  The
+// back-projection that follows clears div_pending.
+// pre / npre: the lane's first partials (i = lane, lane + 32, ...), loaded
+// earlier by the caller to hide their latency (npre = 0: none).
+__device__ __forceinline__ double pending_tau_x(DevScalars* S, const double* __restrict__ partial_div, double N,
+                                               double floor_rel, IterLog* log, bool record,
+                                               const double* pre = nullptr, int npre = 0) {
+    const unsigned np = S->div_pending;
+    if (np == 0u) return S->tau_x;
+    const int lane = threadIdx.x & 31;
+    double a = 0.0;
+    for (int k = 0; k < npre; ++k) a += pre[k];
+    for (unsigned i = lane + 32u * (unsigned)npre; i < np; i += 32u) a += partial_div[i];
+    a = warp_sum(a);
+    const double div = a / (N * S->eps);
+    const double tau_r = S->tau_r;
+    double tx = tau_r * div;
+    const double fl = floor_rel * tau_r;
+    const bool floored = !(tx >= fl);
+    if (floored) tx = fl;
+    if (record && lane == 0) {
+        if (floored) S->floored += 1u;
+        if (!isfinite(tx)) S->nonfinite += 1u;
+        S->div = div;
+        S->tau_x = tx;
+        const unsigned tt = S->t;
+        if (tt >= 1u && tt <= (unsigned)kMaxIters) {
+            IterLog L;
+            L.tau_x = tx;
+            L.tau_p = S->tau_p;
+            L.tau_s = S->tau_s;
+            L.tau_r = tau_r;
+            L.div = div;
+            L.eps = S->eps;
+            log[tt - 1] = L;
+        }
+        S->t = tt + 1u;
+    }
+    return tx;
+}
+
 // One measurement: s (damped against s_prev = sp) into sv; returns tau_s_i.
 __device__ __forceinline__ float output_element(float zi, float sp, float yv, float tau_p, float inv_tp,
                                                 float logI0, int onsager, float damp_s, int truncate,

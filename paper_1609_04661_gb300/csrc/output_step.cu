@@ -9,14 +9,18 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_output_step(const T* z, const float* y, T* s, long long M, int use_prev,
               int from_scalars, double tau_p_arg, double logI0_arg, int onsager, float damp_s,
-              int truncate, double N, DevScalars* S, double* partial, double* tau_s_out) {
+              int truncate, double N, DevScalars* S, double* partial, double* tau_s_out,
+              const double* partial_div, double floor_rel, IterLog* log) {
     __shared__ double sm[32];
     __shared__ float s_tp, s_inv, s_logI0;
-    if (threadIdx.x == 0) {
-        double tp = from_scalars ? S->frob2 * S->tau_x / (double)M : tau_p_arg;
-        s_tp = (float)tp;
-        s_inv = (float)(1.0 / tp);
-        s_logI0 = (float)(from_scalars ? S->logI0 : logI0_arg);
+    if (threadIdx.x < 32) {
+        const double tx = from_scalars ? pending_tau_x(S, partial_div, N, floor_rel, log, blockIdx.x == 0) : 0.0;
+        if (threadIdx.x == 0) {
+            const double tp = from_scalars ? S->frob2 * tx / (double)M : tau_p_arg;
+            s_tp = (float)tp;
+            s_inv = (float)(1.0 / tp);
+            s_logI0 = (float)(from_scalars ? S->logI0 : logI0_arg);
+        }
     }
     __syncthreads();
     const float tau_p = s_tp, inv_tp = s_inv, logI0 = s_logI0;
@@ -44,11 +48,13 @@ int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y
     if (bf)   // z and s in BF16 (a solve with storage = 1); the counts stay FP32
         k_output_step<bf16s><<<blocks, 128, 0, st>>>((const bf16s*)z, y, (bf16s*)s, M, use_prev, from_scalars,
                                                      tau_p_arg, logI0_arg, onsager, damp_s, pl->opt.truncate_z,
-                                                     (double)pl->N, pl->ws.S, pl->ws.partial, tau_s_out);
+                                                     (double)pl->N, pl->ws.S, pl->ws.partial, tau_s_out,
+                                                     pl->ws.partial_div, pl->opt.tau_x_floor, pl->ws.log);
     else
         k_output_step<float><<<blocks, 128, 0, st>>>(z, y, s, M, use_prev, from_scalars, tau_p_arg, logI0_arg,
                                                      onsager, damp_s, pl->opt.truncate_z, (double)pl->N, pl->ws.S,
-                                                     pl->ws.partial, tau_s_out);
+                                                     pl->ws.partial, tau_s_out, pl->ws.partial_div,
+                                                     pl->opt.tau_x_floor, pl->ws.log);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -63,7 +69,7 @@ int launch_output_step_scratch(const float* z, const float* y, float* s, long lo
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
     k_output_step<float><<<(int)blocks, 256, 0, st>>>(z, y, s, M, use_prev, 0, tau_p, logI0, 1, 1.f, 0, 0.0, S,
-                                                      partial, tau_s_out);
+                                                      partial, tau_s_out, nullptr, 0.0, nullptr);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }

@@ -25,6 +25,9 @@ constexpr int kSinoMaxP = 8192;       // two padded buffers and the twiddles: 21
 // (s_prev and y are loaded before the first transform, which hides their
 // latency); beyond 2 n_det = kSinoPre * kSinoThreads they are loaded in place
 constexpr int kSinoPre = 4;
+// TV divergence partials each lane of warp 0 prefetches (10 x 32 covers the
+// 288 blocks of the 512 x 512 denoiser launch)
+constexpr int kDivPre = 10;
 
 // the value a store of v into T and a load back give
 __device__ __forceinline__ float as_stored(float v, const float*) { return v; }
@@ -34,7 +37,8 @@ template <typename T>
 __global__ void __launch_bounds__(kSinoThreads)
 k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __restrict__ hs, int nv, int nd,
             int P, const float* __restrict__ gain, const float2* __restrict__ tw_g, long long M,
-            int onsager, float damp_s, int truncate, DevScalars* S, double* __restrict__ partial) {
+            int onsager, float damp_s, int truncate, DevScalars* S, double* __restrict__ partial,
+            const double* __restrict__ partial_div, double N, double floor_rel, IterLog* log) {
     extern __shared__ float2 smem[];
     const int BL = fft_buf_len(P), TC = fft_twiddle_count(P);
     float2* a = smem;                 // [BL], padded layout
@@ -45,13 +49,18 @@ k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __
     const int va = 2 * blockIdx.x, vb = va + 1;
     const bool hasb = vb < nv;
     const int ne = hasb ? 2 * nd : nd;
-    if (threadIdx.x == 0) {
-        const double tp = S->frob2 * S->tau_x / (double)M;      // Step 2: tau_p
-        s_tp = (float)tp;
-        s_inv = (float)(1.0 / tp);
-        s_logI0 = (float)S->logI0;
-        // max |r| of this iteration is gathered by the back-projection that follows
-        if (blockIdx.x == 0) S->rmax_bits = 0u;
+    // tau_x of the previous iteration may still be in the TV step's partial
+    // sums: warp 0 loads its lanes' first kDivPre of them now and finishes
+    // the sum after the first transform pair, which hides the loads
+    double div_pre[kDivPre];
+    if (threadIdx.x < 32) {
+        const unsigned np = S->div_pending;
+#pragma unroll
+        for (int k = 0; k < kDivPre; ++k) {
+            const unsigned i = threadIdx.x + 32u * k;
+            div_pre[k] = i < np ? partial_div[i] : 0.0;
+        }
+        if (threadIdx.x == 0 && blockIdx.x == 0) S->rmax_bits = 0u;   // refilled by the back-projection
     }
     // s_prev and y of this thread's first kSinoPre elements
     float pre_sp[kSinoPre], pre_y[kSinoPre];
@@ -90,6 +99,16 @@ k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __
     r = fft_stockham(r, o, P, tw, 1.f);
     o = (r == a) ? b : a;
 
+    if (threadIdx.x < 32) {
+        const double tx = pending_tau_x(S, partial_div, N, floor_rel, log, blockIdx.x == 0, div_pre, kDivPre);
+        if (threadIdx.x == 0) {
+            const double tp = S->frob2 * tx / (double)M;          // Step 2: tau_p
+            s_tp = (float)tp;
+            s_inv = (float)(1.0 / tp);
+            s_logI0 = (float)S->logI0;
+        }
+    }
+    __syncthreads();
     // output step on both views; s (as stored) goes into o, zero-padded
     const float tau_p = s_tp, inv_tp = s_inv, logI0 = s_logI0;
     for (int i = nd + threadIdx.x; i < P; i += blockDim.x) o[fpad(i)] = make_float2(0.f, 0.f);
@@ -180,11 +199,13 @@ int launch_sino_step(const dgamp_ct_plan_s* pl, cudaStream_t st, int bf) {
         k_sino_step<bf16s><<<grid, kSinoThreads, sm, st>>>((const bf16s*)w.zraw, w.y, (bf16s*)w.s, (bf16s*)w.hs,
                                                            pl->nv, pl->nd, pl->P, w.gain, w.tw, pl->M,
                                                            pl->opt.onsager, damp_s, pl->opt.truncate_z, w.S,
-                                                           w.partial);
+                                                           w.partial, w.partial_div, (double)pl->N,
+                                                           pl->opt.tau_x_floor, w.log);
     else
         k_sino_step<float><<<grid, kSinoThreads, sm, st>>>(w.zraw, w.y, w.s, w.hs, pl->nv, pl->nd, pl->P, w.gain,
                                                            w.tw, pl->M, pl->opt.onsager, damp_s, pl->opt.truncate_z,
-                                                           w.S, w.partial);
+                                                           w.S, w.partial, w.partial_div, (double)pl->N,
+                                                           pl->opt.tau_x_floor, w.log);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }

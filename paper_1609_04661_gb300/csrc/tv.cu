@@ -114,6 +114,7 @@ struct TvFinal {
     uint2 key;
     double tau_x_floor;
     double* partial;
+    double* partial_div;   // a solve's divergence partials, finished by the next output step
     IterLog* log;
     double* div_out;       // nullable
     int solve_mode;        // 1: update tau_x, the log and t in S
@@ -338,6 +339,16 @@ k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
     if (nimg < 2) return;
     const int nblk = (int)(gridDim.x * gridDim.y * gridDim.z);
     const int bid = (int)((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+    if (F.solve_mode) {
+        // inside a solve the next output step adds the partials (it needs
+        // tau_x first): no grid-wide tail here
+        acc = block_sum(acc, red);
+        if (threadIdx.x == 0) {
+            F.partial_div[bid] = acc;
+            if (bid == 0) S->div_pending = (unsigned)nblk;
+        }
+        return;
+    }
     tv_divergence_finish(acc, nblk, bid, N, S, F, red, &am_last);
 }
 
@@ -472,6 +483,7 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     F.key = probe_key(pl);
     F.tau_x_floor = pl->opt.tau_x_floor;
     F.partial = pl->ws.partial;
+    F.partial_div = pl->ws.partial_div;
     F.log = pl->ws.log;
     F.div_out = div_out;
     F.solve_mode = solve_mode;
