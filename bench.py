@@ -50,7 +50,7 @@ FALLBACK_HBM_GBS = 6800.0
 # launches of one iteration, from the ncu capture summarised in
 # profiles/tv_blocked_ellipse512_v64.md, valid only for the configuration
 # profiled there (steps per launch, region rows) and the current kernel.
-TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 32, "bytes_per_iteration": 2120960 + 8430592}
+TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 64, "bytes_per_iteration": 2121216 + 8434944}
 
 
 # ----------------------------------------------------------------- helpers --
@@ -440,6 +440,10 @@ def run_gpu(args):
     case = synth.make_case(WORKLOAD, seed=1000 + rank)
     T = case["iters"]
     plan = dg.Plan(case["n"], case["n_views"], case["n_det"], **TV)
+    if args.tuning:
+        # pin implementation choices (e.g. to profile the configuration the
+        # plan-time timing picks when run without a profiler)
+        plan.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))})
     counts = torch.as_tensor(case["y"]).cuda()
     mu = torch.empty((case["n"], case["n"]), device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -588,6 +592,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain section")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-batch section")
     ap.add_argument("--c5", action="store_true", help="add the 128-slice 1024x1024 BF16-storage workload (~1 min)")
+    ap.add_argument("--tuning", default="", help="pin the headline plan's tuning, e.g. bp_mode=1,tv_kb=10")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -278,3 +278,16 @@ def test_solve_rejects_bad_arguments(dg, case64):
         for bad in [dict(I0=0.0, iters=3), dict(I0=float("nan"), iters=3), dict(I0=1e4, iters=0)]:
             with pytest.raises(dg.DgampError):
                 pl.solve(cu(c["y"]), bad["I0"], bad["iters"])
+
+
+def test_solve_after_profiling_equals_a_fresh_solve(dg, case64):
+    """profile_iteration runs iterations on the plan's state and may leave the
+    denoiser's divergence partials pending; the next solve starts clean."""
+    c, g = case64
+    with dg.Plan(g.n, g.n_views, g.n_det) as pl:
+        fresh = host(pl.solve(cu(c["y"]), c["I0"], 4))
+        pl.profile_iteration(reps=2)
+        mu, st = pl.solve(cu(c["y"]), c["I0"], 4, with_stats=True)
+        again = host(mu)
+    assert np.array_equal(fresh, again)
+    assert st["iters_done"] == 4 and np.all(np.isfinite(st["tau_x"]))
