@@ -122,11 +122,12 @@ struct TvFinal {
 };
 
 // A block holds a region of kTvRW = 64 columns by RH = 4 WY rows of one image
-// in registers: thread (warp w, lane l) owns rows 4w..4w+3 of columns l and
-// l + 32.  Horizontal neighbours come from warp shuffles (lane 0 and lane 31
-// wrap between the two columns), vertical ones from the thread's own
-// registers except across warps, where the first row's q and the last row's
-// py pass through shared memory (two barriers per step).  After KB steps the
+// in registers: thread (warp w, lane l) owns rows 4w..4w+3 of the adjacent
+// columns 2l and 2l + 1.  A horizontal neighbour is the thread's own other
+// column or, once per row and direction, a warp shuffle from the next lane;
+// vertical neighbours come from the thread's own registers except across
+// warps, where the first row's q and the last row's py pass through shared
+// memory (two barriers per step).  After KB steps the
 // region minus KB pixels on each side holds exact duals and is written back.
 constexpr int kTvU = 2;            // columns per thread
 constexpr int kTvV = 4;            // rows per thread
@@ -149,8 +150,13 @@ __device__ __forceinline__ void tv_region_steps(float (&px)[kTvV][kTvU], float (
         for (int v = 0; v < V; ++v) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const float send = lane == 31 ? (u > 0 ? px[v][u - 1] : 0.f) : px[v][u];
-                const float pxl = __shfl_sync(0xffffffffu, send, (lane + 31) & 31);
+                float pxl;
+                if (u > 0) {
+                    pxl = px[v][u - 1];
+                } else {
+                    const float t = __shfl_up_sync(0xffffffffu, px[v][U - 1], 1);
+                    pxl = lane > 0 ? t : 0.f;
+                }
                 const float pyu = v > 0 ? py[v - 1][u] : (w > 0 ? e_py[w - 1][u][lane] : 0.f);
                 float qq = (px[v][u] - pxl + py[v][u] - pyu) - rl[v][u];
                 if (BORDER && !((inside >> (v * U + u)) & 1u)) qq = 0.f;
@@ -165,8 +171,13 @@ __device__ __forceinline__ void tv_region_steps(float (&px)[kTvV][kTvU], float (
         for (int v = 0; v < V; ++v) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const float send = lane == 0 ? (u + 1 < U ? q[v][u + 1] : 0.f) : q[v][u];
-                const float qr = __shfl_sync(0xffffffffu, send, (lane + 1) & 31);
+                float qr;
+                if (u + 1 < U) {
+                    qr = q[v][u + 1];
+                } else {
+                    const float t = __shfl_down_sync(0xffffffffu, q[v][0], 1);
+                    qr = lane < 31 ? t : 0.f;
+                }
                 const float qd = v + 1 < V ? q[v + 1][u] : (w + 1 < WY ? e_q[w + 1][u][lane] : 0.f);
                 float gx = qr - q[v][u];
                 float gy = qd - q[v][u];
@@ -267,7 +278,7 @@ k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
         const int gi = gi0 + w * V + v;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int gj = gj0 + 32 * u + lane;
+            const int gj = gj0 + U * lane + u;
             const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
             float rv = 0.f;
             float2 p = make_float2(0.f, 0.f);
@@ -298,7 +309,7 @@ k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
             const int gi = gi0 + rr;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int cc = 32 * u + lane;
+                const int cc = U * lane + u;
                 const int gj = gj0 + cc;
                 if (cc < KB || cc >= RW - KB || gi >= n || gj >= n) continue;
                 pout[img + (size_t)gi * n + gj] = make_float2(px[v][u], py[v][u]);
@@ -317,10 +328,15 @@ k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
         const int gi = gi0 + rr;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const float send = lane == 31 ? (u > 0 ? px[v][u - 1] : 0.f) : px[v][u];
-            const float pxl = __shfl_sync(0xffffffffu, send, (lane + 31) & 31);
+            float pxl;
+            if (u > 0) {
+                pxl = px[v][u - 1];
+            } else {
+                const float t = __shfl_up_sync(0xffffffffu, px[v][U - 1], 1);
+                pxl = lane > 0 ? t : 0.f;
+            }
             const float pyu = v > 0 ? py[v - 1][u] : (w > 0 ? e_py[w - 1][u][lane] : 0.f);
-            const int cc = 32 * u + lane;
+            const int cc = U * lane + u;
             const int gj = gj0 + cc;
             if (rr < E || rr >= RH - KB || cc < E || cc >= RW - KB || gi >= n || gj >= n) continue;
             const size_t o = (size_t)gi * n + gj;
