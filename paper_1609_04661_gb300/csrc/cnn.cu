@@ -65,33 +65,56 @@ __device__ __forceinline__ void mma16816(float* c, uint32_t a0, uint32_t a1, uin
 // a1 = relu(b0 + conv(u, W0)), u = r / sigma; also stores u for the weight gradient.
 // Tangent form (b0 == nullptr, mask != nullptr): a1 = conv(u, W0) where the
 // primal layer-1 activation `mask` is positive, else 0.
-__global__ void k_conv_first(const float* __restrict__ r, const float* __restrict__ sigma, int B, int H, int W,
-                             const float* __restrict__ w0, const float* __restrict__ b0,
-                             const bf16* __restrict__ mask, bf16* __restrict__ a1, float* __restrict__ u_out) {
+//
+// Activations are [pixel][64] BF16, 128 bytes per pixel, so the 32 pixels of
+// a warp touch 32 rows: a warp's output rows (and mask rows) pass through
+// shared memory and reach global memory as whole rows, contiguous across the
+// warp.  In shared memory a row takes PSTR = 72 BF16 (144 bytes), so the
+// eight lanes of one 16-byte access phase that touch the same chunk of eight
+// consecutive rows hit distinct banks, while every lane works on the same
+// chunk and the weights it reads are broadcasts.
+constexpr int kC1Threads = 128;
+
+__global__ void __launch_bounds__(kC1Threads)
+k_conv_first(const float* __restrict__ r, const float* __restrict__ sigma, int B, int H, int W,
+             const float* __restrict__ w0, const float* __restrict__ b0,
+             const bf16* __restrict__ mask, bf16* __restrict__ a1, float* __restrict__ u_out) {
     __shared__ float sw[9 * CH + CH];
+    __shared__ __align__(16) bf16 stage[kC1Threads / 32][32 * PSTR];   // one warp's 32 rows
     for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = w0[i];
     for (int i = threadIdx.x; i < CH; i += blockDim.x) sw[9 * CH + i] = b0 ? b0[i] : 0.f;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const long long HW = (long long)H * W, total = (long long)B * HW;
+    const long long p0 = (long long)blockIdx.x * kC1Threads + wp * 32, p = p0 + lane;
+    bf16* S = stage[wp];
+    if (mask) {   // the warp's mask rows, contiguous loads
+        for (int i = lane; i < 32 * 8; i += 32) {
+            const long long pp = p0 + (i >> 3);
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (pp < total) v = *reinterpret_cast<const uint4*>(mask + pp * CH + (i & 7) * 8);
+            *reinterpret_cast<uint4*>(S + (i >> 3) * PSTR + (i & 7) * 8) = v;
+        }
+    }
     __syncthreads();
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long HW = (long long)H * W;
-    if (p >= (long long)B * HW) return;
-    const int b = (int)(p / HW);
-    const int y = (int)((p - b * HW) / W), x = (int)(p - b * HW - (long long)y * W);
+    const bool live = p < total;
+    const int b = live ? (int)(p / HW) : 0;
+    const int y = live ? (int)((p - b * HW) / W) : 0, x = live ? (int)(p - b * HW - (long long)y * W) : 0;
     const float inv = 1.0f / sigma[b];
     const float* img = r + b * HW;
     float u[9];
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
         const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-        u[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? img[(long long)yy * W + xx] * inv : 0.f;
+        u[t] = (live && yy >= 0 && yy < H && xx >= 0 && xx < W) ? img[(long long)yy * W + xx] * inv : 0.f;
     }
-    if (u_out) u_out[p] = u[4];
-    bf16* out = a1 + p * CH;
+    if (u_out && live) u_out[p] = u[4];
 #pragma unroll 1
-    for (int c0 = 0; c0 < CH; c0 += 8) {
+    for (int k = 0; k < 8; ++k) {
+        const int c0 = k * 8;
+        bf16* row = S + lane * PSTR + c0;
         __align__(16) bf16 v[8];
         __align__(16) bf16 mk[8];
-        if (mask) *reinterpret_cast<uint4*>(mk) = *reinterpret_cast<const uint4*>(mask + p * CH + c0);
+        if (mask) *reinterpret_cast<uint4*>(mk) = *reinterpret_cast<const uint4*>(row);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             float acc = sw[9 * CH + c0 + j];
@@ -102,7 +125,14 @@ __global__ void k_conv_first(const float* __restrict__ r, const float* __restric
             else
                 v[j] = __float2bfloat16_rn(fmaxf(acc, 0.f));
         }
-        *reinterpret_cast<uint4*>(out + c0) = *reinterpret_cast<const uint4*>(v);
+        *reinterpret_cast<uint4*>(row) = *reinterpret_cast<const uint4*>(v);
+    }
+    __syncwarp();
+    for (int i = lane; i < 32 * 8; i += 32) {   // the warp's rows, contiguous stores
+        const long long pp = p0 + (i >> 3);
+        if (pp < total)
+            *reinterpret_cast<uint4*>(a1 + pp * CH + (i & 7) * 8) =
+                *reinterpret_cast<const uint4*>(S + (i >> 3) * PSTR + (i & 7) * 8);
     }
 }
 
@@ -118,37 +148,64 @@ __global__ void k_conv_first(const float* __restrict__ r, const float* __restric
 // ------------------------------------------------------------ last layer --
 // f = b16 + conv(a16, W16) (W16 as [tap][ci]); D = r - sigma f.  b16 == nullptr
 // drops the bias (tangent form: r = the direction b, D = b - sigma J_f (b / sigma)).
-__global__ void k_conv_last(const bf16* __restrict__ a16, const float* __restrict__ w16, const float* __restrict__ b16,
-                            const float* __restrict__ r, const float* __restrict__ sigma, int B, int H, int W,
-                            float* __restrict__ f_out, float* __restrict__ d_out) {
-    __shared__ float sw[9 * CH];
+// A block computes kCLRows x kCLCols pixels (warp = one row, lane = one
+// pixel) from the tile of input rows with its one-pixel halo, staged in shared
+// memory by contiguous 16-byte loads (rows PSTR apart, as in k_conv_first);
+// each lane reads its nine 128-byte taps there.
+constexpr int kCLRows = 4, kCLCols = 32;
+constexpr int kCLTile = (kCLRows + 2) * (kCLCols + 2);      // staged pixels
+
+__global__ void __launch_bounds__(32 * kCLRows)
+k_conv_last(const bf16* __restrict__ a16, const float* __restrict__ w16, const float* __restrict__ b16,
+            const float* __restrict__ r, const float* __restrict__ sigma, int B, int H, int W,
+            float* __restrict__ f_out, float* __restrict__ d_out) {
+    __shared__ __align__(16) float sw[9 * CH];
+    __shared__ __align__(16) bf16 tile[kCLTile * PSTR];
     for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = w16[i];
+    const int bz = blockIdx.z, x0 = blockIdx.x * kCLCols, y0 = blockIdx.y * kCLRows;
+    for (int i = threadIdx.x; i < kCLTile * 8; i += blockDim.x) {
+        const int pix = i >> 3, ch = (i & 7) * 8;
+        const int yy = y0 - 1 + pix / (kCLCols + 2), xx = x0 - 1 + pix % (kCLCols + 2);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+            v = *reinterpret_cast<const uint4*>(a16 + (((long long)bz * H + yy) * W + xx) * CH + ch);
+        *reinterpret_cast<uint4*>(tile + pix * PSTR + ch) = v;
+    }
     __syncthreads();
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long HW = (long long)H * W;
-    if (p >= (long long)B * HW) return;
-    const int b = (int)(p / HW);
-    const int y = (int)((p - b * HW) / W), x = (int)(p - b * HW - (long long)y * W);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int y = y0 + wp, x = x0 + lane;
     float acc = b16 ? b16[0] : 0.f;
 #pragma unroll 1
     for (int t = 0; t < 9; ++t) {
-        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-        const bf16* a = a16 + (((long long)b * H + yy) * W + xx) * CH;
+        const bf16* src = tile + ((wp + t / 3) * (kCLCols + 2) + lane + t % 3) * PSTR;
+        const float* wt = sw + t * CH;
 #pragma unroll
-        for (int c0 = 0; c0 < CH; c0 += 8) {
-            const uint4 raw = *reinterpret_cast<const uint4*>(a + c0);
+        for (int k = 0; k < 8; ++k) {
+            const int c0 = k * 8;
+            const uint4 raw = *reinterpret_cast<const uint4*>(src + c0);
+            const float4 wa = *reinterpret_cast<const float4*>(wt + c0);
+            const float4 wb = *reinterpret_cast<const float4*>(wt + c0 + 4);
             const __nv_bfloat162* v2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float2 f2 = __bfloat1622float2(v2[k]);
-                acc = fmaf(f2.x, sw[t * CH + c0 + 2 * k], acc);
-                acc = fmaf(f2.y, sw[t * CH + c0 + 2 * k + 1], acc);
-            }
+            const float2 f0 = __bfloat1622float2(v2[0]), f1 = __bfloat1622float2(v2[1]);
+            const float2 f2 = __bfloat1622float2(v2[2]), f3 = __bfloat1622float2(v2[3]);
+            acc = fmaf(f0.x, wa.x, acc);
+            acc = fmaf(f0.y, wa.y, acc);
+            acc = fmaf(f1.x, wa.z, acc);
+            acc = fmaf(f1.y, wa.w, acc);
+            acc = fmaf(f2.x, wb.x, acc);
+            acc = fmaf(f2.y, wb.y, acc);
+            acc = fmaf(f3.x, wb.z, acc);
+            acc = fmaf(f3.y, wb.w, acc);
         }
     }
+    if (y >= H || x >= W) return;
+    const long long p = ((long long)bz * H + y) * W + x;
     if (f_out) f_out[p] = acc;
-    if (d_out) d_out[p] = r[p] - sigma[b] * acc;
+    if (d_out) d_out[p] = r[p] - sigma[bz] * acc;
+}
+
+static dim3 conv_last_grid(int B, int H, int W) {
+    return dim3((unsigned)((W + kCLCols - 1) / kCLCols), (unsigned)((H + kCLRows - 1) / kCLRows), (unsigned)B);
 }
 
 // g16 = (sum_tap gout[p - off(tap)] W16[tap][ci]) * (a16 > 0)
@@ -521,7 +578,8 @@ static int cnn_forward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int 
     for (int l = 1; l <= L - 2; ++l)
         DGCT_TRY(launch_conv64_tc(0, act(l), c->wh, L - 2, l - 1, c->master + c->b_off[l], nullptr, act(l + 1), B, H,
                                   W, c->sm_count, c->tc_err, st));
-    k_conv_last<<<blocks, 128, 0, st>>>(act(L - 1), c->w16, c->master + c->b_off[L - 1], r, sig, B, H, W, c->f, d_out);
+    k_conv_last<<<conv_last_grid(B, H, W), 32 * kCLRows, 0, st>>>(act(L - 1), c->w16, c->master + c->b_off[L - 1], r, sig, B,
+                                                                H, W, c->f, d_out);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -615,10 +673,12 @@ static int jvp_passes(dgamp_ct_cnn_s* c, const float* r, const float* b, int H, 
         DGCT_TRY(launch_conv64_tc(1, tang(l), c->wh, L - 2, l - 1, nullptr, prim(l + 1), tang(l + 1), 1, H, W,
                                   c->sm_count, c->tc_err, st));
     }
-    k_conv_last<<<blocks, 128, 0, st>>>(prim(L - 1), c->w16, c->master + c->b_off[L - 1], r, c->sig_buf, 1, H, W,
+    k_conv_last<<<conv_last_grid(1, H, W), 32 * kCLRows, 0, st>>>(prim(L - 1), c->w16, c->master + c->b_off[L - 1], r,
+                                                                c->sig_buf, 1, H, W,
                                         nullptr, d_out);
     DGCT_LAUNCH_CHECK();
-    k_conv_last<<<blocks, 128, 0, st>>>(tang(L - 1), c->w16, nullptr, b, c->sig_buf, 1, H, W, nullptr, d_jb);
+    k_conv_last<<<conv_last_grid(1, H, W), 32 * kCLRows, 0, st>>>(tang(L - 1), c->w16, nullptr, b, c->sig_buf, 1, H, W,
+                                                                nullptr, d_jb);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
