@@ -50,10 +50,11 @@ def _images(seed, B=2, H=40, W=36):
     return r.astype(np.float32).astype(np.float64), x.astype(np.float32).astype(np.float64)
 
 
-def test_forward_matches_reference(dg):
+@pytest.mark.parametrize("H,W", [(40, 36), (37, 45)])        # ragged tiles of the end layers
+def test_forward_matches_reference(dg, H, W):
     from paper_1609_04661_gb300.binding import flatten_params
     ws, bs = _params(3)
-    r, _ = _images(4)
+    r, _ = _images(4, H=H, W=W)
     sig = np.array([0.5, 2.0])
     with dg.CNN(17, seed=0) as net:
         net.set_params(flatten_params(ws, bs))
