@@ -1,0 +1,53 @@
+"""Parity at the full size the benchmark times: the 512 x 512 / 64-view /
+729-bin workload (I0 = 1e5, seed 1000) in the benchmark's configuration
+(prox-TV with c = 3 and 20 Chambolle steps, damping 0.5) and with the plan's
+own implementation choices -- the launch configuration bench.py runs: the
+fused sinogram kernel, the tuned TV launches and back-projection.  The
+oracle computes its own ||Phi~||_F^2 and runs the same 5 iterations in FP64;
+the bound is the 1e-3 of the small solve tests.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gamp
+from oracle.geometry import Geometry
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_04661_gb300 import build
+    build.build()
+    import paper_1609_04661_gb300 as dg
+    dg.load()
+    return dg
+
+
+def test_benchmark_workload_against_oracle(dg):
+    c = synth.make_case("ellipse512_v64", seed=1000)
+    g = Geometry(c["n"], c["n_views"], c["n_det"])
+    T = 5
+    kw = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
+    log = []
+    mu_ref = gamp.ct_solve(c["y"], c["I0"], g, T, gamp.Options(**kw), log=log)
+    with dg.Plan(g.n, g.n_views, g.n_det, **kw) as pl:
+        tun = pl.tuning()
+        mu, st = pl.solve(torch.as_tensor(c["y"]).cuda(), c["I0"], T, with_stats=True)
+        mu = mu.cpu().numpy()
+    assert tun["sino_fused"] == 1
+    assert st["iters_done"] == T and np.all(np.isfinite(mu))
+    assert rel(mu, mu_ref) < 1e-3
+    assert np.allclose(st["tau_r"], [lg.tau_r for lg in log], rtol=1e-3)
+    assert np.allclose(st["tau_x"], [lg.tau_x for lg in log], rtol=2e-2)
