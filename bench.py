@@ -50,7 +50,7 @@ FALLBACK_HBM_GBS = 6800.0
 # launches of one iteration, from the ncu capture summarised in
 # profiles/tv_blocked_ellipse512_v64.md, valid only for the configuration
 # profiled there (steps per launch, region rows) and the current kernel.
-TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 64, "bytes_per_iteration": 2121216 + 8434944}
+TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 64, "bytes_per_iteration": 2119936 + 8433664 + 512}
 
 
 # ----------------------------------------------------------------- helpers --
