@@ -156,6 +156,8 @@ typedef struct {
                              of a view that tap it), 1 = ray-driven over 16 x 16 image
                              tiles with per-warp shared-memory accumulators.  Both are the
                              exact transpose of the projector and deterministic */
+    int32_t pj_seg;       /* A: warps that split the step range of one group of 32 rays,
+                             8, 16 or 32 (the partial sums are added in a fixed order) */
 } dgamp_ct_tuning;
 
 /* get: writes the plan's choices.  set: fields < 0 keep the current choice;

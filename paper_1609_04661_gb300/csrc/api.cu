@@ -202,6 +202,7 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_TRY(sino_step_set_smem_limit(pl));
     DGCT_TRY(filter_autotune(pl));
     DGCT_TRY(backproject_autotune(pl));
+    DGCT_TRY(project_autotune(pl));
     pl->sino_fused = sino_step_eligible(pl) ? 1 : 0;
     return DGAMP_CT_OK;
 }
@@ -431,12 +432,14 @@ int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, dgamp_ct_tuning* out) {
     out->tv_rows = pl->tv_rows;
     out->sino_fused = pl->sino_fused;
     out->bp_mode = pl->bp_mode;
+    out->pj_seg = pl->pj_seg;
     return DGAMP_CT_OK;
 }
 
 int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
     if (!pl || !t || t->filter_mode > 1 || t->tv_kb > 10 || t->tv_kb == 0 || t->sino_fused > 1 || t->bp_mode > 1)
         return DGAMP_CT_ERR_INVALID_ARG;
+    if (t->pj_seg >= 0 && t->pj_seg != 8 && t->pj_seg != 16 && t->pj_seg != 32) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->tv_rows >= 0 && t->tv_rows != 32 && t->tv_rows != 64 && t->tv_rows != 128) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->sino_fused == 1 && !sino_step_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (t->filter_mode >= 0) pl->filter_mode = t->filter_mode;
@@ -444,6 +447,7 @@ int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
     if (t->tv_rows > 0) pl->tv_rows = t->tv_rows;
     if (t->sino_fused >= 0) pl->sino_fused = t->sino_fused;
     if (t->bp_mode >= 0) pl->bp_mode = t->bp_mode;
+    if (t->pj_seg > 0) pl->pj_seg = t->pj_seg;
     drop_graph(pl);
     return DGAMP_CT_OK;
 }

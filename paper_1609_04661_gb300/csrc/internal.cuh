@@ -101,6 +101,7 @@ struct dgamp_ct_plan_s {
     int filter_mode = 0;                   // H by 0: FFT, 1: Toeplitz product (plan-time choice)
     int sino_fused = 0;                    // solve: H A x, output step, H s in one kernel (k_sino_step)
     int bp_mode = 0;                       // A^T: 0 pixel-driven gather, 1 ray-driven tiles (plan-time choice)
+    int pj_seg = 8;                        // A: step segments (warps) per ray group, 8/16/32 (plan-time choice)
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;   // stream the graph was captured for (identity only)
@@ -219,6 +220,7 @@ int fill_stats(const dgamp_ct_plan_s* pl, int iters, dgamp_ct_stats* stats);
 int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t st, int bf = 0);
 int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf = 0);
 int backproject_autotune(dgamp_ct_plan_s* pl);
+int project_autotune(dgamp_ct_plan_s* pl);
 int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
                        float* out, int update, cudaStream_t st, int bf = 0, int nparts = 0);
 int launch_frobenius(dgamp_ct_plan_s* pl);

@@ -75,13 +75,15 @@ __device__ __forceinline__ void step_range(float base, float a_step, int n, int&
     s1 = min(n - 1, (int)ceilf(hi) + 1);
 }
 
-// One block = 32 adjacent rays of one view; its 8 warps march disjoint
-// eighths of the step range of those rays and the partial sums are added in
-// a fixed order, so the result does not depend on scheduling.  A warp's 32
-// rays read ~32-46 adjacent floats of one staged line per step.
-constexpr int kPjRays = 32, kPjSeg = 8;
+// One block = 32 adjacent rays of one view; its SEG warps (8, 16 or 32,
+// chosen at plan time) march disjoint parts of the step range of those rays
+// and the partial sums are added in a fixed order, so the result does not
+// depend on scheduling.  A warp's 32 rays read ~32-46 adjacent floats of one
+// staged line per step; the gathers wait on L2, so more warps per ray group
+// hide more of that latency, up to the point where the segments get short.
+constexpr int kPjRays = 32;
 
-template <typename T>
+template <typename T, int kPjSeg>
 __global__ void __launch_bounds__(kPjRays * kPjSeg)
 k_project(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int n, int nd,
           const ViewConst* __restrict__ vcs, T* __restrict__ sino) {
@@ -122,13 +124,23 @@ k_project(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int n, in
     }
 }
 
-int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf) {
-    dim3 blk(kPjRays * kPjSeg), grd((pl->nd + kPjRays - 1) / kPjRays, pl->nv);
+template <int SEG>
+static void launch_project_seg(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf) {
+    dim3 blk(kPjRays * SEG), grd((pl->nd + kPjRays - 1) / kPjRays, pl->nv);
     if (bf)
-        k_project<bf16s><<<grd, blk, 0, st>>>((const bf16s*)pl->ws.XR, (const bf16s*)pl->ws.XC, pl->ldp, pl->n,
-                                              pl->nd, pl->ws.vc, (bf16s*)sino);
+        k_project<bf16s, SEG><<<grd, blk, 0, st>>>((const bf16s*)pl->ws.XR, (const bf16s*)pl->ws.XC, pl->ldp,
+                                                   pl->n, pl->nd, pl->ws.vc, (bf16s*)sino);
     else
-        k_project<float><<<grd, blk, 0, st>>>(pl->ws.XR, pl->ws.XC, pl->ldp, pl->n, pl->nd, pl->ws.vc, sino);
+        k_project<float, SEG><<<grd, blk, 0, st>>>(pl->ws.XR, pl->ws.XC, pl->ldp, pl->n, pl->nd, pl->ws.vc, sino);
+}
+
+int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf) {
+    if (pl->pj_seg == 32)
+        launch_project_seg<32>(pl, sino, st, bf);
+    else if (pl->pj_seg == 16)
+        launch_project_seg<16>(pl, sino, st, bf);
+    else
+        launch_project_seg<8>(pl, sino, st, bf);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -403,6 +415,38 @@ int backproject_autotune(dgamp_ct_plan_s* pl) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     pl->bp_mode = best_mode;
+    return rc;
+}
+
+// Plan-time choice of the step segments per ray group of A (same sums in
+// another order): time 8, 16 and 32 on the plan's geometry (the staged image
+// buffers' contents do not change the work) and keep the fastest.
+int project_autotune(dgamp_ct_plan_s* pl) {
+    cudaEvent_t e0, e1;
+    DGCT_CUDA(cudaEventCreate(&e0));
+    DGCT_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_seg = 8, rc = DGAMP_CT_OK;
+    const int segs[3] = {8, 16, 32};
+    for (int k = 0; k < 3 && rc == DGAMP_CT_OK; ++k) {
+        pl->pj_seg = segs[k];
+        for (int rep = 0; rep < 6 && rc == DGAMP_CT_OK; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, 0);
+            rc = launch_project(pl, pl->ws.zraw, 0, 0);
+        }
+        cudaEventRecord(e1, 0);
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (rc == DGAMP_CT_OK && e != cudaSuccess) rc = cuda_fail(e);
+        float ms = 0.f;
+        if (rc == DGAMP_CT_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == DGAMP_CT_OK && ms < best) {
+            best = ms;
+            best_seg = segs[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pl->pj_seg = best_seg;
     return rc;
 }
 

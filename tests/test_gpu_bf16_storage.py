@@ -78,9 +78,12 @@ def test_storage_option_is_validated_and_single_steps_stay_fp32(dg):
     one on a fresh plan (the guard cells are rewritten at each staging)."""
     c = synth.make_case("ellipse64_v30")
     y = torch.as_tensor(c["y"]).cuda()
+    pin = dict(pj_seg=8, bp_mode=1)      # the two plans sum in the same order
     with dg.Plan(c["n"], c["n_views"], c["n_det"], storage=1) as fresh:
+        fresh.set_tuning(**pin)
         mu_fresh = fresh.solve(y, c["I0"], 3).cpu().numpy()
     with dg.Plan(c["n"], c["n_views"], c["n_det"]) as pl:
+        pl.set_tuning(**pin)
         with pytest.raises(dg.DgampError):
             pl.set_options(storage=2)
         pl.set_options(storage=0)

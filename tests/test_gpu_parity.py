@@ -64,10 +64,13 @@ def _img(n, seed, kind="random"):
 
 @pytest.mark.parametrize("n,nv,nd,ang", GEOMS + [(512, 4, 729, None), (300, 5, 1100, None)])
 @pytest.mark.parametrize("kind", ["random", "phantom"])
-def test_project_matches_oracle(dg, n, nv, nd, ang, kind):
+@pytest.mark.parametrize("pj_seg", [8, 16, 32])            # warps splitting the steps of 32 rays
+def test_project_matches_oracle(dg, n, nv, nd, ang, kind, pj_seg):
     g = Geometry(n, nv, nd, ang)
     x = _img(n, 3, kind)
     with dg.Plan(n, nv, nd, angles=ang) as pl:
+        pl.set_tuning(pj_seg=pj_seg)
+        assert pl.tuning()["pj_seg"] == pj_seg
         z = host(pl.project(cu(x)))
         zp = host(pl.project(cu(x), precond=True))
         again = host(pl.project(cu(x)))
@@ -259,7 +262,7 @@ def test_solve_same_with_either_backprojection(dg, case64, storage):
     out = {}
     for mode in (0, 1):
         with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, damp_x=0.7, damp_s=0.7, storage=storage) as pl:
-            pl.set_tuning(bp_mode=mode)
+            pl.set_tuning(bp_mode=mode, pj_seg=8)
             out[mode] = host(pl.solve(cu(c["y"]), c["I0"], 5))
     assert rel(out[1], out[0]) < (1e-4 if storage == 0 else 3e-3)
 

@@ -60,7 +60,7 @@ def test_fused_solve_matches_oracle_and_unfused(dg, n, nv, nd, I0, trunc):
     for fused in (1, 0):
         with dg.Plan(n, nv, nd, **kw) as pl:
             assert pl.tuning()["sino_fused"] == 1          # the default where P allows it
-            pl.set_tuning(sino_fused=fused)
+            pl.set_tuning(sino_fused=fused, pj_seg=8, bp_mode=1)   # only the sinogram step differs
             mu, st = pl.solve(torch.as_tensor(y).cuda(), I0, T, with_stats=True)
             out[fused] = (mu.cpu().numpy(), st)
     assert rel(out[1][0], ref) < 1e-3
@@ -77,7 +77,7 @@ def test_fused_single_view_one_iteration(dg):
     out = {}
     for fused in (1, 0):
         with dg.Plan(n, nv, nd, c_tv=3.0, k_tv=20) as pl:
-            pl.set_tuning(sino_fused=fused)
+            pl.set_tuning(sino_fused=fused, pj_seg=8, bp_mode=1)   # only the sinogram step differs
             out[fused] = pl.solve(torch.as_tensor(y).cuda(), I0, 1).cpu().numpy()
     assert rel(out[1], ref) < 1e-3
     assert rel(out[1], out[0]) < 1e-5
@@ -91,7 +91,7 @@ def test_fused_bf16_storage_matches_unfused(dg):
     out = {}
     for fused in (1, 0):
         with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, storage=1) as pl:
-            pl.set_tuning(sino_fused=fused)
+            pl.set_tuning(sino_fused=fused, pj_seg=8, bp_mode=1)   # only the sinogram step differs
             out[fused] = pl.solve(y, c["I0"], 5).cpu().numpy()
     # the fused kernel keeps z = H A x in FP32 shared memory; the three-kernel
     # form stores it in BF16, so the two differ by about the BF16 error itself
