@@ -311,7 +311,7 @@ __device__ __forceinline__ void bp_tile_view(const ViewConst& c, const T* __rest
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBtWarps * 32, 4)
+__global__ void __launch_bounds__(kBtWarps * 32, 5)    // 48 registers: 5 blocks per SM, no spills
 k_backproject_tile(const T* __restrict__ sino, int nv, int nd, int n, const ViewConst* __restrict__ vcs,
                    const float* __restrict__ x_in, float* __restrict__ out, int update,
                    DevScalars* __restrict__ S, const double* __restrict__ partial, int nparts, double M) {
