@@ -5,14 +5,18 @@
 //   H s                    the adjoint side, H being symmetric
 // One block takes two views packed as the real and imaginary parts of one
 // complex line (the gain is real and even, so one FFT pair filters both), as
-// the stand-alone filter kernel does.  z stays in shared memory; the
-// twiddle table is staged there once for the four transforms; s is written
-// for the next iteration and, rounded as stored, filtered in place.  tau_s
-// is reduced as in the stand-alone output step (the last block finishes it
-// Each block stores its FP64 partial sum of tau_s_i; the back-projection
-// that follows adds the partials in a fixed order and forms tau_s and tau_r
-// (so no block here waits for the others).  This replaces three launches,
-// two round trips of a sinogram through L2 and a grid-wide reduction tail.
+// the stand-alone filter kernel does.  z stays in shared memory; the twiddle
+// table is staged there once for the four transforms; s is written for the
+// next iteration and, rounded as stored, filtered in place.
+//
+// Reductions.  Each block stores its FP64 partial sum of tau_s_i; the
+// back-projection that follows adds the partials in a fixed order and forms
+// tau_s and tau_r, so no block here waits for the others.  Before the output
+// step the kernel needs tau_x, whose TV divergence (Step 4 of the previous
+// iteration) may still be in partial sums: every block adds those in a fixed
+// order, and block 0 records D', tau_x, the iteration's log and the next t
+// (pending_tau_x).  This replaces three launches, two round trips of a
+// sinogram through L2 and two grid-wide reduction tails.
 #include "fft_device.cuh"
 #include "output_device.cuh"
 
