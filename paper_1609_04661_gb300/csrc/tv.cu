@@ -4,8 +4,9 @@
 // projection (forward differences, Neumann boundary, step 1/8, a fixed
 // number of iterations from a zero dual).  The MC divergence of Eq. MC_SURE
 // with one probe needs D at r and at r + eps b; both images are denoised by
-// the same blocks, and the last launch forms x = D(r), b^T (D(r+eps b) - D(r))
-// in FP64 and -- inside a solve -- tau_x = max(tau_r D', floor tau_r).
+// the same blocks, and the last launch forms x = D(r) and b^T (D(r+eps b) - D(r))
+// in FP64; tau_x = max(tau_r D', floor tau_r) follows from it (inside a solve
+// in the next iteration's output step, see output_device.cuh).
 //
 // Temporal blocking.  One Chambolle step updates p at a pixel from p within
 // one pixel of it:
@@ -253,7 +254,9 @@ __device__ __forceinline__ void tv_divergence_finish(double acc, int nblk, int b
 // and left (div p reads the left and upper neighbours) and KB at the bottom
 // and right; image 0's x (damped in a solve) to x_out and the staged
 // copies; for nimg = 2 the divergence b^T (x_1 - x_0) / (N eps), summed as
-// +b^T x_1 and -b^T x_0 over the blocks of the two images.
+// +b^T x_1 and -b^T x_0 over the blocks of the two images -- inside a solve
+// left as FP64 block partials that the next output step adds (it needs tau_x
+// first), elsewhere finished by the last block.
 template <int WY, int KB, bool FINAL>
 __global__ void __launch_bounds__(32 * WY)
 k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout, int n,
