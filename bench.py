@@ -156,7 +156,34 @@ def _ablation(plan, case, counts, T):
         out[name] = {"psnr_db_final": round(curve[-1], 2), "psnr_db_best": round(curve[best], 2),
                      "best_at_iteration": best + 1, "psnr_db_at_10": round(curve[9], 2) if T >= 10 else None}
     plan.set_options(onsager=1, damp_x=TV["damp_x"], damp_s=TV["damp_s"])
+    # the output step with the exact posterior moments instead of Laplace's
+    # (Appendix A; the paper puts the difference at about 0.1 dB)
+    try:
+        out["exact_moments_damped"] = _exact_moments_curve(plan, case, counts, T, mu)
+    except Exception as e:                      # an ablation entry never takes the bench line down
+        out["exact_moments_damped"] = {"error": f"{type(e).__name__}: {e}"}
+    finally:
+        plan.set_options(output_moments=0)
     return out
+
+
+def _exact_moments_curve(plan, case, counts, T, mu):
+    import torch
+    plan.set_options(output_moments=1)
+    curve = []
+    for t in range(1, T + 1):
+        plan.solve(counts, case["I0"], t, mu_out=mu)
+        curve.append(_psnr(mu.cpu().numpy().astype("float64"), case["mu"]))
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    plan.solve(counts, case["I0"], T, mu_out=mu)
+    e1.record(st)
+    torch.cuda.synchronize()
+    best = max(range(T), key=lambda k: curve[k])
+    return {"psnr_db_final": round(curve[-1], 2), "psnr_db_best": round(curve[best], 2),
+            "best_at_iteration": best + 1, "psnr_db_at_10": round(curve[9], 2) if T >= 10 else None,
+            "iters_per_s": T / (e0.elapsed_time(e1) * 1e-3)}
 
 
 def _batched(dg, rank, world, dist, flush, steps, learned=False):

@@ -96,6 +96,13 @@ typedef struct {
                               and the GAMP scalars in FP64; the counts and the denoiser's
                               images stay FP32.  The single-step entry points always take
                               FP32 buffers. */
+    int32_t  output_moments; /* output step (Algorithm 1, Step 2; Appendix A): 0 (default)
+                              Laplace's approximation (mode and curvature); 1 = the exact
+                              posterior mean and variance of z by quadrature over the
+                              window where the log posterior is within 50 of its maximum
+                              (257-point trapezoid rule).  1 with truncate_z = 1 is
+                              INVALID_ARG.  Inside a solve, 1 runs the three-kernel form of
+                              the sinogram step.  Also used by dgamp_ct_output_step. */
 } dgamp_ct_options;
 
 typedef struct {

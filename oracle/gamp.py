@@ -50,6 +50,7 @@ class Options:
     tau_x_floor: float = 1e-6
     tau_x0: float = 1.0      # initial tau_x (Algorithm 1 uses 1)
     truncate_z: bool = False  # output step on z >= 0 instead of the whole line
+    exact_moments: bool = False  # output step from the exact posterior moments, not Laplace's
 
 
 @dataclasses.dataclass
@@ -143,8 +144,14 @@ def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
     def PhiT(s):
         return _pre.backproject(s.reshape(geom.n_views, geom.n_det), geom)
 
+    if opts.exact_moments and opts.truncate_z:
+        raise ValueError("exact posterior moments are computed on the whole line only")
+
     def gout(p, tau_p):
-        s, tsi, _z0, _v = _out.output_step(p, yv, tau_p, I0, truncate=opts.truncate_z)
+        if opts.exact_moments:
+            s, tsi, _m, _v = _out.output_step_exact(p, yv, tau_p, I0)
+        else:
+            s, tsi, _z0, _v = _out.output_step(p, yv, tau_p, I0, truncate=opts.truncate_z)
         return s, tsi
 
     def denoise_factory(tau_r):

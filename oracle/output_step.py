@@ -116,3 +116,66 @@ def posterior_moments_quadrature(p, y, tau_p, I0, half_width: float = 12.0, n: i
     mean = np.trapezoid(wgt * z, z) / mass
     var = np.trapezoid(wgt * (z - mean) ** 2, z) / mass
     return mean, var
+
+
+# ------------------------------------------------ exact posterior moments ---
+# The output step without Laplace's approximation: s and tau_s_i from the
+# exact posterior mean and variance of z (Appendix A, before its Laplace
+# step; Section 3's s = (E[z] - p)/tau_p, tau_s_i = (1/tau_p)(1 - Var/tau_p)).
+# Relative to the mode z0 = p + delta the log posterior is
+#     l(t) = -t^2 / (2 tau_p) - w0 (e^{-t} - 1 + t),   w0 = I0 e^{-z0},
+# (the mode condition cancels the linear terms): concave, l(0) = 0 and
+# l(t) <= -t^2 / (2 tau_p).  The integrals run over [t_lo, t_hi] where
+# l = -EXACT_LOGCUT on each side (found by bisection inside
+# [0, +-sqrt(2 EXACT_LOGCUT tau_p)]), which holds all but e^-50 of the mass
+# whatever the skew, by the trapezoid rule on a uniform grid.
+EXACT_LOGCUT = 50.0
+
+
+def _exact_l(t, tau_p, lw0):
+    """l(t) with lw0 = log w0.  Near the mode (|t| < 1) w0 (expm1(-t) + t)
+    keeps the t^2/2 behaviour exact; away from it the same term is
+    exp(lw0 - t) + w0 (t - 1), which stays finite where w0 underflows."""
+    with np.errstate(over="ignore", invalid="ignore"):
+        w0 = np.exp(lw0)
+        near = w0 * (np.expm1(-t) + t)
+        far = np.exp(lw0 - t) + w0 * (t - 1.0)
+    return -t * t / (2.0 * tau_p) - np.where(np.abs(t) < 1.0, near, far)
+
+
+def _exact_edge(sign, tau_p, lw0, steps: int = 80):
+    """t on side `sign` (+1 / -1) where l(t) = -EXACT_LOGCUT, by bisection."""
+    lo = np.zeros_like(lw0)
+    hi = sign * np.sqrt(2.0 * EXACT_LOGCUT * tau_p) * np.ones_like(lw0)
+    for _ in range(steps):
+        mid = 0.5 * (lo + hi)
+        above = _exact_l(mid, tau_p, lw0) > -EXACT_LOGCUT
+        lo = np.where(above, mid, lo)
+        hi = np.where(above, hi, mid)
+    return hi
+
+
+def output_step_exact(p, y, tau_p, I0, n: int = 4001):
+    """Algorithm 1, Step 2 with the exact posterior moments.  Returns
+    (s, tau_s_i, mean, var) as fp64 arrays (mean and var of z)."""
+    log_I0 = float(np.log(I0))
+    p = np.asarray(p, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    d = laplace_mode_delta(p, y, tau_p, log_I0)
+    lw0 = log_I0 - (p + d)                   # log of w0 = I0 e^{-z0}
+    t_lo = _exact_edge(-1.0, tau_p, lw0)
+    t_hi = _exact_edge(+1.0, tau_p, lw0)
+    u = np.linspace(0.0, 1.0, n)
+    mean = np.empty_like(p)
+    var = np.empty_like(p)
+    for i0 in range(0, p.size, 256):        # chunks: n grid points per measurement
+        sl = slice(i0, min(p.size, i0 + 256))
+        t = t_lo[sl, None] + (t_hi[sl] - t_lo[sl])[:, None] * u[None, :]
+        wgt = np.exp(_exact_l(t, tau_p, lw0[sl, None]))
+        mass = np.trapezoid(wgt, t, axis=1)
+        m1 = np.trapezoid(wgt * t, t, axis=1) / mass
+        var[sl] = np.trapezoid(wgt * (t - m1[:, None]) ** 2, t, axis=1) / mass
+        mean[sl] = p[sl] + d[sl] + m1
+    s = (mean - p) / tau_p
+    tau_s_i = (1.0 - var / tau_p) / tau_p
+    return s, tau_s_i, mean, var

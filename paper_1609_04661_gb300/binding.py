@@ -58,7 +58,8 @@ class Options(C.Structure):
                 ("eps_rel", C.c_double), ("seed", C.c_uint64), ("slice_id", C.c_int32),
                 ("onsager", C.c_int32), ("damp_x", C.c_double), ("damp_s", C.c_double),
                 ("tau_x_floor", C.c_double), ("use_graph", C.c_int32), ("cnn_scale", C.c_int32),
-                ("tau_x0", C.c_double), ("truncate_z", C.c_int32), ("storage", C.c_int32)]
+                ("tau_x0", C.c_double), ("truncate_z", C.c_int32), ("storage", C.c_int32),
+                ("output_moments", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -242,10 +243,15 @@ class Plan:
         _check(self._lib.dgamp_ct_set_tuning(self._h, C.byref(t)), "set_tuning")
 
     def set_options(self, **options):
-        o = self.options
+        """Change some options; if the library rejects them the plan keeps its
+        previous options (here and in the library)."""
+        o = Options.from_buffer_copy(self.options)
         for k, v in options.items():
+            if k not in dict(Options._fields_):
+                raise TypeError(f"unknown option {k!r}")
             setattr(o, k, v)
         _check(self._lib.dgamp_ct_set_options(self._h, C.byref(o)), "set_options")
+        self.options = o
 
     def _img(self, like=None):
         import torch
@@ -350,7 +356,8 @@ class Plan:
         cnt = C.c_int32()
         _check(self._lib.dgamp_ct_profile_iteration(self._h, int(reps), arr, cap, C.byref(cnt), _stream()),
                "dgamp_ct_profile_iteration")
-        sino = ["sino_step"] if self.tuning()["sino_fused"] else ["filter_z", "output_step", "filter_s"]
+        fused = self.tuning()["sino_fused"] and not self.options.output_moments
+        sino = ["sino_step"] if fused else ["filter_z", "output_step", "filter_s"]
         names = ["project"] + sino + ["backproject_update", "probe_input"]
         if self.options.denoiser == 1:
             names += ["cnn_pair", "denoise_final"]

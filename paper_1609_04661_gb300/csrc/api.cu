@@ -57,6 +57,8 @@ static bool options_ok(const dgamp_ct_options* o) {
     if (o->cnn_scale != 0 && o->cnn_scale != 1) return false;
     if (o->truncate_z != 0 && o->truncate_z != 1) return false;
     if (o->storage != 0 && o->storage != 1) return false;
+    if (o->output_moments != 0 && o->output_moments != 1) return false;
+    if (o->output_moments == 1 && o->truncate_z) return false;
     return true;
 }
 
@@ -218,6 +220,12 @@ int raise_smem_limit(const void* kernel, int bytes) {
 }
 
 // -------------------------------------------------------------- solve ----
+// The solve runs the fused sinogram kernel when the tuning asks for it and the
+// output step is Laplace's (the exact moments take the three-kernel form,
+// whose output-step kernel spreads the heavier per-measurement work over
+// every SM).
+static bool fused_sino_now(const dgamp_ct_plan_s* pl) { return pl->sino_fused && !pl->opt.output_moments; }
+
 // One iteration of Algorithm 1 (Steps 1-4); every scalar it needs lives in
 // DevScalars, so the same launch sequence serves every iteration.
 // With `ev` non-NULL, ev[i] is recorded before kernel i and ev[count] after
@@ -234,7 +242,7 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
     const int bf = pl->opt.storage;                                      // BF16 sinograms / staged image
     DGCT_TRY(launch_project(pl, w.zraw, st, bf));                      // Step 1: A x
     DGCT_TRY(mark());
-    if (pl->sino_fused) {
+    if (fused_sino_now(pl)) {
         DGCT_TRY(launch_sino_step(pl, st, bf));                         // H A x, Step 2, H s
         DGCT_TRY(mark());
     } else {
@@ -246,7 +254,7 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
         DGCT_TRY(mark());
     }
     DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st, bf,          //         r = x + tau_r A^T H s
-                                pl->sino_fused ? sino_step_partials(pl) : 0));
+                                fused_sino_now(pl) ? sino_step_partials(pl) : 0));
     DGCT_TRY(mark());
     // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r
     DGCT_TRY(launch_probe_input(pl, 0, st, pl->opt.denoiser == 1 ? 1 : 0));
@@ -270,7 +278,7 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
 
 // kernels one iteration launches
 static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
-    const int sino = pl->sino_fused ? 1 : 3;        // H A x, output step, H s
+    const int sino = fused_sino_now(pl) ? 1 : 3;    // H A x, output step, H s
     if (pl->opt.denoiser == 1 && pl->cnn) return sino + 3 + cnn_launches_per_pair(pl->cnn) + 1;
     return sino + 3 + tv_num_launches(pl, 1, 0.0);
 }
@@ -278,7 +286,7 @@ static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
 // timed segments of one iteration (dgamp_ct_profile_iteration): every kernel,
 // except that the learned denoiser's launches form one segment
 static int segments_per_iteration(const dgamp_ct_plan_s* pl) {
-    const int sino = pl->sino_fused ? 1 : 3;
+    const int sino = fused_sino_now(pl) ? 1 : 3;
     if (pl->opt.denoiser == 1 && pl->cnn) return sino + 5;
     return sino + 3 + tv_num_launches(pl, 1, 0.0);
 }
@@ -340,6 +348,7 @@ int dgamp_ct_default_options(dgamp_ct_options* o) {
     o->tau_x0 = 1.0;
     o->truncate_z = 0;
     o->storage = 0;
+    o->output_moments = 0;
     return DGAMP_CT_OK;
 }
 

@@ -129,6 +129,64 @@ __device__ __forceinline__ float output_element(float zi, float sp, float yv, fl
     return (clamp || isinf(w)) ? inv_tp : w / fmaf(tau_p, w, 1.f);
 }
 
+// The same measurement with the exact posterior moments of z instead of
+// Laplace's (option output_moments = 1).  Relative to the mode z0 = p + d the
+// log posterior is l(t) = -t^2 / (2 tau_p) - w0 (e^{-t} - 1 + t), w0 =
+// I0 e^{-z0} (the mode condition cancels the linear terms): concave, l(0) =
+// 0, l(t) <= -t^2 / (2 tau_p).  The window [t_lo, t_hi] where l >=
+// -kExactLogCut on each side is found by bisection inside [0, +-sqrt(2 cut
+// tau_p)]; mean and variance of t follow from the trapezoid rule on
+// kExactPts points (the density is smooth, so the rule converges fast, and
+// the window holds all but e^-50 of the mass whatever the skew).  Then
+// s = (d + E[t]) / tau_p and tau_s_i = (1/tau_p)(1 - Var/tau_p).  The
+// Poisson term is w0 (expm1(-t) + t) near the mode (|t| < 1) and
+// exp(log w0 - t) + w0 (t - 1) away from it, which stays finite where w0
+// underflows.
+constexpr float kExactLogCut = 50.f;
+constexpr int kExactPts = 257;
+
+__device__ __forceinline__ float exact_logpost(float t, float inv_tp, float w0, float lw0) {
+    const float poi = fabsf(t) < 1.f ? w0 * (expm1f(-t) + t) : expf(lw0 - t) + w0 * (t - 1.f);
+    return -0.5f * t * t * inv_tp - poi;
+}
+
+__device__ __forceinline__ float exact_edge(float sign, float tau_p, float inv_tp, float w0, float lw0) {
+    float lo = 0.f, hi = sign * sqrtf(2.f * kExactLogCut * tau_p);
+    for (int k = 0; k < 40; ++k) {
+        const float mid = 0.5f * (lo + hi);
+        if (exact_logpost(mid, inv_tp, w0, lw0) > -kExactLogCut)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return hi;
+}
+
+__device__ __forceinline__ float output_element_exact(float zi, float sp, float yv, float tau_p, float inv_tp,
+                                                      float logI0, int onsager, float damp_s, unsigned& capped,
+                                                      float& sv) {
+    const float p = onsager ? fmaf(-tau_p, sp, zi) : zi;
+    const float d = mode_delta(p, yv, tau_p, inv_tp, logI0, capped);
+    const float lw0 = logI0 - p - d;                 // log of w0 = I0 e^{-z0}
+    const float w0 = expf(lw0);
+    const float t_lo = exact_edge(-1.f, tau_p, inv_tp, w0, lw0), t_hi = exact_edge(1.f, tau_p, inv_tp, w0, lw0);
+    const float h = (t_hi - t_lo) / (float)(kExactPts - 1);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int k = 0; k < kExactPts; ++k) {
+        const float t = fmaf((float)k, h, t_lo);
+        float w = expf(exact_logpost(t, inv_tp, w0, lw0));
+        if (k == 0 || k == kExactPts - 1) w *= 0.5f;
+        s0 += w;
+        s1 = fmaf(w, t, s1);
+        s2 = fmaf(w * t, t, s2);
+    }
+    const float m1 = s1 / s0;
+    const float var = fmaxf(s2 / s0 - m1 * m1, 0.f);
+    sv = (d + m1) * inv_tp;
+    if (damp_s != 1.f) sv = damp_s * sv + (1.f - damp_s) * sp;
+    return inv_tp * (1.f - var * inv_tp);
+}
+
 // End of a grid that summed tau_s_i: each block stores its FP64 partial, the
 // last block to arrive adds the partials in a fixed order, forms
 // tau_s = sum / M and (inside a solve) tau_p, tau_s and tau_r = N /

@@ -10,7 +10,7 @@ __global__ void __launch_bounds__(256)
 k_output_step(const T* z, const float* y, T* s, long long M, int use_prev,
               int from_scalars, double tau_p_arg, double logI0_arg, int onsager, float damp_s,
               int truncate, double N, DevScalars* S, double* partial, double* tau_s_out,
-              const double* partial_div, double floor_rel, IterLog* log) {
+              const double* partial_div, double floor_rel, IterLog* log, int exact) {
     __shared__ double sm[32];
     __shared__ float s_tp, s_inv, s_logI0;
     if (threadIdx.x < 32) {
@@ -30,8 +30,10 @@ k_output_step(const T* z, const float* y, T* s, long long M, int use_prev,
          i += (long long)gridDim.x * blockDim.x) {
         const float sp = use_prev ? ldf(s + i) : 0.f;
         float sv;
-        acc += (double)output_element(ldf(z + i), sp, y[i], tau_p, inv_tp, logI0, onsager, damp_s, truncate,
-                                      capped, sv);
+        acc += exact ? (double)output_element_exact(ldf(z + i), sp, y[i], tau_p, inv_tp, logI0, onsager, damp_s,
+                                                    capped, sv)
+                     : (double)output_element(ldf(z + i), sp, y[i], tau_p, inv_tp, logI0, onsager, damp_s, truncate,
+                                              capped, sv);
         stf(s + i, sv);
     }
     finish_tau_s(acc, capped, M, N, from_scalars, S, partial, tau_s_out, sm);
@@ -49,12 +51,13 @@ int launch_output_step(const dgamp_ct_plan_s* pl, const float* z, const float* y
         k_output_step<bf16s><<<blocks, 128, 0, st>>>((const bf16s*)z, y, (bf16s*)s, M, use_prev, from_scalars,
                                                      tau_p_arg, logI0_arg, onsager, damp_s, pl->opt.truncate_z,
                                                      (double)pl->N, pl->ws.S, pl->ws.partial, tau_s_out,
-                                                     pl->ws.partial_div, pl->opt.tau_x_floor, pl->ws.log);
+                                                     pl->ws.partial_div, pl->opt.tau_x_floor, pl->ws.log,
+                                                     pl->opt.output_moments);
     else
         k_output_step<float><<<blocks, 128, 0, st>>>(z, y, s, M, use_prev, from_scalars, tau_p_arg, logI0_arg,
                                                      onsager, damp_s, pl->opt.truncate_z, (double)pl->N, pl->ws.S,
                                                      pl->ws.partial, tau_s_out, pl->ws.partial_div,
-                                                     pl->opt.tau_x_floor, pl->ws.log);
+                                                     pl->opt.tau_x_floor, pl->ws.log, pl->opt.output_moments);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
@@ -69,7 +72,7 @@ int launch_output_step_scratch(const float* z, const float* y, float* s, long lo
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
     k_output_step<float><<<(int)blocks, 256, 0, st>>>(z, y, s, M, use_prev, 0, tau_p, logI0, 1, 1.f, 0, 0.0, S,
-                                                      partial, tau_s_out, nullptr, 0.0, nullptr);
+                                                      partial, tau_s_out, nullptr, 0.0, nullptr, 0);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
