@@ -14,7 +14,7 @@ Modules, each citing the passage it follows:
 * :mod:`oracle.joseph`       -- system matrix A and its transpose (Eq. linCT)
 * :mod:`oracle.precond`      -- Radon preconditioner V (Eqs. PPFT/Aprecon)
 * :mod:`oracle.output_step`  -- Poisson output step, Laplace mode (Sec. 4.2, App. A)
-* :mod:`oracle.tv`           -- proximal TV denoiser (Section 6.3)
+* :mod:`oracle.tv`           -- proximal TV denoiser, l2 and (V^T V)^{-1} norms (Section 6.3)
 * :mod:`oracle.philox`       -- counter-based probe generator for Eq. MC_SURE
 * :mod:`oracle.gamp`         -- the D-GAMP-CT loop (Algorithm 1) and the
                                  i.i.d.-Gaussian GAMP used for state evolution

@@ -51,6 +51,7 @@ class Options:
     tau_x0: float = 1.0      # initial tau_x (Algorithm 1 uses 1)
     truncate_z: bool = False  # output step on z >= 0 instead of the whole line
     exact_moments: bool = False  # output step from the exact posterior moments, not Laplace's
+    tv_metric: bool = False   # prox-TV in the (V^T V)^{-1} norm (Section 6.3) instead of l2
 
 
 @dataclasses.dataclass
@@ -160,6 +161,10 @@ def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
             sigma = float(np.sqrt(tau_r)) if scaled else 1.0
             return _cnn.Denoiser(sigma, ws, bs, bf16=True)
         lam = opts.c_tv * np.sqrt(tau_r)
+        if opts.tv_metric:
+            q_max = _pre.vtv_inverse_norm_bound(geom)
+            return lambda r: _tv.tv_prox_metric(r, lam, opts.k_tv,
+                                                lambda u: _pre.vtv_inverse(u, geom), q_max)
         return lambda r: _tv.tv_prox(r, lam, opts.k_tv)
 
     def probe(t, n):

@@ -123,3 +123,37 @@ def v_inverse(x: np.ndarray, geom: Geometry) -> np.ndarray:
 def v_forward(mu: np.ndarray, geom: Geometry) -> np.ndarray:
     """x = V mu (Eq. precondAMP): radial gain 1/sqrt(max(rho, f0))."""
     return _image_filter(np.asarray(mu, dtype=np.float64), geom, inverse=True)
+
+
+# -------------------------------------------------- (V^T V)^{-1} ----
+# The covariance that the preconditioner gives white noise seen through V^-1
+# (Eq. r_input: r = x + tau_r V^-1 Phi^T s).  On the paper's Fourier grid
+# V = F^-1 C^{1/2} F, so (V^T V)^{-1} = F^-1 C^-1 F, the radial gain |rho|.
+# It is realised like V^-1: the gain max(rho, f0) (the square of V^-1's) on
+# the same m x m zero-padded grid, cropped back to n x n.  The result Q is
+# symmetric and positive definite (a principal block of a positive definite
+# circulant), and ||Q|| <= the largest gain on the grid.
+
+def _vtv_gain(m: int, P: int) -> np.ndarray:
+    fy = np.fft.fftfreq(m)[:, None]
+    fx = np.fft.fftfreq(m)[None, :]
+    return np.maximum(np.sqrt(fx * fx + fy * fy), 1.0 / (2 * P))
+
+
+def image_pad(geom: Geometry) -> int:
+    """m, the side of the zero-padded grid of the image-domain filters."""
+    return 1 << (2 * geom.n - 1).bit_length()
+
+
+def vtv_inverse(u: np.ndarray, geom: Geometry) -> np.ndarray:
+    """Q u with Q = (V^T V)^{-1}: zero-pad to m x m, FFT, times max(rho, f0),
+    IFFT, crop."""
+    n, m = geom.n, image_pad(geom)
+    pad = np.zeros((m, m))
+    pad[:n, :n] = np.asarray(u, dtype=np.float64)
+    return np.fft.ifft2(np.fft.fft2(pad) * _vtv_gain(m, geom.P)).real[:n, :n]
+
+
+def vtv_inverse_norm_bound(geom: Geometry) -> float:
+    """The largest gain of Q on its grid, a bound on ||Q||."""
+    return float(_vtv_gain(image_pad(geom), geom.P).max())
