@@ -103,6 +103,15 @@ typedef struct {
                               (257-point trapezoid rule).  1 with truncate_z = 1 is
                               INVALID_ARG.  Inside a solve, 1 runs the three-kernel form of
                               the sinogram step.  Also used by dgamp_ct_output_step. */
+    int32_t  tv_metric;    /* prox-TV norm (Section 6.3), for denoiser 0 and the TV entry
+                              points: 0 (default) l2; 1 = the Mahalanobis norm of the
+                              covariance Q = (V^T V)^{-1}: x = argmin 1/2 (x-r)^T Q^-1 (x-r)
+                              + lambda TV(x), Q the radial gain max(|rho|, 1/(2P)) on the
+                              m x m zero-padded grid of dgamp_ct_precond_image, cropped.
+                              Solved by k_tv projected-gradient steps on the dual
+                              (x(p) = r + lambda Q div p, p <- Proj_{|p|<=1}(p + grad x(p)
+                              / (8 q_max lambda)), q_max = the largest gain, from p = 0),
+                              returning x(p_k_tv). */
 } dgamp_ct_options;
 
 typedef struct {
@@ -200,7 +209,9 @@ int dgamp_ct_output_step(dgamp_ct_plan_t plan, const float* d_z, const float* d_
                          float* d_s, double* d_tau_s, void* stream);
 
 /* Proximal TV denoiser (Section 6.3): d_x = argmin 1/2||x - r||^2 + lambda TV(x)
-   by k_tv Chambolle iterations from a zero dual (tau = 1/8).  [n][n]. */
+   by k_tv Chambolle iterations from a zero dual (tau = 1/8); with the plan's
+   option tv_metric = 1 the same prox in the (V^T V)^{-1} norm (see the
+   option).  [n][n]. */
 int dgamp_ct_denoise_tv(dgamp_ct_plan_t plan, const float* d_r, double lambda,
                         float* d_x, void* stream);
 

@@ -59,7 +59,7 @@ class Options(C.Structure):
                 ("onsager", C.c_int32), ("damp_x", C.c_double), ("damp_s", C.c_double),
                 ("tau_x_floor", C.c_double), ("use_graph", C.c_int32), ("cnn_scale", C.c_int32),
                 ("tau_x0", C.c_double), ("truncate_z", C.c_int32), ("storage", C.c_int32),
-                ("output_moments", C.c_int32)]
+                ("output_moments", C.c_int32), ("tv_metric", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -351,7 +351,9 @@ class Plan:
 
     def profile_iteration(self, reps: int = 5):
         """Mean per-kernel durations (ms) of one iteration, in launch order."""
-        cap = 8 + max(int(self.options.k_tv), 0)
+        k_tv = max(int(self.options.k_tv), 0)
+        metric = bool(self.options.tv_metric) and k_tv > 0 and self.options.c_tv > 0
+        cap = 8 + (4 * k_tv + 1 if metric else k_tv)
         arr = (C.c_double * cap)()
         cnt = C.c_int32()
         _check(self._lib.dgamp_ct_profile_iteration(self._h, int(reps), arr, cap, C.byref(cnt), _stream()),
@@ -361,6 +363,13 @@ class Plan:
         names = ["project"] + sino + ["backproject_update", "probe_input"]
         if self.options.denoiser == 1:
             names += ["cnn_pair", "denoise_final"]
+        elif metric:
+            # prox-TV in the (V^T V)^{-1} norm: a dual step from p = 0, then per
+            # step x(p) in three FFT passes and a dual step, the last one final
+            names += ["tvm_dual0"]
+            for s in range(1, k_tv + 1):
+                names += [f"tvm_rows_fwd{s}", f"tvm_cols{s}", f"tvm_rows_inv{s}"]
+                names += [f"tvm_dual{s}"] if s < k_tv else ["tv_final"]
         else:
             k = cnt.value - len(names) - 1
             names += [f"tv_block{i}" for i in range(k)] + ["tv_block_final"]

@@ -59,6 +59,7 @@ static bool options_ok(const dgamp_ct_options* o) {
     if (o->storage != 0 && o->storage != 1) return false;
     if (o->output_moments != 0 && o->output_moments != 1) return false;
     if (o->output_moments == 1 && o->truncate_z) return false;
+    if (o->tv_metric != 0 && o->tv_metric != 1) return false;
     return true;
 }
 
@@ -200,6 +201,7 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     }
     const int smem_need = 2 * fft_buf_len(P > pl->m2 ? P : pl->m2) * (int)sizeof(float2);
     DGCT_TRY(fft_set_smem_limits(smem_need > 48 * 1024 ? smem_need : 48 * 1024));
+    DGCT_TRY(tvm_set_smem_limits(smem_need > 48 * 1024 ? smem_need : 48 * 1024));
     DGCT_TRY(toeplitz_set_smem_limit(pl->nd));
     DGCT_TRY(sino_step_set_smem_limit(pl));
     DGCT_TRY(filter_autotune(pl));
@@ -349,6 +351,7 @@ int dgamp_ct_default_options(dgamp_ct_options* o) {
     o->truncate_z = 0;
     o->storage = 0;
     o->output_moments = 0;
+    o->tv_metric = 0;
     return DGAMP_CT_OK;
 }
 

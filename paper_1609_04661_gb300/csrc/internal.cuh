@@ -53,6 +53,12 @@ struct DevScalars {
     unsigned int div_pending;   // TV divergence partial sums left for the next output step (0: none)
 };
 
+// The TV weight: lambda = c_tv sqrt(tau_r) inside a solve, the caller's lambda otherwise.
+__device__ __forceinline__ float solve_lambda(const DevScalars* S, float c_tv, int from_scalars,
+                                              float lambda_arg) {
+    return from_scalars ? c_tv * sqrtf((float)S->tau_r) : lambda_arg;
+}
+
 // Per-iteration log record (what dgamp_ct_stats exposes).
 struct IterLog { double tau_x, tau_p, tau_s, tau_r, div, eps; };
 
@@ -256,6 +262,15 @@ int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lamb
               int solve_mode, int t_arg, double* div_out, cudaStream_t st);
 int launch_probe(const dgamp_ct_plan_s* pl, unsigned t, int64_t n, float* b, uint32_t* words,
                  cudaStream_t st);
+// the TV final step on images the caller has already formed (xbase, nimg of them, [n][n]
+// each): x of image 0 (damped in a solve) to x_out, staged copies, divergence, tau_x
+int launch_tv_final_x(const dgamp_ct_plan_s* pl, int nimg, const float* xbase, float* x_out, int solve_mode,
+                      int t_arg, double* div_out, cudaStream_t st);
+// tv_metric.cu: prox-TV in the (V^T V)^{-1} norm (option tv_metric)
+int tvm_num_launches(const dgamp_ct_plan_s* pl);
+int launch_tvm_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
+                     float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st);
+int tvm_set_smem_limits(int bytes);
 // x, staging, divergence and tau_x from D(r) and J_D(r) b (learned denoiser)
 int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_out, int solve_mode, int t_arg,
                          double* div_out, cudaStream_t st);

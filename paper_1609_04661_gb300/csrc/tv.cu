@@ -31,11 +31,6 @@ constexpr int TB = 32;             // pixel tile edge of the final step
 constexpr int kTvMaxKb = 10;       // most Chambolle steps one launch may run
 constexpr float kTau = 0.125f;
 
-__device__ __forceinline__ float solve_lambda(const DevScalars* S, float c_tv, int from_scalars,
-                                              float lambda_arg) {
-    return from_scalars ? c_tv * sqrtf((float)S->tau_r) : lambda_arg;
-}
-
 // --------------------------------------------------------- probe input ----
 // r2 = r + eps b, eps = eps_rel max(max|r|, 1e-6), or r2 = b itself
 // (write_b = 1: the direction of a forward-mode divergence); b itself also
@@ -434,8 +429,10 @@ static int tv_step_launches(const dgamp_ct_plan_s* pl, int from_scalars, double 
 }
 
 // the step launches, the last of them forming x (or one final launch when
-// the denoiser is the identity: no steps or lambda = 0)
+// the denoiser is the identity: no steps or lambda = 0); the metric form
+// (option tv_metric) has its own sequence, see tv_metric.cu
 int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg) {
+    if (pl->opt.tv_metric && tv_active(pl, from_scalars, lambda_arg)) return tvm_num_launches(pl);
     const int ns = tv_step_launches(pl, from_scalars, lambda_arg);
     return ns > 0 ? ns : 1;
 }
@@ -481,15 +478,8 @@ static int launch_steps(int rows, int steps, const TvLaunch& L, cudaStream_t st,
     return launch_steps_wy<16, FIN>(steps, L, st, F);
 }
 
-// Launch i (0-based) of the denoiser on nimg images of ws.r.
-int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
-                    float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st) {
-    const int n = pl->n;
-    const size_t N = (size_t)pl->N;
-    const int KB = pl->tv_kb;
-    const int ns = tv_step_launches(pl, from_scalars, lambda_arg);
-    float2* buf[2] = {pl->ws.p, pl->ws.p + 2 * N};
-    const float c_tv = (float)pl->opt.c_tv, lam = (float)lambda_arg;
+static TvFinal make_tv_final(const dgamp_ct_plan_s* pl, float* x_out, int solve_mode, int t_arg,
+                             double* div_out) {
     TvFinal F;
     F.x_out = x_out;
     F.XR = solve_mode ? pl->ws.XR : nullptr;
@@ -507,17 +497,37 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     F.div_out = div_out;
     F.solve_mode = solve_mode;
     F.jvp = 0;
-    if (ns == 0) {   // identity denoiser: x = r
-        dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
-        if (nimg == 2)
-            k_tv_final<2><<<grd, 1024, 0, st>>>(pl->ws.r, nullptr, pl->ws.b, n, c_tv, from_scalars, lam, pl->ws.S,
-                                                F);
-        else
-            k_tv_final<1><<<grd, 1024, 0, st>>>(pl->ws.r, nullptr, pl->ws.b, n, c_tv, from_scalars, lam, pl->ws.S,
-                                                F);
-        DGCT_LAUNCH_CHECK();
-        return DGAMP_CT_OK;
-    }
+    return F;
+}
+
+int launch_tv_final_x(const dgamp_ct_plan_s* pl, int nimg, const float* xbase, float* x_out, int solve_mode,
+                      int t_arg, double* div_out, cudaStream_t st) {
+    const int n = pl->n;
+    const TvFinal F = make_tv_final(pl, x_out, solve_mode, t_arg, div_out);
+    dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
+    // no duals: the final step takes xbase as the denoised images
+    if (nimg == 2)
+        k_tv_final<2><<<grd, 1024, 0, st>>>(xbase, nullptr, pl->ws.b, n, 0.f, 0, 0.f, pl->ws.S, F);
+    else
+        k_tv_final<1><<<grd, 1024, 0, st>>>(xbase, nullptr, pl->ws.b, n, 0.f, 0, 0.f, pl->ws.S, F);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// Launch i (0-based) of the denoiser on nimg images of ws.r.
+int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
+                    float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st) {
+    if (pl->opt.tv_metric && tv_active(pl, from_scalars, lambda_arg))
+        return launch_tvm_chunk(pl, nimg, from_scalars, lambda_arg, i, x_out, solve_mode, t_arg, div_out, st);
+    const int n = pl->n;
+    const size_t N = (size_t)pl->N;
+    const int KB = pl->tv_kb;
+    const int ns = tv_step_launches(pl, from_scalars, lambda_arg);
+    float2* buf[2] = {pl->ws.p, pl->ws.p + 2 * N};
+    const float c_tv = (float)pl->opt.c_tv, lam = (float)lambda_arg;
+    if (ns == 0)   // identity denoiser: x = r
+        return launch_tv_final_x(pl, nimg, pl->ws.r, x_out, solve_mode, t_arg, div_out, st);
+    const TvFinal F = make_tv_final(pl, x_out, solve_mode, t_arg, div_out);
     const int steps = (i + 1) * KB <= pl->opt.k_tv ? KB : pl->opt.k_tv - i * KB;
     TvLaunch L{n, nimg, i == 0, pl->ws.r, buf[(i + 1) & 1], buf[i & 1], c_tv, lam, from_scalars, pl->ws.S,
                pl->ws.b};
