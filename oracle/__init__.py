@@ -13,6 +13,7 @@ Modules, each citing the passage it follows:
 * :mod:`oracle.geometry`     -- discretisation conventions (Section 2.1)
 * :mod:`oracle.joseph`       -- system matrix A and its transpose (Eq. linCT)
 * :mod:`oracle.precond`      -- Radon preconditioner V (Eqs. PPFT/Aprecon)
+* :mod:`oracle.fanbeam`      -- flat-detector fan-beam A and Phi~ = A V^-1 (Section 6)
 * :mod:`oracle.output_step`  -- Poisson output step, Laplace mode (Sec. 4.2, App. A)
 * :mod:`oracle.tv`           -- proximal TV denoiser, l2 and (V^T V)^{-1} norms (Section 6.3)
 * :mod:`oracle.philox`       -- counter-based probe generator for Eq. MC_SURE

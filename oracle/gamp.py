@@ -35,6 +35,7 @@ from . import philox as _philox
 from . import precond as _pre
 from . import tv as _tv
 from . import cnn as _cnn
+from . import fanbeam as _fan
 
 
 @dataclasses.dataclass
@@ -136,14 +137,17 @@ def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
     """
     opts = opts or Options()
     yv = np.asarray(y, dtype=np.float64).reshape(-1)
+    # parallel beam (Geometry) or flat-detector fan beam (FanGeometry): the
+    # preconditioned operator Phi~ = A V^-1 of Eq. precondAMP_op either way
+    ops = _fan if isinstance(geom, _fan.FanGeometry) else _pre
     if frob2 is None:
-        frob2 = _pre.frobenius_sq(geom)
+        frob2 = ops.frobenius_sq(geom)
 
     def Phi(x):
-        return _pre.project(x, geom)
+        return ops.project(x, geom)
 
     def PhiT(s):
-        return _pre.backproject(s.reshape(geom.n_views, geom.n_det), geom)
+        return ops.backproject(s.reshape(geom.n_views, geom.n_det), geom)
 
     if opts.exact_moments and opts.truncate_z:
         raise ValueError("exact posterior moments are computed on the whole line only")

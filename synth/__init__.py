@@ -29,7 +29,7 @@ import numpy as np
 __all__ = [
     "Ellipse", "Rect", "Phantom", "random_phantom", "rasterise",
     "analytic_sinogram", "poisson_counts", "view_angles", "make_case",
-    "CASES",
+    "CASES", "FAN_CASES", "fan_lines", "analytic_fan_sinogram", "fan_view_angles",
 ]
 
 
@@ -193,8 +193,13 @@ def analytic_sinogram(ph: Phantom, angles: np.ndarray, n_det: int) -> np.ndarray
     """Exact line integrals ``z[view, bin]`` of the phantom (fp64)."""
     u = np.arange(n_det, dtype=np.float64) - (n_det - 1) / 2.0
     th = np.asarray(angles, dtype=np.float64)[:, None]
-    uu = u[None, :]
-    z = np.zeros((th.shape[0], n_det))
+    return _line_integrals(ph, th, u[None, :])
+
+
+def _line_integrals(ph: Phantom, th, uu) -> np.ndarray:
+    """Line integrals along the lines (th, uu) (broadcast together)."""
+    th, uu = np.broadcast_arrays(np.asarray(th, dtype=np.float64), np.asarray(uu, dtype=np.float64))
+    z = np.zeros(th.shape)
     if ph.rect is not None:
         r1, r2 = _rect_interval(ph.rect, th, uu)
     for e in ph.ellipses:
@@ -207,6 +212,38 @@ def analytic_sinogram(ph: Phantom, angles: np.ndarray, n_det: int) -> np.ndarray
     if ph.rect is not None:
         z += ph.rect.rho * np.maximum(r2 - r1, 0.0)
     return z
+
+
+def fan_lines(angles: np.ndarray, n_det: int, src_dist: float, det_dist: float,
+              det_spacing: float):
+    """Each fan-beam ray as a line (theta', u') of the parallel convention.
+
+    Flat-detector fan beam: at view angle theta the source sits at
+    src_dist (sin theta, -cos theta), the detector centre at
+    det_dist (-sin theta, cos theta), and bin d at the detector centre plus
+    u_d (cos theta, sin theta), u_d = (d - (n_det-1)/2) det_spacing.  The
+    central ray therefore runs along (-sin theta, cos theta), the direction of
+    the parallel-beam ray (theta, 0).  Returns theta', u' of shape
+    [n_views][n_det] with X cos theta' + Y sin theta' = u' the ray's line."""
+    th = np.asarray(angles, dtype=np.float64)[:, None]
+    u = (np.arange(n_det, dtype=np.float64) - (n_det - 1) / 2.0)[None, :] * det_spacing
+    sx, sy = src_dist * np.sin(th), -src_dist * np.cos(th)
+    tx = -det_dist * np.sin(th) + u * np.cos(th)
+    ty = det_dist * np.cos(th) + u * np.sin(th)
+    dx, dy = tx - sx, ty - sy
+    nrm = np.hypot(dx, dy)
+    dx, dy = dx / nrm, dy / nrm
+    # direction (-sin theta', cos theta') = (dx, dy)
+    thp = np.arctan2(-dx, dy)
+    up = sx * np.cos(thp) + sy * np.sin(thp)
+    return thp, up
+
+
+def analytic_fan_sinogram(ph: Phantom, angles: np.ndarray, n_det: int, src_dist: float,
+                          det_dist: float, det_spacing: float) -> np.ndarray:
+    """Exact line integrals of the phantom along the fan-beam rays (fp64)."""
+    thp, up = fan_lines(angles, n_det, src_dist, det_dist, det_spacing)
+    return _line_integrals(ph, thp, up)
 
 
 def poisson_counts(z: np.ndarray, I0: float, seed: int) -> np.ndarray:
@@ -226,13 +263,42 @@ CASES = {
 }
 
 
+#: fan-beam workloads (flat detector, views evenly over 360 degrees, see
+#: fan_lines): name -> (n, n_views, n_det, n_ellipses, rho_max, with_rect,
+#: I0, iters, src_dist, det_dist, det_spacing), distances in pixels
+FAN_CASES = {
+    # 64x64, 5 ellipses, 30 views, 96 bins of 1.95 px, source 112 px and
+    # detector 92 px from the centre (field of view radius 46 px)
+    "fan64_v30": (64, 30, 96, 5, 0.02, False, 1e4, 20, 112.0, 92.0, 1.95),
+    # 512x512, 10 ellipses + rectangle, 102 views (a tenth of 1024), 736 bins
+    # of 1.95 px, source 900 px and detector 740 px from the centre: the
+    # proportions of a clinical fan-beam scanner at 0.66 mm pixels
+    "fan512_v102": (512, 102, 736, 10, 0.02, True, 1e5, 30, 900.0, 740.0, 1.95),
+}
+
+
+def fan_view_angles(n_views: int) -> np.ndarray:
+    """theta_k = 2 pi k / n_views (a full rotation)."""
+    return np.arange(n_views, dtype=np.float64) * (2.0 * math.pi / n_views)
+
+
 def make_case(name: str, seed: int = 1000):
     """Phantom, counts and geometry for one named workload.
 
     Returns a dict with ``mu`` (rasterised phantom, fp64 [n][n]), ``z``
     (analytic sinogram, fp64 [n_views][n_det]), ``y`` (float32 counts),
-    ``I0``, ``n``, ``n_views``, ``n_det``, ``iters``.
+    ``I0``, ``n``, ``n_views``, ``n_det``, ``iters``; a fan-beam workload
+    also has ``angles`` and ``fan`` (src_dist, det_dist, det_spacing).
     """
+    if name in FAN_CASES:
+        n, nv, nd, ne, rmax, rect, I0, iters, sd, dd, ds = FAN_CASES[name]
+        ph = random_phantom(n, ne, seed, rho_max=rmax, with_rect=rect)
+        ang = fan_view_angles(nv)
+        z = analytic_fan_sinogram(ph, ang, nd, sd, dd, ds)
+        y = poisson_counts(z, I0, seed + 7)
+        return dict(name=name, phantom=ph, mu=rasterise(ph, n), z=z, y=y, I0=I0, n=n, n_views=nv,
+                    n_det=nd, iters=iters, seed=seed, angles=ang,
+                    fan=dict(src_dist=sd, det_dist=dd, det_spacing=ds))
     n, nv, nd, ne, rmax, rect, I0, iters = CASES[name]
     ph = random_phantom(n, ne, seed, rho_max=rmax, with_rect=rect)
     ang = view_angles(nv)
