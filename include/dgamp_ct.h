@@ -128,6 +128,20 @@ typedef struct {
     int32_t tau_x_floored; /* iterations whose tau_x took the floor             */
 } dgamp_ct_stats;
 
+/* Flat-detector fan beam (Section 6), in pixel units with the pixel centres
+   of dgamp_ct_geometry: at view angle theta the source sits at
+   src_dist (sin theta, -cos theta), the detector centre at
+   det_dist (-sin theta, cos theta), and bin d at the detector centre plus
+   u_d (cos theta, sin theta), u_d = (d - (n_det-1)/2) det_spacing.  The
+   central ray thus runs along the parallel-beam ray (theta, 0).  base.angles
+   NULL = theta_k = 2 pi k / n_views (a full rotation). */
+typedef struct {
+    dgamp_ct_geometry base;
+    double src_dist;       /* > n / sqrt(2) + 2 and <= 1e8                       */
+    double det_dist;       /* > n / sqrt(2) + 2 and <= 1e8                       */
+    double det_spacing;    /* bin pitch at the detector, > 0 and <= 1e4          */
+} dgamp_ct_fan_geometry;
+
 typedef struct dgamp_ct_plan_s* dgamp_ct_plan_t;
 typedef struct dgamp_ct_cnn_s* dgamp_ct_cnn_t;     /* learned denoiser, see dgamp_ct_cnn_create */
 
@@ -143,6 +157,22 @@ int dgamp_ct_default_options(dgamp_ct_options* opt);
    OOM, CUDA. */
 int dgamp_ct_plan(const dgamp_ct_geometry* g, const dgamp_ct_options* opt,
                   dgamp_ct_plan_t* out);
+
+/* Build a fan-beam plan.  A is Joseph's method along each ray's own
+   direction (by columns when |v_x| >= |v_y|, else by rows; 32.32 fixed-point
+   positions from FP64, so A^T applies exactly A's taps).  Phi~ = A V^-1 with
+   the image-domain cone filter of dgamp_ct_precond_image (Eq. precondAMP_op;
+   the detector-axis H is the parallel-beam form and does not apply), and
+   dgamp_ct_plan_info reports ||Phi~||_F^2 = sum over rays of ||V^-1 a_i||^2
+   (FP64, one ray at a time: plan time grows with n_views n_det).
+   dgamp_ct_project / dgamp_ct_backproject apply A, A^T (precond = 0) or
+   Phi~, Phi~^T (precond = 1); the output step, denoisers, probe and image
+   filter work as for any plan.  dgamp_ct_filter and the solve entry points
+   (solve, solve_host, solve_trace, solve_batched, profile_iteration) return
+   UNSUPPORTED_GEOMETRY for a fan-beam plan.  Synchronous.
+   Errors: INVALID_ARG (as dgamp_ct_plan, and the distance limits), OOM, CUDA. */
+int dgamp_ct_plan_fan(const dgamp_ct_fan_geometry* g, const dgamp_ct_options* opt,
+                      dgamp_ct_plan_t* out);
 
 /* Release the plan and its workspace (synchronises the device first).
    NULL is ignored. */

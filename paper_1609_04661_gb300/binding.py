@@ -30,6 +30,7 @@ EXPORTS = (
     "dgamp_ct_cnn_create", "dgamp_ct_cnn_destroy", "dgamp_ct_cnn_num_params", "dgamp_ct_cnn_set_params",
     "dgamp_ct_cnn_get_params", "dgamp_ct_cnn_denoise", "dgamp_ct_cnn_denoise_jvp", "dgamp_ct_cnn_gradients", "dgamp_ct_cnn_train_step",
     "dgamp_ct_plan_set_cnn", "dgamp_ct_solve_trace", "dgamp_ct_solve_batched", "dgamp_ct_schedule_lpt",
+    "dgamp_ct_plan_fan",
 )
 
 
@@ -45,6 +46,12 @@ class DgampError(RuntimeError):
 class Geometry(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_views", C.c_int32), ("n_det", C.c_int32),
                 ("angles", C.POINTER(C.c_double))]
+
+
+class FanGeometry(C.Structure):
+    """dgamp_ct_fan_geometry (flat-detector fan beam)."""
+    _fields_ = [("base", Geometry), ("src_dist", C.c_double), ("det_dist", C.c_double),
+                ("det_spacing", C.c_double)]
 
 
 class Tuning(C.Structure):
@@ -86,6 +93,7 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_default_options": (C.c_int, [C.POINTER(Options)]),
         "dgamp_ct_plan": (C.c_int, [C.POINTER(Geometry), C.POINTER(Options), C.POINTER(vp)]),
         "dgamp_ct_plan_destroy": (None, [vp]),
+        "dgamp_ct_plan_fan": (C.c_int, [C.POINTER(FanGeometry), C.POINTER(Options), C.POINTER(vp)]),
         "dgamp_ct_set_options": (C.c_int, [vp, C.POINTER(Options)]),
         "dgamp_ct_plan_info": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i32)]),
         "dgamp_ct_project": (C.c_int, [vp, vp, vp, C.c_int, vp]),
@@ -180,7 +188,9 @@ def output_step_noalloc(z, y, s_prev, I0: float, tau_p: float, s_out, tau_s_out)
 class Plan:
     """One geometry's plan (dgamp_ct_plan).  Tensors are float32 CUDA tensors."""
 
-    def __init__(self, n: int, n_views: int, n_det: int, angles=None, **options):
+    def __init__(self, n: int, n_views: int, n_det: int, angles=None, fan=None, **options):
+        """fan: None (parallel beam) or dict(src_dist=, det_dist=, det_spacing=)
+        for the flat-detector fan beam of dgamp_ct_plan_fan."""
         self._lib = load()
         self.n, self.n_views, self.n_det = int(n), int(n_views), int(n_det)
         g = Geometry(self.n, self.n_views, self.n_det, None)
@@ -190,7 +200,12 @@ class Plan:
             g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
         self.options = default_options(**options)
         h = C.c_void_p()
-        _check(self._lib.dgamp_ct_plan(C.byref(g), C.byref(self.options), C.byref(h)), "dgamp_ct_plan")
+        if fan is None:
+            _check(self._lib.dgamp_ct_plan(C.byref(g), C.byref(self.options), C.byref(h)), "dgamp_ct_plan")
+        else:
+            fg = FanGeometry(g, float(fan["src_dist"]), float(fan["det_dist"]), float(fan.get("det_spacing", 1.0)))
+            _check(self._lib.dgamp_ct_plan_fan(C.byref(fg), C.byref(self.options), C.byref(h)),
+                   "dgamp_ct_plan_fan")
         self._h = h
         fr = C.c_double()
         P = C.c_int32()

@@ -22,7 +22,8 @@ int cuda_fail(cudaError_t e) {
 
 static void free_ws(Workspace& w) {
     void* ptrs[] = {w.XR, w.XC, w.x, w.r, w.b, w.p, w.zraw, w.z, w.s, w.hs, w.y, w.fft2d, w.partial,
-                    w.partial_div, w.S, w.log, w.vc, w.gain, w.tw, w.tw2, w.scratch_d, w.hx, w.zraw2};
+                    w.partial_div, w.S, w.log, w.vc, w.gain, w.tw, w.tw2, w.scratch_d, w.hx, w.zraw2,
+                    w.fan_rays, w.fan_views};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -395,6 +396,41 @@ int dgamp_ct_plan(const dgamp_ct_geometry* g, const dgamp_ct_options* opt, dgamp
     return DGAMP_CT_OK;
 }
 
+int dgamp_ct_plan_fan(const dgamp_ct_fan_geometry* g, const dgamp_ct_options* opt, dgamp_ct_plan_t* out) {
+    if (!g || !out) return DGAMP_CT_ERR_INVALID_ARG;
+    *out = nullptr;
+    const dgamp_ct_geometry& b = g->base;
+    if (b.n < 2 || b.n > DGAMP_CT_MAX_N || b.n_views < 1 || b.n_views > DGAMP_CT_MAX_VIEWS || b.n_det < 2)
+        return DGAMP_CT_ERR_INVALID_ARG;
+    // source and detector outside the image's circumscribed circle with a
+    // margin of two pixels (the back-projector projects points one pixel
+    // outside the image through the source), and not so far that the 32.32
+    // positions overflow
+    const double rmin = b.n / std::sqrt(2.0) + 2.0;
+    if (!(g->src_dist > rmin && g->src_dist <= 1e8) || !(g->det_dist > rmin && g->det_dist <= 1e8) ||
+        !(g->det_spacing > 0 && g->det_spacing <= 1e4))
+        return DGAMP_CT_ERR_INVALID_ARG;
+    std::vector<double> ang(b.n_views);
+    for (int k = 0; k < b.n_views; ++k) {
+        ang[k] = b.angles ? b.angles[k] : (double)k * (2.0 * 3.14159265358979323846 / b.n_views);
+        if (!std::isfinite(ang[k])) return DGAMP_CT_ERR_INVALID_ARG;
+    }
+    // the parallel plan of the same sizes provides the workspace, the image
+    // filter and the single-step entry points; the fan rays replace its views
+    dgamp_ct_geometry pg = b;
+    pg.angles = ang.data();
+    dgamp_ct_plan_t pl = nullptr;
+    int rc = dgamp_ct_plan(&pg, opt, &pl);
+    if (rc != DGAMP_CT_OK) return rc;
+    rc = fan_setup(pl, ang, g->src_dist, g->det_dist, g->det_spacing);
+    if (rc != DGAMP_CT_OK) {
+        dgamp_ct_plan_destroy(pl);
+        return rc;
+    }
+    *out = pl;
+    return DGAMP_CT_OK;
+}
+
 void dgamp_ct_plan_destroy(dgamp_ct_plan_t pl) {
     if (!pl) return;
     cudaDeviceSynchronize();
@@ -467,6 +503,15 @@ int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
 int dgamp_ct_project(dgamp_ct_plan_t pl, const float* d_img, float* d_sino, int precond, void* stream) {
     if (!pl || !d_img || !d_sino) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    if (pl->fan) {   // Phi~ x = A (V^-1 x), V^-1 x in ws.r
+        const float* src = d_img;
+        if (precond) {
+            DGCT_TRY(launch_precond_image(pl, d_img, pl->ws.r, 1, st));
+            src = pl->ws.r;
+        }
+        DGCT_TRY(launch_stage_image(pl, src, st));
+        return launch_fan_project(pl, d_sino, st);
+    }
     DGCT_TRY(launch_stage_image(pl, d_img, st));
     if (!precond) return launch_project(pl, d_sino, st);
     DGCT_TRY(launch_project(pl, pl->ws.zraw, st));
@@ -476,6 +521,11 @@ int dgamp_ct_project(dgamp_ct_plan_t pl, const float* d_img, float* d_sino, int 
 int dgamp_ct_backproject(dgamp_ct_plan_t pl, const float* d_sino, float* d_img, int precond, void* stream) {
     if (!pl || !d_sino || !d_img) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    if (pl->fan) {   // Phi~^T s = V^-1 (A^T s), A^T s in ws.r
+        if (!precond) return launch_fan_backproject(pl, d_sino, d_img, st);
+        DGCT_TRY(launch_fan_backproject(pl, d_sino, pl->ws.r, st));
+        return launch_precond_image(pl, pl->ws.r, d_img, 1, st);
+    }
     const float* src = d_sino;
     if (precond) {
         DGCT_TRY(launch_filter(pl, d_sino, pl->ws.hs, st));
@@ -486,6 +536,7 @@ int dgamp_ct_backproject(dgamp_ct_plan_t pl, const float* d_sino, float* d_img, 
 
 int dgamp_ct_filter(dgamp_ct_plan_t pl, const float* d_in, float* d_out, void* stream) {
     if (!pl || !d_in || !d_out) return DGAMP_CT_ERR_INVALID_ARG;
+    if (pl->fan) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;   // H is the parallel-beam form of V^-1
     return launch_filter(pl, d_in, d_out, (cudaStream_t)stream);
 }
 
@@ -538,6 +589,7 @@ int dgamp_ct_precond_image(dgamp_ct_plan_t pl, const float* d_in, float* d_out, 
 int dgamp_ct_profile_iteration(dgamp_ct_plan_t pl, int32_t reps, double* h_ms, int32_t cap,
                                int32_t* count, void* stream) {
     if (!pl || reps < 1 || !h_ms || !count) return DGAMP_CT_ERR_INVALID_ARG;
+    if (pl->fan) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;   // the fan-beam solve is not built yet
     if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
     const int nk = segments_per_iteration(pl);
     *count = nk;
@@ -626,6 +678,7 @@ int dgamp_ct_solve_trace(dgamp_ct_plan_t pl, const float* d_counts, double I0, i
                          float* d_r_trace, double* h_tau_r, void* stream) {
     if (!pl || !d_counts || !d_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
     if (iters < 1 || iters > kMaxIters || !(I0 > 0) || !std::isfinite(I0)) return DGAMP_CT_ERR_INVALID_ARG;
+    if (pl->fan) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;   // the fan-beam solve is not built yet
     if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = (size_t)pl->N;
@@ -651,6 +704,7 @@ int dgamp_ct_solve(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t
                    float* d_x_out, dgamp_ct_stats* stats, void* stream) {
     if (!pl || !d_counts || !d_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
     if (iters < 1 || iters > kMaxIters || !(I0 > 0) || !std::isfinite(I0)) return DGAMP_CT_ERR_INVALID_ARG;
+    if (pl->fan) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;   // the fan-beam solve is not built yet
     if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace& w = pl->ws;
@@ -703,6 +757,7 @@ extern "C" {
 int dgamp_ct_solve_host(dgamp_ct_plan_t pl, const float* h_counts, double I0, int32_t iters, float* h_mu_out,
                         dgamp_ct_stats* stats, void* stream) {
     if (!pl || !h_counts || !h_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
+    if (pl->fan) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;   // the fan-beam solve is not built yet
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = (size_t)pl->N, M = (size_t)pl->M;
     // counts land in the hs buffer (free until the first filter of s), mu in r

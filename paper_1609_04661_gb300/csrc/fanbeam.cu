@@ -1,0 +1,283 @@
+// Flat-detector fan beam (Section 6; option of the plan, dgamp_ct_plan_fan):
+// the Joseph projector A along each ray's own direction, its exact
+// transpose, and ||Phi~||_F^2 for Phi~ = A V^-1 (Eq. precondAMP_op with the
+// image-domain cone filter; the detector-axis form H A is a parallel-beam
+// identity and does not apply).
+//
+// Geometry (pixel units, pixel centres as for parallel beam): at view angle
+// theta the source sits at S = -dso e_c with e_c = (-sin, cos), the detector
+// centre at ddo e_c, and bin d at the detector centre plus u_d e_u with
+// e_u = (cos, sin), u_d = (d - (n_det-1)/2) du.  Ray d runs along
+// v = T_d - S.  A ray with |v_x| >= |v_y| is marched by columns: in column s
+// it sits at the fractional row a0 + s a_step, a_step = -v_y / v_x, and the
+// linear interpolation between the two nearest rows is weighted by
+// w = |v| / |v_x|; any other ray is marched by rows with the fractional
+// column a0 + s a_step, a_step = -v_x / v_y, w = |v| / |v_y|.  Positions are
+// 32.32 fixed point computed once per ray in FP64, so the projector and the
+// back-projector take bit-identical taps.
+//
+// A: one block = 32 adjacent rays of one view; 8 warps march disjoint parts
+// of the step range and add their partial sums in a fixed order.  A ray
+// marched by columns reads the staged transpose XC (line s = column s), one
+// marched by rows the staged rows XR, as in joseph.cu; taps just outside the
+// image read the zero guard cells.
+//
+// A^T: pixel-driven gather, one thread per pixel, views in order.  The rays
+// of view k that can put a tap on pixel (X, Y) through column X are those
+// crossing the segment (X, Y-1)-(X, Y+1); their bins lie between the
+// projections of its end points through the source (bin(p) is monotone
+// along a segment in front of the source), widened by one bin each way.
+// Each candidate is then tested with the projector's own integer position,
+// so the gather applies exactly the projector's taps.  Rays marched by rows
+// are found through the segment (X-1, Y)-(X+1, Y) likewise.
+//
+// ||Phi~||_F^2 = sum over rays of ||V^-1 a_i||^2: plan-time, one ray at a
+// time (its taps scattered into an image, V^-1 by the image filter of
+// fft.cu, the sum of squares in FP64).
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace dgct {
+
+constexpr int kFanSeg = 8;
+
+// ------------------------------------------------------------ projector ----
+template <typename T>
+__global__ void __launch_bounds__(32 * kFanSeg)
+k_fan_project(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int n, int nd,
+              const FanRay* __restrict__ rays, float* __restrict__ sino) {
+    __shared__ float red[kFanSeg][32];
+    const int v = blockIdx.y;
+    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int d = blockIdx.x * 32 + lane;
+    float acc = 0.f, w = 0.f;
+    if (d < nd) {
+        const FanRay R = rays[(size_t)v * nd + d];
+        w = R.w;
+        const T* __restrict__ B = R.col ? XC : XR;
+        int s0, s1;
+        step_range(R.a0, R.a_step, n, s0, s1);
+        const int len = (n + kFanSeg - 1) / kFanSeg;
+        s0 = max(s0, seg * len);
+        s1 = min(s1, seg * len + len - 1);
+        if (s0 <= s1) {
+            long long pos = R.P0 + (long long)s0 * R.PSTEP;
+            const T* __restrict__ line = B + (size_t)s0 * ldp + kPad;
+            for (int s = s0; s <= s1; ++s, pos += R.PSTEP, line += ldp) {
+                int i0;
+                float f;
+                joseph_tap(pos, i0, f);
+                const float x0 = ldf(line + i0), x1 = ldf(line + i0 + 1);
+                acc += fmaf(f, x1 - x0, x0);
+            }
+        }
+    }
+    red[seg][lane] = acc;
+    __syncthreads();
+    if (seg == 0 && d < nd) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < kFanSeg; ++k) t += red[k][lane];
+        sino[(size_t)v * nd + d] = t * w;
+    }
+}
+
+// ------------------------------------------------------- back-projector ----
+__device__ __forceinline__ float fan_bin(const FanView& V, float x, float y) {
+    const float along = fmaf(x, V.ecx, fmaf(y, V.ecy, V.dso));   // > 0: in front of the source
+    const float across = fmaf(x, V.eux, y * V.euy);
+    return V.dsd * across / (along * V.du) + V.half;
+}
+
+__device__ __forceinline__ void fan_candidates(const FanView& V, float x1, float y1, float x2, float y2,
+                                               int nd, int& lo, int& hi) {
+    const float b1 = fan_bin(V, x1, y1), b2 = fan_bin(V, x2, y2);
+    const float bl = fmaxf(fminf(b1, b2), -2.f), bh = fminf(fmaxf(b1, b2), (float)nd + 1.f);
+    lo = max(0, (int)floorf(bl) - 1);
+    hi = min(nd - 1, (int)ceilf(bh) + 1);
+}
+
+__global__ void __launch_bounds__(256)
+k_fan_backproject(const float* __restrict__ sino, const FanRay* __restrict__ rays,
+                  const FanView* __restrict__ views, int n, int nv, int nd, float* __restrict__ img) {
+    const int ix = blockIdx.x * 16 + (threadIdx.x & 15), iy = blockIdx.y * 16 + (threadIdx.x >> 4);
+    if (ix >= n || iy >= n) return;
+    const float c = 0.5f * (float)(n - 1);
+    const float X = (float)ix - c, Y = c - (float)iy;
+    float acc = 0.f;
+    for (int k = 0; k < nv; ++k) {
+        const FanView V = views[k];
+        const FanRay* __restrict__ R = rays + (size_t)k * nd;
+        const float* __restrict__ sk = sino + (size_t)k * nd;
+        int lo, hi;
+        // rays marched by columns that cross column X within one row of Y
+        fan_candidates(V, X, Y - 1.f, X, Y + 1.f, nd, lo, hi);
+        for (int d = lo; d <= hi; ++d) {
+            const FanRay r = R[d];
+            if (!r.col) continue;
+            int i0;
+            float f;
+            joseph_tap(r.P0 + (long long)ix * r.PSTEP, i0, f);
+            if (i0 == iy) acc = fmaf((1.f - f) * r.w, sk[d], acc);
+            else if (i0 == iy - 1) acc = fmaf(f * r.w, sk[d], acc);
+        }
+        // rays marched by rows that cross row Y within one column of X
+        fan_candidates(V, X - 1.f, Y, X + 1.f, Y, nd, lo, hi);
+        for (int d = lo; d <= hi; ++d) {
+            const FanRay r = R[d];
+            if (r.col) continue;
+            int i0;
+            float f;
+            joseph_tap(r.P0 + (long long)iy * r.PSTEP, i0, f);
+            if (i0 == ix) acc = fmaf((1.f - f) * r.w, sk[d], acc);
+            else if (i0 == ix - 1) acc = fmaf(f * r.w, sk[d], acc);
+        }
+    }
+    img[(size_t)iy * n + ix] = acc;
+}
+
+// ------------------------------------------------------- ||Phi~||_F^2 ----
+// The taps of ray `ray` scattered into a zeroed [n][n] image (one block; a
+// ray puts at most one tap on a pixel, so the writes do not collide).
+__global__ void __launch_bounds__(1024)
+k_fan_ray_image(const FanRay* __restrict__ rays, int ray, int n, float* __restrict__ img) {
+    const size_t N = (size_t)n * n;
+    for (size_t i = threadIdx.x; i < N; i += blockDim.x) img[i] = 0.f;
+    __syncthreads();
+    const FanRay R = rays[ray];
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        int i0;
+        float f;
+        joseph_tap(R.P0 + (long long)s * R.PSTEP, i0, f);
+        const float t[2] = {(1.f - f) * R.w, f * R.w};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int q = i0 + j;
+            if (q < 0 || q >= n) continue;
+            const size_t o = R.col ? (size_t)q * n + s : (size_t)s * n + q;
+            img[o] = t[j];
+        }
+    }
+}
+
+// out[slot] = sum of squares of img (FP64, one block, fixed order).
+__global__ void __launch_bounds__(1024)
+k_sum_squares(const float* __restrict__ img, long long N, double* __restrict__ out, int slot) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+        const double v = img[i];
+        acc += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) out[slot] = t;
+    }
+}
+
+// ----------------------------------------------------------------- host ----
+static void fan_constants(int n, int nd, const std::vector<double>& ang, double dso, double ddo, double du,
+                          std::vector<FanRay>& rays, std::vector<FanView>& views) {
+    const double c = 0.5 * (n - 1), half = 0.5 * (nd - 1), q = 4294967296.0;
+    rays.resize(ang.size() * (size_t)nd);
+    views.resize(ang.size());
+    for (size_t k = 0; k < ang.size(); ++k) {
+        const double st = std::sin(ang[k]), ct = std::cos(ang[k]);
+        const double sx = dso * st, sy = -dso * ct;
+        views[k] = FanView{(float)ct, (float)st, (float)-st, (float)ct, (float)dso, (float)(dso + ddo),
+                           (float)du, (float)half};
+        for (int d = 0; d < nd; ++d) {
+            const double u = (d - half) * du;
+            const double vx = -ddo * st + u * ct - sx, vy = ddo * ct + u * st - sy;
+            const double L = std::hypot(vx, vy);
+            FanRay R{};
+            double a0, as, w;
+            if (std::fabs(vx) >= std::fabs(vy)) {       // by columns: row c - (S_y + (X - S_x) v_y / v_x)
+                const double t = vy / vx;
+                a0 = c - sy + (sx + c) * t;
+                as = -t;
+                w = L / std::fabs(vx);
+                R.col = 1;
+            } else {                                     // by rows: column S_x + (Y - S_y) v_x / v_y + c
+                const double t = vx / vy;
+                a0 = sx + c + (c - sy) * t;
+                as = -t;
+                w = L / std::fabs(vy);
+                R.col = 0;
+            }
+            R.P0 = std::llround(a0 * q);
+            R.PSTEP = std::llround(as * q);
+            R.a0 = (float)a0;
+            R.a_step = (float)as;
+            R.w = (float)w;
+            rays[k * (size_t)nd + d] = R;
+        }
+    }
+}
+
+int launch_fan_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st) {
+    const dim3 grd((unsigned)((pl->nd + 31) / 32), (unsigned)pl->nv);
+    k_fan_project<float><<<grd, 32 * kFanSeg, 0, st>>>(pl->ws.XR, pl->ws.XC, pl->ldp, pl->n, pl->nd,
+                                                       pl->ws.fan_rays, sino);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+int launch_fan_backproject(const dgamp_ct_plan_s* pl, const float* sino, float* img, cudaStream_t st) {
+    const dim3 grd((unsigned)((pl->n + 15) / 16), (unsigned)((pl->n + 15) / 16));
+    k_fan_backproject<<<grd, 256, 0, st>>>(sino, pl->ws.fan_rays, pl->ws.fan_views, pl->n, pl->nv, pl->nd, img);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+int fan_setup(dgamp_ct_plan_s* pl, const std::vector<double>& ang, double src_dist, double det_dist,
+              double det_spacing) {
+    std::vector<FanRay> rays;
+    std::vector<FanView> views;
+    fan_constants(pl->n, pl->nd, ang, src_dist, det_dist, det_spacing, rays, views);
+    if (cudaMalloc((void**)&pl->ws.fan_rays, rays.size() * sizeof(FanRay)) != cudaSuccess ||
+        cudaMalloc((void**)&pl->ws.fan_views, views.size() * sizeof(FanView)) != cudaSuccess) {
+        cudaGetLastError();
+        return DGAMP_CT_ERR_OOM;
+    }
+    DGCT_CUDA(cudaMemcpy(pl->ws.fan_rays, rays.data(), rays.size() * sizeof(FanRay), cudaMemcpyHostToDevice));
+    DGCT_CUDA(cudaMemcpy(pl->ws.fan_views, views.data(), views.size() * sizeof(FanView), cudaMemcpyHostToDevice));
+    pl->fan = 1;
+    // ||Phi~||_F^2: ray image in ws.r[0..N), V^-1 of it in ws.r[N..2N), one FP64
+    // sum of squares per ray into scratch, added on the host in ray order
+    const int64_t M = pl->M, N = pl->N;
+    double* sums = nullptr;
+    if (cudaMalloc((void**)&sums, (size_t)M * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return DGAMP_CT_ERR_OOM;
+    }
+    int rc = DGAMP_CT_OK;
+    for (int64_t i = 0; i < M && rc == DGAMP_CT_OK; ++i) {
+        k_fan_ray_image<<<1, 1024>>>(pl->ws.fan_rays, (int)i, pl->n, pl->ws.r);
+        rc = launch_precond_image(pl, pl->ws.r, pl->ws.r + N, 1, 0);
+        if (rc == DGAMP_CT_OK) k_sum_squares<<<1, 1024>>>(pl->ws.r + N, N, sums, (int)i);
+        const cudaError_t e = cudaGetLastError();
+        if (rc == DGAMP_CT_OK && e != cudaSuccess) rc = cuda_fail(e);
+    }
+    std::vector<double> h((size_t)M);
+    if (rc == DGAMP_CT_OK) {
+        const cudaError_t e = cudaMemcpy(h.data(), sums, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+    }
+    cudaFree(sums);
+    if (rc != DGAMP_CT_OK) return rc;
+    double tot = 0.0;
+    for (double v : h) tot += v;
+    pl->frob2 = tot;
+    DGCT_CUDA(cudaMemcpy(&pl->ws.S->frob2, &tot, sizeof(double), cudaMemcpyHostToDevice));
+    return DGAMP_CT_OK;
+}
+
+}  // namespace dgct

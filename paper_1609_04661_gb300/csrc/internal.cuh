@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/dgamp_ct.h"
 
 namespace dgct {
@@ -59,6 +61,23 @@ __device__ __forceinline__ float solve_lambda(const DevScalars* S, float c_tv, i
     return from_scalars ? c_tv * sqrtf((float)S->tau_r) : lambda_arg;
 }
 
+// One fan-beam ray's Joseph constants (fanbeam.cu): its position on the
+// interpolated axis at step s is pos = P0 + s PSTEP in 32.32 fixed point
+// (the fractional row in column s when col = 1, the fractional column in row
+// s otherwise), |PSTEP| <= 2^32; w is the path length per step.
+struct FanRay {
+    long long P0, PSTEP;
+    float a0, a_step, w;
+    int col;
+};
+
+// One fan-beam view: the detector axis e_u, the central direction e_c (the
+// source sits at -dso e_c), the source-detector distance and the bin map
+// bin(p) = dsd (p . e_u) / ((p . e_c + dso) du) + half.
+struct FanView {
+    float eux, euy, ecx, ecy, dso, dsd, du, half;
+};
+
 // Per-iteration log record (what dgamp_ct_stats exposes).
 struct IterLog { double tau_x, tau_p, tau_s, tau_r, div, eps; };
 
@@ -86,6 +105,8 @@ struct Workspace {
     float2* tw2 = nullptr;         // the same for length m2
     double* scratch_d = nullptr;   // plan-time FP64 scratch
     float* b = nullptr;            // the iteration's probe b (Eq. MC_SURE) [n][n]
+    FanRay* fan_rays = nullptr;    // fan-beam plans: [n_views][n_det]
+    FanView* fan_views = nullptr;  // fan-beam plans: [n_views]
 };
 
 }  // namespace dgct
@@ -108,6 +129,7 @@ struct dgamp_ct_plan_s {
     int sino_fused = 0;                    // solve: H A x, output step, H s in one kernel (k_sino_step)
     int bp_mode = 0;                       // A^T: 0 pixel-driven gather, 1 ray-driven tiles (plan-time choice)
     int pj_seg = 8;                        // A: step segments (warps) per ray group, 8/16/32 (plan-time choice)
+    int fan = 0;                           // 1: flat-detector fan beam (dgamp_ct_plan_fan)
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;   // stream the graph was captured for (identity only)
@@ -128,6 +150,22 @@ __device__ __forceinline__ void stf(bf16s* p, float v) { *p = __float2bfloat16_r
 
 __device__ __forceinline__ long long joseph_pos(const ViewConst& c, int d, int s) {
     return c.P0 + (long long)d * c.PDET + (long long)s * c.PSTEP;
+}
+
+// Steps of a ray (position `base` at s = 0, `a_step` per step) whose taps can
+// touch the image: pos in [-1, n) widened by one step each way (|a_step| <= 1,
+// so the taps of the extra steps stay inside the zero guard cells).
+__device__ __forceinline__ void step_range(float base, float a_step, int n, int& s0, int& s1) {
+    if (fabsf(a_step) < 1e-12f) {
+        if (base >= -1.f && base < (float)n) { s0 = 0; s1 = n - 1; } else { s0 = 1; s1 = 0; }
+        return;
+    }
+    float t0 = (-1.f - base) / a_step, t1 = ((float)n - base) / a_step;
+    float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
+    lo = fmaxf(lo, -1.f);
+    hi = fminf(hi, (float)n);
+    s0 = max(0, (int)floorf(lo) - 1);
+    s1 = min(n - 1, (int)ceilf(hi) + 1);
 }
 
 // Split a 32.32 position into its left tap (floor) and the fraction in [0, 1):
@@ -271,6 +309,11 @@ int tvm_num_launches(const dgamp_ct_plan_s* pl);
 int launch_tvm_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,
                      float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st);
 int tvm_set_smem_limits(int bytes);
+// fanbeam.cu: flat-detector fan-beam A, A^T and ||A V^-1||_F^2
+int fan_setup(dgamp_ct_plan_s* pl, const std::vector<double>& ang, double src_dist, double det_dist,
+              double det_spacing);
+int launch_fan_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st);
+int launch_fan_backproject(const dgamp_ct_plan_s* pl, const float* sino, float* img, cudaStream_t st);
 // x, staging, divergence and tau_x from D(r) and J_D(r) b (learned denoiser)
 int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_out, int solve_mode, int t_arg,
                          double* div_out, cudaStream_t st);

@@ -59,22 +59,6 @@ int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t
 }
 
 // --------------------------------------------------------- projection ----
-// Steps of ray `base` (position at s = 0) whose taps can touch the image:
-// pos in [-1, n) widened by one step each way (|a_step| <= 1, so the taps of
-// the extra steps stay inside the zero guard cells).
-__device__ __forceinline__ void step_range(float base, float a_step, int n, int& s0, int& s1) {
-    if (fabsf(a_step) < 1e-12f) {
-        if (base >= -1.f && base < (float)n) { s0 = 0; s1 = n - 1; } else { s0 = 1; s1 = 0; }
-        return;
-    }
-    float t0 = (-1.f - base) / a_step, t1 = ((float)n - base) / a_step;
-    float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
-    lo = fmaxf(lo, -1.f);
-    hi = fminf(hi, (float)n);
-    s0 = max(0, (int)floorf(lo) - 1);
-    s1 = min(n - 1, (int)ceilf(hi) + 1);
-}
-
 // One block = 32 adjacent rays of one view; its SEG warps (8, 16 or 32,
 // chosen at plan time) march disjoint parts of the step range of those rays
 // and the partial sums are added in a fixed order, so the result does not

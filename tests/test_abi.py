@@ -45,16 +45,19 @@ def test_struct_layouts_match_header(lib, tmp_path):
         pytest.skip("no C compiler")
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dgamp_ct.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(dgamp_ct_geometry),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(dgamp_ct_geometry),'
                     ' sizeof(dgamp_ct_options), sizeof(dgamp_ct_stats), offsetof(dgamp_ct_options, seed),'
-                    ' offsetof(dgamp_ct_options, use_graph), offsetof(dgamp_ct_stats, tau_x_floored));'
+                    ' offsetof(dgamp_ct_options, use_graph), offsetof(dgamp_ct_stats, tau_x_floored),'
+                    ' offsetof(dgamp_ct_options, tv_metric), sizeof(dgamp_ct_fan_geometry),'
+                    ' offsetof(dgamp_ct_fan_geometry, det_spacing));'
                     'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     want = [C.sizeof(binding.Geometry), C.sizeof(binding.Options), C.sizeof(binding.Stats),
             binding.Options.seed.offset, binding.Options.use_graph.offset,
-            binding.Stats.tau_x_floored.offset]
+            binding.Stats.tau_x_floored.offset, binding.Options.tv_metric.offset,
+            C.sizeof(binding.FanGeometry), binding.FanGeometry.det_spacing.offset]
     assert got == want
     o = binding.Options()
     assert lib.dgamp_ct_default_options(C.byref(o)) == 0
@@ -77,3 +80,11 @@ def test_argument_errors_need_no_device(lib):
     lib.dgamp_ct_strerror.restype = C.c_char_p
     assert lib.dgamp_ct_strerror(-3) == b"out of device memory"
     assert lib.dgamp_ct_solve(None, None, C.c_double(1.0), 1, None, None, None, None) == -1
+    # fan beam: a source inside the image's circumscribed circle (plus margin)
+    # or a zero bin pitch is refused before any device call
+    fp = lib.dgamp_ct_plan_fan
+    fp.restype = C.c_int
+    assert fp(None, None, C.byref(h)) == -1
+    for sd, dd, du in [(12.0, 100.0, 1.0), (100.0, 13.0, 1.0), (100.0, 100.0, 0.0), (2e8, 100.0, 1.0)]:
+        fg = binding.FanGeometry(binding.Geometry(16, 10, 24, None), sd, dd, du)
+        assert fp(C.byref(fg), None, C.byref(h)) == -1
