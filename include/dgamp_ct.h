@@ -167,9 +167,11 @@ int dgamp_ct_plan(const dgamp_ct_geometry* g, const dgamp_ct_options* opt,
    (FP64, one ray at a time: plan time grows with n_views n_det).
    dgamp_ct_project / dgamp_ct_backproject apply A, A^T (precond = 0) or
    Phi~, Phi~^T (precond = 1); the output step, denoisers, probe and image
-   filter work as for any plan.  dgamp_ct_filter and the solve entry points
-   (solve, solve_host, solve_trace, solve_batched, profile_iteration) return
-   UNSUPPORTED_GEOMETRY for a fan-beam plan.  Synchronous.
+   filter work as for any plan, and so do the solve entry points: one
+   iteration runs V^-1 x, A, the output step (three-kernel form), A^T and
+   V^-1 with the update r = x + tau_r V^-1 A^T s, then the denoiser, all in
+   FP32 storage (option storage is ignored).  dgamp_ct_filter returns
+   UNSUPPORTED_GEOMETRY.  Synchronous.
    Errors: INVALID_ARG (as dgamp_ct_plan, and the distance limits), OOM, CUDA. */
 int dgamp_ct_plan_fan(const dgamp_ct_fan_geometry* g, const dgamp_ct_options* opt,
                       dgamp_ct_plan_t* out);

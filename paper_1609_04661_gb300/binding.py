@@ -199,6 +199,7 @@ class Plan:
             self._angles = np.ascontiguousarray(angles, dtype=np.float64)
             g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
         self.options = default_options(**options)
+        self.fan = fan is not None
         h = C.c_void_p()
         if fan is None:
             _check(self._lib.dgamp_ct_plan(C.byref(g), C.byref(self.options), C.byref(h)), "dgamp_ct_plan")
@@ -373,9 +374,12 @@ class Plan:
         cnt = C.c_int32()
         _check(self._lib.dgamp_ct_profile_iteration(self._h, int(reps), arr, cap, C.byref(cnt), _stream()),
                "dgamp_ct_profile_iteration")
-        fused = self.tuning()["sino_fused"] and not self.options.output_moments
-        sino = ["sino_step"] if fused else ["filter_z", "output_step", "filter_s"]
-        names = ["project"] + sino + ["backproject_update", "probe_input"]
+        if self.fan:
+            names = ["vinv_stage_project", "output_step", "backproject", "vinv_update", "probe_input"]
+        else:
+            fused = self.tuning()["sino_fused"] and not self.options.output_moments
+            sino = ["sino_step"] if fused else ["filter_z", "output_step", "filter_s"]
+            names = ["project"] + sino + ["backproject_update", "probe_input"]
         if self.options.denoiser == 1:
             names += ["cnn_pair", "denoise_final"]
         elif metric:

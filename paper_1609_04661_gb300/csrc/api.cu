@@ -243,6 +243,18 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
     };
     DGCT_TRY(mark());
     const int bf = pl->opt.storage;                                      // BF16 sinograms / staged image
+    if (pl->fan) {
+        // fan beam: Phi~ = A V^-1 with the image-domain filter, FP32 storage
+        DGCT_TRY(launch_precond_image(pl, w.x, w.r, 1, st));             // Step 1: V^-1 x (3 kernels)
+        DGCT_TRY(launch_stage_image(pl, w.r, st, 0));
+        DGCT_TRY(launch_fan_project(pl, w.z, st));                       //         z = A V^-1 x
+        DGCT_TRY(mark());
+        DGCT_TRY(launch_output_step(pl, w.z, w.y, w.s, 1, 1, 0.0, 0.0, nullptr, st, 0));  // Step 2
+        DGCT_TRY(mark());
+        DGCT_TRY(launch_fan_backproject(pl, w.s, w.r, st));              // Step 3: A^T s
+        DGCT_TRY(mark());
+        DGCT_TRY(launch_precond_image_update(pl, w.r, w.x, w.r, st));    //         r = x + tau_r V^-1 A^T s
+    } else {
     DGCT_TRY(launch_project(pl, w.zraw, st, bf));                      // Step 1: A x
     DGCT_TRY(mark());
     if (fused_sino_now(pl)) {
@@ -258,6 +270,7 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
     }
     DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st, bf,          //         r = x + tau_r A^T H s
                                 fused_sino_now(pl) ? sino_step_partials(pl) : 0));
+    }
     DGCT_TRY(mark());
     // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r
     DGCT_TRY(launch_probe_input(pl, 0, st, pl->opt.denoiser == 1 ? 1 : 0));
@@ -279,19 +292,30 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
     return DGAMP_CT_OK;
 }
 
-// kernels one iteration launches
-static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
-    const int sino = fused_sino_now(pl) ? 1 : 3;    // H A x, output step, H s
-    if (pl->opt.denoiser == 1 && pl->cnn) return sino + 3 + cnn_launches_per_pair(pl->cnn) + 1;
-    return sino + 3 + tv_num_launches(pl, 1, 0.0);
+// Steps 1-3 of one iteration: kernels and timed segments.  Parallel beam:
+// A x, the sinogram step (1 or 3 kernels), the back-projection.  Fan beam:
+// V^-1 x (3) with the staging and A (one segment), the output step, A^T,
+// and V^-1 with the update (3, one segment).
+static int front_kernels(const dgamp_ct_plan_s* pl) {
+    if (pl->fan) return 10;
+    return (fused_sino_now(pl) ? 1 : 3) + 2;
+}
+static int front_segments(const dgamp_ct_plan_s* pl) {
+    if (pl->fan) return 4;
+    return (fused_sino_now(pl) ? 1 : 3) + 2;
 }
 
-// timed segments of one iteration (dgamp_ct_profile_iteration): every kernel,
+// kernels one iteration launches: Steps 1-3, the probe, the denoiser
+static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
+    if (pl->opt.denoiser == 1 && pl->cnn) return front_kernels(pl) + 1 + cnn_launches_per_pair(pl->cnn) + 1;
+    return front_kernels(pl) + 1 + tv_num_launches(pl, 1, 0.0);
+}
+
+// timed segments of one iteration (dgamp_ct_profile_iteration): as above,
 // except that the learned denoiser's launches form one segment
 static int segments_per_iteration(const dgamp_ct_plan_s* pl) {
-    const int sino = fused_sino_now(pl) ? 1 : 3;
-    if (pl->opt.denoiser == 1 && pl->cnn) return sino + 5;
-    return sino + 3 + tv_num_launches(pl, 1, 0.0);
+    if (pl->opt.denoiser == 1 && pl->cnn) return front_segments(pl) + 3;
+    return front_segments(pl) + 1 + tv_num_launches(pl, 1, 0.0);
 }
 
 static void drop_graph(dgamp_ct_plan_s* pl) {
@@ -589,7 +613,6 @@ int dgamp_ct_precond_image(dgamp_ct_plan_t pl, const float* d_in, float* d_out, 
 int dgamp_ct_profile_iteration(dgamp_ct_plan_t pl, int32_t reps, double* h_ms, int32_t cap,
                                int32_t* count, void* stream) {
     if (!pl || reps < 1 || !h_ms || !count) return DGAMP_CT_ERR_INVALID_ARG;
-    if (pl->fan) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;   // the fan-beam solve is not built yet
     if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
     const int nk = segments_per_iteration(pl);
     *count = nk;
@@ -678,7 +701,6 @@ int dgamp_ct_solve_trace(dgamp_ct_plan_t pl, const float* d_counts, double I0, i
                          float* d_r_trace, double* h_tau_r, void* stream) {
     if (!pl || !d_counts || !d_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
     if (iters < 1 || iters > kMaxIters || !(I0 > 0) || !std::isfinite(I0)) return DGAMP_CT_ERR_INVALID_ARG;
-    if (pl->fan) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;   // the fan-beam solve is not built yet
     if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = (size_t)pl->N;
@@ -704,7 +726,6 @@ int dgamp_ct_solve(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t
                    float* d_x_out, dgamp_ct_stats* stats, void* stream) {
     if (!pl || !d_counts || !d_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
     if (iters < 1 || iters > kMaxIters || !(I0 > 0) || !std::isfinite(I0)) return DGAMP_CT_ERR_INVALID_ARG;
-    if (pl->fan) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;   // the fan-beam solve is not built yet
     if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace& w = pl->ws;
@@ -757,7 +778,6 @@ extern "C" {
 int dgamp_ct_solve_host(dgamp_ct_plan_t pl, const float* h_counts, double I0, int32_t iters, float* h_mu_out,
                         dgamp_ct_stats* stats, void* stream) {
     if (!pl || !h_counts || !h_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
-    if (pl->fan) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;   // the fan-beam solve is not built yet
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = (size_t)pl->N, M = (size_t)pl->M;
     // counts land in the hs buffer (free until the first filter of s), mu in r

@@ -74,7 +74,6 @@ int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float*
         const dgamp_ct_plan_t pl = plans[i];
         if (!pl || !d_counts[i] || !d_mu_out[i] || !(I0[i] > 0) || !std::isfinite(I0[i])) return DGAMP_CT_ERR_INVALID_ARG;
         if (pl->device != device) return DGAMP_CT_ERR_INVALID_ARG;
-        if (pl->fan) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;        // the fan-beam solve is not built yet
         if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
         if (!seen.insert(pl).second) return DGAMP_CT_ERR_INVALID_ARG;   // a plan holds one slice's state
         if (pl->opt.denoiser == 1 && !nets.insert(pl->cnn).second) return DGAMP_CT_ERR_INVALID_ARG;

@@ -253,6 +253,52 @@ k_img_rows_inv(const float2* __restrict__ C, int n, int m, const float2* __restr
     for (int i = threadIdx.x; i < n; i += blockDim.x) out[(size_t)iy * n + i] = r[fpad(i)].x * sc;
 }
 
+// pass 3 of V^-1 inside a fan-beam solve (Algorithm 1, Step 3 with
+// Phi~^T = V^-1 A^T): r = x + tau_r Re(.) / m^2 with tau_r from the device
+// scalars (the output step formed it), max |r| into S->rmax_bits (the output
+// step reset it), and the consumed divergence flag cleared, as the
+// parallel-beam back-projection does.
+__global__ void __launch_bounds__(512)
+k_img_rows_inv_update(const float2* __restrict__ C, int n, int m, const float2* __restrict__ tw,
+                      const float* __restrict__ x, DevScalars* __restrict__ S, float* __restrict__ out) {
+    extern __shared__ float2 smem[];
+    __shared__ unsigned s_max;
+    float2* a = smem;
+    float2* b = smem + fft_buf_len(m);
+    const int iy = blockIdx.x;
+    if (threadIdx.x == 0) {
+        s_max = 0u;
+        if (iy == 0) S->div_pending = 0u;
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) a[fpad(i)] = C[(size_t)iy * m + i];
+    __syncthreads();
+    const float2* r = fft_stockham(a, b, m, tw, 1.f);
+    const float sc = (float)S->tau_r / ((float)m * (float)m);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const size_t o = (size_t)iy * n + i;
+        const float rv = fmaf(sc, r[fpad(i)].x, x[o]);
+        out[o] = rv;
+        atomicMax(&s_max, __float_as_uint(fabsf(rv)));   // |r| >= 0: bit order is value order
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(&S->rmax_bits, s_max);
+}
+
+int launch_precond_image_update(const dgamp_ct_plan_s* pl, const float* in, const float* x, float* out,
+                                cudaStream_t st) {
+    const int n = pl->n, m = pl->m2;
+    const size_t sm = (size_t)2 * fft_buf_len(m) * sizeof(float2);
+    const int thr = fft_threads(m);
+    const float f0 = 1.0f / (2.0f * (float)pl->P);
+    k_img_rows_fwd<<<n, thr, sm, st>>>(in, n, m, pl->ws.tw2, pl->ws.fft2d);
+    DGCT_LAUNCH_CHECK();
+    k_img_cols<<<m, thr, sm, st>>>(pl->ws.fft2d, n, m, pl->ws.tw2, f0, 0);
+    DGCT_LAUNCH_CHECK();
+    k_img_rows_inv_update<<<n, thr, sm, st>>>(pl->ws.fft2d, n, m, pl->ws.tw2, x, pl->ws.S, out);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
 int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out, int inverse,
                          cudaStream_t st) {
     const int n = pl->n, m = pl->m2;
@@ -275,6 +321,7 @@ int fft_set_smem_limits(int bytes) {
     DGCT_TRY(raise_smem_limit((const void*)k_img_rows_fwd, bytes));
     DGCT_TRY(raise_smem_limit((const void*)k_img_cols, bytes));
     DGCT_TRY(raise_smem_limit((const void*)k_img_rows_inv, bytes));
+    DGCT_TRY(raise_smem_limit((const void*)k_img_rows_inv_update, bytes));
     return DGAMP_CT_OK;
 }
 

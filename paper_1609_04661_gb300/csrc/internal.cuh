@@ -281,6 +281,9 @@ int sino_step_partials(const dgamp_ct_plan_s* pl);   // FP64 partial sums of tau
 int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out, int inverse,
                          cudaStream_t st);
 int fft_set_smem_limits(int bytes);
+// r = x + tau_r V^-1 in (tau_r from S), max |r| into S (a fan-beam solve's Step 3)
+int launch_precond_image_update(const dgamp_ct_plan_s* pl, const float* in, const float* x, float* out,
+                                cudaStream_t st);
 int filter_autotune(dgamp_ct_plan_s* pl);
 int toeplitz_set_smem_limit(int nd);
 // output_step.cu
