@@ -21,6 +21,7 @@ Modules, each citing the passage it follows:
                                  i.i.d.-Gaussian GAMP used for state evolution
                                  (Section 3, Section 4.4)
 * :mod:`oracle.cnn`          -- residual 3x3 CNN denoiser forward/backward
+* :mod:`oracle.state_evolution` -- the scalar SE recursion for the CT slice (Section 4.4)
 
 Everything runs in float64.  Functions whose result is not pinned to an
 independent fact are marked "parity unpinned" in their docstring; at present
