@@ -257,6 +257,79 @@ def _batched(dg, rank, world, dist, flush, steps, learned=False):
             "joseph_steps_per_batch": int(work.sum()), "gpu_launches_per_batch_rank0": int(launches)}
 
 
+def _gpu_ms(fn, reps: int):
+    """Mean CUDA-event time of fn() over reps calls on the current stream."""
+    import torch
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _variants(dg, plan, case, counts, T):
+    """The paper's variants beyond the headline form (opt-in, --variants).
+
+    tv_metric: the headline solve with the prox-TV in the (V^T V)^{-1} norm
+    (Section 6.3), its PSNR curve and iterations/s.  fan512_v102: the
+    flat-detector fan-beam workload (Section 6 geometry, damped as the
+    headline): plan time (||Phi~||_F^2 ray by ray), iterations/s, PSNR, and A
+    and A^T alone with their compulsory bytes 4 (N + M) per launch."""
+    import time
+    import numpy as np
+    import torch
+    import synth
+    out = {}
+    mu = torch.empty((case["n"], case["n"]), device="cuda")
+    try:
+        plan.set_options(tv_metric=1)
+        curve = []
+        for t in range(1, T + 1):
+            plan.solve(counts, case["I0"], t, mu_out=mu)
+            curve.append(_psnr(mu.cpu().numpy().astype("float64"), case["mu"]))
+        ms = _gpu_ms(lambda: plan.solve(counts, case["I0"], T, mu_out=mu), 1)
+        out["tv_metric_damped"] = {"psnr_db_final": round(curve[-1], 2), "psnr_db_best": round(max(curve), 2),
+                                   "psnr_db_at_5": round(curve[4], 2) if T >= 5 else None,
+                                   "iters_per_s": T / (ms * 1e-3)}
+    except Exception as e:                      # a variant never takes the bench line down
+        out["tv_metric_damped"] = {"error": f"{type(e).__name__}: {e}"}
+    finally:
+        plan.set_options(tv_metric=0)
+    try:
+        c = synth.make_case("fan512_v102")
+        f = c["fan"]
+        n, nv, nd, Tf = c["n"], c["n_views"], c["n_det"], c["iters"]
+        t0 = time.perf_counter()
+        fp = dg.Plan(n, nv, nd, fan=f, **TV)
+        plan_s = time.perf_counter() - t0
+        y = torch.as_tensor(c["y"]).cuda()
+        fmu = torch.empty((n, n), device="cuda")
+        fp.solve(y, c["I0"], Tf, mu_out=fmu)                     # warm-up, graph capture
+        ms = _gpu_ms(lambda: fp.solve(y, c["I0"], Tf, mu_out=fmu), 3)
+        x = torch.rand((n, n), device="cuda")
+        sino = torch.rand((nv, nd), device="cuda")
+        img = torch.empty((n, n), device="cuda")
+        zs = torch.empty((nv, nd), device="cuda")
+        fp.project(x, out=zs)
+        fp.backproject(sino, out=img)
+        a_ms = _gpu_ms(lambda: fp.project(x, out=zs), 10)       # includes the image staging
+        at_ms = _gpu_ms(lambda: fp.backproject(sino, out=img), 10)
+        byts = 4.0 * (n * n + nv * nd)
+        out["fan512_v102"] = {"iters_per_s": Tf / (ms * 1e-3), "iterations": Tf,
+                              "psnr_db": round(_psnr(fmu.cpu().numpy().astype("float64"), c["mu"]), 2),
+                              "plan_s": plan_s, "frob_sq": fp.frob_sq,
+                              "project_ms": a_ms, "backproject_ms": at_ms,
+                              "project_gbs": byts / (a_ms * 1e-3) / 1e9, "backproject_gbs": byts / (at_ms * 1e-3) / 1e9,
+                              "kernel_ms": fp.profile_iteration(reps=3)}
+        fp.close()
+    except Exception as e:
+        out["fan512_v102"] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
 def _c5(dg):
     """The large mixed-precision workload: 128 slices of 1024 x 1024, 90 views,
     1449 bins, I0 = 1e5, sinograms and projector images in BF16 (storage = 1),
@@ -582,6 +655,7 @@ def run_gpu(args):
     batched_learned = None if (args.no_batched or args.no_learned) else _batched(dg, rank, world, dist, flush, 1,
                                                                                    learned=True)
     ablation = _ablation(plan, case, counts, T) if rank == 0 and not args.no_learned else None
+    variants = _variants(dg, plan, case, counts, T) if (args.variants and rank == 0) else None
 
     line = None
     if rank == 0:
@@ -600,7 +674,7 @@ def run_gpu(args):
                 "a_plus_at_gbs": a_at_bytes / (a_at_ms * 1e-3) / 1e9,
                 "iteration_ms": iter_ms, "tuning": tun, "kernel_ms": prof, "kernel_share": shares,
                 "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned, "batched": batched, "batched_learned": batched_learned, "large_bf16": c5,
-                "ablation": ablation}
+                "ablation": ablation, "variants": variants}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:
@@ -619,6 +693,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain section")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-batch section")
     ap.add_argument("--c5", action="store_true", help="add the 128-slice 1024x1024 BF16-storage workload (~1 min)")
+    ap.add_argument("--variants", action="store_true",
+                    help="add the (V^T V)^-1-norm prox-TV and the fan-beam workload")
     ap.add_argument("--tuning", default="", help="pin the headline plan's tuning, e.g. bp_mode=1,tv_kb=10")
     args = ap.parse_args()
     if args.impl == "reference":
