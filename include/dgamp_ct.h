@@ -176,6 +176,15 @@ int dgamp_ct_plan(const dgamp_ct_geometry* g, const dgamp_ct_options* opt,
 int dgamp_ct_plan_fan(const dgamp_ct_fan_geometry* g, const dgamp_ct_options* opt,
                       dgamp_ct_plan_t* out);
 
+/* The fan-beam Joseph constants dgamp_ct_plan_fan uploads, on the host (no
+   device needed): for ray i = k n_det + d, its position on the interpolated
+   axis at step s is (p0[i] + s pstep[i]) / 2^32 in 32.32 fixed point (the
+   fractional row in column s when col[i] = 1, the fractional column in row s
+   otherwise) and w[i] its path length per step.  Caller-owned host arrays
+   of n_views n_det entries.  Errors: INVALID_ARG. */
+int dgamp_ct_fan_ray_constants(const dgamp_ct_fan_geometry* g, int64_t* p0, int64_t* pstep, float* w,
+                               int32_t* col);
+
 /* Release the plan and its workspace (synchronises the device first).
    NULL is ignored. */
 void dgamp_ct_plan_destroy(dgamp_ct_plan_t plan);

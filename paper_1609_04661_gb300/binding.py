@@ -30,7 +30,7 @@ EXPORTS = (
     "dgamp_ct_cnn_create", "dgamp_ct_cnn_destroy", "dgamp_ct_cnn_num_params", "dgamp_ct_cnn_set_params",
     "dgamp_ct_cnn_get_params", "dgamp_ct_cnn_denoise", "dgamp_ct_cnn_denoise_jvp", "dgamp_ct_cnn_gradients", "dgamp_ct_cnn_train_step",
     "dgamp_ct_plan_set_cnn", "dgamp_ct_solve_trace", "dgamp_ct_solve_batched", "dgamp_ct_schedule_lpt",
-    "dgamp_ct_plan_fan",
+    "dgamp_ct_plan_fan", "dgamp_ct_fan_ray_constants",
 )
 
 
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_plan": (C.c_int, [C.POINTER(Geometry), C.POINTER(Options), C.POINTER(vp)]),
         "dgamp_ct_plan_destroy": (None, [vp]),
         "dgamp_ct_plan_fan": (C.c_int, [C.POINTER(FanGeometry), C.POINTER(Options), C.POINTER(vp)]),
+        "dgamp_ct_fan_ray_constants": (C.c_int, [C.POINTER(FanGeometry), vp, vp, vp, vp]),
         "dgamp_ct_set_options": (C.c_int, [vp, C.POINTER(Options)]),
         "dgamp_ct_plan_info": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i32)]),
         "dgamp_ct_project": (C.c_int, [vp, vp, vp, C.c_int, vp]),

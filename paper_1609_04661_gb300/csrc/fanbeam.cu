@@ -281,3 +281,27 @@ int fan_setup(dgamp_ct_plan_s* pl, const std::vector<double>& ang, double src_di
 }
 
 }  // namespace dgct
+
+using namespace dgct;
+
+extern "C" int dgamp_ct_fan_ray_constants(const dgamp_ct_fan_geometry* g, int64_t* p0, int64_t* pstep, float* w,
+                                          int32_t* col) {
+    if (!g || !p0 || !pstep || !w || !col) return DGAMP_CT_ERR_INVALID_ARG;
+    const dgamp_ct_geometry& b = g->base;
+    if (b.n < 2 || b.n_views < 1 || b.n_det < 2 || !(g->det_spacing > 0) || !std::isfinite(g->src_dist) ||
+        !std::isfinite(g->det_dist))
+        return DGAMP_CT_ERR_INVALID_ARG;
+    std::vector<double> ang(b.n_views);
+    for (int k = 0; k < b.n_views; ++k)
+        ang[k] = b.angles ? b.angles[k] : (double)k * (2.0 * 3.14159265358979323846 / b.n_views);
+    std::vector<FanRay> rays;
+    std::vector<FanView> views;
+    fan_constants(b.n, b.n_det, ang, g->src_dist, g->det_dist, g->det_spacing, rays, views);
+    for (size_t i = 0; i < rays.size(); ++i) {
+        p0[i] = rays[i].P0;
+        pstep[i] = rays[i].PSTEP;
+        w[i] = rays[i].w;
+        col[i] = rays[i].col;
+    }
+    return DGAMP_CT_OK;
+}
