@@ -173,12 +173,12 @@ def backproject(s: np.ndarray, geom: FanGeometry) -> np.ndarray:
     return _pre.v_inverse(back_project(s, geom), geom)
 
 
-def frobenius_sq(geom: FanGeometry) -> float:
+def frobenius_sq(geom: FanGeometry, views=None) -> float:
     """||Phi~||_F^2 = sum over rays of ||V^-1 a_i||^2, one filtered ray image
-    at a time."""
+    at a time (over the rays of the given views only, when views is set)."""
     S, v = geom.rays()
     tot = 0.0
-    for k in range(geom.n_views):
+    for k in (range(geom.n_views) if views is None else views):
         idx, wts = ray_taps(geom.n, S[k], v[k])
         for d in range(geom.n_det):
             a = np.bincount(idx[:, d].reshape(-1), weights=wts[:, d].reshape(-1), minlength=geom.N)

@@ -114,3 +114,20 @@ def test_geometry_must_enclose_the_image():
     with pytest.raises(ValueError):
         fanbeam.FanGeometry(64, 10, 96, 40.0, 92.0, 1.95)
     assert precond.image_pad(fanbeam.FanGeometry(64, 10, 96, 112.0, 92.0, 1.95)) == 128
+
+
+def test_stored_fan_frobenius_is_the_oracles():
+    """tests/golden/fan_frobenius.txt (written by make_fan_frobenius.py from
+    the oracle alone): the small workload's entry is recomputed here."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "fan_frobenius.txt")
+    vals = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            name, v = line.split()
+            vals[name] = float(v)
+    assert set(vals) == {"fan64_v30", "fan512_v102"}
+    n, nv, nd, _ne, _rm, _rect, _I0, _it, sd, dd, ds = synth.FAN_CASES["fan64_v30"]
+    g = fanbeam.FanGeometry(n, nv, nd, sd, dd, ds)
+    assert vals["fan64_v30"] == pytest.approx(fanbeam.frobenius_sq(g), rel=1e-12)
+    assert vals["fan512_v102"] > 0
