@@ -101,3 +101,32 @@ def test_fan_solve_matches_oracle(dg):
     assert st["iters_done"] == T
     assert rel(host(mu), ref) < 1e-3
     assert list(prof)[:5] == ["vinv_stage_project", "output_step", "backproject", "vinv_update", "probe_input"]
+
+
+def _golden_frobenius(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "golden",
+                        "fan_frobenius.txt")
+    for line in open(path):
+        if line.startswith(name + " "):
+            return float(line.split()[1])
+    raise KeyError(name)
+
+
+def test_fan_full_size_matches_oracle(dg):
+    """fan512_v102 at its own size: ||Phi~||_F^2 against the stored oracle
+    value, and two damped iterations against the oracle (which uses that
+    stored value)."""
+    from oracle import gamp
+    c = synth.make_case("fan512_v102")
+    f = c["fan"]
+    g = fanbeam.FanGeometry(c["n"], c["n_views"], c["n_det"], f["src_dist"], f["det_dist"], f["det_spacing"])
+    frob2 = _golden_frobenius("fan512_v102")
+    kw = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
+    T = 2
+    ref = gamp.ct_solve(c["y"], c["I0"], g, T, gamp.Options(**kw), frob2=frob2)
+    with plan(dg, c["n"], c["n_views"], c["n_det"], f["src_dist"], f["det_dist"], f["det_spacing"], None,
+              **kw) as pl:
+        assert pl.frob_sq == pytest.approx(frob2, rel=1e-5)
+        mu = host(pl.solve(torch.as_tensor(c["y"]).cuda(), c["I0"], T))
+    assert rel(mu, ref) < 1e-3
