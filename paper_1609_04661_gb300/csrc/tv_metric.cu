@@ -24,8 +24,11 @@
 // the last difference in each direction zero, so duals on the last column
 // (x part) and last row (y part) stay zero and div p needs no special case.
 //
-// Launch sequence for K = k_tv >= 1 (4K + 1 launches; image index in
-// blockIdx.y, nimg = 2 for D(r) and D(r + eps b)):
+// The gain max(rho, f0) is real and even, so the filter maps real images to
+// real images: the two images of the MC pair (D(r) and D(r + eps b)) travel
+// as the real and imaginary parts of one complex image through the three
+// FFT passes, which halves their work (a single image has a zero imaginary
+// part).  Launch sequence for K = k_tv >= 1 (4K + 1 launches):
 //   0                      dual step from p = 0 with x_0 = r
 //   4s-3, 4s-2, 4s-1       x_s = r + lambda Q div p_s     (s = 1 .. K)
 //                          (rows: div p and row FFTs; columns: FFT, gain,
@@ -35,7 +38,7 @@
 //                          staged copies, the divergence and tau_x.
 // Buffers (no allocation of their own): the duals use the first 2 N float2
 // of the l2 prox's dual buffer ws.p and x(p) its second half as floats; the
-// row spectra of image i use ws.fft2d + i n m (ws.fft2d holds m^2 >= 2 n m).
+// row spectra use the first n m entries of ws.fft2d (m x m).
 #include <cmath>
 
 #include "fft_device.cuh"
@@ -52,41 +55,50 @@ static float tvm_theta(const dgamp_ct_plan_s* pl) {
     return (float)(1.0 / (8.0 * qmax));
 }
 
-// Rows iy < n of image blockIdx.y: d = div p on the row, zero-padded to m,
-// forward FFT -> C[image][iy][0..m).
+// div p at (iy, i) of one image's duals (zero duals on the last column and row).
+__device__ __forceinline__ float tvm_div(const float2* __restrict__ prow, int iy, int i, int n) {
+    const float2 pc = prow[i];
+    float d = pc.x + pc.y;
+    if (i > 0) d -= prow[i - 1].x;
+    if (iy > 0) d -= prow[i - n].y;     // p_y of the row above
+    return d;
+}
+
+// Row iy < n: div p of image 0 (real part) and image 1 (imaginary part, or
+// zero when nimg = 1), zero-padded to m, forward FFT -> C[iy][0..m).
 __global__ void __launch_bounds__(512)
-k_tvm_rows_fwd(const float2* __restrict__ p, int n, int m, const float2* __restrict__ tw,
+k_tvm_rows_fwd(const float2* __restrict__ p, int nimg, int n, int m, const float2* __restrict__ tw,
                float2* __restrict__ C) {
     extern __shared__ float2 smem[];
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
-    const int iy = blockIdx.x, im = blockIdx.y;
-    const float2* prow = p + (size_t)im * n * n + (size_t)iy * n;
+    const int iy = blockIdx.x;
+    const size_t N = (size_t)n * n;
+    const float2* prow0 = p + (size_t)iy * n;
+    const float2* prow1 = prow0 + N;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        float d = 0.f;
+        float d0 = 0.f, d1 = 0.f;
         if (i < n) {
-            const float2 pc = prow[i];
-            d = pc.x + pc.y;
-            if (i > 0) d -= prow[i - 1].x;
-            if (iy > 0) d -= prow[i - n].y;     // p_y of the row above
+            d0 = tvm_div(prow0, iy, i, n);
+            if (nimg == 2) d1 = tvm_div(prow1, iy, i, n);
         }
-        a[fpad(i)] = make_float2(d, 0.f);
+        a[fpad(i)] = make_float2(d0, d1);
     }
     __syncthreads();
     const float2* r = fft_stockham(a, b, m, tw, -1.f);
-    float2* crow = C + (size_t)im * n * m + (size_t)iy * m;
+    float2* crow = C + (size_t)iy * m;
     for (int i = threadIdx.x; i < m; i += blockDim.x) crow[i] = r[fpad(i)];
 }
 
-// Column kx of image blockIdx.y: forward FFT over the rows (rows >= n are
-// zero), times max(rho, f0), inverse FFT; rows < n are stored back.
+// Column kx: forward FFT over the rows (rows >= n are zero), times
+// max(rho, f0), inverse FFT; rows < n are stored back.
 __global__ void __launch_bounds__(512)
 k_tvm_cols(float2* __restrict__ C, int n, int m, const float2* __restrict__ tw, float f0) {
     extern __shared__ float2 smem[];
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
     const int kx = blockIdx.x;
-    float2* Ci = C + (size_t)blockIdx.y * n * m;
+    float2* Ci = C;
     for (int i = threadIdx.x; i < m; i += blockDim.x)
         a[fpad(i)] = i < n ? Ci[(size_t)i * m + kx] : make_float2(0.f, 0.f);
     __syncthreads();
@@ -104,23 +116,27 @@ k_tvm_cols(float2* __restrict__ C, int n, int m, const float2* __restrict__ tw, 
     for (int i = threadIdx.x; i < n; i += blockDim.x) Ci[(size_t)i * m + kx] = r[fpad(i)];
 }
 
-// Row iy of image blockIdx.y: inverse FFT; X = r + lambda Re(.) / m^2 on the
-// first n columns.
+// Row iy: inverse FFT; on the first n columns X_0 = r_0 + lambda Re(.) / m^2
+// and (nimg = 2) X_1 = r_1 + lambda Im(.) / m^2.
 __global__ void __launch_bounds__(512)
-k_tvm_rows_inv(const float2* __restrict__ C, int n, int m, const float2* __restrict__ tw,
+k_tvm_rows_inv(const float2* __restrict__ C, int nimg, int n, int m, const float2* __restrict__ tw,
                const float* __restrict__ rimg, float* __restrict__ X, const DevScalars* S, float c_tv,
                int from_scalars, float lambda_arg) {
     extern __shared__ float2 smem[];
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
-    const int iy = blockIdx.x, im = blockIdx.y;
-    const float2* crow = C + (size_t)im * n * m + (size_t)iy * m;
+    const int iy = blockIdx.x;
+    const float2* crow = C + (size_t)iy * m;
     for (int i = threadIdx.x; i < m; i += blockDim.x) a[fpad(i)] = crow[i];
     __syncthreads();
     const float2* r = fft_stockham(a, b, m, tw, 1.f);
     const float sc = solve_lambda(S, c_tv, from_scalars, lambda_arg) / ((float)m * (float)m);
-    const size_t row = (size_t)im * n * n + (size_t)iy * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) X[row + i] = fmaf(sc, r[fpad(i)].x, rimg[row + i]);
+    const size_t N = (size_t)n * n, row = (size_t)iy * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float2 v = r[fpad(i)];
+        X[row + i] = fmaf(sc, v.x, rimg[row + i]);
+        if (nimg == 2) X[N + row + i] = fmaf(sc, v.y, rimg[N + row + i]);
+    }
 }
 
 // One dual step on image blockIdx.y, one pixel per thread:
@@ -154,7 +170,7 @@ int launch_tvm_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doub
                      float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st) {
     const int n = pl->n, m = pl->m2, K = pl->opt.k_tv;
     const size_t N = (size_t)pl->N;
-    if (nimg < 1 || nimg > 2 || K < 1 || i < 0 || i > 4 * K || (size_t)nimg * n * m > (size_t)m * m)
+    if (nimg < 1 || nimg > 2 || K < 1 || i < 0 || i > 4 * K || (size_t)n * m > (size_t)m * m)
         return DGAMP_CT_ERR_INVALID_ARG;
     float2* p = pl->ws.p;                                        // [nimg][n][n] float2
     float* X = reinterpret_cast<float*>(pl->ws.p + 2 * N);       // [nimg][n][n] float
@@ -171,14 +187,12 @@ int launch_tvm_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doub
     const size_t sm = (size_t)2 * fft_buf_len(m) * sizeof(float2);
     const int thr = tvm_threads(m);
     if (phase == 0)
-        k_tvm_rows_fwd<<<dim3((unsigned)n, (unsigned)nimg), thr, sm, st>>>(p, n, m, pl->ws.tw2, pl->ws.fft2d);
+        k_tvm_rows_fwd<<<n, thr, sm, st>>>(p, nimg, n, m, pl->ws.tw2, pl->ws.fft2d);
     else if (phase == 1)
-        k_tvm_cols<<<dim3((unsigned)m, (unsigned)nimg), thr, sm, st>>>(pl->ws.fft2d, n, m, pl->ws.tw2,
-                                                                       (float)(1.0 / (2.0 * pl->P)));
+        k_tvm_cols<<<m, thr, sm, st>>>(pl->ws.fft2d, n, m, pl->ws.tw2, (float)(1.0 / (2.0 * pl->P)));
     else
-        k_tvm_rows_inv<<<dim3((unsigned)n, (unsigned)nimg), thr, sm, st>>>(pl->ws.fft2d, n, m, pl->ws.tw2,
-                                                                           pl->ws.r, X, pl->ws.S, c_tv,
-                                                                           from_scalars, lam);
+        k_tvm_rows_inv<<<n, thr, sm, st>>>(pl->ws.fft2d, nimg, n, m, pl->ws.tw2, pl->ws.r, X, pl->ws.S, c_tv,
+                                           from_scalars, lam);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
