@@ -93,7 +93,9 @@ __device__ __forceinline__ float fan_bin(const FanView& V, float x, float y) {
 __device__ __forceinline__ void fan_candidates(const FanView& V, float x1, float y1, float x2, float y2,
                                                int nd, int& lo, int& hi) {
     const float b1 = fan_bin(V, x1, y1), b2 = fan_bin(V, x2, y2);
-    const float bl = fmaxf(fminf(b1, b2), -2.f), bh = fminf(fmaxf(b1, b2), (float)nd + 1.f);
+    // both ends clamped to [-2, nd + 1] before the conversion to int
+    const float bl = fminf(fmaxf(fminf(b1, b2), -2.f), (float)nd + 1.f);
+    const float bh = fmaxf(fminf(fmaxf(b1, b2), (float)nd + 1.f), -2.f);
     lo = max(0, (int)floorf(bl) - 1);
     hi = min(nd - 1, (int)ceilf(bh) + 1);
 }
