@@ -131,3 +131,18 @@ def test_stored_fan_frobenius_is_the_oracles():
     g = fanbeam.FanGeometry(n, nv, nd, sd, dd, ds)
     assert vals["fan64_v30"] == pytest.approx(fanbeam.frobenius_sq(g), rel=1e-12)
     assert vals["fan512_v102"] > 0
+
+
+def test_synthetic_fan_lines_pass_through_source_and_bin():
+    """synth.fan_lines (the synthetic counts' geometry, written apart from the
+    oracle): every line (theta', u') contains the source and its bin's point
+    on the detector, as the oracle's rays do."""
+    ang = np.array([0.0, 0.7, 2.0, 3.9, 5.5])
+    sd, dd, du, nd = 90.0, 70.0, 1.7, 23
+    thp, up = synth.fan_lines(ang, nd, sd, dd, du)
+    g = fanbeam.FanGeometry(40, len(ang), nd, sd, dd, du, angles=tuple(ang))
+    S, v = g.rays()
+    T = S + v
+    for P in (S, T):
+        resid = P[..., 0] * np.cos(thp) + P[..., 1] * np.sin(thp) - up
+        assert np.max(np.abs(resid)) < 1e-9
