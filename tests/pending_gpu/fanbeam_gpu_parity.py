@@ -130,3 +130,21 @@ def test_fan_full_size_matches_oracle(dg):
         assert pl.frob_sq == pytest.approx(frob2, rel=1e-5)
         mu = host(pl.solve(torch.as_tensor(c["y"]).cuda(), c["I0"], T))
     assert rel(mu, ref) < 1e-3
+
+
+def test_fan_full_size_psnr_follows_oracle(dg):
+    """fan512_v102, 10 and 30 damped iterations: the GPU solve's PSNR against
+    the oracle's stored curve (tests/golden/fan_psnr.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "golden", "fan_psnr.txt")
+    curve = [float(v) for v in [ln for ln in open(path) if not ln.startswith("#")][0].split()]
+    c = synth.make_case("fan512_v102")
+    f = c["fan"]
+    kw = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
+    with plan(dg, c["n"], c["n_views"], c["n_det"], f["src_dist"], f["det_dist"], f["det_spacing"], None,
+              **kw) as pl:
+        y = torch.as_tensor(c["y"]).cuda()
+        for T in (10, 30):
+            mu = host(pl.solve(y, c["I0"], T))
+            psnr = 10 * np.log10(c["mu"].max() ** 2 / np.mean((mu - c["mu"]) ** 2))
+            assert abs(psnr - curve[T - 1]) < 0.05
