@@ -107,3 +107,20 @@ def test_metric_option_is_validated(dg):
         with pytest.raises(dg.DgampError):
             pl.set_options(tv_metric=2)
         pl.set_options(tv_metric=1)
+
+
+def test_metric_full_size_psnr_follows_oracle(dg):
+    """The 512 x 512 / 64-view headline slice, damped, with the metric prox:
+    the GPU solve's PSNR after 3 and 6 iterations (6 is the curve's peak)
+    against the oracle's stored curve (tests/golden/metric_psnr.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "golden", "metric_psnr.txt")
+    curve = [float(v) for v in [ln for ln in open(path) if not ln.startswith("#")][0].split()]
+    c = synth.make_case("ellipse512_v64")
+    kw = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5, tv_metric=1)
+    with dg.Plan(c["n"], c["n_views"], c["n_det"], **kw) as pl:
+        y = torch.as_tensor(c["y"]).cuda()
+        for T in (3, 6):
+            mu = host(pl.solve(y, c["I0"], T))
+            psnr = 10 * np.log10(c["mu"].max() ** 2 / np.mean((mu - c["mu"]) ** 2))
+            assert abs(psnr - curve[T - 1]) < 0.05
