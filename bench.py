@@ -486,6 +486,32 @@ def _run_oracle_subprocess(iters: int, warm: int, seed: int = 1000):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def _run_oracle_all_cores(iters: int, warm: int):
+    """The same oracle sample on every host core at once, one single-threaded
+    process per core on its own slice (seeds 1000 + k): the host's aggregate
+    iterations/s when it solves independent slices in parallel."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    procs = []
+    for k in range(cores):
+        code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+                f"print(json.dumps(bench._oracle_sample({iters}, {warm}, {1000 + k})))")
+        procs.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                      text=True, env=env))
+    rates = []
+    for pr in procs:
+        out, err = pr.communicate(timeout=1800)
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        d = json.loads(out.strip().splitlines()[-1])
+        rates.append(len(d) / sum(d))
+    return {"value": sum(rates), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{iters} timed iterations (after {warm}) of the {WORKLOAD} solve on each of {cores} slices "
+                      f"(seeds 1000..{999 + cores}), one single-threaded FP64 numpy process per core, run at once; "
+                      f"value = the sum of their iterations/s; host CPU {_cpu_model()}"}
+
+
 def _cpu_model():
     try:
         with open("/proc/cpuinfo") as f:
@@ -512,7 +538,8 @@ def run_reference(args):
                              "sample": f"{args.steps} timed iterations (after {args.warmup}) of the "
                                        f"{WORKLOAD} solve, FP64 numpy oracle, one thread, "
                                        f"||Phi~||_F^2 precomputed; host CPU {_cpu_model()}"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cpu_all_cores": _run_oracle_all_cores(args.steps, args.warmup)}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -659,16 +686,17 @@ def run_gpu(args):
 
     line = None
     if rank == 0:
-        cpu = None
+        cpu = cpu_all = None
         if world == 1 and not args.no_cpu_baseline:
             per_iter = _run_oracle_subprocess(args.cpu_iters, 0)
             cpu = {"value": len(per_iter) / sum(per_iter), "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"{len(per_iter)} of {T} iterations of the {WORKLOAD} solve (seed 1000), FP64 "
                              f"numpy oracle on one host thread ({_cpu_model()}), ||Phi~||_F^2 precomputed"}
+            cpu_all = _run_oracle_all_cores(args.cpu_iters, 0)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": _config(world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "config": _config(world), "roofline": roof, "cpu_baseline": cpu, "cpu_all_cores": cpu_all, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": int(args.steps * plan.solve_launches(T)),
                 "psnr_db": psnr,
                 "a_plus_at_gbs": a_at_bytes / (a_at_ms * 1e-3) / 1e9,

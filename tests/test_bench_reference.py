@@ -27,3 +27,5 @@ def test_reference_arm_json_line():
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith(bench.WORKLOAD)
+    ac = d["cpu_all_cores"]
+    assert ac["kind"] == "oracle" and ac["cores"] == os.cpu_count() and ac["value"] > 0 and ac["unit"] == d["unit"]
