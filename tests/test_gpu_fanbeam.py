@@ -105,7 +105,7 @@ def test_fan_solve_matches_oracle(dg):
 
 def _golden_frobenius(name):
     import os
-    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "golden",
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
                         "fan_frobenius.txt")
     for line in open(path):
         if line.startswith(name + " "):
@@ -136,7 +136,7 @@ def test_fan_full_size_psnr_follows_oracle(dg):
     """fan512_v102, 10 and 30 damped iterations: the GPU solve's PSNR against
     the oracle's stored curve (tests/golden/fan_psnr.txt)."""
     import os
-    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "golden", "fan_psnr.txt")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fan_psnr.txt")
     curve = [float(v) for v in [ln for ln in open(path) if not ln.startswith("#")][0].split()]
     c = synth.make_case("fan512_v102")
     f = c["fan"]

@@ -114,7 +114,7 @@ def test_metric_full_size_psnr_follows_oracle(dg):
     the GPU solve's PSNR after 3 and 6 iterations (6 is the curve's peak)
     against the oracle's stored curve (tests/golden/metric_psnr.txt)."""
     import os
-    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "golden", "metric_psnr.txt")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "metric_psnr.txt")
     curve = [float(v) for v in [ln for ln in open(path) if not ln.startswith("#")][0].split()]
     c = synth.make_case("ellipse512_v64")
     kw = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5, tv_metric=1)
