@@ -47,9 +47,9 @@ WORKLOAD = "ellipse512_v64"
 TV = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the blocked-TV
-# launches of one iteration, from the ncu capture summarised in
-# profiles/tv_blocked_ellipse512_v64.md, valid only for the configuration
-# profiled there (steps per launch, region rows) and the current kernel.
+# launches of one iteration, from an ncu capture of this workload's headline
+# plan, valid only for the configuration captured (steps per launch, region
+# rows) and the kernel as it was then.
 TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 64, "bytes_per_iteration": 2119936 + 8433664 + 512}
 
 
@@ -271,7 +271,7 @@ def _gpu_ms(fn, reps: int):
 
 
 def _variants(dg, plan, case, counts, T):
-    """The paper's variants beyond the headline form (opt-in, --variants).
+    """The paper's variants beyond the headline form (skipped with --no-variants).
 
     tv_metric: the headline solve with the prox-TV in the (V^T V)^{-1} norm
     (Section 6.3), its PSNR curve and iterations/s.  fan512_v102: the
@@ -459,8 +459,10 @@ def _psnr(mu, ref):
 
 
 # ------------------------------------------------------- oracle (CPU) leg --
-def _oracle_sample(iters: int, warm: int, seed: int):
-    """Run the FP64 oracle on the workload; returns per-iteration seconds."""
+def _oracle_sample(iters: int, warm: int, seed: int, ready=None):
+    """Run the FP64 oracle on the workload; returns per-iteration seconds and
+    the monotonic-clock stamps of the first and last timed iteration's ends.
+    ready(), if given, is called after the set-up and before the solve."""
     import numpy as np  # noqa: F401
     import synth
     from oracle import gamp, precond
@@ -468,58 +470,99 @@ def _oracle_sample(iters: int, warm: int, seed: int):
     c = synth.make_case(WORKLOAD, seed=seed)
     g = Geometry(c["n"], c["n_views"], c["n_det"])
     frob2 = precond.frobenius_sq(g)
-    stamps = [time.perf_counter()]
+    if ready is not None:
+        ready()
+    stamps = [time.monotonic()]
     gamp.ct_solve(c["y"], c["I0"], g, warm + iters, gamp.Options(**TV), frob2=frob2,
-                  on_iter=lambda t, x: stamps.append(time.perf_counter()))
+                  on_iter=lambda t, x: stamps.append(time.monotonic()))
     d = [b - a for a, b in zip(stamps[:-1], stamps[1:])]
-    return d[warm:]
+    return {"per_iter": d[warm:], "t0": stamps[warm], "t1": stamps[-1]}
+
+
+_ORACLE_ENV = dict(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
 
 
 def _run_oracle_subprocess(iters: int, warm: int, seed: int = 1000):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+    env = dict(os.environ, **_ORACLE_ENV)
     code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
             f"print(json.dumps(bench._oracle_sample({iters}, {warm}, {seed})))")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    return json.loads(out.stdout.strip().splitlines()[-1])["per_iter"]
+
+
+def _host_cores():
+    """CPUs this process may run on (its affinity mask), not the machine's count."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 def _run_oracle_all_cores(iters: int, warm: int):
     """The same oracle sample on every host core at once, one single-threaded
     process per core on its own slice (seeds 1000 + k): the host's aggregate
-    iterations/s when it solves independent slices in parallel."""
-    cores = os.cpu_count() or 1
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    procs = []
-    for k in range(cores):
-        code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
-                f"print(json.dumps(bench._oracle_sample({iters}, {warm}, {1000 + k})))")
-        procs.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
-                                      text=True, env=env))
-    rates = []
+    iterations/s when it solves independent slices in parallel.  Every child
+    finishes its set-up, reports ready and waits for one shared start signal,
+    so the timed loops overlap; the rate is all timed iterations over the span
+    from the first timed start to the last timed end."""
+    cores = _host_cores()
+    env = dict(os.environ, **_ORACLE_ENV)
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"go = lambda: (print('READY', flush=True), sys.stdin.readline()); "
+            f"print(json.dumps(bench._oracle_sample({iters}, {warm}, 1000 + int(sys.argv[1]), ready=go)))")
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(k)], stdin=subprocess.PIPE, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env) for k in range(cores)]
+    for pr in procs:                                   # every child has finished its set-up
+        line = pr.stdout.readline()
+        if line.strip() != "READY":
+            err = pr.stderr.read()
+            for q in procs:
+                q.kill()
+            raise RuntimeError(f"oracle child failed before its timed loop: {line!r} {err[-2000:]}")
+    for pr in procs:                                   # one start signal for all
+        pr.stdin.write("go\n")
+        pr.stdin.flush()
+    results = []
     for pr in procs:
         out, err = pr.communicate(timeout=1800)
         if pr.returncode != 0:
             raise RuntimeError(err[-2000:])
-        d = json.loads(out.strip().splitlines()[-1])
-        rates.append(len(d) / sum(d))
-    return {"value": sum(rates), "unit": UNIT, "cores": cores, "kind": "oracle",
+        results.append(json.loads(out.strip().splitlines()[-1]))
+    total = sum(len(r["per_iter"]) for r in results)
+    span = max(r["t1"] for r in results) - min(r["t0"] for r in results)
+    return {"value": total / span, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{iters} timed iterations (after {warm}) of the {WORKLOAD} solve on each of {cores} slices "
-                      f"(seeds 1000..{999 + cores}), one single-threaded FP64 numpy process per core, run at once; "
-                      f"value = the sum of their iterations/s; host CPU {_cpu_model()}"}
+                      f"(seeds 1000..{999 + cores}), one single-threaded FP64 numpy process per core, set-up done "
+                      f"before one shared start signal; value = all timed iterations / the span from the first "
+                      f"timed start to the last timed end; host CPU {_cpu_model()}"}
+
+
+# Arm CPU part numbers (MIDR implementer 0x41) of the server cores this may run on
+_ARM_PARTS = {0xd0c: "Arm Neoverse N1", 0xd40: "Arm Neoverse V1", 0xd49: "Arm Neoverse N2",
+              0xd4f: "Arm Neoverse V2"}
 
 
 def _cpu_model():
+    fields = {}
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.lower().startswith(("model name", "cpu part")):
-                    return line.split(":", 1)[1].strip()
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
     except Exception:
         pass
+    if "model name" in fields:
+        return fields["model name"]
+    part, impl = fields.get("cpu part"), fields.get("cpu implementer")
+    if part:
+        try:
+            name = _ARM_PARTS.get(int(part, 16)) if impl and int(impl, 16) == 0x41 else None
+        except ValueError:
+            name = None
+        return f"{name} ({impl}/{part})" if name else f"implementer {impl}, part {part}"
     return "unknown"
 
 
@@ -682,7 +725,7 @@ def run_gpu(args):
     batched_learned = None if (args.no_batched or args.no_learned) else _batched(dg, rank, world, dist, flush, 1,
                                                                                    learned=True)
     ablation = _ablation(plan, case, counts, T) if rank == 0 and not args.no_learned else None
-    variants = _variants(dg, plan, case, counts, T) if (args.variants and rank == 0) else None
+    variants = _variants(dg, plan, case, counts, T) if (not args.no_variants and rank == 0) else None
 
     line = None
     if rank == 0:
@@ -721,8 +764,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain section")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-batch section")
     ap.add_argument("--c5", action="store_true", help="add the 128-slice 1024x1024 BF16-storage workload (~1 min)")
-    ap.add_argument("--variants", action="store_true",
-                    help="add the (V^T V)^-1-norm prox-TV and the fan-beam workload")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the (V^T V)^-1-norm prox-TV and the fan-beam workload")
     ap.add_argument("--tuning", default="", help="pin the headline plan's tuning, e.g. bp_mode=1,tv_kb=10")
     args = ap.parse_args()
     if args.impl == "reference":
