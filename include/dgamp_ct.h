@@ -412,7 +412,11 @@ int dgamp_ct_cnn_train_step(dgamp_ct_cnn_t net, const float* d_r, const float* d
    measurements (1 <= M <= DGAMP_CT_NOALLOC_MAX_M; larger M returns
    DGAMP_CT_ERR_INVALID_ARG).  The first call on a device looks up the
    scratch's device address with the device current; make that first call
-   before any stream capture.  All calls share the one scratch array: calls
+   before any stream capture.  The address belongs to the device's current
+   context: after cudaDeviceReset, or when the primary context is released
+   and created again, the next call finds a new context id and looks the
+   address up again (so make that call outside a capture too).  All calls
+   share the one scratch array: calls
    that overlap on the GPU (other streams, other host threads) race and
    must be serialised by the caller. */
 #define DGAMP_CT_NOALLOC_MAX_M (1LL << 24)

@@ -9,6 +9,8 @@
 // partial sums of tau_s and the block-arrival counter -- in a file-scope
 // __device__ array of fixed size that every GPU loading the library holds
 // until the process exits.  The caller still passes every input and output.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -31,21 +33,64 @@ constexpr int kMaxDevices = 64;
 // cudaGetSymbolAddress on each device before use.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
+// The looked-up address is valid only for the context it was looked up in:
+// after cudaDeviceReset (or a release and re-creation of the primary
+// context) the module is loaded again and the array may move.  So each
+// device's entry is keyed by the driver's context id, which is never reused
+// within a process, and looked up again whenever the current context's id
+// differs.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
 
-// Device address of g_scratch on the current device, looked up once per device.
+struct Entry {
+    unsigned long long ctx_id;
+    void* addr;
+};
+
+std::mutex g_mu;
+Entry g_cache[kMaxDevices] = {};
+
+void* driver_entry(const char* name) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return p;
+}
+
+// Id of the calling thread's current context (0 if none or not available).
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        get_cur = reinterpret_cast<CtxGetCurrentFn>(driver_entry("cuCtxGetCurrent"));
+        get_id = reinterpret_cast<CtxGetIdFn>(driver_entry("cuCtxGetId"));
+    });
+    if (!get_cur || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_scratch in the current device's context.
 int scratch_address(void** out) {
     int dev = -1;
     DGCT_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return DGAMP_CT_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    unsigned long long id = current_ctx_id();
+    Entry& e = g_cache[dev];
+    if (id == 0 || e.addr == nullptr || e.ctx_id != id) {
         void* p = nullptr;
-        DGCT_CUDA(cudaGetSymbolAddress(&p, g_scratch));
-        g_addr[dev] = p;
+        DGCT_CUDA(cudaGetSymbolAddress(&p, g_scratch));   // also makes the primary context current
+        if (id == 0) id = current_ctx_id();
+        e.addr = p;
+        e.ctx_id = id;   // 0 (no id available): looked up again on every call
     }
-    *out = g_addr[dev];
+    *out = e.addr;
     return DGAMP_CT_OK;
 }
 

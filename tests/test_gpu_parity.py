@@ -232,15 +232,18 @@ def case64():
     return c, Geometry(c["n"], c["n_views"], c["n_det"])
 
 
-@pytest.mark.parametrize("use_graph,damp,trunc", [(1, 1.0, 0), (0, 1.0, 0), (1, 0.5, 0), (1, 1.0, 1)])
-def test_solve_matches_oracle_after_20_iterations(dg, case64, use_graph, damp, trunc):
+@pytest.mark.parametrize("use_graph,damp,trunc,onsager", [(1, 1.0, 0, 1), (0, 1.0, 0, 1), (1, 0.5, 0, 1),
+                                                            (1, 1.0, 1, 1), (1, 1.0, 0, 0), (1, 0.5, 0, 0)])
+def test_solve_matches_oracle_after_20_iterations(dg, case64, use_graph, damp, trunc, onsager):
+    """onsager = 0 is Section 7.1's form without the Onsager term (p = z)."""
     c, g = case64
     T = c["iters"]
     log = []
-    opts = gamp.Options(c_tv=3.0, k_tv=20, damp_x=damp, damp_s=damp, truncate_z=bool(trunc))
+    opts = gamp.Options(c_tv=3.0, k_tv=20, damp_x=damp, damp_s=damp, truncate_z=bool(trunc),
+                        onsager=bool(onsager))
     mu_ref, x_ref = gamp.ct_solve(c["y"], c["I0"], g, T, opts, return_x=True, log=log)
     with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, use_graph=use_graph, damp_x=damp, damp_s=damp,
-                 truncate_z=trunc) as pl:
+                 truncate_z=trunc, onsager=onsager) as pl:
         xo = torch.empty((g.n, g.n), device="cuda")
         mu, st = pl.solve(cu(c["y"]), c["I0"], T, with_stats=True, x_out=xo)
         mu, xo = host(mu), host(xo)
