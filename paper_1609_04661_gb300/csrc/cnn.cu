@@ -508,7 +508,8 @@ struct dgamp_ct_cnn_s {
     int cap_batch = 0;
     int sm_count = 0;           // persistent grid of the tensor-core convolutions
     unsigned* tc_err = nullptr; // set by a tensor-core convolution whose bounded wait timed out
-    uint64_t ws_gen = 0;        // bumped whenever the workspace is reallocated
+    unsigned long long stall_ns = 0;  // timeout test (dgamp_ct_cnn_test_timeout): 0 = off
+    uint64_t ws_gen = 0;        // bumped whenever the workspace is reallocated or captured launches change
 };
 
 static int kGroups = 32;
@@ -577,7 +578,7 @@ static int cnn_forward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int 
     DGCT_LAUNCH_CHECK();
     for (int l = 1; l <= L - 2; ++l)
         DGCT_TRY(launch_conv64_tc(0, act(l), c->wh, L - 2, l - 1, c->master + c->b_off[l], nullptr, act(l + 1), B, H,
-                                  W, c->sm_count, c->tc_err, st));
+                                  W, c->sm_count, c->tc_err, st, c->stall_ns));
     k_conv_last<<<conv_last_grid(B, H, W), 32 * kCLRows, 0, st>>>(act(L - 1), c->w16, c->master + c->b_off[L - 1], r, sig, B,
                                                                 H, W, c->f, d_out);
     DGCT_LAUNCH_CHECK();
@@ -616,7 +617,7 @@ static int cnn_backward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int
         k_reduce_rows<<<1, 64, 0, st>>>(c->partial, G, CH, c->grad + c->b_off[l]);
         DGCT_LAUNCH_CHECK();
         DGCT_TRY(launch_conv64_tc(1, gcur, c->wt, L - 2, l - 1, nullptr, act(l), gnext, B, H, W, c->sm_count,
-                                  c->tc_err, st));
+                                  c->tc_err, st, c->stall_ns));
         bf16* t = gcur;
         gcur = gnext;
         gnext = t;
@@ -669,9 +670,9 @@ static int jvp_passes(dgamp_ct_cnn_s* c, const float* r, const float* b, int H, 
     DGCT_LAUNCH_CHECK();
     for (int l = 1; l <= L - 2; ++l) {
         DGCT_TRY(launch_conv64_tc(0, prim(l), c->wh, L - 2, l - 1, c->master + c->b_off[l], nullptr, prim(l + 1), 1,
-                                  H, W, c->sm_count, c->tc_err, st));
+                                  H, W, c->sm_count, c->tc_err, st, c->stall_ns));
         DGCT_TRY(launch_conv64_tc(1, tang(l), c->wh, L - 2, l - 1, nullptr, prim(l + 1), tang(l + 1), 1, H, W,
-                                  c->sm_count, c->tc_err, st));
+                                  c->sm_count, c->tc_err, st, c->stall_ns));
     }
     k_conv_last<<<conv_last_grid(1, H, W), 32 * kCLRows, 0, st>>>(prim(L - 1), c->w16, c->master + c->b_off[L - 1], r,
                                                                 c->sig_buf, 1, H, W,
@@ -688,13 +689,24 @@ int cnn_launches_per_pair(const dgamp_ct_cnn_s* c) { return 1 + 2 * c->L; }
 uint64_t cnn_ws_generation(const dgamp_ct_cnn_s* c) { return c->ws_gen; }
 }  // namespace dgct
 
-// a tensor-core convolution whose bounded wait ran out sets c->tc_err
-static int cnn_check_timeout(dgamp_ct_cnn_s* c) {
+// a tensor-core convolution whose bounded wait ran out sets c->tc_err; read
+// (and cleared) once the network's work is complete
+namespace dgct {
+int cnn_take_timeout(dgamp_ct_cnn_s* c) {
     unsigned flag = 0;
     DGCT_CUDA(cudaMemcpy(&flag, c->tc_err, sizeof(flag), cudaMemcpyDeviceToHost));
     if (!flag) return DGAMP_CT_OK;
     DGCT_CUDA(cudaMemset(c->tc_err, 0, sizeof(flag)));
     return DGAMP_CT_ERR_TIMEOUT;
+}
+}  // namespace dgct
+static int cnn_check_timeout(dgamp_ct_cnn_s* c) { return cnn_take_timeout(c); }
+
+// finish a single-step call: wait for its work, then report a timed-out wait
+static int cnn_finish(dgamp_ct_cnn_s* c, int rc, cudaStream_t st) {
+    if (rc != DGAMP_CT_OK) return rc;
+    DGCT_CUDA(cudaStreamSynchronize(st));
+    return cnn_check_timeout(c);
 }
 
 static int upload_sigma(dgamp_ct_cnn_s* c, const float* h_sigma, int B, cudaStream_t st) {
@@ -815,7 +827,7 @@ int dgamp_ct_cnn_denoise(dgamp_ct_cnn_t c, const float* d_r, const float* h_sigm
     int rc = cnn_ensure_ws(c, npix, 2, batch);
     if (rc != DGAMP_CT_OK) return rc;
     if ((rc = upload_sigma(c, h_sigma, batch, st)) != DGAMP_CT_OK) return rc;
-    return cnn_forward(c, d_r, c->sig_buf, batch, H, W, d_out, 0, st);
+    return cnn_finish(c, cnn_forward(c, d_r, c->sig_buf, batch, H, W, d_out, 0, st), st);
 }
 
 int dgamp_ct_cnn_denoise_jvp(dgamp_ct_cnn_t c, const float* d_r, const float* d_b, float sigma, int32_t H,
@@ -826,7 +838,18 @@ int dgamp_ct_cnn_denoise_jvp(dgamp_ct_cnn_t c, const float* d_r, const float* d_
     int rc = cnn_ensure_ws(c, (int64_t)H * W, 4, 1);
     if (rc != DGAMP_CT_OK) return rc;
     if ((rc = upload_sigma(c, &sigma, 1, st)) != DGAMP_CT_OK) return rc;
-    return jvp_passes(c, d_r, d_b, H, W, d_out, d_jb, st);
+    return cnn_finish(c, jvp_passes(c, d_r, d_b, H, W, d_out, d_jb, st), st);
+}
+
+int dgamp_ct_cnn_test_timeout(dgamp_ct_cnn_t c, int32_t on) {
+    if (!c || (on != 0 && on != 1)) return DGAMP_CT_ERR_INVALID_ARG;
+    const unsigned long long ns = on ? 1000000ull : 0ull;   // 1 ms
+    if (ns != c->stall_ns) {
+        DGCT_CUDA(cudaDeviceSynchronize());   // no launch of this network in flight changes its behaviour
+        c->stall_ns = ns;
+        c->ws_gen += 1;                       // captured solve graphs hold the old launch arguments
+    }
+    return DGAMP_CT_OK;
 }
 
 int dgamp_ct_cnn_gradients(dgamp_ct_cnn_t c, const float* d_r, const float* d_x, const float* h_sigma, int32_t batch,

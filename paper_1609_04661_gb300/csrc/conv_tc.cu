@@ -104,14 +104,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for phase `parity` of the mbarrier; false on timeout.  The
-// clock is read only when the first try fails.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// Bounded wait for phase `parity` of the mbarrier; false once `bound_ns` has
+// passed.  The clock is read only when the first try fails.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          unsigned long long bound_ns = WAIT_NS) {
     if (mbar_try(mbar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         if (mbar_try(mbar, parity)) return true;
-        if (global_ns() - t0 > WAIT_NS) return false;
+        if (global_ns() - t0 > bound_ns) return false;
     }
 }
 
@@ -249,6 +250,10 @@ __device__ __forceinline__ int next_q(int Q, int s, int H) { return Q + ((s % H 
 __device__ __forceinline__ int acc_of(int k) { return 2 * (k & 1) + ((k >> 1) & 1); }
 
 // MODE 0: out = relu(bias + conv(in, Wk)); MODE 1: out = conv(in, Wk) * (mask > 0).
+// stall_ns > 0 is the timeout test: before any copy or MMA is issued, thread 0
+// waits at most stall_ns on an mbarrier that nothing arrives at, records the
+// timeout in *err and the CTA returns without computing (after freeing its
+// tensor memory), exactly as a wait that ran out in the loop reports it.
 // Wk = layer `layer` of a [layers][co][tap*64 + ci] BF16 array (map_w); the
 // input is [B][H][W][64] BF16 (map_in).  CTA k takes strips [k per, (k+1) per).
 // Warp-specialised, with no block barrier inside the loop:
@@ -267,14 +272,16 @@ template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
 k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_w, int layer,
             const float* __restrict__ bias, const bf16* __restrict__ mask, bf16* __restrict__ out, int B, int H,
-            int W, int per, unsigned* err) {
+            int W, int per, unsigned* err, unsigned long long stall_ns) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t row_full[RING];
     __shared__ __align__(8) uint64_t row_empty[RING];
     __shared__ __align__(8) uint64_t acc_full[4];
     __shared__ __align__(8) uint64_t acc_empty[4];
     __shared__ __align__(8) uint64_t w_bar;
+    __shared__ __align__(8) uint64_t never_bar;   // the timeout test's barrier: nothing arrives
     __shared__ uint32_t tmem_slot;
+    __shared__ int stalled;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t sB = (raw + 1023u) & ~1023u, sA = sB + B_BYTES;
@@ -299,6 +306,8 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
             mbar_init(smem_u32(&acc_empty[b]), EPI_THREADS);
         }
         mbar_init(smem_u32(&w_bar), 1);
+        mbar_init(smem_u32(&never_bar), 1);
+        stalled = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     fence_before();
@@ -306,7 +315,14 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
     fence_after();
     const uint32_t tmem = tmem_slot;
     bool ok = true;
-    if (warp == 0) {
+    if (stall_ns) {
+        if (tid == 0 && !mbar_wait(smem_u32(&never_bar), 0u, stall_ns)) stalled = 1;
+        __syncthreads();
+        ok = stalled == 0;
+    }
+    if (!ok) {
+        // timeout test: nothing was issued, so nothing is in flight
+    } else if (warp == 0) {
         if (lane == 0) {
             // ---- TMA producer ----
             mbar_expect_tx(smem_u32(&w_bar), B_BYTES);
@@ -383,7 +399,7 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
                            smem_u32(&acc_empty[a]));
         }
     }
-    if (!ok) atomicOr(err, 1u);
+    if (!ok && (!stall_ns || tid == 0)) atomicOr(err, 1u);
     fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -435,7 +451,8 @@ static int encode(CUtensorMap* map, cuuint32_t rank, const void* base, const cuu
 // in: [B][H][W][64] BF16; wk_all: [layers][64][576] BF16 (layer `layer` used);
 // out (mode 0: bias + ReLU, mode 1: times mask > 0) like in.
 int launch_conv64_tc(int mode, const void* in, const void* wk_all, int layers, int layer, const float* bias,
-                     const void* mask, void* out, int B, int H, int W, int grid_cap, unsigned* err, cudaStream_t st) {
+                     const void* mask, void* out, int B, int H, int W, int grid_cap, unsigned* err, cudaStream_t st,
+                     unsigned long long stall_ns) {
     const long long nstrips = (long long)B * H * ((W + tc::M - 1) / tc::M);
     if (nstrips <= 0) return DGAMP_CT_OK;
     if (layer < 0 || layer >= layers) return DGAMP_CT_ERR_INVALID_ARG;
@@ -459,10 +476,10 @@ int launch_conv64_tc(int mode, const void* in, const void* wk_all, int layers, i
     typedef __nv_bfloat16 bf16;
     if (mode == 0)
         tc::k_conv64_tc<0><<<grid, tc::THREADS, tc::SMEM, st>>>(map_in, map_w, layer, bias, (const bf16*)mask,
-                                                                (bf16*)out, B, H, W, per, err);
+                                                                (bf16*)out, B, H, W, per, err, stall_ns);
     else
         tc::k_conv64_tc<1><<<grid, tc::THREADS, tc::SMEM, st>>>(map_in, map_w, layer, bias, (const bf16*)mask,
-                                                                (bf16*)out, B, H, W, per, err);
+                                                                (bf16*)out, B, H, W, per, err, stall_ns);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
