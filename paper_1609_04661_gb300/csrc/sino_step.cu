@@ -17,8 +17,12 @@
 // order, and block 0 records D', tau_x, the iteration's log and the next t
 // (pending_tau_x).  This replaces three launches, two round trips of a
 // sinogram through L2 and two grid-wide reduction tails.
+#include <cooperative_groups.h>
+
 #include "fft_device.cuh"
 #include "output_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace dgct {
 
@@ -171,17 +175,291 @@ k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
+// ---------------------------------------------- cluster Toeplitz form ----
+// The same step with H as its Toeplitz product, (H z)[d] = sum_d' h[|d - d'|]
+// z[d'] (the FFT form's operator, fft.cu), spread over a cluster of kCtCL
+// CTAs per view instead of one block per pair of views: the FFT form's four
+// transforms are a serial chain that leaves most SMs idle, while the direct
+// products split freely over output bins.  CTA `rank` of the cluster of view
+// v owns bins [rank per, (rank + 1) per), per = ceil(n_det / kCtCL):
+//   1. it loads the whole row of A x and the kernel hx;
+//   2. kCtWarps warps split the d' range of z = H A x for its bins, each lane
+//      R consecutive bins with a sliding window of hx in registers (R odd:
+//      the lanes' window loads fall on distinct banks), partial sums added
+//      in a fixed order; meanwhile one more warp finishes tau_x (the
+//      previous iteration's divergence) and tau_p;
+//   3. the output step on its bins; s goes to global memory and, as stored,
+//      into the s row of every CTA of the cluster (distributed shared memory);
+//      the block's tau_s_i sum goes to rank 0;
+//   4. one cluster barrier; rank 0 stores the view's tau_s partial (a fixed
+//      order over the ranks); every CTA forms H s for its bins.
+// No CTA reads another's shared memory after the barrier, so there is no
+// second one.  The back-projection adds the n_views partials.
+constexpr int kCtCL = 8;
+constexpr int kCtWarps = 4;
+constexpr int kCtThreads = 32 * (kCtWarps + 1);
+constexpr int kCtPre = 2;              // s_prev and y prefetched per thread (covers 2 x 160 >= 224 bins)
+constexpr int kCtMaxR = 7;             // bins per lane at most: n_det <= kCtCL x 32 x 7 = 1792
+
+__host__ __device__ __forceinline__ int ct_hs_len(int nd, int R) { return 2 * nd + R + 1; }
+
+// acc[k] = sum over d' in [p0, p1) of hs[dl + k - d' + nd] z[d'] (hs = hx shifted by one)
+template <int R>
+__device__ __forceinline__ void ct_product(const float* __restrict__ z, const float* __restrict__ hs, int nd,
+                                           int dl, int p0, int p1, float (&acc)[R]) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) acc[k] = 0.f;
+    if (p0 >= p1) return;
+    int base = dl - p0 + nd;
+    float h[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) h[k] = hs[base + k];
+#pragma unroll 4
+    for (int dp = p0; dp < p1; ++dp) {
+        const float zv = z[dp];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = fmaf(h[k], zv, acc[k]);
+#pragma unroll
+        for (int k = R - 1; k > 0; --k) h[k] = h[k - 1];
+        --base;
+        h[0] = hs[base];
+    }
+}
+
+struct CtShared {
+    double sm[32];
+    double tsum[kCtCL];
+    float s_tp, s_inv, s_logI0;
+};
+
+// View v's cluster, this CTA's part; record: the slice's first CTA (it
+// records the previous iteration's tau_x and log, and resets max |r|).
+template <typename T, int R>
+__device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const float* __restrict__ y, T* s,
+                                              T* __restrict__ hsout, int nd, const float* __restrict__ hx,
+                                              long long M, int onsager, float damp_s, int truncate, DevScalars* S,
+                                              double* __restrict__ partial, const double* __restrict__ partial_div,
+                                              double N, double floor_rel, IterLog* log, int v, bool record,
+                                              float* smf, CtShared& shd) {
+    constexpr int OUT = 32 * R;
+    auto& sm = shd.sm;
+    auto& tsum = shd.tsum;
+    auto& s_tp = shd.s_tp;
+    auto& s_inv = shd.s_inv;
+    auto& s_logI0 = shd.s_logI0;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int per = (nd + kCtCL - 1) / kCtCL;
+    const int d_lo = min(nd, rank * per), d_hi = min(nd, d_lo + per), nown = d_hi - d_lo;
+    const int HL = ct_hs_len(nd, R);
+    float* zs = smf;            // [nd]  A x of the view
+    float* sf = zs + nd;        // [nd]  s of the view, filled by every CTA of the cluster
+    float* hs = sf + nd;        // [HL]  hs[i] = hx[i - 1], zero outside
+    float* red = hs + HL;       // [kCtWarps][OUT]
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const size_t row0 = (size_t)v * nd;
+    // this thread's bins of the output step: s_prev and y now, used after the first product
+    float pre_sp[kCtPre], pre_y[kCtPre];
+#pragma unroll
+    for (int j = 0; j < kCtPre; ++j) {
+        const int o = tid + j * kCtThreads;
+        pre_sp[j] = pre_y[j] = 0.f;
+        if (o < nown) {
+            pre_sp[j] = ldf(s + row0 + d_lo + o);
+            pre_y[j] = y[row0 + d_lo + o];
+        }
+    }
+    for (int i = tid; i < nd; i += kCtThreads) zs[i] = ldf(zraw + row0 + i);
+    for (int i = tid; i < HL; i += kCtThreads) {
+        const int m = i - 1;
+        hs[i] = (m >= 0 && m < 2 * nd - 1) ? hx[m] : 0.f;
+    }
+    __syncthreads();
+    const int len = (nd + kCtWarps - 1) / kCtWarps;
+    const int dl = d_lo + R * lane;
+    if (w < kCtWarps) {
+        // z = H A x for this CTA's bins, warp w's share of d'
+        float acc[R];
+        if (dl < d_hi) ct_product<R>(zs, hs, nd, dl, w * len, min(nd, w * len + len), acc);
+        else
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) red[w * OUT + R * lane + k] = acc[k];
+    } else {
+        // tau_x of the previous iteration (its divergence may still be in
+        // partial sums; every CTA adds them in the same order), then tau_p
+        const double tx = pending_tau_x(S, partial_div, N, floor_rel, log, record);
+        if (lane == 0) {
+            const double tp = S->frob2 * tx / (double)M;
+            s_tp = (float)tp;
+            s_inv = (float)(1.0 / tp);
+            s_logI0 = (float)S->logI0;
+            if (record) S->rmax_bits = 0u;   // refilled by the back-projection
+        }
+    }
+    __syncthreads();
+    // output step on this CTA's bins; s as stored into every CTA's s row
+    const float tau_p = s_tp, inv_tp = s_inv, logI0 = s_logI0;
+    double acc = 0.0;
+    unsigned capped = 0;
+#pragma unroll
+    for (int j = 0; j < kCtPre; ++j) {
+        const int o = tid + j * kCtThreads;
+        if (o < nown) {
+            float zi = 0.f;
+#pragma unroll
+            for (int k = 0; k < kCtWarps; ++k) zi += red[k * OUT + o];
+            float sv;
+            acc += (double)output_element(zi, pre_sp[j], pre_y[j], tau_p, inv_tp, logI0, onsager, damp_s, truncate,
+                                          capped, sv);
+            stf(s + row0 + d_lo + o, sv);
+            const float sq = as_stored(sv, s);
+#pragma unroll
+            for (int r = 0; r < kCtCL; ++r) *cluster.map_shared_rank(sf + d_lo + o, r) = sq;
+        }
+    }
+    capped = warp_sum(capped);
+    if (lane == 0 && capped) atomicAdd(&S->newton_capped, capped);
+    acc = block_sum(acc, sm);
+    if (tid == 0) *cluster.map_shared_rank(&tsum[rank], 0) = acc;
+    cluster.sync();             // every s of the view is in sf; tau_s sums are at rank 0
+    if (rank == 0 && tid == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int r = 0; r < kCtCL; ++r) t += tsum[r];
+        partial[v] = t;
+    }
+    // H s for this CTA's bins
+    if (w < kCtWarps) {
+        float a2[R];
+        if (dl < d_hi) ct_product<R>(sf, hs, nd, dl, w * len, min(nd, w * len + len), a2);
+        else
+#pragma unroll
+            for (int k = 0; k < R; ++k) a2[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k) red[w * OUT + R * lane + k] = a2[k];
+    }
+    __syncthreads();
+    for (int o = tid; o < nown; o += kCtThreads) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < kCtWarps; ++k) t += red[k * OUT + o];
+        stf(hsout + row0 + d_lo + o, t);
+    }
+}
+
+template <typename T, int R>
+__global__ void __cluster_dims__(kCtCL, 1, 1) __launch_bounds__(kCtThreads)
+k_sino_toeplitz(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __restrict__ hsout, int nd,
+                const float* __restrict__ hx, long long M, int onsager, float damp_s, int truncate, DevScalars* S,
+                double* __restrict__ partial, const double* __restrict__ partial_div, double N, double floor_rel,
+                IterLog* log) {
+    extern __shared__ float smf[];
+    __shared__ CtShared shd;
+    sino_ct_block<T, R>(zraw, y, s, hsout, nd, hx, M, onsager, damp_s, truncate, S, partial, partial_div, N, floor_rel,
+                        log, (int)blockIdx.x / kCtCL, blockIdx.x == 0, smf, shd);
+}
+
+// The sinogram step of every slice of a batch in one launch: cluster c
+// (kCtCL CTAs) -> (slice, view); the slices' bins may differ (shared memory
+// is sized for the largest, R chosen for it).
+template <typename T, int R>
+__global__ void __cluster_dims__(kCtCL, 1, 1) __launch_bounds__(kCtThreads)
+k_sino_toeplitz_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ map) {
+    extern __shared__ float smf[];
+    __shared__ CtShared shd;
+    const int c = (int)blockIdx.x / kCtCL;
+    const BatchSlice& B = sl[map[c]];
+    const int v = c - B.off[kPhView];
+    sino_ct_block<T, R>((const T*)B.zraw, B.y, (T*)B.s, (T*)B.hs, B.nd, B.hx, B.M, B.onsager, B.damp_s, B.truncate,
+                        B.S, B.partial, B.partial_div, (double)B.N, B.tau_x_floor, B.log, v, blockIdx.x == (unsigned)(B.off[kPhView] * kCtCL),
+                        smf, shd);
+}
+
+static int ct_lanes_r(int nd) {
+    const int per = (nd + kCtCL - 1) / kCtCL;
+    for (int R = 3; R <= kCtMaxR; R += 2)
+        if (32 * R >= per) return R;
+    return 0;
+}
+
+static int ct_smem(int nd, int R) { return (2 * nd + ct_hs_len(nd, R) + kCtWarps * 32 * R) * (int)sizeof(float); }
+
+int sino_ct_lanes(int nd) { return ct_lanes_r(nd); }
+int sino_ct_smem_bytes(int nd, int R) { return ct_smem(nd, R); }
+
+template <typename T>
+static int launch_ct_batch(const BatchExec& E, cudaStream_t st) {
+    const unsigned grid = (unsigned)(E.nblk[kPhView] * kCtCL);
+    const size_t sm = (size_t)E.ct_smem;
+    if (E.R == 3) {
+        DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz_batch<T, 3>, (int)sm));
+        k_sino_toeplitz_batch<T, 3><<<grid, kCtThreads, sm, st>>>(E.sl, E.map[kPhView]);
+    } else if (E.R == 5) {
+        DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz_batch<T, 5>, (int)sm));
+        k_sino_toeplitz_batch<T, 5><<<grid, kCtThreads, sm, st>>>(E.sl, E.map[kPhView]);
+    } else {
+        DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz_batch<T, 7>, (int)sm));
+        k_sino_toeplitz_batch<T, 7><<<grid, kCtThreads, sm, st>>>(E.sl, E.map[kPhView]);
+    }
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+int launch_sino_batch(const BatchExec& E, cudaStream_t st) {
+    return E.bf ? launch_ct_batch<bf16s>(E, st) : launch_ct_batch<float>(E, st);
+}
+
+bool sino_toeplitz_eligible(const dgamp_ct_plan_s* pl) {
+    return ct_lanes_r(pl->nd) > 0 && pl->nv <= pl->max_partials && ct_smem(pl->nd, ct_lanes_r(pl->nd)) <= 200 * 1024;
+}
+
+template <typename T>
+static int launch_ct(const dgamp_ct_plan_s* pl, cudaStream_t st, int R, const T* zraw, T* s, T* hs) {
+    const Workspace& w = pl->ws;
+    const unsigned grid = (unsigned)(pl->nv * kCtCL);
+    const size_t sm = (size_t)ct_smem(pl->nd, R);
+    const float damp_s = (float)pl->opt.damp_s;
+#define DGCT_CT_ARGS zraw, w.y, s, hs, pl->nd, w.hx, pl->M, pl->opt.onsager, damp_s, pl->opt.truncate_z, w.S, \
+                     w.partial, w.partial_div, (double)pl->N, pl->opt.tau_x_floor, w.log
+    if (R == 3)
+        k_sino_toeplitz<T, 3><<<grid, kCtThreads, sm, st>>>(DGCT_CT_ARGS);
+    else if (R == 5)
+        k_sino_toeplitz<T, 5><<<grid, kCtThreads, sm, st>>>(DGCT_CT_ARGS);
+    else
+        k_sino_toeplitz<T, 7><<<grid, kCtThreads, sm, st>>>(DGCT_CT_ARGS);
+#undef DGCT_CT_ARGS
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+template <typename T>
+static int ct_set_limits(int bytes) {
+    DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz<T, 3>, bytes));
+    DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz<T, 5>, bytes));
+    DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz<T, 7>, bytes));
+    return DGAMP_CT_OK;
+}
+
 static int sino_step_smem(int P) {
     return (2 * fft_buf_len(P) + fft_twiddle_count(P)) * (int)sizeof(float2);
 }
 
-int sino_step_partials(const dgamp_ct_plan_s* pl) { return (pl->nv + 1) / 2; }
+// FP64 tau_s partials the current form leaves in ws.partial: one per block
+// of the FFT form (two views each), one per view of the cluster form
+int sino_step_partials(const dgamp_ct_plan_s* pl) { return pl->sino_fused == 2 ? pl->nv : (pl->nv + 1) / 2; }
 
 bool sino_step_eligible(const dgamp_ct_plan_s* pl) {
     return pl->P <= kSinoMaxP && (pl->nv + 1) / 2 <= pl->max_partials;
 }
 
 int sino_step_set_smem_limit(const dgamp_ct_plan_s* pl) {
+    if (sino_toeplitz_eligible(pl)) {
+        const int bytes = ct_smem(pl->nd, ct_lanes_r(pl->nd));
+        DGCT_TRY(ct_set_limits<float>(bytes));
+        DGCT_TRY(ct_set_limits<bf16s>(bytes));
+    }
     if (!sino_step_eligible(pl)) return DGAMP_CT_OK;
     // set even at or below 48 KB: the static shared memory of the reduction
     // comes on top of the dynamic part
@@ -192,10 +470,17 @@ int sino_step_set_smem_limit(const dgamp_ct_plan_s* pl) {
 }
 
 // z = H zraw, the output step into s (s_prev in, damped s out), hs = H s;
-// bf = 1: the three sinograms in BF16 (counts stay FP32)
+// bf = 1: the three sinograms in BF16 (counts stay FP32).  The plan's
+// sino_fused picks the form: 1 the FFT form, 2 the cluster Toeplitz form.
 int launch_sino_step(const dgamp_ct_plan_s* pl, cudaStream_t st, int bf) {
-    if (!sino_step_eligible(pl)) return DGAMP_CT_ERR_INVALID_ARG;
     const Workspace& w = pl->ws;
+    if (pl->sino_fused == 2) {
+        if (!sino_toeplitz_eligible(pl)) return DGAMP_CT_ERR_INVALID_ARG;
+        const int R = ct_lanes_r(pl->nd);
+        if (bf) return launch_ct<bf16s>(pl, st, R, (const bf16s*)w.zraw, (bf16s*)w.s, (bf16s*)w.hs);
+        return launch_ct<float>(pl, st, R, w.zraw, w.s, w.hs);
+    }
+    if (!sino_step_eligible(pl)) return DGAMP_CT_ERR_INVALID_ARG;
     const int grid = (pl->nv + 1) / 2;
     const size_t sm = (size_t)sino_step_smem(pl->P);
     const float damp_s = (float)pl->opt.damp_s;
@@ -212,6 +497,49 @@ int launch_sino_step(const dgamp_ct_plan_s* pl, cudaStream_t st, int bf) {
                                                            pl->opt.tau_x_floor, w.log);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
+}
+
+// Plan-time choice of the fused form (sino_fused 1: FFT, 2: cluster Toeplitz)
+// by timing both on the plan's geometry; 0 when neither applies.  Runs on
+// zero counts and a zero sinogram (solve_begin resets every buffer and scalar
+// it touches).
+int sino_autotune(dgamp_ct_plan_s* pl) {
+    const bool fft = sino_step_eligible(pl), ct = sino_toeplitz_eligible(pl);
+    pl->sino_fused = fft ? 1 : (ct ? 2 : 0);
+    if (!(fft && ct)) return DGAMP_CT_OK;
+    const Workspace& w = pl->ws;
+    const size_t M = (size_t)pl->M;
+    DGCT_CUDA(cudaMemset(w.zraw, 0, M * sizeof(float)));
+    DGCT_CUDA(cudaMemset(w.y, 0, M * sizeof(float)));
+    DGCT_CUDA(cudaMemset(w.s, 0, M * sizeof(float)));
+    cudaEvent_t e0, e1;
+    DGCT_CUDA(cudaEventCreate(&e0));
+    DGCT_CUDA(cudaEventCreate(&e1));
+    float best = 0.f;
+    int pick = 1, rc = DGAMP_CT_OK;
+    for (int mode = 1; mode <= 2 && rc == DGAMP_CT_OK; ++mode) {
+        pl->sino_fused = mode;
+        for (int i = 0; i < 3 && rc == DGAMP_CT_OK; ++i) rc = launch_sino_step(pl, 0, 0);
+        if (rc != DGAMP_CT_OK) break;
+        cudaEventRecord(e0, 0);
+        for (int i = 0; i < 20 && rc == DGAMP_CT_OK; ++i) rc = launch_sino_step(pl, 0, 0);
+        cudaEventRecord(e1, 0);
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e);
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (mode == 1 || ms < best) {
+            best = ms;
+            pick = mode;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pl->sino_fused = pick;
+    return rc;
 }
 
 }  // namespace dgct

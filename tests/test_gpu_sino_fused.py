@@ -1,7 +1,11 @@
-"""The fused sinogram kernel (H A x, Poisson output step and H s in one
-launch per pair of views) against the FP64 oracle and against the
-three-kernel path, on geometries with an odd number of views (the last
-block holds one view), several FFT lengths and both storage types.
+"""The fused sinogram kernels (H A x, Poisson output step and H s in one
+launch) against the FP64 oracle and against the three-kernel path: the FFT
+form (sino_fused = 1, one block per pair of views) and the cluster Toeplitz
+form (sino_fused = 2, a cluster of 8 blocks per view, each a slice of the
+bins, s shared through distributed shared memory), on geometries with an odd
+number of views (the last FFT block holds one view), bin counts that leave
+some blocks of a cluster empty or ragged, several FFT lengths and both
+storage types.
 
 Tolerances: the FP32 solve keeps the 1e-3 relative bound of the other solve
 tests.  Fused and three-kernel solves run the same arithmetic, but the
@@ -57,15 +61,21 @@ def test_fused_solve_matches_oracle_and_unfused(dg, n, nv, nd, I0, trunc):
     kw = dict(c_tv=3.0, k_tv=20, damp_x=0.7, damp_s=0.7, truncate_z=trunc)
     ref = gamp.ct_solve(y, I0, g, T, gamp.Options(**kw))
     out = {}
-    for fused in (1, 0):
+    forms = (1, 2, 0) if nd <= 1792 else (1, 0)
+    for fused in forms:
         with dg.Plan(n, nv, nd, **kw) as pl:
-            assert pl.tuning()["sino_fused"] == 1          # the default where P allows it
+            assert pl.tuning()["sino_fused"] in (1, 2)      # the faster fused form, timed at plan time
             pl.set_tuning(sino_fused=fused, pj_seg=8, bp_mode=1)   # only the sinogram step differs
             mu, st = pl.solve(torch.as_tensor(y).cuda(), I0, T, with_stats=True)
             out[fused] = (mu.cpu().numpy(), st)
-    assert rel(out[1][0], ref) < 1e-3
-    assert rel(out[1][0], out[0][0]) < 1e-4
-    assert np.allclose(out[1][1]["tau_r"], out[0][1]["tau_r"], rtol=1e-4)
+    for fused in forms[:-1]:
+        assert rel(out[fused][0], ref) < 1e-3, fused
+        assert rel(out[fused][0], out[0][0]) < 1e-4, fused
+        assert np.allclose(out[fused][1]["tau_r"], out[0][1]["tau_r"], rtol=1e-4), fused
+    if nd > 1792:
+        with dg.Plan(n, nv, nd, **kw) as pl:
+            with pytest.raises(dg.DgampError):
+                pl.set_tuning(sino_fused=2)
 
 
 def test_fused_single_view_one_iteration(dg):
@@ -75,12 +85,13 @@ def test_fused_single_view_one_iteration(dg):
     y = counts(n, nv, nd, I0, 141)
     ref = gamp.ct_solve(y, I0, Geometry(n, nv, nd), 1, gamp.Options(c_tv=3.0, k_tv=20))
     out = {}
-    for fused in (1, 0):
+    for fused in (1, 2, 0):
         with dg.Plan(n, nv, nd, c_tv=3.0, k_tv=20) as pl:
             pl.set_tuning(sino_fused=fused, pj_seg=8, bp_mode=1)   # only the sinogram step differs
             out[fused] = pl.solve(torch.as_tensor(y).cuda(), I0, 1).cpu().numpy()
-    assert rel(out[1], ref) < 1e-3
-    assert rel(out[1], out[0]) < 1e-5
+    for fused in (1, 2):
+        assert rel(out[fused], ref) < 1e-3
+        assert rel(out[fused], out[0]) < 1e-5
 
 
 def test_fused_bf16_storage_matches_unfused(dg):
@@ -89,22 +100,43 @@ def test_fused_bf16_storage_matches_unfused(dg):
     g = Geometry(c["n"], c["n_views"], c["n_det"])
     ref = gamp.ct_solve(c["y"], c["I0"], g, 5, gamp.Options(c_tv=3.0, k_tv=20))
     out = {}
-    for fused in (1, 0):
+    for fused in (1, 2, 0):
         with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, storage=1) as pl:
             pl.set_tuning(sino_fused=fused, pj_seg=8, bp_mode=1)   # only the sinogram step differs
             out[fused] = pl.solve(y, c["I0"], 5).cpu().numpy()
-    # the fused kernel keeps z = H A x in FP32 shared memory; the three-kernel
-    # form stores it in BF16, so the two differ by about the BF16 error itself
-    assert rel(out[1], ref) < 1e-2
-    assert rel(out[0], ref) < 1e-2
+    # the fused kernels keep z = H A x in FP32 (registers or shared memory);
+    # the three-kernel form stores it in BF16, so they differ by about the
+    # BF16 error itself
+    for fused in (1, 2, 0):
+        assert rel(out[fused], ref) < 1e-2, fused
 
 
 def test_fused_flag_is_validated(dg):
     with dg.Plan(16, 3, 24) as pl:
         with pytest.raises(dg.DgampError):
-            pl.set_tuning(sino_fused=2)
+            pl.set_tuning(sino_fused=3)
+        pl.set_tuning(sino_fused=2)
+        assert pl.tuning()["sino_fused"] == 2
         pl.set_tuning(sino_fused=0)
         assert pl.tuning()["sino_fused"] == 0
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_cluster_form_at_full_size_matches_fft_form(dg, storage):
+    """The 512 x 512 / 64-view / 729-bin workload, 5 iterations: both fused
+    forms of the sinogram step give the same solve (FP32: to the 1e-4 the
+    fused-vs-three-kernel comparison allows; BF16 storage: to its 1e-2)."""
+    c = synth.make_case("ellipse512_v64")
+    y = torch.as_tensor(c["y"]).cuda()
+    out = {}
+    for fused in (1, 2):
+        with dg.Plan(c["n"], c["n_views"], c["n_det"], c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5,
+                     storage=storage) as pl:
+            pl.set_tuning(sino_fused=fused)
+            mu, st = pl.solve(y, c["I0"], 5, with_stats=True)
+            out[fused] = (mu.cpu().numpy(), st)
+    assert rel(out[2][0], out[1][0]) < (1e-4 if storage == 0 else 1e-2)
+    assert np.allclose(out[2][1]["tau_r"], out[1][1]["tau_r"], rtol=(1e-4 if storage == 0 else 1e-2))
 
 
 def test_large_plan_still_runs_after_a_smaller_plan_is_made(dg):
