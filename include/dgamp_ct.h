@@ -144,6 +144,7 @@ typedef struct {
 
 typedef struct dgamp_ct_plan_s* dgamp_ct_plan_t;
 typedef struct dgamp_ct_cnn_s* dgamp_ct_cnn_t;     /* learned denoiser, see dgamp_ct_cnn_create */
+typedef struct dgamp_ct_batch_s* dgamp_ct_batch_t; /* slices run phase by phase, see dgamp_ct_batch_create */
 
 /* Fill *opt with the defaults: TV, k_tv = 20, c_tv = 3, eps_rel = 1e-3,
    seed = 12345, slice_id = 0, onsager = 1, no damping, floor 1e-6, graph on. */
@@ -204,10 +205,13 @@ typedef struct {
     int32_t tv_kb;        /* Chambolle steps per blocked TV launch, 1..10 */
     int32_t tv_rows;      /* rows of the image region one TV block holds: 32, 64 or 128
                              (the region is 64 columns wide) */
-    int32_t sino_fused;   /* 1 = inside dgamp_ct_solve, H A x, the output step and H s run
-                             as one kernel per pair of views (FFT form of H; needs
-                             P <= 8192); 0 = three kernels, H in filter_mode's form.  The
-                             plan sets 1 where the geometry allows it; filter_mode alone
+    int32_t sino_fused;   /* inside dgamp_ct_solve, H A x, the output step and H s run as
+                             one kernel: 1 = one block per pair of views, H by FFT (needs
+                             P <= 8192); 2 = a cluster of 8 blocks per view, each a slice
+                             of the bins, H as its Toeplitz product and s shared through
+                             distributed shared memory (needs n_det <= 1792); 0 = three
+                             kernels, H in filter_mode's form.  The plan times the forms
+                             the geometry allows and keeps the faster; filter_mode alone
                              governs the single-step entry points */
     int32_t bp_mode;      /* A^T: 0 = pixel-driven gather (each pixel finds the <= 2 rays
                              of a view that tap it), 1 = ray-driven over 16 x 16 image
@@ -218,8 +222,8 @@ typedef struct {
 } dgamp_ct_tuning;
 
 /* get: writes the plan's choices.  set: fields < 0 keep the current choice;
-   out-of-range values return INVALID_ARG, sino_fused = 1 where the geometry
-   does not allow it UNSUPPORTED_GEOMETRY (nothing is changed then).  Setting
+   out-of-range values return INVALID_ARG, a sino_fused form the geometry
+   does not allow UNSUPPORTED_GEOMETRY (nothing is changed then).  Setting
    drops the captured graph. */
 int dgamp_ct_get_tuning(dgamp_ct_plan_t plan, dgamp_ct_tuning* out);
 int dgamp_ct_set_tuning(dgamp_ct_plan_t plan, const dgamp_ct_tuning* tuning);
@@ -283,7 +287,11 @@ int dgamp_ct_precond_image(dgamp_ct_plan_t plan, const float* d_in, float* d_out
    valued, >= 0).  d_x_out (nullable) receives the final x.  With stats !=
    NULL the call synchronises the stream and fills it; otherwise it only
    enqueues work.  Errors: INVALID_ARG (iters < 1, I0 <= 0 or not finite),
-   CUDA, NONFINITE (only with stats: a non-finite scalar appeared). */
+   CUDA, NONFINITE (only with stats: a non-finite scalar appeared), TIMEOUT
+   (only with stats, learned denoiser: a tensor-core convolution's bounded
+   wait ran out, so the image is not valid; without stats the network keeps
+   the flag and its next synchronous call -- a solve with stats or on host
+   buffers, a denoise, a gradient pass -- returns TIMEOUT). */
 int dgamp_ct_solve(dgamp_ct_plan_t plan, const float* d_counts, double I0,
                    int32_t iters, float* d_mu_out, float* d_x_out,
                    dgamp_ct_stats* stats, void* stream);
@@ -305,7 +313,8 @@ int dgamp_ct_solve_trace(dgamp_ct_plan_t plan, const float* d_counts, double I0,
                          float* d_mu_out, float* d_r_trace, double* h_tau_r, void* stream);
 
 /* dgamp_ct_solve on HOST buffers: copies h_counts to the device, solves and
-   copies mu back to h_mu_out; returns after the result is in h_mu_out. */
+   copies mu back to h_mu_out; returns after the result is in h_mu_out.
+   Errors as dgamp_ct_solve; TIMEOUT is reported with or without stats. */
 int dgamp_ct_solve_host(dgamp_ct_plan_t plan, const float* h_counts, double I0,
                         int32_t iters, float* h_mu_out, dgamp_ct_stats* stats,
                         void* stream);
@@ -325,10 +334,40 @@ int dgamp_ct_solve_host(dgamp_ct_plan_t plan, const float* h_counts, double I0,
    concurrently.  Errors: INVALID_ARG (n < 0, a NULL pointer, a repeated
    plan, two learned plans sharing a network, a plan of another device, a
    learned plan without a network, I0 <= 0 or not finite, iters < 1), CUDA,
-   NONFINITE (only with stats). */
+   NONFINITE and TIMEOUT (only with stats; the first error met in slice
+   order). */
 int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float* const* d_counts,
                            const double* I0, int32_t iters, float* const* d_mu_out,
                            dgamp_ct_stats* stats, void* stream);
+
+/* A batch that runs every phase of an iteration as ONE launch over all its
+   slices (the same slices as dgamp_ct_solve_batched: independent, any mix of
+   image sizes, view and bin counts and doses; Section 6 reconstructs one
+   slice per solve).  Each launch covers a work list of (slice, block)
+   items -- A x, the sinogram step (H A x, the output step and H s; a cluster
+   of 8 blocks per view), A^T with the update, the probe, and the prox-TV
+   launches (20 Chambolle steps: 2 launches) -- so one iteration of any
+   number of slices is 6 launches, captured once as a graph and replayed.
+   Slice i's result is bit-identical to dgamp_ct_solve on plans[i] with the
+   batch's implementation choices (dgamp_ct_tuning pj_seg = 16, bp_mode = 1,
+   sino_fused = 2, tv_kb = 10, tv_rows = 64); each plan's own tuning is not
+   used here.
+   create: n >= 1 distinct parallel-beam plans of the current device with the
+   prox-TV denoiser (denoiser = 0, tv_metric = 0, output_moments = 0), one
+   storage type and one k_tv (a multiple of 10), c_tv > 0, n_det <= 1792.
+   The batch refers to the plans' workspaces: they must outlive it, and a
+   plan must not be solved on its own while a batch solve using it runs.
+   Errors: INVALID_ARG, UNSUPPORTED_GEOMETRY, OOM, CUDA.  Synchronous. */
+int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, dgamp_ct_batch_t* out);
+void dgamp_ct_batch_destroy(dgamp_ct_batch_t batch);
+/* Solve every slice: slice i takes d_counts[i] ([n_views][n_det] float32 of
+   plans[i]) and I0[i], runs `iters` iterations and writes mu to d_mu_out[i]
+   ([n][n]).  Stream-ordered; with stats != NULL it synchronises and fills
+   stats[0..n-1] (errors as dgamp_ct_solve_batched). */
+int dgamp_ct_batch_solve(dgamp_ct_batch_t batch, const float* const* d_counts, const double* I0,
+                         int32_t iters, float* const* d_mu_out, dgamp_ct_stats* stats, void* stream);
+/* Kernels one dgamp_ct_batch_solve of `iters` iterations launches (for all slices together). */
+int64_t dgamp_ct_batch_launches(dgamp_ct_batch_t batch, int32_t iters);
 
 /* Host-only scheduler (no device work): assigns n jobs of the given work
    (>= 0) to `queues` queues, largest job first, each to the least-loaded
@@ -345,7 +384,7 @@ int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t plan, int32_t iters);
    kernels one at a time on `stream` with a CUDA event before and after each,
    `reps` times, and writes the mean duration (ms) of each kernel to h_ms
    (host array of `cap` doubles) in launch order: A x; H (z), output step,
-   H (s) -- one fused kernel when the tuning's sino_fused is 1; A^T + update,
+   H (s) -- one fused kernel when the tuning's sino_fused is 1 or 2; A^T + update,
    probe input, then the denoiser: the blocked TV launches (the last one
    final), or the learned network's pair of passes and its final step.
    *count receives the number of kernels.  The iterations run on the plan's
@@ -353,6 +392,16 @@ int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t plan, int32_t iters);
    Synchronous. */
 int dgamp_ct_profile_iteration(dgamp_ct_plan_t plan, int32_t reps, double* h_ms, int32_t cap,
                                int32_t* count, void* stream);
+
+/* Measured FP32 FMA throughput of the current GPU (the denominator of the
+   ALU rooflines of the issue-bound kernels; no counterpart in the paper):
+   every SM runs as many 256-thread blocks as fit, each thread 8 independent
+   FMA chains, `reps` timed launches after one warm-up, CUDA events on
+   `stream`.  *h_tflops receives TFLOP/s (an FMA counts as 2 FLOP) and, if
+   h_sms is not NULL, *h_sms the SM count.  Changes no clock or other GPU
+   setting.  Allocates a small device buffer for the duration of the call;
+   synchronous. */
+int dgamp_ct_measure_fp32_peak(int32_t reps, double* h_tflops, int32_t* h_sms, void* stream);
 
 /* ---------------------------------------------------------------------------
    Learned denoiser (Step 4 of Algorithm 1 with a trained network; the paper's
@@ -365,8 +414,12 @@ int dgamp_ct_profile_iteration(dgamp_ct_plan_t plan, int32_t reps, double* h_ms,
    then b_l[c_out]; the compute copies of the weights are rounded to BF16.
    Images: float32 [batch][H][W] device buffers.  h_sigma: host array of
    `batch` positive floats.  The network object owns its parameters, Adam
-   state and workspace (grown on demand).  Calls are stream-ordered except
-   where a host result is returned (then they synchronise the stream). */
+   state and workspace (grown on demand).  Every wait inside the tensor-core
+   convolution is bounded (2 s); a wait that runs out sets a flag in the
+   network instead of hanging.  denoise, denoise_jvp, gradients and
+   train_step synchronise the stream before they return and then report a
+   flag that was set as DGAMP_CT_ERR_TIMEOUT (clearing it); their outputs
+   are then not valid. */
 
 /* New network with He-initialised weights (std sqrt(2/(9 c_in)), last layer
    x0.1) from `seed`, zero biases.  3 <= layers <= 64.  Synchronous. */
@@ -395,6 +448,13 @@ int dgamp_ct_cnn_denoise_jvp(dgamp_ct_cnn_t net, const float* d_r, const float* 
 int dgamp_ct_cnn_gradients(dgamp_ct_cnn_t net, const float* d_r, const float* d_x, const float* h_sigma,
                            int32_t batch, int32_t H, int32_t W, double* h_loss, float* h_grad,
                            void* stream);
+/* Timeout test switch (on = 1 or 0).  While it is on, every tensor-core
+   convolution of this network first waits with a 1 ms limit on a barrier
+   that nothing arrives at, records the timeout and returns without issuing
+   any copy or tensor-core instruction, so the calls above return
+   DGAMP_CT_ERR_TIMEOUT and the context stays usable.  Synchronises the
+   device when the setting changes; solves re-capture their graph. */
+int dgamp_ct_cnn_test_timeout(dgamp_ct_cnn_t net, int32_t on);
 /* One Adam step (beta 0.9/0.999, eps 1e-8, learning rate lr) on that loss. */
 int dgamp_ct_cnn_train_step(dgamp_ct_cnn_t net, const float* d_r, const float* d_x, const float* h_sigma,
                             int32_t batch, int32_t H, int32_t W, float lr, double* h_loss, void* stream);

@@ -29,8 +29,9 @@ EXPORTS = (
     "dgamp_ct_output_step_noalloc", "dgamp_ct_get_tuning", "dgamp_ct_set_tuning",
     "dgamp_ct_cnn_create", "dgamp_ct_cnn_destroy", "dgamp_ct_cnn_num_params", "dgamp_ct_cnn_set_params",
     "dgamp_ct_cnn_get_params", "dgamp_ct_cnn_denoise", "dgamp_ct_cnn_denoise_jvp", "dgamp_ct_cnn_gradients", "dgamp_ct_cnn_train_step",
-    "dgamp_ct_plan_set_cnn", "dgamp_ct_solve_trace", "dgamp_ct_solve_batched", "dgamp_ct_schedule_lpt",
-    "dgamp_ct_plan_fan", "dgamp_ct_fan_ray_constants",
+    "dgamp_ct_cnn_test_timeout", "dgamp_ct_plan_set_cnn", "dgamp_ct_solve_trace", "dgamp_ct_solve_batched", "dgamp_ct_schedule_lpt",
+    "dgamp_ct_plan_fan", "dgamp_ct_fan_ray_constants", "dgamp_ct_measure_fp32_peak",
+    "dgamp_ct_batch_create", "dgamp_ct_batch_destroy", "dgamp_ct_batch_solve", "dgamp_ct_batch_launches",
 )
 
 
@@ -126,6 +127,12 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_cnn_gradients": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, C.POINTER(dbl), vp, vp]),
         "dgamp_ct_cnn_train_step": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, C.c_float, C.POINTER(dbl), vp]),
         "dgamp_ct_plan_set_cnn": (C.c_int, [vp, vp]),
+        "dgamp_ct_cnn_test_timeout": (C.c_int, [vp, i32]),
+        "dgamp_ct_measure_fp32_peak": (C.c_int, [i32, C.POINTER(dbl), C.POINTER(i32), vp]),
+        "dgamp_ct_batch_create": (C.c_int, [i32, vp, vp]),
+        "dgamp_ct_batch_destroy": (None, [vp]),
+        "dgamp_ct_batch_solve": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
+        "dgamp_ct_batch_launches": (i64, [vp, i32]),
         "dgamp_ct_solve_trace": (C.c_int, [vp, vp, dbl, i32, vp, vp, C.POINTER(dbl), vp]),
     }
     for name, (res, args) in sig.items():
@@ -165,6 +172,16 @@ def _ptr(t, n_expect=None, name="tensor"):
 def _stream():
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def measure_fp32_peak(reps: int = 5):
+    """Measured FP32 FMA throughput of the current GPU (dgamp_ct_measure_fp32_peak):
+    returns (TFLOP/s, SM count)."""
+    tf = C.c_double()
+    sms = C.c_int32()
+    _check(load().dgamp_ct_measure_fp32_peak(int(reps), C.byref(tf), C.byref(sms), _stream()),
+           "dgamp_ct_measure_fp32_peak")
+    return tf.value, sms.value
 
 
 def output_step_noalloc(z, y, s_prev, I0: float, tau_p: float, s_out, tau_s_out):
@@ -485,6 +502,12 @@ class CNN:
                "cnn_gradients")
         return loss.value, g
 
+    def test_timeout(self, on: bool):
+        """Timeout test switch (dgamp_ct_cnn_test_timeout): while on, every
+        tensor-core convolution of this network times out on purpose (a 1 ms
+        wait on a barrier nothing arrives at) and computes nothing."""
+        _check(self._lib.dgamp_ct_cnn_test_timeout(self._h, 1 if on else 0), "cnn_test_timeout")
+
     def train_step(self, r, x, sigma, lr: float):
         B, H, W = tuple(r.shape)
         s = self._sig(sigma, B)
@@ -533,6 +556,63 @@ def solve_batched(plans, counts, I0, iters: int, mu_out=None, with_stats: bool =
                              tau_x_floored=st[k].tau_x_floored)
         return mus, arrays
     return mus
+
+
+class Batch:
+    """A batch of slices run one launch per phase (dgamp_ct_batch_*): holds the
+    plans (which must stay open) and solves them together."""
+
+    def __init__(self, plans):
+        self._lib = load()
+        self.plans = list(plans)
+        n = len(self.plans)
+        P = (C.c_void_p * n)(*[p._h.value if isinstance(p._h, C.c_void_p) else p._h for p in self.plans])
+        h = C.c_void_p()
+        _check(self._lib.dgamp_ct_batch_create(n, P, C.byref(h)), "dgamp_ct_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dgamp_ct_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def launches(self, iters: int) -> int:
+        return int(self._lib.dgamp_ct_batch_launches(self._h, int(iters)))
+
+    def solve(self, counts, I0, iters: int, mu_out=None, with_stats: bool = False):
+        n = len(self.plans)
+        if len(counts) != n or len(I0) != n:
+            raise ValueError("counts and I0 must have one entry per slice")
+        mus = [p._img() for p in self.plans] if mu_out is None else list(mu_out)
+        Cn = (C.c_void_p * n)(*[_ptr(c, p.M, "counts").value for c, p in zip(counts, self.plans)])
+        Mu = (C.c_void_p * n)(*[_ptr(m, p.N, "mu_out").value for m, p in zip(mus, self.plans)])
+        i0 = np.ascontiguousarray(I0, dtype=np.float64)
+        st, arrays = None, None
+        if with_stats:
+            arrays = [{k: np.zeros(iters) for k in ("tau_x", "tau_p", "tau_s", "tau_r", "div")} for _ in range(n)]
+            st = (Stats * n)(*[Stats(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in ar.values()], 0, 0, 0)
+                               for ar in arrays])
+        rc = self._lib.dgamp_ct_batch_solve(self._h, Cn, i0.ctypes.data_as(C.c_void_p), int(iters), Mu,
+                                            st if st is not None else None, _stream())
+        _check(rc, "dgamp_ct_batch_solve")
+        if with_stats:
+            for k in range(n):
+                arrays[k].update(iters_done=st[k].iters_done, newton_capped=st[k].newton_capped,
+                                 tau_x_floored=st[k].tau_x_floored)
+            return mus, arrays
+        return mus
 
 
 def flatten_params(ws, bs) -> np.ndarray:

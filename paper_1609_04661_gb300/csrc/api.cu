@@ -208,7 +208,7 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     DGCT_TRY(filter_autotune(pl));
     DGCT_TRY(backproject_autotune(pl));
     DGCT_TRY(project_autotune(pl));
-    pl->sino_fused = sino_step_eligible(pl) ? 1 : 0;
+    DGCT_TRY(sino_autotune(pl));
     return DGAMP_CT_OK;
 }
 
@@ -509,11 +509,12 @@ int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, dgamp_ct_tuning* out) {
 }
 
 int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
-    if (!pl || !t || t->filter_mode > 1 || t->tv_kb > 10 || t->tv_kb == 0 || t->sino_fused > 1 || t->bp_mode > 1)
+    if (!pl || !t || t->filter_mode > 1 || t->tv_kb > 10 || t->tv_kb == 0 || t->sino_fused > 2 || t->bp_mode > 1)
         return DGAMP_CT_ERR_INVALID_ARG;
     if (t->pj_seg >= 0 && t->pj_seg != 8 && t->pj_seg != 16 && t->pj_seg != 32) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->tv_rows >= 0 && t->tv_rows != 32 && t->tv_rows != 64 && t->tv_rows != 128) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->sino_fused == 1 && !sino_step_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
+    if (t->sino_fused == 2 && !sino_toeplitz_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (t->filter_mode >= 0) pl->filter_mode = t->filter_mode;
     if (t->tv_kb > 0) pl->tv_kb = t->tv_kb;
     if (t->tv_rows > 0) pl->tv_rows = t->tv_rows;
@@ -767,6 +768,8 @@ int fill_stats(const dgamp_ct_plan_s* pl, int iters, dgamp_ct_stats* stats) {
     stats->iters_done = (int32_t)(hs.t - 1u);
     stats->newton_capped = (int32_t)hs.newton_capped;
     stats->tau_x_floored = (int32_t)hs.floored;
+    // a tensor-core convolution of the learned denoiser whose bounded wait ran out
+    if (pl->opt.denoiser == 1 && pl->cnn) DGCT_TRY(cnn_take_timeout(pl->cnn));
     if (hs.nonfinite) return DGAMP_CT_ERR_NONFINITE;
     return DGAMP_CT_OK;
 }
@@ -786,6 +789,7 @@ int dgamp_ct_solve_host(dgamp_ct_plan_t pl, const float* h_counts, double I0, in
     if (rc != DGAMP_CT_OK && rc != DGAMP_CT_ERR_NONFINITE) return rc;
     DGCT_CUDA(cudaMemcpyAsync(h_mu_out, pl->ws.r, N * sizeof(float), cudaMemcpyDeviceToHost, st));
     DGCT_CUDA(cudaStreamSynchronize(st));
+    if (!stats && pl->opt.denoiser == 1 && pl->cnn) DGCT_TRY(cnn_take_timeout(pl->cnn));
     return rc;
 }
 

@@ -81,6 +81,44 @@ struct FanView {
 // Per-iteration log record (what dgamp_ct_stats exposes).
 struct IterLog { double tau_x, tau_p, tau_s, tau_r, div, eps; };
 
+// One slice of a batch (dgamp_ct_batch_*): its geometry, the device
+// workspace of its plan, its options, the per-solve inputs and outputs, and
+// where its blocks start in each phase's grid.  A batch runs every phase of
+// an iteration as one launch over all slices; a block finds its slice in the
+// phase's block -> slice table and its own block index from the offsets.
+enum BatchPhase { kPhProj, kPhView, kPhBp, kPhProbe, kPhTv0, kPhTv1, kPhRow, kPhCol, kPhBegin, kPhases };
+struct BatchSlice {
+    int n, nv, nd, ldp, m2, P;
+    long long N, M;
+    void* XR;                  // staged image (FP32, or BF16 with storage = 1)
+    void* XC;
+    void* zraw;                // A x, s, H s (the storage type)
+    void* s;
+    void* hs;
+    float* x;
+    float* r;                  // r and r + eps b
+    float* b;
+    float* y;
+    float2* p;                 // TV duals, ping-pong
+    float2* fft2d;
+    double* partial;
+    double* partial_div;
+    DevScalars* S;
+    IterLog* log;
+    const ViewConst* vc;
+    const float* hx;
+    const float2* tw2;
+    float c_tv, eps_rel, damp_x, damp_s;
+    double tau_x_floor, frob2, tau_x0;
+    int onsager, truncate;
+    uint2 key;
+    unsigned slice_id;
+    const float* counts;       // per solve
+    float* mu_out;
+    double logI0;
+    int off[kPhases];          // first block of the slice in each phase's grid
+};
+
 struct Workspace {
     float* XR = nullptr;     // staged image, rows padded:  [n][ldp]
     float* XC = nullptr;     // staged transpose:            [n][ldp]
@@ -274,7 +312,9 @@ int launch_filter(const dgamp_ct_plan_s* pl, const float* in, float* out, cudaSt
 // lowering it: the limit belongs to the kernel in the whole context, and a
 // plan made earlier may launch it with more.
 int raise_smem_limit(const void* kernel, int bytes);
-bool sino_step_eligible(const dgamp_ct_plan_s* pl);
+bool sino_step_eligible(const dgamp_ct_plan_s* pl);      // the FFT form (sino_fused = 1) applies
+bool sino_toeplitz_eligible(const dgamp_ct_plan_s* pl);  // the cluster Toeplitz form (sino_fused = 2) applies
+int sino_autotune(dgamp_ct_plan_s* pl);
 int sino_step_set_smem_limit(const dgamp_ct_plan_s* pl);
 int launch_sino_step(const dgamp_ct_plan_s* pl, cudaStream_t st, int bf);
 int sino_step_partials(const dgamp_ct_plan_s* pl);   // FP64 partial sums of tau_s_i it leaves in ws.partial
@@ -320,6 +360,35 @@ int launch_fan_backproject(const dgamp_ct_plan_s* pl, const float* sino, float* 
 // x, staging, divergence and tau_x from D(r) and J_D(r) b (learned denoiser)
 int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_out, int solve_mode, int t_arg,
                          double* div_out, cudaStream_t st);
+// Batched execution (batch.cu): device descriptors and tables of a batch,
+// and the grid of each phase (blocks; clusters for kPhView)
+struct BatchExec {
+    BatchSlice* sl = nullptr;                    // device [ns]
+    uint16_t* map[kPhases] = {};                 // device: block -> slice
+    int nblk[kPhases] = {};
+    int ns = 0;
+    int bf = 0;                                  // BF16 storage
+    int R = 3;                                   // bins per lane of the cluster sinogram kernel
+    int ct_smem = 0;                             // its dynamic shared memory (largest slice)
+    int max_m2 = 0;                              // largest V^-1 FFT length
+};
+// joseph.cu (pj_seg 16, tile back-projection)
+constexpr int kBatchPjSeg = 16;
+constexpr int kBatchTvKb = 10;                   // Chambolle steps per batched TV launch
+int batch_grid_project(int nv, int nd);
+int batch_grid_backproject(int n);
+int launch_project_batch(const BatchExec& E, cudaStream_t st);
+int launch_backproject_batch(const BatchExec& E, cudaStream_t st);
+// sino_step.cu (cluster Toeplitz form)
+int sino_ct_lanes(int nd);                       // 0: n_det too large for the cluster form
+int sino_ct_smem_bytes(int nd, int R);
+int launch_sino_batch(const BatchExec& E, cudaStream_t st);
+// tv.cu (64-row regions, kBatchTvKb steps per launch; `launch` counts from 0)
+int batch_grid_tv(int n, int final_launch);
+int batch_grid_probe(long long N);
+int launch_probe_batch(const BatchExec& E, cudaStream_t st);
+int launch_tv_batch(const BatchExec& E, int launch, bool final_launch, cudaStream_t st);
+
 // cnn.cu
 int cnn_prepare_pair(dgamp_ct_cnn_s* c, int n);
 int cnn_denoise_jvp(dgamp_ct_cnn_s* c, const float* rb, const DevScalars* S, int n, float* out, int scaled,
@@ -327,8 +396,14 @@ int cnn_denoise_jvp(dgamp_ct_cnn_s* c, const float* rb, const DevScalars* S, int
 int cnn_launches_per_pair(const dgamp_ct_cnn_s* c);
 // conv_tc.cu: hidden 64 -> 64 layers on tcgen05 (mode 0: bias + ReLU, mode 1: masked linear)
 int conv64_tc_init();
+// stall_ns > 0: the timeout test (the kernel waits that long on a barrier nothing
+// arrives at, sets *err and computes nothing)
 int launch_conv64_tc(int mode, const void* in, const void* wk_all, int layers, int layer, const float* bias,
-                     const void* mask, void* out, int B, int H, int W, int grid_cap, unsigned* err, cudaStream_t st);
+                     const void* mask, void* out, int B, int H, int W, int grid_cap, unsigned* err, cudaStream_t st,
+                     unsigned long long stall_ns = 0);
+// after the network's work is complete: DGAMP_CT_ERR_TIMEOUT (and the flag cleared)
+// if a tensor-core convolution's bounded wait ran out since the last check
+int cnn_take_timeout(dgamp_ct_cnn_s* c);
 // changes whenever the network's workspace is reallocated (captured graphs hold its pointers)
 uint64_t cnn_ws_generation(const dgamp_ct_cnn_s* c);
 

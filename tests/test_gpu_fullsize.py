@@ -1,10 +1,12 @@
 """Parity at the full size the benchmark times: the 512 x 512 / 64-view /
 729-bin workload (I0 = 1e5, seed 1000) in the benchmark's configuration
-(prox-TV with c = 3 and 20 Chambolle steps, damping 0.5) and with the plan's
-own implementation choices -- the launch configuration bench.py runs: the
-fused sinogram kernel, the tuned TV launches and back-projection.  The
-oracle computes its own ||Phi~||_F^2 and runs the same 5 iterations in FP64;
-the bound is the 1e-3 of the small solve tests.
+(prox-TV with c = 3 and 20 Chambolle steps, damping eta_x = 0.2 and
+eta_s = 0.15) and with the plan's own implementation choices -- the launch
+configuration bench.py runs: the fused sinogram kernel the plan picks, the
+tuned TV launches and back-projection -- for all 30 iterations the benchmark
+runs.  Also 10 iterations with damping 0.5, where the iteration peaks and
+turns over.  The oracle computes its own ||Phi~||_F^2 and runs the same
+iterations in FP64; the bound is the 1e-3 of the small solve tests.
 """
 import numpy as np
 import pytest
@@ -35,18 +37,18 @@ def dg():
     return dg
 
 
-def test_benchmark_workload_against_oracle(dg):
+@pytest.mark.parametrize("damp_x,damp_s,T", [(0.2, 0.15, 30), (0.5, 0.5, 10)])
+def test_benchmark_workload_against_oracle(dg, damp_x, damp_s, T):
     c = synth.make_case("ellipse512_v64", seed=1000)
     g = Geometry(c["n"], c["n_views"], c["n_det"])
-    T = 5
-    kw = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
+    kw = dict(c_tv=3.0, k_tv=20, damp_x=damp_x, damp_s=damp_s)
     log = []
     mu_ref = gamp.ct_solve(c["y"], c["I0"], g, T, gamp.Options(**kw), log=log)
     with dg.Plan(g.n, g.n_views, g.n_det, **kw) as pl:
         tun = pl.tuning()
         mu, st = pl.solve(torch.as_tensor(c["y"]).cuda(), c["I0"], T, with_stats=True)
         mu = mu.cpu().numpy()
-    assert tun["sino_fused"] == 1
+    assert tun["sino_fused"] in (1, 2)
     assert st["iters_done"] == T and np.all(np.isfinite(mu))
     assert rel(mu, mu_ref) < 1e-3
     assert np.allclose(st["tau_r"], [lg.tau_r for lg in log], rtol=1e-3)
