@@ -118,3 +118,329 @@ int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float*
 }
 
 }  // extern "C"
+
+// ===================================================================== //
+// One launch per phase over all slices (dgamp_ct_batch_*).  The stream-pool
+// path above replays one graph per slice, about seven launches per slice and
+// iteration; a batch object instead runs each phase of an iteration as ONE
+// launch over a work list that covers every slice -- the projector, the
+// cluster sinogram step, the tile back-projection, the probe and the two TV
+// launches -- so an iteration of a 64-slice batch is 6 launches, captured
+// once as a graph.  Every block finds its slice in the phase's block ->
+// slice table and runs the same block body as the single-slice kernel, so a
+// slice's result is bit-identical to its own solve with the batch's
+// implementation choices (pj_seg 16, tile back-projection, the cluster
+// sinogram form, 10 TV steps per launch over 64-row regions).
+#include "fft_device.cuh"
+#include "output_device.cuh"
+
+namespace dgct {
+
+// Algorithm 1 initialisation of every slice: y = counts, x = 0, s_prev = 0,
+// the staged images of x = 0 (zeros, guards included) and the scalars.
+__global__ void __launch_bounds__(256) k_batch_begin(const BatchSlice* __restrict__ sl,
+                                                     const uint16_t* __restrict__ map) {
+    const BatchSlice& B = sl[map[blockIdx.x]];
+    const long long e = (long long)((int)blockIdx.x - B.off[kPhBegin]) * blockDim.x + threadIdx.x;
+    if (e < B.M) {
+        B.y[e] = B.counts[e];
+        reinterpret_cast<float*>(B.s)[e] = 0.f;   // zero bits: zero in either storage type
+    }
+    if (e < B.N) B.x[e] = 0.f;
+    if (e < (long long)B.n * B.ldp) {
+        reinterpret_cast<float*>(B.XR)[e] = 0.f;
+        reinterpret_cast<float*>(B.XC)[e] = 0.f;
+    }
+    if (e == 0) {
+        DevScalars s;
+        memset(&s, 0, sizeof(s));
+        s.tau_x = B.tau_x0;
+        s.frob2 = B.frob2;
+        s.logI0 = B.logI0;
+        s.t = 1u;
+        *B.S = s;
+    }
+}
+
+// After the last iteration: each slice's pending divergence (one warp per slice).
+__global__ void k_batch_finish(const BatchSlice* __restrict__ sl) {
+    const BatchSlice& B = sl[blockIdx.x];
+    pending_tau_x(B.S, B.partial_div, (double)B.N, B.tau_x_floor, B.log, true);
+    __syncwarp();
+    if (threadIdx.x == 0) B.S->div_pending = 0u;
+}
+
+// mu = V^-1 x of every slice, the three passes of the image filter (fft.cu):
+// rows of x -> spectrum rows, columns with the gain, inverse rows -> mu.
+__global__ void __launch_bounds__(512) k_batch_vinv_rows(const BatchSlice* __restrict__ sl,
+                                                         const uint16_t* __restrict__ map) {
+    extern __shared__ float2 smem[];
+    const BatchSlice& B = sl[map[blockIdx.x]];
+    const int iy = (int)blockIdx.x - B.off[kPhRow], n = B.n, m = B.m2;
+    float2* a = smem;
+    float2* b = smem + fft_buf_len(m);
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+        a[fpad(i)] = make_float2(i < n ? B.x[(size_t)iy * n + i] : 0.f, 0.f);
+    __syncthreads();
+    float2* r = fft_stockham(a, b, m, B.tw2, -1.f);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) B.fft2d[(size_t)iy * m + i] = r[fpad(i)];
+}
+
+__global__ void __launch_bounds__(512) k_batch_vinv_cols(const BatchSlice* __restrict__ sl,
+                                                         const uint16_t* __restrict__ map) {
+    extern __shared__ float2 smem[];
+    const BatchSlice& B = sl[map[blockIdx.x]];
+    const int kx = (int)blockIdx.x - B.off[kPhCol], n = B.n, m = B.m2;
+    float2* a = smem;
+    float2* b = smem + fft_buf_len(m);
+    float2* C = B.fft2d;
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+        a[fpad(i)] = i < n ? C[(size_t)i * m + kx] : make_float2(0.f, 0.f);
+    __syncthreads();
+    float2* r = fft_stockham(a, b, m, B.tw2, -1.f);
+    float2* o = (r == a) ? b : a;
+    const float f0 = 1.0f / (2.0f * (float)B.P);
+    const float fx = (float)(kx <= m / 2 ? kx : kx - m) / (float)m;
+    for (int ky = threadIdx.x; ky < m; ky += blockDim.x) {
+        const float fy = (float)(ky <= m / 2 ? ky : ky - m) / (float)m;
+        const float g = sqrtf(fmaxf(sqrtf(fx * fx + fy * fy), f0));
+        const float2 v = r[fpad(ky)];
+        r[fpad(ky)] = make_float2(v.x * g, v.y * g);
+    }
+    __syncthreads();
+    r = fft_stockham(r, o, m, B.tw2, 1.f);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) C[(size_t)i * m + kx] = r[fpad(i)];
+}
+
+__global__ void __launch_bounds__(512) k_batch_vinv_rows_inv(const BatchSlice* __restrict__ sl,
+                                                             const uint16_t* __restrict__ map) {
+    extern __shared__ float2 smem[];
+    const BatchSlice& B = sl[map[blockIdx.x]];
+    const int iy = (int)blockIdx.x - B.off[kPhRow], n = B.n, m = B.m2;
+    float2* a = smem;
+    float2* b = smem + fft_buf_len(m);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) a[fpad(i)] = B.fft2d[(size_t)iy * m + i];
+    __syncthreads();
+    float2* r = fft_stockham(a, b, m, B.tw2, 1.f);
+    const float sc = 1.0f / ((float)m * (float)m);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) B.mu_out[(size_t)iy * n + i] = r[fpad(i)].x * sc;
+}
+
+}  // namespace dgct
+
+struct dgamp_ct_batch_s {
+    int device = 0;
+    std::vector<dgamp_ct_plan_t> plans;
+    std::vector<BatchSlice> h;          // host copy of the descriptors
+    BatchExec E;
+    cudaGraphExec_t graph = nullptr;    // one iteration: 6 launches over all slices
+    int tv_launches = 0;
+};
+
+namespace dgct {
+
+static void batch_free(dgamp_ct_batch_s* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->E.sl) cudaFree(b->E.sl);
+    for (int p = 0; p < kPhases; ++p)
+        if (b->E.map[p]) cudaFree(b->E.map[p]);
+    b->graph = nullptr;
+    b->E = BatchExec{};
+}
+
+static int batch_vinv_threads(int m) { return m / 8 < 32 ? 32 : (m / 8 > 512 ? 512 : m / 8); }
+
+// One iteration of every slice: the six batched launches.
+static int batch_iteration(dgamp_ct_batch_s* b, cudaStream_t st) {
+    const BatchExec& E = b->E;
+    DGCT_TRY(launch_project_batch(E, st));                         // Step 1: A x
+    DGCT_TRY(launch_sino_batch(E, st));                            //         H A x, Step 2, H s
+    DGCT_TRY(launch_backproject_batch(E, st));                     // Step 3: r = x + tau_r A^T H s
+    DGCT_TRY(launch_probe_batch(E, st));                           // Step 4: r + eps b
+    for (int i = 0; i < b->tv_launches; ++i)                       //         D(r), D(r + eps b), x, D'
+        DGCT_TRY(launch_tv_batch(E, i, i == b->tv_launches - 1, st));
+    return DGAMP_CT_OK;
+}
+
+static int batch_graph(dgamp_ct_batch_s* b) {
+    if (b->graph) return DGAMP_CT_OK;
+    cudaStream_t cs;
+    DGCT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_fail(e);
+    }
+    const int rc = batch_iteration(b, cs);
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc != DGAMP_CT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return cuda_fail(e);
+    }
+    return DGAMP_CT_OK;
+}
+
+}  // namespace dgct
+
+extern "C" {
+
+int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, dgamp_ct_batch_t* out) {
+    if (!out || n < 1 || n > 65535 || !plans) return DGAMP_CT_ERR_INVALID_ARG;
+    *out = nullptr;
+    int device = 0;
+    DGCT_CUDA(cudaGetDevice(&device));
+    std::set<dgamp_ct_plan_t> seen;
+    const dgamp_ct_plan_s* p0 = plans[0];
+    if (!p0) return DGAMP_CT_ERR_INVALID_ARG;
+    int max_nd = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const dgamp_ct_plan_s* pl = plans[i];
+        if (!pl || !seen.insert(plans[i]).second || pl->device != device) return DGAMP_CT_ERR_INVALID_ARG;
+        const dgamp_ct_options& o = pl->opt;
+        // the batched kernels: parallel beam, prox-TV (l2), Laplace's output step,
+        // one storage type and one step count for all slices
+        if (pl->fan || o.denoiser != 0 || o.tv_metric || o.output_moments) return DGAMP_CT_ERR_INVALID_ARG;
+        if (o.storage != p0->opt.storage || o.k_tv != p0->opt.k_tv) return DGAMP_CT_ERR_INVALID_ARG;
+        if (o.k_tv < kBatchTvKb || o.k_tv % kBatchTvKb != 0 || !(o.c_tv > 0)) return DGAMP_CT_ERR_INVALID_ARG;
+        if (sino_ct_lanes(pl->nd) == 0 || pl->nv > pl->max_partials) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
+        max_nd = std::max(max_nd, pl->nd);
+    }
+    dgamp_ct_batch_s* b = new (std::nothrow) dgamp_ct_batch_s();
+    if (!b) return DGAMP_CT_ERR_OOM;
+    b->device = device;
+    b->plans.assign(plans, plans + n);
+    b->tv_launches = p0->opt.k_tv / kBatchTvKb;
+    BatchExec& E = b->E;
+    E.ns = n;
+    E.bf = p0->opt.storage;
+    E.R = sino_ct_lanes(max_nd);
+    // descriptors and the block -> slice tables, largest slices first in
+    // each grid (the work list order of the LPT scheduler)
+    std::vector<int64_t> work(n);
+    for (int32_t i = 0; i < n; ++i) work[i] = (int64_t)plans[i]->nv * plans[i]->nd * plans[i]->n;
+    std::vector<int32_t> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return work[a] > work[c]; });
+    b->h.resize(n);
+    std::vector<std::vector<uint16_t>> maps(kPhases);
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t i = order[k];
+        const dgamp_ct_plan_s* pl = plans[i];
+        const Workspace& w = pl->ws;
+        BatchSlice& d = b->h[i];
+        memset(&d, 0, sizeof(d));
+        d.n = pl->n; d.nv = pl->nv; d.nd = pl->nd; d.ldp = pl->ldp; d.m2 = pl->m2; d.P = pl->P;
+        d.N = pl->N; d.M = pl->M;
+        d.XR = w.XR; d.XC = w.XC; d.zraw = w.zraw; d.s = w.s; d.hs = w.hs;
+        d.x = w.x; d.r = w.r; d.b = w.b; d.y = w.y; d.p = w.p; d.fft2d = w.fft2d;
+        d.partial = w.partial; d.partial_div = w.partial_div; d.S = w.S; d.log = w.log;
+        d.vc = w.vc; d.hx = w.hx; d.tw2 = w.tw2;
+        d.c_tv = (float)pl->opt.c_tv; d.eps_rel = (float)pl->opt.eps_rel;
+        d.damp_x = (float)pl->opt.damp_x; d.damp_s = (float)pl->opt.damp_s;
+        d.tau_x_floor = pl->opt.tau_x_floor; d.frob2 = pl->frob2; d.tau_x0 = pl->opt.tau_x0;
+        d.onsager = pl->opt.onsager; d.truncate = pl->opt.truncate_z;
+        d.key = make_uint2((unsigned)(pl->opt.seed & 0xffffffffu), (unsigned)(pl->opt.seed >> 32));
+        d.slice_id = (unsigned)pl->opt.slice_id;
+        const long long begin_elems = std::max<long long>(std::max<long long>(pl->M, pl->N), (long long)pl->n * pl->ldp);
+        const int cnt[kPhases] = {batch_grid_project(pl->nv, pl->nd), pl->nv, batch_grid_backproject(pl->n),
+                                  batch_grid_probe(pl->N), batch_grid_tv(pl->n, 0), batch_grid_tv(pl->n, 1),
+                                  pl->n, pl->m2, (int)((begin_elems + 255) / 256)};
+        for (int ph = 0; ph < kPhases; ++ph) {
+            d.off[ph] = (int)maps[ph].size();
+            maps[ph].insert(maps[ph].end(), (size_t)cnt[ph], (uint16_t)i);
+        }
+        E.max_m2 = std::max(E.max_m2, pl->m2);
+    }
+    for (int ph = 0; ph < kPhases; ++ph) E.nblk[ph] = (int)maps[ph].size();
+    E.ct_smem = sino_ct_smem_bytes(max_nd, E.R);
+    int rc = DGAMP_CT_OK;
+    cudaError_t e = cudaMalloc((void**)&E.sl, (size_t)n * sizeof(BatchSlice));
+    for (int ph = 0; ph < kPhases && e == cudaSuccess; ++ph) {
+        e = cudaMalloc((void**)&E.map[ph], maps[ph].size() * sizeof(uint16_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(E.map[ph], maps[ph].data(), maps[ph].size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(E.sl, b->h.data(), (size_t)n * sizeof(BatchSlice), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? DGAMP_CT_ERR_OOM : cuda_fail(e);
+    if (rc == DGAMP_CT_OK) {
+        const int fsm = 2 * fft_buf_len(E.max_m2) * (int)sizeof(float2);
+        const int lim = fsm > 48 * 1024 ? fsm : 48 * 1024;
+        rc = raise_smem_limit((const void*)k_batch_vinv_rows, lim);
+        if (rc == DGAMP_CT_OK) rc = raise_smem_limit((const void*)k_batch_vinv_cols, lim);
+        if (rc == DGAMP_CT_OK) rc = raise_smem_limit((const void*)k_batch_vinv_rows_inv, lim);
+    }
+    if (rc == DGAMP_CT_OK) rc = batch_graph(b);
+    if (rc != DGAMP_CT_OK) {
+        cudaGetLastError();
+        batch_free(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return DGAMP_CT_OK;
+}
+
+void dgamp_ct_batch_destroy(dgamp_ct_batch_t b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    batch_free(b);
+    delete b;
+}
+
+int64_t dgamp_ct_batch_launches(dgamp_ct_batch_t b, int32_t iters) {
+    if (!b || iters < 0) return -1;
+    // the begin kernel, per iteration the projector, sinogram step,
+    // back-projection, probe and TV launches, then the finish and V^-1 (3)
+    return 1 + (int64_t)iters * (4 + b->tv_launches) + 4;
+}
+
+int dgamp_ct_batch_solve(dgamp_ct_batch_t b, const float* const* d_counts, const double* I0, int32_t iters,
+                         float* const* d_mu_out, dgamp_ct_stats* stats, void* stream) {
+    if (!b || !d_counts || !I0 || !d_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
+    if (iters < 1 || iters > kMaxIters) return DGAMP_CT_ERR_INVALID_ARG;
+    int device = 0;
+    DGCT_CUDA(cudaGetDevice(&device));
+    if (device != b->device) return DGAMP_CT_ERR_INVALID_ARG;
+    const int n = b->E.ns;
+    for (int i = 0; i < n; ++i) {
+        if (!d_counts[i] || !d_mu_out[i] || !(I0[i] > 0) || !std::isfinite(I0[i])) return DGAMP_CT_ERR_INVALID_ARG;
+        b->h[i].counts = d_counts[i];
+        b->h[i].mu_out = d_mu_out[i];
+        b->h[i].logI0 = std::log(I0[i]);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const BatchExec& E = b->E;
+    DGCT_CUDA(cudaMemcpyAsync(E.sl, b->h.data(), (size_t)n * sizeof(BatchSlice), cudaMemcpyHostToDevice, st));
+    k_batch_begin<<<E.nblk[kPhBegin], 256, 0, st>>>(E.sl, E.map[kPhBegin]);
+    DGCT_LAUNCH_CHECK();
+    for (int t = 0; t < iters; ++t) DGCT_CUDA(cudaGraphLaunch(b->graph, st));
+    k_batch_finish<<<n, 32, 0, st>>>(E.sl);
+    DGCT_LAUNCH_CHECK();
+    const int thr = batch_vinv_threads(E.max_m2);
+    const size_t fsm = (size_t)2 * fft_buf_len(E.max_m2) * sizeof(float2);
+    k_batch_vinv_rows<<<E.nblk[kPhRow], thr, fsm, st>>>(E.sl, E.map[kPhRow]);
+    DGCT_LAUNCH_CHECK();
+    k_batch_vinv_cols<<<E.nblk[kPhCol], thr, fsm, st>>>(E.sl, E.map[kPhCol]);
+    DGCT_LAUNCH_CHECK();
+    k_batch_vinv_rows_inv<<<E.nblk[kPhRow], thr, fsm, st>>>(E.sl, E.map[kPhRow]);
+    DGCT_LAUNCH_CHECK();
+    if (!stats) return DGAMP_CT_OK;
+    DGCT_CUDA(cudaStreamSynchronize(st));
+    int rc = DGAMP_CT_OK;
+    for (int i = 0; i < n; ++i) {
+        const int r = fill_stats(b->plans[i], iters, &stats[i]);
+        if (r != DGAMP_CT_OK && rc == DGAMP_CT_OK) rc = r;
+    }
+    return rc;
+}
+
+}  // extern "C"

@@ -67,14 +67,13 @@ int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t
 // hide more of that latency, up to the point where the segments get short.
 constexpr int kPjRays = 32;
 
+// The rays of ray group gx of view v (one block's work).
 template <typename T, int kPjSeg>
-__global__ void __launch_bounds__(kPjRays * kPjSeg)
-k_project(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int n, int nd,
-          const ViewConst* __restrict__ vcs, T* __restrict__ sino) {
-    __shared__ float red[kPjSeg][kPjRays];
-    const int v = blockIdx.y;
+__device__ __forceinline__ void project_block(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int n,
+                                              int nd, const ViewConst* __restrict__ vcs, T* __restrict__ sino,
+                                              int gx, int v, float (*red)[kPjRays]) {
     const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
-    const int d = blockIdx.x * kPjRays + lane;
+    const int d = gx * kPjRays + lane;
     const ViewConst c = vcs[v];
     float acc = 0.f;
     if (d < nd) {
@@ -106,6 +105,26 @@ k_project(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int n, in
         for (int k = 0; k < kPjSeg; ++k) t += red[k][lane];
         stf(sino + (size_t)v * nd + d, t * c.w);
     }
+}
+
+template <typename T, int kPjSeg>
+__global__ void __launch_bounds__(kPjRays * kPjSeg)
+k_project(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int n, int nd,
+          const ViewConst* __restrict__ vcs, T* __restrict__ sino) {
+    __shared__ float red[kPjSeg][kPjRays];
+    project_block<T, kPjSeg>(XR, XC, ldp, n, nd, vcs, sino, blockIdx.x, blockIdx.y, red);
+}
+
+// A x of every slice of a batch in one launch: block -> (slice, ray group, view).
+template <typename T, int kPjSeg>
+__global__ void __launch_bounds__(kPjRays * kPjSeg)
+k_project_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ map) {
+    __shared__ float red[kPjSeg][kPjRays];
+    const BatchSlice& B = sl[map[blockIdx.x]];
+    const int l = (int)blockIdx.x - B.off[kPhProj];
+    const int ngx = (B.nd + kPjRays - 1) / kPjRays;
+    project_block<T, kPjSeg>((const T*)B.XR, (const T*)B.XC, B.ldp, B.n, B.nd, B.vc, (T*)B.zraw, l % ngx, l / ngx,
+                             red);
 }
 
 template <int SEG>
@@ -141,14 +160,14 @@ constexpr int kBpViews = 256;
 // of a block into *s_tau_r.  nparts > 0: the fused sinogram kernel left
 // nparts FP64 partial sums of tau_s_i; every block adds them in the same
 // fixed order (lane-strided, then the warp's shuffle tree), forms
-// tau_s = sum / M and tau_r = N / (||Phi~||_F^2 tau_s) in FP64, and block 0
-// records tau_p, tau_s and tau_r in S for the kernels after it.
-// nparts == 0: tau_r is already in S.
+// tau_s = sum / M and tau_r = N / (||Phi~||_F^2 tau_s) in FP64, and the
+// slice's first block (`first`) records tau_p, tau_s and tau_r in S for the
+// kernels after it.  nparts == 0: tau_r is already in S.
 __device__ __forceinline__ void bp_tau_r(DevScalars* __restrict__ S, const double* __restrict__ partial,
-                                         int nparts, double M, double N, float* s_tau_r) {
+                                         int nparts, double M, double N, float* s_tau_r, bool first) {
     const int lane = threadIdx.x & 31;
     // the divergence partials of the previous TV step have been consumed
-    if (lane == 0 && blockIdx.x == 0 && blockIdx.y == 0) S->div_pending = 0u;
+    if (lane == 0 && first) S->div_pending = 0u;
     if (nparts == 0) {
         if (lane == 0) *s_tau_r = (float)S->tau_r;
         return;
@@ -159,7 +178,7 @@ __device__ __forceinline__ void bp_tau_r(DevScalars* __restrict__ S, const doubl
     if (lane == 0) {
         const double tau_s = a / M, tau_r = N / (S->frob2 * tau_s);
         *s_tau_r = (float)tau_r;
-        if (blockIdx.x == 0 && blockIdx.y == 0) {
+        if (first) {
             S->tau_p = S->frob2 * S->tau_x / M;
             S->tau_s = tau_s;
             S->tau_r = tau_r;
@@ -183,7 +202,7 @@ k_backproject(const T* __restrict__ sino, int nv, int nd, int n,
     const bool live = ix < n && iy < n;
     const float fx = (float)ix, fy = (float)iy, fx1 = fx + 1.f, fy1 = fy + 1.f;
     if (tid == 0) s_max = 0u;
-    if (update && tid < 32) bp_tau_r(S, partial, nparts, M, (double)n * n, &s_tau_r);
+    if (update && tid < 32) bp_tau_r(S, partial, nparts, M, (double)n * n, &s_tau_r, blockIdx.x == 0 && blockIdx.y == 0);
     float acc = 0.f;
     for (int v0 = 0; v0 < nv; v0 += kBpViews) {
         const int cnt = min(kBpViews, nv - v0);
@@ -294,21 +313,32 @@ __device__ __forceinline__ void bp_tile_view(const ViewConst& c, const T* __rest
     }
 }
 
+struct BtShared {
+    float accL[kBtWarps][kBtS * kBtLd], accR[kBtWarps][kBtS * kBtLd];
+    unsigned s_max;
+    float s_tau_r;
+};
+
+// Tile (bx, by) of the image; `first` marks the block that records the
+// scalars (bp_tau_r) -- block (0, 0) of the slice.
 template <typename T>
-__global__ void __launch_bounds__(kBtWarps * 32, 5)    // 48 registers: 5 blocks per SM, no spills
-k_backproject_tile(const T* __restrict__ sino, int nv, int nd, int n, const ViewConst* __restrict__ vcs,
-                   const float* __restrict__ x_in, float* __restrict__ out, int update,
-                   DevScalars* __restrict__ S, const double* __restrict__ partial, int nparts, double M) {
-    __shared__ float accL[kBtWarps][kBtS * kBtLd], accR[kBtWarps][kBtS * kBtLd];
-    __shared__ unsigned s_max;
-    __shared__ float s_tau_r;
+__device__ __forceinline__ void backproject_tile_block(const T* __restrict__ sino, int nv, int nd, int n,
+                                                       const ViewConst* __restrict__ vcs,
+                                                       const float* __restrict__ x_in, float* __restrict__ out,
+                                                       int update, DevScalars* __restrict__ S,
+                                                       const double* __restrict__ partial, int nparts, double M,
+                                                       int bx, int by, bool first, BtShared& sh) {
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-    const int tx0 = blockIdx.x * kBtS, ty0 = blockIdx.y * kBtS;
+    const int tx0 = bx * kBtS, ty0 = by * kBtS;
+    auto& accL = sh.accL;
+    auto& accR = sh.accR;
+    auto& s_max = sh.s_max;
+    auto& s_tau_r = sh.s_tau_r;
     float* AL = accL[wp];
     float* AR = accR[wp];
     for (int i = lane; i < kBtS * kBtLd; i += 32) AL[i] = AR[i] = 0.f;
     if (tid == 0) s_max = 0u;
-    if (update && wp == 0) bp_tau_r(S, partial, nparts, M, (double)n * n, &s_tau_r);
+    if (update && wp == 0) bp_tau_r(S, partial, nparts, M, (double)n * n, &s_tau_r, first);
     __syncwarp();
     for (int v = wp; v < nv; v += kBtWarps) {
         const ViewConst c = vcs[v];
@@ -341,6 +371,29 @@ k_backproject_tile(const T* __restrict__ sino, int nv, int nd, int n, const View
     if (tid == 0) atomicMax(&S->rmax_bits, s_max);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kBtWarps * 32, 5)    // 48 registers: 5 blocks per SM, no spills
+k_backproject_tile(const T* __restrict__ sino, int nv, int nd, int n, const ViewConst* __restrict__ vcs,
+                   const float* __restrict__ x_in, float* __restrict__ out, int update,
+                   DevScalars* __restrict__ S, const double* __restrict__ partial, int nparts, double M) {
+    __shared__ BtShared sh;
+    backproject_tile_block<T>(sino, nv, nd, n, vcs, x_in, out, update, S, partial, nparts, M, blockIdx.x, blockIdx.y,
+                              blockIdx.x == 0 && blockIdx.y == 0, sh);
+}
+
+// r = x + tau_r A^T H s of every slice of a batch in one launch (after the
+// cluster sinogram kernel: one tau_s partial per view).
+template <typename T>
+__global__ void __launch_bounds__(kBtWarps * 32, 5)
+k_backproject_tile_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ map) {
+    __shared__ BtShared sh;
+    const BatchSlice& B = sl[map[blockIdx.x]];
+    const int l = (int)blockIdx.x - B.off[kPhBp];
+    const int ntx = (B.n + kBtS - 1) / kBtS;
+    backproject_tile_block<T>((const T*)B.hs, B.nv, B.nd, B.n, B.vc, B.x, B.r, 1, B.S, B.partial, B.nv, (double)B.M,
+                              l % ntx, l / ntx, l == 0, sh);
+}
+
 // nparts > 0 (update = 1 after the fused sinogram kernel): tau_r from the
 // nparts partial sums in ws.partial; else from S.
 int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
@@ -366,6 +419,28 @@ int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float
     else
         k_backproject<float><<<grd, blk, 0, st>>>(sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in, out, update,
                                                   pl->ws.S, part, nparts, M);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// ------------------------------------------------------------ batches ----
+int batch_grid_project(int nv, int nd) { return ((nd + kPjRays - 1) / kPjRays) * nv; }
+int batch_grid_backproject(int n) { return ((n + kBtS - 1) / kBtS) * ((n + kBtS - 1) / kBtS); }
+
+int launch_project_batch(const BatchExec& E, cudaStream_t st) {
+    if (E.bf)
+        k_project_batch<bf16s, kBatchPjSeg><<<E.nblk[kPhProj], kPjRays * kBatchPjSeg, 0, st>>>(E.sl, E.map[kPhProj]);
+    else
+        k_project_batch<float, kBatchPjSeg><<<E.nblk[kPhProj], kPjRays * kBatchPjSeg, 0, st>>>(E.sl, E.map[kPhProj]);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+int launch_backproject_batch(const BatchExec& E, cudaStream_t st) {
+    if (E.bf)
+        k_backproject_tile_batch<bf16s><<<E.nblk[kPhBp], kBtWarps * 32, 0, st>>>(E.sl, E.map[kPhBp]);
+    else
+        k_backproject_tile_batch<float><<<E.nblk[kPhBp], kBtWarps * 32, 0, st>>>(E.sl, E.map[kPhBp]);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }

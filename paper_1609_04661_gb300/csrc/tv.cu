@@ -34,15 +34,14 @@ constexpr float kTau = 0.125f;
 // --------------------------------------------------------- probe input ----
 // r2 = r + eps b, eps = eps_rel max(max|r|, 1e-6), or r2 = b itself
 // (write_b = 1: the direction of a forward-mode divergence); b itself also
-// to bout for the divergence sum.  One thread per block of four probe
-// elements (one Philox call).
-__global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r2, float* __restrict__ bout,
-                              long long N, float eps_rel, int t_arg, unsigned slice, uint2 key,
-                              DevScalars* S, int write_b) {
+// to bout for the divergence sum.  One thread per group of four probe
+// elements (one Philox call): group g below.
+__device__ __forceinline__ void probe_group(const float* __restrict__ r, float* __restrict__ r2,
+                                            float* __restrict__ bout, long long N, float eps_rel, int t_arg,
+                                            unsigned slice, uint2 key, DevScalars* S, int write_b, long long g) {
     const float rmax = __uint_as_float(S->rmax_bits);
     const float eps = eps_rel * fmaxf(rmax, 1e-6f);
     const unsigned t = t_arg > 0 ? (unsigned)t_arg : S->t;
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g == 0) S->eps = (double)eps;
     const long long i0 = 4 * g;
     if (i0 >= N) return;
@@ -54,6 +53,21 @@ __global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r
             r2[i0 + k] = write_b ? bb[k] : fmaf(eps, bb[k], r[i0 + k]);
             bout[i0 + k] = bb[k];
         }
+}
+
+__global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r2, float* __restrict__ bout,
+                              long long N, float eps_rel, int t_arg, unsigned slice, uint2 key,
+                              DevScalars* S, int write_b) {
+    probe_group(r, r2, bout, N, eps_rel, t_arg, slice, key, S, write_b,
+                (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// r + eps b beside r for every slice of a batch (prox-TV), 256 groups per block.
+__global__ void __launch_bounds__(256) k_probe_input_batch(const BatchSlice* __restrict__ sl,
+                                                           const uint16_t* __restrict__ map) {
+    const BatchSlice& B = sl[map[blockIdx.x]];
+    const long long g = (long long)((int)blockIdx.x - B.off[kPhProbe]) * blockDim.x + threadIdx.x;
+    probe_group(B.r, B.r + B.N, B.b, B.N, B.eps_rel, 0, B.slice_id, B.key, B.S, 0, g);
 }
 
 static uint2 probe_key(const dgamp_ct_plan_s* pl) {
@@ -128,6 +142,7 @@ struct TvFinal {
 constexpr int kTvU = 2;            // columns per thread
 constexpr int kTvV = 4;            // rows per thread
 constexpr int kTvRW = 32 * kTvU;   // region width
+constexpr int kTvRowsBatch = 64;   // region height of the batched launches
 
 template <int WY, int KB, bool BORDER>
 __device__ __forceinline__ void tv_region_steps(float (&px)[kTvV][kTvU], float (&py)[kTvV][kTvU],
@@ -252,21 +267,31 @@ __device__ __forceinline__ void tv_divergence_finish(double acc, int nblk, int b
 // +b^T x_1 and -b^T x_0 over the blocks of the two images -- inside a solve
 // left as FP64 block partials that the next output step adds (it needs tau_x
 // first), elsewhere finished by the last block.
+template <int WY>
+struct TvShared {
+    float e_py[WY][kTvU][32];
+    float e_q[WY][kTvU][32];
+    double red[32];
+    bool am_last;
+};
+
+// Region (bx, by) of image bz of a launch whose grid is gx x gy x gz.
 template <int WY, int KB, bool FINAL>
-__global__ void __launch_bounds__(32 * WY)
-k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout, int n,
-           int first, float c_tv, int from_scalars, float lambda_arg, DevScalars* S,
-           const float* __restrict__ bprobe, TvFinal F) {
+__device__ __forceinline__ void tv_steps_block(const float* __restrict__ rbase, const float2* __restrict__ pin,
+                                               float2* __restrict__ pout, int n, int first, float c_tv,
+                                               int from_scalars, float lambda_arg, DevScalars* S,
+                                               const float* __restrict__ bprobe, const TvFinal& F, int bx, int by,
+                                               int bz, int gx, int gy, int gz, TvShared<WY>& sh) {
     constexpr int U = kTvU, V = kTvV, RW = kTvRW, RH = V * WY;
     constexpr int E = FINAL ? KB + 1 : KB;      // top/left margin of the tile
     constexpr int TW = RW - KB - E, TH = RH - KB - E;
-    __shared__ float e_py[WY][U][32];
-    __shared__ float e_q[WY][U][32];
+    auto& e_py = sh.e_py;
+    auto& e_q = sh.e_q;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const size_t N = (size_t)n * n;
-    const int im = (int)blockIdx.z;
+    const int im = bz;
     const size_t img = (size_t)im * N;
-    const int gi0 = (int)blockIdx.y * TH - E, gj0 = (int)blockIdx.x * TW - E;
+    const int gi0 = by * TH - E, gj0 = bx * TW - E;
     const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
     const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
     float px[V][U], py[V][U], rl[V][U];
@@ -316,9 +341,9 @@ k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
         return;
     }
     // ---- final: x = r - lambda div p (e_py holds the last rows' py) ----
-    __shared__ double red[32];
-    __shared__ bool am_last;
-    const int nimg = (int)gridDim.z;
+    auto& red = sh.red;
+    auto& am_last = sh.am_last;
+    const int nimg = gz;
     double acc = 0.0;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -351,8 +376,8 @@ k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
         }
     }
     if (nimg < 2) return;
-    const int nblk = (int)(gridDim.x * gridDim.y * gridDim.z);
-    const int bid = (int)((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+    const int nblk = gx * gy * gz;
+    const int bid = (bz * gy + by) * gx + bx;
     if (F.solve_mode) {
         // inside a solve the next output step adds the partials (it needs
         // tau_x first): no grid-wide tail here
@@ -364,6 +389,96 @@ k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
         return;
     }
     tv_divergence_finish(acc, nblk, bid, N, S, F, red, &am_last);
+}
+
+template <int WY, int KB, bool FINAL>
+__global__ void __launch_bounds__(32 * WY)
+k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout, int n,
+           int first, float c_tv, int from_scalars, float lambda_arg, DevScalars* S,
+           const float* __restrict__ bprobe, TvFinal F) {
+    __shared__ TvShared<WY> sh;
+    tv_steps_block<WY, KB, FINAL>(rbase, pin, pout, n, first, c_tv, from_scalars, lambda_arg, S, bprobe, F,
+                                  blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z, sh);
+}
+
+// TV region dims of a launch: tile width and height of the valid part
+template <int WY, int KB, bool FINAL>
+__host__ __device__ constexpr int tv_tile_w() { return kTvRW - KB - (FINAL ? KB + 1 : KB); }
+template <int WY, int KB, bool FINAL>
+__host__ __device__ constexpr int tv_tile_h() { return kTvV * WY - KB - (FINAL ? KB + 1 : KB); }
+
+// The final-step fields of a solve on batch slice B (as make_tv_final gives
+// them for a plan inside a solve)
+__device__ __forceinline__ TvFinal tv_final_of(const BatchSlice& B, int xbf) {
+    TvFinal F;
+    F.x_out = B.x;
+    F.XR = (float*)B.XR;
+    F.XC = (float*)B.XC;
+    F.ldp = B.ldp;
+    F.xbf = xbf;
+    F.damp_x = B.damp_x;
+    F.t_arg = 0;
+    F.slice = B.slice_id;
+    F.key = B.key;
+    F.tau_x_floor = B.tau_x_floor;
+    F.partial = B.partial;
+    F.partial_div = B.partial_div;
+    F.log = B.log;
+    F.div_out = nullptr;
+    F.solve_mode = 1;
+    F.jvp = 0;
+    return F;
+}
+
+// KB Chambolle steps of both images (r and r + eps b) of every slice of a
+// batch in one launch; first: the duals start at zero; the final launch
+// forms x, the staged copies and the divergence partials as in a solve.
+// Ping-pong dual buffers as in launch_tv_chunk: launch i reads buffer
+// (i + 1) & 1 and writes i & 1.
+template <int WY, int KB, bool FINAL>
+__global__ void __launch_bounds__(32 * WY)
+k_tv_steps_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ map, int phase, int launch,
+                 int xbf) {
+    __shared__ TvShared<WY> sh;
+    const BatchSlice& B = sl[map[blockIdx.x]];
+    const int l = (int)blockIdx.x - B.off[phase];
+    const int n = B.n;
+    const int gx = (n + tv_tile_w<WY, KB, FINAL>() - 1) / tv_tile_w<WY, KB, FINAL>();
+    const int gy = (n + tv_tile_h<WY, KB, FINAL>() - 1) / tv_tile_h<WY, KB, FINAL>();
+    const int bx = l % gx, by = (l / gx) % gy, bz = l / (gx * gy);
+    const size_t N = (size_t)B.N;
+    const float2* pin = B.p + ((launch + 1) & 1) * 2 * N;
+    float2* pout = B.p + (launch & 1) * 2 * N;
+    const TvFinal F = tv_final_of(B, xbf);
+    tv_steps_block<WY, KB, FINAL>(B.r, pin, pout, n, launch == 0, B.c_tv, 1, 0.f, B.S, B.b, F, bx, by, bz, gx, gy,
+                                  2, sh);
+}
+
+int batch_grid_tv(int n, int final_launch) {
+    constexpr int WY = kTvRowsBatch / kTvV;
+    const int tw = final_launch ? tv_tile_w<WY, kBatchTvKb, true>() : tv_tile_w<WY, kBatchTvKb, false>();
+    const int th = final_launch ? tv_tile_h<WY, kBatchTvKb, true>() : tv_tile_h<WY, kBatchTvKb, false>();
+    return ((n + tw - 1) / tw) * ((n + th - 1) / th) * 2;
+}
+
+int batch_grid_probe(long long N) { return (int)(((N + 3) / 4 + 255) / 256); }
+
+int launch_probe_batch(const BatchExec& E, cudaStream_t st) {
+    k_probe_input_batch<<<E.nblk[kPhProbe], 256, 0, st>>>(E.sl, E.map[kPhProbe]);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+int launch_tv_batch(const BatchExec& E, int launch, bool final_launch, cudaStream_t st) {
+    constexpr int WY = kTvRowsBatch / kTvV;
+    if (final_launch)
+        k_tv_steps_batch<WY, kBatchTvKb, true><<<E.nblk[kPhTv1], 32 * WY, 0, st>>>(E.sl, E.map[kPhTv1], kPhTv1,
+                                                                                 launch, E.bf);
+    else
+        k_tv_steps_batch<WY, kBatchTvKb, false><<<E.nblk[kPhTv0], 32 * WY, 0, st>>>(E.sl, E.map[kPhTv0], kPhTv0,
+                                                                                  launch, E.bf);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
 }
 
 // Final step: x = r - lambda div p for NIMG images (p = 0 when pfin is NULL),
