@@ -252,6 +252,19 @@ def _batched(dg, rank, world, dist, flush, steps, learned=False):
 
     ms_serial = timed(serial)
     launches = sum(p.solve_launches(T) for p in plans)
+    phase = None
+    if not learned:
+        # the same slices with every phase of an iteration as one launch over
+        # all of them (dgamp_ct_batch_*), the iteration graph-captured once
+        with dg.Batch(plans) as bobj:
+            for _ in range(2):
+                bobj.solve(counts, I0, T, mu_out=mus)
+            torch.cuda.synchronize()
+            ms_phase = timed(lambda: bobj.solve(counts, I0, T, mu_out=mus))
+            phase = {"ms_per_batch": ms_phase, "iters_per_s": len(batch) * T / (ms_phase / 1e3),
+                     "slices_per_s": len(batch) / (ms_phase / 1e3), "gpu_launches_per_batch_rank0": bobj.launches(T),
+                     "speedup_vs_stream_pool": ms / ms_phase,
+                     "tuning": "pj_seg 16, tile back-projection, cluster sinogram step, 10 TV steps per launch"}
     for p in plans:
         p.close()
     for net in nets:
@@ -263,6 +276,7 @@ def _batched(dg, rank, world, dist, flush, steps, learned=False):
             "ms_per_batch": ms, "iters_per_s": len(batch) * T / (ms / 1e3),
             "slices_per_s": len(batch) / (ms / 1e3),
             "one_stream_ms_per_batch": ms_serial, "concurrency_speedup": ms_serial / ms,
+            "one_launch_per_phase": phase,
             "joseph_steps_per_batch": int(work.sum()), "gpu_launches_per_batch_rank0": int(launches)}
 
 

@@ -99,6 +99,7 @@ def test_learned_batch_equals_single_solves_and_rejects_a_shared_network(dg):
         single = [p.solve(c, i0, T) for p, c, i0 in zip(plans, counts, I0)]
         torch.cuda.synchronize()
         for k in range(len(sl)):
+            assert bool(torch.isfinite(single[k]).all()), k
             assert torch.equal(mus[k], single[k]), k
         plans[1].set_cnn(nets[0])
         with pytest.raises(dg.DgampError):
@@ -108,3 +109,98 @@ def test_learned_batch_equals_single_solves_and_rejects_a_shared_network(dg):
             p.close()
         for n in nets:
             n.close()
+
+
+# ------------------------------------------- one launch per phase (Batch) --
+BATCH_TUNING = dict(pj_seg=16, bp_mode=1, sino_fused=2, tv_kb=10, tv_rows=64)
+MIXED = [  # (n, views, bins, seed, I0): sizes that leave ragged tiles, regions and clusters
+    (64, 30, 95, 1000, 1e4),
+    (48, 13, 73, 1001, 3e4),
+    (37, 8, 55, 1002, 1e5),
+    (96, 17, 137, 1004, 1e5),
+    (128, 40, 182, 1005, 2e4),
+    (72, 11, 103, 1006, 1e4),
+]
+
+
+def _mixed():
+    out = []
+    for n, nv, nd, seed, I0 in MIXED:
+        ph = synth.random_phantom(n, 5, seed)
+        y = synth.poisson_counts(synth.analytic_sinogram(ph, synth.view_angles(nv), nd), I0, seed + 7)
+        out.append(dict(n=n, nv=nv, nd=nd, y=y, I0=I0))
+    return out
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_batch_one_launch_per_phase_is_bit_identical_to_single_solves(dg, storage):
+    """dgamp_ct_batch_solve runs each phase of an iteration as one launch over
+    all slices; every block runs the single-slice kernel's block body, so
+    each slice must equal its own solve with the batch's implementation
+    choices bit for bit (the mu, x-derived log of scalars and counters)."""
+    sl = _mixed()
+    T = 6
+    kw = dict(c_tv=3.0, k_tv=20, damp_x=0.2, damp_s=0.15, storage=storage)
+    plans = [dg.Plan(s["n"], s["nv"], s["nd"], **kw) for s in sl]
+    try:
+        counts = [torch.as_tensor(s["y"]).cuda() for s in sl]
+        I0 = [s["I0"] for s in sl]
+        with dg.Batch(plans) as b:
+            assert b.launches(T) == 1 + 6 * T + 4
+            mus, stats = b.solve(counts, I0, T, with_stats=True)
+            mus2 = b.solve(counts, I0, T)                     # the captured graph replays the same
+            torch.cuda.synchronize()
+            mus = [m.clone() for m in mus]
+        single, sst = [], []
+        for p, c, s in zip(plans, counts, sl):
+            p.set_tuning(**BATCH_TUNING)
+            mu, st = p.solve(c, s["I0"], T, with_stats=True)
+            single.append(mu)
+            sst.append(st)
+        torch.cuda.synchronize()
+        for k in range(len(sl)):
+            assert bool(torch.isfinite(single[k]).all()), k
+            assert torch.equal(mus[k], single[k]), k
+            assert torch.equal(mus2[k], single[k]), k
+            assert stats[k]["iters_done"] == T
+            for key in ("tau_x", "tau_p", "tau_s", "tau_r", "div"):
+                assert np.array_equal(stats[k][key], sst[k][key]), (k, key)
+        if storage == 0:
+            s = sl[0]
+            ref = gamp.ct_solve(s["y"], s["I0"], Geometry(s["n"], s["nv"], s["nd"]), T,
+                                gamp.Options(c_tv=3.0, k_tv=20, damp_x=0.2, damp_s=0.15))
+            assert rel(mus[0].cpu().numpy(), ref) < 1e-3
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_batch_mixed64_subset_matches_stream_pool(dg):
+    """Twelve slices of the mixed 64-slice workload (256-512 pixels, 32-128
+    views), 30 iterations: the batch object against the stream-pool path,
+    whose plans use their own tuned implementation choices (other summation
+    orders), to the 1e-3 of the solve tests."""
+    batch = synth.make_batch("mixed64", count=12)
+    kw = dict(c_tv=3.0, k_tv=20, damp_x=0.2, damp_s=0.15)
+    plans = [dg.Plan(c["n"], c["n_views"], c["n_det"], **kw) for c in batch]
+    try:
+        counts = [torch.as_tensor(c["y"]).cuda() for c in batch]
+        I0 = [c["I0"] for c in batch]
+        T = batch[0]["iters"]
+        with dg.Batch(plans) as b:
+            mb = [m.cpu().numpy() for m in b.solve(counts, I0, T)]
+        mp = [m.cpu().numpy() for m in dg.solve_batched(plans, counts, I0, T)]
+        for k in range(len(batch)):
+            assert rel(mb[k], mp[k]) < 1e-3, k
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_batch_rejects_what_it_cannot_run(dg):
+    with dg.Plan(32, 5, 48, c_tv=3.0, k_tv=20) as a, dg.Plan(32, 5, 48, c_tv=3.0, k_tv=15) as b15, \
+            dg.Plan(32, 5, 48, denoiser=1) as learned, dg.Plan(32, 5, 48, tv_metric=1) as metric, \
+            dg.Plan(32, 5, 48, storage=1) as bf:
+        for bad in ([a, a], [a, b15], [a, learned], [a, metric], [a, bf], []):
+            with pytest.raises((dg.DgampError, ValueError)):
+                dg.Batch(bad)
