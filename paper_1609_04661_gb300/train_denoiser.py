@@ -40,6 +40,7 @@ MAGIC = b"DGCTCNN1"
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "dncnn17_ellipse512_v64.bin")
 PLAIN = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
+WORKLOAD = ["ellipse512_v64"]   # the harvesting and evaluation workload (--workload)
 
 
 def save_weights(path: str, params: np.ndarray, layers: int, scaled: bool) -> None:
@@ -77,7 +78,8 @@ def load_cnn(path: str = DEFAULT_WEIGHTS):
 
 
 def harvest(n_phantoms: int, iters: int, patches_per_iter: int, patch: int, seed0: int = 2000,
-            workload: str = "ellipse512_v64", scaled: bool = True, net=None, rng_seed: int = 7):
+            workload: str | None = None, scaled: bool = True, net=None, rng_seed: int = 7,
+            max_mse: float = 1.0):
     """(r patches, x_true patches, sigma, diagnostics) on the GPU from damped
     solves of training phantoms: r^t is the denoiser input of iteration t
     and x_true = V mu_true.
@@ -90,7 +92,8 @@ def harvest(n_phantoms: int, iters: int, patches_per_iter: int, patch: int, seed
     means along the trajectory.  net: harvest from solves with that network
     as the denoiser (noise-level scaled) instead of prox-TV.
     diagnostics: per iteration, the mean over phantoms of tau_r^t and of the
-    actual mean squared error of r^t."""
+    actual mean squared error of r^t.  Iterates whose actual mean squared
+    error exceeds max_mse (a solve that has diverged) are not harvested."""
     import torch
     import synth
     from .binding import Plan
@@ -99,7 +102,7 @@ def harvest(n_phantoms: int, iters: int, patches_per_iter: int, patch: int, seed
     tau_tab, err_tab = np.zeros(iters), np.zeros(iters)
     plan = None
     for k in range(n_phantoms):
-        c = synth.make_case(workload, seed=seed0 + k)
+        c = synth.make_case(workload or WORKLOAD[0], seed=seed0 + k)
         if plan is None:
             opts = dict(PLAIN)
             if net is not None:
@@ -115,7 +118,7 @@ def harvest(n_phantoms: int, iters: int, patches_per_iter: int, patch: int, seed
             err = float(((rt[t] - xt) ** 2).mean())
             tau_tab[t] += tau_r[t] / n_phantoms
             err_tab[t] += err / n_phantoms
-            if not (np.isfinite(tau_r[t]) and tau_r[t] > 0 and np.isfinite(err)):
+            if not (np.isfinite(tau_r[t]) and tau_r[t] > 0 and np.isfinite(err) and err <= max_mse):
                 continue
             for _ in range(patches_per_iter):
                 i, j = rng.integers(0, n - patch + 1, size=2)
@@ -129,13 +132,13 @@ def harvest(n_phantoms: int, iters: int, patches_per_iter: int, patch: int, seed
     return torch.stack(rs).contiguous(), torch.stack(xs).contiguous(), np.asarray(sg, dtype=np.float32), diag
 
 
-def psnr_curve(net, iters: int, seed: int = 1000, workload: str = "ellipse512_v64"):
+def psnr_curve(net, iters: int, seed: int = 1000, workload: str | None = None):
     """PSNR of mu after t = 1..iters damped iterations on one slice, with the
     network (noise-level scaled) or, for net=None, prox-TV."""
     import torch
     import synth
     from .binding import Plan
-    c = synth.make_case(workload, seed=seed)
+    c = synth.make_case(workload or WORKLOAD[0], seed=seed)
     opts = dict(PLAIN)
     if net is not None:
         opts.update(denoiser=1, cnn_scale=1)
@@ -226,9 +229,14 @@ def main(argv=None):
     ap.add_argument("--sigma", type=float, nargs=2, default=(0.003, 1.0), help="awgn sigma range")
     ap.add_argument("--eval-iters", type=int, default=30, help="PSNR curve on the held-out slice (seed 1000)")
     ap.add_argument("--damp", type=float, default=PLAIN["damp_x"],
-                    help="damping eta_x = eta_s of the harvesting and evaluation solves")
+                    help="damping eta_x (and eta_s unless --damp-s) of the harvesting and evaluation solves")
+    ap.add_argument("--damp-s", type=float, default=None)
+    ap.add_argument("--tau-x0", type=float, default=1.0, help="initial tau_x of those solves (Algorithm 1)")
+    ap.add_argument("--workload", default="ellipse512_v64", help="synth workload of the harvest and evaluation")
     args = ap.parse_args(argv)
-    PLAIN.update(damp_x=args.damp, damp_s=args.damp)
+    PLAIN.update(damp_x=args.damp, damp_s=args.damp if args.damp_s is None else args.damp_s,
+                 tau_x0=args.tau_x0)
+    WORKLOAD[0] = args.workload
     import torch
     from . import build
     build.build()
