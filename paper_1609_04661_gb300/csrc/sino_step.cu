@@ -214,7 +214,8 @@ __device__ __forceinline__ void ct_product(const float* __restrict__ z, const fl
     float h[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) h[k] = hs[base + k];
-#pragma unroll 4
+    // unrolled by R, the window's shift becomes a rotation of registers
+#pragma unroll R
     for (int dp = p0; dp < p1; ++dp) {
         const float zv = z[dp];
 #pragma unroll
@@ -258,6 +259,17 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
     float* red = hs + HL;       // [kCtWarps][OUT]
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const size_t row0 = (size_t)v * nd;
+    // the tau_x warp issues its loads of the divergence partials first, so
+    // that their latency overlaps the loads and the first product
+    double div_pre[kDivPre];
+    if (w == kCtWarps) {
+        const unsigned np = S->div_pending;
+#pragma unroll
+        for (int k = 0; k < kDivPre; ++k) {
+            const unsigned i = (unsigned)lane + 32u * k;
+            div_pre[k] = i < np ? partial_div[i] : 0.0;
+        }
+    }
     // this thread's bins of the output step: s_prev and y now, used after the first product
     float pre_sp[kCtPre], pre_y[kCtPre];
 #pragma unroll
@@ -289,7 +301,7 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
     } else {
         // tau_x of the previous iteration (its divergence may still be in
         // partial sums; every CTA adds them in the same order), then tau_p
-        const double tx = pending_tau_x(S, partial_div, N, floor_rel, log, record);
+        const double tx = pending_tau_x(S, partial_div, N, floor_rel, log, record, div_pre, kDivPre);
         if (lane == 0) {
             const double tp = S->frob2 * tx / (double)M;
             s_tp = (float)tp;

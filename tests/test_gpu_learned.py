@@ -111,6 +111,28 @@ def test_shipped_network_denoises_gaussian_noise(dg, weights):
             assert mse_out < 0.1 * mse_in, (sigma, mse_in, mse_out)
 
 
+def test_shipped_network_beats_prox_tv_as_a_denoiser(dg, weights):
+    """What the trained network gains over the method's plain denoiser, as a
+    denoiser: on a held-out phantom in the preconditioned space with Gaussian
+    noise of level sigma, its output error against that of the prox-TV the
+    solve uses at the same level (lambda = 3 sigma, 20 Chambolle steps)."""
+    params, scaled = weights
+    c = synth.make_case("ellipse512_v64", seed=1000)
+    with dg.CNN(cnn.LAYERS) as net, dg.Plan(c["n"], c["n_views"], c["n_det"], c_tv=3.0, k_tv=20) as pl:
+        net.set_params(params)
+        xt = pl.precond_image(torch.as_tensor(c["mu"], dtype=torch.float32).cuda(), inverse=False)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(5)
+        for sigma in (0.01, 0.1, 1.0):
+            r = (xt + sigma * torch.randn(xt.shape, generator=gen, device="cuda")).contiguous()
+            d_net = net.denoise(r[None].contiguous(), np.array([sigma], dtype=np.float32))[0]
+            d_tv = pl.denoise_tv(r, 3.0 * sigma)
+            mse_net = float(((d_net - xt) ** 2).mean())
+            mse_tv = float(((d_tv - xt) ** 2).mean())
+            print(f"sigma {sigma}: network MSE {mse_net:.3e}, prox-TV MSE {mse_tv:.3e}")
+            assert mse_net < mse_tv, (sigma, mse_net, mse_tv)
+
+
 def test_graph_recaptured_after_network_workspace_grows(dg, weights):
     """Using the attached network elsewhere (here: a gradient pass that keeps
     all 17 activations) regrows its workspace; the next solve must re-capture

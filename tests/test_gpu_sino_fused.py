@@ -69,9 +69,13 @@ def test_fused_solve_matches_oracle_and_unfused(dg, n, nv, nd, I0, trunc):
             mu, st = pl.solve(torch.as_tensor(y).cuda(), I0, T, with_stats=True)
             out[fused] = (mu.cpu().numpy(), st)
     for fused in forms[:-1]:
+        # the FFT form runs the three-kernel path's arithmetic (1e-4, see above);
+        # the Toeplitz form sums H's products in another order, which over five
+        # iterations of the smallest geometries grows to about 1.5e-4
+        tol = 1e-4 if fused == 1 else 5e-4
         assert rel(out[fused][0], ref) < 1e-3, fused
-        assert rel(out[fused][0], out[0][0]) < 1e-4, fused
-        assert np.allclose(out[fused][1]["tau_r"], out[0][1]["tau_r"], rtol=1e-4), fused
+        assert rel(out[fused][0], out[0][0]) < tol, fused
+        assert np.allclose(out[fused][1]["tau_r"], out[0][1]["tau_r"], rtol=tol), fused
     if nd > 1792:
         with dg.Plan(n, nv, nd, **kw) as pl:
             with pytest.raises(dg.DgampError):
