@@ -124,11 +124,12 @@ def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
 
 def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
              opts: Options | None = None, return_x: bool = False, log=None,
-             frob2: float | None = None, on_iter=None, cnn=None):
+             frob2: float | None = None, on_iter=None, cnn=None, cnn_bf16: bool = True):
     """D-GAMP-CT on one slice (parity unpinned).
 
     The denoiser is prox-TV, or with ``cnn = (ws, bs, scaled)`` the learned
-    residual network of ``oracle.cnn`` in its BF16-activation form, run at
+    residual network of ``oracle.cnn`` in its BF16-activation form
+    (``cnn_bf16=False``: unrounded FP64 activations), run at
     sigma = sqrt(tau_r) (scaled) or sigma = 1 (blind).  The full
     reconstruction has no closed form and the paper prints no synthetic
     result; it is checked only through its pinned parts and the tests'
@@ -163,7 +164,7 @@ def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
         if cnn is not None:
             ws, bs, scaled = cnn
             sigma = float(np.sqrt(tau_r)) if scaled else 1.0
-            return _cnn.Denoiser(sigma, ws, bs, bf16=True)
+            return _cnn.Denoiser(sigma, ws, bs, bf16=cnn_bf16)
         lam = opts.c_tv * np.sqrt(tau_r)
         if opts.tv_metric:
             q_max = _pre.vtv_inverse_norm_bound(geom)

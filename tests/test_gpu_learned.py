@@ -84,6 +84,35 @@ def test_learned_solve_matches_oracle(dg, scaled):
     assert rel(mu, mu_ref) < 2e-2
 
 
+def test_shipped_network_in_a_solve_matches_oracle(dg, weights):
+    """The shipped weights inside two damped iterations of the 64 x 64 solve,
+    against the oracle with the same BF16-rounded weights and activation
+    rounding.  These weights amplify BF16 rounding flips far more than a
+    random network on this input (their inputs lie outside their training
+    range), so the bound is 1.5 times the oracle's own distance between its
+    BF16 and FP64 evaluations of the same solve, as for deep networks in
+    test_gpu_cnn_fullsize.py."""
+    from paper_1609_04661_gb300.binding import unflatten_params
+    params, scaled = weights
+    c = synth.make_case("ellipse64_v30")
+    g = Geometry(c["n"], c["n_views"], c["n_det"])
+    T = 2
+    ws, bs = unflatten_params(params)
+    ws = [cnn.bf16_round(w) for w in ws]
+    opts = gamp.Options(damp_x=0.5, damp_s=0.5)
+    mu16 = gamp.ct_solve(c["y"], c["I0"], g, T, opts, cnn=(ws, bs, bool(scaled)))
+    mu64 = gamp.ct_solve(c["y"], c["I0"], g, T, opts, cnn=(ws, bs, bool(scaled)), cnn_bf16=False)
+    with dg.CNN(cnn.LAYERS) as net, dg.Plan(g.n, g.n_views, g.n_det, denoiser=1, cnn_scale=int(scaled),
+                                            damp_x=0.5, damp_s=0.5) as pl:
+        net.set_params(params)
+        pl.set_cnn(net)
+        mu = pl.solve(torch.as_tensor(c["y"]).cuda(), c["I0"], T).cpu().numpy()
+    bound = max(1.5 * rel(mu16, mu64), 2e-2)
+    print(f"shipped network, {T} iterations: GPU vs BF16 oracle {rel(mu, mu16):.2e}, "
+          f"oracle BF16 vs FP64 {rel(mu16, mu64):.2e}")
+    assert rel(mu, mu16) < bound
+
+
 def test_learned_solve_needs_a_network(dg):
     c = synth.make_case("ellipse64_v30")
     with dg.Plan(c["n"], c["n_views"], c["n_det"], denoiser=1) as pl:
