@@ -357,8 +357,12 @@ int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float*
    storage type and one k_tv (a multiple of 10), c_tv > 0, n_det <= 1792.
    The batch refers to the plans' workspaces: they must outlive it, and a
    plan must not be solved on its own while a batch solve using it runs.
+   groups >= 1: the slices are split largest-first into that many groups
+   (at most n); each group's six launches form one branch of the iteration
+   graph and the branches run concurrently, so one group's denoiser can
+   overlap another's projection.  groups = 1 is the single launch per phase.
    Errors: INVALID_ARG, UNSUPPORTED_GEOMETRY, OOM, CUDA.  Synchronous. */
-int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, dgamp_ct_batch_t* out);
+int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, int32_t groups, dgamp_ct_batch_t* out);
 void dgamp_ct_batch_destroy(dgamp_ct_batch_t batch);
 /* Solve every slice: slice i takes d_counts[i] ([n_views][n_det] float32 of
    plans[i]) and I0[i], runs `iters` iterations and writes mu to d_mu_out[i]
@@ -366,7 +370,8 @@ void dgamp_ct_batch_destroy(dgamp_ct_batch_t batch);
    stats[0..n-1] (errors as dgamp_ct_solve_batched). */
 int dgamp_ct_batch_solve(dgamp_ct_batch_t batch, const float* const* d_counts, const double* I0,
                          int32_t iters, float* const* d_mu_out, dgamp_ct_stats* stats, void* stream);
-/* Kernels one dgamp_ct_batch_solve of `iters` iterations launches (for all slices together). */
+/* Kernels one dgamp_ct_batch_solve of `iters` iterations launches (for all slices together):
+   1 + iters * groups * 6 + 4. */
 int64_t dgamp_ct_batch_launches(dgamp_ct_batch_t batch, int32_t iters);
 
 /* Host-only scheduler (no device work): assigns n jobs of the given work

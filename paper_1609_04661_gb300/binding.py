@@ -129,7 +129,7 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_plan_set_cnn": (C.c_int, [vp, vp]),
         "dgamp_ct_cnn_test_timeout": (C.c_int, [vp, i32]),
         "dgamp_ct_measure_fp32_peak": (C.c_int, [i32, C.POINTER(dbl), C.POINTER(i32), vp]),
-        "dgamp_ct_batch_create": (C.c_int, [i32, vp, vp]),
+        "dgamp_ct_batch_create": (C.c_int, [i32, vp, i32, vp]),
         "dgamp_ct_batch_destroy": (None, [vp]),
         "dgamp_ct_batch_solve": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
         "dgamp_ct_batch_launches": (i64, [vp, i32]),
@@ -562,13 +562,15 @@ class Batch:
     """A batch of slices run one launch per phase (dgamp_ct_batch_*): holds the
     plans (which must stay open) and solves them together."""
 
-    def __init__(self, plans):
+    def __init__(self, plans, groups: int = 1):
+        """groups: slices split largest-first into that many groups whose launches
+        run on parallel branches of the iteration graph (1: one launch per phase)."""
         self._lib = load()
         self.plans = list(plans)
         n = len(self.plans)
         P = (C.c_void_p * n)(*[p._h.value if isinstance(p._h, C.c_void_p) else p._h for p in self.plans])
         h = C.c_void_p()
-        _check(self._lib.dgamp_ct_batch_create(n, P, C.byref(h)), "dgamp_ct_batch_create")
+        _check(self._lib.dgamp_ct_batch_create(n, P, int(groups), C.byref(h)), "dgamp_ct_batch_create")
         self._h = h
 
     def close(self):

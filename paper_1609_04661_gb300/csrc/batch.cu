@@ -140,7 +140,8 @@ namespace dgct {
 // the staged images of x = 0 (zeros, guards included) and the scalars.
 __global__ void __launch_bounds__(256) k_batch_begin(const BatchSlice* __restrict__ sl,
                                                      const uint16_t* __restrict__ map) {
-    const BatchSlice& B = sl[map[blockIdx.x]];
+    __shared__ BatchSlice sd;
+    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
     const long long e = (long long)((int)blockIdx.x - B.off[kPhBegin]) * blockDim.x + threadIdx.x;
     if (e < B.M) {
         B.y[e] = B.counts[e];
@@ -175,7 +176,8 @@ __global__ void k_batch_finish(const BatchSlice* __restrict__ sl) {
 __global__ void __launch_bounds__(512) k_batch_vinv_rows(const BatchSlice* __restrict__ sl,
                                                          const uint16_t* __restrict__ map) {
     extern __shared__ float2 smem[];
-    const BatchSlice& B = sl[map[blockIdx.x]];
+    __shared__ BatchSlice sd;
+    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
     const int iy = (int)blockIdx.x - B.off[kPhRow], n = B.n, m = B.m2;
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
@@ -189,7 +191,8 @@ __global__ void __launch_bounds__(512) k_batch_vinv_rows(const BatchSlice* __res
 __global__ void __launch_bounds__(512) k_batch_vinv_cols(const BatchSlice* __restrict__ sl,
                                                          const uint16_t* __restrict__ map) {
     extern __shared__ float2 smem[];
-    const BatchSlice& B = sl[map[blockIdx.x]];
+    __shared__ BatchSlice sd;
+    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
     const int kx = (int)blockIdx.x - B.off[kPhCol], n = B.n, m = B.m2;
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
@@ -215,7 +218,8 @@ __global__ void __launch_bounds__(512) k_batch_vinv_cols(const BatchSlice* __res
 __global__ void __launch_bounds__(512) k_batch_vinv_rows_inv(const BatchSlice* __restrict__ sl,
                                                              const uint16_t* __restrict__ map) {
     extern __shared__ float2 smem[];
-    const BatchSlice& B = sl[map[blockIdx.x]];
+    __shared__ BatchSlice sd;
+    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
     const int iy = (int)blockIdx.x - B.off[kPhRow], n = B.n, m = B.m2;
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
@@ -232,8 +236,9 @@ struct dgamp_ct_batch_s {
     int device = 0;
     std::vector<dgamp_ct_plan_t> plans;
     std::vector<BatchSlice> h;          // host copy of the descriptors
-    BatchExec E;
-    cudaGraphExec_t graph = nullptr;    // one iteration: 6 launches over all slices
+    BatchExec E;                        // the whole batch: begin, finish and V^-1 tables
+    std::vector<BatchExec> grp;         // per group: the tables of the iteration's phases
+    cudaGraphExec_t graph = nullptr;    // one iteration: 6 launches per group, groups on parallel branches
     int tv_launches = 0;
 };
 
@@ -244,15 +249,18 @@ static void batch_free(dgamp_ct_batch_s* b) {
     if (b->E.sl) cudaFree(b->E.sl);
     for (int p = 0; p < kPhases; ++p)
         if (b->E.map[p]) cudaFree(b->E.map[p]);
+    for (auto& g : b->grp)
+        for (int p = 0; p < kPhases; ++p)
+            if (g.map[p]) cudaFree(g.map[p]);
     b->graph = nullptr;
     b->E = BatchExec{};
+    b->grp.clear();
 }
 
 static int batch_vinv_threads(int m) { return m / 8 < 32 ? 32 : (m / 8 > 512 ? 512 : m / 8); }
 
-// One iteration of every slice: the six batched launches.
-static int batch_iteration(dgamp_ct_batch_s* b, cudaStream_t st) {
-    const BatchExec& E = b->E;
+// One iteration of every slice of a group: the six batched launches.
+static int batch_iteration(dgamp_ct_batch_s* b, const BatchExec& E, cudaStream_t st) {
     DGCT_TRY(launch_project_batch(E, st));                         // Step 1: A x
     DGCT_TRY(launch_sino_batch(E, st));                            //         H A x, Step 2, H s
     DGCT_TRY(launch_backproject_batch(E, st));                     // Step 3: r = x + tau_r A^T H s
@@ -262,19 +270,51 @@ static int batch_iteration(dgamp_ct_batch_s* b, cudaStream_t st) {
     return DGAMP_CT_OK;
 }
 
+// The iteration graph: group k's six launches on branch k, forked from and
+// joined back into the capture stream (one branch when there is one group).
 static int batch_graph(dgamp_ct_batch_s* b) {
     if (b->graph) return DGAMP_CT_OK;
+    const int G = (int)b->grp.size();
+    std::vector<cudaStream_t> br(G, nullptr);
+    std::vector<cudaEvent_t> ev(G + 1, nullptr);
     cudaStream_t cs;
     DGCT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < G && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&br[k], cudaStreamNonBlocking);
+    for (int k = 0; k <= G && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    auto cleanup = [&]() {
+        for (auto s_ : br)
+            if (s_) cudaStreamDestroy(s_);
+        for (auto v : ev)
+            if (v) cudaEventDestroy(v);
         cudaStreamDestroy(cs);
+    };
+    if (e != cudaSuccess) {
+        cleanup();
         return cuda_fail(e);
     }
-    const int rc = batch_iteration(b, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e);
+    }
+    int rc = DGAMP_CT_OK;
+    if (G == 1) {
+        rc = batch_iteration(b, b->grp[0], cs);
+    } else {
+        cudaError_t ce = cudaEventRecord(ev[G], cs);                              // fork
+        for (int k = 0; k < G && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(br[k], ev[G], 0);
+        if (ce != cudaSuccess) rc = cuda_fail(ce);
+        for (int k = 0; k < G && rc == DGAMP_CT_OK; ++k) rc = batch_iteration(b, b->grp[k], br[k]);
+        for (int k = 0; k < G; ++k) {                                              // join every branch
+            ce = cudaEventRecord(ev[k], br[k]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, ev[k], 0);
+            if (ce != cudaSuccess && rc == DGAMP_CT_OK) rc = cuda_fail(ce);
+        }
+    }
     e = cudaStreamEndCapture(cs, &g);
-    cudaStreamDestroy(cs);
+    cleanup();
     if (rc != DGAMP_CT_OK) {
         if (g) cudaGraphDestroy(g);
         return rc;
@@ -293,8 +333,8 @@ static int batch_graph(dgamp_ct_batch_s* b) {
 
 extern "C" {
 
-int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, dgamp_ct_batch_t* out) {
-    if (!out || n < 1 || n > 65535 || !plans) return DGAMP_CT_ERR_INVALID_ARG;
+int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, int32_t groups, dgamp_ct_batch_t* out) {
+    if (!out || n < 1 || n > 65535 || !plans || groups < 1) return DGAMP_CT_ERR_INVALID_ARG;
     *out = nullptr;
     int device = 0;
     DGCT_CUDA(cudaGetDevice(&device));
@@ -324,14 +364,25 @@ int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, dgamp_ct_batc
     E.bf = p0->opt.storage;
     E.R = sino_ct_lanes(max_nd);
     // descriptors and the block -> slice tables, largest slices first in
-    // each grid (the work list order of the LPT scheduler)
+    // each grid (the work list order of the LPT scheduler); the iteration's
+    // phases get one set of tables per group (slices split largest-first
+    // over the groups), the once-per-solve phases one for the whole batch
     std::vector<int64_t> work(n);
     for (int32_t i = 0; i < n; ++i) work[i] = (int64_t)plans[i]->nv * plans[i]->nd * plans[i]->n;
     std::vector<int32_t> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return work[a] > work[c]; });
+    const int G = std::min<int32_t>(groups, n);
+    std::vector<int32_t> group_of(n);
+    if (dgamp_ct_schedule_lpt(n, work.data(), G, group_of.data(), nullptr) != DGAMP_CT_OK) {
+        delete b;
+        return DGAMP_CT_ERR_INVALID_ARG;
+    }
+    b->grp.resize(G);
+    std::vector<int> gmax_nd(G, 0);
     b->h.resize(n);
     std::vector<std::vector<uint16_t>> maps(kPhases);
+    std::vector<std::vector<std::vector<uint16_t>>> gmaps(G, std::vector<std::vector<uint16_t>>(kPhases));
     for (int32_t k = 0; k < n; ++k) {
         const int32_t i = order[k];
         const dgamp_ct_plan_s* pl = plans[i];
@@ -354,22 +405,39 @@ int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, dgamp_ct_batc
         const int cnt[kPhases] = {batch_grid_project(pl->nv, pl->nd), pl->nv, batch_grid_backproject(pl->n),
                                   batch_grid_probe(pl->N), batch_grid_tv(pl->n, 0), batch_grid_tv(pl->n, 1),
                                   pl->n, pl->m2, (int)((begin_elems + 255) / 256)};
+        const int gk = group_of[i];
         for (int ph = 0; ph < kPhases; ++ph) {
-            d.off[ph] = (int)maps[ph].size();
-            maps[ph].insert(maps[ph].end(), (size_t)cnt[ph], (uint16_t)i);
+            auto& mp = (ph == kPhRow || ph == kPhCol || ph == kPhBegin) ? maps[ph] : gmaps[gk][ph];
+            d.off[ph] = (int)mp.size();
+            mp.insert(mp.end(), (size_t)cnt[ph], (uint16_t)i);
         }
         E.max_m2 = std::max(E.max_m2, pl->m2);
+        gmax_nd[gk] = std::max(gmax_nd[gk], pl->nd);
     }
     for (int ph = 0; ph < kPhases; ++ph) E.nblk[ph] = (int)maps[ph].size();
     E.ct_smem = sino_ct_smem_bytes(max_nd, E.R);
     int rc = DGAMP_CT_OK;
     cudaError_t e = cudaMalloc((void**)&E.sl, (size_t)n * sizeof(BatchSlice));
-    for (int ph = 0; ph < kPhases && e == cudaSuccess; ++ph) {
-        e = cudaMalloc((void**)&E.map[ph], maps[ph].size() * sizeof(uint16_t));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(E.map[ph], maps[ph].data(), maps[ph].size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    auto upload = [&](uint16_t** dst, const std::vector<uint16_t>& v) {
+        if (v.empty() || e != cudaSuccess) return;
+        e = cudaMalloc((void**)dst, v.size() * sizeof(uint16_t));
+        if (e == cudaSuccess) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    };
+    for (int ph : {kPhRow, kPhCol, kPhBegin}) upload(&E.map[ph], maps[ph]);
+    for (int k = 0; k < G; ++k) {
+        BatchExec& X = b->grp[k];
+        X.ns = n;
+        X.bf = E.bf;
+        X.R = sino_ct_lanes(gmax_nd[k]);
+        X.ct_smem = sino_ct_smem_bytes(gmax_nd[k], X.R);
+        X.max_m2 = E.max_m2;
+        for (int ph = 0; ph < kPhases; ++ph) {
+            X.nblk[ph] = (int)gmaps[k][ph].size();
+            if (ph != kPhRow && ph != kPhCol && ph != kPhBegin) upload(&X.map[ph], gmaps[k][ph]);
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpy(E.sl, b->h.data(), (size_t)n * sizeof(BatchSlice), cudaMemcpyHostToDevice);
+    for (auto& X : b->grp) X.sl = E.sl;
     if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? DGAMP_CT_ERR_OOM : cuda_fail(e);
     if (rc == DGAMP_CT_OK) {
         const int fsm = 2 * fft_buf_len(E.max_m2) * (int)sizeof(float2);
@@ -398,9 +466,9 @@ void dgamp_ct_batch_destroy(dgamp_ct_batch_t b) {
 
 int64_t dgamp_ct_batch_launches(dgamp_ct_batch_t b, int32_t iters) {
     if (!b || iters < 0) return -1;
-    // the begin kernel, per iteration the projector, sinogram step,
+    // the begin kernel, per iteration and group the projector, sinogram step,
     // back-projection, probe and TV launches, then the finish and V^-1 (3)
-    return 1 + (int64_t)iters * (4 + b->tv_launches) + 4;
+    return 1 + (int64_t)iters * (int64_t)b->grp.size() * (4 + b->tv_launches) + 4;
 }
 
 int dgamp_ct_batch_solve(dgamp_ct_batch_t b, const float* const* d_counts, const double* I0, int32_t iters,

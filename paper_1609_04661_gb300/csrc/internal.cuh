@@ -360,6 +360,20 @@ int launch_fan_backproject(const dgamp_ct_plan_s* pl, const float* sino, float* 
 // x, staging, divergence and tau_x from D(r) and J_D(r) b (learned denoiser)
 int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_out, int solve_mode, int t_arg,
                          double* div_out, cudaStream_t st);
+// A block's slice descriptor, copied once into shared memory (every thread
+// takes part; ends with a block barrier), so that the block body reads its
+// fields from shared memory rather than by dependent global loads.
+__device__ __forceinline__ const BatchSlice& load_slice(const BatchSlice* __restrict__ sl, int idx, BatchSlice* sh) {
+    static_assert(sizeof(BatchSlice) % sizeof(int) == 0, "descriptor copied as words");
+    const int* src = reinterpret_cast<const int*>(sl + idx);
+    int* dst = reinterpret_cast<int*>(sh);
+    for (int i = (int)(threadIdx.x + blockDim.x * threadIdx.y); i < (int)(sizeof(BatchSlice) / sizeof(int));
+         i += (int)(blockDim.x * blockDim.y))
+        dst[i] = src[i];
+    __syncthreads();
+    return *sh;
+}
+
 // Batched execution (batch.cu): device descriptors and tables of a batch,
 // and the grid of each phase (blocks; clusters for kPhView)
 struct BatchExec {

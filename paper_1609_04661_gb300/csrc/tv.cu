@@ -65,7 +65,8 @@ __global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r
 // r + eps b beside r for every slice of a batch (prox-TV), 256 groups per block.
 __global__ void __launch_bounds__(256) k_probe_input_batch(const BatchSlice* __restrict__ sl,
                                                            const uint16_t* __restrict__ map) {
-    const BatchSlice& B = sl[map[blockIdx.x]];
+    __shared__ BatchSlice sd;
+    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
     const long long g = (long long)((int)blockIdx.x - B.off[kPhProbe]) * blockDim.x + threadIdx.x;
     probe_group(B.r, B.r + B.N, B.b, B.N, B.eps_rel, 0, B.slice_id, B.key, B.S, 0, g);
 }
@@ -455,7 +456,8 @@ __global__ void __launch_bounds__(32 * WY)
 k_tv_steps_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ map, int phase, int launch,
                  int xbf) {
     __shared__ TvShared<WY> sh;
-    const BatchSlice& B = sl[map[blockIdx.x]];
+    __shared__ BatchSlice sd;
+    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
     const int l = (int)blockIdx.x - B.off[phase];
     const int n = B.n;
     const int gx = (n + tv_tile_w<WY, KB, FINAL>() - 1) / tv_tile_w<WY, KB, FINAL>();

@@ -132,12 +132,13 @@ def _mixed():
     return out
 
 
-@pytest.mark.parametrize("storage", [0, 1])
-def test_batch_one_launch_per_phase_is_bit_identical_to_single_solves(dg, storage):
+@pytest.mark.parametrize("storage,groups", [(0, 1), (1, 1), (0, 3)])
+def test_batch_one_launch_per_phase_is_bit_identical_to_single_solves(dg, storage, groups):
     """dgamp_ct_batch_solve runs each phase of an iteration as one launch over
     all slices; every block runs the single-slice kernel's block body, so
     each slice must equal its own solve with the batch's implementation
-    choices bit for bit (the mu, x-derived log of scalars and counters)."""
+    choices bit for bit (mu and the log of scalars), whether the slices run
+    as one group or as three groups on parallel branches of the graph."""
     sl = _mixed()
     T = 6
     kw = dict(c_tv=3.0, k_tv=20, damp_x=0.2, damp_s=0.15, storage=storage)
@@ -145,8 +146,8 @@ def test_batch_one_launch_per_phase_is_bit_identical_to_single_solves(dg, storag
     try:
         counts = [torch.as_tensor(s["y"]).cuda() for s in sl]
         I0 = [s["I0"] for s in sl]
-        with dg.Batch(plans) as b:
-            assert b.launches(T) == 1 + 6 * T + 4
+        with dg.Batch(plans, groups=groups) as b:
+            assert b.launches(T) == 1 + 6 * groups * T + 4
             mus, stats = b.solve(counts, I0, T, with_stats=True)
             mus2 = b.solve(counts, I0, T)                     # the captured graph replays the same
             torch.cuda.synchronize()
