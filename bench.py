@@ -53,11 +53,14 @@ TV = dict(c_tv=3.0, k_tv=20, damp_x=0.2, damp_s=0.15)
 # above the fan-beam solve diverges)
 TV_HALF = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the blocked-TV
-# launches of one iteration, from an ncu capture of this workload's headline
-# plan, valid only for the configuration captured (steps per launch, region
-# rows) and the kernel as it was then.
-TV_TRAFFIC = None   # no capture of the current kernel yet
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from
+# ncu captures of this workload's headline plan (cold cache), valid only for
+# the configuration captured and the kernels as they were then: the blocked-TV
+# launches of one iteration (10 steps per launch, 64-row regions), the
+# projector (16 step segments) and the tile back-projection.
+TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 64, "bytes_per_iteration": 2117376 + 8431104 + 512}
+A_TRAFFIC = {"pj_seg": 16, "bytes_per_launch": 2142208}
+AT_TRAFFIC = {"bp_mode": 1, "bytes_per_launch": 1263872}
 
 
 # ----------------------------------------------------------------- helpers --
@@ -760,21 +763,23 @@ def run_gpu(args):
     # sits in L2 at this size, so the HBM fraction stays small by nature)
     steps = float(case["n_views"]) * case["n_det"] * case["n"]
 
-    def joseph_roof(kname, label, byts):
+    def joseph_roof(kname, label, byts, traffic):
         ms_k = prof[kname]
         tfl = 4.0 * steps / (ms_k * 1e-3) / 1e12
         return {"kernel": label, "bound": "alu", "achieved": tfl, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": tfl / fp32_peak, "traffic": None, "peak_kind": "measured: " + peak_note,
+                "frac": tfl / fp32_peak, "traffic": traffic, "peak_kind": "measured: " + peak_note,
                 "ray_steps_per_launch": steps, "ray_steps_per_s": steps / (ms_k * 1e-3),
                 "launch_ms": ms_k,
                 "hbm_view": {"algorithmic_bytes_per_launch": byts, "achieved_gbs": byts / (ms_k * 1e-3) / 1e9,
                              "peak_gbs": hbm, "frac": byts / (ms_k * 1e-3) / 1e9 / hbm,
                              "peak_kind": f"{peak_kind} copy bandwidth"}}
 
-    roof_a = joseph_roof("project", f"k_project (A, {tun['pj_seg']} step segments)", algo["project"])
+    roof_a = joseph_roof("project", f"k_project (A, {tun['pj_seg']} step segments)", algo["project"],
+                         A_TRAFFIC["bytes_per_launch"] if tun["pj_seg"] == A_TRAFFIC["pj_seg"] else None)
     roof_at = joseph_roof("backproject_update",
                           "k_backproject_tile (A^T + update)" if tun["bp_mode"] == 1 else "k_backproject (A^T + update)",
-                          algo["backproject_update"])
+                          algo["backproject_update"],
+                          AT_TRAFFIC["bytes_per_launch"] if tun["bp_mode"] == AT_TRAFFIC["bp_mode"] else None)
     a_at_bytes = algo["project"] + algo["backproject_update"]
     a_at_ms = prof["project"] + prof["backproject_update"]
     learned = None
