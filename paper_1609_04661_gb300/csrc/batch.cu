@@ -351,7 +351,7 @@ int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, int32_t group
         if (pl->fan || o.denoiser != 0 || o.tv_metric || o.output_moments) return DGAMP_CT_ERR_INVALID_ARG;
         if (o.storage != p0->opt.storage || o.k_tv != p0->opt.k_tv) return DGAMP_CT_ERR_INVALID_ARG;
         if (o.k_tv < kBatchTvKb || o.k_tv % kBatchTvKb != 0 || !(o.c_tv > 0)) return DGAMP_CT_ERR_INVALID_ARG;
-        if (sino_ct_lanes(pl->nd) == 0 || pl->nv > pl->max_partials) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
+        if (sino_ct_config(pl->nd, nullptr) == 0 || pl->nv > pl->max_partials) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
         max_nd = std::max(max_nd, pl->nd);
     }
     dgamp_ct_batch_s* b = new (std::nothrow) dgamp_ct_batch_s();
@@ -362,7 +362,7 @@ int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, int32_t group
     BatchExec& E = b->E;
     E.ns = n;
     E.bf = p0->opt.storage;
-    E.R = sino_ct_lanes(max_nd);
+    E.R = sino_ct_config(max_nd, &E.cl);
     // descriptors and the block -> slice tables, largest slices first in
     // each grid (the work list order of the LPT scheduler); the iteration's
     // phases get one set of tables per group (slices split largest-first
@@ -415,7 +415,7 @@ int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, int32_t group
         gmax_nd[gk] = std::max(gmax_nd[gk], pl->nd);
     }
     for (int ph = 0; ph < kPhases; ++ph) E.nblk[ph] = (int)maps[ph].size();
-    E.ct_smem = sino_ct_smem_bytes(max_nd, E.R);
+    E.ct_smem = sino_ct_smem_bytes(max_nd, E.R, E.cl);
     int rc = DGAMP_CT_OK;
     cudaError_t e = cudaMalloc((void**)&E.sl, (size_t)n * sizeof(BatchSlice));
     auto upload = [&](uint16_t** dst, const std::vector<uint16_t>& v) {
@@ -428,8 +428,8 @@ int dgamp_ct_batch_create(int32_t n, const dgamp_ct_plan_t* plans, int32_t group
         BatchExec& X = b->grp[k];
         X.ns = n;
         X.bf = E.bf;
-        X.R = sino_ct_lanes(gmax_nd[k]);
-        X.ct_smem = sino_ct_smem_bytes(gmax_nd[k], X.R);
+        X.R = sino_ct_config(gmax_nd[k], &X.cl);
+        X.ct_smem = sino_ct_smem_bytes(gmax_nd[k], X.R, X.cl);
         X.max_m2 = E.max_m2;
         for (int ph = 0; ph < kPhases; ++ph) {
             X.nblk[ph] = (int)gmaps[k][ph].size();

@@ -383,6 +383,7 @@ struct BatchExec {
     int ns = 0;
     int bf = 0;                                  // BF16 storage
     int R = 3;                                   // bins per lane of the cluster sinogram kernel
+    int cl = 8;                                  // its CTAs per view (4 or 8)
     int ct_smem = 0;                             // its dynamic shared memory (largest slice)
     int max_m2 = 0;                              // largest V^-1 FFT length
 };
@@ -394,8 +395,8 @@ int batch_grid_backproject(int n);
 int launch_project_batch(const BatchExec& E, cudaStream_t st);
 int launch_backproject_batch(const BatchExec& E, cudaStream_t st);
 // sino_step.cu (cluster Toeplitz form)
-int sino_ct_lanes(int nd);                       // 0: n_det too large for the cluster form
-int sino_ct_smem_bytes(int nd, int R);
+int sino_ct_config(int nd, int* cl);             // bins per lane (0: n_det too large), CTAs per view
+int sino_ct_smem_bytes(int nd, int R, int cl);
 int launch_sino_batch(const BatchExec& E, cudaStream_t st);
 // tv.cu (64-row regions, kBatchTvKb steps per launch; `launch` counts from 0)
 int batch_grid_tv(int n, int final_launch);

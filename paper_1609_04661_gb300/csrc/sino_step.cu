@@ -177,13 +177,13 @@ k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __
 
 // ---------------------------------------------- cluster Toeplitz form ----
 // The same step with H as its Toeplitz product, (H z)[d] = sum_d' h[|d - d'|]
-// z[d'] (the FFT form's operator, fft.cu), spread over a cluster of kCtCL
+// z[d'] (the FFT form's operator, fft.cu), spread over a cluster of CL
 // CTAs per view instead of one block per pair of views: the FFT form's four
 // transforms are a serial chain that leaves most SMs idle, while the direct
 // products split freely over output bins.  CTA `rank` of the cluster of view
-// v owns bins [rank per, (rank + 1) per), per = ceil(n_det / kCtCL):
+// v owns bins [rank per, (rank + 1) per), per = ceil(n_det / CL):
 //   1. it loads the whole row of A x and the kernel hx;
-//   2. kCtWarps warps split the d' range of z = H A x for its bins, each lane
+//   2. W warps split the d' range of z = H A x for its bins, each lane
 //      R consecutive bins with a sliding window of hx in registers (R odd:
 //      the lanes' window loads fall on distinct banks), partial sums added
 //      in a fixed order; meanwhile one more warp finishes tau_x (the
@@ -195,12 +195,16 @@ k_sino_step(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __
 //      order over the ranks); every CTA forms H s for its bins.
 // No CTA reads another's shared memory after the barrier, so there is no
 // second one.  The back-projection adds the n_views partials.
-constexpr int kCtCL = 8;
-constexpr int kCtWarps = 4;
-constexpr int kCtThreads = 32 * (kCtWarps + 1);
+// Two shapes, chosen by the number of bins: up to 896 bins, a cluster of 4
+// CTAs per view with 8 product warps and up to 7 bins per lane (more
+// multiply-adds per shared-memory load, shorter serial chains); beyond that, 8
+// CTAs with 4 product warps (up to 1792 bins).
+constexpr int kCtMaxCL = 8;
 constexpr int kCtPre = 2;              // s_prev and y prefetched per thread (covers 2 x 160 >= 224 bins)
-constexpr int kCtMaxR = 7;             // bins per lane at most: n_det <= kCtCL x 32 x 7 = 1792
+constexpr int kCtMaxR = 7;             // bins per lane at most
+constexpr int kCtSmallNd = 4 * 32 * kCtMaxR;   // 896: the 4-CTA shape up to here
 
+__host__ __device__ constexpr int ct_threads(int W) { return 32 * (W + 1); }
 __host__ __device__ __forceinline__ int ct_hs_len(int nd, int R) { return 2 * nd + R + 1; }
 
 // acc[k] = sum over d' in [p0, p1) of hs[dl + k - d' + nd] z[d'] (hs = hx shifted by one)
@@ -229,13 +233,14 @@ __device__ __forceinline__ void ct_product(const float* __restrict__ z, const fl
 
 struct CtShared {
     double sm[32];
-    double tsum[kCtCL];
+    double tsum[kCtMaxCL];
     float s_tp, s_inv, s_logI0;
 };
 
-// View v's cluster, this CTA's part; record: the slice's first CTA (it
-// records the previous iteration's tau_x and log, and resets max |r|).
-template <typename T, int R>
+// View v's cluster (CL CTAs, W product warps each), this CTA's part;
+// record: the slice's first CTA (it records the previous iteration's tau_x
+// and log, and resets max |r|).
+template <typename T, int R, int CL, int W>
 __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const float* __restrict__ y, T* s,
                                               T* __restrict__ hsout, int nd, const float* __restrict__ hx,
                                               long long M, int onsager, float damp_s, int truncate, DevScalars* S,
@@ -243,6 +248,7 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
                                               double N, double floor_rel, IterLog* log, int v, bool record,
                                               float* smf, CtShared& shd) {
     constexpr int OUT = 32 * R;
+    constexpr int TH = ct_threads(W);
     auto& sm = shd.sm;
     auto& tsum = shd.tsum;
     auto& s_tp = shd.s_tp;
@@ -250,19 +256,19 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
     auto& s_logI0 = shd.s_logI0;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int per = (nd + kCtCL - 1) / kCtCL;
+    const int per = (nd + CL - 1) / CL;
     const int d_lo = min(nd, rank * per), d_hi = min(nd, d_lo + per), nown = d_hi - d_lo;
     const int HL = ct_hs_len(nd, R);
     float* zs = smf;            // [nd]  A x of the view
     float* sf = zs + nd;        // [nd]  s of the view, filled by every CTA of the cluster
     float* hs = sf + nd;        // [HL]  hs[i] = hx[i - 1], zero outside
-    float* red = hs + HL;       // [kCtWarps][OUT]
+    float* red = hs + HL;       // [W][OUT]
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const size_t row0 = (size_t)v * nd;
     // the tau_x warp issues its loads of the divergence partials first, so
     // that their latency overlaps the loads and the first product
     double div_pre[kDivPre];
-    if (w == kCtWarps) {
+    if (w == W) {
         const unsigned np = S->div_pending;
 #pragma unroll
         for (int k = 0; k < kDivPre; ++k) {
@@ -274,22 +280,22 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
     float pre_sp[kCtPre], pre_y[kCtPre];
 #pragma unroll
     for (int j = 0; j < kCtPre; ++j) {
-        const int o = tid + j * kCtThreads;
+        const int o = tid + j * TH;
         pre_sp[j] = pre_y[j] = 0.f;
         if (o < nown) {
             pre_sp[j] = ldf(s + row0 + d_lo + o);
             pre_y[j] = y[row0 + d_lo + o];
         }
     }
-    for (int i = tid; i < nd; i += kCtThreads) zs[i] = ldf(zraw + row0 + i);
-    for (int i = tid; i < HL; i += kCtThreads) {
+    for (int i = tid; i < nd; i += TH) zs[i] = ldf(zraw + row0 + i);
+    for (int i = tid; i < HL; i += TH) {
         const int m = i - 1;
         hs[i] = (m >= 0 && m < 2 * nd - 1) ? hx[m] : 0.f;
     }
     __syncthreads();
-    const int len = (nd + kCtWarps - 1) / kCtWarps;
+    const int len = (nd + W - 1) / W;
     const int dl = d_lo + R * lane;
-    if (w < kCtWarps) {
+    if (w < W) {
         // z = H A x for this CTA's bins, warp w's share of d'
         float acc[R];
         if (dl < d_hi) ct_product<R>(zs, hs, nd, dl, w * len, min(nd, w * len + len), acc);
@@ -317,18 +323,18 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
     unsigned capped = 0;
 #pragma unroll
     for (int j = 0; j < kCtPre; ++j) {
-        const int o = tid + j * kCtThreads;
+        const int o = tid + j * TH;
         if (o < nown) {
             float zi = 0.f;
 #pragma unroll
-            for (int k = 0; k < kCtWarps; ++k) zi += red[k * OUT + o];
+            for (int k = 0; k < W; ++k) zi += red[k * OUT + o];
             float sv;
             acc += (double)output_element(zi, pre_sp[j], pre_y[j], tau_p, inv_tp, logI0, onsager, damp_s, truncate,
                                           capped, sv);
             stf(s + row0 + d_lo + o, sv);
             const float sq = as_stored(sv, s);
 #pragma unroll
-            for (int r = 0; r < kCtCL; ++r) *cluster.map_shared_rank(sf + d_lo + o, r) = sq;
+            for (int r = 0; r < CL; ++r) *cluster.map_shared_rank(sf + d_lo + o, r) = sq;
         }
     }
     capped = warp_sum(capped);
@@ -339,11 +345,11 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
     if (rank == 0 && tid == 0) {
         double t = 0.0;
 #pragma unroll
-        for (int r = 0; r < kCtCL; ++r) t += tsum[r];
+        for (int r = 0; r < CL; ++r) t += tsum[r];
         partial[v] = t;
     }
     // H s for this CTA's bins
-    if (w < kCtWarps) {
+    if (w < W) {
         float a2[R];
         if (dl < d_hi) ct_product<R>(sf, hs, nd, dl, w * len, min(nd, w * len + len), a2);
         else
@@ -353,71 +359,85 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
         for (int k = 0; k < R; ++k) red[w * OUT + R * lane + k] = a2[k];
     }
     __syncthreads();
-    for (int o = tid; o < nown; o += kCtThreads) {
+    for (int o = tid; o < nown; o += TH) {
         float t = 0.f;
 #pragma unroll
-        for (int k = 0; k < kCtWarps; ++k) t += red[k * OUT + o];
+        for (int k = 0; k < W; ++k) t += red[k * OUT + o];
         stf(hsout + row0 + d_lo + o, t);
     }
 }
 
-template <typename T, int R>
-__global__ void __cluster_dims__(kCtCL, 1, 1) __launch_bounds__(kCtThreads)
+template <typename T, int R, int CL, int W>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ct_threads(W))
 k_sino_toeplitz(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __restrict__ hsout, int nd,
                 const float* __restrict__ hx, long long M, int onsager, float damp_s, int truncate, DevScalars* S,
                 double* __restrict__ partial, const double* __restrict__ partial_div, double N, double floor_rel,
                 IterLog* log) {
     extern __shared__ float smf[];
     __shared__ CtShared shd;
-    sino_ct_block<T, R>(zraw, y, s, hsout, nd, hx, M, onsager, damp_s, truncate, S, partial, partial_div, N, floor_rel,
-                        log, (int)blockIdx.x / kCtCL, blockIdx.x == 0, smf, shd);
+    sino_ct_block<T, R, CL, W>(zraw, y, s, hsout, nd, hx, M, onsager, damp_s, truncate, S, partial, partial_div, N,
+                               floor_rel, log, (int)blockIdx.x / CL, blockIdx.x == 0, smf, shd);
 }
 
 // The sinogram step of every slice of a batch in one launch: cluster c
-// (kCtCL CTAs) -> (slice, view); the slices' bins may differ (shared memory
-// is sized for the largest, R chosen for it).
-template <typename T, int R>
-__global__ void __cluster_dims__(kCtCL, 1, 1) __launch_bounds__(kCtThreads)
+// (CL CTAs) -> (slice, view); the slices' bins may differ (the shape, R and
+// the shared memory are those of the largest).
+template <typename T, int R, int CL, int W>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ct_threads(W))
 k_sino_toeplitz_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ map) {
     extern __shared__ float smf[];
     __shared__ CtShared shd;
-    const int c = (int)blockIdx.x / kCtCL;
+    const int c = (int)blockIdx.x / CL;
     __shared__ BatchSlice sd;
     const BatchSlice& B = load_slice(sl, map[c], &sd);
     const int v = c - B.off[kPhView];
-    sino_ct_block<T, R>((const T*)B.zraw, B.y, (T*)B.s, (T*)B.hs, B.nd, B.hx, B.M, B.onsager, B.damp_s, B.truncate,
-                        B.S, B.partial, B.partial_div, (double)B.N, B.tau_x_floor, B.log, v, blockIdx.x == (unsigned)(B.off[kPhView] * kCtCL),
-                        smf, shd);
+    sino_ct_block<T, R, CL, W>((const T*)B.zraw, B.y, (T*)B.s, (T*)B.hs, B.nd, B.hx, B.M, B.onsager, B.damp_s,
+                               B.truncate, B.S, B.partial, B.partial_div, (double)B.N, B.tau_x_floor, B.log, v,
+                               blockIdx.x == (unsigned)(B.off[kPhView] * CL), smf, shd);
 }
 
-static int ct_lanes_r(int nd) {
-    const int per = (nd + kCtCL - 1) / kCtCL;
+// Shape for n_det bins: returns R (bins per lane; 0 = too many bins) and the
+// cluster size in *cl (4 or 8, with 8 or 4 product warps).
+int sino_ct_config(int nd, int* cl) {
+    const int c = nd <= kCtSmallNd ? 4 : 8;
+    const int per = (nd + c - 1) / c;
+    if (cl) *cl = c;
     for (int R = 3; R <= kCtMaxR; R += 2)
         if (32 * R >= per) return R;
     return 0;
 }
 
-static int ct_smem(int nd, int R) { return (2 * nd + ct_hs_len(nd, R) + kCtWarps * 32 * R) * (int)sizeof(float); }
+static int ct_warps(int cl) { return cl == 4 ? 8 : 4; }
 
-int sino_ct_lanes(int nd) { return ct_lanes_r(nd); }
-int sino_ct_smem_bytes(int nd, int R) { return ct_smem(nd, R); }
+static int ct_smem(int nd, int R, int cl) {
+    return (2 * nd + ct_hs_len(nd, R) + ct_warps(cl) * 32 * R) * (int)sizeof(float);
+}
+
+int sino_ct_smem_bytes(int nd, int R, int cl) { return ct_smem(nd, R, cl); }
+
+// one instantiation per (R, shape); F(kernel pointer, threads, cluster size)
+template <typename T, bool BATCH, typename Fn>
+static int ct_dispatch(int R, int cl, Fn&& f) {
+#define DGCT_CT_K(RR, CC, WW)                                                                         \
+    if (R == RR && cl == CC) {                                                                        \
+        if (BATCH) return f((const void*)k_sino_toeplitz_batch<T, RR, CC, WW>, ct_threads(WW), CC);   \
+        return f((const void*)k_sino_toeplitz<T, RR, CC, WW>, ct_threads(WW), CC);                    \
+    }
+    DGCT_CT_K(3, 4, 8) DGCT_CT_K(5, 4, 8) DGCT_CT_K(7, 4, 8)
+    DGCT_CT_K(3, 8, 4) DGCT_CT_K(5, 8, 4) DGCT_CT_K(7, 8, 4)
+#undef DGCT_CT_K
+    return DGAMP_CT_ERR_INVALID_ARG;
+}
 
 template <typename T>
 static int launch_ct_batch(const BatchExec& E, cudaStream_t st) {
-    const unsigned grid = (unsigned)(E.nblk[kPhView] * kCtCL);
     const size_t sm = (size_t)E.ct_smem;
-    if (E.R == 3) {
-        DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz_batch<T, 3>, (int)sm));
-        k_sino_toeplitz_batch<T, 3><<<grid, kCtThreads, sm, st>>>(E.sl, E.map[kPhView]);
-    } else if (E.R == 5) {
-        DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz_batch<T, 5>, (int)sm));
-        k_sino_toeplitz_batch<T, 5><<<grid, kCtThreads, sm, st>>>(E.sl, E.map[kPhView]);
-    } else {
-        DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz_batch<T, 7>, (int)sm));
-        k_sino_toeplitz_batch<T, 7><<<grid, kCtThreads, sm, st>>>(E.sl, E.map[kPhView]);
-    }
-    DGCT_LAUNCH_CHECK();
-    return DGAMP_CT_OK;
+    void* args[] = {(void*)&E.sl, (void*)&E.map[kPhView]};
+    return ct_dispatch<T, true>(E.R, E.cl, [&](const void* k, int threads, int cl) -> int {
+        DGCT_TRY(raise_smem_limit(k, (int)sm));
+        DGCT_CUDA(cudaLaunchKernel(k, dim3((unsigned)(E.nblk[kPhView] * cl)), dim3(threads), args, sm, st));
+        return DGAMP_CT_OK;
+    });
 }
 
 int launch_sino_batch(const BatchExec& E, cudaStream_t st) {
@@ -425,34 +445,39 @@ int launch_sino_batch(const BatchExec& E, cudaStream_t st) {
 }
 
 bool sino_toeplitz_eligible(const dgamp_ct_plan_s* pl) {
-    return ct_lanes_r(pl->nd) > 0 && pl->nv <= pl->max_partials && ct_smem(pl->nd, ct_lanes_r(pl->nd)) <= 200 * 1024;
+    int cl = 0;
+    const int R = sino_ct_config(pl->nd, &cl);
+    return R > 0 && pl->nv <= pl->max_partials && ct_smem(pl->nd, R, cl) <= 200 * 1024;
 }
 
 template <typename T>
-static int launch_ct(const dgamp_ct_plan_s* pl, cudaStream_t st, int R, const T* zraw, T* s, T* hs) {
+static int launch_ct(const dgamp_ct_plan_s* pl, cudaStream_t st, const T* zraw, T* s, T* hs) {
     const Workspace& w = pl->ws;
-    const unsigned grid = (unsigned)(pl->nv * kCtCL);
-    const size_t sm = (size_t)ct_smem(pl->nd, R);
-    const float damp_s = (float)pl->opt.damp_s;
-#define DGCT_CT_ARGS zraw, w.y, s, hs, pl->nd, w.hx, pl->M, pl->opt.onsager, damp_s, pl->opt.truncate_z, w.S, \
-                     w.partial, w.partial_div, (double)pl->N, pl->opt.tau_x_floor, w.log
-    if (R == 3)
-        k_sino_toeplitz<T, 3><<<grid, kCtThreads, sm, st>>>(DGCT_CT_ARGS);
-    else if (R == 5)
-        k_sino_toeplitz<T, 5><<<grid, kCtThreads, sm, st>>>(DGCT_CT_ARGS);
-    else
-        k_sino_toeplitz<T, 7><<<grid, kCtThreads, sm, st>>>(DGCT_CT_ARGS);
-#undef DGCT_CT_ARGS
-    DGCT_LAUNCH_CHECK();
-    return DGAMP_CT_OK;
+    int cl = 0;
+    const int R = sino_ct_config(pl->nd, &cl);
+    const size_t sm = (size_t)ct_smem(pl->nd, R, cl);
+    int nd = pl->nd, onsager = pl->opt.onsager, truncate = pl->opt.truncate_z;
+    long long M = pl->M;
+    float damp_s = (float)pl->opt.damp_s;
+    double N = (double)pl->N, floor_rel = pl->opt.tau_x_floor;
+    const float* y = w.y;
+    const float* hx = w.hx;
+    DevScalars* S = w.S;
+    double* partial = w.partial;
+    const double* partial_div = w.partial_div;
+    IterLog* log = w.log;
+    void* args[] = {(void*)&zraw, (void*)&y, (void*)&s, (void*)&hs, (void*)&nd, (void*)&hx, (void*)&M,
+                    (void*)&onsager, (void*)&damp_s, (void*)&truncate, (void*)&S, (void*)&partial,
+                    (void*)&partial_div, (void*)&N, (void*)&floor_rel, (void*)&log};
+    return ct_dispatch<T, false>(R, cl, [&](const void* k, int threads, int c) -> int {
+        DGCT_CUDA(cudaLaunchKernel(k, dim3((unsigned)(pl->nv * c)), dim3(threads), args, sm, st));
+        return DGAMP_CT_OK;
+    });
 }
 
 template <typename T>
-static int ct_set_limits(int bytes) {
-    DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz<T, 3>, bytes));
-    DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz<T, 5>, bytes));
-    DGCT_TRY(raise_smem_limit((const void*)k_sino_toeplitz<T, 7>, bytes));
-    return DGAMP_CT_OK;
+static int ct_set_limits(int bytes, int R, int cl) {
+    return ct_dispatch<T, false>(R, cl, [&](const void* k, int, int) -> int { return raise_smem_limit(k, bytes); });
 }
 
 static int sino_step_smem(int P) {
@@ -469,9 +494,11 @@ bool sino_step_eligible(const dgamp_ct_plan_s* pl) {
 
 int sino_step_set_smem_limit(const dgamp_ct_plan_s* pl) {
     if (sino_toeplitz_eligible(pl)) {
-        const int bytes = ct_smem(pl->nd, ct_lanes_r(pl->nd));
-        DGCT_TRY(ct_set_limits<float>(bytes));
-        DGCT_TRY(ct_set_limits<bf16s>(bytes));
+        int cl = 0;
+        const int R = sino_ct_config(pl->nd, &cl);
+        const int bytes = ct_smem(pl->nd, R, cl);
+        DGCT_TRY(ct_set_limits<float>(bytes, R, cl));
+        DGCT_TRY(ct_set_limits<bf16s>(bytes, R, cl));
     }
     if (!sino_step_eligible(pl)) return DGAMP_CT_OK;
     // set even at or below 48 KB: the static shared memory of the reduction
@@ -489,9 +516,8 @@ int launch_sino_step(const dgamp_ct_plan_s* pl, cudaStream_t st, int bf) {
     const Workspace& w = pl->ws;
     if (pl->sino_fused == 2) {
         if (!sino_toeplitz_eligible(pl)) return DGAMP_CT_ERR_INVALID_ARG;
-        const int R = ct_lanes_r(pl->nd);
-        if (bf) return launch_ct<bf16s>(pl, st, R, (const bf16s*)w.zraw, (bf16s*)w.s, (bf16s*)w.hs);
-        return launch_ct<float>(pl, st, R, w.zraw, w.s, w.hs);
+        if (bf) return launch_ct<bf16s>(pl, st, (const bf16s*)w.zraw, (bf16s*)w.s, (bf16s*)w.hs);
+        return launch_ct<float>(pl, st, w.zraw, w.s, w.hs);
     }
     if (!sino_step_eligible(pl)) return DGAMP_CT_ERR_INVALID_ARG;
     const int grid = (pl->nv + 1) / 2;
