@@ -58,7 +58,7 @@ FALLBACK_HBM_GBS = 6800.0
 # the configuration captured and the kernels as they were then: the blocked-TV
 # launches of one iteration (10 steps per launch, 64-row regions), the
 # projector (16 step segments) and the tile back-projection.
-TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 64, "bytes_per_iteration": 2117376 + 8431104 + 512}
+TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 64, "tv_vrows": 4, "bytes_per_iteration": 2117376 + 8431104 + 512}
 A_TRAFFIC = {"pj_seg": 16, "bytes_per_launch": 2142208}
 AT_TRAFFIC = {"bp_mode": 1, "bytes_per_launch": 1263872}
 
@@ -736,7 +736,8 @@ def run_gpu(args):
     tv_launches = [k for k in prof if k.startswith("tv_block")]
     tun = plan.tuning()
     traffic = (TV_TRAFFIC["bytes_per_iteration"] if TV_TRAFFIC is not None and
-               (tun["tv_kb"], tun["tv_rows"]) == (TV_TRAFFIC["tv_kb"], TV_TRAFFIC["tv_rows"]) else None)
+               (tun["tv_kb"], tun["tv_rows"], tun["tv_vrows"]) ==
+               (TV_TRAFFIC["tv_kb"], TV_TRAFFIC["tv_rows"], TV_TRAFFIC["tv_vrows"]) else None)
     tv_flop = (19.0 * TV["k_tv"] * 2 + 5.0 * 2) * N
     # ALU peak: the library's FP32 FMA microbenchmark, measured here (TFLOP/s,
     # an FMA = 2 FLOP); the unit-count figure at the sampled clock beside it
@@ -748,7 +749,8 @@ def run_gpu(args):
     tv_tflops = tv_flop / (tv_ms * 1e-3) / 1e12
     tv_bytes = sum(algo[k] for k in tv_launches)
     roof = {"kernel": f"k_tv_steps ({len(tv_launches)} launches per iteration, KB={tun['tv_kb']}, "
-                                f"{tun['tv_rows']} region rows)", "bound": "alu",
+                                f"{tun['tv_rows'] if tun['tv_vrows'] == 4 else 64} region rows, "
+                                f"{tun['tv_vrows']} rows per thread)", "bound": "alu",
             "achieved": tv_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tv_tflops / fp32_peak,
             "traffic": traffic,
             "traffic_note": "DRAM bytes of the TV launches of one iteration (ncu, cold cache), null unless the "

@@ -219,6 +219,9 @@ typedef struct {
                              exact transpose of the projector and deterministic */
     int32_t pj_seg;       /* A: warps that split the step range of one group of 32 rays,
                              8, 16 or 32 (the partial sums are added in a fixed order) */
+    int32_t tv_vrows;     /* rows of the TV region each thread holds: 4, or 8 (then the
+                             region is 64 rows high whatever tv_rows says: half the
+                             threads of the 4-row form, twice the pixels each) */
 } dgamp_ct_tuning;
 
 /* get: writes the plan's choices.  set: fields < 0 keep the current choice;
@@ -350,7 +353,7 @@ int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float*
    number of slices is 6 launches, captured once as a graph and replayed.
    Slice i's result is bit-identical to dgamp_ct_solve on plans[i] with the
    batch's implementation choices (dgamp_ct_tuning pj_seg = 16, bp_mode = 1,
-   sino_fused = 2, tv_kb = 10, tv_rows = 64); each plan's own tuning is not
+   sino_fused = 2, tv_kb = 10, tv_rows = 64, tv_vrows = 4); each plan's own tuning is not
    used here.
    create: n >= 1 distinct parallel-beam plans of the current device with the
    prox-TV denoiser (denoiser = 0, tv_metric = 0, output_moments = 0), one

