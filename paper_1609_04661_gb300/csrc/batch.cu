@@ -140,8 +140,7 @@ namespace dgct {
 // the staged images of x = 0 (zeros, guards included) and the scalars.
 __global__ void __launch_bounds__(256) k_batch_begin(const BatchSlice* __restrict__ sl,
                                                      const uint16_t* __restrict__ map) {
-    __shared__ BatchSlice sd;
-    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
+    const BatchSlice& B = sl[map[blockIdx.x]];
     const long long e = (long long)((int)blockIdx.x - B.off[kPhBegin]) * blockDim.x + threadIdx.x;
     if (e < B.M) {
         B.y[e] = B.counts[e];
@@ -176,8 +175,7 @@ __global__ void k_batch_finish(const BatchSlice* __restrict__ sl) {
 __global__ void __launch_bounds__(512) k_batch_vinv_rows(const BatchSlice* __restrict__ sl,
                                                          const uint16_t* __restrict__ map) {
     extern __shared__ float2 smem[];
-    __shared__ BatchSlice sd;
-    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
+    const BatchSlice& B = sl[map[blockIdx.x]];
     const int iy = (int)blockIdx.x - B.off[kPhRow], n = B.n, m = B.m2;
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
@@ -191,8 +189,7 @@ __global__ void __launch_bounds__(512) k_batch_vinv_rows(const BatchSlice* __res
 __global__ void __launch_bounds__(512) k_batch_vinv_cols(const BatchSlice* __restrict__ sl,
                                                          const uint16_t* __restrict__ map) {
     extern __shared__ float2 smem[];
-    __shared__ BatchSlice sd;
-    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
+    const BatchSlice& B = sl[map[blockIdx.x]];
     const int kx = (int)blockIdx.x - B.off[kPhCol], n = B.n, m = B.m2;
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
@@ -218,8 +215,7 @@ __global__ void __launch_bounds__(512) k_batch_vinv_cols(const BatchSlice* __res
 __global__ void __launch_bounds__(512) k_batch_vinv_rows_inv(const BatchSlice* __restrict__ sl,
                                                              const uint16_t* __restrict__ map) {
     extern __shared__ float2 smem[];
-    __shared__ BatchSlice sd;
-    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
+    const BatchSlice& B = sl[map[blockIdx.x]];
     const int iy = (int)blockIdx.x - B.off[kPhRow], n = B.n, m = B.m2;
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);

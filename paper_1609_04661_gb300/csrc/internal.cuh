@@ -342,6 +342,8 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
                     float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st);
 int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, float* x_out,
               int solve_mode, int t_arg, double* div_out, cudaStream_t st);
+// inside a solve, the first TV launch draws the probe (no k_probe_input launch)
+bool tv_probe_fused(const dgamp_ct_plan_s* pl);
 int launch_probe(const dgamp_ct_plan_s* pl, unsigned t, int64_t n, float* b, uint32_t* words,
                  cudaStream_t st);
 // the TV final step on images the caller has already formed (xbase, nimg of them, [n][n]
@@ -361,20 +363,6 @@ int launch_fan_backproject(const dgamp_ct_plan_s* pl, const float* sino, float* 
 // x, staging, divergence and tau_x from D(r) and J_D(r) b (learned denoiser)
 int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_out, int solve_mode, int t_arg,
                          double* div_out, cudaStream_t st);
-// A block's slice descriptor, copied once into shared memory (every thread
-// takes part; ends with a block barrier), so that the block body reads its
-// fields from shared memory rather than by dependent global loads.
-__device__ __forceinline__ const BatchSlice& load_slice(const BatchSlice* __restrict__ sl, int idx, BatchSlice* sh) {
-    static_assert(sizeof(BatchSlice) % sizeof(int) == 0, "descriptor copied as words");
-    const int* src = reinterpret_cast<const int*>(sl + idx);
-    int* dst = reinterpret_cast<int*>(sh);
-    for (int i = (int)(threadIdx.x + blockDim.x * threadIdx.y); i < (int)(sizeof(BatchSlice) / sizeof(int));
-         i += (int)(blockDim.x * blockDim.y))
-        dst[i] = src[i];
-    __syncthreads();
-    return *sh;
-}
-
 // Batched execution (batch.cu): device descriptors and tables of a batch,
 // and the grid of each phase (blocks; clusters for kPhView)
 struct BatchExec {

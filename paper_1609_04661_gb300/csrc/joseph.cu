@@ -120,8 +120,7 @@ template <typename T, int kPjSeg>
 __global__ void __launch_bounds__(kPjRays * kPjSeg)
 k_project_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ map) {
     __shared__ float red[kPjSeg][kPjRays];
-    __shared__ BatchSlice sd;
-    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
+    const BatchSlice& B = sl[map[blockIdx.x]];
     const int l = (int)blockIdx.x - B.off[kPhProj];
     const int ngx = (B.nd + kPjRays - 1) / kPjRays;
     project_block<T, kPjSeg>((const T*)B.XR, (const T*)B.XC, B.ldp, B.n, B.nd, B.vc, (T*)B.zraw, l % ngx, l / ngx,
@@ -388,8 +387,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBtWarps * 32, 5)
 k_backproject_tile_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ map) {
     __shared__ BtShared sh;
-    __shared__ BatchSlice sd;
-    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
+    const BatchSlice& B = sl[map[blockIdx.x]];
     const int l = (int)blockIdx.x - B.off[kPhBp];
     const int ntx = (B.n + kBtS - 1) / kBtS;
     backproject_tile_block<T>((const T*)B.hs, B.nv, B.nd, B.n, B.vc, B.x, B.r, 1, B.S, B.partial, B.nv, (double)B.M,

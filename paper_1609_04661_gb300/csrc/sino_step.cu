@@ -388,8 +388,7 @@ k_sino_toeplitz_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restr
     extern __shared__ float smf[];
     __shared__ CtShared shd;
     const int c = (int)blockIdx.x / CL;
-    __shared__ BatchSlice sd;
-    const BatchSlice& B = load_slice(sl, map[c], &sd);
+    const BatchSlice& B = sl[map[c]];
     const int v = c - B.off[kPhView];
     sino_ct_block<T, R, CL, W>((const T*)B.zraw, B.y, (T*)B.s, (T*)B.hs, B.nd, B.hx, B.M, B.onsager, B.damp_s,
                                B.truncate, B.S, B.partial, B.partial_div, (double)B.N, B.tau_x_floor, B.log, v,

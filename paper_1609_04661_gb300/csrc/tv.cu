@@ -65,8 +65,7 @@ __global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r
 // r + eps b beside r for every slice of a batch (prox-TV), 256 groups per block.
 __global__ void __launch_bounds__(256) k_probe_input_batch(const BatchSlice* __restrict__ sl,
                                                            const uint16_t* __restrict__ map) {
-    __shared__ BatchSlice sd;
-    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
+    const BatchSlice& B = sl[map[blockIdx.x]];
     const long long g = (long long)((int)blockIdx.x - B.off[kPhProbe]) * blockDim.x + threadIdx.x;
     probe_group(B.r, B.r + B.N, B.b, B.N, B.eps_rel, 0, B.slice_id, B.key, B.S, 0, g);
 }
@@ -130,6 +129,10 @@ struct TvFinal {
     double* div_out;       // nullable
     int solve_mode;        // 1: update tau_x, the log and t in S
     int jvp;               // learned denoiser: dn[1] is J_D b (divergence b^T J_D b / N)
+    int gen_probe;         // first of several step launches in a solve: draw b itself (see tv_steps_block)
+    float eps_rel;         // the MC step's relative size (gen_probe)
+    float* b_out;          // b, written here (gen_probe)
+    float* r2_out;         // r + eps b, the second image's buffer, written here (gen_probe)
 };
 
 // A block holds a region of kTvRW = 64 columns by RH = 4 WY rows of one image
@@ -310,6 +313,21 @@ __device__ __forceinline__ void tv_steps_block(const float* __restrict__ rbase, 
     const int gi0 = by * TH - E, gj0 = bx * TW - E;
     const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
     const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
+    // The probe of Eq. MC_SURE drawn here instead of by k_probe_input (the
+    // first of several step launches of a solve): the second image's blocks
+    // form r + eps b from the first image's r with the same Philox call and
+    // the same fma as k_probe_input, and store b and r + eps b on their
+    // write-back region for the final launch.
+    const bool gen = !FINAL && first && F.gen_probe && im == 1;
+    float eps = 0.f;
+    unsigned tprobe = 0u;
+    if (gen) {
+        eps = F.eps_rel * fmaxf(__uint_as_float(S->rmax_bits), 1e-6f);
+        tprobe = S->t;
+        if (bx == 0 && by == 0 && threadIdx.x == 0) S->eps = (double)eps;
+    }
+    unsigned pg = 0xffffffffu;        // the Philox group held in pb
+    float4 pb = make_float4(0.f, 0.f, 0.f, 0.f);
     float px[V][U], py[V][U], rl[V][U];
     unsigned inside = 0u, lastc = 0u, lastr = 0u;
 #pragma unroll
@@ -323,7 +341,24 @@ __device__ __forceinline__ void tv_steps_block(const float* __restrict__ rbase, 
             float2 p = make_float2(0.f, 0.f);
             if (in) {
                 const size_t o = img + (size_t)gi * n + gj;
-                rv = rbase[o];
+                if (gen) {
+                    const size_t o0 = (size_t)gi * n + gj;
+                    const unsigned g = (unsigned)(o0 >> 2);
+                    if (g != pg) {
+                        pb = probe4(g, tprobe, F.slice, F.key);
+                        pg = g;
+                    }
+                    const unsigned c = (unsigned)(o0 & 3);
+                    const float bv = c == 0 ? pb.x : (c == 1 ? pb.y : (c == 2 ? pb.z : pb.w));
+                    rv = fmaf(eps, bv, rbase[o0]);
+                    const int rr = w * V + v, cc = U * lane + u;
+                    if (rr >= KB && rr < RH - KB && cc >= KB && cc < RW - KB) {
+                        F.b_out[o0] = bv;
+                        F.r2_out[o0] = rv;
+                    }
+                } else {
+                    rv = rbase[o];
+                }
                 if (!first) p = pin[o];
             }
             rl[v][u] = rv * inv_lam;
@@ -443,6 +478,10 @@ __device__ __forceinline__ TvFinal tv_final_of(const BatchSlice& B, int xbf) {
     F.div_out = nullptr;
     F.solve_mode = 1;
     F.jvp = 0;
+    F.gen_probe = 0;     // a batch draws the probe in its own launch
+    F.eps_rel = B.eps_rel;
+    F.b_out = B.b;
+    F.r2_out = B.r + B.N;
     return F;
 }
 
@@ -456,8 +495,7 @@ __global__ void __launch_bounds__(32 * WY)
 k_tv_steps_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ map, int phase, int launch,
                  int xbf) {
     __shared__ TvShared<WY> sh;
-    __shared__ BatchSlice sd;
-    const BatchSlice& B = load_slice(sl, map[blockIdx.x], &sd);
+    const BatchSlice& B = sl[map[blockIdx.x]];
     const int l = (int)blockIdx.x - B.off[phase];
     const int n = B.n;
     const int gx = (n + tv_tile_w<WY, KB, FINAL>() - 1) / tv_tile_w<WY, KB, FINAL>();
@@ -631,7 +669,17 @@ static TvFinal make_tv_final(const dgamp_ct_plan_s* pl, float* x_out, int solve_
     F.div_out = div_out;
     F.solve_mode = solve_mode;
     F.jvp = 0;
+    F.gen_probe = 0;
+    F.eps_rel = (float)pl->opt.eps_rel;
+    F.b_out = pl->ws.b;
+    F.r2_out = pl->ws.r + pl->N;
     return F;
+}
+
+// Inside a solve the prox-TV denoiser's first launch draws the probe itself
+// when there are several step launches (the last one needs b and r + eps b).
+bool tv_probe_fused(const dgamp_ct_plan_s* pl) {
+    return pl->opt.denoiser == 0 && !pl->opt.tv_metric && tv_step_launches(pl, 1, 0.0) >= 2;
 }
 
 int launch_tv_final_x(const dgamp_ct_plan_s* pl, int nimg, const float* xbase, float* x_out, int solve_mode,
@@ -661,7 +709,8 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     const float c_tv = (float)pl->opt.c_tv, lam = (float)lambda_arg;
     if (ns == 0)   // identity denoiser: x = r
         return launch_tv_final_x(pl, nimg, pl->ws.r, x_out, solve_mode, t_arg, div_out, st);
-    const TvFinal F = make_tv_final(pl, x_out, solve_mode, t_arg, div_out);
+    TvFinal F = make_tv_final(pl, x_out, solve_mode, t_arg, div_out);
+    F.gen_probe = (solve_mode && i == 0 && nimg == 2 && tv_probe_fused(pl)) ? 1 : 0;
     const int steps = (i + 1) * KB <= pl->opt.k_tv ? KB : pl->opt.k_tv - i * KB;
     TvLaunch L{n, nimg, i == 0, pl->ws.r, buf[(i + 1) & 1], buf[i & 1], c_tv, lam, from_scalars, pl->ws.S,
                pl->ws.b};
@@ -825,6 +874,10 @@ int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_ou
     F.div_out = div_out;
     F.solve_mode = solve_mode;
     F.jvp = 1;
+    F.gen_probe = 0;
+    F.eps_rel = (float)pl->opt.eps_rel;
+    F.b_out = pl->ws.b;
+    F.r2_out = pl->ws.r + pl->N;
     const int n = pl->n;
     dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
     k_denoise_final<<<grd, 1024, 0, st>>>(dn, pl->ws.b, n, pl->ws.S, F);
