@@ -266,7 +266,7 @@ def _batched(dg, rank, world, dist, flush, steps, learned=False):
         # (groups = 1), and split into groups whose launches run on parallel
         # graph branches
         runs = {}
-        for groups in (1, 2, 4, 8):
+        for groups in sorted({1, 2, 4, 8, 16, len(mine)}):
             with dg.Batch(plans, groups=groups) as bobj:
                 for _ in range(2):
                     bobj.solve(counts, I0, T, mu_out=mus)

@@ -394,16 +394,12 @@ class Plan:
         cnt = C.c_int32()
         _check(self._lib.dgamp_ct_profile_iteration(self._h, int(reps), arr, cap, C.byref(cnt), _stream()),
                "dgamp_ct_profile_iteration")
-        # with prox-TV in several step launches the first one draws the probe
-        tun = self.tuning()
-        tv_launches = -(-k_tv // max(int(tun["tv_kb"]), 1)) if (k_tv > 0 and self.options.c_tv > 0) else 0
-        probe = [] if (self.options.denoiser == 0 and not metric and tv_launches >= 2) else ["probe_input"]
         if self.fan:
-            names = ["vinv_stage_project", "output_step", "backproject", "vinv_update"] + probe
+            names = ["vinv_stage_project", "output_step", "backproject", "vinv_update", "probe_input"]
         else:
-            fused = tun["sino_fused"] and not self.options.output_moments
+            fused = self.tuning()["sino_fused"] and not self.options.output_moments
             sino = ["sino_step"] if fused else ["filter_z", "output_step", "filter_s"]
-            names = ["project"] + sino + ["backproject_update"] + probe
+            names = ["project"] + sino + ["backproject_update", "probe_input"]
         if self.options.denoiser == 1:
             names += ["cnn_pair", "denoise_final"]
         elif metric:

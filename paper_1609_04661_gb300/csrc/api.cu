@@ -271,12 +271,9 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
     DGCT_TRY(launch_backproject(pl, w.hs, w.x, w.r, 1, st, bf,          //         r = x + tau_r A^T H s
                                 fused_sino_now(pl) ? sino_step_partials(pl) : 0));
     }
-    // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r;
-    // the blocked prox-TV draws it in its first launch when it has several
-    if (!tv_probe_fused(pl)) {
-        DGCT_TRY(mark());
-        DGCT_TRY(launch_probe_input(pl, 0, st, pl->opt.denoiser == 1 ? 1 : 0));
-    }
+    DGCT_TRY(mark());
+    // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r
+    DGCT_TRY(launch_probe_input(pl, 0, st, pl->opt.denoiser == 1 ? 1 : 0));
     if (pl->opt.denoiser == 1) {
         // learned denoiser: D(r) and its forward-mode derivative J_D(r) b, then x, D', tau_x
         DGCT_TRY(mark());
@@ -311,14 +308,14 @@ static int front_segments(const dgamp_ct_plan_s* pl) {
 // kernels one iteration launches: Steps 1-3, the probe, the denoiser
 static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
     if (pl->opt.denoiser == 1 && pl->cnn) return front_kernels(pl) + 1 + cnn_launches_per_pair(pl->cnn) + 1;
-    return front_kernels(pl) + (tv_probe_fused(pl) ? 0 : 1) + tv_num_launches(pl, 1, 0.0);
+    return front_kernels(pl) + 1 + tv_num_launches(pl, 1, 0.0);
 }
 
 // timed segments of one iteration (dgamp_ct_profile_iteration): as above,
 // except that the learned denoiser's launches form one segment
 static int segments_per_iteration(const dgamp_ct_plan_s* pl) {
     if (pl->opt.denoiser == 1 && pl->cnn) return front_segments(pl) + 3;
-    return front_segments(pl) + (tv_probe_fused(pl) ? 0 : 1) + tv_num_launches(pl, 1, 0.0);
+    return front_segments(pl) + 1 + tv_num_launches(pl, 1, 0.0);
 }
 
 static void drop_graph(dgamp_ct_plan_s* pl) {

@@ -342,8 +342,6 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
                     float* x_out, int solve_mode, int t_arg, double* div_out, cudaStream_t st);
 int launch_tv(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, float* x_out,
               int solve_mode, int t_arg, double* div_out, cudaStream_t st);
-// inside a solve, the first TV launch draws the probe (no k_probe_input launch)
-bool tv_probe_fused(const dgamp_ct_plan_s* pl);
 int launch_probe(const dgamp_ct_plan_s* pl, unsigned t, int64_t n, float* b, uint32_t* words,
                  cudaStream_t st);
 // the TV final step on images the caller has already formed (xbase, nimg of them, [n][n]

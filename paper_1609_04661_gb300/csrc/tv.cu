@@ -129,10 +129,6 @@ struct TvFinal {
     double* div_out;       // nullable
     int solve_mode;        // 1: update tau_x, the log and t in S
     int jvp;               // learned denoiser: dn[1] is J_D b (divergence b^T J_D b / N)
-    int gen_probe;         // first of several step launches in a solve: draw b itself (see tv_steps_block)
-    float eps_rel;         // the MC step's relative size (gen_probe)
-    float* b_out;          // b, written here (gen_probe)
-    float* r2_out;         // r + eps b, the second image's buffer, written here (gen_probe)
 };
 
 // A block holds a region of kTvRW = 64 columns by RH = 4 WY rows of one image
@@ -313,21 +309,6 @@ __device__ __forceinline__ void tv_steps_block(const float* __restrict__ rbase, 
     const int gi0 = by * TH - E, gj0 = bx * TW - E;
     const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
     const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
-    // The probe of Eq. MC_SURE drawn here instead of by k_probe_input (the
-    // first of several step launches of a solve): the second image's blocks
-    // form r + eps b from the first image's r with the same Philox call and
-    // the same fma as k_probe_input, and store b and r + eps b on their
-    // write-back region for the final launch.
-    const bool gen = !FINAL && first && F.gen_probe && im == 1;
-    float eps = 0.f;
-    unsigned tprobe = 0u;
-    if (gen) {
-        eps = F.eps_rel * fmaxf(__uint_as_float(S->rmax_bits), 1e-6f);
-        tprobe = S->t;
-        if (bx == 0 && by == 0 && threadIdx.x == 0) S->eps = (double)eps;
-    }
-    unsigned pg = 0xffffffffu;        // the Philox group held in pb
-    float4 pb = make_float4(0.f, 0.f, 0.f, 0.f);
     float px[V][U], py[V][U], rl[V][U];
     unsigned inside = 0u, lastc = 0u, lastr = 0u;
 #pragma unroll
@@ -341,24 +322,7 @@ __device__ __forceinline__ void tv_steps_block(const float* __restrict__ rbase, 
             float2 p = make_float2(0.f, 0.f);
             if (in) {
                 const size_t o = img + (size_t)gi * n + gj;
-                if (gen) {
-                    const size_t o0 = (size_t)gi * n + gj;
-                    const unsigned g = (unsigned)(o0 >> 2);
-                    if (g != pg) {
-                        pb = probe4(g, tprobe, F.slice, F.key);
-                        pg = g;
-                    }
-                    const unsigned c = (unsigned)(o0 & 3);
-                    const float bv = c == 0 ? pb.x : (c == 1 ? pb.y : (c == 2 ? pb.z : pb.w));
-                    rv = fmaf(eps, bv, rbase[o0]);
-                    const int rr = w * V + v, cc = U * lane + u;
-                    if (rr >= KB && rr < RH - KB && cc >= KB && cc < RW - KB) {
-                        F.b_out[o0] = bv;
-                        F.r2_out[o0] = rv;
-                    }
-                } else {
-                    rv = rbase[o];
-                }
+                rv = rbase[o];
                 if (!first) p = pin[o];
             }
             rl[v][u] = rv * inv_lam;
@@ -478,10 +442,6 @@ __device__ __forceinline__ TvFinal tv_final_of(const BatchSlice& B, int xbf) {
     F.div_out = nullptr;
     F.solve_mode = 1;
     F.jvp = 0;
-    F.gen_probe = 0;     // a batch draws the probe in its own launch
-    F.eps_rel = B.eps_rel;
-    F.b_out = B.b;
-    F.r2_out = B.r + B.N;
     return F;
 }
 
@@ -669,17 +629,7 @@ static TvFinal make_tv_final(const dgamp_ct_plan_s* pl, float* x_out, int solve_
     F.div_out = div_out;
     F.solve_mode = solve_mode;
     F.jvp = 0;
-    F.gen_probe = 0;
-    F.eps_rel = (float)pl->opt.eps_rel;
-    F.b_out = pl->ws.b;
-    F.r2_out = pl->ws.r + pl->N;
     return F;
-}
-
-// Inside a solve the prox-TV denoiser's first launch draws the probe itself
-// when there are several step launches (the last one needs b and r + eps b).
-bool tv_probe_fused(const dgamp_ct_plan_s* pl) {
-    return pl->opt.denoiser == 0 && !pl->opt.tv_metric && tv_step_launches(pl, 1, 0.0) >= 2;
 }
 
 int launch_tv_final_x(const dgamp_ct_plan_s* pl, int nimg, const float* xbase, float* x_out, int solve_mode,
@@ -709,8 +659,7 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     const float c_tv = (float)pl->opt.c_tv, lam = (float)lambda_arg;
     if (ns == 0)   // identity denoiser: x = r
         return launch_tv_final_x(pl, nimg, pl->ws.r, x_out, solve_mode, t_arg, div_out, st);
-    TvFinal F = make_tv_final(pl, x_out, solve_mode, t_arg, div_out);
-    F.gen_probe = (solve_mode && i == 0 && nimg == 2 && tv_probe_fused(pl)) ? 1 : 0;
+    const TvFinal F = make_tv_final(pl, x_out, solve_mode, t_arg, div_out);
     const int steps = (i + 1) * KB <= pl->opt.k_tv ? KB : pl->opt.k_tv - i * KB;
     TvLaunch L{n, nimg, i == 0, pl->ws.r, buf[(i + 1) & 1], buf[i & 1], c_tv, lam, from_scalars, pl->ws.S,
                pl->ws.b};
@@ -874,10 +823,6 @@ int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_ou
     F.div_out = div_out;
     F.solve_mode = solve_mode;
     F.jvp = 1;
-    F.gen_probe = 0;
-    F.eps_rel = (float)pl->opt.eps_rel;
-    F.b_out = pl->ws.b;
-    F.r2_out = pl->ws.r + pl->N;
     const int n = pl->n;
     dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
     k_denoise_final<<<grd, 1024, 0, st>>>(dn, pl->ws.b, n, pl->ws.S, F);

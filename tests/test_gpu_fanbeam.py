@@ -100,7 +100,7 @@ def test_fan_solve_matches_oracle(dg):
             pl.filter(torch.zeros((c["n_views"], c["n_det"]), device="cuda"))
     assert st["iters_done"] == T
     assert rel(host(mu), ref) < 1e-3
-    assert list(prof)[:4] == ["vinv_stage_project", "output_step", "backproject", "vinv_update"]
+    assert list(prof)[:5] == ["vinv_stage_project", "output_step", "backproject", "vinv_update", "probe_input"]
 
 
 def _golden_frobenius(name):
