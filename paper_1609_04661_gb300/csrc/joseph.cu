@@ -87,7 +87,7 @@ __device__ __forceinline__ void project_block(const T* __restrict__ XR, const T*
         if (s0 <= s1) {
             long long pos = joseph_pos(c, d, s0);
             const T* __restrict__ line = B + (size_t)s0 * ldp + kPad;
-#pragma unroll 8
+#pragma unroll 4
             for (int s = s0; s <= s1; ++s, pos += c.PSTEP, line += ldp) {
                 int i0;
                 float f;
