@@ -15,12 +15,13 @@
 //
 // The 64 -> 64 layers (forward, input gradient and forward-mode tangent) are
 // implicit GEMMs on the tcgen05 tensor cores with TMEM accumulators
-// (conv_tc.cu).  The weight gradient (M = 64 co, N = 64 ci per tap, K =
-// pixels, mma.sync m16n8k16 BF16) writes per-block FP32 partials that a
-// second kernel adds in a fixed order.  The first (1 -> 64) and last
+// (conv_tc.cu), and so is their weight gradient (M = 64 co, N = 64 ci per
+// tap, K = pixels), which writes per-CTA FP32 partials that a second kernel
+// adds in a fixed order.  The first (1 -> 64) and last
 // (64 -> 1) layers are small and run on the CUDA cores.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -32,34 +33,9 @@ namespace dgct {
 
 constexpr int CH = 64;          // hidden channels
 constexpr int KW = 9 * CH;      // GEMM K of a hidden layer (576)
-constexpr int TH = 8, TWD = 16; // pixel tile of the weight-gradient kernel (128 pixels)
 constexpr int PSTR = 72;        // shared-memory stride (bf16) of one pixel's 64 channels
-constexpr int CONV_THREADS = 128;
 
 typedef __nv_bfloat16 bf16;
-
-// ------------------------------------------------------------ PTX helpers --
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma16816(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
 
 // ---------------------------------------------------------- first layer --
 // a1 = relu(b0 + conv(u, W0)), u = r / sigma; also stores u for the weight gradient.
@@ -243,70 +219,6 @@ __global__ void k_dgrad_last(const float* __restrict__ gout, const float* __rest
 }
 
 // ----------------------------------------------------- weight gradients --
-// Hidden layer: partial[group][tap][co][ci] = sum over the group's pixels of
-// g[p][co] * a[p + off(tap)][ci] (tensor cores: M = co, N = ci, K = pixels).
-__global__ void __launch_bounds__(CONV_THREADS)
-k_wgrad64(const bf16* __restrict__ a, const bf16* __restrict__ g, int B, int H, int W, int ngroups,
-          float* __restrict__ partial) {
-    __shared__ __align__(16) bf16 sg[TH * TWD * PSTR];
-    __shared__ __align__(16) bf16 sa[TH * TWD * PSTR];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int q = lane >> 3, j = lane & 7, gid = lane >> 2, tig = lane & 3;
-    const int tap = blockIdx.y, dy = tap / 3 - 1, dx = tap % 3 - 1;
-    const int group = blockIdx.x;
-    const int tiles_x = (W + TWD - 1) / TWD, tiles_y = (H + TH - 1) / TH;
-    const int ntiles = B * tiles_x * tiles_y;
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
-    for (int tile = group; tile < ntiles; tile += ngroups) {
-        const int b = tile / (tiles_x * tiles_y);
-        const int rem = tile - b * tiles_x * tiles_y;
-        const int y0 = (rem / tiles_x) * TH, x0 = (rem - (rem / tiles_x) * tiles_x) * TWD;
-        __syncthreads();
-        for (int i = tid; i < TH * TWD * 8; i += CONV_THREADS) {
-            const int pix = i >> 3, c = i & 7;
-            const int y = y0 + pix / TWD, x = x0 + pix % TWD;
-            uint4 gv = make_uint4(0u, 0u, 0u, 0u), av = make_uint4(0u, 0u, 0u, 0u);
-            if (y < H && x < W) {
-                gv = *reinterpret_cast<const uint4*>(g + (((long long)b * H + y) * W + x) * CH + c * 8);
-                const int yy = y + dy, xx = x + dx;
-                if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    av = *reinterpret_cast<const uint4*>(a + (((long long)b * H + yy) * W + xx) * CH + c * 8);
-            }
-            *reinterpret_cast<uint4*>(sg + pix * PSTR + c * 8) = gv;
-            *reinterpret_cast<uint4*>(sa + pix * PSTR + c * 8) = av;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < TH * TWD / 16; ++ks) {
-            // A[m = co][k = pixel]: stored [pixel][co] -> transposed load
-            uint32_t a0, a1, a2, a3;
-            ldsm_x4_t(a0, a1, a2, a3, sg + (ks * 16 + j + 8 * (q >> 1)) * PSTR + warp * 16 + 8 * (q & 1));
-#pragma unroll
-            for (int np = 0; np < 4; ++np) {
-                // B[k = pixel][n = ci]: stored [pixel][ci] -> transposed load
-                uint32_t b0, b1, b2, b3;
-                ldsm_x4_t(b0, b1, b2, b3, sa + (ks * 16 + j + 8 * (q & 1)) * PSTR + np * 16 + 8 * (q >> 1));
-                mma16816(acc[2 * np], a0, a1, a2, a3, b0, b1);
-                mma16816(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
-            }
-        }
-    }
-    float* out = partial + ((size_t)group * 9 + tap) * CH * CH;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const int ci = nt * 8 + 2 * tig;
-        const int co = warp * 16 + gid;
-        out[co * CH + ci] = acc[nt][0];
-        out[co * CH + ci + 1] = acc[nt][1];
-        out[(co + 8) * CH + ci] = acc[nt][2];
-        out[(co + 8) * CH + ci + 1] = acc[nt][3];
-    }
-}
-
 // grad W (reference layout [tap][ci][co]) = sum over groups of partial[group][tap][co][ci]
 __global__ void k_reduce_wgrad64(const float* __restrict__ partial, int ngroups, float* __restrict__ gw) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;     // index in [tap][ci][co]
@@ -513,6 +425,7 @@ struct dgamp_ct_cnn_s {
 };
 
 static int kGroups = 32;
+constexpr int kWgGroupsMax = 64;   // most CTA groups of the tensor-core weight gradient
 
 static void cnn_free_ws(dgamp_ct_cnn_s* c) {
     void* ptrs[] = {c->act, c->g0, c->g1, c->f, c->gout, c->partial, c->dpart, c->loss, c->sig_buf};
@@ -543,7 +456,8 @@ static int cnn_ensure_ws(dgamp_ct_cnn_s* c, int64_t npix, int nstore, int batch)
     if ((rc = A((void**)&c->g1, (size_t)cap * CH * sizeof(bf16))) != DGAMP_CT_OK) return rc;
     if ((rc = A((void**)&c->f, (size_t)cap * sizeof(float))) != DGAMP_CT_OK) return rc;
     if ((rc = A((void**)&c->gout, (size_t)cap * sizeof(float))) != DGAMP_CT_OK) return rc;
-    if ((rc = A((void**)&c->partial, (size_t)kGroups * 9 * CH * CH * sizeof(float))) != DGAMP_CT_OK) return rc;
+    const size_t wg_groups = (size_t)(kGroups > kWgGroupsMax ? kGroups : kWgGroupsMax);
+    if ((rc = A((void**)&c->partial, wg_groups * 9 * CH * CH * sizeof(float))) != DGAMP_CT_OK) return rc;
     if ((rc = A((void**)&c->dpart, 1024 * sizeof(double))) != DGAMP_CT_OK) return rc;
     if ((rc = A((void**)&c->loss, sizeof(double))) != DGAMP_CT_OK) return rc;
     if ((rc = A((void**)&c->sig_buf, (size_t)cb * sizeof(float))) != DGAMP_CT_OK) return rc;
@@ -592,6 +506,9 @@ static int cnn_backward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int
     auto act = [&](int l) -> bf16* { return c->act + (size_t)(l - 1) * c->cap_pix * CH; };
     const unsigned blocks = (unsigned)((npix + 127) / 128);
     const int G = kGroups;
+    // CTA groups of the hidden layers' weight gradient: 3 CTAs (one per tap
+    // row) per group, about one CTA per SM
+    const int Gw = std::max(1, std::min(kWgGroupsMax, c->sm_count / 3));
     // last layer weights and bias
     k_wgrad_last<<<G, 256, 0, st>>>(act(L - 1), c->gout, B, H, W, G, c->partial);
     DGCT_LAUNCH_CHECK();
@@ -608,9 +525,8 @@ static int cnn_backward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int
     DGCT_LAUNCH_CHECK();
     for (int l = L - 2; l >= 1; --l) {
         // layer l maps a_l -> z_{l+1}; gcur = dL/dz_{l+1}
-        k_wgrad64<<<dim3(G, 9), CONV_THREADS, 0, st>>>(act(l), gcur, B, H, W, G, c->partial);
-        DGCT_LAUNCH_CHECK();
-        k_reduce_wgrad64<<<(9 * CH * CH + 255) / 256, 256, 0, st>>>(c->partial, G, c->grad + c->w_off[l]);
+        DGCT_TRY(launch_wgrad64_tc(act(l), gcur, B, H, W, Gw, c->partial, c->tc_err, st, c->stall_ns));
+        k_reduce_wgrad64<<<(9 * CH * CH + 255) / 256, 256, 0, st>>>(c->partial, Gw, c->grad + c->w_off[l]);
         DGCT_LAUNCH_CHECK();
         k_bias_partial<<<G, 256, 0, st>>>(gcur, npix, G, c->partial);
         DGCT_LAUNCH_CHECK();

@@ -408,6 +408,184 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
     }
 }
 
+// ---------------------------------------------------- weight gradient ----
+// partial[group][tap][co][ci] = sum over the group's pixels p of
+//   g[p][co] a[p + (dy - 1, dx - 1)][ci],   tap = 3 dy + dx,
+// a GEMM per tap with M = 64 output channels, N = 64 input channels and the
+// pixels as K.  Both operands lie pixel-major in global memory (one pixel's
+// 64 channels = one 128-byte row), which read with pixels as K is the
+// MN-major operand layout with the 128-byte swizzle: the same TMA copies as
+// the forward kernel's (a strip of 128 gradient pixels, a halo row of 130
+// activation pixels) feed the MMAs with no transposition, and the three dx
+// taps of a row start 0, 1 and 2 pixel rows into the halo row.
+//
+// CTA (group, dy) takes a contiguous range of strips and accumulates taps
+// (dy, 0..2) over all of them in tensor memory: three 64-column FP32
+// accumulators.  With M = 64 the accumulator's row m lies in TMEM lane
+// 32 (m / 16) + m % 16 (the first 16 lanes of each quarter); the four
+// warps read their quarters once, at the end.  Warp 0 (one lane) loads
+// strips into a ring of WG_STAGES stages, warp 1 (one lane) issues 3 x 8
+// MMAs per strip and releases the stage with a commit.
+constexpr int WG_G_BYTES = M * 128;                    // 128 gradient pixels
+constexpr int WG_STAGE = WG_G_BYTES + A_ROW;           // + one halo row slot (136 pixels)
+constexpr int WG_STAGES = 5;
+constexpr int WG_SMEM = 1024 + WG_STAGES * WG_STAGE;
+constexpr int WG_THREADS = 128;
+constexpr unsigned WG_TMEM_COLS = 256;                 // three 64-column accumulators
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both MN-major, N = 64, M = 64
+constexpr uint32_t IDESC_WG = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                              ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16_wg(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(d_tmem), "l"(a), "l"(b), "r"(IDESC_WG), "r"(accumulate));
+}
+
+// MN-major operand, 128-byte swizzle, 64 elements along M or N (one swizzle
+// atom, so the leading-dimension offset is not used): rows of 128 bytes are
+// successive K (pixels), 8-row groups 1024 bytes apart.  The swizzle follows
+// the absolute shared-memory address, as the TMA wrote it, so the start may
+// move by whole rows.
+__device__ __forceinline__ uint64_t sdesc_sw128_mn(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
+__global__ void __launch_bounds__(WG_THREADS, 1)
+k_wgrad64_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_g, int B, int H,
+             int W, int per, float* __restrict__ partial, unsigned* err, unsigned long long stall_ns) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[WG_STAGES];
+    __shared__ __align__(8) uint64_t empty[WG_STAGES];
+    __shared__ __align__(8) uint64_t acc_full;
+    __shared__ __align__(8) uint64_t never_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int stalled;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int group = blockIdx.x, dy = blockIdx.y;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t s_base = (raw + 1023u) & ~1023u;
+    const int nx = (W + M - 1) / M;
+    const int nstrips = B * H * nx;
+    const int s0 = group * per;
+    const int s1 = s0 + per < nstrips ? s0 + per : nstrips;
+    float* out = partial + ((size_t)group * 9 + 3 * dy) * CH * CH;
+    if (s0 >= s1) {   // no strips: zero partials
+        for (int i = tid; i < 3 * CH * CH; i += WG_THREADS) out[i] = 0.f;
+        return;
+    }
+    const int nk = s1 - s0;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(WG_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < WG_STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(&acc_full), 1);
+        mbar_init(smem_u32(&never_bar), 1);
+        stalled = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_slot;
+    bool run = true;   // false only in the timeout test: nothing is issued
+    if (stall_ns) {
+        if (tid == 0 && !mbar_wait(smem_u32(&never_bar), 0u, stall_ns)) stalled = 1;
+        __syncthreads();
+        run = stalled == 0;
+    }
+    bool ok = run;
+    if (run && warp == 0 && lane == 0) {
+        // ---- TMA producer ----
+        int k = 0;
+        for (; k < nk; ++k) {
+            const int st = k % WG_STAGES;
+            if (k >= WG_STAGES && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((k / WG_STAGES - 1) & 1))) {
+                ok = false;
+                break;
+            }
+            const Strip t = strip_of(s0 + k, H, nx);
+            const uint32_t sg = s_base + (uint32_t)(st * WG_STAGE), sa = sg + WG_G_BYTES;
+            const uint32_t bar = smem_u32(&full[st]);
+            mbar_expect_tx(bar, WG_G_BYTES + ROW_BYTES);
+            tma_4d(sg, &map_g, 0, t.x0, t.y, t.b, bar);
+            tma_4d(sa, &map_a, 0, t.x0 - 1, t.y + dy - 1, t.b, bar);
+        }
+        // every copy issued has landed before the CTA may exit (bounded)
+        for (int j = (k > WG_STAGES ? k - WG_STAGES : 0); j < k; ++j)
+            if (!mbar_wait(smem_u32(&full[j % WG_STAGES]), (uint32_t)((j / WG_STAGES) & 1))) ok = false;
+    } else if (run && warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        for (int k = 0; k < nk; ++k) {
+            const int st = k % WG_STAGES;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((k / WG_STAGES) & 1))) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const uint32_t sg = s_base + (uint32_t)(st * WG_STAGE), sa = sg + WG_G_BYTES;
+            const uint64_t gd = sdesc_sw128_mn(sg), ad = sdesc_sw128_mn(sa);
+#pragma unroll
+            for (int ks = 0; ks < M / 16; ++ks) {
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    // 16 pixels (rows) per MMA; tap dx reads the halo row dx rows later
+                    mma_bf16_wg(tmem + (uint32_t)(dx * 64), gd + (uint64_t)((ks * 16 * 128) >> 4),
+                                ad + (uint64_t)(((ks * 16 + dx) * 128) >> 4), (k | ks) != 0 ? 1u : 0u);
+                }
+            }
+            mma_commit(smem_u32(&empty[st]));
+        }
+        // arrives once every MMA issued above has completed
+        mma_commit(smem_u32(&acc_full));
+    }
+    __syncwarp();
+    // ---- epilogue: all four warps, once ----
+    if (run) {
+        int got = 0;
+        if (lane == 0) got = mbar_wait(smem_u32(&acc_full), 0u) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) {
+            ok = false;
+        } else {
+            fence_after();
+            const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+            const int co = warp * 16 + lane;     // lanes 0..15 hold rows 16 warp .. + 15
+#pragma unroll 1
+            for (int c = 0; c < 3 * 64; c += 16) {
+                float v[16];
+                tmem_ld16(tmem + lane_base + (uint32_t)c, v);   // warp-collective
+                if (lane < 16) {
+                    const int tap = c >> 6, ci = c & 63;
+                    float4* dst = reinterpret_cast<float4*>(out + ((size_t)tap * CH + co) * CH + ci);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+            }
+        }
+    }
+    if (!ok && (run || tid == 0)) atomicOr(err, 1u);
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(WG_TMEM_COLS)
+                     : "memory");
+    }
+}
+
 }  // namespace tc
 }  // namespace dgct
 
@@ -416,6 +594,7 @@ namespace dgct {
 int conv64_tc_init() {
     DGCT_CUDA(cudaFuncSetAttribute(tc::k_conv64_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
     DGCT_CUDA(cudaFuncSetAttribute(tc::k_conv64_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
+    DGCT_CUDA(cudaFuncSetAttribute(tc::k_wgrad64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::WG_SMEM));
     return DGAMP_CT_OK;
 }
 
@@ -480,6 +659,35 @@ int launch_conv64_tc(int mode, const void* in, const void* wk_all, int layers, i
     else
         tc::k_conv64_tc<1><<<grid, tc::THREADS, tc::SMEM, st>>>(map_in, map_w, layer, bias, (const bf16*)mask,
                                                                 (bf16*)out, B, H, W, per, err, stall_ns);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// a: the layer's input activations, g: the gradient at its output, both
+// [B][H][W][64] BF16; partial: [groups][9][64 co][64 ci] FP32, every group
+// written (zeros for a group without strips).
+int launch_wgrad64_tc(const void* a, const void* g, int B, int H, int W, int groups, float* partial, unsigned* err,
+                      cudaStream_t st, unsigned long long stall_ns) {
+    if (groups < 1) return DGAMP_CT_ERR_INVALID_ARG;
+    const long long nstrips = (long long)B * H * ((W + tc::M - 1) / tc::M);
+    if (nstrips <= 0) {
+        DGCT_CUDA(cudaMemsetAsync(partial, 0, (size_t)groups * 9 * 64 * 64 * sizeof(float), st));
+        return DGAMP_CT_OK;
+    }
+    CUtensorMap map_a, map_g;
+    const cuuint64_t dims[4] = {64, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {128, (cuuint64_t)W * 128, (cuuint64_t)H * W * 128};
+    {
+        const cuuint32_t box[4] = {64, (cuuint32_t)tc::HWL, 1, 1};
+        DGCT_TRY(encode(&map_a, 4, a, dims, strides, box));
+    }
+    {
+        const cuuint32_t box[4] = {64, (cuuint32_t)tc::M, 1, 1};
+        DGCT_TRY(encode(&map_g, 4, g, dims, strides, box));
+    }
+    const int per = (int)((nstrips + groups - 1) / groups);
+    tc::k_wgrad64_tc<<<dim3(groups, 3), tc::WG_THREADS, tc::WG_SMEM, st>>>(map_a, map_g, B, H, W, per, partial, err,
+                                                                          stall_ns);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }
