@@ -219,106 +219,152 @@ __global__ void k_dgrad_last(const float* __restrict__ gout, const float* __rest
 }
 
 // ----------------------------------------------------- weight gradients --
-// grad W (reference layout [tap][ci][co]) = sum over groups of partial[group][tap][co][ci]
+// All parameter gradients are sums over the batch's pixels.  Each kernel below
+// sums a fixed range of pixels per block in FP32 (a thread's pixels, then the
+// block's threads in a fixed tree) and writes one row of FP32 partials; a
+// second kernel adds the rows in a fixed order.  Nothing depends on timing, so
+// the gradients are reproducible run to run.
+
+// grad W (reference layout [tap][ci][co]) = sum over groups of
+// partial[group][tap][ci][co] (the tensor-core kernel's layout)
 __global__ void k_reduce_wgrad64(const float* __restrict__ partial, int ngroups, float* __restrict__ gw) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;     // index in [tap][ci][co]
     if (i >= 9 * CH * CH) return;
-    const int tap = i / (CH * CH), ci = (i / CH) % CH, co = i % CH;
-    double s = 0.0;
-    for (int gq = 0; gq < ngroups; ++gq) s += partial[((size_t)gq * 9 + tap) * CH * CH + co * CH + ci];
-    gw[i] = (float)s;
+    float s = 0.f;
+    for (int gq = 0; gq < ngroups; ++gq) s += partial[(size_t)gq * 9 * CH * CH + i];
+    gw[i] = s;
 }
 
-// per-group partial sums of a [npix][64] bf16 tensor over pixels (bias gradient)
-__global__ void k_bias_partial(const bf16* __restrict__ g, long long npix, int ngroups, float* __restrict__ partial) {
-    const int c = threadIdx.x & 63, sub = threadIdx.x >> 6, nsub = blockDim.x >> 6;
-    double s = 0.0;
-    for (long long p = (long long)blockIdx.x * nsub + sub; p < npix; p += (long long)ngroups * nsub)
-        s += (double)__bfloat162float(g[p * CH + c]);
-    __shared__ double sm[16][CH];
-    sm[sub][c] = s;
+// out[col] = sum over rows of partial[row][col]: one warp per column, the
+// lanes' strided sums then a butterfly (the same order every run)
+__global__ void k_reduce_cols(const float* __restrict__ partial, int nrows, int width, float* __restrict__ out) {
+    const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (col >= width) return;
+    float s = 0.f;
+    for (int r = lane; r < nrows; r += 32) s += partial[(size_t)r * width + col];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[col] = s;
+}
+
+// Blocks of the pixel-sum kernels: about 256 pixels each, at most kColBlocks.
+constexpr int kColBlocks = 1024;
+static int col_blocks(long long npix) {
+    const long long b = (npix + 255) / 256;
+    return (int)std::min<long long>(std::max<long long>(b, 1), kColBlocks);
+}
+
+// Thread layout of the pixel-sum kernels (256 threads): thread t takes the
+// 8 channels 8 (t % 8) .. + 7 of every 32nd pixel of the block's range,
+// starting at pixel t / 8; a warp holds 4 pixel lanes, summed by shuffles
+// across lanes 8 and 16 apart, then the 8 warps through shared memory.
+template <int NV>
+__device__ __forceinline__ void block_colsum(float (&s)[NV][8], float (*sm)[NV * CH], float* __restrict__ out) {
+    const int cg = threadIdx.x & 7, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            s[v][k] += __shfl_xor_sync(0xffffffffu, s[v][k], 8);
+            s[v][k] += __shfl_xor_sync(0xffffffffu, s[v][k], 16);
+        }
+    if (lane < 8)
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sm[warp][v * CH + cg * 8 + k] = s[v][k];
     __syncthreads();
-    if (sub == 0) {
-        double t = 0.0;
-        for (int k = 0; k < nsub; ++k) t += sm[k][c];
-        partial[blockIdx.x * CH + c] = (float)t;
+    for (int i = threadIdx.x; i < NV * CH; i += blockDim.x) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += sm[w][i];
+        out[i] = t;
     }
 }
 
-__global__ void k_reduce_rows(const float* __restrict__ partial, int ngroups, int width, float* __restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= width) return;
-    double s = 0.0;
-    for (int gq = 0; gq < ngroups; ++gq) s += partial[(size_t)gq * width + i];
-    out[i] = (float)s;
+__device__ __forceinline__ void unpack8(const uint4& v, float* f) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 t = __bfloat1622float2(h[k]);
+        f[2 * k] = t.x;
+        f[2 * k + 1] = t.y;
+    }
 }
 
-// First layer: partial[group][tap*64 + co] = sum_p u[p + off(tap)] g1[p][co];
-// partial[group][9*64 + co] = sum_p g1[p][co].  u is the scaled input r/sigma.
-__global__ void k_wgrad_first(const float* __restrict__ r, const float* __restrict__ sigma, const bf16* __restrict__ g1,
-                              int B, int H, int W, int ngroups, float* __restrict__ partial) {
-    const int c = threadIdx.x & 63, sub = threadIdx.x >> 6, nsub = blockDim.x >> 6;
-    const long long HW = (long long)H * W, npix = B * HW;
-    double s[10];
+// bias gradient: partial[block][c] = sum over the block's pixels of g[p][c]
+__global__ void __launch_bounds__(256) k_bias_partial(const bf16* __restrict__ g, long long npix, long long per,
+                                                      float* __restrict__ partial) {
+    __shared__ float sm[8][CH];
+    const int cg = threadIdx.x & 7, pl = threadIdx.x >> 3;
+    const long long p0 = (long long)blockIdx.x * per, p1 = std::min(p0 + per, npix);
+    float s[1][8] = {};
+    for (long long p = p0 + pl; p < p1; p += 32) {
+        float f[8];
+        unpack8(*reinterpret_cast<const uint4*>(g + p * CH + cg * 8), f);
 #pragma unroll
-    for (int t = 0; t < 10; ++t) s[t] = 0.0;
-    for (long long p = (long long)blockIdx.x * nsub + sub; p < npix; p += (long long)ngroups * nsub) {
+        for (int k = 0; k < 8; ++k) s[0][k] += f[k];
+    }
+    block_colsum<1>(s, sm, partial + (size_t)blockIdx.x * CH);
+}
+
+// First layer: partial[block][tap*64 + co] = sum_p u[p + off(tap)] g1[p][co];
+// partial[block][9*64 + co] = sum_p g1[p][co].  u is the scaled input r/sigma.
+__global__ void __launch_bounds__(256) k_wgrad_first(const float* __restrict__ r, const float* __restrict__ sigma,
+                                                     const bf16* __restrict__ g1, int B, int H, int W, long long per,
+                                                     float* __restrict__ partial) {
+    __shared__ float sm[8][10 * CH];
+    const int cg = threadIdx.x & 7, pl = threadIdx.x >> 3;
+    const long long HW = (long long)H * W, npix = B * HW;
+    const long long p0 = (long long)blockIdx.x * per, p1 = std::min(p0 + per, npix);
+    float s[10][8] = {};
+    for (long long p = p0 + pl; p < p1; p += 32) {
         const int b = (int)(p / HW);
         const int y = (int)((p - b * HW) / W), x = (int)(p - b * HW - (long long)y * W);
-        const float gv = __bfloat162float(g1[p * CH + c]);
         const float inv = 1.0f / sigma[b];
+        float gv[8];
+        unpack8(*reinterpret_cast<const uint4*>(g1 + p * CH + cg * 8), gv);
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-            if (yy >= 0 && yy < H && xx >= 0 && xx < W) s[t] += (double)(r[b * HW + (long long)yy * W + xx] * inv) * gv;
-        }
-        s[9] += gv;
-    }
-    __shared__ double sm[4][10 * CH];          // launched with 256 threads: 4 pixel lanes x 64 channels
+            const float u = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? r[b * HW + (long long)yy * W + xx] * inv : 0.f;
 #pragma unroll
-    for (int t = 0; t < 10; ++t) sm[sub][t * CH + c] = s[t];
-    __syncthreads();
-    if (sub == 0)
-        for (int t = 0; t < 10; ++t) {
-            double v = 0.0;
-            for (int k = 0; k < nsub; ++k) v += sm[k][t * CH + c];
-            partial[(size_t)blockIdx.x * 10 * CH + t * CH + c] = (float)v;
+            for (int k = 0; k < 8; ++k) s[t][k] = fmaf(u, gv[k], s[t][k]);
         }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[9][k] += gv[k];
+    }
+    block_colsum<10>(s, sm, partial + (size_t)blockIdx.x * 10 * CH);
 }
 
-// Last layer: partial[group][tap*64 + ci] = sum_p a16[p + off(tap)][ci] gout[p]; [9*64] = sum gout.
-__global__ void k_wgrad_last(const bf16* __restrict__ a16, const float* __restrict__ gout, int B, int H, int W,
-                             int ngroups, float* __restrict__ partial) {
-    const int c = threadIdx.x & 63, sub = threadIdx.x >> 6, nsub = blockDim.x >> 6;
+// Last layer: partial[block][tap*64 + ci] = sum_p a16[p + off(tap)][ci] gout[p];
+// partial[block][9*64] = sum_p gout[p] (columns 9*64 + 1 .. 10*64 - 1 are zero).
+__global__ void __launch_bounds__(256) k_wgrad_last(const bf16* __restrict__ a16, const float* __restrict__ gout,
+                                                    int B, int H, int W, long long per, float* __restrict__ partial) {
+    __shared__ float sm[8][10 * CH];
+    const int cg = threadIdx.x & 7, pl = threadIdx.x >> 3;
     const long long HW = (long long)H * W, npix = B * HW;
-    double s[10];
-#pragma unroll
-    for (int t = 0; t < 10; ++t) s[t] = 0.0;
-    for (long long p = (long long)blockIdx.x * nsub + sub; p < npix; p += (long long)ngroups * nsub) {
+    const long long p0 = (long long)blockIdx.x * per, p1 = std::min(p0 + per, npix);
+    float s[10][8] = {};
+    for (long long p = p0 + pl; p < p1; p += 32) {
         const int b = (int)(p / HW);
         const int y = (int)((p - b * HW) / W), x = (int)(p - b * HW - (long long)y * W);
         const float gv = gout[p];
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                s[t] += (double)__bfloat162float(a16[(((long long)b * H + yy) * W + xx) * CH + c]) * gv;
-        }
-        if (c == 0) s[9] += gv;
-    }
-    __shared__ double sm[4][10 * CH];          // launched with 256 threads: 4 pixel lanes x 64 channels
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                float f[8];
+                unpack8(*reinterpret_cast<const uint4*>(a16 + (((long long)b * H + yy) * W + xx) * CH + cg * 8), f);
 #pragma unroll
-    for (int t = 0; t < 10; ++t) sm[sub][t * CH + c] = s[t];
-    __syncthreads();
-    if (sub == 0)
-        for (int t = 0; t < 10; ++t) {
-            double v = 0.0;
-            for (int k = 0; k < nsub; ++k) v += sm[k][t * CH + c];
-            partial[(size_t)blockIdx.x * 10 * CH + t * CH + c] = (float)v;
+                for (int k = 0; k < 8; ++k) s[t][k] = fmaf(f[k], gv, s[t][k]);
+            }
         }
+        if (cg == 0) s[9][0] += gv;
+    }
+    block_colsum<10>(s, sm, partial + (size_t)blockIdx.x * 10 * CH);
 }
 
-// ------------------------------------------------------------- training --
 // e = (r - sigma f) - x_true; loss partials sum e^2; gout = -2 sigma e / count
 __global__ void k_loss(const float* __restrict__ r, const float* __restrict__ sigma, const float* __restrict__ f,
                        const float* __restrict__ xt, long long HW, long long npix, float* __restrict__ gout,
@@ -424,7 +470,6 @@ struct dgamp_ct_cnn_s {
     uint64_t ws_gen = 0;        // bumped whenever the workspace is reallocated or captured launches change
 };
 
-static int kGroups = 32;
 constexpr int kWgGroupsMax = 64;   // most CTA groups of the tensor-core weight gradient
 
 static void cnn_free_ws(dgamp_ct_cnn_s* c) {
@@ -456,8 +501,9 @@ static int cnn_ensure_ws(dgamp_ct_cnn_s* c, int64_t npix, int nstore, int batch)
     if ((rc = A((void**)&c->g1, (size_t)cap * CH * sizeof(bf16))) != DGAMP_CT_OK) return rc;
     if ((rc = A((void**)&c->f, (size_t)cap * sizeof(float))) != DGAMP_CT_OK) return rc;
     if ((rc = A((void**)&c->gout, (size_t)cap * sizeof(float))) != DGAMP_CT_OK) return rc;
-    const size_t wg_groups = (size_t)(kGroups > kWgGroupsMax ? kGroups : kWgGroupsMax);
-    if ((rc = A((void**)&c->partial, wg_groups * 9 * CH * CH * sizeof(float))) != DGAMP_CT_OK) return rc;
+    // the larger of the tensor-core weight gradient's partials and the pixel sums' (+ their reduction)
+    const size_t n_part = std::max((size_t)kWgGroupsMax * 9 * CH * CH, (size_t)(kColBlocks + 1) * 10 * CH);
+    if ((rc = A((void**)&c->partial, n_part * sizeof(float))) != DGAMP_CT_OK) return rc;
     if ((rc = A((void**)&c->dpart, 1024 * sizeof(double))) != DGAMP_CT_OK) return rc;
     if ((rc = A((void**)&c->loss, sizeof(double))) != DGAMP_CT_OK) return rc;
     if ((rc = A((void**)&c->sig_buf, (size_t)cb * sizeof(float))) != DGAMP_CT_OK) return rc;
@@ -505,20 +551,22 @@ static int cnn_backward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int
     const int L = c->L;
     auto act = [&](int l) -> bf16* { return c->act + (size_t)(l - 1) * c->cap_pix * CH; };
     const unsigned blocks = (unsigned)((npix + 127) / 128);
-    const int G = kGroups;
+    // blocks of the pixel sums and the pixels each takes
+    const int nb = col_blocks(npix);
+    const long long per = (npix + nb - 1) / nb;
+    const unsigned rgrid = (unsigned)((10 * CH + 7) / 8);   // k_reduce_cols: 8 columns per 256 threads
     // CTA groups of the hidden layers' weight gradient: 3 CTAs (one per tap
     // row) per group, about one CTA per SM
     const int Gw = std::max(1, std::min(kWgGroupsMax, c->sm_count / 3));
     // last layer weights and bias
-    k_wgrad_last<<<G, 256, 0, st>>>(act(L - 1), c->gout, B, H, W, G, c->partial);
+    k_wgrad_last<<<nb, 256, 0, st>>>(act(L - 1), c->gout, B, H, W, per, c->partial);
     DGCT_LAUNCH_CHECK();
-    k_reduce_rows<<<(10 * CH + 255) / 256, 256, 0, st>>>(c->partial, G, 10 * CH, c->partial + (size_t)G * 10 * CH);
+    float* red = c->partial + (size_t)nb * 10 * CH;
+    k_reduce_cols<<<rgrid, 256, 0, st>>>(c->partial, nb, 10 * CH, red);
     DGCT_LAUNCH_CHECK();
     // scatter [tap*64+ci] -> grad W[L-1] ([tap][ci][1]) and [9*64] -> b
-    DGCT_CUDA(cudaMemcpyAsync(c->grad + c->w_off[L - 1], c->partial + (size_t)G * 10 * CH, 9 * CH * sizeof(float),
-                              cudaMemcpyDeviceToDevice, st));
-    DGCT_CUDA(cudaMemcpyAsync(c->grad + c->b_off[L - 1], c->partial + (size_t)G * 10 * CH + 9 * CH, sizeof(float),
-                              cudaMemcpyDeviceToDevice, st));
+    DGCT_CUDA(cudaMemcpyAsync(c->grad + c->w_off[L - 1], red, 9 * CH * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    DGCT_CUDA(cudaMemcpyAsync(c->grad + c->b_off[L - 1], red + 9 * CH, sizeof(float), cudaMemcpyDeviceToDevice, st));
     bf16* gcur = c->g0;
     bf16* gnext = c->g1;
     k_dgrad_last<<<blocks, 128, 0, st>>>(c->gout, c->w16, act(L - 1), gcur, B, H, W);
@@ -528,9 +576,9 @@ static int cnn_backward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int
         DGCT_TRY(launch_wgrad64_tc(act(l), gcur, B, H, W, Gw, c->partial, c->tc_err, st, c->stall_ns));
         k_reduce_wgrad64<<<(9 * CH * CH + 255) / 256, 256, 0, st>>>(c->partial, Gw, c->grad + c->w_off[l]);
         DGCT_LAUNCH_CHECK();
-        k_bias_partial<<<G, 256, 0, st>>>(gcur, npix, G, c->partial);
+        k_bias_partial<<<nb, 256, 0, st>>>(gcur, npix, per, c->partial);
         DGCT_LAUNCH_CHECK();
-        k_reduce_rows<<<1, 64, 0, st>>>(c->partial, G, CH, c->grad + c->b_off[l]);
+        k_reduce_cols<<<(CH + 7) / 8, 256, 0, st>>>(c->partial, nb, CH, c->grad + c->b_off[l]);
         DGCT_LAUNCH_CHECK();
         DGCT_TRY(launch_conv64_tc(1, gcur, c->wt, L - 2, l - 1, nullptr, act(l), gnext, B, H, W, c->sm_count,
                                   c->tc_err, st, c->stall_ns));
@@ -539,9 +587,9 @@ static int cnn_backward(dgamp_ct_cnn_s* c, const float* r, const float* sig, int
         gnext = t;
     }
     // first layer: gcur = dL/dz_1
-    k_wgrad_first<<<G, 256, 0, st>>>(r, sig, gcur, B, H, W, G, c->partial);
+    k_wgrad_first<<<nb, 256, 0, st>>>(r, sig, gcur, B, H, W, per, c->partial);
     DGCT_LAUNCH_CHECK();
-    k_reduce_rows<<<(10 * CH + 255) / 256, 256, 0, st>>>(c->partial, G, 10 * CH, c->grad + c->w_off[0]);
+    k_reduce_cols<<<rgrid, 256, 0, st>>>(c->partial, nb, 10 * CH, c->grad + c->w_off[0]);
     DGCT_LAUNCH_CHECK();   // w_off[0] .. +9*64 are W0 [tap][0][co]; the next 64 are b0 (b_off[0] == w_off[0] + 576)
     return DGAMP_CT_OK;
 }

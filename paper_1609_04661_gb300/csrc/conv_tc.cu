@@ -409,7 +409,7 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
 }
 
 // ---------------------------------------------------- weight gradient ----
-// partial[group][tap][co][ci] = sum over the group's pixels p of
+// partial[group][tap][ci][co] = sum over the group's pixels p of
 //   g[p][co] a[p + (dy - 1, dx - 1)][ci],   tap = 3 dy + dx,
 // a GEMM per tap with M = 64 output channels, N = 64 input channels and the
 // pixels as K.  Both operands lie pixel-major in global memory (one pixel's
@@ -566,12 +566,11 @@ k_wgrad64_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ 
             for (int c = 0; c < 3 * 64; c += 16) {
                 float v[16];
                 tmem_ld16(tmem + lane_base + (uint32_t)c, v);   // warp-collective
-                if (lane < 16) {
+                if (lane < 16) {   // 16 output channels of one warp: 64 contiguous bytes per ci
                     const int tap = c >> 6, ci = c & 63;
-                    float4* dst = reinterpret_cast<float4*>(out + ((size_t)tap * CH + co) * CH + ci);
+                    float* dst = out + ((size_t)tap * CH + ci) * CH + co;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    for (int j = 0; j < 16; ++j) dst[(size_t)j * CH] = v[j];
                 }
             }
         }
@@ -664,7 +663,7 @@ int launch_conv64_tc(int mode, const void* in, const void* wk_all, int layers, i
 }
 
 // a: the layer's input activations, g: the gradient at its output, both
-// [B][H][W][64] BF16; partial: [groups][9][64 co][64 ci] FP32, every group
+// [B][H][W][64] BF16; partial: [groups][9][64 ci][64 co] FP32, every group
 // written (zeros for a group without strips).
 int launch_wgrad64_tc(const void* a, const void* g, int B, int H, int W, int groups, float* partial, unsigned* err,
                       cudaStream_t st, unsigned long long stall_ns) {

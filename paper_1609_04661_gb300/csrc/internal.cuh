@@ -403,7 +403,7 @@ int conv64_tc_init();
 int launch_conv64_tc(int mode, const void* in, const void* wk_all, int layers, int layer, const float* bias,
                      const void* mask, void* out, int B, int H, int W, int grid_cap, unsigned* err, cudaStream_t st,
                      unsigned long long stall_ns = 0);
-// weight gradient of a hidden layer on tcgen05: partial[groups][9][co][ci]
+// weight gradient of a hidden layer on tcgen05: partial[groups][9][ci][co]
 int launch_wgrad64_tc(const void* a, const void* g, int B, int H, int W, int groups, float* partial, unsigned* err,
                       cudaStream_t st, unsigned long long stall_ns = 0);
 // after the network's work is complete: DGAMP_CT_ERR_TIMEOUT (and the flag cleared)
