@@ -149,6 +149,42 @@ def _learned_vs_plain(dg, plan, case, counts, T, plain_iters_per_s):
                              "algorithmic_flop_per_iteration": flop}}
 
 
+def _training(dg, steps: int = 20):
+    """One Adam step of the 17-layer network on a batch of 32 patches of 64 x 64
+    (the training batch of train_denoiser.py): forward, backward (data and
+    weight gradients of every layer) and the update, timed with CUDA events on
+    the launching stream.  Synthetic patches; the loss is read back each step
+    as training does."""
+    import numpy as np
+    import torch
+    B, H, W = 32, 64, 64
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0.0, 1.0, (B, H, W)).astype(np.float32)
+    sig = np.exp(rng.uniform(np.log(0.005), np.log(0.1), B)).astype(np.float32)
+    r = (x + sig[:, None, None] * rng.standard_normal((B, H, W))).astype(np.float32)
+    rt, xt = torch.as_tensor(r).cuda(), torch.as_tensor(x).cuda()
+    with dg.CNN(17, seed=3) as net:
+        for _ in range(3):
+            net.train_step(rt, xt, sig, 1e-4)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            net.train_step(rt, xt, sig, 1e-4)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    # forward, data gradient and weight gradient of the hidden layers, plus the end layers
+    flop = 3.0 * B * H * W * CNN_FLOP_PER_PIXEL
+    peak, kind = _bf16_peak()
+    achieved = flop / (ms * 1e-3) / 1e12
+    return {"workload": f"17-layer 64-channel network, {B} patches of {H}x{W}, Adam, loss read back each step",
+            "ms_per_step": ms, "patches_per_s": B / (ms * 1e-3), "flop_per_step": flop,
+            "tflops": achieved, "frac_of_bf16_peak": achieved / peak, "peak_kind": f"{kind} cuBLAS bf16 burst",
+            "note": "64-wide patches fill half of each 128-pixel strip of the tensor-core kernels"}
+
+
 def _ablation(plan, case, counts, T):
     """PSNR after t = 1..T iterations with and without the Onsager term and
     the damping (Sections 7.1 and 7.2), on the benchmark slice; and with the
@@ -792,6 +828,7 @@ def run_gpu(args):
     batched_learned = None if (args.no_batched or args.no_learned) else _batched(dg, rank, world, dist, flush, 1,
                                                                                    learned=True)
     ablation = _ablation(plan, case, counts, T) if rank == 0 and not args.no_learned else None
+    training = _training(dg) if rank == 0 and not args.no_learned else None
     variants = _variants(dg, plan, case, counts, T) if (not args.no_variants and rank == 0) else None
 
     line = None
@@ -813,7 +850,7 @@ def run_gpu(args):
                 "roofline_A": roof_a, "roofline_AT": roof_at, "fp32_fma_peak_tflops": fp32_peak,
                 "iteration_ms": iter_ms, "tuning": tun, "kernel_ms": prof, "kernel_share": shares,
                 "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned, "batched": batched, "batched_learned": batched_learned, "large_bf16": c5,
-                "ablation": ablation, "variants": variants}
+                "ablation": ablation, "variants": variants, "training": training}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:
