@@ -75,6 +75,7 @@ __device__ __forceinline__ void project_block(const T* __restrict__ XR, const T*
     const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
     const int d = gx * kPjRays + lane;
     const ViewConst c = vcs[v];
+    pdl_wait();      // the staged image is the previous kernel's output
     float acc = 0.f;
     if (d < nd) {
         const T* __restrict__ B = c.col ? XC : XR;
@@ -128,23 +129,22 @@ k_project_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ 
 }
 
 template <int SEG>
-static void launch_project_seg(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf) {
+static cudaError_t launch_project_seg(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf) {
     dim3 blk(kPjRays * SEG), grd((pl->nd + kPjRays - 1) / kPjRays, pl->nv);
     if (bf)
-        k_project<bf16s, SEG><<<grd, blk, 0, st>>>((const bf16s*)pl->ws.XR, (const bf16s*)pl->ws.XC, pl->ldp,
-                                                   pl->n, pl->nd, pl->ws.vc, (bf16s*)sino);
-    else
-        k_project<float, SEG><<<grd, blk, 0, st>>>(pl->ws.XR, pl->ws.XC, pl->ldp, pl->n, pl->nd, pl->ws.vc, sino);
+        return launch_pdl(k_project<bf16s, SEG>, grd, blk, 0, st, (const bf16s*)pl->ws.XR, (const bf16s*)pl->ws.XC,
+                          pl->ldp, pl->n, pl->nd, (const ViewConst*)pl->ws.vc, (bf16s*)sino);
+    return launch_pdl(k_project<float, SEG>, grd, blk, 0, st, (const float*)pl->ws.XR, (const float*)pl->ws.XC,
+                      pl->ldp, pl->n, pl->nd, (const ViewConst*)pl->ws.vc, sino);
 }
 
 int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf) {
     if (pl->pj_seg == 32)
-        launch_project_seg<32>(pl, sino, st, bf);
+        DGCT_CUDA(launch_project_seg<32>(pl, sino, st, bf));
     else if (pl->pj_seg == 16)
-        launch_project_seg<16>(pl, sino, st, bf);
+        DGCT_CUDA(launch_project_seg<16>(pl, sino, st, bf));
     else
-        launch_project_seg<8>(pl, sino, st, bf);
-    DGCT_LAUNCH_CHECK();
+        DGCT_CUDA(launch_project_seg<8>(pl, sino, st, bf));
     return DGAMP_CT_OK;
 }
 
@@ -338,6 +338,7 @@ __device__ __forceinline__ void backproject_tile_block(const T* __restrict__ sin
     float* AR = accR[wp];
     for (int i = lane; i < kBtS * kBtLd; i += 32) AL[i] = AR[i] = 0.f;
     if (tid == 0) s_max = 0u;
+    pdl_wait();      // H s and the tau_s partials are the previous kernel's output
     if (update && wp == 0) bp_tau_r(S, partial, nparts, M, (double)n * n, &s_tau_r, first);
     __syncwarp();
     for (int v = wp; v < nv; v += kBtWarps) {
@@ -402,14 +403,13 @@ int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float
     const double* part = pl->ws.partial;
     if (pl->bp_mode == 1) {
         dim3 grd((pl->n + kBtS - 1) / kBtS, (pl->n + kBtS - 1) / kBtS);
+        const ViewConst* vc = pl->ws.vc;
         if (bf)
-            k_backproject_tile<bf16s><<<grd, kBtWarps * 32, 0, st>>>((const bf16s*)sino, pl->nv, pl->nd, pl->n,
-                                                                     pl->ws.vc, x_in, out, update, pl->ws.S, part,
-                                                                     nparts, M);
+            DGCT_CUDA(launch_pdl(k_backproject_tile<bf16s>, grd, dim3(kBtWarps * 32), 0, st, (const bf16s*)sino,
+                                 pl->nv, pl->nd, pl->n, vc, x_in, out, update, pl->ws.S, part, nparts, M));
         else
-            k_backproject_tile<float><<<grd, kBtWarps * 32, 0, st>>>(sino, pl->nv, pl->nd, pl->n, pl->ws.vc, x_in,
-                                                                     out, update, pl->ws.S, part, nparts, M);
-        DGCT_LAUNCH_CHECK();
+            DGCT_CUDA(launch_pdl(k_backproject_tile<float>, grd, dim3(kBtWarps * 32), 0, st, sino, pl->nv, pl->nd,
+                                 pl->n, vc, x_in, out, update, pl->ws.S, part, nparts, M));
         return DGAMP_CT_OK;
     }
     dim3 blk(32, 8), grd((pl->n + 31) / 32, (pl->n + 7) / 8);
@@ -428,20 +428,24 @@ int batch_grid_project(int nv, int nd) { return ((nd + kPjRays - 1) / kPjRays) *
 int batch_grid_backproject(int n) { return ((n + kBtS - 1) / kBtS) * ((n + kBtS - 1) / kBtS); }
 
 int launch_project_batch(const BatchExec& E, cudaStream_t st) {
+    const BatchSlice* sl = E.sl;
+    const uint16_t* map = E.map[kPhProj];
+    const dim3 grd(E.nblk[kPhProj]), blk(kPjRays * kBatchPjSeg);
     if (E.bf)
-        k_project_batch<bf16s, kBatchPjSeg><<<E.nblk[kPhProj], kPjRays * kBatchPjSeg, 0, st>>>(E.sl, E.map[kPhProj]);
+        DGCT_CUDA(launch_pdl(k_project_batch<bf16s, kBatchPjSeg>, grd, blk, 0, st, sl, map));
     else
-        k_project_batch<float, kBatchPjSeg><<<E.nblk[kPhProj], kPjRays * kBatchPjSeg, 0, st>>>(E.sl, E.map[kPhProj]);
-    DGCT_LAUNCH_CHECK();
+        DGCT_CUDA(launch_pdl(k_project_batch<float, kBatchPjSeg>, grd, blk, 0, st, sl, map));
     return DGAMP_CT_OK;
 }
 
 int launch_backproject_batch(const BatchExec& E, cudaStream_t st) {
+    const BatchSlice* sl = E.sl;
+    const uint16_t* map = E.map[kPhBp];
+    const dim3 grd(E.nblk[kPhBp]), blk(kBtWarps * 32);
     if (E.bf)
-        k_backproject_tile_batch<bf16s><<<E.nblk[kPhBp], kBtWarps * 32, 0, st>>>(E.sl, E.map[kPhBp]);
+        DGCT_CUDA(launch_pdl(k_backproject_tile_batch<bf16s>, grd, blk, 0, st, sl, map));
     else
-        k_backproject_tile_batch<float><<<E.nblk[kPhBp], kBtWarps * 32, 0, st>>>(E.sl, E.map[kPhBp]);
-    DGCT_LAUNCH_CHECK();
+        DGCT_CUDA(launch_pdl(k_backproject_tile_batch<float>, grd, blk, 0, st, sl, map));
     return DGAMP_CT_OK;
 }
 

@@ -265,6 +265,13 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
     float* red = hs + HL;       // [W][OUT]
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const size_t row0 = (size_t)v * nd;
+    // the filter is constant over a solve: staged before waiting on the
+    // previous kernel, whose output (A x) and scalars everything else reads
+    for (int i = tid; i < HL; i += TH) {
+        const int m = i - 1;
+        hs[i] = (m >= 0 && m < 2 * nd - 1) ? hx[m] : 0.f;
+    }
+    pdl_wait();
     // the tau_x warp issues its loads of the divergence partials first, so
     // that their latency overlaps the loads and the first product
     double div_pre[kDivPre];
@@ -288,10 +295,6 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
         }
     }
     for (int i = tid; i < nd; i += TH) zs[i] = ldf(zraw + row0 + i);
-    for (int i = tid; i < HL; i += TH) {
-        const int m = i - 1;
-        hs[i] = (m >= 0 && m < 2 * nd - 1) ? hx[m] : 0.f;
-    }
     __syncthreads();
     const int len = (nd + W - 1) / W;
     const int dl = d_lo + R * lane;
@@ -434,7 +437,7 @@ static int launch_ct_batch(const BatchExec& E, cudaStream_t st) {
     void* args[] = {(void*)&E.sl, (void*)&E.map[kPhView]};
     return ct_dispatch<T, true>(E.R, E.cl, [&](const void* k, int threads, int cl) -> int {
         DGCT_TRY(raise_smem_limit(k, (int)sm));
-        DGCT_CUDA(cudaLaunchKernel(k, dim3((unsigned)(E.nblk[kPhView] * cl)), dim3(threads), args, sm, st));
+        DGCT_CUDA(launch_pdl_c(k, dim3((unsigned)(E.nblk[kPhView] * cl)), dim3(threads), sm, st, args));
         return DGAMP_CT_OK;
     });
 }
@@ -469,7 +472,7 @@ static int launch_ct(const dgamp_ct_plan_s* pl, cudaStream_t st, const T* zraw, 
                     (void*)&onsager, (void*)&damp_s, (void*)&truncate, (void*)&S, (void*)&partial,
                     (void*)&partial_div, (void*)&N, (void*)&floor_rel, (void*)&log};
     return ct_dispatch<T, false>(R, cl, [&](const void* k, int threads, int c) -> int {
-        DGCT_CUDA(cudaLaunchKernel(k, dim3((unsigned)(pl->nv * c)), dim3(threads), args, sm, st));
+        DGCT_CUDA(launch_pdl_c(k, dim3((unsigned)(pl->nv * c)), dim3(threads), sm, st, args));
         return DGAMP_CT_OK;
     });
 }

@@ -39,6 +39,7 @@ constexpr float kTau = 0.125f;
 __device__ __forceinline__ void probe_group(const float* __restrict__ r, float* __restrict__ r2,
                                             float* __restrict__ bout, long long N, float eps_rel, int t_arg,
                                             unsigned slice, uint2 key, DevScalars* S, int write_b, long long g) {
+    pdl_wait();      // r and the scalars are the previous kernels' output
     const float rmax = __uint_as_float(S->rmax_bits);
     const float eps = eps_rel * fmaxf(rmax, 1e-6f);
     const unsigned t = t_arg > 0 ? (unsigned)t_arg : S->t;
@@ -77,10 +78,9 @@ static uint2 probe_key(const dgamp_ct_plan_s* pl) {
 int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st, int write_b) {
     const long long N = pl->N;
     const long long groups = (N + 3) / 4;
-    k_probe_input<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(
-        pl->ws.r, pl->ws.r + N, pl->ws.b, N, (float)pl->opt.eps_rel, t_arg, (unsigned)pl->opt.slice_id,
-        probe_key(pl), pl->ws.S, write_b);
-    DGCT_LAUNCH_CHECK();
+    DGCT_CUDA(launch_pdl(k_probe_input, dim3((unsigned)((groups + 255) / 256)), dim3(256), 0, st,
+                         (const float*)pl->ws.r, pl->ws.r + N, pl->ws.b, N, (float)pl->opt.eps_rel, t_arg,
+                         (unsigned)pl->opt.slice_id, probe_key(pl), pl->ws.S, write_b));
     return DGAMP_CT_OK;
 }
 
@@ -307,6 +307,7 @@ __device__ __forceinline__ void tv_steps_block(const float* __restrict__ rbase, 
     const int im = bz;
     const size_t img = (size_t)im * N;
     const int gi0 = by * TH - E, gj0 = bx * TW - E;
+    pdl_wait();      // r, the duals and the scalars are earlier kernels' output
     const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
     const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
     float px[V][U], py[V][U], rl[V][U];
@@ -479,20 +480,21 @@ int batch_grid_tv(int n, int final_launch) {
 int batch_grid_probe(long long N) { return (int)(((N + 3) / 4 + 255) / 256); }
 
 int launch_probe_batch(const BatchExec& E, cudaStream_t st) {
-    k_probe_input_batch<<<E.nblk[kPhProbe], 256, 0, st>>>(E.sl, E.map[kPhProbe]);
-    DGCT_LAUNCH_CHECK();
+    const BatchSlice* sl = E.sl;
+    const uint16_t* map = E.map[kPhProbe];
+    DGCT_CUDA(launch_pdl(k_probe_input_batch, dim3(E.nblk[kPhProbe]), dim3(256), 0, st, sl, map));
     return DGAMP_CT_OK;
 }
 
 int launch_tv_batch(const BatchExec& E, int launch, bool final_launch, cudaStream_t st) {
     constexpr int WY = kTvRowsBatch / kTvV;
+    const BatchSlice* sl = E.sl;
     if (final_launch)
-        k_tv_steps_batch<WY, kBatchTvKb, true><<<E.nblk[kPhTv1], 32 * WY, 0, st>>>(E.sl, E.map[kPhTv1], kPhTv1,
-                                                                                 launch, E.bf);
+        DGCT_CUDA(launch_pdl(k_tv_steps_batch<WY, kBatchTvKb, true>, dim3(E.nblk[kPhTv1]), dim3(32 * WY), 0, st, sl,
+                             (const uint16_t*)E.map[kPhTv1], (int)kPhTv1, launch, E.bf));
     else
-        k_tv_steps_batch<WY, kBatchTvKb, false><<<E.nblk[kPhTv0], 32 * WY, 0, st>>>(E.sl, E.map[kPhTv0], kPhTv0,
-                                                                                  launch, E.bf);
-    DGCT_LAUNCH_CHECK();
+        DGCT_CUDA(launch_pdl(k_tv_steps_batch<WY, kBatchTvKb, false>, dim3(E.nblk[kPhTv0]), dim3(32 * WY), 0, st, sl,
+                             (const uint16_t*)E.map[kPhTv0], (int)kPhTv0, launch, E.bf));
     return DGAMP_CT_OK;
 }
 
@@ -579,25 +581,26 @@ struct TvLaunch {
 };
 
 template <int WY, int KB, bool FIN, int V>
-static void launch_steps_kb(const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
+static cudaError_t launch_steps_kb(const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
     constexpr int E = FIN ? KB + 1 : KB;
     constexpr int TW = kTvRW - KB - E, TH = V * WY - KB - E;
     dim3 grd((L.n + TW - 1) / TW, (L.n + TH - 1) / TH, L.nimg);
-    k_tv_steps<WY, KB, FIN, V><<<grd, 32 * WY, 0, st>>>(L.r, L.pin, L.pout, L.n, L.first, L.c_tv, L.fs, L.lam, L.S,
-                                                        L.b, F);
+    return launch_pdl(k_tv_steps<WY, KB, FIN, V>, grd, dim3(32 * WY), 0, st, L.r, L.pin, L.pout, L.n, L.first,
+                      L.c_tv, L.fs, L.lam, L.S, L.b, F);
 }
 
 template <int WY, bool FIN, int V = kTvV>
 static int launch_steps_wy(int steps, const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
+    cudaError_t e = cudaSuccess;
 #define DGCT_TV_CASE(KB) \
-    case KB: launch_steps_kb<WY, KB, FIN, V>(L, st, F); break;
+    case KB: e = launch_steps_kb<WY, KB, FIN, V>(L, st, F); break;
     switch (steps) {
         DGCT_TV_CASE(1) DGCT_TV_CASE(2) DGCT_TV_CASE(3) DGCT_TV_CASE(4) DGCT_TV_CASE(5)
         DGCT_TV_CASE(6) DGCT_TV_CASE(7) DGCT_TV_CASE(8) DGCT_TV_CASE(9) DGCT_TV_CASE(10)
         default: return DGAMP_CT_ERR_INVALID_ARG;
     }
 #undef DGCT_TV_CASE
-    DGCT_LAUNCH_CHECK();
+    DGCT_CUDA(e);
     return DGAMP_CT_OK;
 }
 
