@@ -320,11 +320,16 @@ static int segments_per_iteration(const dgamp_ct_plan_s* pl) {
 
 static void drop_graph(dgamp_ct_plan_s* pl) {
     if (pl->graph) cudaGraphExecDestroy(pl->graph);
-    pl->graph = nullptr;
+    if (pl->graph_k) cudaGraphExecDestroy(pl->graph_k);
+    pl->graph = pl->graph_k = nullptr;
 }
 
-static int ensure_graph(dgamp_ct_plan_s* pl) {
-    if (pl->graph) return DGAMP_CT_OK;
+// Iterations per launch of the longer graph: consecutive iterations in one
+// graph run back to back with no graph-launch boundary between them.
+constexpr int kGraphIters = 5;
+
+// k iterations captured as one graph into *out
+static int capture_iterations(dgamp_ct_plan_s* pl, int k, cudaGraphExec_t* out) {
     cudaStream_t cs;
     DGCT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
@@ -333,8 +338,8 @@ static int ensure_graph(dgamp_ct_plan_s* pl) {
         cudaStreamDestroy(cs);
         return cuda_fail(e);
     }
-    int rc = enqueue_iteration(pl, cs);
-    pl->graph_cnn_gen = pl->cnn ? cnn_ws_generation(pl->cnn) : 0;
+    int rc = DGAMP_CT_OK;
+    for (int i = 0; i < k && rc == DGAMP_CT_OK; ++i) rc = enqueue_iteration(pl, cs);
     e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
     if (rc != DGAMP_CT_OK) {
@@ -342,12 +347,31 @@ static int ensure_graph(dgamp_ct_plan_s* pl) {
         return rc;
     }
     if (e != cudaSuccess) return cuda_fail(e);
-    e = cudaGraphInstantiate(&pl->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        pl->graph = nullptr;
+        *out = nullptr;
         return cuda_fail(e);
     }
+    return DGAMP_CT_OK;
+}
+
+// the one-iteration graph, and the kGraphIters one when `iters` can use it
+static int ensure_graph(dgamp_ct_plan_s* pl, int iters) {
+    if (!pl->graph) {
+        DGCT_TRY(capture_iterations(pl, 1, &pl->graph));
+        pl->graph_cnn_gen = pl->cnn ? cnn_ws_generation(pl->cnn) : 0;
+    }
+    if (iters >= kGraphIters && !pl->graph_k) DGCT_TRY(capture_iterations(pl, kGraphIters, &pl->graph_k));
+    return DGAMP_CT_OK;
+}
+
+// `iters` iterations through the captured graphs
+static int launch_graphs(dgamp_ct_plan_s* pl, int iters, cudaStream_t st) {
+    DGCT_TRY(ensure_graph(pl, iters));
+    int t = 0;
+    for (; t + kGraphIters <= iters; t += kGraphIters) DGCT_CUDA(cudaGraphLaunch(pl->graph_k, st));
+    for (; t < iters; ++t) DGCT_CUDA(cudaGraphLaunch(pl->graph, st));
     return DGAMP_CT_OK;
 }
 
@@ -690,7 +714,7 @@ static int solve_begin(dgamp_ct_plan_s* pl, const float* d_counts, double I0, cu
         // the network may have been used (and its workspace regrown) since the
         // graph was captured: make room again and re-capture if it moved
         DGCT_TRY(cnn_prepare_pair(pl->cnn, pl->n));
-        if (pl->graph && pl->graph_cnn_gen != cnn_ws_generation(pl->cnn)) drop_graph(pl);
+        if ((pl->graph || pl->graph_k) && pl->graph_cnn_gen != cnn_ws_generation(pl->cnn)) drop_graph(pl);
     }
     k_init_scalars<<<1, 1, 0, st>>>(w.S, pl->frob2, std::log(I0), pl->opt.tau_x0);
     DGCT_LAUNCH_CHECK();
@@ -736,8 +760,7 @@ int dgamp_ct_solve(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t
     const size_t N = (size_t)pl->N;
     DGCT_TRY(solve_begin(pl, d_counts, I0, st));
     if (pl->opt.use_graph) {
-        DGCT_TRY(ensure_graph(pl));
-        for (int t = 0; t < iters; ++t) DGCT_CUDA(cudaGraphLaunch(pl->graph, st));
+        DGCT_TRY(launch_graphs(pl, iters, st));
     } else {
         for (int t = 0; t < iters; ++t) DGCT_TRY(enqueue_iteration(pl, st));
     }

@@ -235,6 +235,7 @@ struct dgamp_ct_batch_s {
     BatchExec E;                        // the whole batch: begin, finish and V^-1 tables
     std::vector<BatchExec> grp;         // per group: the tables of the iteration's phases
     cudaGraphExec_t graph = nullptr;    // one iteration: 6 launches per group, groups on parallel branches
+    cudaGraphExec_t graph_k = nullptr;  // kBatchGraphIters iterations, one after the other
     int tv_launches = 0;
 };
 
@@ -242,13 +243,14 @@ namespace dgct {
 
 static void batch_free(dgamp_ct_batch_s* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_k) cudaGraphExecDestroy(b->graph_k);
     if (b->E.sl) cudaFree(b->E.sl);
     for (int p = 0; p < kPhases; ++p)
         if (b->E.map[p]) cudaFree(b->E.map[p]);
     for (auto& g : b->grp)
         for (int p = 0; p < kPhases; ++p)
             if (g.map[p]) cudaFree(g.map[p]);
-    b->graph = nullptr;
+    b->graph = b->graph_k = nullptr;
     b->E = BatchExec{};
     b->grp.clear();
 }
@@ -266,10 +268,13 @@ static int batch_iteration(dgamp_ct_batch_s* b, const BatchExec& E, cudaStream_t
     return DGAMP_CT_OK;
 }
 
-// The iteration graph: group k's six launches on branch k, forked from and
-// joined back into the capture stream (one branch when there is one group).
-static int batch_graph(dgamp_ct_batch_s* b) {
-    if (b->graph) return DGAMP_CT_OK;
+// Iterations per launch of the longer batch graph.
+constexpr int kBatchGraphIters = 5;
+
+// The graph of `iters` iterations: in each, group k's six launches on branch
+// k, forked from and joined back into the capture stream (one branch when
+// there is one group).
+static int batch_graph_iters(dgamp_ct_batch_s* b, int iters, cudaGraphExec_t* out) {
     const int G = (int)b->grp.size();
     std::vector<cudaStream_t> br(G, nullptr);
     std::vector<cudaEvent_t> ev(G + 1, nullptr);
@@ -296,17 +301,19 @@ static int batch_graph(dgamp_ct_batch_s* b) {
         return cuda_fail(e);
     }
     int rc = DGAMP_CT_OK;
-    if (G == 1) {
-        rc = batch_iteration(b, b->grp[0], cs);
-    } else {
-        cudaError_t ce = cudaEventRecord(ev[G], cs);                              // fork
-        for (int k = 0; k < G && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(br[k], ev[G], 0);
-        if (ce != cudaSuccess) rc = cuda_fail(ce);
-        for (int k = 0; k < G && rc == DGAMP_CT_OK; ++k) rc = batch_iteration(b, b->grp[k], br[k]);
-        for (int k = 0; k < G; ++k) {                                              // join every branch
-            ce = cudaEventRecord(ev[k], br[k]);
-            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, ev[k], 0);
-            if (ce != cudaSuccess && rc == DGAMP_CT_OK) rc = cuda_fail(ce);
+    for (int it = 0; it < iters && rc == DGAMP_CT_OK; ++it) {
+        if (G == 1) {
+            rc = batch_iteration(b, b->grp[0], cs);
+        } else {
+            cudaError_t ce = cudaEventRecord(ev[G], cs);                              // fork
+            for (int k = 0; k < G && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(br[k], ev[G], 0);
+            if (ce != cudaSuccess) rc = cuda_fail(ce);
+            for (int k = 0; k < G && rc == DGAMP_CT_OK; ++k) rc = batch_iteration(b, b->grp[k], br[k]);
+            for (int k = 0; k < G; ++k) {                                              // join every branch
+                ce = cudaEventRecord(ev[k], br[k]);
+                if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, ev[k], 0);
+                if (ce != cudaSuccess && rc == DGAMP_CT_OK) rc = cuda_fail(ce);
+            }
         }
     }
     e = cudaStreamEndCapture(cs, &g);
@@ -316,12 +323,18 @@ static int batch_graph(dgamp_ct_batch_s* b) {
         return rc;
     }
     if (e != cudaSuccess) return cuda_fail(e);
-    e = cudaGraphInstantiate(&b->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        b->graph = nullptr;
+        *out = nullptr;
         return cuda_fail(e);
     }
+    return DGAMP_CT_OK;
+}
+
+static int batch_graph(dgamp_ct_batch_s* b) {
+    if (!b->graph) DGCT_TRY(batch_graph_iters(b, 1, &b->graph));
+    if (!b->graph_k) DGCT_TRY(batch_graph_iters(b, kBatchGraphIters, &b->graph_k));
     return DGAMP_CT_OK;
 }
 
@@ -486,7 +499,9 @@ int dgamp_ct_batch_solve(dgamp_ct_batch_t b, const float* const* d_counts, const
     DGCT_CUDA(cudaMemcpyAsync(E.sl, b->h.data(), (size_t)n * sizeof(BatchSlice), cudaMemcpyHostToDevice, st));
     k_batch_begin<<<E.nblk[kPhBegin], 256, 0, st>>>(E.sl, E.map[kPhBegin]);
     DGCT_LAUNCH_CHECK();
-    for (int t = 0; t < iters; ++t) DGCT_CUDA(cudaGraphLaunch(b->graph, st));
+    int t = 0;
+    for (; t + kBatchGraphIters <= iters; t += kBatchGraphIters) DGCT_CUDA(cudaGraphLaunch(b->graph_k, st));
+    for (; t < iters; ++t) DGCT_CUDA(cudaGraphLaunch(b->graph, st));
     k_batch_finish<<<n, 32, 0, st>>>(E.sl);
     DGCT_LAUNCH_CHECK();
     const int thr = batch_vinv_threads(E.max_m2);

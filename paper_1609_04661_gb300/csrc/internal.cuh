@@ -170,7 +170,8 @@ struct dgamp_ct_plan_s {
     int pj_seg = 8;                        // A: step segments (warps) per ray group, 8/16/32 (plan-time choice)
     int fan = 0;                           // 1: flat-detector fan beam (dgamp_ct_plan_fan)
     // captured iteration graph
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;       // one iteration
+    cudaGraphExec_t graph_k = nullptr;     // kGraphIters iterations (captured when a solve is that long)
     cudaStream_t graph_stream = nullptr;   // stream the graph was captured for (identity only)
     uint64_t graph_cnn_gen = 0;            // network workspace generation the graph was captured with
     int kernels_per_iter = 0;
