@@ -541,6 +541,7 @@ int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
     if (t->tv_vrows >= 0 && t->tv_vrows != 4 && t->tv_vrows != 8) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->sino_fused == 1 && !sino_step_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (t->sino_fused == 2 && !sino_toeplitz_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
+    if (pl->fan && t->bp_mode == 1 && pl->fan_stride <= 0) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (t->filter_mode >= 0) pl->filter_mode = t->filter_mode;
     if (t->tv_kb > 0) pl->tv_kb = t->tv_kb;
     if (t->tv_rows > 0) pl->tv_rows = t->tv_rows;

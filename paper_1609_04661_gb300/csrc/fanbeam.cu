@@ -22,7 +22,27 @@
 // marched by rows the staged rows XR, as in joseph.cu; taps just outside the
 // image read the zero guard cells.
 //
-// A^T: pixel-driven gather, one thread per pixel, views in order.  The rays
+// A^T, ray-driven tiles (bp_mode 1, the default where it applies): one
+// block = one 16 x 16 image tile, warp w takes views w, w + 8, ...  The rays
+// of a view that can put a tap in the tile are those whose bins lie between
+// the bins of the corners of the tile grown by one pixel (the bin map is
+// monotone along any segment in front of the source, so its extremes over
+// the square are at the corners), widened by one bin each way.  A warp's 32
+// lanes take rays S apart, S the plan's stride, and march them over the
+// tile's 16 steps with the projector's own integer positions, adding
+// (1 - f) s w at the left tap into one accumulator tile and f s w at the
+// right tap into another -- rays marched by columns in one pass, rays
+// marched by rows in another.  The two half-warps take the even and the odd
+// bin offsets of a pass, each with its own pair of accumulator tiles, so a
+// stride of 2 costs no second pass.  S is the smallest stride for which any two
+// rays of a view marched the same way and S or more bins apart are at least
+// one pixel apart on every march line through the image (checked at plan
+// time from the integer positions), so no two lanes add to the same word of
+// an accumulator in the same step.  The warps' tiles are summed in a fixed
+// order.  Where no stride up to kFtMaxStride suffices (a source very close
+// to the image with fine bins), the gather below is used.
+//
+// A^T, pixel-driven gather (bp_mode 0): one thread per pixel, views in order.  The rays
 // of view k that can put a tap on pixel (X, Y) through column X are those
 // crossing the segment (X, Y-1)-(X, Y+1); their bins lie between the
 // projections of its end points through the source (bin(p) is monotone
@@ -139,6 +159,100 @@ k_fan_backproject(const float* __restrict__ sino, const FanRay* __restrict__ ray
     img[(size_t)iy * n + ix] = acc;
 }
 
+constexpr int kFtS = 16, kFtLd = kFtS + 1, kFtWarps = 8, kFtMaxStride = 8;
+
+// two accumulator pairs per warp: the two half-warps of a pass take rays of
+// neighbouring bins, each half into its own pair
+struct FtShared {
+    float accL[kFtWarps][2][kFtS * kFtLd], accR[kFtWarps][2][kFtS * kFtLd];
+};
+
+// One pass of a warp over the tile: the lanes whose rays are marched by
+// columns (COL = 1: step k = column tx0 + k, taps along rows) or by rows.
+template <int COL>
+__device__ __forceinline__ void fan_tile_pass(const FanRay& r, float sw, bool on, int tx0, int ty0, int ncol,
+                                              int nrow, float* __restrict__ AL, float* __restrict__ AR) {
+    constexpr int as = COL ? 1 : kFtLd, ac = COL ? kFtLd : 1;     // accumulator strides: step, tap
+    if (!on) return;
+    const int s0 = COL ? tx0 : ty0, c0 = COL ? ty0 : tx0;
+    const int ns = COL ? ncol : nrow, nc = COL ? nrow : ncol;
+    // position relative to the tile: the left tap's index in the tile is the high word
+    long long pos = r.P0 + (long long)s0 * r.PSTEP - ((long long)c0 << 32);
+    auto step = [&](int k) {
+        const int rel = (int)(pos >> 32);
+        const float f = __uint_as_float(0x3F800000u | ((unsigned)pos >> 9)) - 1.0f;
+        const int at = k * as + rel * ac;
+        if ((unsigned)rel < (unsigned)nc) AL[at] += (1.f - f) * sw;
+        if ((unsigned)(rel + 1) < (unsigned)nc) AR[at + ac] += f * sw;
+        pos += r.PSTEP;
+    };
+    if (ns == kFtS) {
+#pragma unroll
+        for (int k = 0; k < kFtS; ++k) step(k);
+    } else {
+        for (int k = 0; k < ns; ++k) step(k);
+    }
+}
+
+__global__ void __launch_bounds__(kFtWarps * 32, 4)
+k_fan_backproject_tile(const float* __restrict__ sino, const FanRay* __restrict__ rays,
+                       const FanView* __restrict__ views, int n, int nv, int nd, int stride,
+                       float* __restrict__ img) {
+    __shared__ FtShared sh;
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    const int tx0 = blockIdx.x * kFtS, ty0 = blockIdx.y * kFtS;
+    const int ncol = min(kFtS, n - tx0), nrow = min(kFtS, n - ty0);
+    const int half = lane >> 4, hl = lane & 15;
+    float* AL = sh.accL[wp][half];
+    float* AR = sh.accR[wp][half];
+    for (int i = hl; i < kFtS * kFtLd; i += 16) AL[i] = AR[i] = 0.f;
+    __syncwarp();
+    // lane stride rounded up to even: pass p gives bin offset 2p + half to each
+    // half-warp, whose 16 lanes then take rays `st` bins apart
+    const int st = stride + (stride & 1);
+    // the tile grown by one pixel each way, centred coordinates (x right, y up)
+    const float c = 0.5f * (float)(n - 1);
+    const float xa = (float)(tx0 - 1) - c, xb = (float)(tx0 + ncol) - c;
+    const float ya = c - (float)(ty0 - 1), yb = c - (float)(ty0 + nrow);
+    for (int v = wp; v < nv; v += kFtWarps) {
+        const FanView V = views[v];
+        const float b0 = fan_bin(V, xa, ya), b1 = fan_bin(V, xa, yb), b2 = fan_bin(V, xb, ya), b3 = fan_bin(V, xb, yb);
+        const float bl = fminf(fmaxf(fminf(fminf(b0, b1), fminf(b2, b3)), -2.f), (float)nd + 1.f);
+        const float bh = fmaxf(fminf(fmaxf(fmaxf(b0, b1), fmaxf(b2, b3)), (float)nd + 1.f), -2.f);
+        const int lo = max(0, (int)floorf(bl) - 1), hi = min(nd - 1, (int)ceilf(bh) + 1);
+        const FanRay* __restrict__ R = rays + (size_t)v * nd;
+        const float* __restrict__ sk = sino + (size_t)v * nd;
+        for (int base = lo; base <= hi; base += 16 * st) {
+            for (int p = 0; 2 * p < st; ++p) {
+                const int d = base + 2 * p + half + st * hl;
+                const bool valid = d <= hi;
+                FanRay r{};
+                float sw = 0.f;
+                if (valid) {
+                    r = R[d];
+                    sw = sk[d] * r.w;
+                }
+                const bool by_col = valid && r.col, by_row = valid && !r.col;
+                if (__any_sync(0xffffffffu, by_col)) fan_tile_pass<1>(r, sw, by_col, tx0, ty0, ncol, nrow, AL, AR);
+                __syncwarp();
+                if (__any_sync(0xffffffffu, by_row)) fan_tile_pass<0>(r, sw, by_row, tx0, ty0, ncol, nrow, AL, AR);
+                __syncwarp();
+            }
+        }
+    }
+    __syncthreads();
+    for (int p = tid; p < kFtS * kFtS; p += blockDim.x) {
+        const int ly = p / kFtS, lx = p % kFtS;
+        if (lx >= ncol || ly >= nrow) continue;
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < kFtWarps; ++w)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) t += sh.accL[w][h][ly * kFtLd + lx] + sh.accR[w][h][ly * kFtLd + lx];
+        img[(size_t)(ty0 + ly) * n + tx0 + lx] = t;
+    }
+}
+
 // ------------------------------------------------------- ||Phi~||_F^2 ----
 // The taps of ray `ray` scattered into a zeroed [n][n] image (one block; a
 // ray puts at most one tap on a pixel, so the writes do not collide).
@@ -234,9 +348,39 @@ int launch_fan_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st) 
 
 int launch_fan_backproject(const dgamp_ct_plan_s* pl, const float* sino, float* img, cudaStream_t st) {
     const dim3 grd((unsigned)((pl->n + 15) / 16), (unsigned)((pl->n + 15) / 16));
-    k_fan_backproject<<<grd, 256, 0, st>>>(sino, pl->ws.fan_rays, pl->ws.fan_views, pl->n, pl->nv, pl->nd, img);
+    if (pl->bp_mode == 1 && pl->fan_stride > 0)
+        k_fan_backproject_tile<<<grd, kFtWarps * 32, 0, st>>>(sino, pl->ws.fan_rays, pl->ws.fan_views, pl->n, pl->nv,
+                                                              pl->nd, pl->fan_stride, img);
+    else
+        k_fan_backproject<<<grd, 256, 0, st>>>(sino, pl->ws.fan_rays, pl->ws.fan_views, pl->n, pl->nv, pl->nd, img);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
+}
+
+// Smallest lane stride S of the tile back-projection: for every view and
+// every bin d, the next ray d + kS (k >= 1) marched the same way is at least
+// one pixel away from ray d at both ends of the march (s = 0 and s = n - 1,
+// the same side at both, so everywhere between: the gap is linear in s).
+// Positions along a march line are monotone in the bin, so rays further
+// apart are further apart still.  0 when no S <= kFtMaxStride works.
+static int fan_tile_stride(const std::vector<FanRay>& rays, int nv, int nd, int n) {
+    const double one = 4294967296.0;
+    for (int S = 1; S <= kFtMaxStride; ++S) {
+        bool ok = true;
+        for (int v = 0; v < nv && ok; ++v) {
+            const FanRay* R = rays.data() + (size_t)v * nd;
+            for (int d = 0; d < nd && ok; ++d) {
+                int e = d + S;
+                while (e < nd && R[e].col != R[d].col) e += S;
+                if (e >= nd) continue;
+                const double g0 = (double)(R[e].P0 - R[d].P0);
+                const double g1 = g0 + (double)(n - 1) * (double)(R[e].PSTEP - R[d].PSTEP);
+                if (!(g0 * g1 > 0.0) || std::fabs(g0) < one || std::fabs(g1) < one) ok = false;
+            }
+        }
+        if (ok) return S;
+    }
+    return 0;
 }
 
 int fan_setup(dgamp_ct_plan_s* pl, const std::vector<double>& ang, double src_dist, double det_dist,
@@ -252,6 +396,8 @@ int fan_setup(dgamp_ct_plan_s* pl, const std::vector<double>& ang, double src_di
     DGCT_CUDA(cudaMemcpy(pl->ws.fan_rays, rays.data(), rays.size() * sizeof(FanRay), cudaMemcpyHostToDevice));
     DGCT_CUDA(cudaMemcpy(pl->ws.fan_views, views.data(), views.size() * sizeof(FanView), cudaMemcpyHostToDevice));
     pl->fan = 1;
+    pl->fan_stride = fan_tile_stride(rays, pl->nv, pl->nd, pl->n);
+    pl->bp_mode = pl->fan_stride > 0 ? 1 : 0;
     // ||Phi~||_F^2: ray image in ws.r[0..N), V^-1 of it in ws.r[N..2N), one FP64
     // sum of squares per ray into scratch, added on the host in ray order
     const int64_t M = pl->M, N = pl->N;

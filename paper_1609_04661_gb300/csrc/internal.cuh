@@ -169,6 +169,7 @@ struct dgamp_ct_plan_s {
     int bp_mode = 0;                       // A^T: 0 pixel-driven gather, 1 ray-driven tiles (plan-time choice)
     int pj_seg = 8;                        // A: step segments (warps) per ray group, 8/16/32 (plan-time choice)
     int fan = 0;                           // 1: flat-detector fan beam (dgamp_ct_plan_fan)
+    int fan_stride = 0;                    // fan A^T tiles: ray stride of one pass (0: tiles not applicable)
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;       // one iteration
     cudaGraphExec_t graph_k = nullptr;     // kGraphIters iterations (captured when a solve is that long)

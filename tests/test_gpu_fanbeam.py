@@ -55,13 +55,25 @@ def plan(dg, n, nv, nd, sd, dd, du, ang, **kw):
     return dg.Plan(n, nv, nd, angles=ang, fan=dict(src_dist=sd, det_dist=dd, det_spacing=du), **kw)
 
 
-@pytest.mark.parametrize("n,nv,nd,sd,dd,du,ang", GEOMS)
-def test_fan_operators_match_oracle(dg, n, nv, nd, sd, dd, du, ang):
+# A^T in both forms: ray-driven tiles (bp_mode 1; the first three geometries
+# admit a lane stride, the closest-source one does not) and the pixel gather
+TILE_OK = [True, True, True, False]
+
+
+@pytest.mark.parametrize("bp_mode", [0, 1])
+@pytest.mark.parametrize("n,nv,nd,sd,dd,du,ang,tile_ok", [g + (t,) for g, t in zip(GEOMS, TILE_OK)])
+def test_fan_operators_match_oracle(dg, n, nv, nd, sd, dd, du, ang, tile_ok, bp_mode):
     g = fanbeam.FanGeometry(n, nv, nd, sd, dd, du, angles=ang)
     rng = np.random.default_rng(n)
     x = np.cumsum(rng.standard_normal((n, n)), axis=0) * 0.1
     s = rng.standard_normal((nv, nd))
     with plan(dg, n, nv, nd, sd, dd, du, ang) as pl:
+        assert pl.tuning()["bp_mode"] == (1 if tile_ok else 0)      # the plan's default form
+        if bp_mode == 1 and not tile_ok:
+            with pytest.raises(dg.binding.DgampError):
+                pl.set_tuning(bp_mode=1)
+            return
+        pl.set_tuning(bp_mode=bp_mode)
         z = host(pl.project(cu(x), precond=False))
         bt = host(pl.backproject(cu(s), precond=False))
         zp = host(pl.project(cu(x), precond=True))
