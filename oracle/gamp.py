@@ -8,7 +8,10 @@ i.i.d.-Gaussian problem whose state evolution pins it (Section 4.4,
   Step 1  z = Phi~ x;  tau_p = ||Phi~||_F^2 tau_x / M;  p = z - tau_p s_prev
   Step 2  (s, tau_s_i) = g_out(p, y, tau_p);  tau_s = mean(tau_s_i)
   Step 3  tau_r = N / (||Phi~||_F^2 tau_s);  r = x + tau_r Phi~^T s
-  Step 4  x+ = D(r);  tau_x = tau_r * D'(r)   (D' by Eq. MC_SURE, K = 1)
+  Step 4  x+ = D(r);  tau_x = tau_r * D'(r)   (D' by Eq. MC_SURE, K = 1);
+          with several denoisers (Selected) each runs on r and the one with
+          the lowest SURE estimate of the risk R(x, tau_r) of Section 4.3
+          gives x+ and D'
 
 Initialisation x = 0, tau_x = 1 (Algorithm 1, first line); the previous
 s is taken as 0 (implied, not stated).  The result is mu = V^-1 x.
@@ -63,6 +66,7 @@ class IterLog:
     tau_r: float
     div: float
     eps: float
+    risks: list | None = None   # SURE of each candidate (Selected), else None
 
 
 def mc_divergence(denoise: Callable[[np.ndarray], np.ndarray], r: np.ndarray,
@@ -70,6 +74,36 @@ def mc_divergence(denoise: Callable[[np.ndarray], np.ndarray], r: np.ndarray,
     """Eq. MC_SURE with one probe: b^T (D(r + eps b) - D(r)) / (N eps)."""
     d2 = denoise(r + eps * b)
     return float(b.reshape(-1) @ (d2 - x_new).reshape(-1)) / (b.size * eps)
+
+
+def _divergence(D, r, x_new, b, eps) -> float:
+    """D'(r): Eq. MC_SURE, or its eps -> 0 limit b^T J_D(r) b / N for a
+    denoiser that provides its directional derivative (the learned network)."""
+    jvp = getattr(D, "jvp", None)
+    if jvp is not None:
+        return float(np.vdot(b, jvp(r, b))) / r.size
+    return mc_divergence(D, r, x_new, b, eps)
+
+
+def sure_risk(r: np.ndarray, x_new: np.ndarray, div: float, tau_r: float) -> float:
+    """Stein's unbiased estimate of the denoiser's risk R(x, tau_r) of
+    Section 4.3, (1/N) E||D(x + sqrt(tau_r) psi) - x||^2, from its input r and
+    output x_new alone: ||x_new - r||^2 / N - tau_r + 2 tau_r D'(r), with D'
+    the (Monte-Carlo) divergence of Eq. MC_SURE (the estimate behind that
+    equation's reference).  Unbiased when r = x + sqrt(tau_r) psi."""
+    d = (np.asarray(x_new, dtype=np.float64) - np.asarray(r, dtype=np.float64)).reshape(-1)
+    return float(d @ d) / d.size - tau_r + 2.0 * tau_r * div
+
+
+class Selected:
+    """Step 4 with several denoisers (the plain one first): every iteration
+    runs each of them on r, with its own divergence, and keeps the one whose
+    SURE risk estimate is lowest; a tie keeps the earlier one.  With the
+    learned network second, prox-TV is its fallback and the judge of its
+    error."""
+
+    def __init__(self, candidates):
+        self.candidates = list(candidates)
 
 
 def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
@@ -100,21 +134,28 @@ def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
         r = x + tau_r * PhiT(s).reshape(x.shape)
         # Step 4: denoising and divergence
         D = denoise_factory(tau_r)
-        x_new = D(r)
         b = probe(t, r.size).reshape(r.shape)
         eps = opts.eps_rel * max(float(np.max(np.abs(r))), 1e-6)
-        jvp = getattr(D, "jvp", None)
-        if jvp is not None:
-            # Eq. MC_SURE in its eps -> 0 limit, b^T J_D(r) b / N, for a
-            # denoiser that provides its directional derivative
-            div = float(np.vdot(b, jvp(r, b))) / r.size
+        risks = None
+        if isinstance(D, Selected):
+            best = None
+            risks = []
+            for Dk in D.candidates:
+                xk = Dk(r)
+                dk = _divergence(Dk, r, xk, b, eps)
+                rk = sure_risk(r, xk, dk, tau_r)
+                risks.append(rk)
+                if best is None or rk < best[2]:
+                    best = (xk, dk, rk)
+            x_new, div = best[0], best[1]
         else:
-            div = mc_divergence(D, r, x_new, b, eps)
+            x_new = D(r)
+            div = _divergence(D, r, x_new, b, eps)
         tau_x = max(tau_r * div, opts.tau_x_floor * tau_r)
         if opts.damp_x != 1.0:
             x_new = opts.damp_x * x_new + (1.0 - opts.damp_x) * x
         if log is not None:
-            log.append(IterLog(tau_x, tau_p, tau_s, tau_r, div, eps))
+            log.append(IterLog(tau_x, tau_p, tau_s, tau_r, div, eps, risks))
         x = x_new
         s_prev = s
         if on_iter is not None:
@@ -124,13 +165,16 @@ def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
 
 def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
              opts: Options | None = None, return_x: bool = False, log=None,
-             frob2: float | None = None, on_iter=None, cnn=None, cnn_bf16: bool = True):
+             frob2: float | None = None, on_iter=None, cnn=None, cnn_bf16: bool = True,
+             select: bool = False):
     """D-GAMP-CT on one slice (parity unpinned).
 
     The denoiser is prox-TV, or with ``cnn = (ws, bs, scaled)`` the learned
     residual network of ``oracle.cnn`` in its BF16-activation form
     (``cnn_bf16=False``: unrounded FP64 activations), run at
-    sigma = sqrt(tau_r) (scaled) or sigma = 1 (blind).  The full
+    sigma = sqrt(tau_r) (scaled) or sigma = 1 (blind).  With ``select`` both
+    run every iteration and the lower SURE risk estimate decides
+    (:class:`Selected`, prox-TV first).  The full
     reconstruction has no closed form and the paper prints no synthetic
     result; it is checked only through its pinned parts and the tests'
     qualitative checks (error falls over the iterations, the Onsager term
@@ -160,17 +204,24 @@ def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
             s, tsi, _z0, _v = _out.output_step(p, yv, tau_p, I0, truncate=opts.truncate_z)
         return s, tsi
 
-    def denoise_factory(tau_r):
-        if cnn is not None:
-            ws, bs, scaled = cnn
-            sigma = float(np.sqrt(tau_r)) if scaled else 1.0
-            return _cnn.Denoiser(sigma, ws, bs, bf16=cnn_bf16)
+    if select and cnn is None:
+        raise ValueError("select needs the learned network (cnn)")
+
+    def plain(tau_r):
         lam = opts.c_tv * np.sqrt(tau_r)
         if opts.tv_metric:
             q_max = _pre.vtv_inverse_norm_bound(geom)
             return lambda r: _tv.tv_prox_metric(r, lam, opts.k_tv,
                                                 lambda u: _pre.vtv_inverse(u, geom), q_max)
         return lambda r: _tv.tv_prox(r, lam, opts.k_tv)
+
+    def denoise_factory(tau_r):
+        if cnn is None:
+            return plain(tau_r)
+        ws, bs, scaled = cnn
+        sigma = float(np.sqrt(tau_r)) if scaled else 1.0
+        learned = _cnn.Denoiser(sigma, ws, bs, bf16=cnn_bf16)
+        return Selected([plain(tau_r), learned]) if select else learned
 
     def probe(t, n):
         return _philox.probe_normals(n, opts.seed, t, opts.slice_id)
