@@ -75,7 +75,26 @@ class Stats(C.Structure):
     _fields_ = [("tau_x", C.POINTER(C.c_double)), ("tau_p", C.POINTER(C.c_double)),
                 ("tau_s", C.POINTER(C.c_double)), ("tau_r", C.POINTER(C.c_double)),
                 ("div", C.POINTER(C.c_double)), ("iters_done", C.c_int32),
-                ("newton_capped", C.c_int32), ("tau_x_floored", C.c_int32)]
+                ("newton_capped", C.c_int32), ("tau_x_floored", C.c_int32),
+                ("risk_plain", C.POINTER(C.c_double)), ("risk_learned", C.POINTER(C.c_double)),
+                ("learned_kept", C.c_int32)]
+
+
+_STAT_ARRAYS = ("tau_x", "tau_p", "tau_s", "tau_r", "div")
+
+
+def _new_stats(iters: int):
+    """A Stats record with host arrays for every per-iteration field."""
+    arrays = {k: np.zeros(iters) for k in _STAT_ARRAYS + ("risk_plain", "risk_learned")}
+    p = {k: a.ctypes.data_as(C.POINTER(C.c_double)) for k, a in arrays.items()}
+    st = Stats(*[p[k] for k in _STAT_ARRAYS], 0, 0, 0, p["risk_plain"], p["risk_learned"], 0)
+    return st, arrays
+
+
+def _stats_dict(st, arrays):
+    arrays.update(iters_done=st.iters_done, newton_capped=st.newton_capped, tau_x_floored=st.tau_x_floored,
+                  learned_kept=st.learned_kept)
+    return arrays
 
 
 _lib = None
@@ -362,17 +381,14 @@ class Plan:
         mu = self._img() if mu_out is None else mu_out
         st, arrays = None, None
         if with_stats:
-            arrays = {k: np.zeros(iters) for k in ("tau_x", "tau_p", "tau_s", "tau_r", "div")}
-            st = Stats(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrays.values()], 0, 0, 0)
+            st, arrays = _new_stats(iters)
         rc = self._lib.dgamp_ct_solve(self._h, _ptr(counts, self.M, "counts"), float(I0), int(iters),
                                       _ptr(mu, self.N, "mu_out"),
                                       _ptr(x_out, self.N, "x_out") if x_out is not None else None,
                                       C.byref(st) if st is not None else None, _stream())
         _check(rc, "dgamp_ct_solve")
         if with_stats:
-            arrays.update(iters_done=st.iters_done, newton_capped=st.newton_capped,
-                          tau_x_floored=st.tau_x_floored)
-            return mu, arrays
+            return mu, _stats_dict(st, arrays)
         return mu
 
     def solve_host(self, counts: np.ndarray, I0: float, iters: int, mu_out: np.ndarray | None = None):
@@ -400,7 +416,11 @@ class Plan:
             fused = self.tuning()["sino_fused"] and not self.options.output_moments
             sino = ["sino_step"] if fused else ["filter_z", "output_step", "filter_s"]
             names = ["project"] + sino + ["backproject_update", "probe_input"]
-        if self.options.denoiser == 1:
+        if self.options.denoiser == 2:
+            k = cnt.value - len(names) - 4      # the TV launches
+            names += ["cnn_pair", "probe_tv"] + [f"tv_block{i}" for i in range(k - 1)] + ["tv_block_final"]
+            names += ["select_sums", "select_final"]
+        elif self.options.denoiser == 1:
             names += ["cnn_pair", "denoise_final"]
         elif metric:
             # prox-TV in the (V^T V)^{-1} norm: a dual step from p = 0, then per
@@ -415,7 +435,7 @@ class Plan:
         return dict(zip(names, [arr[i] for i in range(cnt.value)]))
 
     def set_cnn(self, net):
-        """Attach a learned denoiser (a CNN) or detach it (None); use with options.denoiser = 1."""
+        """Attach a learned denoiser (a CNN) or detach it (None); use with options.denoiser = 1 (the network) or 2 (the network judged by prox-TV)."""
         _check(self._lib.dgamp_ct_plan_set_cnn(self._h, net._h if net is not None else None), "plan_set_cnn")
         self._cnn = net
 
@@ -546,17 +566,14 @@ def solve_batched(plans, counts, I0, iters: int, mu_out=None, with_stats: bool =
     i0 = np.ascontiguousarray(I0, dtype=np.float64)
     st, arrays = None, None
     if with_stats:
-        arrays = [{k: np.zeros(iters) for k in ("tau_x", "tau_p", "tau_s", "tau_r", "div")} for _ in range(n)]
-        st = (Stats * n)(*[Stats(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in ar.values()], 0, 0, 0)
-                           for ar in arrays])
+        made = [_new_stats(iters) for _ in range(n)]
+        arrays = [a for _, a in made]
+        st = (Stats * n)(*[r for r, _ in made])
     rc = lib.dgamp_ct_solve_batched(n, P, Cn, i0.ctypes.data_as(C.c_void_p), int(iters), Mu,
                                     st if st is not None else None, _stream())
     _check(rc, "dgamp_ct_solve_batched")
     if with_stats:
-        for k in range(n):
-            arrays[k].update(iters_done=st[k].iters_done, newton_capped=st[k].newton_capped,
-                             tau_x_floored=st[k].tau_x_floored)
-        return mus, arrays
+        return mus, [_stats_dict(st[k], arrays[k]) for k in range(n)]
     return mus
 
 
@@ -605,17 +622,14 @@ class Batch:
         i0 = np.ascontiguousarray(I0, dtype=np.float64)
         st, arrays = None, None
         if with_stats:
-            arrays = [{k: np.zeros(iters) for k in ("tau_x", "tau_p", "tau_s", "tau_r", "div")} for _ in range(n)]
-            st = (Stats * n)(*[Stats(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in ar.values()], 0, 0, 0)
-                               for ar in arrays])
+            made = [_new_stats(iters) for _ in range(n)]
+            arrays = [a for _, a in made]
+            st = (Stats * n)(*[r for r, _ in made])
         rc = self._lib.dgamp_ct_batch_solve(self._h, Cn, i0.ctypes.data_as(C.c_void_p), int(iters), Mu,
                                             st if st is not None else None, _stream())
         _check(rc, "dgamp_ct_batch_solve")
         if with_stats:
-            for k in range(n):
-                arrays[k].update(iters_done=st[k].iters_done, newton_capped=st[k].newton_capped,
-                                 tau_x_floored=st[k].tau_x_floored)
-            return mus, arrays
+            return mus, [_stats_dict(st[k], arrays[k]) for k in range(n)]
         return mus
 
 

@@ -48,7 +48,7 @@ static int ilog2(int v) {
 }
 
 static bool options_ok(const dgamp_ct_options* o) {
-    if (o->denoiser != 0 && o->denoiser != 1) return false;
+    if (o->denoiser < 0 || o->denoiser > 2) return false;
     if (o->k_tv < 0 || o->k_tv > 100000) return false;
     if (!std::isfinite(o->c_tv) || o->c_tv < 0) return false;
     if (!std::isfinite(o->eps_rel) || o->eps_rel <= 0) return false;
@@ -229,6 +229,9 @@ int raise_smem_limit(const void* kernel, int bytes) {
 // every SM).
 static bool fused_sino_now(const dgamp_ct_plan_s* pl) { return pl->sino_fused && !pl->opt.output_moments; }
 
+// denoiser 1 (the CNN) and 2 (the CNN judged by prox-TV) run the network
+static bool uses_cnn(const dgamp_ct_plan_s* pl) { return pl->opt.denoiser == 1 || pl->opt.denoiser == 2; }
+
 // One iteration of Algorithm 1 (Steps 1-4); every scalar it needs lives in
 // DevScalars, so the same launch sequence serves every iteration.
 // With `ev` non-NULL, ev[i] is recorded before kernel i and ev[count] after
@@ -273,8 +276,27 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
     }
     DGCT_TRY(mark());
     // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r
-    DGCT_TRY(launch_probe_input(pl, 0, st, pl->opt.denoiser == 1 ? 1 : 0));
-    if (pl->opt.denoiser == 1) {
+    DGCT_TRY(launch_probe_input(pl, 0, st, uses_cnn(pl) ? 1 : 0));
+    if (pl->opt.denoiser == 2) {
+        // both denoisers on r, each with its divergence: the CNN and its
+        // forward-mode derivative along b, then r + eps b beside r (the same
+        // b) for prox-TV, written to dn[2] with its divergence in S; the lower
+        // SURE risk estimate decides x, D' and tau_x
+        const size_t N = (size_t)pl->N;
+        DGCT_TRY(mark());
+        DGCT_TRY(cnn_denoise_jvp(pl->cnn, w.r, w.S, pl->n, pl->dn, pl->opt.cnn_scale, st));
+        DGCT_TRY(mark());
+        DGCT_TRY(launch_probe_input(pl, 0, st, 0));
+        const int ntv = tv_num_launches(pl, 1, 0.0);
+        for (int i = 0; i < ntv; ++i) {
+            DGCT_TRY(mark());
+            DGCT_TRY(launch_tv_chunk(pl, 2, 1, 0.0, i, pl->dn + 2 * N, 0, 0, &w.S->div_plain, st));
+        }
+        DGCT_TRY(mark());
+        DGCT_TRY(launch_select(pl, 0, st));
+        DGCT_TRY(mark());
+        DGCT_TRY(launch_select(pl, 1, st));
+    } else if (pl->opt.denoiser == 1) {
         // learned denoiser: D(r) and its forward-mode derivative J_D(r) b, then x, D', tau_x
         DGCT_TRY(mark());
         DGCT_TRY(cnn_denoise_jvp(pl->cnn, w.r, w.S, pl->n, pl->dn, pl->opt.cnn_scale, st));
@@ -307,6 +329,8 @@ static int front_segments(const dgamp_ct_plan_s* pl) {
 
 // kernels one iteration launches: Steps 1-3, the probe, the denoiser
 static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
+    if (pl->opt.denoiser == 2 && pl->cnn)
+        return front_kernels(pl) + 1 + cnn_launches_per_pair(pl->cnn) + 1 + tv_num_launches(pl, 1, 0.0) + 2;
     if (pl->opt.denoiser == 1 && pl->cnn) return front_kernels(pl) + 1 + cnn_launches_per_pair(pl->cnn) + 1;
     return front_kernels(pl) + 1 + tv_num_launches(pl, 1, 0.0);
 }
@@ -314,6 +338,8 @@ static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
 // timed segments of one iteration (dgamp_ct_profile_iteration): as above,
 // except that the learned denoiser's launches form one segment
 static int segments_per_iteration(const dgamp_ct_plan_s* pl) {
+    // denoiser 2: the probe, the CNN pair, the second probe, the TV launches, the two selection kernels
+    if (pl->opt.denoiser == 2 && pl->cnn) return front_segments(pl) + 3 + tv_num_launches(pl, 1, 0.0) + 2;
     if (pl->opt.denoiser == 1 && pl->cnn) return front_segments(pl) + 3;
     return front_segments(pl) + 1 + tv_num_launches(pl, 1, 0.0);
 }
@@ -494,7 +520,8 @@ int dgamp_ct_plan_set_cnn(dgamp_ct_plan_t pl, dgamp_ct_cnn_t net) {
     pl->cnn = net;
     if (!net) return DGAMP_CT_OK;
     if (!pl->dn) {
-        cudaError_t e = cudaMalloc(&pl->dn, 2 * (size_t)pl->N * sizeof(float));
+        // D(r) and J_D(r) b of the CNN, and prox-TV's D(r) when it judges the CNN (denoiser 2)
+        cudaError_t e = cudaMalloc(&pl->dn, 3 * (size_t)pl->N * sizeof(float));
         if (e != cudaSuccess) {
             pl->dn = nullptr;
             pl->cnn = nullptr;
@@ -642,7 +669,7 @@ int dgamp_ct_precond_image(dgamp_ct_plan_t pl, const float* d_in, float* d_out, 
 int dgamp_ct_profile_iteration(dgamp_ct_plan_t pl, int32_t reps, double* h_ms, int32_t cap,
                                int32_t* count, void* stream) {
     if (!pl || reps < 1 || !h_ms || !count) return DGAMP_CT_ERR_INVALID_ARG;
-    if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
+    if (uses_cnn(pl) && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
     const int nk = segments_per_iteration(pl);
     *count = nk;
     if (cap < nk) return DGAMP_CT_ERR_INVALID_ARG;
@@ -711,7 +738,7 @@ static int solve_begin(dgamp_ct_plan_s* pl, const float* d_counts, double I0, cu
     DGCT_CUDA(cudaMemsetAsync(w.x, 0, N * sizeof(float), st));
     DGCT_CUDA(cudaMemsetAsync(w.s, 0, M * sizeof(float), st));
     DGCT_TRY(launch_stage_image(pl, w.x, st, pl->opt.storage));
-    if (pl->opt.denoiser == 1) {
+    if (uses_cnn(pl)) {
         // the network may have been used (and its workspace regrown) since the
         // graph was captured: make room again and re-capture if it moved
         DGCT_TRY(cnn_prepare_pair(pl->cnn, pl->n));
@@ -730,7 +757,7 @@ int dgamp_ct_solve_trace(dgamp_ct_plan_t pl, const float* d_counts, double I0, i
                          float* d_r_trace, double* h_tau_r, void* stream) {
     if (!pl || !d_counts || !d_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
     if (iters < 1 || iters > kMaxIters || !(I0 > 0) || !std::isfinite(I0)) return DGAMP_CT_ERR_INVALID_ARG;
-    if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
+    if (uses_cnn(pl) && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = (size_t)pl->N;
     DGCT_TRY(solve_begin(pl, d_counts, I0, st));
@@ -755,7 +782,7 @@ int dgamp_ct_solve(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t
                    float* d_x_out, dgamp_ct_stats* stats, void* stream) {
     if (!pl || !d_counts || !d_mu_out) return DGAMP_CT_ERR_INVALID_ARG;
     if (iters < 1 || iters > kMaxIters || !(I0 > 0) || !std::isfinite(I0)) return DGAMP_CT_ERR_INVALID_ARG;
-    if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
+    if (uses_cnn(pl) && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace& w = pl->ws;
     const size_t N = (size_t)pl->N;
@@ -791,12 +818,16 @@ int fill_stats(const dgamp_ct_plan_s* pl, int iters, dgamp_ct_stats* stats) {
         if (stats->tau_s) stats->tau_s[t] = lg[t].tau_s;
         if (stats->tau_r) stats->tau_r[t] = lg[t].tau_r;
         if (stats->div) stats->div[t] = lg[t].div;
+        const bool judged = pl->opt.denoiser == 2;
+        if (stats->risk_plain) stats->risk_plain[t] = judged ? lg[t].risk_plain : NAN;
+        if (stats->risk_learned) stats->risk_learned[t] = judged ? lg[t].risk_learned : NAN;
     }
+    stats->learned_kept = (int32_t)hs.learned_kept;
     stats->iters_done = (int32_t)(hs.t - 1u);
     stats->newton_capped = (int32_t)hs.newton_capped;
     stats->tau_x_floored = (int32_t)hs.floored;
     // a tensor-core convolution of the learned denoiser whose bounded wait ran out
-    if (pl->opt.denoiser == 1 && pl->cnn) DGCT_TRY(cnn_take_timeout(pl->cnn));
+    if (uses_cnn(pl) && pl->cnn) DGCT_TRY(cnn_take_timeout(pl->cnn));
     if (hs.nonfinite) return DGAMP_CT_ERR_NONFINITE;
     return DGAMP_CT_OK;
 }
@@ -816,7 +847,7 @@ int dgamp_ct_solve_host(dgamp_ct_plan_t pl, const float* h_counts, double I0, in
     if (rc != DGAMP_CT_OK && rc != DGAMP_CT_ERR_NONFINITE) return rc;
     DGCT_CUDA(cudaMemcpyAsync(h_mu_out, pl->ws.r, N * sizeof(float), cudaMemcpyDeviceToHost, st));
     DGCT_CUDA(cudaStreamSynchronize(st));
-    if (!stats && pl->opt.denoiser == 1 && pl->cnn) DGCT_TRY(cnn_take_timeout(pl->cnn));
+    if (!stats && uses_cnn(pl) && pl->cnn) DGCT_TRY(cnn_take_timeout(pl->cnn));
     return rc;
 }
 

@@ -74,9 +74,10 @@ int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float*
         const dgamp_ct_plan_t pl = plans[i];
         if (!pl || !d_counts[i] || !d_mu_out[i] || !(I0[i] > 0) || !std::isfinite(I0[i])) return DGAMP_CT_ERR_INVALID_ARG;
         if (pl->device != device) return DGAMP_CT_ERR_INVALID_ARG;
-        if (pl->opt.denoiser == 1 && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
+        const bool cnn = pl->opt.denoiser == 1 || pl->opt.denoiser == 2;
+        if (cnn && !pl->cnn) return DGAMP_CT_ERR_INVALID_ARG;
         if (!seen.insert(pl).second) return DGAMP_CT_ERR_INVALID_ARG;   // a plan holds one slice's state
-        if (pl->opt.denoiser == 1 && !nets.insert(pl->cnn).second) return DGAMP_CT_ERR_INVALID_ARG;
+        if (cnn && !nets.insert(pl->cnn).second) return DGAMP_CT_ERR_INVALID_ARG;
         work[i] = (int64_t)pl->nv * pl->nd * pl->n;                   // Joseph steps of one projection
     }
     const int32_t queues = std::min<int32_t>(n, kBatchStreams);

@@ -53,6 +53,12 @@ struct DevScalars {
     unsigned int floored;
     unsigned int nonfinite;
     unsigned int div_pending;   // TV divergence partial sums left for the next output step (0: none)
+    // denoiser 2 (learned, judged by prox-TV): the candidates' divergences
+    // and SURE risk estimates of the current iteration, the kept one
+    double div_plain, div_learned;
+    double risk_plain, risk_learned;
+    unsigned int keep_learned;  // 1: this iteration keeps the CNN's output
+    unsigned int learned_kept;  // iterations of the solve that kept it
 };
 
 // The TV weight: lambda = c_tv sqrt(tau_r) inside a solve, the caller's lambda otherwise.
@@ -79,7 +85,10 @@ struct FanView {
 };
 
 // Per-iteration log record (what dgamp_ct_stats exposes).
-struct IterLog { double tau_x, tau_p, tau_s, tau_r, div, eps; };
+struct IterLog {
+    double tau_x, tau_p, tau_s, tau_r, div, eps;
+    double risk_plain = 0.0, risk_learned = 0.0;   // denoiser 2 only
+};
 
 // One slice of a batch (dgamp_ct_batch_*): its geometry, the device
 // workspace of its plan, its options, the per-solve inputs and outputs, and
@@ -408,6 +417,9 @@ int launch_fan_backproject(const dgamp_ct_plan_s* pl, const float* sino, float* 
 // x, staging, divergence and tau_x from D(r) and J_D(r) b (learned denoiser)
 int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_out, int solve_mode, int t_arg,
                          double* div_out, cudaStream_t st);
+// denoiser 2: part 0 forms both candidates' SURE risk estimates and keeps one,
+// part 1 writes the kept output as x, the staged copies, tau_x and the log
+int launch_select(const dgamp_ct_plan_s* pl, int part, cudaStream_t st);
 // Batched execution (batch.cu): device descriptors and tables of a batch,
 // and the grid of each phase (blocks; clusters for kPhView)
 struct BatchExec {

@@ -833,6 +833,125 @@ int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_ou
     return DGAMP_CT_OK;
 }
 
+// ------------------------- denoiser 2: the CNN judged by prox-TV -----
+// Both denoisers have run on r: dn[0] = D_cnn(r), dn[1] = J_cnn(r) b,
+// dn[2] = D_tv(r), and S->div_plain holds prox-TV's divergence (Eq. MC_SURE).
+// k_select_sums adds, over the pixels, (D_cnn(r) - r)^2, b J_cnn b and
+// (D_tv(r) - r)^2 (FP32 per thread, FP64 per block and across blocks, in a
+// fixed order); its last block forms each candidate's SURE risk estimate
+//   ||D(r) - r||^2 / N - tau_r + 2 tau_r D'(r)
+// and keeps the CNN where its estimate is strictly lower.  k_select_final
+// then writes the kept output as x (damped), the staged copies, tau_x, the
+// log record and the next t.
+constexpr int kSelBlocks = 256;
+
+__global__ void __launch_bounds__(256)
+k_select_sums(const float* __restrict__ r, const float* __restrict__ dn, const float* __restrict__ bprobe,
+              long long N, DevScalars* S, double* __restrict__ partial) {
+    __shared__ double red[32];
+    __shared__ bool am_last;
+    pdl_wait();
+    float s_cnn = 0.f, s_jb = 0.f, s_tv = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float rv = r[i];
+        const float dc = dn[i] - rv, dt = dn[2 * N + i] - rv;
+        s_cnn = fmaf(dc, dc, s_cnn);
+        s_jb = fmaf(bprobe[i], dn[N + i], s_jb);
+        s_tv = fmaf(dt, dt, s_tv);
+    }
+    const double a = block_sum((double)s_cnn, red);
+    const double b = block_sum((double)s_jb, red);
+    const double c = block_sum((double)s_tv, red);
+    const int nblk = gridDim.x, bid = blockIdx.x;
+    if (threadIdx.x == 0) {
+        partial[3 * bid] = a;
+        partial[3 * bid + 1] = b;
+        partial[3 * bid + 2] = c;
+        __threadfence();
+        const unsigned prev = atomicAdd(&S->done_div, 1u);
+        am_last = (prev == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double pa = 0.0, pb = 0.0, pc = 0.0;
+    const volatile double* P = partial;
+    for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
+        pa += P[3 * k];
+        pb += P[3 * k + 1];
+        pc += P[3 * k + 2];
+    }
+    const double ta = block_sum(pa, red), tb = block_sum(pb, red), tc = block_sum(pc, red);
+    if (threadIdx.x != 0) return;
+    const double Nd = (double)N, tau_r = S->tau_r;
+    const double div_l = tb / Nd, div_p = S->div_plain;
+    const double risk_l = ta / Nd - tau_r + 2.0 * tau_r * div_l;
+    const double risk_p = tc / Nd - tau_r + 2.0 * tau_r * div_p;
+    const unsigned keep = risk_l < risk_p ? 1u : 0u;
+    S->div_learned = div_l;
+    S->risk_learned = risk_l;
+    S->risk_plain = risk_p;
+    S->keep_learned = keep;
+    S->div = keep ? div_l : div_p;
+    S->done_div = 0u;
+}
+
+__global__ void __launch_bounds__(1024)
+k_select_final(const float* __restrict__ dn, int n, DevScalars* S, TvFinal F) {
+    __shared__ float tile[TB][TB + 1];
+    pdl_wait();
+    const size_t N = (size_t)n * n;
+    const int tid = threadIdx.x, ta = tid >> 5, tb = tid & 31;
+    const int gi = blockIdx.y * TB + ta, gj = blockIdx.x * TB + tb;
+    const float* __restrict__ src = S->keep_learned ? dn : dn + 2 * N;
+    float xv = 0.f;
+    if (gi < n && gj < n) {
+        const size_t o = (size_t)gi * n + gj;
+        xv = src[o];
+        if (F.damp_x != 1.f) xv = F.damp_x * xv + (1.f - F.damp_x) * F.x_out[o];
+        F.x_out[o] = xv;
+        stage_store(F.XR, F.xbf, (size_t)gi * F.ldp + kPad + gj, xv);
+    }
+    tile[ta][tb] = xv;
+    __syncthreads();
+    const int gj2 = blockIdx.x * TB + ta, gi2 = blockIdx.y * TB + tb;
+    if (gi2 < n && gj2 < n) stage_store(F.XC, F.xbf, (size_t)gj2 * F.ldp + kPad + gi2, tile[tb][ta]);
+    if (blockIdx.x != 0 || blockIdx.y != 0 || tid != 0) return;
+    // tau_x from the kept divergence, the log record and the next t (one thread)
+    const double tau_r = S->tau_r, div = S->div;
+    double tx = tau_r * div;
+    const double fl = F.tau_x_floor * tau_r;
+    if (!(tx >= fl)) { tx = fl; S->floored += 1u; }
+    if (!isfinite(tx)) S->nonfinite += 1u;
+    S->tau_x = tx;
+    S->learned_kept += S->keep_learned;
+    const unsigned tt = S->t;
+    if (tt >= 1u && tt <= (unsigned)kMaxIters) {
+        IterLog L;
+        L.tau_x = tx; L.tau_p = S->tau_p; L.tau_s = S->tau_s; L.tau_r = tau_r;
+        L.div = div; L.eps = S->eps;
+        L.risk_plain = S->risk_plain;
+        L.risk_learned = S->risk_learned;
+        F.log[tt - 1] = L;
+    }
+    S->t = tt + 1u;
+}
+
+int launch_select(const dgamp_ct_plan_s* pl, int part, cudaStream_t st) {
+    const int n = pl->n;
+    const long long N = pl->N;
+    if (part == 0) {
+        DGCT_CUDA(launch_pdl(k_select_sums, dim3(kSelBlocks), dim3(256), 0, st, (const float*)pl->ws.r,
+                             (const float*)pl->dn, (const float*)pl->ws.b, N, pl->ws.S, pl->ws.partial));
+        return DGAMP_CT_OK;
+    }
+    TvFinal F = make_tv_final(pl, pl->ws.x, 1, 0, nullptr);
+    dim3 grd((n + TB - 1) / TB, (n + TB - 1) / TB);
+    DGCT_CUDA(launch_pdl(k_select_final, grd, dim3(1024), 0, st, (const float*)pl->dn, n, pl->ws.S, F));
+    return DGAMP_CT_OK;
+}
+
 // ------------------------------------------------------------ probe -----
 __global__ void k_probe(long long n, unsigned t, unsigned slice, uint2 key, float* __restrict__ b,
                         uint32_t* __restrict__ words) {

@@ -84,6 +84,78 @@ def test_learned_solve_matches_oracle(dg, scaled):
     assert rel(mu, mu_ref) < 2e-2
 
 
+@pytest.mark.parametrize("c_tv", [3.0, 0.3])
+def test_judged_learned_solve_matches_oracle(dg, c_tv):
+    """Denoiser 2: the seeded network and prox-TV both run every iteration
+    and the lower SURE risk estimate keeps one (oracle.gamp.Selected).  The
+    GPU must keep the same denoiser as the oracle in every iteration, with
+    the same risk estimates and reconstruction to the learned solve's 2e-2.
+    c_tv = 0.3 makes prox-TV a weak smoother, so the network is kept in some
+    iterations; with c_tv = 3 prox-TV is kept throughout."""
+    from paper_1609_04661_gb300.binding import flatten_params
+    c = synth.make_case("ellipse64_v30")
+    g = Geometry(c["n"], c["n_views"], c["n_det"])
+    T = 5
+    ws, bs = cnn.init_params(21)
+    rng = np.random.default_rng(22)
+    bs = [np.asarray(rng.standard_normal(b.shape) * 0.02, dtype=np.float32).astype(np.float64) for b in bs]
+    kw = dict(c_tv=c_tv, k_tv=20, damp_x=0.5, damp_s=0.5)
+    log = []
+    mu_ref, x_ref = gamp.ct_solve(c["y"], c["I0"], g, T, gamp.Options(**kw), return_x=True, log=log,
+                                  cnn=(ws, bs, True), select=True)
+    keep_ref = [bool(lg.risks[1] < lg.risks[0]) for lg in log]
+    with dg.CNN(cnn.LAYERS) as net, dg.Plan(g.n, g.n_views, g.n_det, denoiser=2, cnn_scale=1, **kw) as pl:
+        net.set_params(flatten_params(ws, bs))
+        pl.set_cnn(net)
+        xo = torch.empty((g.n, g.n), device="cuda")
+        mu, st = pl.solve(torch.as_tensor(c["y"]).cuda(), c["I0"], T, with_stats=True, x_out=xo)
+        mu, xo = mu.cpu().numpy(), xo.cpu().numpy()
+    keep = [bool(a < b) for a, b in zip(st["risk_learned"], st["risk_plain"])]
+    print(f"c_tv {c_tv}: kept the network in iterations {[t + 1 for t, k in enumerate(keep_ref) if k]}")
+    assert st["iters_done"] == T
+    assert keep == keep_ref
+    assert st["learned_kept"] == sum(keep_ref)
+    assert np.allclose(st["risk_plain"], [lg.risks[0] for lg in log], rtol=2e-2, atol=1e-4)
+    assert np.allclose(st["risk_learned"], [lg.risks[1] for lg in log], rtol=2e-2, atol=1e-4)
+    assert np.allclose(st["tau_r"], [lg.tau_r for lg in log], rtol=2e-2)
+    assert rel(xo, x_ref) < 2e-2
+    assert rel(mu, mu_ref) < 2e-2
+
+
+def test_judged_solve_keeps_the_shipped_network_where_it_wins(dg, weights):
+    """Denoiser 2 with the shipped weights and c_tv = 3 on the 64 x 64 case:
+    the oracle's SURE estimates keep the network in every one of the five
+    iterations (by 15% or more), so the GPU must keep it in every iteration
+    too, and then its solve is the learned solve (denoiser 1) up to the order
+    of the divergence sum."""
+    from paper_1609_04661_gb300.binding import unflatten_params
+    params, scaled = weights
+    c = synth.make_case("ellipse64_v30")
+    g = Geometry(c["n"], c["n_views"], c["n_det"])
+    T = 5
+    kw = dict(c_tv=3.0, k_tv=20, damp_x=0.5, damp_s=0.5)
+    ws, bs = unflatten_params(params)
+    ws = [cnn.bf16_round(w) for w in ws]
+    log = []
+    gamp.ct_solve(c["y"], c["I0"], g, T, gamp.Options(**kw), log=log, cnn=(ws, bs, bool(scaled)), select=True)
+    assert all(lg.risks[1] < 0.85 * lg.risks[0] if lg.risks[0] > 0 else lg.risks[1] < lg.risks[0] for lg in log)
+    y = torch.as_tensor(c["y"]).cuda()
+    with dg.CNN(cnn.LAYERS) as net:
+        net.set_params(params)
+        with dg.Plan(g.n, g.n_views, g.n_det, denoiser=2, cnn_scale=int(scaled), **kw) as pl:
+            pl.set_cnn(net)
+            mu2, st2 = pl.solve(y, c["I0"], T, with_stats=True)
+            mu2 = mu2.cpu().numpy()
+        with dg.Plan(g.n, g.n_views, g.n_det, denoiser=1, cnn_scale=int(scaled), **kw) as pl:
+            pl.set_cnn(net)
+            mu1, st1 = pl.solve(y, c["I0"], T, with_stats=True)
+            mu1 = mu1.cpu().numpy()
+    assert st2["learned_kept"] == T
+    assert np.all(st2["risk_learned"] < st2["risk_plain"])
+    assert np.allclose(st2["div"], st1["div"], rtol=1e-4)
+    assert rel(mu2, mu1) < 1e-4
+
+
 def test_shipped_network_in_a_solve_matches_oracle(dg, weights):
     """The shipped weights inside two damped iterations of the 64 x 64 solve,
     against the oracle with the same BF16-rounded weights and activation
