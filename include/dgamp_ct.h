@@ -74,7 +74,10 @@ typedef struct {
                               judge: each one's risk R(x, tau_r) of Section 4.3 is estimated
                               by SURE, ||D(r) - r||^2 / N - tau_r + 2 tau_r D'(r) (D' from
                               Eq. MC_SURE for prox-TV, its eps -> 0 limit for the CNN), and
-                              the lower estimate gives x and tau_x (a tie keeps prox-TV) */
+                              the lower estimate gives x and tau_x (a tie keeps prox-TV); the
+                              CNN is kept only while 0 < D' < M/N (tau_x = tau_r D' is a
+                              variance, and below M/N tau_r shrinks from one iteration to
+                              the next when tau_p is large) */
     int32_t  k_tv;         /* Chambolle iterations per denoiser call (fixed)     */
     double   c_tv;         /* TV weight: lambda = c_tv * sqrt(tau_r)             */
     double   eps_rel;      /* MC step: eps = eps_rel * max(max|r|, 1e-6) (Eq. MC_SURE);
@@ -132,10 +135,11 @@ typedef struct {
     int32_t newton_capped; /* output-step elements that hit the iteration cap   */
     int32_t tau_x_floored; /* iterations whose tau_x took the floor             */
     /* Denoiser 2 only (optional host arrays of length >= iters, NULL = skip):
-       the SURE risk estimates of prox-TV and of the CNN in iteration t;
-       the CNN's output was kept where risk_learned[t-1] < risk_plain[t-1]. */
+       the SURE risk estimates of prox-TV and of the CNN in iteration t, and
+       whether that iteration kept the CNN's output. */
     double* risk_plain;
     double* risk_learned;
+    int32_t* kept_learned; /* 1 where iteration t kept the CNN's output, else 0  */
     int32_t learned_kept;  /* denoiser 2: iterations that kept the CNN's output */
 } dgamp_ct_stats;
 

@@ -67,6 +67,8 @@ class IterLog:
     div: float
     eps: float
     risks: list | None = None   # SURE of each candidate (Selected), else None
+    divs: list | None = None    # the divergence of each candidate (Selected), else None
+    kept: int = 0               # index of the kept candidate (Selected)
 
 
 def mc_divergence(denoise: Callable[[np.ndarray], np.ndarray], r: np.ndarray,
@@ -100,10 +102,20 @@ class Selected:
     runs each of them on r, with its own divergence, and keeps the one whose
     SURE risk estimate is lowest; a tie keeps the earlier one.  With the
     learned network second, prox-TV is its fallback and the judge of its
-    error."""
+    error.
 
-    def __init__(self, candidates):
+    ``max_div``: a candidate after the first is kept only if its divergence
+    lies in (0, max_div).  tau_x = tau_r D' is a variance, so D' <= 0 (which
+    the floor on tau_x would hide) is no estimate of it; and in Algorithm 1
+    with a large tau_p the output step gives tau_s near 1/tau_p, so
+    tau_r^{t+1} is about tau_r^t D' / delta (delta = M/N): a denoiser with
+    D' >= delta makes tau_r grow from one iteration to the next, and the
+    SURE estimate, which takes tau_r as the noise level of r, can then not
+    be trusted."""
+
+    def __init__(self, candidates, max_div=None):
         self.candidates = list(candidates)
+        self.max_div = max_div
 
 
 def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
@@ -136,17 +148,21 @@ def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
         D = denoise_factory(tau_r)
         b = probe(t, r.size).reshape(r.shape)
         eps = opts.eps_rel * max(float(np.max(np.abs(r))), 1e-6)
-        risks = None
+        risks = divs = None
+        kept = 0
         if isinstance(D, Selected):
             best = None
-            risks = []
-            for Dk in D.candidates:
+            risks, divs = [], []
+            for k, Dk in enumerate(D.candidates):
                 xk = Dk(r)
                 dk = _divergence(Dk, r, xk, b, eps)
                 rk = sure_risk(r, xk, dk, tau_r)
                 risks.append(rk)
-                if best is None or rk < best[2]:
+                divs.append(dk)
+                eligible = k == 0 or D.max_div is None or 0.0 < dk < D.max_div
+                if best is None or (eligible and rk < best[2]):
                     best = (xk, dk, rk)
+                    kept = k
             x_new, div = best[0], best[1]
         else:
             x_new = D(r)
@@ -155,7 +171,7 @@ def gamp(Phi, PhiT, frob2: float, M: int, N: int, gout, denoise_factory,
         if opts.damp_x != 1.0:
             x_new = opts.damp_x * x_new + (1.0 - opts.damp_x) * x
         if log is not None:
-            log.append(IterLog(tau_x, tau_p, tau_s, tau_r, div, eps, risks))
+            log.append(IterLog(tau_x, tau_p, tau_s, tau_r, div, eps, risks, divs, kept))
         x = x_new
         s_prev = s
         if on_iter is not None:
@@ -174,7 +190,7 @@ def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
     (``cnn_bf16=False``: unrounded FP64 activations), run at
     sigma = sqrt(tau_r) (scaled) or sigma = 1 (blind).  With ``select`` both
     run every iteration and the lower SURE risk estimate decides
-    (:class:`Selected`, prox-TV first).  The full
+    (:class:`Selected`, prox-TV first; the network only with 0 < D' < M/N).  The full
     reconstruction has no closed form and the paper prints no synthetic
     result; it is checked only through its pinned parts and the tests'
     qualitative checks (error falls over the iterations, the Onsager term
@@ -221,7 +237,7 @@ def ct_solve(y: np.ndarray, I0: float, geom: Geometry, T: int,
         ws, bs, scaled = cnn
         sigma = float(np.sqrt(tau_r)) if scaled else 1.0
         learned = _cnn.Denoiser(sigma, ws, bs, bf16=cnn_bf16)
-        return Selected([plain(tau_r), learned]) if select else learned
+        return Selected([plain(tau_r), learned], max_div=geom.M / geom.N) if select else learned
 
     def probe(t, n):
         return _philox.probe_normals(n, opts.seed, t, opts.slice_id)

@@ -77,7 +77,7 @@ class Stats(C.Structure):
                 ("div", C.POINTER(C.c_double)), ("iters_done", C.c_int32),
                 ("newton_capped", C.c_int32), ("tau_x_floored", C.c_int32),
                 ("risk_plain", C.POINTER(C.c_double)), ("risk_learned", C.POINTER(C.c_double)),
-                ("learned_kept", C.c_int32)]
+                ("kept_learned", C.POINTER(C.c_int32)), ("learned_kept", C.c_int32)]
 
 
 _STAT_ARRAYS = ("tau_x", "tau_p", "tau_s", "tau_r", "div")
@@ -87,7 +87,9 @@ def _new_stats(iters: int):
     """A Stats record with host arrays for every per-iteration field."""
     arrays = {k: np.zeros(iters) for k in _STAT_ARRAYS + ("risk_plain", "risk_learned")}
     p = {k: a.ctypes.data_as(C.POINTER(C.c_double)) for k, a in arrays.items()}
-    st = Stats(*[p[k] for k in _STAT_ARRAYS], 0, 0, 0, p["risk_plain"], p["risk_learned"], 0)
+    arrays["kept_learned"] = np.zeros(iters, dtype=np.int32)
+    kept = arrays["kept_learned"].ctypes.data_as(C.POINTER(C.c_int32))
+    st = Stats(*[p[k] for k in _STAT_ARRAYS], 0, 0, 0, p["risk_plain"], p["risk_learned"], kept, 0)
     return st, arrays
 
 

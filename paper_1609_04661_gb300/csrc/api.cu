@@ -821,6 +821,7 @@ int fill_stats(const dgamp_ct_plan_s* pl, int iters, dgamp_ct_stats* stats) {
         const bool judged = pl->opt.denoiser == 2;
         if (stats->risk_plain) stats->risk_plain[t] = judged ? lg[t].risk_plain : NAN;
         if (stats->risk_learned) stats->risk_learned[t] = judged ? lg[t].risk_learned : NAN;
+        if (stats->kept_learned) stats->kept_learned[t] = judged ? lg[t].keep_learned : 0;
     }
     stats->learned_kept = (int32_t)hs.learned_kept;
     stats->iters_done = (int32_t)(hs.t - 1u);

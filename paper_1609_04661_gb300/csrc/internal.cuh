@@ -88,6 +88,7 @@ struct FanView {
 struct IterLog {
     double tau_x, tau_p, tau_s, tau_r, div, eps;
     double risk_plain = 0.0, risk_learned = 0.0;   // denoiser 2 only
+    int keep_learned = 0;
 };
 
 // One slice of a batch (dgamp_ct_batch_*): its geometry, the device

@@ -840,14 +840,19 @@ int launch_denoise_final(const dgamp_ct_plan_s* pl, const float* dn, float* x_ou
 // (D_tv(r) - r)^2 (FP32 per thread, FP64 per block and across blocks, in a
 // fixed order); its last block forms each candidate's SURE risk estimate
 //   ||D(r) - r||^2 / N - tau_r + 2 tau_r D'(r)
-// and keeps the CNN where its estimate is strictly lower.  k_select_final
+// and keeps the CNN where its estimate is strictly lower and its divergence
+// lies in (0, M/N).  (tau_x = tau_r D' is a variance, so D' <= 0 estimates
+// nothing; and with a large tau_p the output step gives tau_s near 1/tau_p,
+// so tau_r^{t+1} is about tau_r^t D'/(M/N): a denoiser with D' >= M/N makes
+// tau_r grow, and SURE, which takes tau_r as the noise level of r, cannot be
+// trusted then.)  k_select_final
 // then writes the kept output as x (damped), the staged copies, tau_x, the
 // log record and the next t.
 constexpr int kSelBlocks = 256;
 
 __global__ void __launch_bounds__(256)
 k_select_sums(const float* __restrict__ r, const float* __restrict__ dn, const float* __restrict__ bprobe,
-              long long N, DevScalars* S, double* __restrict__ partial) {
+              long long N, double max_div, DevScalars* S, double* __restrict__ partial) {
     __shared__ double red[32];
     __shared__ bool am_last;
     pdl_wait();
@@ -888,7 +893,7 @@ k_select_sums(const float* __restrict__ r, const float* __restrict__ dn, const f
     const double div_l = tb / Nd, div_p = S->div_plain;
     const double risk_l = ta / Nd - tau_r + 2.0 * tau_r * div_l;
     const double risk_p = tc / Nd - tau_r + 2.0 * tau_r * div_p;
-    const unsigned keep = risk_l < risk_p ? 1u : 0u;
+    const unsigned keep = (risk_l < risk_p && div_l > 0.0 && div_l < max_div) ? 1u : 0u;
     S->div_learned = div_l;
     S->risk_learned = risk_l;
     S->risk_plain = risk_p;
@@ -933,6 +938,7 @@ k_select_final(const float* __restrict__ dn, int n, DevScalars* S, TvFinal F) {
         L.div = div; L.eps = S->eps;
         L.risk_plain = S->risk_plain;
         L.risk_learned = S->risk_learned;
+        L.keep_learned = (int)S->keep_learned;
         F.log[tt - 1] = L;
     }
     S->t = tt + 1u;
@@ -942,8 +948,9 @@ int launch_select(const dgamp_ct_plan_s* pl, int part, cudaStream_t st) {
     const int n = pl->n;
     const long long N = pl->N;
     if (part == 0) {
+        const double max_div = (double)pl->M / (double)pl->N;
         DGCT_CUDA(launch_pdl(k_select_sums, dim3(kSelBlocks), dim3(256), 0, st, (const float*)pl->ws.r,
-                             (const float*)pl->dn, (const float*)pl->ws.b, N, pl->ws.S, pl->ws.partial));
+                             (const float*)pl->dn, (const float*)pl->ws.b, N, max_div, pl->ws.S, pl->ws.partial));
         return DGAMP_CT_OK;
     }
     TvFinal F = make_tv_final(pl, pl->ws.x, 1, 0, nullptr);

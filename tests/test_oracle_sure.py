@@ -95,3 +95,18 @@ def test_selection_tie_keeps_the_first_denoiser():
     x_sel, log = _awgn_run(lambda tau_r: gamp.Selected([first, second]))
     assert np.array_equal(x_sel, x_ref)
     assert all(lg.risks[0] == lg.risks[1] for lg in log)
+
+
+def test_selection_skips_a_candidate_whose_divergence_is_too_large():
+    # the MMSE denoiser has the lower risk, but its divergence 1/(1 + tau_r)
+    # is not below max_div = 1e-12: the first candidate (a poor one) is kept
+    mmse = gamp.gaussian_prior_denoiser
+    poor = lambda tau_r: (lambda r: 2.0 * r)
+    x_poor, _ = _awgn_run(poor, T=3)
+    x_free, log_free = _awgn_run(lambda tau_r: gamp.Selected([poor(tau_r), mmse(tau_r)]), T=3)
+    x_cap, log_cap = _awgn_run(lambda tau_r: gamp.Selected([poor(tau_r), mmse(tau_r)], max_div=1e-12), T=3)
+    assert np.array_equal(x_cap, x_poor)
+    # without the bound the MMSE candidate wins, so the bound is what decides
+    assert all(lg.risks[1] < lg.risks[0] for lg in log_free)
+    assert all(lg.div > 1e-12 for lg in log_free)
+    assert not np.array_equal(x_free, x_poor)
