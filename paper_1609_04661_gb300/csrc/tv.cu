@@ -417,6 +417,234 @@ k_tv_steps(const float* __restrict__ rbase, const float2* __restrict__ pin, floa
                                      blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z, sh);
 }
 
+// ---------------------------------------- both images in one thread ----
+// The two images of the MC pair (r and r + eps b) take the same steps on
+// the same pixels, so one thread can hold both: every value is a pair
+// (image 0, image 1) and the dual step's additions and multiplications run
+// as packed FP32 pairs (one instruction for both images, sm_100 and later).
+// Each lane of a pair is rounded exactly as the one-image kernel rounds it
+// (a - b as fma(b, -1, a) is the same correctly rounded difference), so the
+// duals and x are bit-identical to the one-image form; only the FP64
+// divergence sum, b (x_1 - x_0) per pixel here, adds in another order.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 shfl_up2(float2 v, int d) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v, int d) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+
+template <int WY>
+struct TvShared2 {
+    float2 e_py[WY][kTvU][32];
+    float2 e_q[WY][kTvU][32];
+    double red[32];
+    bool am_last;
+};
+
+template <int WY, int KB, bool BORDER, int V>
+__device__ __forceinline__ void tv_region_steps2(float2 (&px)[V][kTvU], float2 (&py)[V][kTvU],
+                                                 const float2 (&rl)[V][kTvU], unsigned inside, unsigned lastc,
+                                                 unsigned lastr, float2 (*e_py)[kTvU][32], float2 (*e_q)[kTvU][32]) {
+    constexpr int U = kTvU;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float2 zero = make_float2(0.f, 0.f), tau = make_float2(kTau, kTau), one = make_float2(1.f, 1.f);
+    float2 q[V][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) e_py[w][u][lane] = py[V - 1][u];
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < KB; ++k) {
+        // q = div p - r / lambda  (zero outside the image)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float2 pxl;
+                if (u > 0) {
+                    pxl = px[v][u - 1];
+                } else {
+                    const float2 t = shfl_up2(px[v][U - 1], 1);
+                    pxl = lane > 0 ? t : zero;
+                }
+                const float2 pyu = v > 0 ? py[v - 1][u] : (w > 0 ? e_py[w - 1][u][lane] : zero);
+                float2 qq = sub2(sub2(add2(sub2(px[v][u], pxl), py[v][u]), pyu), rl[v][u]);
+                if (BORDER && !((inside >> (v * U + u)) & 1u)) qq = zero;
+                q[v][u] = qq;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) e_q[w][u][lane] = q[0][u];
+        __syncthreads();
+        // p <- (p + tau grad q) / (1 + tau |grad q|)  (grad q = 0 across the last row/column)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float2 qr;
+                if (u + 1 < U) {
+                    qr = q[v][u + 1];
+                } else {
+                    const float2 t = shfl_down2(q[v][0], 1);
+                    qr = lane < 31 ? t : zero;
+                }
+                const float2 qd = v + 1 < V ? q[v + 1][u] : (w + 1 < WY ? e_q[w + 1][u][lane] : zero);
+                float2 gx = sub2(qr, q[v][u]);
+                float2 gy = sub2(qd, q[v][u]);
+                bool upd = true;
+                if (BORDER) {
+                    const int bit = v * U + u;
+                    upd = (inside >> bit) & 1u;
+                    if ((lastc >> bit) & 1u) gx = zero;
+                    if ((lastr >> bit) & 1u) gy = zero;
+                }
+                if (upd) {
+                    const float2 g2 = fma2(gx, gx, mul2(gy, gy));
+                    const float2 nrm = make_float2(sqrt_approx(g2.x), sqrt_approx(g2.y));
+                    const float2 den = fma2(tau, nrm, one);
+                    const float2 inv = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+                    px[v][u] = mul2(fma2(tau, gx, px[v][u]), inv);
+                    py[v][u] = mul2(fma2(tau, gy, py[v][u]), inv);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) e_py[w][u][lane] = py[V - 1][u];
+        __syncthreads();
+    }
+}
+
+// Region (bx, by) of both images (a launch of gx x gy blocks); as
+// tv_steps_block with nimg = 2, the divergence summed as b (x_1 - x_0).
+template <int WY, int KB, bool FINAL, int V>
+__device__ __forceinline__ void tv_steps_block2(const float* __restrict__ rbase, const float2* __restrict__ pin,
+                                                float2* __restrict__ pout, int n, int first, float c_tv,
+                                                int from_scalars, float lambda_arg, DevScalars* S,
+                                                const float* __restrict__ bprobe, const TvFinal& F, int bx, int by,
+                                                int gx, int gy, TvShared2<WY>& sh) {
+    constexpr int U = kTvU, RW = kTvRW, RH = V * WY;
+    constexpr int E = FINAL ? KB + 1 : KB;
+    constexpr int TW = RW - KB - E, TH = RH - KB - E;
+    auto& e_py = sh.e_py;
+    auto& e_q = sh.e_q;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t N = (size_t)n * n;
+    const int gi0 = by * TH - E, gj0 = bx * TW - E;
+    pdl_wait();      // r, the duals and the scalars are earlier kernels' output
+    const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
+    const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
+    float2 px[V][U], py[V][U], rl[V][U];
+    unsigned inside = 0u, lastc = 0u, lastr = 0u;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int gi = gi0 + w * V + v;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int gj = gj0 + U * lane + u;
+            const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
+            float r0 = 0.f, r1 = 0.f;
+            float2 p0 = make_float2(0.f, 0.f), p1 = make_float2(0.f, 0.f);
+            if (in) {
+                const size_t o = (size_t)gi * n + gj;
+                r0 = rbase[o];
+                r1 = rbase[N + o];
+                if (!first) {
+                    p0 = pin[o];
+                    p1 = pin[N + o];
+                }
+            }
+            rl[v][u] = make_float2(r0 * inv_lam, r1 * inv_lam);
+            px[v][u] = make_float2(p0.x, p1.x);
+            py[v][u] = make_float2(p0.y, p1.y);
+            const unsigned bit = 1u << (v * U + u);
+            if (in) inside |= bit;
+            if (gj == n - 1) lastc |= bit;
+            if (gi == n - 1) lastr |= bit;
+        }
+    }
+    const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + RH < n && gj0 + RW < n;
+    if (interior)
+        tv_region_steps2<WY, KB, false, V>(px, py, rl, inside, lastc, lastr, e_py, e_q);
+    else
+        tv_region_steps2<WY, KB, true, V>(px, py, rl, inside, lastc, lastr, e_py, e_q);
+    if (!FINAL) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int rr = w * V + v;
+            if (rr < KB || rr >= RH - KB) continue;
+            const int gi = gi0 + rr;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int cc = U * lane + u;
+                const int gj = gj0 + cc;
+                if (cc < KB || cc >= RW - KB || gi >= n || gj >= n) continue;
+                const size_t o = (size_t)gi * n + gj;
+                pout[o] = make_float2(px[v][u].x, py[v][u].x);
+                pout[N + o] = make_float2(px[v][u].y, py[v][u].y);
+            }
+        }
+        return;
+    }
+    // ---- final: x = r - lambda div p for both images (e_py holds the last rows' py) ----
+    auto& red = sh.red;
+    auto& am_last = sh.am_last;
+    double acc = 0.0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int rr = w * V + v;
+        const int gi = gi0 + rr;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float2 pxl;
+            if (u > 0) {
+                pxl = px[v][u - 1];
+            } else {
+                const float2 t = shfl_up2(px[v][U - 1], 1);
+                pxl = lane > 0 ? t : make_float2(0.f, 0.f);
+            }
+            const float2 pyu = v > 0 ? py[v - 1][u] : (w > 0 ? e_py[w - 1][u][lane] : make_float2(0.f, 0.f));
+            const int cc = U * lane + u;
+            const int gj = gj0 + cc;
+            if (rr < E || rr >= RH - KB || cc < E || cc >= RW - KB || gi >= n || gj >= n) continue;
+            const size_t o = (size_t)gi * n + gj;
+            const float dv0 = px[v][u].x - pxl.x + py[v][u].x - pyu.x;
+            const float dv1 = px[v][u].y - pxl.y + py[v][u].y - pyu.y;
+            const float x0 = rbase[o] - lam * dv0;
+            const float x1 = rbase[N + o] - lam * dv1;
+            acc += (double)bprobe[o] * ((double)x1 - (double)x0);
+            float xo = x0;
+            if (F.solve_mode && F.damp_x != 1.f) xo = F.damp_x * xo + (1.f - F.damp_x) * F.x_out[o];
+            F.x_out[o] = xo;
+            if (F.XR) stage_store(F.XR, F.xbf, (size_t)gi * F.ldp + kPad + gj, xo);
+            if (F.XC) stage_store(F.XC, F.xbf, (size_t)gj * F.ldp + kPad + gi, xo);
+        }
+    }
+    const int nblk = gx * gy;
+    const int bid = by * gx + bx;
+    if (F.solve_mode) {
+        acc = block_sum(acc, red);
+        if (threadIdx.x == 0) {
+            F.partial_div[bid] = acc;
+            if (bid == 0) S->div_pending = (unsigned)nblk;
+        }
+        return;
+    }
+    tv_divergence_finish(acc, nblk, bid, N, S, F, red, &am_last);
+}
+
+template <int WY, int KB, bool FINAL, int V>
+__global__ void __launch_bounds__(32 * WY)
+k_tv_steps2(const float* __restrict__ rbase, const float2* __restrict__ pin, float2* __restrict__ pout, int n,
+            int first, float c_tv, int from_scalars, float lambda_arg, DevScalars* S,
+            const float* __restrict__ bprobe, TvFinal F) {
+    __shared__ TvShared2<WY> sh;
+    tv_steps_block2<WY, KB, FINAL, V>(rbase, pin, pout, n, first, c_tv, from_scalars, lambda_arg, S, bprobe, F,
+                                      blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, sh);
+}
+
 // TV region dims of a launch: tile width and height of the valid part
 template <int WY, int KB, bool FINAL>
 __host__ __device__ constexpr int tv_tile_w() { return kTvRW - KB - (FINAL ? KB + 1 : KB); }
@@ -455,26 +683,26 @@ template <int WY, int KB, bool FINAL>
 __global__ void __launch_bounds__(32 * WY)
 k_tv_steps_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ map, int phase, int launch,
                  int xbf) {
-    __shared__ TvShared<WY> sh;
+    __shared__ TvShared2<WY> sh;
     const BatchSlice& B = sl[map[blockIdx.x]];
     const int l = (int)blockIdx.x - B.off[phase];
     const int n = B.n;
     const int gx = (n + tv_tile_w<WY, KB, FINAL>() - 1) / tv_tile_w<WY, KB, FINAL>();
     const int gy = (n + tv_tile_h<WY, KB, FINAL>() - 1) / tv_tile_h<WY, KB, FINAL>();
-    const int bx = l % gx, by = (l / gx) % gy, bz = l / (gx * gy);
+    const int bx = l % gx, by = l / gx;
     const size_t N = (size_t)B.N;
     const float2* pin = B.p + ((launch + 1) & 1) * 2 * N;
     float2* pout = B.p + (launch & 1) * 2 * N;
     const TvFinal F = tv_final_of(B, xbf);
-    tv_steps_block<WY, KB, FINAL>(B.r, pin, pout, n, launch == 0, B.c_tv, 1, 0.f, B.S, B.b, F, bx, by, bz, gx, gy,
-                                  2, sh);
+    tv_steps_block2<WY, KB, FINAL, kTvV>(B.r, pin, pout, n, launch == 0, B.c_tv, 1, 0.f, B.S, B.b, F, bx, by, gx,
+                                         gy, sh);
 }
 
 int batch_grid_tv(int n, int final_launch) {
     constexpr int WY = kTvRowsBatch / kTvV;
     const int tw = final_launch ? tv_tile_w<WY, kBatchTvKb, true>() : tv_tile_w<WY, kBatchTvKb, false>();
     const int th = final_launch ? tv_tile_h<WY, kBatchTvKb, true>() : tv_tile_h<WY, kBatchTvKb, false>();
-    return ((n + tw - 1) / tw) * ((n + th - 1) / th) * 2;
+    return ((n + tw - 1) / tw) * ((n + th - 1) / th);   // both images of a region in one block
 }
 
 int batch_grid_probe(long long N) { return (int)(((N + 3) / 4 + 255) / 256); }
@@ -580,11 +808,22 @@ struct TvLaunch {
     const float* b;
 };
 
+// The MC pair's launches take the two-image kernel in 32- and 64-row regions
+// of 4-row threads (about 100 registers a thread); the 128-row and 8-row
+// shapes would spill there and keep the one-image kernel.
+template <int WY, int V>
+constexpr bool tv_paired_shape() { return V == 4 && (WY == 8 || WY == 16); }
+
 template <int WY, int KB, bool FIN, int V>
 static cudaError_t launch_steps_kb(const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
     constexpr int E = FIN ? KB + 1 : KB;
     constexpr int TW = kTvRW - KB - E, TH = V * WY - KB - E;
-    dim3 grd((L.n + TW - 1) / TW, (L.n + TH - 1) / TH, L.nimg);
+    if constexpr (tv_paired_shape<WY, V>()) if (L.nimg == 2) {   // the MC pair: both images in one thread
+        const dim3 grd((L.n + TW - 1) / TW, (L.n + TH - 1) / TH);
+        return launch_pdl(k_tv_steps2<WY, KB, FIN, V>, grd, dim3(32 * WY), 0, st, L.r, L.pin, L.pout, L.n,
+                          L.first, L.c_tv, L.fs, L.lam, L.S, L.b, F);
+    }
+    const dim3 grd((L.n + TW - 1) / TW, (L.n + TH - 1) / TH, L.nimg);
     return launch_pdl(k_tv_steps<WY, KB, FIN, V>, grd, dim3(32 * WY), 0, st, L.r, L.pin, L.pout, L.n, L.first,
                       L.c_tv, L.fs, L.lam, L.S, L.b, F);
 }
