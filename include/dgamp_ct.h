@@ -234,9 +234,12 @@ typedef struct {
                              exact transpose of the projector and deterministic */
     int32_t pj_seg;       /* A: warps that split the step range of one group of 32 rays,
                              8, 16 or 32 (the partial sums are added in a fixed order) */
-    int32_t tv_vrows;     /* rows of the TV region each thread holds: 4, or 8 (then the
-                             region is 64 rows high whatever tv_rows says: half the
-                             threads of the 4-row form, twice the pixels each) */
+    int32_t tv_vrows;     /* rows of the TV region each thread holds: 4; 8 or 2 (then the
+                             region is 64 rows high whatever tv_rows says: half or twice
+                             the threads of the 4-row form, twice or half the pixels
+                             each).  Inside a solve, both images of the MC pair share a
+                             thread for 4-row threads in 32- or 64-row regions and for
+                             2-row threads */
 } dgamp_ct_tuning;
 
 /* get: writes the plan's choices.  set: fields < 0 keep the current choice;

@@ -285,7 +285,7 @@ class Plan:
         "tv_kb": steps per TV launch, "tv_rows": rows of a TV block's region, "sino_fused": 1 if the
         solve runs H A x, the output step and H s as one kernel, "bp_mode": 0 pixel-driven | 1
         ray-driven A^T, "pj_seg": warps splitting the steps of 32 rays in A, "tv_vrows": rows of a TV
-        region per thread}."""
+        region per thread (2, 4 or 8)}."""
         t = Tuning()
         _check(self._lib.dgamp_ct_get_tuning(self._h, C.byref(t)), "get_tuning")
         return {name: getattr(t, name) for name, _ in Tuning._fields_}

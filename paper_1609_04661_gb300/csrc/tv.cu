@@ -809,10 +809,11 @@ struct TvLaunch {
 };
 
 // The MC pair's launches take the two-image kernel in 32- and 64-row regions
-// of 4-row threads (about 100 registers a thread); the 128-row and 8-row
-// shapes would spill there and keep the one-image kernel.
+// of 4-row threads (about 100 registers a thread) and in 64-row regions of
+// 2-row threads (1024 threads); the 128-row and 8-row shapes would spill
+// there and keep the one-image kernel.
 template <int WY, int V>
-constexpr bool tv_paired_shape() { return V == 4 && (WY == 8 || WY == 16); }
+constexpr bool tv_paired_shape() { return (V == 4 && (WY == 8 || WY == 16)) || (V == 2 && WY == 32); }
 
 template <int WY, int KB, bool FIN, int V>
 static cudaError_t launch_steps_kb(const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
@@ -847,6 +848,7 @@ static int launch_steps_wy(int steps, const TvLaunch& L, cudaStream_t st, const 
 template <bool FIN>
 static int launch_steps(int rows, int vrows, int steps, const TvLaunch& L, cudaStream_t st, const TvFinal& F) {
     if (vrows == 8) return launch_steps_wy<8, FIN, 8>(steps, L, st, F);
+    if (vrows == 2) return launch_steps_wy<32, FIN, 2>(steps, L, st, F);
     if (rows == 128) return launch_steps_wy<32, FIN>(steps, L, st, F);
     if (rows == 32) return launch_steps_wy<8, FIN>(steps, L, st, F);
     return launch_steps_wy<16, FIN>(steps, L, st, F);
@@ -939,8 +941,9 @@ int tv_autotune(dgamp_ct_plan_s* pl) {
     float best = 1e30f;
     int best_kb = pl->tv_kb, best_rows = pl->tv_rows, best_v = pl->tv_vrows;
     // (region rows, rows per thread): the 4-row threads at three heights, and
-    // 64-row regions of 8-row threads (half the threads, each with twice the pixels)
-    const int shapes[][2] = {{kTvRowChoices[0], 4}, {kTvRowChoices[1], 4}, {kTvRowChoices[2], 4}, {64, 8}};
+    // 64-row regions of 8-row threads (half the threads, each with twice the
+    // pixels) and of 2-row threads (twice the threads, half the pixels each)
+    const int shapes[][2] = {{kTvRowChoices[0], 4}, {kTvRowChoices[1], 4}, {kTvRowChoices[2], 4}, {64, 8}, {64, 2}};
     for (const auto& sh : shapes) {
         const int rows = sh[0];
         for (int kb : kTvKbChoices) {

@@ -174,7 +174,7 @@ def test_truncated_output_step_matches_oracle(dg):
     assert ts == pytest.approx(np.mean(tsi_ref), rel=1e-5)
 
 
-@pytest.mark.parametrize("rows,vrows", [(32, 4), (64, 4), (128, 4), (64, 8)])   # region height, rows per thread
+@pytest.mark.parametrize("rows,vrows", [(32, 4), (64, 4), (128, 4), (64, 8), (64, 2)])   # region height, rows per thread
 @pytest.mark.parametrize("kb", [1, 3, 7, 10])           # steps per blocked launch (remainders too)
 @pytest.mark.parametrize("n,lam", [(64, 0.3), (77, 0.05), (33, 0.0), (130, 0.2), (300, 0.1)])
 def test_tv_matches_oracle(dg, n, lam, kb, rows, vrows):
@@ -183,6 +183,35 @@ def test_tv_matches_oracle(dg, n, lam, kb, rows, vrows):
         pl.set_tuning(tv_kb=kb, tv_rows=rows, tv_vrows=vrows)
         x = host(pl.denoise_tv(cu(r), lam))
     assert rel(x, tv.tv_prox(r, lam, 20)) < 1e-5
+
+
+@pytest.mark.parametrize("kb", [3, 10])
+@pytest.mark.parametrize("n", [64, 77, 300])
+def test_tv_pair_forms_agree(dg, n, kb):
+    """The MC pair (r and r + eps b) with both images in one thread (packed
+    FP32 pairs: 32- and 64-row regions of 4-row threads, 64-row regions of
+    2-row threads) or in separate blocks (128-row regions, 8-row threads):
+    the same x bit for bit, the same divergence up to the order of its FP64
+    sum, and the oracle's to its tolerance."""
+    r = np.cumsum(np.random.default_rng(10).standard_normal((n, n)), axis=0) * 0.2
+    tau_r, t = 0.01, 5
+    shapes = [(32, 4), (64, 4), (64, 2), (128, 4), (64, 8)]
+    out = []
+    with dg.Plan(n, 10, 2 * n, k_tv=20, c_tv=3.0, seed=77) as pl:
+        for rows, vrows in shapes:
+            pl.set_tuning(tv_kb=kb, tv_rows=rows, tv_vrows=vrows)
+            x, dv = pl.denoise_div(cu(r), tau_r, t)
+            out.append((host(x), float(host(dv)[0])))
+    for (x, dv), shape in zip(out[1:], shapes[1:]):
+        assert np.array_equal(x, out[0][0]), shape
+        assert dv == pytest.approx(out[0][1], rel=1e-9), shape
+    lam = 3.0 * np.sqrt(tau_r)
+    D = lambda v: tv.tv_prox(v, lam, 20)
+    x_ref = D(r)
+    b = philox.probe_normals(n * n, 77, t, 0).reshape(n, n)
+    eps = 1e-3 * max(np.max(np.abs(r)), 1e-6)
+    assert rel(out[0][0], x_ref) < 1e-5
+    assert out[0][1] == pytest.approx(gamp.mc_divergence(D, r, x_ref, b, eps), rel=2e-3)
 
 
 def test_probe_words_bitexact_and_normals_close(dg):
