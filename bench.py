@@ -809,6 +809,7 @@ def run_gpu(args):
     # ALU peak: the library's FP32 FMA microbenchmark, measured here (TFLOP/s,
     # an FMA = 2 FLOP); the unit-count figure at the sampled clock beside it
     fp32_peak, sms = dg.binding.measure_fp32_peak(5)
+    fp32x2_peak, _ = dg.binding.measure_fp32x2_peak(5)   # packed pairs: issue slots, not FMA rate
     clk_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     alu_derived = sms * 128 * 2 * clk_mhz * 1e6 / 1e12
     peak_note = (f"FP32 FMA microbenchmark (dgamp_ct_measure_fp32_peak) in this run on {sms} SMs; "
@@ -879,6 +880,7 @@ def run_gpu(args):
                 "psnr_db": psnr,
                 "a_plus_at_gbs": a_at_bytes / (a_at_ms * 1e-3) / 1e9,
                 "roofline_A": roof_a, "roofline_AT": roof_at, "fp32_fma_peak_tflops": fp32_peak,
+                "fp32x2_fma_peak_tflops": fp32x2_peak,
                 "iteration_ms": iter_ms, "tuning": tun, "kernel_ms": prof, "kernel_share": shares,
                 "tv_share": tv_ms / iter_ms, "learned_vs_plain": learned, "batched": batched, "batched_learned": batched_learned, "large_bf16": c5,
                 "ablation": ablation, "variants": variants, "training": training}

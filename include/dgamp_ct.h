@@ -429,6 +429,11 @@ int dgamp_ct_profile_iteration(dgamp_ct_plan_t plan, int32_t reps, double* h_ms,
    synchronous. */
 int dgamp_ct_measure_fp32_peak(int32_t reps, double* h_tflops, int32_t* h_sms, void* stream);
 
+/* The same with the chains as packed FP32 pairs (two FMAs per instruction,
+   sm_100 and later), counting 4 FLOP per instruction: whether the packed
+   form raises the FMA rate or only saves issue slots.  As above otherwise. */
+int dgamp_ct_measure_fp32x2_peak(int32_t reps, double* h_tflops, int32_t* h_sms, void* stream);
+
 /* ---------------------------------------------------------------------------
    Learned denoiser (Step 4 of Algorithm 1 with a trained network; the paper's
    Section 4.3 admits any denoiser and Section 1 points to residual CNNs).

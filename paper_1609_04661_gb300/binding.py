@@ -30,7 +30,7 @@ EXPORTS = (
     "dgamp_ct_cnn_create", "dgamp_ct_cnn_destroy", "dgamp_ct_cnn_num_params", "dgamp_ct_cnn_set_params",
     "dgamp_ct_cnn_get_params", "dgamp_ct_cnn_denoise", "dgamp_ct_cnn_denoise_jvp", "dgamp_ct_cnn_gradients", "dgamp_ct_cnn_train_step",
     "dgamp_ct_cnn_test_timeout", "dgamp_ct_plan_set_cnn", "dgamp_ct_solve_trace", "dgamp_ct_solve_batched", "dgamp_ct_schedule_lpt",
-    "dgamp_ct_plan_fan", "dgamp_ct_fan_ray_constants", "dgamp_ct_measure_fp32_peak",
+    "dgamp_ct_plan_fan", "dgamp_ct_fan_ray_constants", "dgamp_ct_measure_fp32_peak", "dgamp_ct_measure_fp32x2_peak",
     "dgamp_ct_batch_create", "dgamp_ct_batch_destroy", "dgamp_ct_batch_solve", "dgamp_ct_batch_launches",
 )
 
@@ -151,6 +151,7 @@ def load(path: str = LIB_PATH):
         "dgamp_ct_plan_set_cnn": (C.c_int, [vp, vp]),
         "dgamp_ct_cnn_test_timeout": (C.c_int, [vp, i32]),
         "dgamp_ct_measure_fp32_peak": (C.c_int, [i32, C.POINTER(dbl), C.POINTER(i32), vp]),
+        "dgamp_ct_measure_fp32x2_peak": (C.c_int, [i32, C.POINTER(dbl), C.POINTER(i32), vp]),
         "dgamp_ct_batch_create": (C.c_int, [i32, vp, i32, vp]),
         "dgamp_ct_batch_destroy": (None, [vp]),
         "dgamp_ct_batch_solve": (C.c_int, [vp, vp, vp, i32, vp, vp, vp]),
@@ -203,6 +204,15 @@ def measure_fp32_peak(reps: int = 5):
     sms = C.c_int32()
     _check(load().dgamp_ct_measure_fp32_peak(int(reps), C.byref(tf), C.byref(sms), _stream()),
            "dgamp_ct_measure_fp32_peak")
+    return tf.value, sms.value
+
+
+def measure_fp32x2_peak(reps: int = 5):
+    """The same with packed FP32 pairs (dgamp_ct_measure_fp32x2_peak): (TFLOP/s, SM count)."""
+    tf = C.c_double()
+    sms = C.c_int32()
+    _check(load().dgamp_ct_measure_fp32x2_peak(int(reps), C.byref(tf), C.byref(sms), _stream()),
+           "dgamp_ct_measure_fp32x2_peak")
     return tf.value, sms.value
 
 
