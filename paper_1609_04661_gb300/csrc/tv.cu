@@ -953,7 +953,8 @@ int tv_autotune(dgamp_ct_plan_s* pl) {
             int rc = DGAMP_CT_OK;
             for (int rep = 0; rep < 4 && rc == DGAMP_CT_OK; ++rep) {      // first rep warms up
                 if (rep == 1) cudaEventRecord(e0, 0);
-                rc = launch_tv(pl, 2, 0, 1.0, pl->ws.x, 0, 1, nullptr, 0);
+                // as inside a solve (staged copies, divergence partials), lambda = 1
+                rc = launch_tv(pl, 2, 0, 1.0, pl->ws.x, 1, 1, nullptr, 0);
             }
             cudaEventRecord(e1, 0);
             cudaError_t e = cudaEventSynchronize(e1);
