@@ -54,6 +54,7 @@
 // ||Phi~||_F^2 = sum over rays of ||V^-1 a_i||^2: plan-time, one ray at a
 // time (its taps scattered into an image, V^-1 by the image filter of
 // fft.cu, the sum of squares in FP64).
+#include <algorithm>
 #include <cmath>
 
 #include "internal.cuh"
@@ -254,13 +255,17 @@ k_fan_backproject_tile(const float* __restrict__ sino, const FanRay* __restrict_
 }
 
 // ------------------------------------------------------- ||Phi~||_F^2 ----
-// The taps of ray `ray` scattered into a zeroed [n][n] image (one block; a
-// ray puts at most one tap on a pixel, so the writes do not collide).
+// Ray ray0 + b's taps scattered into zeroed image b of a batch ([nimg][n][n],
+// one block per image; a ray puts at most one tap on a pixel, so the writes
+// do not collide).  Rays past the last (nrays) leave their image zero.
 __global__ void __launch_bounds__(1024)
-k_fan_ray_image(const FanRay* __restrict__ rays, int ray, int n, float* __restrict__ img) {
+k_fan_ray_image(const FanRay* __restrict__ rays, long long ray0, long long nrays, int n, float* __restrict__ img) {
     const size_t N = (size_t)n * n;
+    img += (size_t)blockIdx.x * N;
     for (size_t i = threadIdx.x; i < N; i += blockDim.x) img[i] = 0.f;
     __syncthreads();
+    const long long ray = ray0 + blockIdx.x;
+    if (ray >= nrays) return;
     const FanRay R = rays[ray];
     for (int s = threadIdx.x; s < n; s += blockDim.x) {
         int i0;
@@ -277,10 +282,14 @@ k_fan_ray_image(const FanRay* __restrict__ rays, int ray, int n, float* __restri
     }
 }
 
-// out[slot] = sum of squares of img (FP64, one block, fixed order).
+// out[slot0 + b] = sum of squares of image b (FP64, one block per image,
+// fixed order), for the images of rays before nrays.
 __global__ void __launch_bounds__(1024)
-k_sum_squares(const float* __restrict__ img, long long N, double* __restrict__ out, int slot) {
+k_sum_squares(const float* __restrict__ img, long long N, double* __restrict__ out, long long slot0,
+              long long nrays) {
     __shared__ double red[32];
+    if (slot0 + blockIdx.x >= nrays) return;
+    img += (size_t)blockIdx.x * N;
     double acc = 0.0;
     for (long long i = threadIdx.x; i < N; i += blockDim.x) {
         const double v = img[i];
@@ -294,7 +303,7 @@ k_sum_squares(const float* __restrict__ img, long long N, double* __restrict__ o
         double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) out[slot] = t;
+        if (threadIdx.x == 0) out[slot0 + blockIdx.x] = t;
     }
 }
 
@@ -398,22 +407,35 @@ int fan_setup(dgamp_ct_plan_s* pl, const std::vector<double>& ang, double src_di
     pl->fan = 1;
     pl->fan_stride = fan_tile_stride(rays, pl->nv, pl->nd, pl->n);
     pl->bp_mode = pl->fan_stride > 0 ? 1 : 0;
-    // ||Phi~||_F^2: ray image in ws.r[0..N), V^-1 of it in ws.r[N..2N), one FP64
-    // sum of squares per ray into scratch, added on the host in ray order
+    // ||Phi~||_F^2: batches of B rays -- their tap images, V^-1 of them (the
+    // image filter, batched), one FP64 sum of squares per ray into `sums` --
+    // added on the host in ray order.  Each ray's arithmetic is that of the
+    // single-image filter.  B keeps the scratch near 512 MB.
     const int64_t M = pl->M, N = pl->N;
+    const size_t per_img = (size_t)N * 2 * sizeof(float) + (size_t)pl->n * pl->m2 * sizeof(float2);
+    const int B = (int)std::max<size_t>(1, std::min<size_t>(64, ((size_t)512 << 20) / per_img));
     double* sums = nullptr;
-    if (cudaMalloc((void**)&sums, (size_t)M * sizeof(double)) != cudaSuccess) {
+    float* imgs = nullptr;
+    float2* C = nullptr;
+    if (cudaMalloc((void**)&sums, (size_t)M * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&imgs, (size_t)B * N * 2 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&C, (size_t)B * pl->n * pl->m2 * sizeof(float2)) != cudaSuccess) {
         cudaGetLastError();
+        cudaFree(sums);
+        cudaFree(imgs);
+        cudaFree(C);
         return DGAMP_CT_ERR_OOM;
     }
     int rc = DGAMP_CT_OK;
-    for (int64_t i = 0; i < M && rc == DGAMP_CT_OK; ++i) {
-        k_fan_ray_image<<<1, 1024>>>(pl->ws.fan_rays, (int)i, pl->n, pl->ws.r);
-        rc = launch_precond_image(pl, pl->ws.r, pl->ws.r + N, 1, 0);
-        if (rc == DGAMP_CT_OK) k_sum_squares<<<1, 1024>>>(pl->ws.r + N, N, sums, (int)i);
+    for (int64_t i = 0; i < M && rc == DGAMP_CT_OK; i += B) {
+        k_fan_ray_image<<<B, 1024>>>(pl->ws.fan_rays, i, M, pl->n, imgs);
+        rc = launch_precond_images(pl, imgs, imgs + (size_t)B * N, C, B, 1, 0);
+        if (rc == DGAMP_CT_OK) k_sum_squares<<<B, 1024>>>(imgs + (size_t)B * N, N, sums, i, M);
         const cudaError_t e = cudaGetLastError();
         if (rc == DGAMP_CT_OK && e != cudaSuccess) rc = cuda_fail(e);
     }
+    cudaFree(imgs);
+    cudaFree(C);
     std::vector<double> h((size_t)M);
     if (rc == DGAMP_CT_OK) {
         const cudaError_t e = cudaMemcpy(h.data(), sums, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost);

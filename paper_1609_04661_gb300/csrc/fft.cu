@@ -195,6 +195,8 @@ int toeplitz_set_smem_limit(int nd) {
 }
 
 // ------------------------------------------------------- V^-1 / V image --
+// Image blockIdx.y of a batch (img and out [nimg][n][n], C [nimg][n][m]); a
+// single image is the batch of one.
 // pass 1: rows iy < n of the m x m padded image -> C[iy][:]
 __global__ void __launch_bounds__(512)
 k_img_rows_fwd(const float* __restrict__ img, int n, int m, const float2* __restrict__ tw,
@@ -203,6 +205,8 @@ k_img_rows_fwd(const float* __restrict__ img, int n, int m, const float2* __rest
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
     const int iy = blockIdx.x;
+    img += (size_t)blockIdx.y * n * n;
+    C += (size_t)blockIdx.y * n * m;
     for (int i = threadIdx.x; i < m; i += blockDim.x)
         a[fpad(i)] = make_float2(i < n ? img[(size_t)iy * n + i] : 0.f, 0.f);
     __syncthreads();
@@ -219,6 +223,7 @@ k_img_cols(float2* __restrict__ C, int n, int m, const float2* __restrict__ tw, 
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
     const int kx = blockIdx.x;
+    C += (size_t)blockIdx.y * n * m;
     for (int i = threadIdx.x; i < m; i += blockDim.x)
         a[fpad(i)] = i < n ? C[(size_t)i * m + kx] : make_float2(0.f, 0.f);
     __syncthreads();
@@ -246,6 +251,8 @@ k_img_rows_inv(const float2* __restrict__ C, int n, int m, const float2* __restr
     float2* a = smem;
     float2* b = smem + fft_buf_len(m);
     const int iy = blockIdx.x;
+    C += (size_t)blockIdx.y * n * m;
+    out += (size_t)blockIdx.y * n * n;
     for (int i = threadIdx.x; i < m; i += blockDim.x) a[fpad(i)] = C[(size_t)iy * m + i];
     __syncthreads();
     float2* r = fft_stockham(a, b, m, tw, 1.f);
@@ -311,6 +318,25 @@ int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out,
     k_img_cols<<<m, thr, sm, st>>>(pl->ws.fft2d, n, m, pl->ws.tw2, f0, inverse ? 0 : 1);
     DGCT_LAUNCH_CHECK();
     k_img_rows_inv<<<n, thr, sm, st>>>(pl->ws.fft2d, n, m, pl->ws.tw2, out);
+    DGCT_LAUNCH_CHECK();
+    return DGAMP_CT_OK;
+}
+
+// nimg images at once ([nimg][n][n] in and out) through the scratch C
+// ([nimg][n][m] complex, the caller's); the same kernels and arithmetic per
+// image as launch_precond_image
+int launch_precond_images(const dgamp_ct_plan_s* pl, const float* in, float* out, float2* C, int nimg, int inverse,
+                          cudaStream_t st) {
+    if (nimg < 1) return DGAMP_CT_ERR_INVALID_ARG;
+    const int n = pl->n, m = pl->m2;
+    const size_t sm = (size_t)2 * fft_buf_len(m) * sizeof(float2);
+    const int thr = fft_threads(m);
+    const float f0 = 1.0f / (2.0f * (float)pl->P);
+    k_img_rows_fwd<<<dim3(n, nimg), thr, sm, st>>>(in, n, m, pl->ws.tw2, C);
+    DGCT_LAUNCH_CHECK();
+    k_img_cols<<<dim3(m, nimg), thr, sm, st>>>(C, n, m, pl->ws.tw2, f0, inverse ? 0 : 1);
+    DGCT_LAUNCH_CHECK();
+    k_img_rows_inv<<<dim3(n, nimg), thr, sm, st>>>(C, n, m, pl->ws.tw2, out);
     DGCT_LAUNCH_CHECK();
     return DGAMP_CT_OK;
 }

@@ -162,8 +162,8 @@ struct Workspace {
 struct dgamp_ct_cnn_s;
 
 struct dgamp_ct_plan_s {
-    dgamp_ct_cnn_s* cnn = nullptr;         // learned denoiser (not owned), used when opt.denoiser == 1
-    float* dn = nullptr;                   // [2][n][n] its outputs D(r), J_D(r) b
+    dgamp_ct_cnn_s* cnn = nullptr;         // learned denoiser (not owned), used when opt.denoiser is 1 or 2
+    float* dn = nullptr;                   // [3][n][n]: its D(r), J_D(r) b; prox-TV's D(r) (denoiser 2)
     int device = 0;
     int n = 0, nv = 0, nd = 0, P = 0, logP = 0, m2 = 0, logm2 = 0, ldp = 0;
     int64_t N = 0, M = 0;
@@ -378,6 +378,9 @@ int launch_sino_step(const dgamp_ct_plan_s* pl, cudaStream_t st, int bf);
 int sino_step_partials(const dgamp_ct_plan_s* pl);   // FP64 partial sums of tau_s_i it leaves in ws.partial
 int launch_precond_image(const dgamp_ct_plan_s* pl, const float* in, float* out, int inverse,
                          cudaStream_t st);
+// the same on nimg images at once ([nimg][n][n]) through the caller's scratch C ([nimg][n][m2] complex)
+int launch_precond_images(const dgamp_ct_plan_s* pl, const float* in, float* out, float2* C, int nimg, int inverse,
+                          cudaStream_t st);
 int fft_set_smem_limits(int bytes);
 // r = x + tau_r V^-1 in (tau_r from S), max |r| into S (a fan-beam solve's Step 3)
 int launch_precond_image_update(const dgamp_ct_plan_s* pl, const float* in, const float* x, float* out,
