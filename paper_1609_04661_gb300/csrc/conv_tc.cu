@@ -10,13 +10,14 @@
 // halo row, and the operand of tap (dy, dx) is the row slot of input row
 // y + dy - 1 started dx rows later.  Weights are staged once per CTA, one 64 x 64
 // block per tap.  A CTA takes a contiguous range of strips, consecutive rows
-// of one 128-column band, so each strip needs one new input row: a ring of six
-// row slots keeps three in use and three loading ahead.  The FP32
-// accumulators live in tensor memory, two of them (128 columns), so the
-// epilogue of one strip (tcgen05.ld, bias + ReLU or the mask, BF16 store)
-// overlaps the MMAs of the next.
+// of one 128-column band, so each strip needs one new input row: a ring of
+// NI + 4 row slots keeps the NI + 2 rows that the NI issuing warps' strips
+// read and two loading ahead.  The FP32 accumulators live in tensor memory,
+// two per issuing warp (64 columns each), so the epilogue of one strip
+// (tcgen05.ld, bias + ReLU or the mask, BF16 store) overlaps the MMAs of the
+// next.
 //
-// One elected thread issues the 36 MMAs of a strip and commits them to an
+// One elected thread per issuing warp issues the 36 MMAs of a strip and commits them to an
 // mbarrier; every wait on it is bounded and reports a timeout through
 // *err instead of hanging.
 #include <cuda.h>
@@ -34,16 +35,19 @@ constexpr int M = 128;                    // pixels per strip (MMA M)
 constexpr int HWL = M + 2;                // halo pixels loaded per row
 constexpr int HWP = 136;                  // row slot: 136 pixels x 128 B = 17 x 1024 B
 constexpr int A_ROW = HWP * 128;          // bytes of one row slot (pixel-major, 128-byte swizzle)
-constexpr int RING = 6;                   // row slots: three rows in use, three loading ahead
+constexpr int NI = 4;                     // MMA-issuing warps (strip k goes to warp 1 + k % NI)
+constexpr int RING = NI + 4;              // row slots: NI + 2 rows in use, two loading ahead
 constexpr int A_BYTES = RING * A_ROW;     // the ring
 constexpr int ROW_BYTES = HWL * 128;      // bytes one row load delivers (130 pixels x 64 channels)
 constexpr int B_TAP = 64 * 128;           // one tap of the weights: 64 co x 64 ci, 128-byte swizzle
 constexpr int B_BYTES = 9 * B_TAP;
 constexpr int SMEM = 1024 + B_BYTES + A_BYTES;       // + alignment slack
-constexpr int EPI_WARP0 = 4;              // warps 4..11: epilogue; warp 0: TMA; warps 1, 2: MMA
+constexpr int EPI_WARP0 = 8;              // warps 8..15: epilogue; warp 0: TMA; warps 1..NI: MMA
+                                          // (the epilogue warps start at a multiple of 4: warp % 4 is
+                                          // the TMEM lane quarter a warp may read)
 constexpr int THREADS = 32 * (EPI_WARP0 + 8);
 constexpr int EPI_THREADS = 32 * 8;
-constexpr unsigned TMEM_COLS = 256;       // four 64-column FP32 accumulators, two per MMA warp
+constexpr unsigned TMEM_COLS = 128 * NI;  // 2 NI 64-column FP32 accumulators, two per MMA warp
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bound of every mbarrier wait (2 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -246,8 +250,8 @@ __device__ __forceinline__ void epilogue(uint32_t tcol, const Strip& s, int H, i
 // inside a band, +3 when strip s starts a new band
 __device__ __forceinline__ int next_q(int Q, int s, int H) { return Q + ((s % H == 0) ? 3 : 1); }
 
-// accumulator of a CTA's strip k: MMA warp k % 2, its own buffer (k / 2) % 2
-__device__ __forceinline__ int acc_of(int k) { return 2 * (k & 1) + ((k >> 1) & 1); }
+// accumulator of a CTA's strip k: MMA warp k % NI, its own buffer (k / NI) % 2
+__device__ __forceinline__ int acc_of(int k) { return 2 * (k % NI) + ((k / NI) & 1); }
 
 // MODE 0: out = relu(bias + conv(in, Wk)); MODE 1: out = conv(in, Wk) * (mask > 0).
 // stall_ns > 0 is the timeout test: before any copy or MMA is issued, thread 0
@@ -258,15 +262,15 @@ __device__ __forceinline__ int acc_of(int k) { return 2 * (k & 1) + ((k >> 1) & 
 // input is [B][H][W][64] BF16 (map_in).  CTA k takes strips [k per, (k+1) per).
 // Warp-specialised, with no block barrier inside the loop:
 //   warp 0 (one lane): TMA producer -- weights, then input rows into the ring,
-//     a slot refilled once both MMA warps have released its previous row;
-//   warps 1 and 2 (one lane each): MMA issuers for the even and the odd
-//     strips -- a single issuing thread cannot feed the tensor core with
-//     N = 64 instructions, two can.  Each waits for its strip's three rows
-//     and a free accumulator of its own, issues 9 taps x 4 channel steps,
-//     commits acc_full, and commits row_empty for every row below its next
-//     strip's first row (each row gets one release from each MMA warp, so a
-//     slot is refilled only after both warps' MMAs reading it are done);
-//   warps 4..11: epilogue -- wait acc_full, read TMEM, free the accumulator
+//     a slot refilled once every MMA warp has released its previous row;
+//   warps 1..NI (one lane each): MMA issuers, warp 1 + X for the strips k
+//     with k % NI == X -- one issuing thread cannot feed the tensor core
+//     with N = 64 instructions.  Each waits for its strip's three rows and a
+//     free accumulator of its own, issues 9 taps x 4 channel steps, commits
+//     acc_full, and commits row_empty for every row below its next strip's
+//     first row (each row gets one release from each MMA warp, so a slot is
+//     refilled only after all the MMAs reading it are done);
+//   warps 8..15: epilogue -- wait acc_full, read TMEM, free the accumulator
 //     (acc_empty), then bias + ReLU or mask and the BF16 store.
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -276,8 +280,8 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t row_full[RING];
     __shared__ __align__(8) uint64_t row_empty[RING];
-    __shared__ __align__(8) uint64_t acc_full[4];
-    __shared__ __align__(8) uint64_t acc_empty[4];
+    __shared__ __align__(8) uint64_t acc_full[2 * NI];
+    __shared__ __align__(8) uint64_t acc_empty[2 * NI];
     __shared__ __align__(8) uint64_t w_bar;
     __shared__ __align__(8) uint64_t never_bar;   // the timeout test's barrier: nothing arrives
     __shared__ uint32_t tmem_slot;
@@ -299,9 +303,9 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
     if (tid == 0) {
         for (int r = 0; r < RING; ++r) {
             mbar_init(smem_u32(&row_full[r]), 1);
-            mbar_init(smem_u32(&row_empty[r]), 2);
+            mbar_init(smem_u32(&row_empty[r]), NI);
         }
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < 2 * NI; ++b) {
             mbar_init(smem_u32(&acc_full[b]), 1);
             mbar_init(smem_u32(&acc_empty[b]), EPI_THREADS);
         }
@@ -341,9 +345,9 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
                 load_row(&map_in, cur, H, nx, s1, sA, row_full);
             }
         }
-    } else if (warp == 1 || warp == 2) {
+    } else if (warp >= 1 && warp <= NI) {
         if (lane == 0) {
-            // ---- MMA issuer X for strips k with k % 2 == X ----
+            // ---- MMA issuer X for strips k with k % NI == X ----
             const int X = warp - 1;
             int q_total = 0;   // input rows of the CTA: first row of the last strip + 3
             for (int s = s0 + 1; s < s1; ++s) q_total = next_q(q_total, s, H);
@@ -354,10 +358,11 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
             int k = 0;
             for (int s = s0; s < s1; ++s, ++k) {
                 if (k > 0) Q = next_q(Q, s, H);
-                if ((k & 1) != X) continue;
+                if (k % NI != X) continue;
                 for (; fx < Q; ++fx) mma_commit(smem_u32(&row_empty[fx % RING]));   // rows this warp skips
                 const int a = acc_of(k);
-                if (k >= 4 && !mbar_wait(smem_u32(&acc_empty[a]), (uint32_t)(((k - 4) >> 2) & 1))) ok = false;
+                if (k >= 2 * NI && !mbar_wait(smem_u32(&acc_empty[a]), (uint32_t)(((k - 2 * NI) / (2 * NI)) & 1)))
+                    ok = false;
 #pragma unroll 1
                 for (int dy = 0; dy < 3; ++dy) {
                     const int q = Q + dy;
@@ -381,9 +386,12 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
                     }
                 }
                 mma_commit(smem_u32(&acc_full[a]));
-                // release the rows below this warp's next strip (strip k + 2)
+                // release the rows below this warp's next strip (strip k + NI)
                 int bound = q_total;
-                if (s + 2 < s1) bound = next_q(next_q(Q, s + 1, H), s + 2, H);
+                if (s + NI < s1) {
+                    bound = Q;
+                    for (int j = 1; j <= NI; ++j) bound = next_q(bound, s + j, H);
+                }
                 for (; fx < bound; ++fx) mma_commit(smem_u32(&row_empty[fx % RING]));
             }
             for (; fx < q_total; ++fx) mma_commit(smem_u32(&row_empty[fx % RING]));
@@ -393,7 +401,7 @@ k_conv64_tc(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ 
         int k = 0;
         for (int s = s0; s < s1; ++s, ++k) {
             const int a = acc_of(k);
-            if (!mbar_wait(smem_u32(&acc_full[a]), (uint32_t)((k >> 2) & 1))) ok = false;
+            if (!mbar_wait(smem_u32(&acc_full[a]), (uint32_t)((k / (2 * NI)) & 1))) ok = false;
             fence_after();
             epilogue<MODE>(tmem + (uint32_t)(a * 64), strip_of(s, H, nx), H, W, bias, mask, out,
                            smem_u32(&acc_empty[a]));
