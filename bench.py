@@ -60,7 +60,7 @@ FALLBACK_HBM_GBS = 6800.0
 # 64-row regions of 2-row threads), the projector (16 step segments) and the
 # tile back-projection.
 TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 64, "tv_vrows": 2, "bytes_per_iteration": 2112512 + 8421888 + 256}
-A_TRAFFIC = {"pj_seg": 16, "bytes_per_launch": 2142208}
+A_TRAFFIC = {"form": (0, 16), "bytes_per_launch": 2142208}      # (pj_band, pj_waves), or (0, pj_seg)
 AT_TRAFFIC = {"bp_mode": 1, "bytes_per_launch": 1263872}
 
 
@@ -844,8 +844,11 @@ def run_gpu(args):
                              "peak_gbs": hbm, "frac": byts / (ms_k * 1e-3) / 1e9 / hbm,
                              "peak_kind": f"{peak_kind} copy bandwidth"}}
 
-    roof_a = joseph_roof("project", f"k_project (A, {tun['pj_seg']} step segments)", algo["project"],
-                         A_TRAFFIC["bytes_per_launch"] if tun["pj_seg"] == A_TRAFFIC["pj_seg"] else None)
+    a_form = (tun["pj_band"], tun["pj_waves"]) if tun["pj_band"] else (0, tun["pj_seg"])
+    roof_a = joseph_roof("project",
+                         f"k_project_band + k_band_sum (A, {tun['pj_band']}-line bands, {tun['pj_waves']} wave(s))"
+                         if tun["pj_band"] else f"k_project (A, {tun['pj_seg']} step segments)", algo["project"],
+                         A_TRAFFIC["bytes_per_launch"] if a_form == A_TRAFFIC["form"] else None)
     roof_at = joseph_roof("backproject_update",
                           "k_backproject_tile (A^T + update)" if tun["bp_mode"] == 1 else "k_backproject (A^T + update)",
                           algo["backproject_update"],

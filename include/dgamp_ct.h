@@ -240,6 +240,16 @@ typedef struct {
                              each).  Inside a solve, both images of the MC pair share a
                              thread for 4-row threads in 32- or 64-row regions and for
                              2-row threads */
+    int32_t pj_band;      /* A: 0 = the ray-group form above; 16 or 32 = the banded form:
+                             a block copies that many consecutive lines of the staged image
+                             into shared memory and takes the steps inside them of a
+                             contiguous chunk of rays, writing per-band partial sums that a
+                             second kernel adds in band order (the sums of the ray-group
+                             form with the same split; offered where a 16-line band of FP32
+                             fits in 100 KB, parallel beam only).  Setting pj_seg with
+                             pj_band < 0 picks the ray-group form */
+    int32_t pj_waves;     /* A, banded form: 1 or 2 full waves of resident blocks; the
+                             rays are cut into that many chunks per band */
 } dgamp_ct_tuning;
 
 /* get: writes the plan's choices.  set: fields < 0 keep the current choice;
@@ -370,7 +380,7 @@ int dgamp_ct_solve_batched(int32_t n, const dgamp_ct_plan_t* plans, const float*
    launches (20 Chambolle steps: 2 launches) -- so one iteration of any
    number of slices is 6 launches, captured once as a graph and replayed.
    Slice i's result is bit-identical to dgamp_ct_solve on plans[i] with the
-   batch's implementation choices (dgamp_ct_tuning pj_seg = 16, bp_mode = 1,
+   batch's implementation choices (dgamp_ct_tuning pj_seg = 16, pj_band = 0, bp_mode = 1,
    sino_fused = 2, tv_kb = 10, tv_rows = 64, tv_vrows = 4); each plan's own tuning is not
    used here.
    create: n >= 1 distinct parallel-beam plans of the current device with the

@@ -23,7 +23,7 @@ int cuda_fail(cudaError_t e) {
 static void free_ws(Workspace& w) {
     void* ptrs[] = {w.XR, w.XC, w.x, w.r, w.b, w.p, w.zraw, w.z, w.s, w.hs, w.y, w.fft2d, w.partial,
                     w.partial_div, w.S, w.log, w.vc, w.gain, w.tw, w.tw2, w.scratch_d, w.hx, w.zraw2,
-                    w.fan_rays, w.fan_views};
+                    w.fan_rays, w.fan_views, w.pj_order, w.pj_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -153,6 +153,21 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
     std::vector<ViewConst> vc;
     view_constants(pl->n, pl->nd, ang, vc);
     DGCT_CUDA(cudaMemcpy(w.vc, vc.data(), vc.size() * sizeof(ViewConst), cudaMemcpyHostToDevice));
+    // banded A: the views in orientation order, and its partial sums where a
+    // band of 16 lines fits the shared memory the plan allows
+    {
+        std::vector<int> order;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int v = 0; v < pl->nv; ++v)
+                if (vc[v].col == pass) order.push_back(v);
+        pl->pj_n0 = 0;
+        for (int v = 0; v < pl->nv; ++v) pl->pj_n0 += vc[v].col == 0;
+        DGCT_TRY(dalloc(&w.pj_order, (size_t)pl->nv));
+        DGCT_CUDA(cudaMemcpy(w.pj_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
+        const size_t nb16 = (size_t)((pl->n + 15) / 16), part = nb16 * M;
+        if (16 * pl->ldp * (int)sizeof(float) <= 100 * 1024 && part * sizeof(float) <= ((size_t)512 << 20))
+            DGCT_TRY(dalloc(&w.pj_part, part));
+    }
 
     const int P = pl->P;
     std::vector<float> g(P);
@@ -320,7 +335,7 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
 // and V^-1 with the update (3, one segment).
 static int front_kernels(const dgamp_ct_plan_s* pl) {
     if (pl->fan) return 10;
-    return (fused_sino_now(pl) ? 1 : 3) + 2;
+    return (fused_sino_now(pl) ? 1 : 3) + 2 + (pl->pj_band ? 1 : 0);
 }
 static int front_segments(const dgamp_ct_plan_s* pl) {
     if (pl->fan) return 4;
@@ -557,6 +572,8 @@ int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, dgamp_ct_tuning* out) {
     out->bp_mode = pl->bp_mode;
     out->pj_seg = pl->pj_seg;
     out->tv_vrows = pl->tv_vrows;
+    out->pj_band = pl->pj_band;
+    out->pj_waves = pl->pj_waves;
     return DGAMP_CT_OK;
 }
 
@@ -566,6 +583,9 @@ int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
     if (t->pj_seg >= 0 && t->pj_seg != 8 && t->pj_seg != 16 && t->pj_seg != 32) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->tv_rows >= 0 && t->tv_rows != 32 && t->tv_rows != 64 && t->tv_rows != 128) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->tv_vrows >= 0 && t->tv_vrows != 2 && t->tv_vrows != 4 && t->tv_vrows != 8) return DGAMP_CT_ERR_INVALID_ARG;
+    if (t->pj_band >= 0 && t->pj_band != 0 && t->pj_band != 16 && t->pj_band != 32) return DGAMP_CT_ERR_INVALID_ARG;
+    if (t->pj_waves >= 0 && t->pj_waves != 1 && t->pj_waves != 2) return DGAMP_CT_ERR_INVALID_ARG;
+    if (t->pj_band > 0 && (pl->fan || !project_band_smem(pl, t->pj_band))) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (t->sino_fused == 1 && !sino_step_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (t->sino_fused == 2 && !sino_toeplitz_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (pl->fan && t->bp_mode == 1 && pl->fan_stride <= 0) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
@@ -575,6 +595,10 @@ int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
     if (t->sino_fused >= 0) pl->sino_fused = t->sino_fused;
     if (t->bp_mode >= 0) pl->bp_mode = t->bp_mode;
     if (t->pj_seg > 0) pl->pj_seg = t->pj_seg;
+    if (t->pj_seg > 0 && t->pj_band < 0) pl->pj_band = 0;     // a segment count picks the ray-group form
+    if (t->pj_band >= 0) pl->pj_band = t->pj_band;
+    if (t->pj_waves > 0) pl->pj_waves = t->pj_waves;
+    if (int rc = project_band_chunks(pl)) return rc;       // checked above: fits
     if (t->tv_vrows > 0) pl->tv_vrows = t->tv_vrows;
     drop_graph(pl);
     return DGAMP_CT_OK;

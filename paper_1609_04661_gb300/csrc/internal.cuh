@@ -155,6 +155,8 @@ struct Workspace {
     float* b = nullptr;            // the iteration's probe b (Eq. MC_SURE) [n][n]
     FanRay* fan_rays = nullptr;    // fan-beam plans: [n_views][n_det]
     FanView* fan_views = nullptr;  // fan-beam plans: [n_views]
+    int* pj_order = nullptr;       // banded A: views marching over rows, then over columns [n_views]
+    float* pj_part = nullptr;      // banded A: per-band partial sums [ceil(n / 16)][n_views][n_det]
 };
 
 }  // namespace dgct
@@ -178,6 +180,10 @@ struct dgamp_ct_plan_s {
     int sino_fused = 0;                    // solve: H A x, output step, H s in one kernel (k_sino_step)
     int bp_mode = 0;                       // A^T: 0 pixel-driven gather, 1 ray-driven tiles (plan-time choice)
     int pj_seg = 8;                        // A: step segments (warps) per ray group, 8/16/32 (plan-time choice)
+    int pj_band = 0;                       // A: 0 ray-group form; 16 or 32: lines per shared-memory band
+    int pj_waves = 1;                      // A, banded form: full waves of blocks (1 or 2)
+    int pj_c0 = 0, pj_c1 = 0;              // A, banded form: ray chunks per band of each orientation
+    int pj_n0 = 0;                         // views that march over rows (the first pj_n0 of ws.pj_order)
     int fan = 0;                           // 1: flat-detector fan beam (dgamp_ct_plan_fan)
     int fan_stride = 0;                    // fan A^T tiles: ray stride of one pass (0: tiles not applicable)
     // captured iteration graph
@@ -361,6 +367,8 @@ int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t
 int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf = 0);
 int backproject_autotune(dgamp_ct_plan_s* pl);
 int project_autotune(dgamp_ct_plan_s* pl);
+int project_band_smem(const dgamp_ct_plan_s* pl, int BR);
+int project_band_chunks(dgamp_ct_plan_s* pl);
 int launch_backproject(const dgamp_ct_plan_s* pl, const float* sino, const float* x_in,
                        float* out, int update, cudaStream_t st, int bf = 0, int nparts = 0);
 int launch_frobenius(dgamp_ct_plan_s* pl);

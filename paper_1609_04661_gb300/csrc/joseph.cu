@@ -128,6 +128,160 @@ k_project_batch(const BatchSlice* __restrict__ sl, const uint16_t* __restrict__ 
                              red);
 }
 
+// ------------------------------------------------ banded projection ----
+// The same sums as project_block, organised around the image instead of the
+// rays.  A block copies BR consecutive march lines of the staged image
+// (lines b*BR .. b*BR + BR - 1 of XR for the views that march over rows, of
+// XC for the others; they are contiguous) into shared memory once, and takes
+// the steps inside that band of a contiguous chunk of rays from there.  The
+// gathers then wait on shared memory instead of L2, and a staged line is
+// read from L2 once per chunk instead of once per ray group that crosses it.
+// Rays are listed per orientation, view by view in `order` (the n0 views
+// that march over rows, then the rest); each orientation's list is cut into
+// C0 or C1 equal chunks, so the views of a block share one orientation, and
+// the plan picks the chunk counts that fill whole waves of the GPU.  The
+// block writes the band's partial sum of each of its rays to part[b][v][d]
+// (0 where the ray has no step in the band); k_band_sum then adds the bands
+// in order and applies the path length per step.  Each partial sums its
+// steps in order from 0, like one segment of project_block, so with BR equal
+// to the segment length of the ray-group form (n = 512, BR = 32 and 16
+// segments) the two forms give identical bits.
+constexpr int kBandThreads = 512;
+constexpr int kBandMaxViews = 8;            // a chunk spans at most this many views
+constexpr int kBandSmemMax = 100 * 1024;    // largest band the plan considers (bytes)
+
+template <typename T>
+__global__ void __launch_bounds__(kBandThreads, 3)
+k_project_band(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int n, int nd, int nv,
+               const ViewConst* __restrict__ vcs, const int* __restrict__ order, int n0, int BR, int C0, int C1,
+               float* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char band_raw[];
+    __shared__ ViewConst svc[kBandMaxViews];
+    __shared__ int sv[kBandMaxViews];
+    T* band = reinterpret_cast<T*>(band_raw);
+    const int b = blockIdx.x, c = blockIdx.y;
+    const int col = c >= C0 ? 1 : 0;
+    const int C = col ? C1 : C0, ci = col ? c - C0 : c;
+    const long long tot = (long long)(col ? nv - n0 : n0) * nd;     // rays of this orientation
+    const int lo = (int)(tot * ci / C), hi = (int)(tot * (ci + 1) / C);
+    const int vfirst = lo / nd, nvb = (hi - 1) / nd - vfirst + 1;   // views of the chunk (<= kBandMaxViews)
+    const int r0 = b * BR, rows = min(BR, n - r0);
+    if (threadIdx.x < nvb) {                         // plan constants: read before the wait
+        const int v = order[(col ? n0 : 0) + vfirst + threadIdx.x];
+        sv[threadIdx.x] = v;
+        svc[threadIdx.x] = vcs[v];
+    }
+    pdl_wait();      // the staged image is the previous kernel's output
+    {
+        const T* __restrict__ src = (col ? XC : XR) + (size_t)r0 * ldp;
+        const int bytes = rows * ldp * (int)sizeof(T);      // a multiple of 8 (ldp % 4 == 0)
+        const uint4* __restrict__ s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(band);
+        const int n16 = bytes >> 4;
+#pragma unroll 4
+        for (int i = threadIdx.x; i < n16; i += kBandThreads) d4[i] = s4[i];
+        if ((bytes & 15) && threadIdx.x == 0)
+            reinterpret_cast<uint2*>(band)[bytes / 8 - 1] = reinterpret_cast<const uint2*>(src)[bytes / 8 - 1];
+    }
+    __syncthreads();
+    for (int g = lo + threadIdx.x; g < hi; g += kBandThreads) {
+        const int vv = g / nd, d = g - vv * nd, j = vv - vfirst;
+        const ViewConst& cv = svc[j];
+        float acc = 0.f;
+        const float base = fmaf((float)d, cv.a_det, cv.a0);
+        int s0, s1;
+        step_range(base, cv.a_step, n, s0, s1);
+        s0 = max(s0, r0);
+        s1 = min(s1, r0 + rows - 1);
+        if (s0 <= s1) {
+            long long pos = joseph_pos(cv, d, s0);
+            const long long pstep = cv.PSTEP;
+            const T* line = band + (s0 - r0) * ldp + kPad;
+#pragma unroll 4
+            for (int s = s0; s <= s1; ++s, pos += pstep, line += ldp) {
+                int i0;
+                float f;
+                joseph_tap(pos, i0, f);
+                const float x0 = ldf(line + i0), x1 = ldf(line + i0 + 1);
+                acc += fmaf(f, x1 - x0, x0);
+            }
+        }
+        part[((size_t)b * nv + sv[j]) * nd + d] = acc;
+    }
+}
+
+// sino[v][d] = w_v * sum over bands b = 0, 1, ... of part[b][v][d]; the loads
+// of 16 bands are issued before their adds.
+constexpr int kBandSumThreads = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kBandSumThreads)
+k_band_sum(const float* __restrict__ part, int nb, int M, int nd, const ViewConst* __restrict__ vcs,
+           T* __restrict__ sino) {
+    const int i = blockIdx.x * kBandSumThreads + threadIdx.x;
+    const float w = i < M ? vcs[i / nd].w : 0.f;
+    pdl_wait();
+    if (i >= M) return;
+    float t = 0.f;
+    int b = 0;
+    for (; b + 16 <= nb; b += 16) {
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = part[(size_t)(b + k) * M + i];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) t += v[k];
+    }
+    for (; b < nb; ++b) t += part[(size_t)b * M + i];
+    stf(sino + i, t * w);
+}
+
+// Shared memory of a band of BR lines; 0 if the plan cannot take the form.
+int project_band_smem(const dgamp_ct_plan_s* pl, int BR) {
+    if (!pl->ws.pj_part || (BR != 16 && BR != 32)) return 0;
+    const int bytes = BR * pl->ldp * (int)sizeof(float);
+    return bytes <= kBandSmemMax ? bytes : 0;
+}
+
+// Chunks per band of each orientation for bands of pj_band lines: pj_waves
+// full waves of resident blocks over the bands, split between the two
+// orientations by their views, each chunk at most kBandMaxViews - 1 views
+// long (so it touches at most kBandMaxViews) and at least one ray.
+int project_band_chunks(dgamp_ct_plan_s* pl) {
+    pl->pj_c0 = pl->pj_c1 = 0;
+    if (!pl->pj_band) return DGAMP_CT_OK;
+    const int smem = project_band_smem(pl, pl->pj_band);
+    if (!smem) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
+    int bps = 0, sms = 0;
+    DGCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_project_band<float>, kBandThreads, smem));
+    DGCT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device));
+    const int nb = (pl->n + pl->pj_band - 1) / pl->pj_band;
+    const int total = std::max(2, pl->pj_waves * std::max(bps, 1) * sms / nb);
+    const int n0 = pl->pj_n0, n1 = pl->nv - n0;
+    auto fit = [&](int want, int nvo) {
+        if (nvo == 0) return 0;
+        want = std::max(want, (nvo + kBandMaxViews - 2) / (kBandMaxViews - 1));
+        return (int)std::min<long long>(std::max(want, 1), (long long)nvo * pl->nd);
+    };
+    pl->pj_c0 = fit((int)std::lround((double)total * n0 / pl->nv), n0);
+    pl->pj_c1 = fit(total - pl->pj_c0, n1);
+    return DGAMP_CT_OK;
+}
+
+template <typename T>
+static cudaError_t launch_project_band(const dgamp_ct_plan_s* pl, T* sino, cudaStream_t st) {
+    const int BR = pl->pj_band;
+    const int nb = (pl->n + BR - 1) / BR;
+    const dim3 grd(nb, pl->pj_c0 + pl->pj_c1);
+    const size_t smem = (size_t)BR * pl->ldp * sizeof(T);
+    cudaError_t e = launch_pdl(k_project_band<T>, grd, dim3(kBandThreads), smem, st, (const T*)pl->ws.XR,
+                               (const T*)pl->ws.XC, pl->ldp, pl->n, pl->nd, pl->nv, (const ViewConst*)pl->ws.vc,
+                               (const int*)pl->ws.pj_order, pl->pj_n0, BR, pl->pj_c0, pl->pj_c1, pl->ws.pj_part);
+    if (e != cudaSuccess) return e;
+    const int M = (int)pl->M;
+    return launch_pdl(k_band_sum<T>, dim3((M + kBandSumThreads - 1) / kBandSumThreads), dim3(kBandSumThreads), 0, st,
+                      (const float*)pl->ws.pj_part, nb, M, pl->nd, (const ViewConst*)pl->ws.vc, sino);
+}
+
 template <int SEG>
 static cudaError_t launch_project_seg(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf) {
     dim3 blk(kPjRays * SEG), grd((pl->nd + kPjRays - 1) / kPjRays, pl->nv);
@@ -139,6 +293,13 @@ static cudaError_t launch_project_seg(const dgamp_ct_plan_s* pl, float* sino, cu
 }
 
 int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf) {
+    if (pl->pj_band) {
+        if (bf)
+            DGCT_CUDA(launch_project_band<bf16s>(pl, (bf16s*)sino, st));
+        else
+            DGCT_CUDA(launch_project_band<float>(pl, sino, st));
+        return DGAMP_CT_OK;
+    }
     if (pl->pj_seg == 32)
         DGCT_CUDA(launch_project_seg<32>(pl, sino, st, bf));
     else if (pl->pj_seg == 16)
@@ -481,18 +642,30 @@ int backproject_autotune(dgamp_ct_plan_s* pl) {
     return rc;
 }
 
-// Plan-time choice of the step segments per ray group of A (same sums in
-// another order): time 8, 16 and 32 on the plan's geometry (the staged image
-// buffers' contents do not change the work) and keep the fastest.
+// Plan-time choice of the form of A (same sums in another order): the ray-
+// group form with 8, 16 and 32 step segments, and where the plan allows it
+// the banded form with 16- or 32-line bands in one or two waves; each
+// is timed on the plan's geometry (the staged image buffers' contents do not
+// change the work) and the fastest is kept.
 int project_autotune(dgamp_ct_plan_s* pl) {
+    const int big = project_band_smem(pl, 32) ? project_band_smem(pl, 32) : project_band_smem(pl, 16);
+    if (big > 48 * 1024) {
+        DGCT_TRY(raise_smem_limit((const void*)k_project_band<float>, big));
+        DGCT_TRY(raise_smem_limit((const void*)k_project_band<bf16s>, big));
+    }
     cudaEvent_t e0, e1;
     DGCT_CUDA(cudaEventCreate(&e0));
     DGCT_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_seg = 8, rc = DGAMP_CT_OK;
-    const int segs[3] = {8, 16, 32};
-    for (int k = 0; k < 3 && rc == DGAMP_CT_OK; ++k) {
-        pl->pj_seg = segs[k];
+    int best_seg = 8, best_band = 0, best_waves = 1, rc = DGAMP_CT_OK;
+    // {pj_seg, pj_band, pj_waves}
+    const int forms[7][3] = {{8, 0, 1}, {16, 0, 1}, {32, 0, 1}, {16, 16, 1}, {16, 16, 2}, {16, 32, 1}, {16, 32, 2}};
+    for (int k = 0; k < 7 && rc == DGAMP_CT_OK; ++k) {
+        if (forms[k][1] && !project_band_smem(pl, forms[k][1])) continue;
+        pl->pj_seg = forms[k][0];
+        pl->pj_band = forms[k][1];
+        pl->pj_waves = forms[k][2];
+        rc = project_band_chunks(pl);
         for (int rep = 0; rep < 6 && rc == DGAMP_CT_OK; ++rep) {
             if (rep == 1) cudaEventRecord(e0, 0);
             rc = launch_project(pl, pl->ws.zraw, 0, 0);
@@ -504,12 +677,17 @@ int project_autotune(dgamp_ct_plan_s* pl) {
         if (rc == DGAMP_CT_OK) cudaEventElapsedTime(&ms, e0, e1);
         if (rc == DGAMP_CT_OK && ms < best) {
             best = ms;
-            best_seg = segs[k];
+            best_seg = pl->pj_seg;
+            best_band = pl->pj_band;
+            best_waves = pl->pj_waves;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     pl->pj_seg = best_seg;
+    pl->pj_band = best_band;
+    pl->pj_waves = best_waves;
+    if (rc == DGAMP_CT_OK) rc = project_band_chunks(pl);
     return rc;
 }
 

@@ -79,6 +79,56 @@ def test_project_matches_oracle(dg, n, nv, nd, ang, kind, pj_seg):
     assert np.array_equal(z, again)                          # deterministic
 
 
+# the banded A: bands of 16 or 32 staged lines in shared memory, the rays cut
+# into chunks that fill one or two waves (chunks that start and end inside a
+# view); 37 views leave an odd number of each orientation, 4096 views make a
+# chunk span many views' worth of the limit, n = 37, 50, 129, 300 a short last band
+@pytest.mark.parametrize("n,nv,nd,ang", GEOMS + [(512, 4, 729, None), (300, 5, 1100, None), (96, 37, 140, None),
+                                                 (16, 4096, 24, None)])
+@pytest.mark.parametrize("band,waves", [(16, 1), (16, 2), (32, 1), (32, 2)])
+def test_banded_project_matches_oracle(dg, n, nv, nd, ang, band, waves):
+    g = Geometry(n, nv, nd, ang)
+    x = _img(n, 3, "phantom")
+    with dg.Plan(n, nv, nd, angles=ang) as pl:
+        pl.set_tuning(pj_band=band, pj_waves=waves)
+        t = pl.tuning()
+        assert (t["pj_band"], t["pj_waves"]) == (band, waves)
+        z = host(pl.project(cu(x)))
+        zp = host(pl.project(cu(x), precond=True))
+        again = host(pl.project(cu(x)))
+        pl.set_tuning(pj_seg=8)                               # a segment count picks the ray-group form
+        assert pl.tuning()["pj_band"] == 0
+    assert rel(z, joseph.forward_project(x, g)) < 1e-5
+    assert rel(zp, precond.project(x, g)) < 1e-5
+    assert np.array_equal(z, again)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_banded_project_equals_sixteen_segments_at_512(dg, storage):
+    """At n = 512 a 32-line band is one of 16 segments of the ray-group form:
+    both forms add the same steps in the same order, so A x and a solve that
+    stores its sinograms in FP32 or BF16 agree bit for bit."""
+    n, nv, nd = 512, 16, 729
+    x = _img(n, 4, "phantom")
+    g = Geometry(n, nv, nd)
+    y = np.random.default_rng(5).poisson(1e4 * np.exp(-joseph.forward_project(0.02 * x, g))).astype(np.float32)
+    out = {}
+    rest = dict(filter_mode=1, sino_fused=2, bp_mode=1, tv_kb=10, tv_rows=64, tv_vrows=4)   # the same elsewhere
+    for form in ({"pj_seg": 16}, {"pj_band": 32, "pj_waves": 1}):
+        with dg.Plan(n, nv, nd, storage=storage, damp_x=0.5, damp_s=0.5) as pl:
+            pl.set_tuning(**rest, **form)
+            out[len(form)] = (host(pl.project(cu(x))), host(pl.solve(cu(y), 1e4, 3)))
+    assert np.array_equal(out[1][0], out[2][0])
+    assert np.array_equal(out[1][1], out[2][1])
+
+
+def test_banded_project_tuning_checks(dg):
+    with dg.Plan(64, 10, 95) as pl:
+        for bad in ({"pj_band": 8}, {"pj_band": 64}, {"pj_waves": 3}):
+            with pytest.raises(Exception):
+                pl.set_tuning(**bad)
+
+
 @pytest.mark.parametrize("n,nv,nd,ang", GEOMS + [(512, 4, 729, None)])
 @pytest.mark.parametrize("bp_mode", [0, 1])                # pixel-driven gather, ray-driven tiles
 def test_backproject_matches_oracle(dg, n, nv, nd, ang, bp_mode):
