@@ -845,9 +845,14 @@ def run_gpu(args):
                              "peak_kind": f"{peak_kind} copy bandwidth"}}
 
     a_form = (tun["pj_band"], tun["pj_waves"]) if tun["pj_band"] else (0, tun["pj_seg"])
-    roof_a = joseph_roof("project",
-                         f"k_project_band + k_band_sum (A, {tun['pj_band']}-line bands, {tun['pj_waves']} wave(s))"
-                         if tun["pj_band"] else f"k_project (A, {tun['pj_seg']} step segments)", algo["project"],
+    if not tun["pj_band"]:
+        a_label = f"k_project (A, {tun['pj_seg']} step segments)"
+    elif tun["sino_fused"] == 2:
+        a_label = (f"k_project_band (A as {tun['pj_band']}-line band partials, {tun['pj_waves']} wave(s); "
+                   "the cluster sinogram kernel adds them)")
+    else:
+        a_label = f"k_project_band + k_band_sum (A, {tun['pj_band']}-line bands, {tun['pj_waves']} wave(s))"
+    roof_a = joseph_roof("project", a_label, algo["project"],
                          A_TRAFFIC["bytes_per_launch"] if a_form == A_TRAFFIC["form"] else None)
     roof_at = joseph_roof("backproject_update",
                           "k_backproject_tile (A^T + update)" if tun["bp_mode"] == 1 else "k_backproject (A^T + update)",

@@ -165,8 +165,10 @@ static int plan_alloc(dgamp_ct_plan_s* pl, const std::vector<double>& ang) {
         DGCT_TRY(dalloc(&w.pj_order, (size_t)pl->nv));
         DGCT_CUDA(cudaMemcpy(w.pj_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
         const size_t nb16 = (size_t)((pl->n + 15) / 16), part = nb16 * M;
-        if (16 * pl->ldp * (int)sizeof(float) <= 100 * 1024 && part * sizeof(float) <= ((size_t)512 << 20))
+        if (16 * pl->ldp * (int)sizeof(float) <= 100 * 1024 && part * sizeof(float) <= ((size_t)512 << 20)) {
             DGCT_TRY(dalloc(&w.pj_part, part));
+            DGCT_CUDA(cudaMemset(w.pj_part, 0, part * sizeof(float)));
+        }
     }
 
     const int P = pl->P;
@@ -273,7 +275,7 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
         DGCT_TRY(mark());
         DGCT_TRY(launch_precond_image_update(pl, w.r, w.x, w.r, st));    //         r = x + tau_r V^-1 A^T s
     } else {
-    DGCT_TRY(launch_project(pl, w.zraw, st, bf));                      // Step 1: A x
+    DGCT_TRY(launch_project(pl, w.zraw, st, bf, !project_sum_in_sino(pl)));   // Step 1: A x
     DGCT_TRY(mark());
     if (fused_sino_now(pl)) {
         DGCT_TRY(launch_sino_step(pl, st, bf));                         // H A x, Step 2, H s
@@ -335,7 +337,7 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
 // and V^-1 with the update (3, one segment).
 static int front_kernels(const dgamp_ct_plan_s* pl) {
     if (pl->fan) return 10;
-    return (fused_sino_now(pl) ? 1 : 3) + 2 + (pl->pj_band ? 1 : 0);
+    return (fused_sino_now(pl) ? 1 : 3) + 2 + (pl->pj_band && !project_sum_in_sino(pl) ? 1 : 0);
 }
 static int front_segments(const dgamp_ct_plan_s* pl) {
     if (pl->fan) return 4;

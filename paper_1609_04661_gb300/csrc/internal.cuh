@@ -364,7 +364,13 @@ int fill_stats(const dgamp_ct_plan_s* pl, int iters, dgamp_ct_stats* stats);
 // joseph.cu
 // bf = 1: the staged image XR/XC and the sinogram `sino` hold BF16 (solve with storage = 1)
 int launch_stage_image(const dgamp_ct_plan_s* pl, const float* img, cudaStream_t st, int bf = 0);
-int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf = 0);
+// sum = false (banded form only): leave A x as band partials in ws.pj_part
+// for the cluster sinogram kernel, which adds them itself
+int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf = 0, bool sum = true);
+// inside a solve the cluster sinogram kernel adds the banded projector's partials
+inline bool project_sum_in_sino(const dgamp_ct_plan_s* pl) {
+    return pl->pj_band && pl->sino_fused == 2 && !pl->opt.output_moments && !pl->fan;
+}
 int backproject_autotune(dgamp_ct_plan_s* pl);
 int project_autotune(dgamp_ct_plan_s* pl);
 int project_band_smem(const dgamp_ct_plan_s* pl, int BR);

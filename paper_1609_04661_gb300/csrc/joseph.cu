@@ -268,7 +268,7 @@ int project_band_chunks(dgamp_ct_plan_s* pl) {
 }
 
 template <typename T>
-static cudaError_t launch_project_band(const dgamp_ct_plan_s* pl, T* sino, cudaStream_t st) {
+static cudaError_t launch_project_band(const dgamp_ct_plan_s* pl, T* sino, cudaStream_t st, bool sum) {
     const int BR = pl->pj_band;
     const int nb = (pl->n + BR - 1) / BR;
     const dim3 grd(nb, pl->pj_c0 + pl->pj_c1);
@@ -276,7 +276,7 @@ static cudaError_t launch_project_band(const dgamp_ct_plan_s* pl, T* sino, cudaS
     cudaError_t e = launch_pdl(k_project_band<T>, grd, dim3(kBandThreads), smem, st, (const T*)pl->ws.XR,
                                (const T*)pl->ws.XC, pl->ldp, pl->n, pl->nd, pl->nv, (const ViewConst*)pl->ws.vc,
                                (const int*)pl->ws.pj_order, pl->pj_n0, BR, pl->pj_c0, pl->pj_c1, pl->ws.pj_part);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !sum) return e;
     const int M = (int)pl->M;
     return launch_pdl(k_band_sum<T>, dim3((M + kBandSumThreads - 1) / kBandSumThreads), dim3(kBandSumThreads), 0, st,
                       (const float*)pl->ws.pj_part, nb, M, pl->nd, (const ViewConst*)pl->ws.vc, sino);
@@ -292,12 +292,12 @@ static cudaError_t launch_project_seg(const dgamp_ct_plan_s* pl, float* sino, cu
                       pl->ldp, pl->n, pl->nd, (const ViewConst*)pl->ws.vc, sino);
 }
 
-int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf) {
+int launch_project(const dgamp_ct_plan_s* pl, float* sino, cudaStream_t st, int bf, bool sum) {
     if (pl->pj_band) {
         if (bf)
-            DGCT_CUDA(launch_project_band<bf16s>(pl, (bf16s*)sino, st));
+            DGCT_CUDA(launch_project_band<bf16s>(pl, (bf16s*)sino, st, sum));
         else
-            DGCT_CUDA(launch_project_band<float>(pl, sino, st));
+            DGCT_CUDA(launch_project_band<float>(pl, sino, st, sum));
         return DGAMP_CT_OK;
     }
     if (pl->pj_seg == 32)

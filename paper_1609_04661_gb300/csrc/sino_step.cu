@@ -246,7 +246,8 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
                                               long long M, int onsager, float damp_s, int truncate, DevScalars* S,
                                               double* __restrict__ partial, const double* __restrict__ partial_div,
                                               double N, double floor_rel, IterLog* log, int v, bool record,
-                                              float* smf, CtShared& shd) {
+                                              float* smf, CtShared& shd, const float* __restrict__ part = nullptr,
+                                              int nb = 0, float wv = 0.f) {
     constexpr int OUT = 32 * R;
     constexpr int TH = ct_threads(W);
     auto& sm = shd.sm;
@@ -271,6 +272,9 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
         const int m = i - 1;
         hs[i] = (m >= 0 && m < 2 * nd - 1) ? hx[m] : 0.f;
     }
+    // every CTA of the cluster has started before the first write into another's
+    // shared memory: arrive now, wait just before that write
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
     pdl_wait();
     // the tau_x warp issues its loads of the divergence partials first, so
     // that their latency overlaps the loads and the first product
@@ -294,7 +298,37 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
             pre_y[j] = y[row0 + d_lo + o];
         }
     }
-    for (int i = tid; i < nd; i += TH) zs[i] = ldf(zraw + row0 + i);
+    if (part) {
+        // A x from the banded projector's partial sums (nb bands, added in
+        // band order, times the path length per step, rounded as the storage
+        // type would store it): each CTA its own bins, then to every CTA
+        for (int o = tid; o < nown; o += TH) {
+            const float* __restrict__ pp = part + row0 + d_lo + o;
+            float t = 0.f;
+            int b = 0;
+            for (; b + 8 <= nb; b += 8) {
+                float pv[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) pv[k] = pp[(size_t)(b + k) * M];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) t += pv[k];
+            }
+            for (; b < nb; ++b) t += pp[(size_t)b * M];
+            zs[d_lo + o] = as_stored(t * wv, zraw);
+        }
+        asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+        __syncthreads();
+        for (int o = tid; o < nown; o += TH) {
+            const float z = zs[d_lo + o];
+#pragma unroll
+            for (int r = 0; r < CL; ++r)
+                if (r != rank) *cluster.map_shared_rank(zs + d_lo + o, r) = z;
+        }
+        cluster.sync();         // every bin of zs is in every CTA
+    } else {
+        for (int i = tid; i < nd; i += TH) zs[i] = ldf(zraw + row0 + i);
+        asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+    }
     __syncthreads();
     const int len = (nd + W - 1) / W;
     const int dl = d_lo + R * lane;
@@ -371,15 +405,16 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
 }
 
 template <typename T, int R, int CL, int W>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ct_threads(W))
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ct_threads(W), 2)
 k_sino_toeplitz(const T* __restrict__ zraw, const float* __restrict__ y, T* s, T* __restrict__ hsout, int nd,
                 const float* __restrict__ hx, long long M, int onsager, float damp_s, int truncate, DevScalars* S,
                 double* __restrict__ partial, const double* __restrict__ partial_div, double N, double floor_rel,
-                IterLog* log) {
+                IterLog* log, const float* __restrict__ part, int nb, const ViewConst* __restrict__ vcs) {
     extern __shared__ float smf[];
     __shared__ CtShared shd;
+    const int v = (int)blockIdx.x / CL;
     sino_ct_block<T, R, CL, W>(zraw, y, s, hsout, nd, hx, M, onsager, damp_s, truncate, S, partial, partial_div, N,
-                               floor_rel, log, (int)blockIdx.x / CL, blockIdx.x == 0, smf, shd);
+                               floor_rel, log, v, blockIdx.x == 0, smf, shd, part, nb, part ? vcs[v].w : 0.f);
 }
 
 // The sinogram step of every slice of a batch in one launch: cluster c
@@ -468,9 +503,14 @@ static int launch_ct(const dgamp_ct_plan_s* pl, cudaStream_t st, const T* zraw, 
     double* partial = w.partial;
     const double* partial_div = w.partial_div;
     IterLog* log = w.log;
+    // with the banded projector the kernel adds its band partials itself
+    const float* part = project_sum_in_sino(pl) ? w.pj_part : nullptr;
+    int nb = part ? (pl->n + pl->pj_band - 1) / pl->pj_band : 0;
+    const ViewConst* vcs = w.vc;
     void* args[] = {(void*)&zraw, (void*)&y, (void*)&s, (void*)&hs, (void*)&nd, (void*)&hx, (void*)&M,
                     (void*)&onsager, (void*)&damp_s, (void*)&truncate, (void*)&S, (void*)&partial,
-                    (void*)&partial_div, (void*)&N, (void*)&floor_rel, (void*)&log};
+                    (void*)&partial_div, (void*)&N, (void*)&floor_rel, (void*)&log, (void*)&part, (void*)&nb,
+                    (void*)&vcs};
     return ct_dispatch<T, false>(R, cl, [&](const void* k, int threads, int c) -> int {
         DGCT_CUDA(launch_pdl_c(k, dim3((unsigned)(pl->nv * c)), dim3(threads), sm, st, args));
         return DGAMP_CT_OK;
