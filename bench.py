@@ -57,10 +57,10 @@ FALLBACK_HBM_GBS = 6800.0
 # ncu captures of this workload's headline plan (cold cache), valid only for
 # the configuration captured and the kernels as they were then: the blocked-TV
 # launches of one iteration (both images per thread, 10 steps per launch,
-# 64-row regions of 2-row threads), the projector (16 step segments) and the
-# tile back-projection.
+# 64-row regions of 2-row threads), the banded projector (32-line bands, one
+# wave) and the tile back-projection.
 TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 64, "tv_vrows": 2, "bytes_per_iteration": 2112512 + 8421888 + 256}
-A_TRAFFIC = {"form": (0, 16), "bytes_per_launch": 2142208}      # (pj_band, pj_waves), or (0, pj_seg)
+A_TRAFFIC = {"form": (32, 1), "bytes_per_launch": 2147328}      # (pj_band, pj_waves), or (0, pj_seg)
 AT_TRAFFIC = {"bp_mode": 1, "bytes_per_launch": 1263872}
 
 
