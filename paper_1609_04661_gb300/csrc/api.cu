@@ -92,6 +92,7 @@ static void view_constants(int n, int nd, const std::vector<double>& ang, std::v
         const double ad = v.col ? -1.0 / st : 1.0 / ct;
         const double q = 4294967296.0;
         v.inv_adet = (float)(1.0 / ad);
+        v.inv_astep = as != 0.0 ? (float)(1.0 / as) : 0.f;
         v.P0 = (long long)std::llround(a0 * q);
         v.PSTEP = (long long)std::llround(as * q);
         v.PDET = (long long)std::llround(ad * q);

@@ -32,7 +32,7 @@ struct ViewConst {
     float inv_adet;               // 1 / a_det
     int col;                      // 1: march over columns, interpolate along rows
     int sg;                       // sign of PDET: +1 if position grows with d
-    int pad;
+    float inv_astep;              // 1 / a_step (0 when a_step is 0)
 };
 
 // Scalars of Algorithm 1 that live on the device for the whole solve.
@@ -218,6 +218,24 @@ __device__ __forceinline__ void step_range(float base, float a_step, int n, int&
         return;
     }
     float t0 = (-1.f - base) / a_step, t1 = ((float)n - base) / a_step;
+    float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
+    lo = fmaxf(lo, -1.f);
+    hi = fminf(hi, (float)n);
+    s0 = max(0, (int)floorf(lo) - 1);
+    s1 = min(n - 1, (int)ceilf(hi) + 1);
+}
+
+// step_range with the reciprocal of a_step in place of two divisions.  The
+// bounds may move by a rounding error of the reciprocal, well inside the
+// one-step widening, so the range still holds every step with a tap in the
+// image, and any extra step's taps fall in the zero guard cells (adding an
+// exact 0).
+__device__ __forceinline__ void step_range_rcp(float base, float a_step, float inv_astep, int n, int& s0, int& s1) {
+    if (fabsf(a_step) < 1e-12f) {
+        if (base >= -1.f && base < (float)n) { s0 = 0; s1 = n - 1; } else { s0 = 1; s1 = 0; }
+        return;
+    }
+    float t0 = (-1.f - base) * inv_astep, t1 = ((float)n - base) * inv_astep;
     float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
     lo = fmaxf(lo, -1.f);
     hi = fminf(hi, (float)n);

@@ -184,13 +184,17 @@ k_project_band(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int 
             reinterpret_cast<uint2*>(band)[bytes / 8 - 1] = reinterpret_cast<const uint2*>(src)[bytes / 8 - 1];
     }
     __syncthreads();
-    for (int g = lo + threadIdx.x; g < hi; g += kBandThreads) {
-        const int vv = g / nd, d = g - vv * nd, j = vv - vfirst;
+    // this thread's rays lo + tid, lo + tid + kBandThreads, ...: the view and
+    // bin of the first by one division, then stepped
+    int g = lo + threadIdx.x;
+    int j = g / nd, d = g - j * nd;
+    j -= vfirst;
+    for (; g < hi; g += kBandThreads) {
         const ViewConst& cv = svc[j];
         float acc = 0.f;
         const float base = fmaf((float)d, cv.a_det, cv.a0);
         int s0, s1;
-        step_range(base, cv.a_step, n, s0, s1);
+        step_range_rcp(base, cv.a_step, cv.inv_astep, n, s0, s1);
         s0 = max(s0, r0);
         s1 = min(s1, r0 + rows - 1);
         if (s0 <= s1) {
@@ -207,6 +211,7 @@ k_project_band(const T* __restrict__ XR, const T* __restrict__ XC, int ldp, int 
             }
         }
         part[((size_t)b * nv + sv[j]) * nd + d] = acc;
+        for (d += kBandThreads; d >= nd; d -= nd) ++j;
     }
 }
 
