@@ -250,12 +250,6 @@ typedef struct {
                              pj_band < 0 picks the ray-group form */
     int32_t pj_waves;     /* A, banded form: 1 or 2 full waves of resident blocks; the
                              rays are cut into that many chunks per band */
-    int32_t probe_tv;     /* 1 (default): a prox-TV solve whose TV launches all take the
-                             two-image kernel draws every iteration's probe b (Eq. MC_SURE)
-                             before its first iteration, one launch for up to 256 MB of
-                             them, and the TV kernel forms r + eps b itself, so no probe
-                             kernel runs per iteration (the same values: bit-identical
-                             results); 0: a probe kernel per iteration */
 } dgamp_ct_tuning;
 
 /* get: writes the plan's choices.  set: fields < 0 keep the current choice;

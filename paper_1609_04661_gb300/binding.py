@@ -59,8 +59,7 @@ class Tuning(C.Structure):
     """dgamp_ct_tuning."""
     _fields_ = [("filter_mode", C.c_int32), ("tv_kb", C.c_int32), ("tv_rows", C.c_int32),
                 ("sino_fused", C.c_int32), ("bp_mode", C.c_int32), ("pj_seg", C.c_int32),
-                ("tv_vrows", C.c_int32), ("pj_band", C.c_int32), ("pj_waves", C.c_int32),
-                ("probe_tv", C.c_int32)]
+                ("tv_vrows", C.c_int32), ("pj_band", C.c_int32), ("pj_waves", C.c_int32)]
 
 
 class Options(C.Structure):
@@ -297,8 +296,7 @@ class Plan:
         solve runs H A x, the output step and H s as one kernel, "bp_mode": 0 pixel-driven | 1
         ray-driven A^T, "pj_seg": warps splitting the steps of 32 rays in A, "tv_vrows": rows of a TV
         region per thread (2, 4 or 8), "pj_band": 0 for that ray-group A or the lines of a shared-memory
-        band of the banded A (16 or 32), "pj_waves": full waves of blocks of the banded A (1 or 2),
-        "probe_tv": 1 if a prox-TV solve draws all its probes before the first iteration}."""
+        band of the banded A (16 or 32), "pj_waves": full waves of blocks of the banded A (1 or 2)}."""
         t = Tuning()
         _check(self._lib.dgamp_ct_get_tuning(self._h, C.byref(t)), "get_tuning")
         return {name: getattr(t, name) for name, _ in Tuning._fields_}

@@ -23,7 +23,7 @@ int cuda_fail(cudaError_t e) {
 static void free_ws(Workspace& w) {
     void* ptrs[] = {w.XR, w.XC, w.x, w.r, w.b, w.p, w.zraw, w.z, w.s, w.hs, w.y, w.fft2d, w.partial,
                     w.partial_div, w.S, w.log, w.vc, w.gain, w.tw, w.tw2, w.scratch_d, w.hx, w.zraw2,
-                    w.fan_rays, w.fan_views, w.pj_order, w.pj_part, w.ball};
+                    w.fan_rays, w.fan_views, w.pj_order, w.pj_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -293,10 +293,8 @@ static int enqueue_iteration(dgamp_ct_plan_s* pl, cudaStream_t st, cudaEvent_t* 
                                 fused_sino_now(pl) ? sino_step_partials(pl) : 0));
     }
     DGCT_TRY(mark());
-    // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r;
-    // with the probes drawn before the solve the TV kernel forms r + eps b
-    // (the timed segment stays, empty)
-    if (!probe_pre_now(pl)) DGCT_TRY(launch_probe_input(pl, 0, st, uses_cnn(pl) ? 1 : 0));
+    // Step 4: the probe b (learned denoiser) or r + eps b (prox-TV) beside r
+    DGCT_TRY(launch_probe_input(pl, 0, st, uses_cnn(pl) ? 1 : 0));
     if (pl->opt.denoiser == 2) {
         // both denoisers on r, each with its divergence: the CNN and its
         // forward-mode derivative along b, then r + eps b beside r (the same
@@ -347,23 +345,12 @@ static int front_segments(const dgamp_ct_plan_s* pl) {
     return (fused_sino_now(pl) ? 1 : 3) + 2;
 }
 
-// A prox-TV solve of `iters` iterations whose TV launches all take the
-// two-image kernel draws every iteration's probe b before the first (the
-// same values as k_probe_input's, up to 256 MB of them), so no probe kernel
-// runs per iteration.
-constexpr size_t kProbeAllMaxBytes = (size_t)256 << 20;
-
-static bool probes_before(const dgamp_ct_plan_s* pl, int iters) {
-    return pl->probe_tv && pl->opt.denoiser == 0 && tv_pair_kernel(pl) &&
-           (size_t)iters * (size_t)pl->N * sizeof(float) <= kProbeAllMaxBytes;
-}
-
 // kernels one iteration launches: Steps 1-3, the probe, the denoiser
-static int kernels_per_iteration(const dgamp_ct_plan_s* pl, bool pre) {
+static int kernels_per_iteration(const dgamp_ct_plan_s* pl) {
     if (pl->opt.denoiser == 2 && pl->cnn)
         return front_kernels(pl) + 1 + cnn_launches_per_pair(pl->cnn) + 1 + tv_num_launches(pl, 1, 0.0) + 2;
     if (pl->opt.denoiser == 1 && pl->cnn) return front_kernels(pl) + 1 + cnn_launches_per_pair(pl->cnn) + 1;
-    return front_kernels(pl) + (pre ? 0 : 1) + tv_num_launches(pl, 1, 0.0);
+    return front_kernels(pl) + 1 + tv_num_launches(pl, 1, 0.0);
 }
 
 // timed segments of one iteration (dgamp_ct_profile_iteration): as above,
@@ -415,11 +402,6 @@ static int capture_iterations(dgamp_ct_plan_s* pl, int k, cudaGraphExec_t* out) 
 
 // the one-iteration graph, and the kGraphIters one when `iters` can use it
 static int ensure_graph(dgamp_ct_plan_s* pl, int iters) {
-    // the graphs bake in whether the probes were drawn before the solve, and where
-    if ((pl->graph || pl->graph_k) && (pl->graph_probe_pre != pl->probe_pre || pl->graph_ball != pl->ws.ball))
-        drop_graph(pl);
-    pl->graph_probe_pre = pl->probe_pre;
-    pl->graph_ball = pl->ws.ball;
     if (!pl->graph) {
         DGCT_TRY(capture_iterations(pl, 1, &pl->graph));
         pl->graph_cnn_gen = pl->cnn ? cnn_ws_generation(pl->cnn) : 0;
@@ -595,7 +577,6 @@ int dgamp_ct_get_tuning(dgamp_ct_plan_t pl, dgamp_ct_tuning* out) {
     out->tv_vrows = pl->tv_vrows;
     out->pj_band = pl->pj_band;
     out->pj_waves = pl->pj_waves;
-    out->probe_tv = pl->probe_tv;
     return DGAMP_CT_OK;
 }
 
@@ -607,7 +588,6 @@ int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
     if (t->tv_vrows >= 0 && t->tv_vrows != 2 && t->tv_vrows != 4 && t->tv_vrows != 8) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->pj_band >= 0 && t->pj_band != 0 && t->pj_band != 16 && t->pj_band != 32) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->pj_waves >= 0 && t->pj_waves != 1 && t->pj_waves != 2) return DGAMP_CT_ERR_INVALID_ARG;
-    if (t->probe_tv > 1) return DGAMP_CT_ERR_INVALID_ARG;
     if (t->pj_band > 0 && (pl->fan || !project_band_smem(pl, t->pj_band))) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (t->sino_fused == 1 && !sino_step_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
     if (t->sino_fused == 2 && !sino_toeplitz_eligible(pl)) return DGAMP_CT_ERR_UNSUPPORTED_GEOMETRY;
@@ -621,8 +601,6 @@ int dgamp_ct_set_tuning(dgamp_ct_plan_t pl, const dgamp_ct_tuning* t) {
     if (t->pj_seg > 0 && t->pj_band < 0) pl->pj_band = 0;     // a segment count picks the ray-group form
     if (t->pj_band >= 0) pl->pj_band = t->pj_band;
     if (t->pj_waves > 0) pl->pj_waves = t->pj_waves;
-    if (t->probe_tv >= 0) pl->probe_tv = t->probe_tv;
-    pl->probe_pre = 0;                                     // until the next solve draws its probes
     if (int rc = project_band_chunks(pl)) return rc;       // checked above: fits
     if (t->tv_vrows > 0) pl->tv_vrows = t->tv_vrows;
     drop_graph(pl);
@@ -745,11 +723,9 @@ int dgamp_ct_profile_iteration(dgamp_ct_plan_t pl, int32_t reps, double* h_ms, i
 
 int64_t dgamp_ct_solve_launches(dgamp_ct_plan_t pl, int32_t iters) {
     if (!pl || iters < 0) return -1;
-    // per iteration, plus the image staging and scalar init before (and the
-    // probes of every iteration when they are drawn first), and the
+    // per iteration, plus the image staging and scalar init before, and the
     // pending-divergence finish and the three V^-1 passes after
-    const bool pre = probes_before(pl, iters);
-    return (int64_t)iters * kernels_per_iteration(pl, pre) + 6 + (pre ? 1 : 0);
+    return (int64_t)iters * kernels_per_iteration(pl) + 6;
 }
 
 }  // extern "C"
@@ -800,23 +776,6 @@ static int solve_begin(dgamp_ct_plan_s* pl, const float* d_counts, double I0, cu
     return DGAMP_CT_OK;
 }
 
-// The probes of a solve drawn before its first iteration, where probes_before allows.
-static int prepare_probes(dgamp_ct_plan_s* pl, int iters, cudaStream_t st) {
-    const size_t N = (size_t)pl->N;
-    pl->probe_pre = 0;
-    if (!probes_before(pl, iters)) return DGAMP_CT_OK;
-    if (iters > pl->ball_iters) {
-        if (pl->ws.ball) DGCT_CUDA(cudaFree(pl->ws.ball));
-        pl->ws.ball = nullptr;
-        pl->ball_iters = 0;
-        DGCT_TRY(dalloc(&pl->ws.ball, (size_t)iters * N));
-        pl->ball_iters = iters;
-    }
-    DGCT_TRY(launch_probe_all(pl, iters, st));
-    pl->probe_pre = 1;
-    return DGAMP_CT_OK;
-}
-
 }  // namespace dgct
 
 extern "C" {
@@ -829,7 +788,6 @@ int dgamp_ct_solve_trace(dgamp_ct_plan_t pl, const float* d_counts, double I0, i
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = (size_t)pl->N;
     DGCT_TRY(solve_begin(pl, d_counts, I0, st));
-    DGCT_TRY(prepare_probes(pl, iters, st));
     for (int t = 0; t < iters; ++t) {
         DGCT_TRY(enqueue_iteration(pl, st));
         if (d_r_trace)   // r^t: the denoiser input of iteration t+1 (ws.r image 0)
@@ -856,7 +814,6 @@ int dgamp_ct_solve(dgamp_ct_plan_t pl, const float* d_counts, double I0, int32_t
     Workspace& w = pl->ws;
     const size_t N = (size_t)pl->N;
     DGCT_TRY(solve_begin(pl, d_counts, I0, st));
-    DGCT_TRY(prepare_probes(pl, iters, st));
     if (pl->opt.use_graph) {
         DGCT_TRY(launch_graphs(pl, iters, st));
     } else {

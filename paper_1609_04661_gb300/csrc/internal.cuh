@@ -157,7 +157,6 @@ struct Workspace {
     FanView* fan_views = nullptr;  // fan-beam plans: [n_views]
     int* pj_order = nullptr;       // banded A: views marching over rows, then over columns [n_views]
     float* pj_part = nullptr;      // banded A: per-band partial sums [ceil(n / 16)][n_views][n_det]
-    float* ball = nullptr;         // probes of a solve's iterations, drawn before it [ball_iters][n][n]
 };
 
 }  // namespace dgct
@@ -184,11 +183,6 @@ struct dgamp_ct_plan_s {
     int pj_band = 0;                       // A: 0 ray-group form; 16 or 32: lines per shared-memory band
     int pj_waves = 1;                      // A, banded form: full waves of blocks (1 or 2)
     int pj_c0 = 0, pj_c1 = 0;              // A, banded form: ray chunks per band of each orientation
-    int probe_tv = 1;                      // prox-TV solves: draw every iteration's probe before the solve
-    int probe_pre = 0;                     // the current solve does (set per solve)
-    int ball_iters = 0;                    // iterations ws.ball holds
-    int graph_probe_pre = 0;               // probe_pre and ws.ball when the graphs were captured
-    const float* graph_ball = nullptr;
     int pj_n0 = 0;                         // views that march over rows (the first pj_n0 of ws.pj_order)
     int fan = 0;                           // 1: flat-detector fan beam (dgamp_ct_plan_fan)
     int fan_stride = 0;                    // fan A^T tiles: ray stride of one pass (0: tiles not applicable)
@@ -434,13 +428,6 @@ int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st, in
 int launch_absmax(const dgamp_ct_plan_s* pl, const float* r, cudaStream_t st);
 bool tv_active(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg);
 int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_arg);
-bool tv_pair_kernel(const dgamp_ct_plan_s* pl);
-int launch_probe_all(const dgamp_ct_plan_s* pl, int T, cudaStream_t st);
-// this solve's probes were drawn before it: no probe kernel per iteration; the
-// two-image TV kernel forms r + eps b itself
-inline bool probe_pre_now(const dgamp_ct_plan_s* pl) {
-    return pl->probe_pre && pl->ws.ball && pl->opt.denoiser == 0 && tv_pair_kernel(pl);
-}
 int tv_set_smem_limits();
 int tv_autotune(dgamp_ct_plan_s* pl);
 int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, double lambda_arg, int i,

@@ -63,21 +63,6 @@ __global__ void k_probe_input(const float* __restrict__ r, float* __restrict__ r
                 (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// The probes of iterations 1..T of a solve, drawn before its first iteration:
-// ball[t - 1][i] is the b that k_probe_input draws in iteration t.
-__global__ void k_probe_all(float* __restrict__ ball, long long N, int T, unsigned slice, uint2 key) {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x, i0 = 4 * g;
-    if (i0 >= N) return;
-    for (int t = (int)blockIdx.y + 1; t <= T; t += (int)gridDim.y) {
-        const float4 b = probe4((unsigned)g, (unsigned)t, slice, key);
-        const float bb[4] = {b.x, b.y, b.z, b.w};
-        float* __restrict__ out = ball + (size_t)(t - 1) * (size_t)N;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (i0 + k < N) out[i0 + k] = bb[k];
-    }
-}
-
 // r + eps b beside r for every slice of a batch (prox-TV), 256 groups per block.
 __global__ void __launch_bounds__(256) k_probe_input_batch(const BatchSlice* __restrict__ sl,
                                                            const uint16_t* __restrict__ map) {
@@ -88,14 +73,6 @@ __global__ void __launch_bounds__(256) k_probe_input_batch(const BatchSlice* __r
 
 static uint2 probe_key(const dgamp_ct_plan_s* pl) {
     return make_uint2((unsigned)(pl->opt.seed & 0xffffffffu), (unsigned)(pl->opt.seed >> 32));
-}
-
-int launch_probe_all(const dgamp_ct_plan_s* pl, int T, cudaStream_t st) {
-    const long long groups = (pl->N + 3) / 4;
-    const dim3 grd((unsigned)((groups + 255) / 256), (unsigned)std::min(T, 65535));
-    k_probe_all<<<grd, 256, 0, st>>>(pl->ws.ball, pl->N, T, (unsigned)pl->opt.slice_id, probe_key(pl));
-    DGCT_LAUNCH_CHECK();
-    return DGAMP_CT_OK;
 }
 
 int launch_probe_input(const dgamp_ct_plan_s* pl, int t_arg, cudaStream_t st, int write_b) {
@@ -152,12 +129,6 @@ struct TvFinal {
     double* div_out;       // nullable
     int solve_mode;        // 1: update tau_x, the log and t in S
     int jvp;               // learned denoiser: dn[1] is J_D b (divergence b^T J_D b / N)
-    // the MC pair with the probes drawn before the solve (k_probe_all): the
-    // second image r + eps b is formed from r and b of iteration S->t instead
-    // of read (nullptr: read at r + N, b at bprobe)
-    const float* ball = nullptr;
-    int ball_iters = 1;
-    float eps_rel = 0.f;
 };
 
 // A block holds a region of kTvRW = 64 columns by RH = 4 WY rows of one image
@@ -565,15 +536,6 @@ __device__ __forceinline__ void tv_steps_block2(const float* __restrict__ rbase,
     pdl_wait();      // r, the duals and the scalars are earlier kernels' output
     const float lam = solve_lambda(S, c_tv, from_scalars, lambda_arg);
     const float inv_lam = lam > 0.f ? 1.0f / lam : 0.f;
-    // probes drawn before the solve: b of this iteration, and eps as
-    // k_probe_input forms it (its S->eps record by the first launch)
-    const float* __restrict__ bt = bprobe;
-    float eps = 0.f;
-    if (F.ball) {
-        bt = F.ball + (size_t)((S->t - 1u) % (unsigned)F.ball_iters) * N;
-        eps = F.eps_rel * fmaxf(__uint_as_float(S->rmax_bits), 1e-6f);
-        if (first && bx == 0 && by == 0 && threadIdx.x == 0) S->eps = (double)eps;
-    }
     float2 px[V][U], py[V][U], rl[V][U];
     unsigned inside = 0u, lastc = 0u, lastr = 0u;
 #pragma unroll
@@ -588,7 +550,7 @@ __device__ __forceinline__ void tv_steps_block2(const float* __restrict__ rbase,
             if (in) {
                 const size_t o = (size_t)gi * n + gj;
                 r0 = rbase[o];
-                r1 = F.ball ? fmaf(eps, bt[o], r0) : rbase[N + o];
+                r1 = rbase[N + o];
                 if (!first) {
                     p0 = pin[o];
                     p1 = pin[N + o];
@@ -650,10 +612,9 @@ __device__ __forceinline__ void tv_steps_block2(const float* __restrict__ rbase,
             const size_t o = (size_t)gi * n + gj;
             const float dv0 = px[v][u].x - pxl.x + py[v][u].x - pyu.x;
             const float dv1 = px[v][u].y - pxl.y + py[v][u].y - pyu.y;
-            const float r0 = rbase[o];
-            const float x0 = r0 - lam * dv0;
-            const float x1 = (F.ball ? fmaf(eps, bt[o], r0) : rbase[N + o]) - lam * dv1;
-            acc += (double)bt[o] * ((double)x1 - (double)x0);
+            const float x0 = rbase[o] - lam * dv0;
+            const float x1 = rbase[N + o] - lam * dv1;
+            acc += (double)bprobe[o] * ((double)x1 - (double)x0);
             float xo = x0;
             if (F.solve_mode && F.damp_x != 1.f) xo = F.damp_x * xo + (1.f - F.damp_x) * F.x_out[o];
             F.x_out[o] = xo;
@@ -836,14 +797,6 @@ int tv_num_launches(const dgamp_ct_plan_s* pl, int from_scalars, double lambda_a
     return ns > 0 ? ns : 1;
 }
 
-// A solve's MC pair runs every TV launch in the two-image kernel (the shapes
-// launch_steps maps to a paired kernel), with at least one Chambolle launch.
-bool tv_pair_kernel(const dgamp_ct_plan_s* pl) {
-    if (pl->opt.tv_metric || tv_step_launches(pl, 1, 0.0) <= 0) return false;
-    if (pl->tv_vrows == 2) return true;
-    return pl->tv_vrows == 4 && (pl->tv_rows == 32 || pl->tv_rows == 64);
-}
-
 struct TvLaunch {
     int n, nimg, first;
     const float* r;
@@ -950,12 +903,7 @@ int launch_tv_chunk(const dgamp_ct_plan_s* pl, int nimg, int from_scalars, doubl
     const float c_tv = (float)pl->opt.c_tv, lam = (float)lambda_arg;
     if (ns == 0)   // identity denoiser: x = r
         return launch_tv_final_x(pl, nimg, pl->ws.r, x_out, solve_mode, t_arg, div_out, st);
-    TvFinal F = make_tv_final(pl, x_out, solve_mode, t_arg, div_out);
-    if (solve_mode && nimg == 2 && probe_pre_now(pl)) {
-        F.ball = pl->ws.ball;
-        F.ball_iters = pl->ball_iters;
-        F.eps_rel = (float)pl->opt.eps_rel;
-    }
+    const TvFinal F = make_tv_final(pl, x_out, solve_mode, t_arg, div_out);
     const int steps = (i + 1) * KB <= pl->opt.k_tv ? KB : pl->opt.k_tv - i * KB;
     TvLaunch L{n, nimg, i == 0, pl->ws.r, buf[(i + 1) & 1], buf[i & 1], c_tv, lam, from_scalars, pl->ws.S,
                pl->ws.b};

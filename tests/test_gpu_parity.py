@@ -122,29 +122,6 @@ def test_banded_project_equals_sixteen_segments_at_512(dg, storage):
     assert np.array_equal(out[1][1], out[2][1])
 
 
-@pytest.mark.parametrize("storage,vrows", [(0, 2), (0, 4), (1, 2)])
-def test_probes_drawn_before_the_solve_change_nothing(dg, storage, vrows):
-    """probe_tv = 1 draws every iteration's probe before the solve and lets the
-    two-image TV kernel form r + eps b; probe_tv = 0 runs the probe kernel each
-    iteration.  Same b, same eps, same sums: identical bits, one launch
-    instead of T."""
-    n, nv, nd, T = 96, 24, 140, 7
-    g = Geometry(n, nv, nd)
-    x = _img(n, 6, "phantom")
-    y = np.random.default_rng(7).poisson(1e4 * np.exp(-joseph.forward_project(0.02 * x, g))).astype(np.float32)
-    out = {}
-    for probe_tv in (0, 1):
-        with dg.Plan(n, nv, nd, storage=storage, damp_x=0.5, damp_s=0.5) as pl:
-            pl.set_tuning(tv_vrows=vrows, tv_rows=64, probe_tv=probe_tv)
-            launches = pl.solve_launches(T)
-            mu, st = pl.solve(cu(y), 1e4, T, with_stats=True)
-            out[probe_tv] = (host(mu), st, launches)
-    assert np.array_equal(out[0][0], out[1][0])
-    for k in ("tau_x", "tau_r", "div"):
-        assert np.array_equal(np.asarray(out[0][1][k]), np.asarray(out[1][1][k])), k
-    assert out[1][2] == out[0][2] - T + 1
-
-
 def test_banded_project_tuning_checks(dg):
     with dg.Plan(64, 10, 95) as pl:
         for bad in ({"pj_band": 8}, {"pj_band": 64}, {"pj_waves": 3}):
