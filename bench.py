@@ -60,7 +60,7 @@ FALLBACK_HBM_GBS = 6800.0
 # 64-row regions of 2-row threads), the banded projector (32-line bands, one
 # wave) and the tile back-projection.
 TV_TRAFFIC = {"tv_kb": 10, "tv_rows": 64, "tv_vrows": 2, "bytes_per_iteration": 2112512 + 8421888 + 256}
-A_TRAFFIC = {"form": (32, 1), "bytes_per_launch": 2147328}      # (pj_band, pj_waves), or (0, pj_seg)
+A_TRAFFIC = {"form": (32, 1), "bytes_per_launch": 2145280}      # (pj_band, pj_waves), or (0, pj_seg)
 AT_TRAFFIC = {"bp_mode": 1, "bytes_per_launch": 1263872}
 
 
