@@ -244,18 +244,20 @@ typedef struct {
                              a block copies that many consecutive lines of the staged image
                              into shared memory and takes the steps inside them of a
                              contiguous chunk of rays, writing per-band partial sums that a
-                             second kernel adds in band order (the sums of the ray-group
-                             form with the same split; offered where a 16-line band of FP32
-                             fits in 100 KB, parallel beam only).  Setting pj_seg with
-                             pj_band < 0 picks the ray-group form */
+                             second kernel adds in band order (inside a solve with
+                             sino_fused = 2 the cluster sinogram kernel adds them itself).
+                             These are the sums of the ray-group form with the same split.
+                             Offered where a 16-line band of FP32 fits in 100 KB, parallel
+                             beam only.  Setting pj_seg with pj_band < 0 picks the
+                             ray-group form */
     int32_t pj_waves;     /* A, banded form: 1 or 2 full waves of resident blocks; the
                              rays are cut into that many chunks per band */
 } dgamp_ct_tuning;
 
 /* get: writes the plan's choices.  set: fields < 0 keep the current choice;
-   out-of-range values return INVALID_ARG, a sino_fused form the geometry
-   does not allow UNSUPPORTED_GEOMETRY (nothing is changed then).  Setting
-   drops the captured graph. */
+   out-of-range values return INVALID_ARG, a sino_fused form or a pj_band the
+   plan does not allow UNSUPPORTED_GEOMETRY (nothing is changed then).
+   Setting drops the captured graph. */
 int dgamp_ct_get_tuning(dgamp_ct_plan_t plan, dgamp_ct_tuning* out);
 int dgamp_ct_set_tuning(dgamp_ct_plan_t plan, const dgamp_ct_tuning* tuning);
 
