@@ -45,11 +45,12 @@ def test_struct_layouts_match_header(lib, tmp_path):
         pytest.skip("no C compiler")
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dgamp_ct.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(dgamp_ct_geometry),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(dgamp_ct_geometry),'
                     ' sizeof(dgamp_ct_options), sizeof(dgamp_ct_stats), offsetof(dgamp_ct_options, seed),'
                     ' offsetof(dgamp_ct_options, use_graph), offsetof(dgamp_ct_stats, tau_x_floored),'
                     ' offsetof(dgamp_ct_options, tv_metric), sizeof(dgamp_ct_fan_geometry),'
-                    ' offsetof(dgamp_ct_fan_geometry, det_spacing));'
+                    ' offsetof(dgamp_ct_fan_geometry, det_spacing), sizeof(dgamp_ct_tuning),'
+                    ' offsetof(dgamp_ct_tuning, pj_band), offsetof(dgamp_ct_tuning, pj_waves));'
                     'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
@@ -57,7 +58,8 @@ def test_struct_layouts_match_header(lib, tmp_path):
     want = [C.sizeof(binding.Geometry), C.sizeof(binding.Options), C.sizeof(binding.Stats),
             binding.Options.seed.offset, binding.Options.use_graph.offset,
             binding.Stats.tau_x_floored.offset, binding.Options.tv_metric.offset,
-            C.sizeof(binding.FanGeometry), binding.FanGeometry.det_spacing.offset]
+            C.sizeof(binding.FanGeometry), binding.FanGeometry.det_spacing.offset, C.sizeof(binding.Tuning),
+            binding.Tuning.pj_band.offset, binding.Tuning.pj_waves.offset]
     assert got == want
     o = binding.Options()
     assert lib.dgamp_ct_default_options(C.byref(o)) == 0
