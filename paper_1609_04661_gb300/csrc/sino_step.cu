@@ -306,12 +306,12 @@ __device__ __forceinline__ void sino_ct_block(const T* __restrict__ zraw, const 
             const float* __restrict__ pp = part + row0 + d_lo + o;
             float t = 0.f;
             int b = 0;
-            for (; b + 8 <= nb; b += 8) {
-                float pv[8];
+            for (; b + 16 <= nb; b += 16) {
+                float pv[16];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) pv[k] = pp[(size_t)(b + k) * M];
+                for (int k = 0; k < 16; ++k) pv[k] = pp[(size_t)(b + k) * M];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) t += pv[k];
+                for (int k = 0; k < 16; ++k) t += pv[k];
             }
             for (; b < nb; ++b) t += pp[(size_t)b * M];
             zs[d_lo + o] = as_stored(t * wv, zraw);
