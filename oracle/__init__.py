@@ -25,6 +25,8 @@ Modules, each citing the passage it follows:
 
 Everything runs in float64.  Functions whose result is not pinned to an
 independent fact are marked "parity unpinned" in their docstring; at present
-that is only the full CT reconstruction (:func:`oracle.gamp.ct_solve`), which
-the paper never reports on a synthetic input.
+those are the full CT reconstruction (:func:`oracle.gamp.ct_solve`), which
+the paper never reports on a synthetic input, and the state-evolution
+recursion run on CT data (:func:`oracle.state_evolution.ct_state_evolution`),
+whose recursion is pinned only through its i.i.d.-Gaussian reduction.
 """
