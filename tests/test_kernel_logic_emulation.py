@@ -12,7 +12,11 @@ checked on the GPU by their parity tests; here they pin the design on the CPU:
 * the metric prox-TV launch sequence (tv_metric.cu): a dual step from p = 0,
   then per step the three FFT passes with the MC pair packed as the real and
   imaginary parts of one complex image, then the dual step, must give the
-  oracle's tv_prox_metric for both images.
+  oracle's tv_prox_metric for both images;
+* the banded projector's work split (joseph.cu, project_band_chunks and
+  k_project_band): the chunks of each orientation's (view, bin) list cover
+  every ray once, and no chunk spans more views than the block's shared
+  table holds (8), for every occupancy the plan may see.
 """
 import ctypes as C
 import math
@@ -144,3 +148,41 @@ def test_metric_tv_launch_sequence(n, K):
     for im in range(2):
         ref = tv.tv_prox_metric(r[im], lam, K, lambda u: precond.vtv_inverse(u, g), precond.vtv_inverse_norm_bound(g))
         assert np.abs(X[im] - ref).max() < 1e-6
+
+
+# ------------------------------------------------ banded projector split ----
+BAND_MAX_VIEWS = 8          # kBandMaxViews: the block's shared view table
+
+
+def _band_chunks(total, n0, nv, nd):
+    """Chunks per band of each orientation, as project_band_chunks picks them."""
+    def fit(want, nvo):
+        if nvo == 0:
+            return 0
+        want = max(want, (nvo + BAND_MAX_VIEWS - 2) // (BAND_MAX_VIEWS - 1))
+        return min(max(want, 1), nvo * nd)
+    c0 = fit(int(math.floor(total * n0 / nv + 0.5)), n0)
+    return c0, fit(total - c0, nv - n0)
+
+
+@pytest.mark.parametrize("n,nv,nd", [(512, 64, 729), (37, 13, 55), (96, 37, 140), (16, 4096, 24), (300, 5, 1100),
+                                     (1024, 90, 1449), (2, 3, 3), (16, 2, 4096), (50, 1, 73)])
+@pytest.mark.parametrize("band", [16, 32])
+def test_band_split_covers_every_ray_once(n, nv, nd, band):
+    nb = (n + band - 1) // band
+    for n0 in sorted({0, nv // 2, nv - (nv // 3), nv}):
+        for bps in (1, 2, 3):
+            for waves in (1, 2):
+                total = max(2, waves * bps * 152 // nb)
+                c0, c1 = _band_chunks(total, n0, nv, nd)
+                assert c0 + c1 <= 65535
+                for nvo, C in ((n0, c0), (nv - n0, c1)):
+                    tot = nvo * nd
+                    assert (C == 0) == (nvo == 0)
+                    covered = 0
+                    for ci in range(C):
+                        lo, hi = tot * ci // C, tot * (ci + 1) // C
+                        assert lo == covered and hi > lo
+                        covered = hi
+                        assert (hi - 1) // nd - lo // nd + 1 <= BAND_MAX_VIEWS
+                    assert covered == tot
